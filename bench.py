@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 PSDF hot path; prints ONE JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+One step = one pass of the value+gradient path over the dense-clutter
+workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
+100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
+PSDF_Forward with the pose gradient (scan + epilogue kernels) followed by
+PSDF_Backward (pose and edge-endpoint gradients of sum(phi)).  The metric
+is pose x edge pair-evaluations per second.
+
+Under torchrun (N > 1) every rank evaluates its own 4,096 poses on the same
+scene (weak scaling, no data-path collective); the value is the total pair
+count over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PSDF pose×edge pair-evals/s (value+grad), learned-cull vs full scan, ≤1e-5 m err"
+UNIT = "pair-evals/s"
+WORKLOAD = "dense-clutter: 4096 poses x 100000 edges (25000 rectangles, 200x200 m), 0.6x0.4 m footprint"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(rank: int):
+    from paper_2607_04310_b300 import scenegen as sg
+    w = sg.dense_clutter(4)
+    if rank > 0:  # weak scaling: every rank gets its own queries on the same scene
+        g = sg.rng(4000 + rank)
+        w.poses = sg.poses_uniform(g, w.P, 0.0, 200.0)
+    return w
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _sources_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_04310_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        rec = d.get(kernel, {})
+        if rec.get("sources") == _sources_digest() and rec.get("workload") == workload:
+            return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# --------------------------------------------------------------------------
+def _oracle_rate(w, seconds: float, seed: int = 0):
+    import oracle
+    g = np.random.default_rng(seed)
+    n = 4
+    while True:
+        idx = g.choice(w.P, size=min(n, w.P), replace=False)
+        t0 = time.perf_counter()
+        oracle.psdf_eval(w.footprint, w.edges, w.offsets, w.poses[idx])
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= w.P:
+            break
+        n = min(w.P, max(n * 2, int(n * seconds / max(dt, 1e-3) * 1.05)))
+    return len(idx) * w.E / dt, len(idx), dt
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    w = _workload(0)
+    cores = oracle.max_threads()
+    per_step = max(1.0, 60.0 / max(a.steps + a.warmup, 1))
+    rate, n, dt = _oracle_rate(w, min(per_step, 10.0))
+    # each step: the oracle on a bounded sample of the same workload
+    times = []
+    g = np.random.default_rng(1)
+    for i in range(a.warmup + a.steps):
+        idx = g.choice(w.P, size=n, replace=False)
+        t0 = time.perf_counter()
+        oracle.psdf_eval(w.footprint, w.edges, w.offsets, w.poses[idx])
+        t = time.perf_counter() - t0
+        if i >= a.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = a.steps * n * w.E / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000.0 * tot / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_poses_per_step": int(n),
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d of 4096 poses x 100000 edges per step" % n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# B300 arm
+# --------------------------------------------------------------------------
+def run_b300(a, rank, world, local):
+    import torch
+    from paper_2607_04310_b300 import psdf, roofline
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    w = _workload(rank)
+    m = w.footprint.shape[0]
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    info = scene.info()
+    prm = psdf.make_params()
+    P = w.P
+    poses = torch.as_tensor(w.poses, device=dev).contiguous()
+    phi = torch.empty(P, device=dev)
+    dphi = torch.empty((P, 3), device=dev)
+    act = torch.empty(P, dtype=torch.int32, device=dev)
+    ws = psdf.workspace(P, dev)
+    gphi = torch.ones(P, device=dev)
+    gpose = torch.empty((P, 3), device=dev)
+    gedges = torch.zeros((w.E, 4), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ps):
+        psdf.psdf_eval_grad(w.footprint, scene, ps, prm, phi, dphi, act, ws, stream)
+        psdf.psdf_backward(w.footprint, scene, ps, prm, act, gphi, gpose, gedges, stream)
+
+    for _ in range(max(a.warmup, 3)):
+        step(poses)
+    torch.cuda.synchronize()
+    if psdf.psdf_workspace_status(ws, stream) != 0:
+        raise RuntimeError("device-side failure during warm-up")
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed between) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    psdf.psdf_profile_reset()
+    psdf.psdf_profile_enable(True)
+    with ClockSampler(local) as clk:
+        for i in range(a.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step(poses)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    psdf.psdf_profile_enable(False)
+    if pg:
+        pg.barrier()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = sum(ms) / len(ms)
+    n_scan, scan_ms = psdf.psdf_profile_read("scan")
+    n_epi, epi_ms = psdf.psdf_profile_read("epilogue")
+    n_bwd, bwd_ms = psdf.psdf_profile_read("backward")
+    psdf.psdf_profile_reset()
+    if psdf.psdf_workspace_status(ws, stream) != 0:
+        raise RuntimeError("device-side failure during the timed steps")
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    h_poses = torch.as_tensor(w.poses).pin_memory()
+    h_phi = torch.empty(P).pin_memory()
+    h_dphi = torch.empty((P, 3)).pin_memory()
+    h_act = torch.empty(P, dtype=torch.int32).pin_memory()
+    d_poses = torch.empty_like(poses)
+
+    def e2e_step():
+        d_poses.copy_(h_poses, non_blocking=True)
+        psdf.psdf_eval_grad(w.footprint, scene, d_poses, prm, phi, dphi, act, ws, stream)
+        psdf.psdf_backward(w.footprint, scene, d_poses, prm, act, gphi, gpose, gedges, stream)
+        h_phi.copy_(phi, non_blocking=True)
+        h_dphi.copy_(dphi, non_blocking=True)
+        h_act.copy_(act, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for i in range(a.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        e2e_step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    e_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    e2e_step_ms = sum(e_ms) / len(e_ms)
+
+    # ---- aggregate over ranks ----------------------------------------------
+    pairs = float(P) * w.E
+    t_max = ms_step
+    if pg:
+        t = torch.tensor([ms_step, e2e_step_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max, e2e_step_ms = float(t[0]), float(t[1])
+    value = world * pairs / (t_max / 1000.0)
+    e2e_value = world * pairs / (e2e_step_ms / 1000.0)
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (scan) ------------------------------
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = roofline.fp32_peak_tflops(props.multi_processor_count, sm_max)
+    flops_launch = roofline.flops_per_pose(m, w.offsets) * P
+    scan_avg_ms = scan_ms / max(n_scan, 1)
+    achieved = flops_launch / (scan_avg_ms / 1000.0) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "impl": "b300",
+        "config": {"workload": WORKLOAD, "poses_per_gpu": P, "edges": w.E,
+                   "obstacles": w.M, "tiles": int(info.n_tiles), "footprint_vertices": m,
+                   "path": "full scan (eval_grad + backward)",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "kernel": "scan", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz "
+                                    "(max SM clock in MEASURED_PEAKS.json)"
+                                    % (props.multi_processor_count, sm_max),
+                     "flops_per_launch": flops_launch, "avg_launch_ms": scan_avg_ms,
+                     "traffic": _traffic("scan", WORKLOAD)},
+        "kernels_ms_per_step": {"scan": scan_ms / a.steps, "epilogue": epi_ms / a.steps,
+                                "backward": bwd_ms / a.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * P,
+                "d2h_bytes_per_step": (4 + 12 + 4) * P, "ms_per_step": e2e_step_ms},
+        "gpu_launches": (n_scan + n_epi + n_bwd) + a.steps,  # + one key-init kernel per step
+        "clocks": clocks,
+    }
+    if not a.no_cpu_baseline and world == 1:
+        import oracle
+        rate, n, dt = _oracle_rate(w, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(),
+                                "kind": "oracle",
+                                "sample": "%d of 4096 poses x 100000 edges, %.1f s" % (n, dt)}
+    print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    rank, world, local = _dist()
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    return run_b300(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

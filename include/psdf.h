@@ -1,0 +1,197 @@
+/*
+ * psdf.h -- C ABI of the B300 (sm_103a) Polygonal Signed Distance Function
+ * library, libpsdf_b300.so.
+ *
+ * The library evaluates the PSDF of "GPU-Accelerated Polygonal Signed
+ * Distance Functions for Real-Time Collision Avoidance": the signed distance
+ * phi(x, E) between a convex polygonal robot footprint posed at
+ * x = (px, py, theta) and a set of obstacle boundary edges E, plus its
+ * gradient (Sec. III-B, Sec. IV, Alg. 1 PSDF_Forward / PSDF_Backward).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All floating point data is IEEE float32; all arithmetic on the device is
+ *    float32.
+ *  - Footprint: HOST pointer, float[m][2], the robot polygon in its local
+ *    frame, counter-clockwise, strictly convex, 3 <= m <= 16 (Assumption 1,
+ *    Sec. IV-A.1).  The library copies it by value into every launch.
+ *  - Poses and all per-pose outputs are DEVICE pointers owned by the caller:
+ *    poses float[P][3] = (px, py, theta); phi float[P]; dphi float[P][3];
+ *    active uint32[P].  The library never allocates caller outputs.
+ *  - Every evaluation call is asynchronous on `stream` (a cudaStream_t passed
+ *    as void*, NULL = the legacy default stream); nothing is read back to the
+ *    host and no device memory is allocated, so calls can be captured in a
+ *    CUDA graph after the scene exists.
+ *  - Return value: PSDF_OK (0) or one of the PSDF_ERR_* codes below.  Nothing
+ *    throws across the ABI; psdf_last_error() returns a message for the last
+ *    failing call on the calling thread.  Argument errors are detected on the
+ *    host before anything is launched.
+ *
+ * Active pair id (uint32): (edge << 8) | (kind << 4) | l, where `edge` is the
+ * edge index in the caller's original numbering (CSR row, or i * mbar + j for
+ * the padded layout), `l` a robot vertex / edge / axis index and `kind`:
+ *   0 robot vertex l -> obstacle edge (closest point on [A, B), or B for a
+ *     one-edge obstacle)               1 obstacle vertex A -> robot edge l
+ *   2 one-edge obstacle's B -> robot edge l
+ *   3/4 robot axis l: overlap = obstacle max - robot min / robot max -
+ *     obstacle min, extreme obstacle vertex A of `edge`      5/6 same, B
+ *   7/8 obstacle axis of `edge`: overlap = obstacle max - robot min (robot
+ *     extreme vertex l) / robot max - obstacle min (robot extreme vertex l).
+ * Among equal values the lowest (value, id) wins; across obstacles the one
+ * whose first edge has the lowest original index.  0xFFFFFFFF = none (empty
+ * scene).  Separated distances are compared through their squares.
+ */
+#ifndef PSDF_H
+#define PSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSDF_OK 0
+#define PSDF_ERR_ARG 1             /* null pointer, negative or oversize count  */
+#define PSDF_ERR_FOOTPRINT 2       /* m outside [3,16], not CCW strictly convex */
+#define PSDF_ERR_DEGENERATE_EDGE 3 /* an edge shorter than 1e-6 m               */
+#define PSDF_ERR_LAYOUT 4          /* bad offsets / mask, unclosed or non-convex
+                                      polygon, 2-edge obstacle                  */
+#define PSDF_ERR_CUDA 5            /* a CUDA runtime call failed                */
+#define PSDF_ERR_TIMEOUT 6         /* a bounded device-side wait ran out        */
+#define PSDF_ERR_CAPACITY 7        /* workspace too small / size limit exceeded */
+
+#define PSDF_PAIR_NONE 0xFFFFFFFFu
+#define PSDF_MAX_FOOTPRINT 16
+#define PSDF_MAX_OBSTACLE_EDGES 256
+
+typedef struct psdf_scene psdf_scene; /* opaque: owns the device copy of E  */
+
+/* Tolerances of Sec. IV-B / IV-C.  eps_seg: epsilon added to |v|^2 in the
+ * projection factor u; eps_axis: epsilon added to |u| in the obstacle-axis
+ * normal; eps_sat: the separating-axis tolerance.  eta <= 0 selects the hard
+ * minimum of the overlaps (the exact penetration depth, Sec. IV-C); eta > 0
+ * the log-sum-exp soft minimum of Eq. penetration_depth. */
+typedef struct {
+  float eps_seg;
+  float eps_axis;
+  float eps_sat;
+  float eta;
+} psdf_params;
+
+typedef struct {
+  int64_t n_edges;
+  int32_t n_obstacles;
+  int32_t n_tiles;
+  int32_t tile_edges;   /* maximum edges per tile                         */
+  int32_t max_obstacle_edges;
+  float bbox[4];        /* xmin, ymin, xmax, ymax of all endpoints          */
+  int64_t device_bytes; /* device memory owned by the scene                 */
+} psdf_scene_info;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *psdf_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int psdf_version(void);
+
+/* ---- scene preparation (Alg. 1 EncodeEdges + upload, Sec. IV-A.2) -------
+ * Validates the edge set, sorts obstacles along a Morton curve of their
+ * centroids, packs them into tiles of at most `tile_edges` edges (no obstacle
+ * straddles a tile; 0 selects 256), precomputes per-edge constants and
+ * uploads everything to the current device (synchronously, on `stream`).
+ *
+ * psdf_scene_create_csr: edges HOST float[E][4] rows (Ax, Ay, Bx, By) in the
+ * world frame; offsets HOST int32[M+1], obstacle i owns rows
+ * offsets[i] .. offsets[i+1]-1 (offsets[0] = 0, non-decreasing).  An obstacle
+ * is a single segment (1 edge) or a closed convex CCW polygon (>= 3 edges,
+ * B of each edge bit-equal to A of the next, wrapping around).  M = 0 gives an
+ * empty scene (phi = +inf).
+ *
+ * psdf_scene_create_padded: the paper's padded tensors A, B HOST
+ * float[Mbar][mbar][2] and mask S HOST uint8[Mbar][mbar]; the valid entries of
+ * each row must come first; rows with no valid entry are skipped.  Pair ids
+ * report i * mbar + j.
+ *
+ * `params` (nullable = all zero) fixes eps_seg and eps_axis, which enter the
+ * per-edge precompute (1 / (|u|^2 + eps_seg), 1 / (|u| + eps_axis)); every
+ * evaluation of the scene must pass the same two values (else PSDF_ERR_ARG).
+ * eps_sat and eta are free per call.
+ *
+ * The scene is freed with psdf_scene_destroy (NULL is accepted).  A scene may
+ * be evaluated from several streams at once; it is never written after
+ * creation. */
+int psdf_scene_create_csr(const float *edges, const int32_t *offsets, int32_t M,
+                          int32_t tile_edges, const psdf_params *params, void *stream,
+                          psdf_scene **out);
+int psdf_scene_create_padded(const float *A, const float *B, const uint8_t *S, int32_t Mbar,
+                             int32_t mbar, int32_t tile_edges, const psdf_params *params,
+                             void *stream, psdf_scene **out);
+int psdf_scene_destroy(psdf_scene *scene);
+int psdf_scene_get_info(const psdf_scene *scene, psdf_scene_info *info);
+
+/* ---- workspace ----------------------------------------------------------
+ * Device scratch needed by psdf_eval / psdf_eval_grad for P poses (one
+ * 64-bit min-key per pose, plus an error word).  The caller allocates it
+ * (>= 256-byte aligned) and may reuse it across calls on the same stream;
+ * calls that overlap on the GPU need separate workspaces. */
+size_t psdf_workspace_bytes(int64_t P);
+
+/* Synchronizes `stream` and reports a device-side failure recorded in the
+ * workspace by the last evaluation: PSDF_ERR_TIMEOUT if a bounded wait ran
+ * out (the affected poses then hold phi = NaN, active = PSDF_PAIR_NONE),
+ * else PSDF_OK. */
+int psdf_workspace_status(const void *workspace, void *stream);
+
+/* ---- PSDF_Forward (Alg. 1; Sec. IV-A.3 stages 1-4, Eq. psdf_value) -------
+ * phi[p] = min over obstacles of sd(P0(x_p), P_i) for every pose.  `active`
+ * (nullable) receives the active pair id.  Full scan over every edge tile. */
+int psdf_eval(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
+              int64_t P, const psdf_params *params, float *phi, uint32_t *active,
+              void *workspace, size_t workspace_bytes, void *stream);
+
+/* Value and gradient d phi / d (px, py, theta) through the active pair
+ * (the active-branch subgradient of Sec. IV-D; Alg. 1 PSDF_Backward with a
+ * unit seed).  dphi is float[P][3]; active is nullable. */
+int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scene *scene,
+                   const float *poses, int64_t P, const psdf_params *params, float *phi,
+                   float *dphi, uint32_t *active, void *workspace, size_t workspace_bytes,
+                   void *stream);
+
+/* ---- backward (vector-Jacobian product of phi, Sec. IV-D) ----------------
+ * Given the active pair ids of a previous psdf_eval / psdf_eval_grad with the
+ * same footprint, scene, poses and params, and an upstream gradient
+ * grad_phi[P]:
+ *   grad_pose[p][k] = grad_phi[p] * d phi_p / d pose_p[k]   (overwritten;
+ *                                                             nullable)
+ *   grad_edges[e][c] += sum_p grad_phi[p] * d phi_p / d edges[e][c]
+ *                       (accumulated; nullable; float[E][4] in the caller's
+ *                        original row order: CSR rows, or Mbar*mbar rows for a
+ *                        padded scene)
+ * A closed polygon's vertex is stored twice (A of its edge, B of the previous
+ * edge); its gradient is reported in the A slot and the B slots of closed
+ * polygons stay zero (the derivative with respect to one copy alone is not
+ * defined).  A one-edge obstacle's A and B get their own gradients.
+ * Accumulation into grad_edges uses float atomics (summation order varies). */
+int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
+                  const float *poses, int64_t P, const psdf_params *params,
+                  const uint32_t *active, const float *grad_phi, float *grad_pose,
+                  float *grad_edges, void *stream);
+
+/* ---- tracing -----------------------------------------------------------
+ * When enabled, the library brackets each launch of its kernels with CUDA
+ * events recorded on the launch stream (not during stream capture).
+ * psdf_profile_read synchronizes those events and returns, for the kernel
+ * named `kernel` ("scan", "epilogue", "backward", "all"), the number of
+ * launches and their summed device time since the last reset.  Names that
+ * match no kernel report zero launches. */
+int psdf_profile_enable(int on);
+int psdf_profile_reset(void);
+int psdf_profile_read(const char *kernel, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSDF_H */

@@ -1,0 +1,647 @@
+// PSDF_Forward / PSDF_Backward (Alg. 1) on sm_103a.
+//
+// Full-scan forward: grid = (pose blocks of 128) x (chunks of edge tiles).
+// One thread owns one pose; the CTA streams its chunk of obstacle-contiguous
+// edge tiles through shared memory with bulk asynchronous copies (TMA,
+// cp.async.bulk + mbarrier, double-buffered).  Every lane reads the same
+// edge record at the same time (shared-memory broadcast) and keeps all
+// per-obstacle reductions (min distance, SAT intervals, min overlap) in
+// registers, so no shuffles are needed inside the hot loop.  The per-pose
+// result is a 64-bit min-key (ordered value, obstacle rank) merged across
+// CTAs with one atomicMin per pose per CTA.  A per-pose epilogue re-derives
+// the active pair of the winning obstacle and its closed-form gradient.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "profile.h"
+#include "psdf_device.cuh"
+#include "psdf_internal.h"
+
+namespace psdf {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int code, const std::string &msg)
+{
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return PSDF_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy + mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 128;
+constexpr unsigned kWaitLimit = 1u << 22;  // try_wait polls before giving up
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy completing on an mbarrier; dst/src 16-byte
+// aligned and bytes a multiple of 16 (guaranteed by the tile layout)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar)
+{
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__global__ void init_keys_kernel(unsigned long long *keys, long long P, int *err)
+{
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) keys[i] = ~0ull;
+  if (i == 0) *err = 0;
+}
+
+// Full scan: each CTA = kScanThreads poses x tiles [t0, t1).
+template <int M>
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(
+    FootprintK F, ParamsK prm, const float *__restrict__ poses, long long P,
+    const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob, int n_tiles,
+    int tiles_per_chunk, int blob_cap, unsigned long long *__restrict__ keys,
+    int *__restrict__ err)
+{
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *const buf0 = smem + 128;  // buffer b lives at buf0 + b * blob_cap
+
+  const int t0 = blockIdx.y * tiles_per_chunk;
+  const int t1 = min(n_tiles, t0 + tiles_per_chunk);
+  if (t0 >= t1) return;  // uniform over the CTA
+
+  const long long p = (long long)blockIdx.x * kScanThreads + threadIdx.x;
+  const bool live = p < P;
+  float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
+  if (live) {
+    px = poses[3 * p];
+    py = poses[3 * p + 1];
+    sincosf(poses[3 * p + 2], &s, &c);
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const TileHdr h = tiles[t0];
+    mbar_arrive_expect_tx(&bars[0], (unsigned)h.blob_bytes);
+    bulk_g2s(buf0, blob + h.blob_off, (unsigned)h.blob_bytes, &bars[0]);
+  }
+  unsigned pending = 1u;  // bit b: a copy into buffer b is in flight
+  unsigned phase = 0u;    // bit b: parity of buffer b's next completion
+  unsigned long long best = ~0ull;
+  bool ok = true;
+  for (int t = t0; t < t1; ++t) {
+    const int b = (t - t0) & 1;
+    if (t + 1 < t1) {
+      if (threadIdx.x == 0) {
+        const TileHdr hn = tiles[t + 1];
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bars[b ^ 1], (unsigned)hn.blob_bytes);
+        bulk_g2s(buf0 + (b ^ 1) * blob_cap, blob + hn.blob_off, (unsigned)hn.blob_bytes,
+                 &bars[b ^ 1]);
+      }
+      pending |= 1u << (b ^ 1);
+    }
+    bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
+    got = __syncthreads_and(got);
+    if (!got) {
+      ok = false;
+      break;
+    }
+    pending &= ~(1u << b);
+    phase ^= 1u << b;
+    const TileHdr h = tiles[t];
+    const unsigned char *tb = buf0 + b * blob_cap;
+    const int4 *ob = reinterpret_cast<const int4 *>(tb);
+    const float4 *vt = reinterpret_cast<const float4 *>(tb + 16 * h.n_obs);
+    for (int o = 0; o < h.n_obs; ++o) {
+      const int4 rec = ob[o];
+      const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
+      const unsigned long long key = pack_key(v, rec.z);
+      best = key < best ? key : best;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    // record the failure, then give copies still in flight a bounded chance
+    // to land before the CTA's shared memory is released
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    for (int q = 0; q < 2; ++q)
+      if ((pending >> q) & 1u) (void)mbar_wait_bounded(&bars[q], (phase >> q) & 1u);
+    return;
+  }
+  if (live && best != ~0ull) atomicMin(&keys[p], best);
+}
+
+// Per-pose epilogue: value, active pair, optional pose gradient.
+template <int M>
+__global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
+                                const float *__restrict__ poses, long long P,
+                                const ObsRec *__restrict__ obs, const float4 *__restrict__ vtx,
+                                const int *__restrict__ far, const int *__restrict__ row2obs,
+                                const unsigned long long *__restrict__ keys,
+                                const int *__restrict__ err, float *__restrict__ phi,
+                                float *__restrict__ dphi, unsigned *__restrict__ active)
+{
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const unsigned long long key = keys[p];
+  if (*err) {
+    const float nan = __int_as_float(0x7fc00000);
+    phi[p] = nan;
+    if (active) active[p] = PSDF_PAIR_NONE;
+    if (dphi) dphi[3 * p] = dphi[3 * p + 1] = dphi[3 * p + 2] = nan;
+    return;
+  }
+  if (key == ~0ull) {  // no obstacle at all
+    phi[p] = kInf;
+    if (active) active[p] = PSDF_PAIR_NONE;
+    if (dphi) dphi[3 * p] = dphi[3 * p + 1] = dphi[3 * p + 2] = 0.f;
+    return;
+  }
+  const float px = poses[3 * p], py = poses[3 * p + 1];
+  float s, c;
+  sincosf(poses[3 * p + 2], &s, &c);
+  const int rank = (int)(unsigned)(key & 0xffffffffu);
+  const int sidx = row2obs[rank];
+  const ObsRec o = obs[sidx];
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  const Active a = obstacle_detail<M>(F, px, py, c, s, vt, o.n, o.orig_first, prm.eps_sat);
+  phi[p] = a.separated ? sqrtf(a.val) : a.val;
+  if (active) active[p] = a.pid;
+  if (dphi) {
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (a.separated || a.dlt > 0.f) {
+      const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n,
+                                    o.orig_first, a.kind, a.l, a.k, a.t, eps_axis);
+      g0 = g.gp[0];
+      g1 = g.gp[1];
+      g2 = g.gp[2];
+    }
+    dphi[3 * p] = g0;
+    dphi[3 * p + 1] = g1;
+    dphi[3 * p + 2] = g2;
+  }
+}
+
+// Overlap of a penetration-kind active pair (to find the flat branch of
+// max(delta, 0)); same arithmetic as the scan.
+template <int M>
+__device__ float active_overlap(const FootprintK &F, float px, float py, float c, float s,
+                                const float4 *vt, int n, int kind, int l, int k)
+{
+  const bool seg = (n == 1);
+  if (kind >= kRAxisOMax && kind <= kRAxisRMaxB) {
+    const bool isB = (kind == kRAxisOMaxB || kind == kRAxisRMaxB);
+    const float4 a = vt[2 * k], b = vt[1];
+    const V2 X = isB ? to_local(b.z, b.w, px, py, c, s) : to_local(a.x, a.y, px, py, c, s);
+    float nx = 0.f, ny = 0.f, lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+      if (q == l) { nx = F.nx[q]; ny = F.ny[q]; lo = F.alo[q]; hi = F.ahi[q]; }
+    const float pr = __fmaf_rn(X.x, nx, __fmul_rn(X.y, ny));
+    return (kind == kRAxisOMax || kind == kRAxisOMaxB) ? __fsub_rn(pr, lo) : __fsub_rn(hi, pr);
+  }
+  const float4 ak = vt[2 * k], bk = vt[2 * k + 1];
+  const V2 A = to_local(ak.x, ak.y, px, py, c, s);
+  V2 B;
+  if (seg) B = to_local(bk.z, bk.w, px, py, c, s);
+  else {
+    const float4 an = vt[2 * ((k + 1) % n)];
+    B = to_local(an.x, an.y, px, py, c, s);
+  }
+  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+  float smin = kInf, smax = -kInf;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const float wx = __fsub_rn(F.vx[q], A.x), wy = __fsub_rn(F.vy[q], A.y);
+    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+    smin = fminf(smin, sl);
+    smax = fmaxf(smax, sl);
+  }
+  return (kind == kOAxisOMax) ? __fmaf_rn(-smin, ak.w, bk.y) : __fmaf_rn(smax, ak.w, -bk.x);
+}
+
+// Recomputes the projection parameter of a distance-kind active pair.
+template <int M>
+__device__ float active_t(const FootprintK &F, float px, float py, float c, float s,
+                          const float4 *vt, int n, int kind, int l, int k)
+{
+  float vx = 0.f, vy = 0.f, ex = 0.f, ey = 0.f, ie = 0.f;
+#pragma unroll
+  for (int q = 0; q < M; ++q)
+    if (q == l) { vx = F.vx[q]; vy = F.vy[q]; ex = F.ex[q]; ey = F.ey[q]; ie = F.inv_e2[q]; }
+  const bool seg = (n == 1);
+  if (kind == kVertEdge) {
+    const float4 ak = vt[2 * k];
+    const V2 A = to_local(ak.x, ak.y, px, py, c, s);
+    V2 B;
+    if (seg) B = to_local(vt[1].z, vt[1].w, px, py, c, s);
+    else {
+      const float4 an = vt[2 * ((k + 1) % n)];
+      B = to_local(an.x, an.y, px, py, c, s);
+    }
+    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const float wx = __fsub_rn(vx, A.x), wy = __fsub_rn(vy, A.y);
+    return __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak.z));
+  }
+  const V2 X = (kind == kObsVRobotEdge) ? to_local(vt[2 * k].x, vt[2 * k].y, px, py, c, s)
+                                        : to_local(vt[1].z, vt[1].w, px, py, c, s);
+  const float wx = __fsub_rn(vx, X.x), wy = __fsub_rn(vy, X.y);
+  return __fmul_rn(-__fmaf_rn(wx, ex, __fmul_rn(wy, ey)), ie);
+}
+
+template <int M>
+__global__ void backward_kernel(FootprintK F, float eps_axis, const float *__restrict__ poses,
+                                long long P, const ObsRec *__restrict__ obs,
+                                const float4 *__restrict__ vtx, const int *__restrict__ far,
+                                const int *__restrict__ row2obs, long long rows_total,
+                                const unsigned *__restrict__ active,
+                                const float *__restrict__ grad_phi, float *__restrict__ grad_pose,
+                                float *__restrict__ grad_edges)
+{
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const unsigned pid = active[p];
+  const float gphi = grad_phi[p];
+  const long long row = pid >> kPairShiftEdge;
+  const int kind = (pid >> kPairShiftKind) & 0xF;
+  const int l = pid & 0xF;
+  int sidx = -1;
+  if (pid != PSDF_PAIR_NONE && row < rows_total && l < F.m && kind <= kOAxisRMax)
+    sidx = row2obs[row];
+  if (sidx < 0) {
+    if (grad_pose) grad_pose[3 * p] = grad_pose[3 * p + 1] = grad_pose[3 * p + 2] = 0.f;
+    return;
+  }
+  const ObsRec o = obs[sidx];
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  int k = (int)(row - o.orig_first);
+  if (kind == kObsBRobotEdge || kind == kRAxisOMaxB || kind == kRAxisRMaxB) k = 0;
+  const float px = poses[3 * p], py = poses[3 * p + 1];
+  float s, c;
+  sincosf(poses[3 * p + 2], &s, &c);
+  float t = 0.f;
+  bool flat = false;
+  if (kind <= kObsBRobotEdge) {
+    t = active_t<M>(F, px, py, c, s, vt, o.n, kind, l, k);
+  } else {
+    flat = !(active_overlap<M>(F, px, py, c, s, vt, o.n, kind, l, k) > 0.f);
+  }
+  if (flat) {
+    if (grad_pose) grad_pose[3 * p] = grad_pose[3 * p + 1] = grad_pose[3 * p + 2] = 0.f;
+    return;
+  }
+  const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first,
+                                kind, l, k, t, eps_axis);
+  if (grad_pose) {
+    grad_pose[3 * p] = gphi * g.gp[0];
+    grad_pose[3 * p + 1] = gphi * g.gp[1];
+    grad_pose[3 * p + 2] = gphi * g.gp[2];
+  }
+  if (grad_edges) {
+    for (int i = 0; i < g.nrow; ++i) {
+      atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]], gphi * g.gx[i]);
+      atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1], gphi * g.gy[i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DeviceInfo {
+  int sms = 0;
+};
+
+DeviceInfo device_info()
+{
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1);
+  if (cache[dev].sms == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev].sms = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+}  // namespace
+
+// Footprint validation (Assumption 1) and constants.
+int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F)
+{
+  if (!fp) return fail(PSDF_ERR_ARG, "footprint is NULL");
+  if (m < 3 || m > kMaxM)
+    return fail(PSDF_ERR_FOOTPRINT, "footprint must have 3..16 vertices, got " + std::to_string(m));
+  std::memset(F, 0, sizeof(*F));
+  F->m = m;
+  double turn = 0.0, rad = 0.0;
+  for (int l = 0; l < m; ++l) {
+    if (!std::isfinite(fp[2 * l]) || !std::isfinite(fp[2 * l + 1]))
+      return fail(PSDF_ERR_FOOTPRINT, "footprint has a non-finite vertex");
+    const int ln = (l + 1) % m, l2 = (l + 2) % m;
+    const float ex = fp[2 * ln] - fp[2 * l], ey = fp[2 * ln + 1] - fp[2 * l + 1];
+    const float fx = fp[2 * l2] - fp[2 * ln], fy = fp[2 * l2 + 1] - fp[2 * ln + 1];
+    const double len = std::sqrt((double)ex * ex + (double)ey * ey);
+    if (len < 1e-6) return fail(PSDF_ERR_FOOTPRINT, "footprint edge shorter than 1e-6 m");
+    const double cr = (double)ex * fy - (double)ey * fx, dt = (double)ex * fx + (double)ey * fy;
+    if (!(cr > 0.0))
+      return fail(PSDF_ERR_FOOTPRINT, "footprint is not strictly convex counter-clockwise");
+    turn += std::atan2(cr, dt);
+    F->vx[l] = fp[2 * l];
+    F->vy[l] = fp[2 * l + 1];
+    F->ex[l] = ex;
+    F->ey[l] = ey;
+    F->inv_e2[l] = (float)(1.0 / ((double)ex * ex + (double)ey * ey + eps_seg));
+    F->nx[l] = (float)(ey / len);
+    F->ny[l] = (float)(-ex / len);
+    rad = std::max(rad, std::sqrt((double)fp[2 * l] * fp[2 * l] + (double)fp[2 * l + 1] * fp[2 * l + 1]));
+  }
+  if (std::fabs(turn - 2.0 * M_PI) > 1e-6)
+    return fail(PSDF_ERR_FOOTPRINT, "footprint does not turn exactly once");
+  for (int l = 0; l < m; ++l) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int q = 0; q < m; ++q) {
+      const double pr = (double)F->vx[q] * F->nx[l] + (double)F->vy[q] * F->ny[l];
+      lo = std::min(lo, pr);
+      hi = std::max(hi, pr);
+    }
+    F->alo[l] = (float)lo;
+    F->ahi[l] = (float)hi;
+  }
+  F->radius = (float)(rad * (1.0 + 1e-6));
+  return PSDF_OK;
+}
+
+static int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
+                           const psdf_params *params, void *workspace, size_t ws_bytes)
+{
+  if (!scene) return fail(PSDF_ERR_ARG, "scene is NULL");
+  if (P < 0) return fail(PSDF_ERR_ARG, "P < 0");
+  if (P > ((int64_t)1 << 40)) return fail(PSDF_ERR_CAPACITY, "P too large");
+  if (P > 0 && !poses) return fail(PSDF_ERR_ARG, "poses is NULL");
+  if (!params) return fail(PSDF_ERR_ARG, "params is NULL");
+  if (params->eps_seg != scene->eps_seg || params->eps_axis != scene->eps_axis)
+    return fail(PSDF_ERR_ARG,
+                "params eps_seg/eps_axis differ from the values the scene was prepared with");
+  if (!(params->eps_sat >= 0.f)) return fail(PSDF_ERR_ARG, "eps_sat must be >= 0");
+  if (params->eta > 0.f) return fail(PSDF_ERR_ARG, "soft-min penetration (eta > 0) is not available in this build");
+  if (P > 0) {
+    if (!workspace) return fail(PSDF_ERR_ARG, "workspace is NULL");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(PSDF_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < psdf_workspace_bytes(P))
+      return fail(PSDF_ERR_CAPACITY, "workspace smaller than psdf_workspace_bytes(P)");
+  }
+  cudaPointerAttributes attr;
+  if (P > 0 && cudaPointerGetAttributes(&attr, poses) == cudaSuccess &&
+      attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(PSDF_ERR_ARG, "poses must be a device pointer");
+  cudaGetLastError();
+  return PSDF_OK;
+}
+
+template <int M>
+static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                       const psdf_params *prm, float *phi, float *dphi, unsigned *active,
+                       void *ws, cudaStream_t st)
+{
+  int *err = reinterpret_cast<int *>(ws);
+  unsigned long long *keys =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(ws) + 256);
+  ParamsK pk{prm->eps_sat, prm->eta};
+  const int init_blocks = (int)((P + 255) / 256);
+  init_keys_kernel<<<init_blocks, 256, 0, st>>>(keys, P, err);
+  if (sc->n_tiles > 0) {
+    const DeviceInfo di = device_info();
+    const long long pose_blocks = (P + kScanThreads - 1) / kScanThreads;
+    if (pose_blocks > 2147483647LL) return fail(PSDF_ERR_CAPACITY, "too many poses for one launch");
+    // aim for about 32 CTAs per SM in total (several waves of resident CTAs)
+    const long long target = (long long)di.sms * 32;
+    long long tpc = (pose_blocks * sc->n_tiles + target - 1) / target;
+    tpc = std::max<long long>(1, std::min<long long>(tpc, sc->n_tiles));
+    const long long chunks = (sc->n_tiles + tpc - 1) / tpc;
+    if (chunks > 65535) return fail(PSDF_ERR_CAPACITY, "too many tile chunks");
+    const int blob_cap = (sc->max_blob_bytes + 127) / 128 * 128;
+    const size_t smem = 128 + 2 * (size_t)blob_cap;
+    dim3 grid((unsigned)pose_blocks, (unsigned)chunks);
+    ProfileScope prof("scan", st);
+    scan_kernel<M><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, sc->d_tiles, sc->d_blob,
+                                                     sc->n_tiles, (int)tpc, blob_cap, keys, err);
+  }
+  {
+    ProfileScope prof("epilogue", st);
+    epilogue_kernel<M><<<init_blocks, 256, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
+                                                    sc->d_vtx, sc->d_far, sc->d_row2obs, keys,
+                                                    err, phi, dphi, active);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return PSDF_OK;
+}
+
+template <int M>
+static int launch_backward(const FootprintK &F, const psdf_scene *sc, const float *poses,
+                           long long P, const unsigned *active, const float *grad_phi,
+                           float *grad_pose, float *grad_edges, cudaStream_t st)
+{
+  const int blocks = (int)((P + 255) / 256);
+  ProfileScope prof("backward", st);
+  backward_kernel<M><<<blocks, 256, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_obs, sc->d_vtx,
+                                             sc->d_far, sc->d_row2obs, sc->rows_total, active,
+                                             grad_phi, grad_pose, grad_edges);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return PSDF_OK;
+}
+
+// Runtime footprint size -> compile-time M (fully unrolled robot loops).
+template <template <int> class Fn, class... Args>
+static int dispatch_m(int m, Args &&...args)
+{
+  switch (m) {
+    case 3: return Fn<3>::run(args...);
+    case 4: return Fn<4>::run(args...);
+    case 5: return Fn<5>::run(args...);
+    case 6: return Fn<6>::run(args...);
+    case 7: return Fn<7>::run(args...);
+    case 8: return Fn<8>::run(args...);
+    case 9: return Fn<9>::run(args...);
+    case 10: return Fn<10>::run(args...);
+    case 11: return Fn<11>::run(args...);
+    case 12: return Fn<12>::run(args...);
+    case 13: return Fn<13>::run(args...);
+    case 14: return Fn<14>::run(args...);
+    case 15: return Fn<15>::run(args...);
+    case 16: return Fn<16>::run(args...);
+    default: return fail(PSDF_ERR_FOOTPRINT, "unsupported footprint size");
+  }
+}
+
+template <int M>
+struct EvalCall {
+  static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                 const psdf_params *prm, float *phi, float *dphi, unsigned *active, void *ws,
+                 cudaStream_t st)
+  {
+    return launch_eval<M>(F, sc, poses, P, prm, phi, dphi, active, ws, st);
+  }
+};
+
+template <int M>
+struct BackwardCall {
+  static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                 const unsigned *active, const float *grad_phi, float *grad_pose,
+                 float *grad_edges, cudaStream_t st)
+  {
+    return launch_backward<M>(F, sc, poses, P, active, grad_phi, grad_pose, grad_edges, st);
+  }
+};
+
+static int eval_common(const float *footprint, int32_t m, const psdf_scene *scene,
+                       const float *poses, int64_t P, const psdf_params *params, float *phi,
+                       float *dphi, unsigned *active, void *ws, size_t ws_bytes, void *stream)
+{
+  int rc = check_eval_args(scene, poses, P, params, ws, ws_bytes);
+  if (rc) return rc;
+  if (P > 0 && !phi) return fail(PSDF_ERR_ARG, "phi is NULL");
+  FootprintK F;
+  rc = make_footprint(footprint, m, scene->eps_seg, &F);
+  if (rc) return rc;
+  if (P == 0) return PSDF_OK;
+  return dispatch_m<EvalCall>(m, F, scene, poses, (long long)P, params, phi, dphi, active, ws,
+                              (cudaStream_t)stream);
+}
+
+}  // namespace psdf
+
+using namespace psdf;
+
+extern "C" int psdf_eval(const float *footprint, int32_t m, const psdf_scene *scene,
+                         const float *poses, int64_t P, const psdf_params *params, float *phi,
+                         uint32_t *active, void *workspace, size_t workspace_bytes, void *stream)
+{
+  return eval_common(footprint, m, scene, poses, P, params, phi, nullptr, active, workspace,
+                     workspace_bytes, stream);
+}
+
+extern "C" int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scene *scene,
+                              const float *poses, int64_t P, const psdf_params *params,
+                              float *phi, float *dphi, uint32_t *active, void *workspace,
+                              size_t workspace_bytes, void *stream)
+{
+  if (P > 0 && !dphi) return fail(PSDF_ERR_ARG, "dphi is NULL");
+  return eval_common(footprint, m, scene, poses, P, params, phi, dphi, active, workspace,
+                     workspace_bytes, stream);
+}
+
+extern "C" int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
+                             const float *poses, int64_t P, const psdf_params *params,
+                             const uint32_t *active, const float *grad_phi, float *grad_pose,
+                             float *grad_edges, void *stream)
+{
+  int rc = check_eval_args(scene, poses, P, params, (void *)256, (size_t)-1);
+  if (rc) return rc;
+  if (P > 0 && (!active || !grad_phi)) return fail(PSDF_ERR_ARG, "active or grad_phi is NULL");
+  FootprintK F;
+  rc = make_footprint(footprint, m, scene->eps_seg, &F);
+  if (rc) return rc;
+  if (P == 0) return PSDF_OK;
+  return dispatch_m<BackwardCall>(m, F, scene, poses, (long long)P, active, grad_phi, grad_pose,
+                                  grad_edges, (cudaStream_t)stream);
+}
+
+extern "C" const char *psdf_last_error(void) { return g_err.c_str(); }
+
+extern "C" int psdf_version(void) { return 100; }
+
+extern "C" size_t psdf_workspace_bytes(int64_t P)
+{
+  if (P < 1) P = 1;
+  return 256 + (size_t)((8 * P + 255) / 256 * 256);
+}
+
+extern "C" int psdf_workspace_status(const void *workspace, void *stream)
+{
+  if (!workspace) return fail(PSDF_ERR_ARG, "workspace is NULL");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int v = 0;
+  e = cudaMemcpy(&v, workspace, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(workspace status)");
+  if (v) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out (edge tile copy)");
+  return PSDF_OK;
+}

@@ -1,0 +1,455 @@
+// Device arithmetic of the PSDF (Sec. IV-A.3 stages 1-4), float32.
+//
+// Every operation that feeds a per-obstacle value is written with explicit
+// round-to-nearest intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, ...), which
+// the compiler may not contract or reassociate.  The scan kernel (values
+// only) and the per-pose epilogue (active pair + gradient) therefore compute
+// bit-identical values for the same (pose, obstacle): the epilogue recovers
+// exactly the minimum the scan selected.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psdf_internal.h"
+
+namespace psdf {
+
+struct V2 {
+  float x, y;
+};
+
+constexpr float kInf = __builtin_huge_valf();
+
+// Stage 1: world -> robot-local frame, R(theta)^T (X - p).
+__device__ __forceinline__ V2 to_local(float X, float Y, float px, float py, float c, float s)
+{
+  const float dx = __fsub_rn(X, px), dy = __fsub_rn(Y, py);
+  V2 r;
+  r.x = __fmaf_rn(c, dx, __fmul_rn(s, dy));
+  r.y = __fmaf_rn(c, dy, -__fmul_rn(s, dx));
+  return r;
+}
+
+// Total order on float values as unsigned bits (-0 is folded onto +0 first
+// so that the order matches IEEE comparison).
+__device__ __forceinline__ uint32_t ordered_bits(float v)
+{
+  const uint32_t b = __float_as_uint(__fadd_rn(v, 0.0f));
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float from_ordered_bits(uint32_t o)
+{
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Min-key of one obstacle: (ordered value << 32) | rank, rank = the caller's
+// row of the obstacle's first edge.  Its minimum over obstacles realises
+// Eq. psdf_value with the lowest-rank tie-break.
+__device__ __forceinline__ unsigned long long pack_key(float v, int rank)
+{
+  return ((unsigned long long)ordered_bits(v) << 32) | (unsigned)rank;
+}
+
+__device__ __forceinline__ unsigned make_pid(int edge, int kind, int l)
+{
+  return ((unsigned)edge << kPairShiftEdge) | ((unsigned)kind << kPairShiftKind) | (unsigned)l;
+}
+
+// Stage 4 (Sec. IV-D), hard penetration: value compared across obstacles.
+// Separated -> squared distance (monotone in d); otherwise -max(delta_min, 0).
+__device__ __forceinline__ float synth_value(float d2min, float dmin_axes, float eps_sat)
+{
+  const bool separated = dmin_axes < -eps_sat;
+  return separated ? d2min : -fmaxf(dmin_axes, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// value-only evaluation of one obstacle (the scan's inner loop)
+// ---------------------------------------------------------------------------
+// One edge of a closed polygon, from A (= vertex k, local) to B (= vertex
+// k+1, local).  Accumulates: d2min (squared separation, Sec. IV-B), the
+// obstacle's projections on the robot axes (pmax/pmin, Sec. IV-C) and the
+// overlap on this edge's own axis.
+template <int M, bool SEG>
+__device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float inv_len2,
+                                          float inv_len, float alpha_p, float beta_p,
+                                          float (&pmax)[M], float (&pmin)[M], float &d2min,
+                                          float &dlt)
+{
+  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+  float smin = kInf, smax = -kInf;
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    // robot vertex l -> obstacle edge: t = clamp((v - A).u / (|u|^2 + eps))
+    const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
+    const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), inv_len2));
+    float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
+    if (SEG) {
+      // a segment's far endpoint is its own vertex: use it exactly
+      rx = (t == 1.0f) ? __fsub_rn(F.vx[l], B.x) : rx;
+      ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
+    }
+    const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+    // polygon: t == 1 is the next edge's start vertex, counted there
+    d2min = (SEG || t < 1.0f) ? fminf(d2min, d2) : d2min;
+    // robot vertex projected on rot90(u), measured from A (obstacle axis)
+    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+    smin = fminf(smin, sl);
+    smax = fmaxf(smax, sl);
+    // obstacle vertex A -> interior of robot edge l
+    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    d2min = (tp > 0.0f && tp < 1.0f) ? fminf(d2min, d2p) : d2min;
+    // obstacle vertex A on the robot axis n_l
+    const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
+    pmax[l] = fmaxf(pmax[l], pr);
+    pmin[l] = fminf(pmin[l], pr);
+  }
+  // overlap on this edge's axis: obstacle interval [alpha', beta'] vs the
+  // robot interval [smin, smax] / (|u| + eps)
+  const float da = __fmaf_rn(-smin, inv_len, beta_p);
+  const float db = __fmaf_rn(smax, inv_len, -alpha_p);
+  dlt = fminf(dlt, fminf(da, db));
+}
+
+// A segment's B endpoint as an extra obstacle vertex: robot-edge distances
+// and robot-axis projections.
+template <int M>
+__device__ __forceinline__ void extra_vertex(const FootprintK &F, V2 X, float (&pmax)[M],
+                                             float (&pmin)[M], float &d2min)
+{
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float wx = __fsub_rn(F.vx[l], X.x), wy = __fsub_rn(F.vy[l], X.y);
+    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    d2min = (tp > 0.0f && tp < 1.0f) ? fminf(d2min, d2p) : d2min;
+    const float pr = __fmaf_rn(X.x, F.nx[l], __fmul_rn(X.y, F.ny[l]));
+    pmax[l] = fmaxf(pmax[l], pr);
+    pmin[l] = fminf(pmin[l], pr);
+  }
+}
+
+template <int M>
+__device__ __forceinline__ float robot_axes_min(const FootprintK &F, const float (&pmax)[M],
+                                                const float (&pmin)[M], float dlt)
+{
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float da = __fsub_rn(pmax[l], F.alo[l]);
+    const float db = __fsub_rn(F.ahi[l], pmin[l]);
+    dlt = fminf(dlt, fminf(da, db));
+  }
+  return dlt;
+}
+
+// Value of one obstacle whose vertex records start at vt (2 float4 per vertex).
+template <int M>
+__device__ __forceinline__ float obstacle_value(const FootprintK &F, float px, float py,
+                                                float c, float s, const float4 *vt, int n,
+                                                float eps_sat)
+{
+  float pmax[M], pmin[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    pmax[l] = -kInf;
+    pmin[l] = kInf;
+  }
+  float d2min = kInf, dlt = kInf;
+  const float4 a0 = vt[0], b0 = vt[1];
+  const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
+  if (n == 1) {
+    const V2 B0 = to_local(b0.z, b0.w, px, py, c, s);
+    edge_step<M, true>(F, A0, B0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min, dlt);
+    extra_vertex<M>(F, B0, pmax, pmin, d2min);
+  } else {
+    V2 Acur = A0;
+    float4 acur = a0, bcur = b0;
+    for (int k = 0; k < n; ++k) {
+      V2 Anx = A0;
+      float4 anx = a0, bnx = b0;
+      if (k + 1 < n) {
+        anx = vt[2 * (k + 1)];
+        bnx = vt[2 * (k + 1) + 1];
+        Anx = to_local(anx.x, anx.y, px, py, c, s);
+      }
+      edge_step<M, false>(F, Acur, Anx, acur.z, acur.w, bcur.x, bcur.y, pmax, pmin, d2min, dlt);
+      Acur = Anx;
+      acur = anx;
+      bcur = bnx;
+    }
+  }
+  dlt = robot_axes_min<M>(F, pmax, pmin, dlt);
+  return synth_value(d2min, dlt, eps_sat);
+}
+
+// ---------------------------------------------------------------------------
+// detail of one obstacle: active pair (lowest (value, pair id)) + gradient
+// ---------------------------------------------------------------------------
+struct Active {
+  float val;      // the obstacle's min-key value (d^2 or -pen)
+  float d2min;    // squared separation
+  float dlt;      // min overlap over all axes
+  bool separated;
+  unsigned pid;
+  int kind, l, k; // k: obstacle edge (kinds 0,1,7,8), extreme vertex (3,4), 0 (2,5,6)
+  float t;        // projection parameter (kinds 0-2)
+};
+
+__device__ __forceinline__ bool better(float v, unsigned pid, float bv, unsigned bpid)
+{
+  return v < bv || (v == bv && pid < bpid);
+}
+
+template <int M>
+__device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px, float py,
+                                                  float c, float s, const float4 *vt, int n,
+                                                  int orig_first, float eps_sat)
+{
+  const bool seg = (n == 1);
+  float pmax[M], pmin[M];
+  int kmax[M], kmin[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    pmax[l] = -kInf;
+    pmin[l] = kInf;
+    kmax[l] = 0;
+    kmin[l] = 0;
+  }
+  float d2min = kInf, dlt = kInf;
+  // best distance candidate and best axis candidate
+  float bd = kInf, ba = kInf;
+  unsigned pd = PSDF_PAIR_NONE, pa = PSDF_PAIR_NONE;
+  int dk = 0, dl = 0, dkind = 0, ak = 0, al = 0, akind = 0;
+  float dt_ = 0.f;
+  const float4 a0 = vt[0], b0 = vt[1];
+  const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
+  const int nv = seg ? 2 : n;  // vertex set size
+  for (int k = 0; k < n; ++k) {
+    const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
+    const V2 A = (k == 0) ? A0 : to_local(ak4.x, ak4.y, px, py, c, s);
+    V2 B;
+    if (seg) {
+      B = to_local(b0.z, b0.w, px, py, c, s);
+    } else if (k + 1 < n) {
+      const float4 an = vt[2 * (k + 1)];
+      B = to_local(an.x, an.y, px, py, c, s);
+    } else {
+      B = A0;
+    }
+    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const int edge = orig_first + k;
+    float smin = kInf, smax = -kInf;
+    int lsmin = 0, lsmax = 0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
+      const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak4.z));
+      float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
+      if (seg) {
+        rx = (t == 1.0f) ? __fsub_rn(F.vx[l], B.x) : rx;
+        ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
+      }
+      const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+      if (seg || t < 1.0f) {
+        d2min = fminf(d2min, d2);
+        const unsigned pid = make_pid(edge, kVertEdge, l);
+        if (better(d2, pid, bd, pd)) { bd = d2; pd = pid; dkind = kVertEdge; dl = l; dk = k; dt_ = t; }
+      }
+      const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+      if (sl < smin) { smin = sl; lsmin = l; }
+      if (sl > smax) { smax = sl; lsmax = l; }
+      const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+      const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+      const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+      if (tp > 0.0f && tp < 1.0f) {
+        d2min = fminf(d2min, d2p);
+        const unsigned pid = make_pid(edge, kObsVRobotEdge, l);
+        if (better(d2p, pid, bd, pd)) { bd = d2p; pd = pid; dkind = kObsVRobotEdge; dl = l; dk = k; dt_ = tp; }
+      }
+      const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
+      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = k; }
+      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = k; }
+    }
+    const float da = __fmaf_rn(-smin, ak4.w, bk4.y);
+    const float db = __fmaf_rn(smax, ak4.w, -bk4.x);
+    dlt = fminf(dlt, fminf(da, db));
+    {
+      const unsigned pid = make_pid(edge, kOAxisOMax, lsmin);
+      if (better(da, pid, ba, pa)) { ba = da; pa = pid; akind = kOAxisOMax; al = lsmin; ak = k; }
+    }
+    {
+      const unsigned pid = make_pid(edge, kOAxisRMax, lsmax);
+      if (better(db, pid, ba, pa)) { ba = db; pa = pid; akind = kOAxisRMax; al = lsmax; ak = k; }
+    }
+  }
+  if (seg) {
+    // the segment's B endpoint: robot-edge distances and axis projections
+    const V2 Bv = to_local(b0.z, b0.w, px, py, c, s);
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const float wx = __fsub_rn(F.vx[l], Bv.x), wy = __fsub_rn(F.vy[l], Bv.y);
+      const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+      const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+      const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+      if (tp > 0.0f && tp < 1.0f) {
+        d2min = fminf(d2min, d2p);
+        const unsigned pid = make_pid(orig_first, kObsBRobotEdge, l);
+        if (better(d2p, pid, bd, pd)) { bd = d2p; pd = pid; dkind = kObsBRobotEdge; dl = l; dk = 0; dt_ = tp; }
+      }
+      const float pr = __fmaf_rn(Bv.x, F.nx[l], __fmul_rn(Bv.y, F.ny[l]));
+      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = 1; }
+      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = 1; }
+    }
+  }
+  (void)nv;
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float da = __fsub_rn(pmax[l], F.alo[l]);
+    const float db = __fsub_rn(F.ahi[l], pmin[l]);
+    dlt = fminf(dlt, fminf(da, db));
+    const bool bA = seg && kmax[l] == 1, bB = seg && kmin[l] == 1;
+    const int eA = seg ? orig_first : orig_first + kmax[l];
+    const int eB = seg ? orig_first : orig_first + kmin[l];
+    const unsigned pidA = make_pid(eA, bA ? kRAxisOMaxB : kRAxisOMax, l);
+    const unsigned pidB = make_pid(eB, bB ? kRAxisRMaxB : kRAxisRMax, l);
+    if (better(da, pidA, ba, pa)) { ba = da; pa = pidA; akind = bA ? kRAxisOMaxB : kRAxisOMax; al = l; ak = kmax[l]; }
+    if (better(db, pidB, ba, pa)) { ba = db; pa = pidB; akind = bB ? kRAxisRMaxB : kRAxisRMax; al = l; ak = kmin[l]; }
+  }
+  Active r;
+  r.d2min = d2min;
+  r.dlt = dlt;
+  r.separated = dlt < -eps_sat;
+  r.val = synth_value(d2min, dlt, eps_sat);
+  if (r.separated) {
+    r.pid = pd; r.kind = dkind; r.l = dl; r.k = dk; r.t = dt_;
+  } else {
+    r.pid = pa; r.kind = akind; r.l = al; r.k = ak; r.t = 0.f;
+  }
+  return r;
+}
+
+// Pose gradient and edge-gradient contributions of one active pair
+// (active-branch subgradient of Sec. IV-D, closed form per kind).
+struct Grad {
+  float gp[3];     // d sd / d (px, py, theta)
+  int nrow;        // edge contributions: caller row, slot column (0 = A, 2 = B)
+  int row[3], col[3];
+  float gx[3], gy[3];
+};
+
+__device__ __forceinline__ void add_row(Grad &g, int row, int col, float gx, float gy)
+{
+  for (int i = 0; i < g.nrow; ++i)
+    if (g.row[i] == row && g.col[i] == col) {
+      g.gx[i] += gx;
+      g.gy[i] += gy;
+      return;
+    }
+  g.row[g.nrow] = row;
+  g.col[g.nrow] = col;
+  g.gx[g.nrow] = gx;
+  g.gy[g.nrow] = gy;
+  ++g.nrow;
+}
+
+// kind/l/k/t describe the active pair of obstacle (vt, n, orig_first); far
+// holds the far-vertex index of each of its edges (pose-invariant).
+template <int M>
+__device__ Grad active_grad(const FootprintK &F, float px, float py, float c, float s,
+                            const float4 *vt, const int *far, int n, int orig_first, int kind,
+                            int l, int k, float t, float eps_axis)
+{
+  Grad g;
+  g.gp[0] = g.gp[1] = g.gp[2] = 0.f;
+  g.nrow = 0;
+  const bool seg = (n == 1);
+  // stored world endpoints of edge k (B of a polygon edge = next vertex's A)
+  auto worldA = [&](int kk) { const float4 a = vt[2 * kk]; V2 r; r.x = a.x; r.y = a.y; return r; };
+  auto worldB = [&](int kk) {
+    V2 r;
+    if (seg) { const float4 b = vt[1]; r.x = b.z; r.y = b.w; }
+    else { const float4 a = vt[2 * ((kk + 1) % n)]; r.x = a.x; r.y = a.y; }
+    return r;
+  };
+  // gradient of edge k's B endpoint goes to the next vertex's A slot for a
+  // closed polygon, to the B slot for a segment
+  auto rowB = [&](int kk) { return seg ? orig_first : orig_first + (kk + 1) % n; };
+  const int colB = seg ? 2 : 0;
+  float vx[M], vy[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) { vx[q] = F.vx[q]; vy[q] = F.vy[q]; }
+  float lvx = 0.f, lvy = 0.f, lex = 0.f, ley = 0.f, lnx = 0.f, lny = 0.f;
+#pragma unroll
+  for (int q = 0; q < M; ++q)
+    if (q == l) { lvx = vx[q]; lvy = vy[q]; lex = F.ex[q]; ley = F.ey[q]; lnx = F.nx[q]; lny = F.ny[q]; }
+
+  if (kind == kVertEdge) {
+    const V2 Aw = worldA(k), Bw = worldB(k);
+    const V2 A = to_local(Aw.x, Aw.y, px, py, c, s), B = to_local(Bw.x, Bw.y, px, py, c, s);
+    const float ux = B.x - A.x, uy = B.y - A.y;
+    float rx, ry;
+    if (t == 1.0f) { rx = lvx - B.x; ry = lvy - B.y; }
+    else { rx = (lvx - A.x) - t * ux; ry = (lvy - A.y) - t * uy; }
+    const float d = sqrtf(rx * rx + ry * ry);
+    const float hx = d > 0.f ? rx / d : 0.f, hy = d > 0.f ? ry / d : 0.f;
+    const float wx = c * hx - s * hy, wy = s * hx + c * hy;  // R r^
+    g.gp[0] = wx; g.gp[1] = wy; g.gp[2] = -hx * lvy + hy * lvx;  // r^ . (J v)
+    add_row(g, orig_first + k, 0, -(1.f - t) * wx, -(1.f - t) * wy);
+    add_row(g, rowB(k), colB, -t * wx, -t * wy);
+  } else if (kind == kObsVRobotEdge || kind == kObsBRobotEdge) {
+    const V2 Xw = (kind == kObsVRobotEdge) ? worldA(k) : worldB(0);
+    const V2 X = to_local(Xw.x, Xw.y, px, py, c, s);
+    const float qx = lvx + t * lex, qy = lvy + t * ley;
+    const float rx = X.x - qx, ry = X.y - qy;
+    const float d = sqrtf(rx * rx + ry * ry);
+    const float hx = d > 0.f ? rx / d : 0.f, hy = d > 0.f ? ry / d : 0.f;
+    const float wx = c * hx - s * hy, wy = s * hx + c * hy;
+    g.gp[0] = -wx; g.gp[1] = -wy; g.gp[2] = -(-hx * qy + hy * qx);  // -r^ . (J q)
+    if (kind == kObsVRobotEdge) add_row(g, orig_first + k, 0, wx, wy);
+    else add_row(g, orig_first, 2, wx, wy);
+  } else if (kind >= kRAxisOMax && kind <= kRAxisRMaxB) {
+    const bool sideA = (kind == kRAxisOMax || kind == kRAxisOMaxB);
+    const bool isB = (kind == kRAxisOMaxB || kind == kRAxisRMaxB);
+    const V2 Xw = isB ? worldB(0) : worldA(k);
+    const V2 X = to_local(Xw.x, Xw.y, px, py, c, s);
+    const float sg = sideA ? 1.f : -1.f;
+    const float Rnx = c * lnx - s * lny, Rny = s * lnx + c * lny;
+    const float Jnx = -lny, Jny = lnx;
+    g.gp[0] = sg * Rnx; g.gp[1] = sg * Rny; g.gp[2] = -sg * (X.x * Jnx + X.y * Jny);
+    if (isB) add_row(g, orig_first, 2, -sg * Rnx, -sg * Rny);
+    else add_row(g, orig_first + k, 0, -sg * Rnx, -sg * Rny);
+  } else if (kind == kOAxisOMax || kind == kOAxisRMax) {
+    const bool sideA = (kind == kOAxisOMax);
+    const V2 Aw = worldA(k), Bw = worldB(k);
+    const float ux = Bw.x - Aw.x, uy = Bw.y - Aw.y;
+    const float len = sqrtf(ux * ux + uy * uy);
+    const float gd = 1.f / (len + eps_axis);
+    const float npx = -uy * gd, npy = ux * gd;           // n' (world)
+    const float ntx = c * npx + s * npy, nty = -s * npx + c * npy;  // R^T n'
+    const float Rvx = c * lvx - s * lvy, Rvy = s * lvx + c * lvy;
+    const float Jvx = -lvy, Jvy = lvx;
+    const int xk = sideA ? (seg ? 0 : far[k]) : k;        // vertex receiving d/dX
+    const V2 Xw = worldA(xk);
+    const float sgn = sideA ? 1.f : -1.f;                 // delta = sgn <X - p - R v*, n'>
+    const float Dx = sgn * (Xw.x - px - Rvx), Dy = sgn * (Xw.y - py - Rvy);
+    // sd = -delta
+    g.gp[0] = sgn * npx; g.gp[1] = sgn * npy; g.gp[2] = sgn * (Jvx * ntx + Jvy * nty);
+    add_row(g, orig_first + xk, 0, -sgn * npx, -sgn * npy);
+    const float uhx = ux / len, uhy = uy / len;
+    const float JtDx = Dy, JtDy = -Dx;
+    const float JuD = -uy * Dx + ux * Dy;
+    const float gpr = -gd * gd;
+    const float dux = gd * JtDx + gpr * uhx * JuD, duy = gd * JtDy + gpr * uhy * JuD;
+    // d delta / dA = -du, d delta / dB = du; sd = -delta
+    add_row(g, orig_first + k, 0, dux, duy);
+    add_row(g, rowB(k), colB, -dux, -duy);
+  }
+  return g;
+}
+
+}  // namespace psdf

@@ -1,0 +1,102 @@
+// Internal data layout of libpsdf_b300 (host + device).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/psdf.h"
+
+namespace psdf {
+
+constexpr int kMaxM = PSDF_MAX_FOOTPRINT;       // robot vertices
+constexpr int kMaxObsEdges = PSDF_MAX_OBSTACLE_EDGES;
+constexpr int kDefaultTileEdges = 256;
+constexpr int kMaxTileEdges = 256;
+constexpr int kPairShiftEdge = 8;
+constexpr int kPairShiftKind = 4;
+constexpr unsigned kMaxEdgeIndex = (1u << 24) - 1;  // fits the pair-id edge field
+
+// Kinds of the active pair (see include/psdf.h).
+enum Kind : int {
+  kVertEdge = 0,
+  kObsVRobotEdge = 1,
+  kObsBRobotEdge = 2,
+  kRAxisOMax = 3,
+  kRAxisRMax = 4,
+  kRAxisOMaxB = 5,
+  kRAxisRMaxB = 6,
+  kOAxisOMax = 7,
+  kOAxisRMax = 8,
+};
+
+// Robot footprint constants, passed BY VALUE as a kernel parameter so that
+// every lane reads them through the constant bank (Sec. IV-A.1: the local
+// footprint is pose-invariant).
+struct FootprintK {
+  float vx[kMaxM], vy[kMaxM];    // vertices v_l (CCW, local)
+  float ex[kMaxM], ey[kMaxM];    // robot edges e_l = v_{l+1} - v_l
+  float inv_e2[kMaxM];           // 1 / (|e_l|^2 + eps_seg)
+  float nx[kMaxM], ny[kMaxM];    // outward unit normals n_l
+  float alo[kMaxM], ahi[kMaxM];  // robot interval on n_l: [alpha_P, beta_P]
+  float radius;                  // max_l |v_l| (bounding radius about the pose)
+  int m;
+};
+
+// Per-call scalar parameters.
+struct ParamsK {
+  float eps_sat;
+  float eta;  // <= 0: hard minimum
+};
+
+// Tile header.  A tile is a contiguous blob in device memory:
+//   int4   obs[n_obs]        {vtx_begin (within tile), n_edges, rank, sorted obstacle}
+//   float4 vtx[2 * n_vtx]    per obstacle vertex k (= start of edge k):
+//                            a = {Ax, Ay, 1/(|u|^2+eps_seg), 1/(|u|+eps_axis)}
+//                            b = {alpha', beta', Bx, By}
+// alpha', beta': the obstacle's interval on its own edge normal
+// rot90(u)/(|u|+eps_axis), measured from the edge's start A (pose-invariant).
+struct TileHdr {
+  int blob_off;    // byte offset of the blob (16-byte aligned)
+  int blob_bytes;  // multiple of 16
+  int n_obs;
+  int n_vtx;
+  float aabb[4];   // xmin, ymin, xmax, ymax of the tile's endpoints
+};
+
+// Obstacle record in sorted (tile) order, for the per-pose epilogue and the
+// backward: vertex records live at vtx[2 * (vtx_global + k)].
+struct ObsRec {
+  int vtx_global;  // first vertex record (sorted order)
+  int n;           // edges (1 = segment)
+  int orig_first;  // caller's row index of its first edge (the tie-break rank)
+  int tile;
+};
+
+}  // namespace psdf
+
+struct psdf_scene {
+  int64_t rows_total = 0;  // caller's row count (E for CSR, Mbar * mbar padded)
+  int32_t M = 0, n_tiles = 0, tile_edges = 0, max_obs_edges = 0;
+  int64_t n_edges = 0;
+  float bbox[4] = {0, 0, 0, 0};
+  float eps_seg = 0.f, eps_axis = 0.f;
+  int device = 0;
+  // device arrays
+  psdf::TileHdr *d_tiles = nullptr;
+  unsigned char *d_blob = nullptr;
+  psdf::ObsRec *d_obs = nullptr;   // [M] sorted
+  float4 *d_vtx = nullptr;         // [2 * n_edges] sorted vertex records
+  int *d_far = nullptr;            // [n_edges] far vertex index within its obstacle
+  int *d_row2obs = nullptr;        // [rows_total] caller row -> sorted obstacle (-1: none)
+  size_t device_bytes = 0;
+  // host copies used for launch configuration
+  int max_blob_bytes = 0;
+};
+
+namespace psdf {
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+}  // namespace psdf

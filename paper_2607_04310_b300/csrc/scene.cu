@@ -1,0 +1,351 @@
+// Scene preparation: Alg. 1 "EncodeEdges + upload" (Sec. IV-A.2), re-laid out
+// for the B300 kernels.  Host code: validation (Assumption 1), Morton sort of
+// obstacles, obstacle-contiguous tiles, per-edge constants, upload.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "psdf_internal.h"
+
+namespace psdf {
+
+namespace {
+
+uint32_t spread_bits(uint32_t x)
+{
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+uint32_t morton2(uint32_t x, uint32_t y) { return spread_bits(x) | (spread_bits(y) << 1); }
+
+struct ObsIn {
+  int64_t first_row;  // caller's row of the first edge
+  int n;              // edges
+};
+
+// Check one obstacle against Assumption 1 and the layout rules.
+int validate_obstacle(const float *rows, const ObsIn &o, int64_t idx)
+{
+  const float *e = rows + 4 * o.first_row;
+  for (int k = 0; k < o.n; ++k)
+    for (int c = 0; c < 4; ++c)
+      if (!std::isfinite(e[4 * k + c]))
+        return fail(PSDF_ERR_ARG, "obstacle " + std::to_string(idx) + ": non-finite coordinate");
+  if (o.n == 2 || o.n < 1)
+    return fail(PSDF_ERR_LAYOUT, "obstacle " + std::to_string(idx) +
+                                     " has " + std::to_string(o.n) +
+                                     " edges (1 = segment, >= 3 = closed polygon)");
+  if (o.n > kMaxObsEdges)
+    return fail(PSDF_ERR_CAPACITY, "obstacle " + std::to_string(idx) + " has more than " +
+                                       std::to_string(kMaxObsEdges) + " edges");
+  for (int k = 0; k < o.n; ++k) {
+    double ux = (double)e[4 * k + 2] - e[4 * k], uy = (double)e[4 * k + 3] - e[4 * k + 1];
+    if (std::sqrt(ux * ux + uy * uy) < 1e-6)
+      return fail(PSDF_ERR_DEGENERATE_EDGE,
+                  "edge row " + std::to_string(o.first_row + k) + " is shorter than 1e-6 m");
+  }
+  if (o.n >= 3) {
+    double turn = 0.0;
+    for (int k = 0; k < o.n; ++k) {
+      int kn = (k + 1) % o.n;
+      if (e[4 * k + 2] != e[4 * kn] || e[4 * k + 3] != e[4 * kn + 1])
+        return fail(PSDF_ERR_LAYOUT, "obstacle " + std::to_string(idx) + ": B of edge row " +
+                                         std::to_string(o.first_row + k) +
+                                         " differs from A of the next edge (not closed)");
+      double ux = (double)e[4 * k + 2] - e[4 * k], uy = (double)e[4 * k + 3] - e[4 * k + 1];
+      double vx = (double)e[4 * kn + 2] - e[4 * kn], vy = (double)e[4 * kn + 3] - e[4 * kn + 1];
+      double cr = ux * vy - uy * vx, dt = ux * vx + uy * vy;
+      if (cr < 0.0)
+        return fail(PSDF_ERR_LAYOUT, "obstacle " + std::to_string(idx) +
+                                         " is not convex counter-clockwise");
+      turn += std::atan2(cr, dt);
+    }
+    if (std::fabs(turn - 2.0 * M_PI) > 1e-6)
+      return fail(PSDF_ERR_LAYOUT, "obstacle " + std::to_string(idx) +
+                                       " does not turn exactly once (not a simple convex CCW polygon)");
+  }
+  return PSDF_OK;
+}
+
+template <class T>
+int dev_upload(T **dst, const std::vector<T> &src, cudaStream_t st, size_t *bytes)
+{
+  size_t nb = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void **)dst, nb);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scene)");
+  *bytes += nb;
+  if (!src.empty()) {
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(scene)");
+  }
+  return PSDF_OK;
+}
+
+}  // namespace
+
+void free_scene(psdf_scene *s)
+{
+  if (!s) return;
+  cudaFree(s->d_tiles);
+  cudaFree(s->d_blob);
+  cudaFree(s->d_obs);
+  cudaFree(s->d_vtx);
+  cudaFree(s->d_far);
+  cudaFree(s->d_row2obs);
+  delete s;
+}
+
+// rows: caller's edge rows [rows_total][4]; obstacles in caller order.
+int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
+                int tile_edges, const psdf_params *prm, cudaStream_t st, psdf_scene **out)
+{
+  if (tile_edges == 0) tile_edges = kDefaultTileEdges;
+  if (tile_edges < 1 || tile_edges > kMaxTileEdges)
+    return fail(PSDF_ERR_ARG, "tile_edges must be in [1, " + std::to_string(kMaxTileEdges) + "]");
+  const double eps_seg = prm ? prm->eps_seg : 0.0;
+  const double eps_axis = prm ? prm->eps_axis : 0.0;
+  if (!(eps_seg >= 0.0) || !(eps_axis >= 0.0))
+    return fail(PSDF_ERR_ARG, "eps_seg and eps_axis must be >= 0");
+  const int M = (int)obs.size();
+  int64_t n_edges = 0;
+  int max_n = 0;
+  for (int i = 0; i < M; ++i) {
+    int rc = validate_obstacle(rows, obs[i], i);
+    if (rc) return rc;
+    n_edges += obs[i].n;
+    max_n = std::max(max_n, obs[i].n);
+    if (obs[i].first_row + obs[i].n - 1 > (int64_t)kMaxEdgeIndex)
+      return fail(PSDF_ERR_CAPACITY, "edge rows above 2^24 - 1 do not fit the pair id");
+  }
+  if (max_n > tile_edges)
+    return fail(PSDF_ERR_ARG, "an obstacle has more edges than tile_edges");
+
+  // bounding box and Morton order of obstacle centroids
+  float bb[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
+  std::vector<double> cx(M), cy(M);
+  for (int i = 0; i < M; ++i) {
+    const float *e = rows + 4 * obs[i].first_row;
+    double sx = 0, sy = 0;
+    for (int k = 0; k < obs[i].n; ++k) {
+      for (int c = 0; c < 2; ++c) {
+        float x = e[4 * k + 2 * c], y = e[4 * k + 2 * c + 1];
+        bb[0] = std::min(bb[0], x); bb[1] = std::min(bb[1], y);
+        bb[2] = std::max(bb[2], x); bb[3] = std::max(bb[3], y);
+      }
+      sx += e[4 * k] + e[4 * k + 2];
+      sy += e[4 * k + 1] + e[4 * k + 3];
+    }
+    cx[i] = sx / (2.0 * obs[i].n);
+    cy[i] = sy / (2.0 * obs[i].n);
+  }
+  std::vector<uint32_t> code(M);
+  double span = std::max((double)bb[2] - bb[0], (double)bb[3] - bb[1]);
+  if (!(span > 0)) span = 1.0;
+  for (int i = 0; i < M; ++i) {
+    uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (cx[i] - bb[0]) / span * 65535.0));
+    uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (cy[i] - bb[1]) / span * 65535.0));
+    code[i] = morton2(qx, qy);
+  }
+  std::vector<int> order(M);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return code[a] < code[b]; });
+
+  // greedy packing into obstacle-contiguous tiles
+  std::vector<int> tile_first;  // first sorted obstacle of each tile
+  {
+    int acc = 0;
+    for (int s = 0; s < M; ++s) {
+      int n = obs[order[s]].n;
+      if (s == 0 || acc + n > tile_edges) {
+        tile_first.push_back(s);
+        acc = 0;
+      }
+      acc += n;
+    }
+  }
+  const int T = (int)tile_first.size();
+  tile_first.push_back(M);
+
+  std::vector<TileHdr> tiles(T);
+  std::vector<ObsRec> orec(M);
+  std::vector<float4> vtx(2 * (size_t)n_edges);
+  std::vector<int> far(n_edges);
+  std::vector<int> row2obs(std::max<int64_t>(rows_total, 0), -1);
+  std::vector<unsigned char> blob;
+  int64_t vglob = 0;
+  int max_blob = 0;
+  for (int t = 0; t < T; ++t) {
+    int s0 = tile_first[t], s1 = tile_first[t + 1];
+    int nv = 0;
+    for (int s = s0; s < s1; ++s) nv += obs[order[s]].n;
+    const int nobs = s1 - s0;
+    const int bytes = 16 * nobs + 32 * nv;
+    TileHdr h;
+    h.blob_off = (int)blob.size();
+    h.blob_bytes = bytes;
+    h.n_obs = nobs;
+    h.n_vtx = nv;
+    float ab[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
+    blob.resize(blob.size() + bytes);
+    int4 *ob = (int4 *)(blob.data() + h.blob_off);
+    float4 *vb = (float4 *)(blob.data() + h.blob_off + 16 * nobs);
+    int vloc = 0;
+    for (int s = s0; s < s1; ++s) {
+      const ObsIn &o = obs[order[s]];
+      const float *e = rows + 4 * o.first_row;
+      ob[s - s0] = make_int4(vloc, o.n, (int)o.first_row, s);
+      orec[s] = ObsRec{(int)vglob, o.n, (int)o.first_row, t};
+      for (int k = 0; k < o.n; ++k) row2obs[o.first_row + k] = s;
+      // obstacle vertex set: A of every edge, plus B for a segment
+      const int nw = (o.n == 1) ? 2 : o.n;
+      for (int k = 0; k < o.n; ++k) {
+        double ax = e[4 * k], ay = e[4 * k + 1], bx = e[4 * k + 2], by = e[4 * k + 3];
+        double ux = bx - ax, uy = by - ay;
+        double len2 = ux * ux + uy * uy, len = std::sqrt(len2);
+        double nxp = -uy / (len + eps_axis), nyp = ux / (len + eps_axis);
+        double lo = INFINITY, hi = -INFINITY;
+        int kfar = 0;
+        for (int q = 0; q < nw; ++q) {
+          double wx = (o.n == 1 && q == 1) ? (double)e[2] : (double)e[4 * q];
+          double wy = (o.n == 1 && q == 1) ? (double)e[3] : (double)e[4 * q + 1];
+          double pr = (wx - ax) * nxp + (wy - ay) * nyp;
+          if (pr < lo) lo = pr;
+          if (pr > hi) { hi = pr; kfar = q; }
+        }
+        if (o.n == 1) { lo = 0.0; hi = 0.0; kfar = 0; }
+        float4 a = make_float4(e[4 * k], e[4 * k + 1], (float)(1.0 / (len2 + eps_seg)),
+                               (float)(1.0 / (len + eps_axis)));
+        float4 b = make_float4((float)lo, (float)hi, e[4 * k + 2], e[4 * k + 3]);
+        vb[2 * (vloc + k)] = a;
+        vb[2 * (vloc + k) + 1] = b;
+        vtx[2 * (vglob + k)] = a;
+        vtx[2 * (vglob + k) + 1] = b;
+        far[vglob + k] = kfar;
+        for (int c = 0; c < 2; ++c) {
+          float x = e[4 * k + 2 * c], y = e[4 * k + 2 * c + 1];
+          ab[0] = std::min(ab[0], x); ab[1] = std::min(ab[1], y);
+          ab[2] = std::max(ab[2], x); ab[3] = std::max(ab[3], y);
+        }
+      }
+      vloc += o.n;
+      vglob += o.n;
+    }
+    std::memcpy(h.aabb, ab, sizeof(ab));
+    tiles[t] = h;
+    max_blob = std::max(max_blob, bytes);
+  }
+
+  psdf_scene *s = new psdf_scene();
+  s->rows_total = rows_total;
+  s->M = M;
+  s->n_tiles = T;
+  s->tile_edges = tile_edges;
+  s->max_obs_edges = max_n;
+  s->n_edges = n_edges;
+  std::memcpy(s->bbox, bb, sizeof(bb));
+  if (M == 0) { s->bbox[0] = s->bbox[1] = s->bbox[2] = s->bbox[3] = 0.f; }
+  s->eps_seg = (float)eps_seg;
+  s->eps_axis = (float)eps_axis;
+  s->max_blob_bytes = max_blob;
+  cudaGetDevice(&s->device);
+  int rc = PSDF_OK;
+  if (!rc) rc = dev_upload(&s->d_tiles, tiles, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_blob, blob, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_obs, orec, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_vtx, vtx, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_far, far, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_row2obs, row2obs, st, &s->device_bytes);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "scene upload");
+  }
+  if (rc) {
+    free_scene(s);
+    return rc;
+  }
+  *out = s;
+  return PSDF_OK;
+}
+
+}  // namespace psdf
+
+using namespace psdf;
+
+extern "C" int psdf_scene_create_csr(const float *edges, const int32_t *offsets, int32_t M,
+                                     int32_t tile_edges, const psdf_params *params,
+                                     void *stream, psdf_scene **out)
+{
+  if (!out) return fail(PSDF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (M < 0) return fail(PSDF_ERR_ARG, "M < 0");
+  if (!offsets) return fail(PSDF_ERR_ARG, "offsets is NULL");
+  if (offsets[0] != 0) return fail(PSDF_ERR_LAYOUT, "offsets[0] must be 0");
+  std::vector<ObsIn> obs(M);
+  for (int i = 0; i < M; ++i) {
+    if (offsets[i + 1] < offsets[i]) return fail(PSDF_ERR_LAYOUT, "offsets decrease");
+    obs[i] = ObsIn{offsets[i], offsets[i + 1] - offsets[i]};
+  }
+  int64_t E = offsets[M];
+  if (E > 0 && !edges) return fail(PSDF_ERR_ARG, "edges is NULL");
+  return build_scene(edges, E, obs, tile_edges, params, (cudaStream_t)stream, out);
+}
+
+extern "C" int psdf_scene_create_padded(const float *A, const float *B, const uint8_t *S,
+                                        int32_t Mbar, int32_t mbar, int32_t tile_edges,
+                                        const psdf_params *params, void *stream,
+                                        psdf_scene **out)
+{
+  if (!out) return fail(PSDF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (Mbar < 0 || mbar < 0) return fail(PSDF_ERR_ARG, "negative padded size");
+  int64_t rows_total = (int64_t)Mbar * mbar;
+  if (rows_total > 0 && (!A || !B || !S)) return fail(PSDF_ERR_ARG, "A, B or S is NULL");
+  std::vector<float> rows(4 * (size_t)rows_total);
+  std::vector<ObsIn> obs;
+  for (int i = 0; i < Mbar; ++i) {
+    int n = 0;
+    bool gap = false;
+    for (int j = 0; j < mbar; ++j) {
+      int64_t r = (int64_t)i * mbar + j;
+      rows[4 * r] = A[2 * r];
+      rows[4 * r + 1] = A[2 * r + 1];
+      rows[4 * r + 2] = B[2 * r];
+      rows[4 * r + 3] = B[2 * r + 1];
+      if (S[r] > 1) return fail(PSDF_ERR_LAYOUT, "mask S holds a value other than 0 or 1");
+      if (S[r]) {
+        if (gap) return fail(PSDF_ERR_LAYOUT, "valid mask entries of a row must come first");
+        ++n;
+      } else {
+        gap = true;
+      }
+    }
+    if (n > 0) obs.push_back(ObsIn{(int64_t)i * mbar, n});
+  }
+  return build_scene(rows.data(), rows_total, obs, tile_edges, params, (cudaStream_t)stream, out);
+}
+
+extern "C" int psdf_scene_destroy(psdf_scene *scene)
+{
+  free_scene(scene);
+  return PSDF_OK;
+}
+
+extern "C" int psdf_scene_get_info(const psdf_scene *s, psdf_scene_info *info)
+{
+  if (!s || !info) return fail(PSDF_ERR_ARG, "scene or info is NULL");
+  info->n_edges = s->n_edges;
+  info->n_obstacles = s->M;
+  info->n_tiles = s->n_tiles;
+  info->tile_edges = s->tile_edges;
+  info->max_obstacle_edges = s->max_obs_edges;
+  std::memcpy(info->bbox, s->bbox, sizeof(s->bbox));
+  info->device_bytes = (int64_t)s->device_bytes;
+  return PSDF_OK;
+}

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libpsdf_b300.so (C ABI in include/psdf.h).
+
+Argument marshalling only: every step of the PSDF runs in the library's CUDA
+kernels.  Functions carry the C names; device buffers are torch CUDA tensors
+(PyTorch supplies memory and streams), host inputs are numpy arrays.  If the
+library is missing this module raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsdf_b300.so")
+
+PSDF_OK = 0
+PSDF_ERR_ARG = 1
+PSDF_ERR_FOOTPRINT = 2
+PSDF_ERR_DEGENERATE_EDGE = 3
+PSDF_ERR_LAYOUT = 4
+PSDF_ERR_CUDA = 5
+PSDF_ERR_TIMEOUT = 6
+PSDF_ERR_CAPACITY = 7
+PAIR_NONE = 0xFFFFFFFF
+
+KINDS = {0: "robot vertex -> obstacle edge", 1: "obstacle vertex A -> robot edge",
+         2: "segment B -> robot edge", 3: "robot axis, obstacle max - robot min",
+         4: "robot axis, robot max - obstacle min", 5: "robot axis (B), obstacle max - robot min",
+         6: "robot axis (B), robot max - obstacle min",
+         7: "obstacle axis, obstacle max - robot min",
+         8: "obstacle axis, robot max - obstacle min"}
+
+
+class PsdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("psdf error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps_seg", ctypes.c_float), ("eps_axis", ctypes.c_float),
+                ("eps_sat", ctypes.c_float), ("eta", ctypes.c_float)]
+
+
+class SceneInfo(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int64), ("n_obstacles", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int32), ("tile_edges", ctypes.c_int32),
+                ("max_obstacle_edges", ctypes.c_int32), ("bbox", ctypes.c_float * 4),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_SIGS = {
+    "psdf_last_error": (ctypes.c_char_p, []),
+    "psdf_version": (ctypes.c_int, []),
+    "psdf_scene_create_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                             ctypes.POINTER(_vp)]),
+    "psdf_scene_create_padded": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, _vp, _vp, ctypes.POINTER(_vp)]),
+    "psdf_scene_destroy": (ctypes.c_int, [_vp]),
+    "psdf_scene_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(SceneInfo)]),
+    "psdf_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "psdf_workspace_status": (ctypes.c_int, [_vp, _vp]),
+    "psdf_eval": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
+                                 _vp, ctypes.c_size_t, _vp]),
+    "psdf_eval_grad": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp,
+                                      _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "psdf_backward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp,
+                                     _vp, _vp, _vp, _vp]),
+    "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "psdf_profile_reset": (ctypes.c_int, []),
+    "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built; run `python -m paper_2607_04310_b300.build` "
+                               "(there is no CPU fallback)" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def last_error() -> str:
+    return load().psdf_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != PSDF_OK:
+        raise PsdfError(rc, last_error())
+
+
+def _ptr(t) -> Optional[int]:
+    """Device/host address of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(eps_seg=0.0, eps_axis=0.0, eps_sat=0.0, eta=0.0) -> Params:
+    return Params(eps_seg, eps_axis, eps_sat, eta)
+
+
+# --------------------------------------------------------------------------
+# scene
+# --------------------------------------------------------------------------
+class Scene:
+    """Owns a psdf_scene (device copy of the edge set and its precompute)."""
+
+    def __init__(self, handle: int, n_rows: int, params: Params):
+        self.handle = ctypes.c_void_p(handle)
+        self.n_rows = n_rows
+        self.params = params
+
+    @classmethod
+    def from_csr(cls, edges, offsets, tile_edges: int = 0, params: Optional[Params] = None,
+                 stream=None) -> "Scene":
+        e = np.ascontiguousarray(edges, dtype=np.float32).reshape(-1, 4)
+        o = np.ascontiguousarray(offsets, dtype=np.int32)
+        prm = params or Params()
+        out = ctypes.c_void_p()
+        _check(load().psdf_scene_create_csr(_ptr(e), _ptr(o), len(o) - 1, tile_edges,
+                                            ctypes.byref(prm), _stream(stream),
+                                            ctypes.byref(out)))
+        return cls(out.value, e.shape[0], prm)
+
+    @classmethod
+    def from_padded(cls, A, B, S, tile_edges: int = 0, params: Optional[Params] = None,
+                    stream=None) -> "Scene":
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        B = np.ascontiguousarray(B, dtype=np.float32)
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        Mbar, mbar = S.shape
+        prm = params or Params()
+        out = ctypes.c_void_p()
+        _check(load().psdf_scene_create_padded(_ptr(A), _ptr(B), _ptr(S), Mbar, mbar,
+                                               tile_edges, ctypes.byref(prm), _stream(stream),
+                                               ctypes.byref(out)))
+        return cls(out.value, Mbar * mbar, prm)
+
+    def info(self) -> SceneInfo:
+        inf = SceneInfo()
+        _check(load().psdf_scene_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def close(self) -> None:
+        if self.handle and self.handle.value:
+            load().psdf_scene_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# C entry points, same names (device buffers = torch CUDA tensors)
+# --------------------------------------------------------------------------
+def psdf_workspace_bytes(P: int) -> int:
+    return int(load().psdf_workspace_bytes(int(P)))
+
+
+def psdf_workspace_status(workspace, stream=None) -> int:
+    return int(load().psdf_workspace_status(_ptr(workspace), _stream(stream)))
+
+
+def psdf_eval(footprint: np.ndarray, scene: Scene, poses, params: Params, phi, active,
+              workspace, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses), poses.shape[0],
+                            ctypes.byref(params), _ptr(phi), _ptr(active), _ptr(workspace),
+                            workspace.numel(), _stream(stream)))
+
+
+def psdf_eval_grad(footprint: np.ndarray, scene: Scene, poses, params: Params, phi, dphi,
+                   active, workspace, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval_grad(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                 poses.shape[0], ctypes.byref(params), _ptr(phi), _ptr(dphi),
+                                 _ptr(active), _ptr(workspace), workspace.numel(),
+                                 _stream(stream)))
+
+
+def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, active, grad_phi,
+                  grad_pose, grad_edges, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_backward(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                poses.shape[0], ctypes.byref(params), _ptr(active),
+                                _ptr(grad_phi), _ptr(grad_pose), _ptr(grad_edges),
+                                _stream(stream)))
+
+
+def psdf_profile_enable(on: bool) -> None:
+    _check(load().psdf_profile_enable(1 if on else 0))
+
+
+def psdf_profile_reset() -> None:
+    _check(load().psdf_profile_reset())
+
+
+def psdf_profile_read(kernel: str) -> Tuple[int, float]:
+    """(launches, total device milliseconds) of a traced kernel."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(load().psdf_profile_read(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+# --------------------------------------------------------------------------
+# allocation helpers (torch owns the memory; the library computes)
+# --------------------------------------------------------------------------
+def workspace(P: int, device="cuda"):
+    import torch
+    return torch.empty(psdf_workspace_bytes(P), dtype=torch.uint8, device=device)
+
+
+def eval_grad(scene: Scene, footprint: np.ndarray, poses, params: Optional[Params] = None,
+              grad: bool = True, ws=None, stream=None) -> Tuple:
+    """(phi [P], dphi [P,3] or None, active [P] int32 view of the uint32 ids)."""
+    import torch
+    prm = params or scene.params
+    P = poses.shape[0]
+    phi = torch.empty(P, dtype=torch.float32, device=poses.device)
+    active = torch.empty(P, dtype=torch.int32, device=poses.device)
+    ws = workspace(P, poses.device) if ws is None else ws
+    if grad:
+        dphi = torch.empty((P, 3), dtype=torch.float32, device=poses.device)
+        psdf_eval_grad(footprint, scene, poses, prm, phi, dphi, active, ws, stream)
+        return phi, dphi, active
+    psdf_eval(footprint, scene, poses, prm, phi, active, ws, stream)
+    return phi, None, active
+
+
+def pair_ids(active) -> np.ndarray:
+    """uint32 pair ids from the int32 tensor the helpers return."""
+    a = active.detach().cpu().numpy() if hasattr(active, "detach") else np.asarray(active)
+    return a.view(np.uint32) if a.dtype == np.int32 else a.astype(np.uint32)
