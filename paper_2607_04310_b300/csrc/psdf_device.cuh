@@ -2,10 +2,20 @@
 //
 // Every operation that feeds a per-obstacle value is written with explicit
 // round-to-nearest intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, ...), which
-// the compiler may not contract or reassociate.  The scan kernel (values
-// only) and the per-pose epilogue (active pair + gradient) therefore compute
-// bit-identical values for the same (pose, obstacle): the epilogue recovers
-// exactly the minimum the scan selected.
+// the compiler may not contract or reassociate, so a value is the same bits
+// wherever it is computed.
+//
+// Two candidate sets.  The scan (values only) takes the minimum over every
+// clamped point-to-segment candidate, including the clamps that land on a
+// segment's far end (a robot vertex to the next polygon vertex, an obstacle
+// vertex to a robot vertex).  Each of those is a second copy of a candidate
+// the set already holds exactly (Sec. IV-B: the endpoints are vertices, and
+// a vertex-to-vertex distance is never below the vertex-to-edge distance of
+// the edge that starts there), so the minimum changes by rounding at most,
+// and the scan saves a compare and a select per robot vertex and edge.  The
+// epilogue, which names the active pair, uses the exact candidate set: far-
+// end clamps excluded, obstacle-vertex candidates only for interior
+// projections.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -92,17 +102,16 @@ __device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float
       ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
     }
     const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
-    // polygon: t == 1 is the next edge's start vertex, counted there
-    d2min = (SEG || t < 1.0f) ? fminf(d2min, d2) : d2min;
     // robot vertex projected on rot90(u), measured from A (obstacle axis)
     const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
     smin = fminf(smin, sl);
     smax = fmaxf(smax, sl);
-    // obstacle vertex A -> interior of robot edge l
-    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    // obstacle vertex A -> robot edge l, t' = clamp((A - v).e / (|e|^2 + eps))
+    const float tp =
+        __saturatef(__fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]));
     const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
-    d2min = (tp > 0.0f && tp < 1.0f) ? fminf(d2min, d2p) : d2min;
+    d2min = fminf(d2min, fminf(d2, d2p));
     // obstacle vertex A on the robot axis n_l
     const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
     pmax[l] = fmaxf(pmax[l], pr);
@@ -124,10 +133,11 @@ __device__ __forceinline__ void extra_vertex(const FootprintK &F, V2 X, float (&
 #pragma unroll
   for (int l = 0; l < M; ++l) {
     const float wx = __fsub_rn(F.vx[l], X.x), wy = __fsub_rn(F.vy[l], X.y);
-    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    const float tp =
+        __saturatef(__fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]));
     const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
-    d2min = (tp > 0.0f && tp < 1.0f) ? fminf(d2min, d2p) : d2min;
+    d2min = fminf(d2min, d2p);
     const float pr = __fmaf_rn(X.x, F.nx[l], __fmul_rn(X.y, F.ny[l]));
     pmax[l] = fmaxf(pmax[l], pr);
     pmin[l] = fminf(pmin[l], pr);
