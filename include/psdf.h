@@ -179,6 +179,30 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
                   const uint32_t *active, const float *grad_phi, float *grad_pose,
                   float *grad_edges, void *stream);
 
+/* ---- value + gradient without any device allocation ---------------------
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory while they run -- a control loop with a hard period (an
+ * allocation may synchronize the device and stall it), a plug-in whose host
+ * framework owns the whole memory pool, code running where the allocator is
+ * locked.  It computes exactly what psdf_eval_grad computes (same inputs,
+ * outputs, kernels and results) but takes its scratch from a fixed device
+ * array built into the library instead of a caller workspace, and it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  - The array holds PSDF_NOALLOC_MAX_POSES keys (2 MiB + 256 bytes); every
+ *    GPU that loads the library keeps it until the process exits.  P above
+ *    the maximum is rejected with PSDF_ERR_CAPACITY.
+ *  - The first call on a device looks up the array's device address (once,
+ *    with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array: calls whose kernels overlap on the GPU
+ *    (other streams, other threads) race and must be serialized by the
+ *    caller.  Each call re-initializes the scratch it uses, so the previous
+ *    call's contents never leak into its results. */
+#define PSDF_NOALLOC_MAX_POSES 262144
+int psdf_eval_grad_noalloc(const float *footprint, int32_t m, const psdf_scene *scene,
+                           const float *poses, int64_t P, const psdf_params *params, float *phi,
+                           float *dphi, uint32_t *active, void *stream);
+
 /* ---- tracing -----------------------------------------------------------
  * When enabled, the library brackets each launch of its kernels with CUDA
  * events recorded on the launch stream (not during stream capture).

@@ -571,9 +571,9 @@ struct BackwardCall {
   }
 };
 
-static int eval_common(const float *footprint, int32_t m, const psdf_scene *scene,
-                       const float *poses, int64_t P, const psdf_params *params, float *phi,
-                       float *dphi, unsigned *active, void *ws, size_t ws_bytes, void *stream)
+int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
+                int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,
+                void *ws, size_t ws_bytes, void *stream)
 {
   int rc = check_eval_args(scene, poses, P, params, ws, ws_bytes);
   if (rc) return rc;

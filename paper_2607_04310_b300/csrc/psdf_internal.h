@@ -96,6 +96,10 @@ struct psdf_scene {
 };
 
 namespace psdf {
+// value (+ gradient if dphi) evaluation with a given workspace (eval.cu)
+int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
+                int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,
+                void *ws, size_t ws_bytes, void *stream);
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);

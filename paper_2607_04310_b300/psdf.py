@@ -71,6 +71,8 @@ _SIGS = {
                                       _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_backward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                      _vp, _vp, _vp, _vp]),
+    "psdf_eval_grad_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
+                                              _vp, _vp, _vp, _vp, _vp]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -218,6 +220,19 @@ def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, ac
                                 poses.shape[0], ctypes.byref(params), _ptr(active),
                                 _ptr(grad_phi), _ptr(grad_pose), _ptr(grad_edges),
                                 _stream(stream)))
+
+
+NOALLOC_MAX_POSES = 262144
+
+
+def psdf_eval_grad_noalloc(footprint: np.ndarray, scene: Scene, poses, params: Params, phi,
+                           dphi, active, stream=None) -> int:
+    """psdf_eval_grad with the library's built-in scratch (no allocation).
+    Returns the status code (0 = PSDF_OK) without raising."""
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    return int(load().psdf_eval_grad_noalloc(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                             poses.shape[0], ctypes.byref(params), _ptr(phi),
+                                             _ptr(dphi), _ptr(active), _stream(stream)))
 
 
 def psdf_profile_enable(on: bool) -> None:
