@@ -179,6 +179,88 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
                   const uint32_t *active, const float *grad_phi, float *grad_pose,
                   float *grad_edges, void *stream);
 
+/* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
+ * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
+ * the edge tiles.  Poses are grouped into blocks of 32 by a spatial sort.
+ * Each pose proposes its k best tiles -- by the tile-proposal network's
+ * predicted signed distance (PSDF_PROPOSE_MLP) or by the conservative lower
+ * bound below (PSDF_PROPOSE_BOUND) -- and every block evaluates the union of
+ * its poses' proposals exactly.  Then, for every tile not yet evaluated and
+ * every pose, a conservative lower bound
+ *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)   (rounded down)
+ * on the signed distance of every obstacle in the tile is compared with the
+ * pose's current minimum; a tile is evaluated ("fallback") unless LB exceeds
+ * it for every pose of the block.  No skipped tile can hold a smaller value
+ * or a tie, so phi, the active pair and the gradient equal the full scan's.
+ * The network only changes how much work the exact part does. */
+typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
+
+#define PSDF_MLP_IN 16
+#define PSDF_MLP_HIDDEN 64
+#define PSDF_PROPOSE_BOUND 1
+#define PSDF_PROPOSE_MLP 2
+#define PSDF_CULL_MAX_K 4
+
+typedef struct {
+  int32_t mode; /* PSDF_PROPOSE_BOUND or PSDF_PROPOSE_MLP */
+  int32_t k;    /* proposals per pose, 1..PSDF_CULL_MAX_K */
+} psdf_cull_opts;
+
+typedef struct {
+  int64_t pose_blocks;    /* blocks of 32 poses                                  */
+  int64_t tiles;          /* edge tiles in the scene                             */
+  int64_t proposed_items; /* (block, tile) pairs evaluated from the proposals    */
+  int64_t fallback_items; /* (block, tile) pairs added by the lower-bound check  */
+  int64_t fallback_poses; /* poses needing at least one tile beyond the proposal */
+} psdf_cull_stats;
+
+/* Tile-proposal network: 16 inputs -> 64 ReLU units -> 1 output, FP16 weights
+ * with FP32 accumulation (tensor-core mma).  W1 HOST float[64][16] row-major
+ * (the hidden bias is the weight of input 15, which is the constant 1), w2
+ * HOST float[64], b2 scalar; the weights are rounded to FP16 on upload. */
+int psdf_mlp_create(const float *W1, const float *w2, float b2, psdf_mlp **out);
+int psdf_mlp_destroy(psdf_mlp *mlp);
+
+/* The network's inputs for (pose p, tile t), float[P][n_tiles][16] (DEVICE):
+ * 0..7  the tile AABB corners (xmin,ymin) (xmax,ymin) (xmax,ymax) (xmin,ymax)
+ *       in the pose frame, clamped to [-20, 20] m, times 0.1
+ * 8..11 the corners' distances to p, clamped to [0, 30] m, times 0.1
+ * 12    the distance from p to the AABB, clamped to [0, 30] m, times 0.1
+ * 13    the footprint radius max_l |v_l| (m)
+ * 14    the tile's edge count / 256
+ * 15    1 */
+int psdf_tile_features(const float *footprint, int32_t m, const psdf_scene *scene,
+                       const float *poses, int64_t P, float *features, void *stream);
+
+/* Network outputs (predicted signed distance of the tile's nearest obstacle)
+ * for every (pose, tile), float[P][n_tiles] (DEVICE). */
+int psdf_mlp_scores(const psdf_mlp *mlp, const float *footprint, int32_t m,
+                    const psdf_scene *scene, const float *poses, int64_t P, float *scores,
+                    void *stream);
+
+/* Exact per-tile minimum signed distance for every (pose, tile),
+ * float[P][n_tiles] (DEVICE): the training labels of the network. */
+int psdf_tile_values(const float *footprint, int32_t m, const psdf_scene *scene,
+                     const float *poses, int64_t P, const psdf_params *params, float *values,
+                     void *stream);
+
+/* The cull's lower bound LB (metres, may be negative) for every (pose, tile),
+ * float[P][n_tiles] (DEVICE). */
+int psdf_tile_lower_bounds(const float *footprint, int32_t m, const psdf_scene *scene,
+                           const float *poses, int64_t P, float *lb, void *stream);
+
+size_t psdf_cull_workspace_bytes(int64_t P, const psdf_scene *scene);
+
+/* dphi and active are nullable; mlp may be NULL for PSDF_PROPOSE_BOUND. */
+int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
+                     const psdf_mlp *mlp, const psdf_cull_opts *opts, const float *poses,
+                     int64_t P, const psdf_params *params, float *phi, float *dphi,
+                     uint32_t *active, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Synchronizes `stream` and copies the counters of the last psdf_eval_culled
+ * that used `workspace` (PSDF_ERR_TIMEOUT if it recorded a device failure). */
+int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cull_stats *stats);
+
 /* ---- value + gradient without any device allocation ---------------------
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory while they run -- a control loop with a hard period (an

@@ -383,7 +383,7 @@ struct DeviceInfo {
   int sms = 0;
 };
 
-DeviceInfo device_info()
+DeviceInfo device_info_impl()
 {
   static std::mutex mu;
   static std::vector<DeviceInfo> cache;
@@ -400,6 +400,8 @@ DeviceInfo device_info()
 }
 
 }  // namespace
+
+int device_sms() { return device_info_impl().sms; }
 
 // Footprint validation (Assumption 1) and constants.
 int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F)
@@ -447,8 +449,8 @@ int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F)
   return PSDF_OK;
 }
 
-static int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
-                           const psdf_params *params, void *workspace, size_t ws_bytes)
+int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
+                    const psdf_params *params, void *workspace, size_t ws_bytes)
 {
   if (!scene) return fail(PSDF_ERR_ARG, "scene is NULL");
   if (P < 0) return fail(PSDF_ERR_ARG, "P < 0");
@@ -486,7 +488,7 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   const int init_blocks = (int)((P + 255) / 256);
   init_keys_kernel<<<init_blocks, 256, 0, st>>>(keys, P, err);
   if (sc->n_tiles > 0) {
-    const DeviceInfo di = device_info();
+    const DeviceInfo di = device_info_impl();
     const long long pose_blocks = (P + kScanThreads - 1) / kScanThreads;
     if (pose_blocks > 2147483647LL) return fail(PSDF_ERR_CAPACITY, "too many poses for one launch");
     // aim for about 32 CTAs per SM in total (several waves of resident CTAs)
@@ -562,6 +564,23 @@ struct EvalCall {
 };
 
 template <int M>
+struct EpilogueCall {
+  static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                 const ParamsK &pk, const unsigned long long *keys, const int *err, float *phi,
+                 float *dphi, unsigned *active, cudaStream_t st)
+  {
+    const int blocks = (int)((P + 255) / 256);
+    ProfileScope prof("epilogue", st);
+    epilogue_kernel<M><<<blocks, 256, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
+                                               sc->d_vtx, sc->d_far, sc->d_row2obs, keys, err,
+                                               phi, dphi, active);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PSDF_OK;
+  }
+};
+
+template <int M>
 struct BackwardCall {
   static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                  const unsigned *active, const float *grad_phi, float *grad_pose,
@@ -570,6 +589,13 @@ struct BackwardCall {
     return launch_backward<M>(F, sc, poses, P, active, grad_phi, grad_pose, grad_edges, st);
   }
 };
+
+int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                    const ParamsK &pk, const unsigned long long *keys, const int *err,
+                    float *phi, float *dphi, unsigned *active, cudaStream_t st)
+{
+  return dispatch_m<EpilogueCall>(F.m, F, sc, poses, P, pk, keys, err, phi, dphi, active, st);
+}
 
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,

@@ -96,6 +96,15 @@ struct psdf_scene {
 };
 
 namespace psdf {
+// shared host helpers (eval.cu)
+int device_sms();
+int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F);
+int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
+                    const psdf_params *params, void *workspace, size_t ws_bytes);
+// per-pose epilogue (value, active pair, optional gradient) from 64-bit keys
+int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                    const ParamsK &pk, const unsigned long long *keys, const int *err,
+                    float *phi, float *dphi, unsigned *active, cudaStream_t st);
 // value (+ gradient if dphi) evaluation with a given workspace (eval.cu)
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,

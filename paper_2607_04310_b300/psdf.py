@@ -73,6 +73,21 @@ _SIGS = {
                                      _vp, _vp, _vp, _vp]),
     "psdf_eval_grad_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
                                               _vp, _vp, _vp, _vp, _vp]),
+    "psdf_mlp_create": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.POINTER(_vp)]),
+    "psdf_mlp_destroy": (ctypes.c_int, [_vp]),
+    "psdf_tile_features": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                          _vp]),
+    "psdf_mlp_scores": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                       _vp]),
+    "psdf_tile_values": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                        _vp, _vp]),
+    "psdf_tile_lower_bounds": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
+                                              _vp, _vp]),
+    "psdf_cull_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, _vp]),
+    "psdf_eval_culled": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                        ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                        ctypes.c_size_t, _vp]),
+    "psdf_cull_stats_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -223,6 +238,103 @@ def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, ac
 
 
 NOALLOC_MAX_POSES = 262144
+PROPOSE_BOUND = 1
+PROPOSE_MLP = 2
+
+
+class CullOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32)]
+
+
+class CullStats(ctypes.Structure):
+    _fields_ = [("pose_blocks", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("proposed_items", ctypes.c_int64), ("fallback_items", ctypes.c_int64),
+                ("fallback_poses", ctypes.c_int64)]
+
+
+class Mlp:
+    """Owns a psdf_mlp (tile-proposal network weights on the device)."""
+
+    def __init__(self, W1, w2, b2: float):
+        W1 = np.ascontiguousarray(W1, dtype=np.float32).reshape(64, 16)
+        w2 = np.ascontiguousarray(w2, dtype=np.float32).reshape(64)
+        out = ctypes.c_void_p()
+        _check(load().psdf_mlp_create(_ptr(W1), _ptr(w2), float(b2), ctypes.byref(out)))
+        self.handle = out
+        self.W1, self.w2, self.b2 = W1, w2, float(b2)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().psdf_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psdf_tile_features(footprint, scene: Scene, poses, out, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_tile_features(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                     poses.shape[0], _ptr(out), _stream(stream)))
+
+
+def psdf_mlp_scores(mlp: Mlp, footprint, scene: Scene, poses, out, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_mlp_scores(mlp.handle, _ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                  poses.shape[0], _ptr(out), _stream(stream)))
+
+
+def psdf_tile_values(footprint, scene: Scene, poses, params: Params, out, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_tile_values(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                   poses.shape[0], ctypes.byref(params), _ptr(out),
+                                   _stream(stream)))
+
+
+def psdf_tile_lower_bounds(footprint, scene: Scene, poses, out, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_tile_lower_bounds(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                         poses.shape[0], _ptr(out), _stream(stream)))
+
+
+def psdf_cull_workspace_bytes(P: int, scene: Scene) -> int:
+    return int(load().psdf_cull_workspace_bytes(int(P), scene.handle))
+
+
+def psdf_eval_culled(footprint, scene: Scene, mlp: Optional[Mlp], opts: CullOpts, poses,
+                     params: Params, phi, dphi, active, workspace, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval_culled(_ptr(fp), fp.shape[0], scene.handle,
+                                   mlp.handle if mlp is not None else None, ctypes.byref(opts),
+                                   _ptr(poses), poses.shape[0], ctypes.byref(params), _ptr(phi),
+                                   _ptr(dphi), _ptr(active), _ptr(workspace), workspace.numel(),
+                                   _stream(stream)))
+
+
+def psdf_cull_stats_read(workspace, stream=None) -> CullStats:
+    st = CullStats()
+    _check(load().psdf_cull_stats_read(_ptr(workspace), _stream(stream), ctypes.byref(st)))
+    return st
+
+
+def eval_culled(scene: Scene, footprint, poses, mlp: Optional[Mlp] = None, k: int = 2,
+                params: Optional[Params] = None, grad: bool = True, ws=None, stream=None):
+    """(phi, dphi or None, active, workspace) through the exact tile cull."""
+    import torch
+    prm = params or scene.params
+    P = poses.shape[0]
+    opts = CullOpts(PROPOSE_MLP if mlp is not None else PROPOSE_BOUND, k)
+    phi = torch.empty(P, dtype=torch.float32, device=poses.device)
+    act = torch.empty(P, dtype=torch.int32, device=poses.device)
+    dphi = torch.empty((P, 3), dtype=torch.float32, device=poses.device) if grad else None
+    if ws is None:
+        ws = torch.empty(psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8,
+                         device=poses.device)
+    psdf_eval_culled(footprint, scene, mlp, opts, poses, prm, phi, dphi, act, ws, stream)
+    return phi, dphi, act, ws
 
 
 def psdf_eval_grad_noalloc(footprint: np.ndarray, scene: Scene, poses, params: Params, phi,

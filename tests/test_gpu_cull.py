@@ -1,0 +1,183 @@
+"""Exact tile cull: bit-for-bit equal to the full scan for every proposal
+mode (even an untrained network), a valid lower bound, and the network's
+inputs and outputs against the numpy reference."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2607_04310_b300 import psdf
+from paper_2607_04310_b300 import scenegen as sg
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def _bits(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def _random_mlp(seed):
+    W1, w2, b2 = omlp.init_weights(seed)
+    return psdf.Mlp(W1.astype(np.float32), w2.astype(np.float32), 0.25)
+
+
+def _compare_cull(w, scene, poses, mlp=None, k=2):
+    phi0, dphi0, act0 = psdf.eval_grad(scene, w.footprint, poses)
+    phi1, dphi1, act1, ws = psdf.eval_culled(scene, w.footprint, poses, mlp=mlp, k=k)
+    st = psdf.psdf_cull_stats_read(ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(phi0), _bits(phi1))
+    assert np.array_equal(_bits(act0), _bits(act1))
+    assert np.array_equal(_bits(dphi0), _bits(dphi1))
+    return st
+
+
+@pytest.mark.parametrize("mode,k", [("bound", 1), ("bound", 2), ("bound", 4), ("mlp", 1),
+                                    ("mlp", 3)])
+def test_cull_equals_full_scan_dense_clutter(mode, k):
+    """4,096 poses x 100,000 edges (the bench workload): every output bit equal."""
+    w = sg.dense_clutter(4)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    poses = torch.as_tensor(w.poses, device="cuda")
+    mlp = _random_mlp(7) if mode == "mlp" else None
+    st = _compare_cull(w, scene, poses, mlp=mlp, k=k)
+    T = scene.info().n_tiles
+    nb = (w.P + 31) // 32
+    assert 0 < st.proposed_items <= nb * 32 * k
+    assert st.proposed_items + st.fallback_items <= nb * T
+    if mode == "bound":
+        # the bound-ordered cull must skip most of the tiles
+        assert st.proposed_items + st.fallback_items < 0.2 * nb * T
+
+
+def test_cull_equals_full_scan_octagon_lidar_and_ragged():
+    w = sg.octagon_lidar(1)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    for P in (w.P, 1, 31, 33, 100):
+        poses = torch.as_tensor(w.poses[:P], device="cuda")
+        _compare_cull(w, scene, poses, k=2)
+        _compare_cull(w, scene, poses, mlp=_random_mlp(3), k=2)
+
+
+def test_cull_with_penetrations_and_small_tiles():
+    w = sg.plain_rect_small(0)
+    g = np.random.default_rng(3)
+    n = 700
+    idx = g.integers(0, w.E, size=n)
+    poses_np = np.concatenate([w.edges[idx, 0:2] + g.normal(size=(n, 2)) * 0.4,
+                               g.uniform(-math.pi, math.pi, size=(n, 1))], axis=1)
+    poses = torch.as_tensor(poses_np.astype(np.float32), device="cuda")
+    for te in (4, 16, 64):
+        scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=te)
+        _compare_cull(w, scene, poses, k=1)
+        _compare_cull(w, scene, poses, mlp=_random_mlp(te), k=2)
+
+
+def test_cull_far_poses_and_empty_scene():
+    w = sg.plain_rect_small(0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    far = torch.tensor([[500.0, -300.0, 0.1], [-1e4, 1e4, 2.0], [10.0, 10.0, 0.0]], device="cuda")
+    _compare_cull(w, scene, far, k=1)
+    empty = psdf.Scene.from_csr(np.zeros((0, 4), np.float32), np.zeros(1, np.int32))
+    phi, dphi, act, _ = psdf.eval_culled(empty, w.footprint, far, k=1)
+    torch.cuda.synchronize()
+    assert torch.all(torch.isinf(phi))
+
+
+def test_lower_bound_is_below_every_tile_value():
+    w = sg.dense_clutter(4, n_rects=4000, n_poses=512, field_side=80.0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    T = scene.info().n_tiles
+    poses = torch.as_tensor(w.poses, device="cuda")
+    vals = torch.empty((w.P, T), device="cuda")
+    lb = torch.empty((w.P, T), device="cuda")
+    psdf.psdf_tile_values(w.footprint, scene, poses, scene.params, vals)
+    psdf.psdf_tile_lower_bounds(w.footprint, scene, poses, lb)
+    phi, _, _ = psdf.eval_grad(scene, w.footprint, poses)
+    torch.cuda.synchronize()
+    v = vals.cpu().numpy()
+    b = lb.cpu().numpy()
+    assert np.all(b <= v)
+    # the minimum over tiles is phi
+    assert np.max(np.abs(v.min(axis=1) - phi.cpu().numpy())) <= 1e-6
+    # and the bound is informative: most tiles are ruled out at the minimum
+    assert np.mean(b > phi.cpu().numpy()[:, None]) > 0.9
+
+
+def test_tile_values_against_oracle_per_tile():
+    """tile values = min over the tile's obstacles of the oracle's sd; tile
+    membership recovered from the scene's own AABBs (rectangles lie inside
+    exactly one tile's AABB by construction of the packing)."""
+    w = sg.plain_rect_small(0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=16)
+    T = scene.info().n_tiles
+    poses = torch.as_tensor(w.poses, device="cuda")
+    vals = torch.empty((w.P, T), device="cuda")
+    psdf.psdf_tile_values(w.footprint, scene, poses, scene.params, vals)
+    torch.cuda.synchronize()
+    sd = oracle.obstacle_sd(w.footprint, w.edges, w.offsets, w.poses)      # [P, M]
+    v = vals.cpu().numpy()
+    # every obstacle's sd appears as some tile's minimum or above it, and
+    # every tile minimum is some obstacle's sd
+    for p in range(w.P):
+        for t in range(T):
+            assert np.min(np.abs(sd[p] - v[p, t])) <= 1e-5
+    assert np.max(np.abs(v.min(axis=1) - sd.min(axis=1))) <= 1e-5
+
+
+def test_features_and_scores_match_numpy_reference():
+    w = sg.dense_clutter(4, n_rects=3000, n_poses=300, field_side=70.0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    info = scene.info()
+    T = info.n_tiles
+    poses = torch.as_tensor(w.poses, device="cuda")
+    feats = torch.empty((w.P, T, 16), device="cuda")
+    psdf.psdf_tile_features(w.footprint, scene, poses, feats)
+    mlp = _random_mlp(11)
+    scores = torch.empty((w.P, T), device="cuda")
+    psdf.psdf_mlp_scores(mlp, w.footprint, scene, poses, scores)
+    torch.cuda.synchronize()
+    F = feats.cpu().numpy().astype(np.float64)
+    # tile AABBs and edge counts: recover the AABB from the corner features of pose 0
+    # is circular, so check the inputs' invariants instead: corner distances agree
+    # with the corner coordinates, and the scores agree with the reference MLP on
+    # the GPU's own inputs (rounded like the kernel)
+    d_from_xy = 0.1 * np.minimum(np.hypot(10 * F[:, :, 0:8:2], 10 * F[:, :, 1:8:2]), 30)
+    inside = np.all(np.abs(F[:, :, 0:8]) < 1.99, axis=2)
+    assert np.max(np.abs(d_from_xy[inside] - F[:, :, 8:12][inside])) <= 1e-5
+    assert np.all(F[:, :, 15] == 1.0)
+    fp64 = w.footprint.astype(np.float64)
+    assert np.allclose(F[:, :, 13], np.max(np.hypot(fp64[:, 0], fp64[:, 1])), rtol=1e-5)
+    ref = omlp.forward_f16(F.reshape(-1, 16), mlp.W1, mlp.w2, mlp.b2).reshape(w.P, T)
+    got = scores.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 2e-3 * max(1.0, np.abs(ref).max())
+
+
+def test_features_match_numpy_definition():
+    """inputs recomputed from their definition with the scene's tile AABBs
+    (the AABB is the extent of the corner features at a pose far outside)."""
+    w = sg.dense_clutter(4, n_rects=600, n_poses=64, field_side=30.0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    T = scene.info().n_tiles
+    # a probe pose at the field centre with theta = 0 sees every corner within
+    # the 20 m clamp, in world axes
+    probe = torch.tensor([[15.0, 15.0, 0.0]], device="cuda")
+    f0 = torch.empty((1, T, 16), device="cuda")
+    psdf.psdf_tile_features(w.footprint, scene, probe, f0)
+    torch.cuda.synchronize()
+    c = f0.cpu().numpy()[0].astype(np.float64)
+    aabb = np.stack([c[:, 0], c[:, 1], c[:, 4], c[:, 5]], axis=1) * 10.0 + 15.0
+    counts = c[:, 14] * 256.0
+    poses = torch.as_tensor(w.poses, device="cuda")
+    feats = torch.empty((w.P, T, 16), device="cuda")
+    psdf.psdf_tile_features(w.footprint, scene, poses, feats)
+    torch.cuda.synchronize()
+    rf = float(np.max(np.hypot(w.footprint[:, 0], w.footprint[:, 1])))
+    ref = omlp.tile_features(aabb, counts, w.poses, rf)
+    assert np.max(np.abs(feats.cpu().numpy() - ref)) <= 2e-5
