@@ -261,6 +261,35 @@ int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
  * that used `workspace` (PSDF_ERR_TIMEOUT if it recorded a device failure). */
 int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cull_stats *stats);
 
+/* ---- training the tile-proposal network on the GPU ----------------------
+ * Model s = w2 . relu(W1 x) + b2 (the network above, FP32 during training),
+ * loss = mean over rows of (s - y)^2 where y is a clamped exact tile value
+ * (psdf_tile_values).  Parameters are laid out as one float[1089] vector:
+ * W1 row-major [64][16] | w2 [64] | b2.  Gradients are reduced in a fixed
+ * order without atomics, so every step is reproducible bit for bit.
+ * X DEVICE float[rows][16], y DEVICE float[rows]; idx (DEVICE int32[N],
+ * nullable) selects the N rows of a step (NULL = the first N rows).
+ * loss (DEVICE float, nullable) receives the step's mean loss before the
+ * update.  Optimizer: Adam (0.9, 0.999, 1e-8) with bias correction. */
+#define PSDF_MLP_PARAMS 1089
+typedef struct psdf_trainer psdf_trainer;
+int psdf_trainer_create(const float *W1, const float *w2, float b2, float lr,
+                        psdf_trainer **out);
+int psdf_trainer_destroy(psdf_trainer *trainer);
+int psdf_trainer_set_lr(psdf_trainer *trainer, float lr);
+/* gradient of the loss over rows 0..N-1 into DEVICE float[1089] */
+int psdf_trainer_grad(psdf_trainer *trainer, const float *X, const float *y, int64_t N,
+                      float *grad, float *loss, void *stream);
+/* one Adam step on the rows idx[0..N-1] (or 0..N-1) */
+int psdf_trainer_step(psdf_trainer *trainer, const float *X, const float *y, const int32_t *idx,
+                      int64_t N, float *loss, void *stream);
+/* state for checkpoints (HOST float[1089] each, nullable on get); both
+ * synchronize the device */
+int psdf_trainer_get(const psdf_trainer *trainer, float *params, float *m, float *v,
+                     int64_t *step);
+int psdf_trainer_set(psdf_trainer *trainer, const float *params, const float *m, const float *v,
+                     int64_t step);
+
 /* ---- value + gradient without any device allocation ---------------------
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory while they run -- a control loop with a hard period (an

@@ -88,6 +88,14 @@ _SIGS = {
                                         ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_size_t, _vp]),
     "psdf_cull_stats_read": (ctypes.c_int, [_vp, _vp, _vp]),
+    "psdf_trainer_create": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float,
+                                           ctypes.POINTER(_vp)]),
+    "psdf_trainer_destroy": (ctypes.c_int, [_vp]),
+    "psdf_trainer_set_lr": (ctypes.c_int, [_vp, ctypes.c_float]),
+    "psdf_trainer_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
+    "psdf_trainer_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "psdf_trainer_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
+    "psdf_trainer_set": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
