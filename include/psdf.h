@@ -244,8 +244,9 @@ int psdf_tile_values(const float *footprint, int32_t m, const psdf_scene *scene,
                      const float *poses, int64_t P, const psdf_params *params, float *values,
                      void *stream);
 
-/* The cull's lower bound LB (metres, may be negative) for every (pose, tile),
- * float[P][n_tiles] (DEVICE). */
+/* The cull's bound LB (metres) for every (pose, tile), float[P][n_tiles]
+ * (DEVICE).  LB > 0 proves that every obstacle of the tile is separated from
+ * the posed footprint by more than LB; LB <= 0 makes no claim. */
 int psdf_tile_lower_bounds(const float *footprint, int32_t m, const psdf_scene *scene,
                            const float *poses, int64_t P, float *lb, void *stream);
 
