@@ -6,9 +6,13 @@
 One step = one pass of the value+gradient path over the dense-clutter
 workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
 100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
-PSDF_Forward with the pose gradient (scan + epilogue kernels) followed by
-PSDF_Backward (pose and edge-endpoint gradients of sum(phi)).  The metric
-is pose x edge pair-evaluations per second.
+the exact tile cull with the learned proposal (spatial pose sort, network
+scores on tensor cores, exact evaluation of the proposed tiles, lower-bound
+fallback, epilogue with the pose gradient) followed by PSDF_Backward (pose
+and edge-endpoint gradients of sum(phi)).  The metric counts pose x edge
+pairs of the whole scene per second (the cull's results equal the full
+scan's bit for bit, checked in the run); the full scan and the bound-ordered
+cull are timed on the same GPU for the speedup.
 
 Under torchrun (N > 1) every rank evaluates its own 4,096 poses on the same
 scene (weak scaling, no data-path collective); the value is the total pair
@@ -209,9 +213,29 @@ def run_reference(a, rank, world):
 # --------------------------------------------------------------------------
 # B300 arm
 # --------------------------------------------------------------------------
+CULL_K = 1
+
+
+def _time_steps(step, steps, flush, stream, clocks=None):
+    """Device time of each step (CUDA events on the launching stream), L2
+    flushed before every step outside the timed interval."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
 def run_b300(a, rank, world, local):
     import torch
     from paper_2607_04310_b300 import psdf, roofline
+    from paper_2607_04310_b300 import train_cull
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -224,130 +248,160 @@ def run_b300(a, rank, world, local):
     m = w.footprint.shape[0]
     scene = psdf.Scene.from_csr(w.edges, w.offsets)
     info = scene.info()
+    T = int(info.n_tiles)
+    W1, w2, b2, wmeta = train_cull.load_weights()
+    mlp = psdf.Mlp(W1, w2, b2)
     prm = psdf.make_params()
     P = w.P
+    nb = (P + 31) // 32
     poses = torch.as_tensor(w.poses, device=dev).contiguous()
     phi = torch.empty(P, device=dev)
     dphi = torch.empty((P, 3), device=dev)
     act = torch.empty(P, dtype=torch.int32, device=dev)
     ws = psdf.workspace(P, dev)
+    cws = torch.empty(psdf.psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8, device=dev)
     gphi = torch.ones(P, device=dev)
     gpose = torch.empty((P, 3), device=dev)
     gedges = torch.zeros((w.E, 4), device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    learned = psdf.CullOpts(psdf.PROPOSE_MLP, CULL_K)
+    bound = psdf.CullOpts(psdf.PROPOSE_BOUND, CULL_K)
 
-    def step(ps):
-        psdf.psdf_eval_grad(w.footprint, scene, ps, prm, phi, dphi, act, ws, stream)
+    def step_learned(ps=poses):
+        psdf.psdf_eval_culled(w.footprint, scene, mlp, learned, ps, prm, phi, dphi, act, cws,
+                              stream)
         psdf.psdf_backward(w.footprint, scene, ps, prm, act, gphi, gpose, gedges, stream)
 
-    for _ in range(max(a.warmup, 3)):
-        step(poses)
-    torch.cuda.synchronize()
-    if psdf.psdf_workspace_status(ws, stream) != 0:
-        raise RuntimeError("device-side failure during warm-up")
+    def step_bound():
+        psdf.psdf_eval_culled(w.footprint, scene, None, bound, poses, prm, phi, dphi, act, cws,
+                              stream)
+        psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges, stream)
 
-    # ---- device-timed steps (inputs resident in HBM; L2 flushed between) ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    def step_full():
+        psdf.psdf_eval_grad(w.footprint, scene, poses, prm, phi, dphi, act, ws, stream)
+        psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges, stream)
+
+    # exactness in this run: learned cull vs full scan, every output bit
+    step_full()
+    ref = (phi.clone(), dphi.clone(), act.clone())
+    step_learned()
+    torch.cuda.synchronize()
+    exact = bool(torch.equal(ref[0].view(torch.int32), phi.view(torch.int32)) and
+                 torch.equal(ref[1].view(torch.int32), dphi.view(torch.int32)) and
+                 torch.equal(ref[2], act))
+    for _ in range(max(a.warmup, 3)):
+        step_learned()
+    torch.cuda.synchronize()
+    st = psdf.psdf_cull_stats_read(cws, stream)
+
+    # ---- headline: learned cull, device-timed, with live kernel tracing -----
     if pg:
         pg.barrier()
-    torch.cuda.synchronize()
     psdf.psdf_profile_reset()
     psdf.psdf_profile_enable(True)
     with ClockSampler(local) as clk:
-        for i in range(a.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            step(poses)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
+        ms = _time_steps(step_learned, a.steps, flush, stream)
     psdf.psdf_profile_enable(False)
     if pg:
         pg.barrier()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_step = sum(ms) / len(ms)
-    n_scan, scan_ms = psdf.psdf_profile_read("scan")
-    n_epi, epi_ms = psdf.psdf_profile_read("epilogue")
-    n_bwd, bwd_ms = psdf.psdf_profile_read("backward")
+    prof = {k: psdf.psdf_profile_read(k) for k in
+            ("propose", "cull_eval", "fallback", "epilogue", "backward")}
     psdf.psdf_profile_reset()
-    if psdf.psdf_workspace_status(ws, stream) != 0:
-        raise RuntimeError("device-side failure during the timed steps")
+    st = psdf.psdf_cull_stats_read(cws, stream)
 
-    # ---- end to end through the C ABI with host buffers --------------------
-    h_poses = torch.as_tensor(w.poses).pin_memory()
-    h_phi = torch.empty(P).pin_memory()
-    h_dphi = torch.empty((P, 3)).pin_memory()
-    h_act = torch.empty(P, dtype=torch.int32).pin_memory()
-    d_poses = torch.empty_like(poses)
+    # ---- comparison paths on the same GPU -------------------------------------
+    for _ in range(3):
+        step_full()
+    full_ms = sum(_time_steps(step_full, a.steps, flush, stream)) / a.steps
+    for _ in range(3):
+        step_bound()
+    bound_ms = sum(_time_steps(step_bound, a.steps, flush, stream)) / a.steps
+    st_bound = psdf.psdf_cull_stats_read(cws, stream)
 
-    def e2e_step():
-        d_poses.copy_(h_poses, non_blocking=True)
-        psdf.psdf_eval_grad(w.footprint, scene, d_poses, prm, phi, dphi, act, ws, stream)
-        psdf.psdf_backward(w.footprint, scene, d_poses, prm, act, gphi, gpose, gedges, stream)
-        h_phi.copy_(phi, non_blocking=True)
-        h_dphi.copy_(dphi, non_blocking=True)
-        h_act.copy_(act, non_blocking=True)
-
+    # ---- end to end through the C ABI with host buffers ----------------------
     e2e_step_ms = float("nan")
     if not a.no_e2e:
+        h_poses = torch.as_tensor(w.poses).pin_memory()
+        h_phi = torch.empty(P).pin_memory()
+        h_dphi = torch.empty((P, 3)).pin_memory()
+        h_act = torch.empty(P, dtype=torch.int32).pin_memory()
+        d_poses = torch.empty_like(poses)
+
+        def e2e_step():
+            d_poses.copy_(h_poses, non_blocking=True)
+            step_learned(d_poses)
+            h_phi.copy_(phi, non_blocking=True)
+            h_dphi.copy_(dphi, non_blocking=True)
+            h_act.copy_(act, non_blocking=True)
+
         for _ in range(3):
             e2e_step()
-        torch.cuda.synchronize()
-        for i in range(a.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            e2e_step()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        e_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        e2e_step_ms = sum(e_ms) / len(e_ms)
+        e2e_step_ms = sum(_time_steps(e2e_step, a.steps, flush, stream)) / a.steps
 
     # ---- aggregate over ranks ----------------------------------------------
     pairs = float(P) * w.E
     t_max = ms_step
     if pg:
-        t = torch.tensor([ms_step, e2e_step_ms], device=dev)
+        t = torch.tensor([ms_step, e2e_step_ms, full_ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max, e2e_step_ms = float(t[0]), float(t[1])
+        t_max, e2e_step_ms, full_ms = float(t[0]), float(t[1]), float(t[2])
     value = world * pairs / (t_max / 1000.0)
-    e2e_value = world * pairs / (e2e_step_ms / 1000.0)
     if rank != 0:
         if pg:
             pg.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (scan) ------------------------------
+    # ---- roofline of the dominant kernel (the exact evaluation of the items) --
     props = torch.cuda.get_device_properties(dev)
     peaks = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = roofline.fp32_peak_tflops(props.multi_processor_count, sm_max)
-    flops_launch = roofline.flops_per_pose(m, w.offsets) * P
-    scan_avg_ms = scan_ms / max(n_scan, 1)
-    achieved = flops_launch / (scan_avg_ms / 1000.0) / 1e12
-    clocks = clk.summary()
+    items = int(st.proposed_items + st.fallback_items)
+    flops_pose_all_tiles = roofline.flops_per_pose(m, w.offsets)
+    flops_step = items * 32 * flops_pose_all_tiles / T
+    n_ev, ev_ms = prof["cull_eval"]
+    achieved = flops_step * a.steps / (ev_ms / 1000.0) / 1e12
+    evaluated_pairs = items * 32 * (w.E / T)
+    launches_per_step = 10  # init, cells, scan, scatter, propose, eval x2, fallback, epilogue, backward
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "impl": "b300",
         "config": {"workload": WORKLOAD, "poses_per_gpu": P, "edges": w.E,
-                   "obstacles": w.M, "tiles": int(info.n_tiles), "footprint_vertices": m,
-                   "path": "full scan (eval_grad + backward)",
+                   "obstacles": w.M, "tiles": T, "footprint_vertices": m,
+                   "path": "learned tile cull (k=%d) + pose gradient + backward" % CULL_K,
+                   "pair_count": "effective: poses x edges of the whole scene",
                    "l2": "flushed between timed steps (256 MiB write)"},
-        "roofline": {"bound": "alu", "kernel": "scan", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
+        "speedup_vs_full_scan": full_ms / ms_step,
+        "exact_vs_full_scan": exact,
+        "full_scan": {"value": pairs / (full_ms / 1000.0), "ms_per_step": full_ms},
+        "bound_cull": {"value": pairs / (bound_ms / 1000.0), "ms_per_step": bound_ms,
+                       "evaluated_fraction": (st_bound.proposed_items + st_bound.fallback_items) / (nb * T),
+                       "fallback_rate": st_bound.fallback_poses / P},
+        "cull": {"candidate_fraction": st.proposed_items / (nb * T),
+                 "evaluated_fraction": items / (nb * T),
+                 "fallback_rate": st.fallback_poses / P,
+                 "proposed_items": int(st.proposed_items),
+                 "fallback_items": int(st.fallback_items),
+                 "evaluated_pair_evals_per_s": evaluated_pairs / (ms_step / 1000.0),
+                 "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp")},
+        "roofline": {"bound": "alu", "kernel": "eval_items (exact evaluation of culled tiles)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
                      "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz "
                                     "(max SM clock in MEASURED_PEAKS.json)"
                                     % (props.multi_processor_count, sm_max),
-                     "flops_per_launch": flops_launch, "avg_launch_ms": scan_avg_ms,
-                     "traffic": _traffic("scan", WORKLOAD)},
-        "kernels_ms_per_step": {"scan": scan_ms / a.steps, "epilogue": epi_ms / a.steps,
-                                "backward": bwd_ms / a.steps},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * P,
-                "d2h_bytes_per_step": (4 + 12 + 4) * P, "ms_per_step": e2e_step_ms},
-        "gpu_launches": (n_scan + n_epi + n_bwd) + a.steps,  # + one key-init kernel per step
-        "clocks": clocks,
+                     "flops_per_step": flops_step, "avg_launch_ms": ev_ms / max(n_ev, 1),
+                     "traffic": _traffic("eval_items", WORKLOAD)},
+        "kernels_ms_per_step": {k: v[1] / a.steps for k, v in prof.items()},
+        "e2e": {"value": world * pairs / (e2e_step_ms / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": 12 * P, "d2h_bytes_per_step": (4 + 12 + 4) * P,
+                "ms_per_step": e2e_step_ms},
+        "gpu_launches": launches_per_step * a.steps,
+        "clocks": clk.summary(),
     }
     if not a.no_cpu_baseline and world == 1:
         import oracle

@@ -42,6 +42,8 @@ constexpr int kCellBits = 6;
 constexpr int kCells = 1 << (2 * kCellBits);
 constexpr int kProposeWarps = 8;
 constexpr int kMaxK = PSDF_CULL_MAX_K;
+constexpr int kFallbackWarps = 8;
+constexpr int kTileChunk = 512;  // tiles staged in shared memory at a time
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
 
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
     px = poses[3 * (long long)p];
     py = poses[3 * (long long)p + 1];
   }
+  __shared__ float4 ab_s[kTileChunk];
   float sc[K];
   int id[K];
 #pragma unroll
@@ -399,9 +402,20 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
     sc[i] = kInf;
     id[i] = -1;
   }
-  const int t0 = (int)((long long)n_tiles * warp / kProposeWarps);
-  const int t1 = (int)((long long)n_tiles * (warp + 1) / kProposeWarps);
-  for (int t = t0; t < t1; ++t) topk_insert<K>(sc, id, tile_lb(tiles[t].aabb, px, py, rfoot), t);
+  for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
+    const int cn = min(kTileChunk, n_tiles - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+      const TileHdr h = tiles[c0 + i];
+      ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
+    }
+    __syncthreads();
+    for (int i = warp; i < cn; i += kProposeWarps) {
+      const float4 a4 = ab_s[i];
+      const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+      topk_insert<K>(sc, id, tile_lb(ab, px, py, rfoot), c0 + i);
+    }
+  }
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     cand_s[(lane * kProposeWarps + warp) * K + i] = sc[i];
@@ -455,16 +469,26 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
     sca[i] = scb[i] = kInf;
     ida[i] = idb[i] = -1;
   }
-  const int t0 = (int)((long long)n_tiles * range / kRanges);
-  const int t1 = (int)((long long)n_tiles * (range + 1) / kRanges);
-  for (int t = t0; t < t1; ++t) {
-    const TileHdr h = tiles[t];
-    float s_a, s_b;
-    mlp_rows(w, h.aabb, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot,
-             (float)h.n_vtx * (1.f / 256.f), s_a, s_b);
-    if (q == 0) {
-      topk_insert<K>(sca, ida, s_a + b2, t);
-      topk_insert<K>(scb, idb, s_b + b2, t);
+  __shared__ float4 ab_s[kTileChunk];
+  __shared__ float ef_s[kTileChunk];
+  for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
+    const int cn = min(kTileChunk, n_tiles - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+      const TileHdr h = tiles[c0 + i];
+      ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
+      ef_s[i] = (float)h.n_vtx * (1.f / 256.f);
+    }
+    __syncthreads();
+    for (int i = range; i < cn; i += kRanges) {
+      const float4 a4 = ab_s[i];
+      const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+      float s_a, s_b;
+      mlp_rows(w, ab, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[i], s_a, s_b);
+      if (q == 0) {
+        topk_insert<K>(sca, ida, s_a + b2, c0 + i);
+        topk_insert<K>(scb, idb, s_b + b2, c0 + i);
+      }
     }
   }
   if (q == 0) {
@@ -483,19 +507,45 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
 // ---------------------------------------------------------------------------
 // exact evaluation of (block, tile) items, fallback check
 // ---------------------------------------------------------------------------
+constexpr int kEvalWarps = 4;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// One warp per (block, tile) item.  The warp first copies the tile's blob
+// into its own slice of shared memory (16-byte cp.async per lane; blob sizes
+// are multiples of 16), then every lane evaluates the tile's obstacles for
+// its pose, reading the records from shared memory as a broadcast.
 template <int M>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kEvalWarps * 32)
     eval_items(FootprintK F, ParamsK prm, const float *__restrict__ poses,
                const int *__restrict__ perm, long long P, const TileHdr *__restrict__ tiles,
                const unsigned char *__restrict__ blob, const int2 *__restrict__ items,
-               const int *__restrict__ n_items, unsigned long long *__restrict__ keys)
+               const int *__restrict__ n_items, int blob_cap,
+               unsigned long long *__restrict__ keys)
 {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char esm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char *mine = esm + (size_t)warp * blob_cap;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const int n = *n_items;
   for (long long i = gw; i < n; i += nw) {
     const int2 it = items[i];
+    const TileHdr h = tiles[it.y];
+    const unsigned char *src = blob + h.blob_off;
+    __syncwarp();  // the previous item's reads of `mine` are done
+    for (int off = 16 * lane; off < h.blob_bytes; off += 16 * 32) cp_async16(mine + off, src + off);
     const long long ps = (long long)it.x * kBlockPoses + lane;
     const bool valid = ps < P;
     float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
@@ -506,10 +556,10 @@ __global__ void __launch_bounds__(128)
       py = poses[3 * p + 1];
       sincosf(poses[3 * p + 2], &s, &c);
     }
-    const TileHdr h = tiles[it.y];
-    const unsigned char *tb = blob + h.blob_off;
-    const int4 *ob = reinterpret_cast<const int4 *>(tb);
-    const float4 *vt = reinterpret_cast<const float4 *>(tb + 16 * h.n_obs);
+    cp_async_wait_all();
+    __syncwarp();
+    const int4 *ob = reinterpret_cast<const int4 *>(mine);
+    const float4 *vt = reinterpret_cast<const float4 *>(mine + 16 * h.n_obs);
     unsigned long long best = ~0ull;
     for (int o = 0; o < h.n_obs; ++o) {
       const int4 rec = ob[o];
@@ -521,17 +571,21 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-__global__ void cull_fallback(const float *__restrict__ poses, const int *__restrict__ perm,
-                              long long P, long long nb, const TileHdr *__restrict__ tiles,
-                              int n_tiles, float rfoot, int words,
-                              const unsigned *__restrict__ prop_bits,
-                              const unsigned long long *__restrict__ keys,
-                              int2 *__restrict__ items, CullCounters *ctr)
+
+// One CTA per pose block; each warp takes every 8th tile of a staged chunk,
+// its lanes are the block's 32 poses.
+__global__ void __launch_bounds__(kFallbackWarps * 32)
+    cull_fallback(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
+                  long long nb, const TileHdr *__restrict__ tiles, int n_tiles, float rfoot,
+                  int words, const unsigned *__restrict__ prop_bits,
+                  const unsigned long long *__restrict__ keys, int2 *__restrict__ items,
+                  CullCounters *ctr)
 {
-  const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long b = gw; b < nb; b += nw) {
+  __shared__ float4 ab_s[kTileChunk];
+  __shared__ unsigned bits_s[kTileChunk / 32];
+  __shared__ unsigned any_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
     const long long ps = b * kBlockPoses + lane;
     const bool valid = ps < P;
     float px = 0.f, py = 0.f, best = -kInf;
@@ -542,19 +596,35 @@ __global__ void cull_fallback(const float *__restrict__ poses, const int *__rest
       const unsigned long long key = keys[p];
       best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
     }
+    if (threadIdx.x == 0) any_s = 0u;
     bool any = false;
-    for (int t = 0; t < n_tiles; ++t) {
-      const bool proposed = (prop_bits[b * words + (t >> 5)] >> (t & 31)) & 1u;
-      const bool need = valid && !proposed && !(tile_lb_value(tiles[t].aabb, px, py, rfoot) > best);
-      const unsigned m = __ballot_sync(0xffffffffu, need);
-      if (m && lane == 0) {
-        const int idx = atomicAdd(&ctr->n_items2, 1);
-        items[idx] = make_int2((int)b, t);
+    for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
+      const int cn = min(kTileChunk, n_tiles - c0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+        const TileHdr h = tiles[c0 + i];
+        ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
       }
-      any |= need;
+      for (int i = threadIdx.x; i < (cn + 31) / 32; i += blockDim.x)
+        bits_s[i] = prop_bits[b * words + (c0 >> 5) + i];
+      __syncthreads();
+      for (int i = warp; i < cn; i += kFallbackWarps) {
+        const float4 a4 = ab_s[i];
+        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+        const bool proposed = (bits_s[i >> 5] >> (i & 31)) & 1u;
+        const bool need = valid && !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (m && lane == 0) {
+          const int idx = atomicAdd(&ctr->n_items2, 1);
+          items[idx] = make_int2((int)b, c0 + i);
+        }
+        any |= need;
+      }
     }
     const unsigned fm = __ballot_sync(0xffffffffu, any);
-    if (lane == 0 && fm) atomicAdd(&ctr->fallback_poses, __popc(fm));
+    if (lane == 0 && fm) atomicOr(&any_s, fm);
+    __syncthreads();
+    if (threadIdx.x == 0 && any_s) atomicAdd(&ctr->fallback_poses, __popc(any_s));
   }
 }
 
@@ -660,8 +730,17 @@ struct CullEvalCall {
                  long long P, const psdf_scene *sc, const int2 *items, const int *n_items,
                  unsigned long long *keys, int grid, cudaStream_t st)
   {
-    eval_items<M><<<grid, 128, 0, st>>>(F, pk, poses, perm, P, sc->d_tiles, sc->d_blob, items,
-                                        n_items, keys);
+    const int blob_cap = (sc->max_blob_bytes + 15) / 16 * 16;
+    const size_t smem = (size_t)kEvalWarps * blob_cap;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(eval_items<M>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_items)");
+    }
+    eval_items<M><<<grid, kEvalWarps * 32, smem, st>>>(F, pk, poses, perm, P, sc->d_tiles,
+                                                       sc->d_blob, items, n_items, blob_cap,
+                                                       keys);
     return PSDF_OK;
   }
 };
@@ -908,7 +987,7 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
       }
 #undef PSDF_PROPOSE
     }
-    const int eval_grid = device_sms() * 16;
+    const int eval_grid = device_sms() * 8;
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<CullEvalCall>(m, F, pk, poses, (const int *)perm, (long long)P, scene,
@@ -918,8 +997,8 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     }
     {
       ProfileScope prof("fallback", st);
-      const long long fb_warps = std::min<long long>(L.nb, (long long)device_sms() * 64);
-      cull_fallback<<<(unsigned)((fb_warps + 3) / 4), 128, 0, st>>>(
+      const long long fb_ctas = std::min<long long>(L.nb, (long long)device_sms() * 8);
+      cull_fallback<<<(unsigned)fb_ctas, kFallbackWarps * 32, 0, st>>>(
           poses, perm, P, L.nb, scene->d_tiles, scene->n_tiles, F.radius, L.words, bits, keys,
           items2, ctr);
     }
