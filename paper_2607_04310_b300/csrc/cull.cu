@@ -40,7 +40,7 @@ namespace psdf {
 constexpr int kBlockPoses = 32;
 constexpr int kCellBits = 6;
 constexpr int kCells = 1 << (2 * kCellBits);
-constexpr int kProposeWarps = 8;
+constexpr int kEvalParts = 4;  // obstacle ranges per (block, tile) item
 constexpr int kMaxK = PSDF_CULL_MAX_K;
 constexpr int kFallbackWarps = 8;
 constexpr int kTileChunk = 512;  // tiles staged in shared memory at a time
@@ -56,10 +56,20 @@ struct CullCounters {
 };
 
 struct CullLayout {
-  size_t keys, perm, cell, hist, bits, items1, items2, total;
+  size_t keys, perm, cell, hist, bits, items1, items2, cand_s, cand_i, total;
   long long nb;
-  int words;
+  int words, splits;
 };
+
+// Tile splits of the proposal scoring: enough (group, split) warps to fill
+// the GPU, at most 1024 tiles per split staged in shared memory.
+static int score_splits(long long P, int n_tiles)
+{
+  const long long groups = std::max<long long>(1, (P + 15) / 16);
+  long long sp = (2048 + groups - 1) / groups;
+  sp = std::max<long long>(sp, (n_tiles + 1023) / 1024);
+  return (int)std::max<long long>(1, std::min<long long>(sp, 64));
+}
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -76,6 +86,10 @@ static CullLayout cull_layout(long long P, int n_tiles)
   L.bits = o; o = align256(o + 4 * (size_t)L.nb * L.words);
   L.items1 = o; o = align256(o + 8 * (size_t)L.nb * kBlockPoses * kMaxK);
   L.items2 = o; o = align256(o + 8 * (size_t)L.nb * std::max(n_tiles, 1));
+  L.splits = score_splits(P, n_tiles);
+  const size_t nc = (size_t)std::max<long long>(P, 1) * L.splits * kMaxK;
+  L.cand_s = o; o = align256(o + 4 * nc);
+  L.cand_i = o; o = align256(o + 4 * nc);
   L.total = o;
   return L;
 }
@@ -330,71 +344,51 @@ __device__ __forceinline__ void topk_insert(float (&sc)[K], int (&id)[K], float 
   }
 }
 
-// Shared tail of the proposal kernels: merge the per-range candidates of each
-// pose, mark the block's union in a bitmask and emit (block, tile) items.
+// Candidates of a pose for one tile split: its K best (score, tile), kept in
+// global memory at cand[(sorted pose * splits + split) * K + i].
 template <int K>
-__device__ void propose_finish(int b, bool (&valid_slot)[1], float *cand_s, int *cand_i,
-                               int n_ranges, unsigned *bits_s, int words,
-                               unsigned *__restrict__ prop_bits, int2 *__restrict__ items,
-                               CullCounters *ctr, long long P)
+__device__ __forceinline__ void store_cand(float *cand_s, int *cand_i, long long ps, int split,
+                                           int splits, const float (&sc)[K], const int (&id)[K])
 {
-  const int tid = threadIdx.x;
-  for (int wd = tid; wd < words; wd += blockDim.x) bits_s[wd] = 0u;
-  __syncthreads();
-  if (tid < kBlockPoses && (long long)b * kBlockPoses + tid < P) {
-    float sc[K];
-    int id[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-      sc[i] = kInf;
-      id[i] = -1;
-    }
-    for (int r = 0; r < n_ranges; ++r)
-      for (int i = 0; i < K; ++i) {
-        const int c = (tid * n_ranges + r) * K + i;
-        if (cand_i[c] >= 0) topk_insert<K>(sc, id, cand_s[c], cand_i[c]);
-      }
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (id[i] >= 0) atomicOr(&bits_s[id[i] >> 5], 1u << (id[i] & 31));
+  for (int i = 0; i < K; ++i) {
+    cand_s[(ps * splits + split) * K + i] = sc[i];
+    cand_i[(ps * splits + split) * K + i] = id[i];
   }
-  __syncthreads();
-  for (int wd = tid; wd < words; wd += blockDim.x) {
-    unsigned m = bits_s[wd];
-    prop_bits[(long long)b * words + wd] = m;
-    if (m) {
-      int base = atomicAdd(&ctr->n_items1, __popc(m));
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        items[base++] = make_int2(b, wd * 32 + bit);
-      }
-    }
-  }
-  (void)valid_slot;
 }
 
-template <int K>
-__global__ void __launch_bounds__(kProposeWarps * 32, 2)
-    propose_bound(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
-                  const TileHdr *__restrict__ tiles, int n_tiles, float rfoot, int words,
-                  unsigned *__restrict__ prop_bits, int2 *__restrict__ items,
-                  CullCounters *ctr)
+// Stage the AABBs (and edge fractions) of tiles [t0, t1) in shared memory.
+__device__ __forceinline__ void stage_tiles(const TileHdr *__restrict__ tiles, int t0, int t1,
+                                            float4 *ab_s, float *ef_s)
 {
-  extern __shared__ __align__(16) unsigned char sm[];
-  float *cand_s = reinterpret_cast<float *>(sm);
-  int *cand_i = reinterpret_cast<int *>(cand_s + kBlockPoses * kProposeWarps * K);
-  unsigned *bits_s = reinterpret_cast<unsigned *>(cand_i + kBlockPoses * kProposeWarps * K);
-  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long ps = (long long)b * kBlockPoses + lane;
-  const bool valid = ps < P;
-  float px = 0.f, py = 0.f;
-  if (valid) {
-    const int p = perm[ps];
-    px = poses[3 * (long long)p];
-    py = poses[3 * (long long)p + 1];
+  for (int i = threadIdx.x; i < t1 - t0; i += blockDim.x) {
+    const TileHdr h = tiles[t0 + i];
+    ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
+    if (ef_s) ef_s[i] = (float)h.n_vtx * (1.f / 256.f);
   }
-  __shared__ float4 ab_s[kTileChunk];
+}
+
+constexpr int kScoreWarps = 4;
+constexpr int kMaxSplitTiles = 1024;  // tiles per split staged in shared memory
+
+// Bound proposal scores: warp = 32 sorted poses, blockIdx.y = tile split.
+template <int K>
+__global__ void __launch_bounds__(kScoreWarps * 32)
+    score_bound(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
+                const TileHdr *__restrict__ tiles, int n_tiles, int splits, float rfoot,
+                float *__restrict__ cand_s, int *__restrict__ cand_i)
+{
+  __shared__ float4 ab_s[kMaxSplitTiles];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int split = blockIdx.y;
+  const int t0 = (int)((long long)n_tiles * split / splits);
+  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
+  stage_tiles(tiles, t0, t1, ab_s, nullptr);
+  __syncthreads();
+  const long long ps = ((long long)blockIdx.x * kScoreWarps + warp) * 32 + lane;
+  if (ps >= P) return;
+  const long long p = perm[ps];
+  const float px = poses[3 * p], py = poses[3 * p + 1];
   float sc[K];
   int id[K];
 #pragma unroll
@@ -402,51 +396,35 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
     sc[i] = kInf;
     id[i] = -1;
   }
-  for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
-    const int cn = min(kTileChunk, n_tiles - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-      const TileHdr h = tiles[c0 + i];
-      ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
-    }
-    __syncthreads();
-    for (int i = warp; i < cn; i += kProposeWarps) {
-      const float4 a4 = ab_s[i];
-      const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-      topk_insert<K>(sc, id, tile_lb(ab, px, py, rfoot), c0 + i);
-    }
+  for (int i = 0; i < t1 - t0; ++i) {
+    const float4 a4 = ab_s[i];
+    const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+    topk_insert<K>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
   }
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    cand_s[(lane * kProposeWarps + warp) * K + i] = sc[i];
-    cand_i[(lane * kProposeWarps + warp) * K + i] = id[i];
-  }
-  bool vs[1] = {valid};
-  propose_finish<K>(b, vs, cand_s, cand_i, kProposeWarps, bits_s, words, prop_bits, items, ctr,
-                    P);
+  store_cand<K>(cand_s, cand_i, ps, split, splits, sc, id);
 }
 
-// Network proposal: warps 0-3 score poses 0-15 of the block, warps 4-7 poses
-// 16-31, each warp a quarter of the tiles; 16 poses are the 16 rows of every
-// tensor-core tile.
+// Network proposal scores: warp = 16 sorted poses (the 16 rows of every
+// tensor-core tile), blockIdx.y = tile split; two tiles in flight per step.
 template <int K>
-__global__ void __launch_bounds__(kProposeWarps * 32, 2)
-    propose_mlp(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
-                const TileHdr *__restrict__ tiles, int n_tiles, float rfoot, int words,
-                const uint32_t *__restrict__ frag, float b2, unsigned *__restrict__ prop_bits,
-                int2 *__restrict__ items, CullCounters *ctr)
+__global__ void __launch_bounds__(kScoreWarps * 32)
+    score_mlp(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
+              const TileHdr *__restrict__ tiles, int n_tiles, int splits, float rfoot,
+              const uint32_t *__restrict__ frag, float b2, float *__restrict__ cand_s,
+              int *__restrict__ cand_i)
 {
-  extern __shared__ __align__(16) unsigned char sm[];
-  constexpr int kRanges = kProposeWarps / 2;
-  float *cand_s = reinterpret_cast<float *>(sm);
-  int *cand_i = reinterpret_cast<int *>(cand_s + kBlockPoses * kRanges * K);
-  unsigned *bits_s = reinterpret_cast<unsigned *>(cand_i + kBlockPoses * kRanges * K);
-  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int half = warp / kRanges, range = warp % kRanges;
+  __shared__ float4 ab_s[kMaxSplitTiles];
+  __shared__ float ef_s[kMaxSplitTiles];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int split = blockIdx.y;
+  const int t0 = (int)((long long)n_tiles * split / splits);
+  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
+  stage_tiles(tiles, t0, t1, ab_s, ef_s);
+  __syncthreads();
+  const long long group = (long long)blockIdx.x * kScoreWarps + warp;
+  if (group * 16 >= P) return;  // uniform over the warp
   const int g = lane >> 2, q = lane & 3;
-  const int slot_a = half * 16 + g, slot_b = half * 16 + g + 8;
-  const long long psa = (long long)b * kBlockPoses + slot_a;
-  const long long psb = (long long)b * kBlockPoses + slot_b;
+  const long long psa = group * 16 + g, psb = group * 16 + g + 8;
   float pxa = 0.f, pya = 0.f, ca = 1.f, sa = 0.f, pxb = 0.f, pyb = 0.f, cb = 1.f, sb = 0.f;
   if (psa < P) {
     const long long p = perm[psa];
@@ -469,39 +447,77 @@ __global__ void __launch_bounds__(kProposeWarps * 32, 2)
     sca[i] = scb[i] = kInf;
     ida[i] = idb[i] = -1;
   }
-  __shared__ float4 ab_s[kTileChunk];
-  __shared__ float ef_s[kTileChunk];
-  for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
-    const int cn = min(kTileChunk, n_tiles - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-      const TileHdr h = tiles[c0 + i];
-      ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
-      ef_s[i] = (float)h.n_vtx * (1.f / 256.f);
-    }
-    __syncthreads();
-    for (int i = range; i < cn; i += kRanges) {
-      const float4 a4 = ab_s[i];
-      const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-      float s_a, s_b;
-      mlp_rows(w, ab, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[i], s_a, s_b);
-      if (q == 0) {
-        topk_insert<K>(sca, ida, s_a + b2, c0 + i);
-        topk_insert<K>(scb, idb, s_b + b2, c0 + i);
+  const int n = t1 - t0;
+  for (int i = 0; i < n; i += 2) {
+    const int j = min(i + 1, n - 1);
+    const float4 a4 = ab_s[i], b4 = ab_s[j];
+    const float ab0[4] = {a4.x, a4.y, a4.z, a4.w};
+    const float ab1[4] = {b4.x, b4.y, b4.z, b4.w};
+    float s0a, s0b, s1a, s1b;
+    mlp_rows(w, ab0, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[i], s0a, s0b);
+    mlp_rows(w, ab1, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[j], s1a, s1b);
+    if (q == 0) {
+      topk_insert<K>(sca, ida, s0a + b2, t0 + i);
+      topk_insert<K>(scb, idb, s0b + b2, t0 + i);
+      if (j != i) {
+        topk_insert<K>(sca, ida, s1a + b2, t0 + j);
+        topk_insert<K>(scb, idb, s1b + b2, t0 + j);
       }
     }
   }
   if (q == 0) {
+    if (psa < P) store_cand<K>(cand_s, cand_i, psa, split, splits, sca, ida);
+    if (psb < P) store_cand<K>(cand_s, cand_i, psb, split, splits, scb, idb);
+  }
+}
+
+// One warp per block of 32 sorted poses: merge each pose's candidates over
+// the splits into its K best, mark the block's union, emit (block, tile) items.
+template <int K>
+__global__ void __launch_bounds__(128)
+    propose_union(long long P, long long nb, int splits, int words,
+                  const float *__restrict__ cand_s, const int *__restrict__ cand_i,
+                  unsigned *__restrict__ prop_bits, int2 *__restrict__ items, CullCounters *ctr)
+{
+  extern __shared__ unsigned ubits[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * 4 + warp;
+  unsigned *bits_s = ubits + warp * words;
+  if (b >= nb) return;  // uniform over the warp
+  for (int wd = lane; wd < words; wd += 32) bits_s[wd] = 0u;
+  __syncwarp();
+  const long long ps = b * kBlockPoses + lane;
+  if (ps < P) {
+    float sc[K];
+    int id[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      cand_s[(slot_a * kRanges + range) * K + i] = sca[i];
-      cand_i[(slot_a * kRanges + range) * K + i] = ida[i];
-      cand_s[(slot_b * kRanges + range) * K + i] = scb[i];
-      cand_i[(slot_b * kRanges + range) * K + i] = idb[i];
+      sc[i] = kInf;
+      id[i] = -1;
+    }
+    for (int sp = 0; sp < splits; ++sp)
+      for (int i = 0; i < K; ++i) {
+        const long long c = (ps * splits + sp) * K + i;
+        const int t = cand_i[c];
+        if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
+      }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (id[i] >= 0) atomicOr(&bits_s[id[i] >> 5], 1u << (id[i] & 31));
+  }
+  __syncwarp();
+  for (int wd = lane; wd < words; wd += 32) {
+    unsigned m = bits_s[wd];
+    prop_bits[b * words + wd] = m;
+    if (m) {
+      int base = atomicAdd(&ctr->n_items1, __popc(m));
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        items[base++] = make_int2((int)b, wd * 32 + bit);
+      }
     }
   }
-  bool vs[1] = {true};
-  propose_finish<K>(b, vs, cand_s, cand_i, kRanges, bits_s, words, prop_bits, items, ctr, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,16 +538,17 @@ __device__ __forceinline__ void cp_async_wait_all()
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// One warp per (block, tile) item.  The warp first copies the tile's blob
-// into its own slice of shared memory (16-byte cp.async per lane; blob sizes
-// are multiples of 16), then every lane evaluates the tile's obstacles for
-// its pose, reading the records from shared memory as a broadcast.
+// One warp per work unit = (block, tile, part): part `pt` of `parts` covers
+// the tile's obstacles [pt * n_obs / parts, (pt + 1) * n_obs / parts).  The
+// warp copies those obstacle records and their vertex records into its own
+// slice of shared memory (16-byte cp.async per lane), then every lane
+// evaluates them for its pose, reading the records as a broadcast.
 template <int M>
 __global__ void __launch_bounds__(kEvalWarps * 32)
     eval_items(FootprintK F, ParamsK prm, const float *__restrict__ poses,
                const int *__restrict__ perm, long long P, const TileHdr *__restrict__ tiles,
                const unsigned char *__restrict__ blob, const int2 *__restrict__ items,
-               const int *__restrict__ n_items, int blob_cap,
+               const int *__restrict__ n_items, int parts, int blob_cap,
                unsigned long long *__restrict__ keys)
 {
   extern __shared__ __align__(16) unsigned char esm[];
@@ -539,13 +556,26 @@ __global__ void __launch_bounds__(kEvalWarps * 32)
   unsigned char *mine = esm + (size_t)warp * blob_cap;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int n = *n_items;
-  for (long long i = gw; i < n; i += nw) {
-    const int2 it = items[i];
+  const long long n = (long long)(*n_items) * parts;
+  for (long long u = gw; u < n; u += nw) {
+    const int2 it = items[u / parts];
+    const int pt = (int)(u % parts);
     const TileHdr h = tiles[it.y];
+    const int o0 = (int)((long long)h.n_obs * pt / parts);
+    const int o1 = (int)((long long)h.n_obs * (pt + 1) / parts);
+    if (o0 >= o1) continue;  // uniform over the warp
     const unsigned char *src = blob + h.blob_off;
-    __syncwarp();  // the previous item's reads of `mine` are done
-    for (int off = 16 * lane; off < h.blob_bytes; off += 16 * 32) cp_async16(mine + off, src + off);
+    const int4 *gob = reinterpret_cast<const int4 *>(src);
+    const int4 first = gob[o0], last = gob[o1 - 1];
+    const int v0 = first.x, v1 = last.x + last.y;  // vertex range of the part
+    const int obytes = 16 * (o1 - o0);
+    const int vbytes = 32 * (v1 - v0);
+    const unsigned char *vsrc = src + 16 * h.n_obs + 32 * v0;
+    __syncwarp();  // the previous unit's reads of `mine` are done
+    for (int off = 16 * lane; off < obytes; off += 16 * 32)
+      cp_async16(mine + off, src + 16 * o0 + off);
+    for (int off = 16 * lane; off < vbytes; off += 16 * 32)
+      cp_async16(mine + obytes + off, vsrc + off);
     const long long ps = (long long)it.x * kBlockPoses + lane;
     const bool valid = ps < P;
     float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
@@ -559,18 +589,18 @@ __global__ void __launch_bounds__(kEvalWarps * 32)
     cp_async_wait_all();
     __syncwarp();
     const int4 *ob = reinterpret_cast<const int4 *>(mine);
-    const float4 *vt = reinterpret_cast<const float4 *>(mine + 16 * h.n_obs);
+    const float4 *vt = reinterpret_cast<const float4 *>(mine + obytes);
     unsigned long long best = ~0ull;
-    for (int o = 0; o < h.n_obs; ++o) {
+    for (int o = 0; o < o1 - o0; ++o) {
       const int4 rec = ob[o];
-      const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
+      const float v =
+          obstacle_value<M>(F, px, py, c, s, vt + 2 * (rec.x - v0), rec.y, prm.eps_sat);
       const unsigned long long key = pack_key(v, rec.z);
       best = key < best ? key : best;
     }
     if (valid && best != ~0ull) atomicMin(&keys[p], best);
   }
 }
-
 
 // One CTA per pose block; each warp takes every 8th tile of a staged chunk,
 // its lanes are the block's 32 poses.
@@ -739,8 +769,8 @@ struct CullEvalCall {
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_items)");
     }
     eval_items<M><<<grid, kEvalWarps * 32, smem, st>>>(F, pk, poses, perm, P, sc->d_tiles,
-                                                       sc->d_blob, items, n_items, blob_cap,
-                                                       keys);
+                                                       sc->d_blob, items, n_items, kEvalParts,
+                                                       blob_cap, keys);
     return PSDF_OK;
   }
 };
@@ -963,22 +993,31 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
                                    hist);
     cull_scan<<<1, 1024, 0, st>>>(hist);
     cull_scatter<<<pb, 256, 0, st>>>(cell, P, hist, perm);
-    // proposals
+    // proposals: per-pose K best tiles per split, then each block's union
     const int K = opts->k;
-    const int n_ranges = opts->mode == PSDF_PROPOSE_MLP ? kProposeWarps / 2 : kProposeWarps;
-    const size_t smem = (size_t)kBlockPoses * n_ranges * K * 8 + 4 * (size_t)L.words;
-    if (smem > 48 * 1024) return fail(PSDF_ERR_CAPACITY, "scene has too many tiles for the cull");
+    if (L.splits > 64 || (scene->n_tiles + L.splits - 1) / L.splits > kMaxSplitTiles)
+      return fail(PSDF_ERR_CAPACITY, "scene has too many tiles for the cull");
+    float *cand_s = reinterpret_cast<float *>(ws + L.cand_s);
+    int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
     {
       ProfileScope prof("propose", st);
-      const unsigned nb = (unsigned)L.nb;
+      const bool net = opts->mode == PSDF_PROPOSE_MLP;
+      const long long warps = net ? (P + 15) / 16 : (P + 31) / 32;
+      dim3 sg((unsigned)((warps + kScoreWarps - 1) / kScoreWarps), (unsigned)L.splits);
+      const unsigned ub = (unsigned)((L.nb + 3) / 4);
+      const size_t usmem = 4 * sizeof(unsigned) * (size_t)L.words;
+      if (usmem > 48 * 1024) return fail(PSDF_ERR_CAPACITY, "scene has too many tiles for the cull");
 #define PSDF_PROPOSE(KK)                                                                      \
-  if (opts->mode == PSDF_PROPOSE_MLP)                                                         \
-    propose_mlp<KK><<<nb, kProposeWarps * 32, smem, st>>>(                                    \
-        poses, perm, P, scene->d_tiles, scene->n_tiles, F.radius, L.words, mlp->d_frag,       \
-        mlp->b2, bits, items1, ctr);                                                          \
+  if (net)                                                                                    \
+    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, perm, P, scene->d_tiles,            \
+                                                   scene->n_tiles, L.splits, F.radius,        \
+                                                   mlp->d_frag, mlp->b2, cand_s, cand_i);     \
   else                                                                                        \
-    propose_bound<KK><<<nb, kProposeWarps * 32, smem, st>>>(                                  \
-        poses, perm, P, scene->d_tiles, scene->n_tiles, F.radius, L.words, bits, items1, ctr);
+    score_bound<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, perm, P, scene->d_tiles,          \
+                                                     scene->n_tiles, L.splits, F.radius,      \
+                                                     cand_s, cand_i);                         \
+  propose_union<KK><<<ub, 128, usmem, st>>>(P, L.nb, L.splits, L.words, cand_s, cand_i, bits, \
+                                            items1, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
