@@ -181,18 +181,18 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
 
 /* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
  * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
- * the edge tiles.  Poses are grouped into blocks of 32 by a spatial sort.
- * Each pose proposes its k best tiles -- by the tile-proposal network's
- * predicted signed distance (PSDF_PROPOSE_MLP) or by the conservative lower
- * bound below (PSDF_PROPOSE_BOUND) -- and every block evaluates the union of
- * its poses' proposals exactly.  Then, for every tile not yet evaluated and
- * every pose, a conservative lower bound
- *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)   (rounded down)
+ * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
+ * tile-proposal network's predicted signed distance (PSDF_PROPOSE_MLP) or by
+ * the conservative bound below (PSDF_PROPOSE_BOUND) -- and those pairs are
+ * evaluated exactly.  Then, for every tile the pose did not propose, a
+ * conservative lower bound
+ *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
  * on the signed distance of every obstacle in the tile is compared with the
- * pose's current minimum; a tile is evaluated ("fallback") unless LB exceeds
- * it for every pose of the block.  No skipped tile can hold a smaller value
- * or a tie, so phi, the active pair and the gradient equal the full scan's.
- * The network only changes how much work the exact part does. */
+ * pose's current minimum; the pair is evaluated ("fallback") unless LB
+ * exceeds it.  No skipped pair can hold a smaller value or a tie, so phi,
+ * the active pair and the gradient equal the full scan's.  The network only
+ * changes how much work the exact part does.  Pairs are bucketed by tile and
+ * each tile is evaluated once for all the poses that need it. */
 typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
 
 #define PSDF_MLP_IN 16
@@ -207,10 +207,10 @@ typedef struct {
 } psdf_cull_opts;
 
 typedef struct {
-  int64_t pose_blocks;    /* blocks of 32 poses                                  */
-  int64_t tiles;          /* edge tiles in the scene                             */
-  int64_t proposed_items; /* (block, tile) pairs evaluated from the proposals    */
-  int64_t fallback_items; /* (block, tile) pairs added by the lower-bound check  */
+  int64_t pose_blocks;    /* reserved (0)                                        */
+  int64_t tiles;          /* reserved (0)                                        */
+  int64_t proposed_items; /* (pose, tile) pairs evaluated from the proposals     */
+  int64_t fallback_items; /* (pose, tile) pairs added by the lower-bound check   */
   int64_t fallback_poses; /* poses needing at least one tile beyond the proposal */
 } psdf_cull_stats;
 

@@ -1,24 +1,25 @@
 // Exact tile cull with a proposal (psdf_eval_culled and its helpers).
 //
-// Pipeline (one stream, no host synchronization):
-//   1. cull_init        keys = +inf, counters and cell histogram cleared
-//   2. cull_cells / cull_scan / cull_scatter
-//                       spatial counting sort of the poses on a 64 x 64 grid
-//                       in Morton order; blocks of 32 consecutive sorted poses
-//   3. propose_*        every pose ranks all tiles (tile-proposal network on
-//                       tensor cores, or the conservative bound) and keeps its
-//                       k best; each block's union -> (block, tile) work items
-//   4. eval_items       one warp per item: the block's 32 poses x the tile's
-//                       obstacles, exactly as the full scan evaluates them
-//   5. cull_fallback    per pose and tile not yet evaluated: lower bound on
-//                       the tile's values vs the pose's current minimum; any
-//                       pose of the block that cannot rule the tile out adds a
-//                       work item
-//   6. eval_items       the fallback items
-//   7. epilogue         as for the full scan
-// Skipped tiles hold only values strictly above each pose's minimum, and the
-// minimum over 64-bit keys does not depend on evaluation order, so the result
-// is the full scan's bit for bit.
+// Work is organised as (pose, tile) pairs, bucketed by tile:
+//   1. cull_init       keys = +inf, per-tile counters and flags cleared
+//   2. score_*         every pose ranks all tiles (tile-proposal network on
+//                      tensor cores, or the conservative bound); K best per
+//                      tile split
+//   3. merge_emit      per pose: its K best tiles over all splits; count them
+//                      per tile
+//   4. tiles_scan      per-tile offsets (exclusive prefix sum)
+//   5. scatter_prop    per-tile lists of the poses that proposed the tile
+//   6. eval_lists      one CTA per tile: the tile's blob staged in shared
+//                      memory, lanes = (pose, obstacle range) pairs so that
+//                      warps stay full, exact evaluation, one atomicMin per
+//                      lane into the pose's 64-bit key
+//   7. fb_count / tiles_scan / fb_scatter / eval_lists
+//                      fallback: every tile a pose did not propose whose
+//                      lower bound does not exceed the pose's current minimum
+//   8. epilogue        as for the full scan
+// A skipped (pose, tile) pair holds only values strictly above the pose's
+// minimum, and the minimum over 64-bit keys does not depend on evaluation
+// order, so the result equals the full scan's bit for bit.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -37,29 +38,28 @@ struct psdf_mlp {
 
 namespace psdf {
 
-constexpr int kBlockPoses = 32;
-constexpr int kCellBits = 6;
-constexpr int kCells = 1 << (2 * kCellBits);
-constexpr int kEvalParts = 4;  // obstacle ranges per (block, tile) item
 constexpr int kMaxK = PSDF_CULL_MAX_K;
-constexpr int kFallbackWarps = 8;
-constexpr int kTileChunk = 512;  // tiles staged in shared memory at a time
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
+constexpr int kScoreWarps = 4;
+constexpr int kMaxSplitTiles = 1024;  // tiles per split staged in shared memory
+constexpr int kListThreads = 128;     // threads of an eval_lists CTA
+constexpr int kMaxScanTiles = 1024 * 64;
 
-// counters at the start of the workspace (after the error word)
+// counters at the start of the workspace
 struct CullCounters {
   int err;
-  int n_items1;
-  int n_items2;
-  int fallback_poses;
+  int n_prop;          // proposed (pose, tile) pairs
+  int n_fb;            // fallback (pose, tile) pairs
+  int fallback_poses;  // poses with at least one fallback pair
 };
 
 struct CullLayout {
-  size_t keys, perm, cell, hist, bits, items1, items2, cand_s, cand_i, total;
-  long long nb;
-  int words, splits;
+  size_t keys, prop, flags, cand_s, cand_i, hist1, cur1, hist2, cur2, list1, list2, total;
+  int splits;
 };
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Tile splits of the proposal scoring: enough (group, split) warps to fill
 // the GPU, at most 1024 tiles per split staged in shared memory.
@@ -67,29 +67,28 @@ static int score_splits(long long P, int n_tiles)
 {
   const long long groups = std::max<long long>(1, (P + 15) / 16);
   long long sp = (2048 + groups - 1) / groups;
-  sp = std::max<long long>(sp, (n_tiles + 1023) / 1024);
+  sp = std::max<long long>(sp, (n_tiles + kMaxSplitTiles - 1) / kMaxSplitTiles);
   return (int)std::max<long long>(1, std::min<long long>(sp, 64));
 }
-
-static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 static CullLayout cull_layout(long long P, int n_tiles)
 {
   CullLayout L;
-  L.nb = (std::max<long long>(P, 1) + kBlockPoses - 1) / kBlockPoses;
-  L.words = std::max(1, (n_tiles + 31) / 32);
-  size_t o = 256;
-  L.keys = o; o = align256(o + 8 * (size_t)std::max<long long>(P, 1));
-  L.perm = o; o = align256(o + 4 * (size_t)std::max<long long>(P, 1));
-  L.cell = o; o = align256(o + 4 * (size_t)std::max<long long>(P, 1));
-  L.hist = o; o = align256(o + 4 * (size_t)kCells);
-  L.bits = o; o = align256(o + 4 * (size_t)L.nb * L.words);
-  L.items1 = o; o = align256(o + 8 * (size_t)L.nb * kBlockPoses * kMaxK);
-  L.items2 = o; o = align256(o + 8 * (size_t)L.nb * std::max(n_tiles, 1));
+  const size_t Pz = (size_t)std::max<long long>(P, 1);
+  const size_t Tz = (size_t)std::max(n_tiles, 1);
   L.splits = score_splits(P, n_tiles);
-  const size_t nc = (size_t)std::max<long long>(P, 1) * L.splits * kMaxK;
-  L.cand_s = o; o = align256(o + 4 * nc);
-  L.cand_i = o; o = align256(o + 4 * nc);
+  size_t o = 256;
+  L.keys = o; o = align256(o + 8 * Pz);
+  L.prop = o; o = align256(o + 4 * Pz * kMaxK);
+  L.flags = o; o = align256(o + 4 * Pz);
+  L.cand_s = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
+  L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
+  L.hist1 = o; o = align256(o + 4 * Tz);
+  L.cur1 = o; o = align256(o + 4 * Tz);
+  L.hist2 = o; o = align256(o + 4 * Tz);
+  L.cur2 = o; o = align256(o + 4 * Tz);
+  L.list1 = o; o = align256(o + 4 * Pz * kMaxK);
+  L.list2 = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
   return L;
 }
@@ -98,15 +97,17 @@ static CullLayout cull_layout(long long P, int n_tiles)
 // conservative lower bound and network inputs
 // ---------------------------------------------------------------------------
 // Lower bound (metres) on the separation of the posed footprint from any
-// point of the tile's AABB, with a margin that covers the float32 error of
-// the evaluated values; every operation rounds toward -inf.
+// point of the tile's AABB: distance from p to the AABB minus the footprint
+// radius, minus a margin of 1e-4 m + 1e-5 of the distance.  The margin is far
+// above the float32 rounding of this bound and of the evaluated values
+// (about 1e-6 of the distance), so a positive bound is below every obstacle
+// value the kernels compute for the tile.
 __device__ __forceinline__ float tile_lb(const float *ab, float px, float py, float rfoot)
 {
-  const float dx = fmaxf(fmaxf(__fsub_rd(ab[0], px), __fsub_rd(px, ab[2])), 0.f);
-  const float dy = fmaxf(fmaxf(__fsub_rd(ab[1], py), __fsub_rd(py, ab[3])), 0.f);
-  const float d = __fsqrt_rd(__fadd_rd(__fmul_rd(dx, dx), __fmul_rd(dy, dy)));
-  const float margin = __fmaf_ru(d, 1e-5f, 1e-4f);
-  return __fsub_rd(__fsub_rd(d, rfoot), margin);
+  const float dx = fmaxf(fmaxf(ab[0] - px, px - ab[2]), 0.f);
+  const float dy = fmaxf(fmaxf(ab[1] - py, py - ab[3]), 0.f);
+  const float d = sqrtf(dx * dx + dy * dy);
+  return (d - rfoot) - (1e-4f + 1e-5f * d);
 }
 
 // The same bound in the min-key value domain (squared separation, or -inf
@@ -114,12 +115,19 @@ __device__ __forceinline__ float tile_lb(const float *ab, float px, float py, fl
 __device__ __forceinline__ float tile_lb_value(const float *ab, float px, float py, float rfoot)
 {
   const float lb = tile_lb(ab, px, py, rfoot);
-  return lb > 0.f ? __fmul_rd(lb, lb) : -kInf;
+  return lb > 0.f ? lb * lb * (1.f - 1e-6f) : -kInf;
 }
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi)
 {
   return fminf(fmaxf(x, lo), hi);
+}
+
+__device__ __forceinline__ float approx_sqrt(float x)
+{
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // Network inputs 2q, 2q+1: AABB corner q (0..3) in the pose frame.
@@ -133,29 +141,22 @@ __device__ __forceinline__ void feat_corner(const float *ab, int q, float px, fl
   f1 = 0.1f * clampf(-s * dx + c * dy, -20.f, 20.f);
 }
 
-__device__ __forceinline__ float corner_dist(const float *ab, int q, float px, float py)
-{
-  const float cx = (q == 1 || q == 2) ? ab[2] : ab[0];
-  const float cy = (q >= 2) ? ab[3] : ab[1];
-  return 0.1f * fminf(sqrtf((cx - px) * (cx - px) + (cy - py) * (cy - py)), 30.f);
-}
-
-// Network inputs 8 + 2q, 9 + 2q.
+// Network inputs 8 + 2q, 9 + 2q, without divergence across the quad:
+// q = 0: distances to corners 0, 1; q = 1: to corners 2, 3; q = 2: distance
+// to the AABB, footprint radius; q = 3: edge fraction, 1.
 __device__ __forceinline__ void feat_rest(const float *ab, int q, float px, float py,
                                           float rfoot, float edge_frac, float &f0, float &f1)
 {
-  if (q < 2) {
-    f0 = corner_dist(ab, 2 * q, px, py);
-    f1 = corner_dist(ab, 2 * q + 1, px, py);
-  } else if (q == 2) {
-    const float dx = fmaxf(fmaxf(ab[0] - px, px - ab[2]), 0.f);
-    const float dy = fmaxf(fmaxf(ab[1] - py, py - ab[3]), 0.f);
-    f0 = 0.1f * fminf(sqrtf(dx * dx + dy * dy), 30.f);
-    f1 = rfoot;
-  } else {
-    f0 = edge_frac;
-    f1 = 1.f;
-  }
+  // point a: corner 0 (q = 0), corner 2 (q = 1), the AABB point nearest p (q = 2)
+  const float ax = (q == 0) ? ab[0] : (q == 1) ? ab[2] : clampf(px, ab[0], ab[2]);
+  const float ay = (q == 0) ? ab[1] : (q == 1) ? ab[3] : clampf(py, ab[1], ab[3]);
+  // point b: corner 1 (q = 0), corner 3 (q = 1)
+  const float bx = (q == 0) ? ab[2] : ab[0];
+  const float by = (q == 0) ? ab[1] : ab[3];
+  const float da = approx_sqrt((ax - px) * (ax - px) + (ay - py) * (ay - py));
+  const float db = approx_sqrt((bx - px) * (bx - px) + (by - py) * (by - py));
+  f0 = (q == 3) ? edge_frac : 0.1f * fminf(da, 30.f);
+  f1 = (q == 3) ? 1.f : (q == 2) ? rfoot : 0.1f * fminf(db, 30.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -238,91 +239,6 @@ __device__ __forceinline__ void mlp_rows(const MlpFrags &w, const float *ab, int
 }
 
 // ---------------------------------------------------------------------------
-// pose sort
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int spread6(int x)
-{
-  x &= 63;
-  x = (x | (x << 4)) & 0x30F;
-  x = (x | (x << 2)) & 0x333;
-  x = (x | (x << 1)) & 0x555;
-  return x;
-}
-
-__global__ void cull_init(unsigned long long *keys, long long P, int *hist,
-                          CullCounters *ctr)
-{
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P) keys[i] = ~0ull;
-  if (i < kCells) hist[i] = 0;
-  if (i == 0) {
-    ctr->err = 0;
-    ctr->n_items1 = 0;
-    ctr->n_items2 = 0;
-    ctr->fallback_poses = 0;
-  }
-}
-
-__global__ void cull_cells(const float *__restrict__ poses, long long P, float x0, float y0,
-                           float inv_cell, int *__restrict__ cell, int *__restrict__ hist)
-{
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  float fx = (poses[3 * p] - x0) * inv_cell, fy = (poses[3 * p + 1] - y0) * inv_cell;
-  fx = (fx == fx) ? clampf(fx, 0.f, 63.f) : 0.f;  // NaN poses go to cell 0
-  fy = (fy == fy) ? clampf(fy, 0.f, 63.f) : 0.f;
-  const int code = spread6((int)fx) | (spread6((int)fy) << 1);
-  cell[p] = code;
-  atomicAdd(&hist[code], 1);
-}
-
-// exclusive scan of the 4096-bin histogram, one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) cull_scan(int *hist)
-{
-  __shared__ int warp_sum[32];
-  const int tid = threadIdx.x;
-  int v[4], s = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    v[i] = hist[4 * tid + i];
-    s += v[i];
-  }
-  int incl = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((tid & 31) >= o) incl += n;
-  }
-  if ((tid & 31) == 31) warp_sum[tid >> 5] = incl;
-  __syncthreads();
-  if (tid < 32) {
-    int w = warp_sum[tid], wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_up_sync(0xffffffffu, wi, o);
-      if (tid >= o) wi += n;
-    }
-    warp_sum[tid] = wi - w;
-  }
-  __syncthreads();
-  int base = warp_sum[tid >> 5] + incl - s;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    hist[4 * tid + i] = base;
-    base += v[i];
-  }
-}
-
-__global__ void cull_scatter(const int *__restrict__ cell, long long P, int *__restrict__ offs,
-                             int *__restrict__ perm)
-{
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const int pos = atomicAdd(&offs[cell[p]], 1);
-  perm[pos] = (int)p;
-}
-
-// ---------------------------------------------------------------------------
 // proposals
 // ---------------------------------------------------------------------------
 template <int K>
@@ -344,16 +260,14 @@ __device__ __forceinline__ void topk_insert(float (&sc)[K], int (&id)[K], float 
   }
 }
 
-// Candidates of a pose for one tile split: its K best (score, tile), kept in
-// global memory at cand[(sorted pose * splits + split) * K + i].
 template <int K>
-__device__ __forceinline__ void store_cand(float *cand_s, int *cand_i, long long ps, int split,
+__device__ __forceinline__ void store_cand(float *cand_s, int *cand_i, long long p, int split,
                                            int splits, const float (&sc)[K], const int (&id)[K])
 {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    cand_s[(ps * splits + split) * K + i] = sc[i];
-    cand_i[(ps * splits + split) * K + i] = id[i];
+    cand_s[(p * splits + split) * K + i] = sc[i];
+    cand_i[(p * splits + split) * K + i] = id[i];
   }
 }
 
@@ -368,26 +282,41 @@ __device__ __forceinline__ void stage_tiles(const TileHdr *__restrict__ tiles, i
   }
 }
 
-constexpr int kScoreWarps = 4;
-constexpr int kMaxSplitTiles = 1024;  // tiles per split staged in shared memory
+__global__ void cull_init(unsigned long long *keys, int *flags, long long P, int *hist1,
+                          int *hist2, int T, CullCounters *ctr)
+{
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) {
+    keys[i] = ~0ull;
+    flags[i] = 0;
+  }
+  if (i < T) {
+    hist1[i] = 0;
+    hist2[i] = 0;
+  }
+  if (i == 0) {
+    ctr->err = 0;
+    ctr->n_prop = 0;
+    ctr->n_fb = 0;
+    ctr->fallback_poses = 0;
+  }
+}
 
-// Bound proposal scores: warp = 32 sorted poses, blockIdx.y = tile split.
+// Bound proposal scores: thread = pose, blockIdx.y = tile split.
 template <int K>
 __global__ void __launch_bounds__(kScoreWarps * 32)
-    score_bound(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
-                const TileHdr *__restrict__ tiles, int n_tiles, int splits, float rfoot,
-                float *__restrict__ cand_s, int *__restrict__ cand_i)
+    score_bound(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+                int n_tiles, int splits, float rfoot, float *__restrict__ cand_s,
+                int *__restrict__ cand_i)
 {
   __shared__ float4 ab_s[kMaxSplitTiles];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int split = blockIdx.y;
   const int t0 = (int)((long long)n_tiles * split / splits);
   const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
   stage_tiles(tiles, t0, t1, ab_s, nullptr);
   __syncthreads();
-  const long long ps = ((long long)blockIdx.x * kScoreWarps + warp) * 32 + lane;
-  if (ps >= P) return;
-  const long long p = perm[ps];
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
   const float px = poses[3 * p], py = poses[3 * p + 1];
   float sc[K];
   int id[K];
@@ -401,17 +330,16 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
     const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
     topk_insert<K>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
   }
-  store_cand<K>(cand_s, cand_i, ps, split, splits, sc, id);
+  store_cand<K>(cand_s, cand_i, p, split, splits, sc, id);
 }
 
-// Network proposal scores: warp = 16 sorted poses (the 16 rows of every
+// Network proposal scores: warp = 16 poses (the 16 rows of every
 // tensor-core tile), blockIdx.y = tile split; two tiles in flight per step.
 template <int K>
 __global__ void __launch_bounds__(kScoreWarps * 32)
-    score_mlp(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
-              const TileHdr *__restrict__ tiles, int n_tiles, int splits, float rfoot,
-              const uint32_t *__restrict__ frag, float b2, float *__restrict__ cand_s,
-              int *__restrict__ cand_i)
+    score_mlp(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+              int n_tiles, int splits, float rfoot, const uint32_t *__restrict__ frag, float b2,
+              float *__restrict__ cand_s, int *__restrict__ cand_i)
 {
   __shared__ float4 ab_s[kMaxSplitTiles];
   __shared__ float ef_s[kMaxSplitTiles];
@@ -424,19 +352,17 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
   const long long group = (long long)blockIdx.x * kScoreWarps + warp;
   if (group * 16 >= P) return;  // uniform over the warp
   const int g = lane >> 2, q = lane & 3;
-  const long long psa = group * 16 + g, psb = group * 16 + g + 8;
+  const long long pa = group * 16 + g, pb = group * 16 + g + 8;
   float pxa = 0.f, pya = 0.f, ca = 1.f, sa = 0.f, pxb = 0.f, pyb = 0.f, cb = 1.f, sb = 0.f;
-  if (psa < P) {
-    const long long p = perm[psa];
-    pxa = poses[3 * p];
-    pya = poses[3 * p + 1];
-    sincosf(poses[3 * p + 2], &sa, &ca);
+  if (pa < P) {
+    pxa = poses[3 * pa];
+    pya = poses[3 * pa + 1];
+    sincosf(poses[3 * pa + 2], &sa, &ca);
   }
-  if (psb < P) {
-    const long long p = perm[psb];
-    pxb = poses[3 * p];
-    pyb = poses[3 * p + 1];
-    sincosf(poses[3 * p + 2], &sb, &cb);
+  if (pb < P) {
+    pxb = poses[3 * pb];
+    pyb = poses[3 * pb + 1];
+    sincosf(poses[3 * pb + 2], &sb, &cb);
   }
   MlpFrags w;
   load_frags(frag, lane, w);
@@ -466,65 +392,97 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
     }
   }
   if (q == 0) {
-    if (psa < P) store_cand<K>(cand_s, cand_i, psa, split, splits, sca, ida);
-    if (psb < P) store_cand<K>(cand_s, cand_i, psb, split, splits, scb, idb);
+    if (pa < P) store_cand<K>(cand_s, cand_i, pa, split, splits, sca, ida);
+    if (pb < P) store_cand<K>(cand_s, cand_i, pb, split, splits, scb, idb);
   }
 }
 
-// One warp per block of 32 sorted poses: merge each pose's candidates over
-// the splits into its K best, mark the block's union, emit (block, tile) items.
+// Per pose: its K best tiles over the splits -> prop[p * K + i], counted per tile.
 template <int K>
-__global__ void __launch_bounds__(128)
-    propose_union(long long P, long long nb, int splits, int words,
-                  const float *__restrict__ cand_s, const int *__restrict__ cand_i,
-                  unsigned *__restrict__ prop_bits, int2 *__restrict__ items, CullCounters *ctr)
+__global__ void merge_emit(long long P, int splits, const float *__restrict__ cand_s,
+                           const int *__restrict__ cand_i, int *__restrict__ prop,
+                           int *__restrict__ hist)
 {
-  extern __shared__ unsigned ubits[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long b = (long long)blockIdx.x * 4 + warp;
-  unsigned *bits_s = ubits + warp * words;
-  if (b >= nb) return;  // uniform over the warp
-  for (int wd = lane; wd < words; wd += 32) bits_s[wd] = 0u;
-  __syncwarp();
-  const long long ps = b * kBlockPoses + lane;
-  if (ps < P) {
-    float sc[K];
-    int id[K];
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float sc[K];
+  int id[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    sc[i] = kInf;
+    id[i] = -1;
+  }
+  for (int sp = 0; sp < splits; ++sp)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      sc[i] = kInf;
-      id[i] = -1;
+      const long long c = (p * splits + sp) * K + i;
+      const int t = cand_i[c];
+      if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
     }
-    for (int sp = 0; sp < splits; ++sp)
-      for (int i = 0; i < K; ++i) {
-        const long long c = (ps * splits + sp) * K + i;
-        const int t = cand_i[c];
-        if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
-      }
 #pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (id[i] >= 0) atomicOr(&bits_s[id[i] >> 5], 1u << (id[i] & 31));
+  for (int i = 0; i < K; ++i) {
+    prop[p * kMaxK + i] = id[i];
+    if (id[i] >= 0) atomicAdd(&hist[id[i]], 1);
   }
-  __syncwarp();
-  for (int wd = lane; wd < words; wd += 32) {
-    unsigned m = bits_s[wd];
-    prop_bits[b * words + wd] = m;
-    if (m) {
-      int base = atomicAdd(&ctr->n_items1, __popc(m));
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        items[base++] = make_int2((int)b, wd * 32 + bit);
-      }
+#pragma unroll
+  for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
+}
+
+// Exclusive prefix sum of per-tile counts (one CTA of 1024 threads, each a
+// run of consecutive tiles); cur[t] = off[t] (the scatter cursor), and the
+// total goes to *total.
+__global__ void __launch_bounds__(1024) tiles_scan(const int *__restrict__ hist, int T,
+                                                   int *__restrict__ off, int *total)
+{
+  __shared__ int warp_sum[32];
+  const int tid = threadIdx.x;
+  const int per = (T + 1023) / 1024;
+  const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
+  int s = 0;
+  for (int i = b0; i < b1; ++i) s += hist[i];
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((tid & 31) >= o) incl += n;
+  }
+  if ((tid & 31) == 31) warp_sum[tid >> 5] = incl;
+  __syncthreads();
+  if (tid < 32) {
+    const int w = warp_sum[tid];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, wi, o);
+      if (tid >= o) wi += n;
     }
+    warp_sum[tid] = wi - w;
+  }
+  __syncthreads();
+  int base = warp_sum[tid >> 5] + incl - s;
+  for (int i = b0; i < b1; ++i) {
+    off[i] = base;
+    base += hist[i];
+  }
+  if (tid == 1023) *total = base;
+}
+
+// Lists of poses per tile for the proposals.
+__global__ void scatter_prop(long long P, const int *__restrict__ prop, int *__restrict__ cur,
+                             int *__restrict__ list)
+{
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+#pragma unroll
+  for (int i = 0; i < kMaxK; ++i) {
+    const int t = prop[p * kMaxK + i];
+    if (t >= 0) list[atomicAdd(&cur[t], 1)] = (int)p;
   }
 }
 
 // ---------------------------------------------------------------------------
-// exact evaluation of (block, tile) items, fallback check
+// exact evaluation of the per-tile lists
 // ---------------------------------------------------------------------------
-constexpr int kEvalWarps = 4;
-
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
@@ -538,124 +496,99 @@ __device__ __forceinline__ void cp_async_wait_all()
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// One warp per work unit = (block, tile, part): part `pt` of `parts` covers
-// the tile's obstacles [pt * n_obs / parts, (pt + 1) * n_obs / parts).  The
-// warp copies those obstacle records and their vertex records into its own
-// slice of shared memory (16-byte cp.async per lane), then every lane
-// evaluates them for its pose, reading the records as a broadcast.
+// One CTA per tile.  The tile's blob is copied into shared memory (16-byte
+// cp.async per thread).  The tile's cnt poses are split over S obstacle
+// ranges each, S = clamp(128 / cnt, 1, n_obs), so that cnt * S lanes (about
+// one CTA's worth when few poses need the tile) share the work; lane l
+// evaluates pose list[l / S] against obstacle range l % S and merges its
+// minimum into the pose's key.
 template <int M>
-__global__ void __launch_bounds__(kEvalWarps * 32)
-    eval_items(FootprintK F, ParamsK prm, const float *__restrict__ poses,
-               const int *__restrict__ perm, long long P, const TileHdr *__restrict__ tiles,
-               const unsigned char *__restrict__ blob, const int2 *__restrict__ items,
-               const int *__restrict__ n_items, int parts, int blob_cap,
-               unsigned long long *__restrict__ keys)
+__global__ void __launch_bounds__(kListThreads)
+    eval_lists(FootprintK F, ParamsK prm, const float *__restrict__ poses,
+               const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob,
+               const int *__restrict__ hist, const int *__restrict__ off,
+               const int *__restrict__ list, unsigned long long *__restrict__ keys)
 {
-  extern __shared__ __align__(16) unsigned char esm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char *mine = esm + (size_t)warp * blob_cap;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long n = (long long)(*n_items) * parts;
-  for (long long u = gw; u < n; u += nw) {
-    const int2 it = items[u / parts];
-    const int pt = (int)(u % parts);
-    const TileHdr h = tiles[it.y];
-    const int o0 = (int)((long long)h.n_obs * pt / parts);
-    const int o1 = (int)((long long)h.n_obs * (pt + 1) / parts);
-    if (o0 >= o1) continue;  // uniform over the warp
-    const unsigned char *src = blob + h.blob_off;
-    const int4 *gob = reinterpret_cast<const int4 *>(src);
-    const int4 first = gob[o0], last = gob[o1 - 1];
-    const int v0 = first.x, v1 = last.x + last.y;  // vertex range of the part
-    const int obytes = 16 * (o1 - o0);
-    const int vbytes = 32 * (v1 - v0);
-    const unsigned char *vsrc = src + 16 * h.n_obs + 32 * v0;
-    __syncwarp();  // the previous unit's reads of `mine` are done
-    for (int off = 16 * lane; off < obytes; off += 16 * 32)
-      cp_async16(mine + off, src + 16 * o0 + off);
-    for (int off = 16 * lane; off < vbytes; off += 16 * 32)
-      cp_async16(mine + obytes + off, vsrc + off);
-    const long long ps = (long long)it.x * kBlockPoses + lane;
-    const bool valid = ps < P;
-    float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
-    long long p = 0;
-    if (valid) {
-      p = perm[ps];
-      px = poses[3 * p];
-      py = poses[3 * p + 1];
-      sincosf(poses[3 * p + 2], &s, &c);
-    }
-    cp_async_wait_all();
-    __syncwarp();
-    const int4 *ob = reinterpret_cast<const int4 *>(mine);
-    const float4 *vt = reinterpret_cast<const float4 *>(mine + obytes);
+  extern __shared__ __align__(16) unsigned char tsm[];
+  const int t = blockIdx.x;
+  const int cnt = hist[t];
+  if (cnt == 0) return;  // uniform over the CTA
+  const TileHdr h = tiles[t];
+  const unsigned char *src = blob + h.blob_off;
+  for (int o = 16 * threadIdx.x; o < h.blob_bytes; o += 16 * kListThreads)
+    cp_async16(tsm + o, src + o);
+  const int S = max(1, min(kListThreads / cnt, h.n_obs));
+  const long long L = (long long)cnt * S;
+  const int base = off[t];
+  cp_async_wait_all();
+  __syncthreads();
+  const int4 *ob = reinterpret_cast<const int4 *>(tsm);
+  const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
+  for (long long l = threadIdx.x; l < L; l += kListThreads) {
+    const int pi = (int)(l / S), part = (int)(l % S);
+    const long long p = list[base + pi];
+    const float px = poses[3 * p], py = poses[3 * p + 1];
+    float s, c;
+    sincosf(poses[3 * p + 2], &s, &c);
+    const int o0 = (int)((long long)h.n_obs * part / S);
+    const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
     unsigned long long best = ~0ull;
-    for (int o = 0; o < o1 - o0; ++o) {
+    for (int o = o0; o < o1; ++o) {
       const int4 rec = ob[o];
-      const float v =
-          obstacle_value<M>(F, px, py, c, s, vt + 2 * (rec.x - v0), rec.y, prm.eps_sat);
+      const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
       const unsigned long long key = pack_key(v, rec.z);
       best = key < best ? key : best;
     }
-    if (valid && best != ~0ull) atomicMin(&keys[p], best);
+    if (best != ~0ull) atomicMin(&keys[p], best);
   }
 }
 
-// One CTA per pose block; each warp takes every 8th tile of a staged chunk,
-// its lanes are the block's 32 poses.
-__global__ void __launch_bounds__(kFallbackWarps * 32)
-    cull_fallback(const float *__restrict__ poses, const int *__restrict__ perm, long long P,
-                  long long nb, const TileHdr *__restrict__ tiles, int n_tiles, float rfoot,
-                  int words, const unsigned *__restrict__ prop_bits,
-                  const unsigned long long *__restrict__ keys, int2 *__restrict__ items,
-                  CullCounters *ctr)
+// ---------------------------------------------------------------------------
+// fallback: (pose, tile) pairs whose bound does not exceed the pose's minimum
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool fb_need(const float *ab, float px, float py, float rfoot,
+                                        float best, int t, const int (&pr)[kMaxK])
 {
-  __shared__ float4 ab_s[kTileChunk];
-  __shared__ unsigned bits_s[kTileChunk / 32];
-  __shared__ unsigned any_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
-    const long long ps = b * kBlockPoses + lane;
-    const bool valid = ps < P;
-    float px = 0.f, py = 0.f, best = -kInf;
-    if (valid) {
-      const long long p = perm[ps];
-      px = poses[3 * p];
-      py = poses[3 * p + 1];
-      const unsigned long long key = keys[p];
-      best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
+  bool proposed = false;
+#pragma unroll
+  for (int i = 0; i < kMaxK; ++i) proposed |= (pr[i] == t);
+  return !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
+}
+
+// SCATTER = false: count the pairs per tile and flag the poses; SCATTER =
+// true: write them into the per-tile lists (same decisions).
+template <bool SCATTER>
+__global__ void __launch_bounds__(128)
+    fb_pairs(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+             int n_tiles, int splits, float rfoot, const unsigned long long *__restrict__ keys,
+             const int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ cur,
+             int *__restrict__ list, int *__restrict__ flags, CullCounters *ctr)
+{
+  __shared__ float4 ab_s[kMaxSplitTiles];
+  const int split = blockIdx.y;
+  const int t0 = (int)((long long)n_tiles * split / splits);
+  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
+  stage_tiles(tiles, t0, t1, ab_s, nullptr);
+  __syncthreads();
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float px = poses[3 * p], py = poses[3 * p + 1];
+  const unsigned long long key = keys[p];
+  const float best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
+  int pr[kMaxK];
+#pragma unroll
+  for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
+  bool any = false;
+  for (int i = 0; i < t1 - t0; ++i) {
+    const float4 a4 = ab_s[i];
+    const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+    if (fb_need(ab, px, py, rfoot, best, t0 + i, pr)) {
+      any = true;
+      if (SCATTER) list[atomicAdd(&cur[t0 + i], 1)] = (int)p;
+      else atomicAdd(&hist[t0 + i], 1);
     }
-    if (threadIdx.x == 0) any_s = 0u;
-    bool any = false;
-    for (int c0 = 0; c0 < n_tiles; c0 += kTileChunk) {
-      const int cn = min(kTileChunk, n_tiles - c0);
-      __syncthreads();
-      for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-        const TileHdr h = tiles[c0 + i];
-        ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
-      }
-      for (int i = threadIdx.x; i < (cn + 31) / 32; i += blockDim.x)
-        bits_s[i] = prop_bits[b * words + (c0 >> 5) + i];
-      __syncthreads();
-      for (int i = warp; i < cn; i += kFallbackWarps) {
-        const float4 a4 = ab_s[i];
-        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        const bool proposed = (bits_s[i >> 5] >> (i & 31)) & 1u;
-        const bool need = valid && !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
-        const unsigned m = __ballot_sync(0xffffffffu, need);
-        if (m && lane == 0) {
-          const int idx = atomicAdd(&ctr->n_items2, 1);
-          items[idx] = make_int2((int)b, c0 + i);
-        }
-        any |= need;
-      }
-    }
-    const unsigned fm = __ballot_sync(0xffffffffu, any);
-    if (lane == 0 && fm) atomicOr(&any_s, fm);
-    __syncthreads();
-    if (threadIdx.x == 0 && any_s) atomicAdd(&ctr->fallback_poses, __popc(any_s));
   }
+  if (!SCATTER && any && atomicExch(&flags[p], 1) == 0) atomicAdd(&ctr->fallback_poses, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -755,22 +688,20 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 // host side
 // ---------------------------------------------------------------------------
 template <int M>
-struct CullEvalCall {
-  static int run(const FootprintK &F, const ParamsK &pk, const float *poses, const int *perm,
-                 long long P, const psdf_scene *sc, const int2 *items, const int *n_items,
-                 unsigned long long *keys, int grid, cudaStream_t st)
+struct ListEvalCall {
+  static int run(const FootprintK &F, const ParamsK &pk, const float *poses,
+                 const psdf_scene *sc, const int *hist, const int *off, const int *list,
+                 unsigned long long *keys, cudaStream_t st)
   {
-    const int blob_cap = (sc->max_blob_bytes + 15) / 16 * 16;
-    const size_t smem = (size_t)kEvalWarps * blob_cap;
+    const size_t smem = (size_t)(sc->max_blob_bytes + 15) / 16 * 16;
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(eval_items<M>,
+      cudaError_t e = cudaFuncSetAttribute(eval_lists<M>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_items)");
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
-    eval_items<M><<<grid, kEvalWarps * 32, smem, st>>>(F, pk, poses, perm, P, sc->d_tiles,
-                                                       sc->d_blob, items, n_items, kEvalParts,
-                                                       blob_cap, keys);
+    eval_lists<M><<<sc->n_tiles, kListThreads, smem, st>>>(F, pk, poses, sc->d_tiles,
+                                                          sc->d_blob, hist, off, list, keys);
     return PSDF_OK;
   }
 };
@@ -965,7 +896,11 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   if (rc) return rc;
   if (P == 0) return PSDF_OK;
   if (P > (1LL << 31) - 1) return fail(PSDF_ERR_CAPACITY, "P too large for the cull");
-  const CullLayout L = cull_layout(P, scene->n_tiles);
+  if (scene->n_tiles > kMaxScanTiles) return fail(PSDF_ERR_CAPACITY, "too many tiles for the cull");
+  const int T = scene->n_tiles;
+  if ((long long)P * std::max(T, 1) > (1LL << 31) - 1)
+    return fail(PSDF_ERR_CAPACITY, "poses x tiles too large for the cull's pair lists");
+  const CullLayout L = cull_layout(P, T);
   if (!workspace) return fail(PSDF_ERR_ARG, "workspace is NULL");
   if (((uintptr_t)workspace & 255u) != 0) return fail(PSDF_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace_bytes < L.total)
@@ -974,50 +909,36 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
   CullCounters *ctr = reinterpret_cast<CullCounters *>(ws);
   unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
-  int *perm = reinterpret_cast<int *>(ws + L.perm);
-  int *cell = reinterpret_cast<int *>(ws + L.cell);
-  int *hist = reinterpret_cast<int *>(ws + L.hist);
-  unsigned *bits = reinterpret_cast<unsigned *>(ws + L.bits);
-  int2 *items1 = reinterpret_cast<int2 *>(ws + L.items1);
-  int2 *items2 = reinterpret_cast<int2 *>(ws + L.items2);
+  int *prop = reinterpret_cast<int *>(ws + L.prop);
+  int *flags = reinterpret_cast<int *>(ws + L.flags);
+  float *cand_s = reinterpret_cast<float *>(ws + L.cand_s);
+  int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
+  int *hist1 = reinterpret_cast<int *>(ws + L.hist1);
+  int *cur1 = reinterpret_cast<int *>(ws + L.cur1);
+  int *hist2 = reinterpret_cast<int *>(ws + L.hist2);
+  int *cur2 = reinterpret_cast<int *>(ws + L.cur2);
+  int *list1 = reinterpret_cast<int *>(ws + L.list1);
+  int *list2 = reinterpret_cast<int *>(ws + L.list2);
   ParamsK pk{params->eps_sat, params->eta};
-  const int init_n = (int)std::max<long long>(P, kCells);
-  cull_init<<<(init_n + 255) / 256, 256, 0, st>>>(keys, P, hist, ctr);
-  if (scene->n_tiles > 0) {
-    // spatial sort of the poses over the scene's bounding box (poses outside
-    // it clamp to the border cells)
-    const float span = std::max(std::max(scene->bbox[2] - scene->bbox[0],
-                                         scene->bbox[3] - scene->bbox[1]), 1e-3f);
-    const int pb = (int)((P + 255) / 256);
-    cull_cells<<<pb, 256, 0, st>>>(poses, P, scene->bbox[0], scene->bbox[1], 64.f / span, cell,
-                                   hist);
-    cull_scan<<<1, 1024, 0, st>>>(hist);
-    cull_scatter<<<pb, 256, 0, st>>>(cell, P, hist, perm);
-    // proposals: per-pose K best tiles per split, then each block's union
+  const int init_n = (int)std::max<long long>(P, T);
+  cull_init<<<(init_n + 255) / 256, 256, 0, st>>>(keys, flags, P, hist1, hist2, T, ctr);
+  if (T > 0) {
     const int K = opts->k;
-    if (L.splits > 64 || (scene->n_tiles + L.splits - 1) / L.splits > kMaxSplitTiles)
-      return fail(PSDF_ERR_CAPACITY, "scene has too many tiles for the cull");
-    float *cand_s = reinterpret_cast<float *>(ws + L.cand_s);
-    int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
+    const bool net = opts->mode == PSDF_PROPOSE_MLP;
+    const unsigned pb = (unsigned)((P + 127) / 128);
     {
       ProfileScope prof("propose", st);
-      const bool net = opts->mode == PSDF_PROPOSE_MLP;
       const long long warps = net ? (P + 15) / 16 : (P + 31) / 32;
-      dim3 sg((unsigned)((warps + kScoreWarps - 1) / kScoreWarps), (unsigned)L.splits);
-      const unsigned ub = (unsigned)((L.nb + 3) / 4);
-      const size_t usmem = 4 * sizeof(unsigned) * (size_t)L.words;
-      if (usmem > 48 * 1024) return fail(PSDF_ERR_CAPACITY, "scene has too many tiles for the cull");
+      dim3 sg(net ? (unsigned)((warps + kScoreWarps - 1) / kScoreWarps) : pb, (unsigned)L.splits);
 #define PSDF_PROPOSE(KK)                                                                      \
   if (net)                                                                                    \
-    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, perm, P, scene->d_tiles,            \
-                                                   scene->n_tiles, L.splits, F.radius,        \
-                                                   mlp->d_frag, mlp->b2, cand_s, cand_i);     \
+    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, P, scene->d_tiles, T, L.splits,     \
+                                                   F.radius, mlp->d_frag, mlp->b2, cand_s,    \
+                                                   cand_i);                                   \
   else                                                                                        \
-    score_bound<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, perm, P, scene->d_tiles,          \
-                                                     scene->n_tiles, L.splits, F.radius,      \
-                                                     cand_s, cand_i);                         \
-  propose_union<KK><<<ub, 128, usmem, st>>>(P, L.nb, L.splits, L.words, cand_s, cand_i, bits, \
-                                            items1, ctr);
+    score_bound<KK><<<sg, 128, 0, st>>>(poses, P, scene->d_tiles, T, L.splits, F.radius,      \
+                                        cand_s, cand_i);                                      \
+  merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -1025,27 +946,33 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
         default: PSDF_PROPOSE(4) break;
       }
 #undef PSDF_PROPOSE
+      tiles_scan<<<1, 1024, 0, st>>>(hist1, T, cur1, &ctr->n_prop);
+      scatter_prop<<<pb, 128, 0, st>>>(P, prop, cur1, list1);
     }
-    const int eval_grid = device_sms() * 8;
+    // after scatter_prop, cur1[t] = off1[t] + hist1[t]; the lists start at
+    // cur1[t] - hist1[t] -- recompute the offsets into cur1 for the evaluation
+    tiles_scan<<<1, 1024, 0, st>>>(hist1, T, cur1, &ctr->n_prop);
     {
       ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<CullEvalCall>(m, F, pk, poses, (const int *)perm, (long long)P, scene,
-                                         (const int2 *)items1, (const int *)&ctr->n_items1,
-                                         keys, eval_grid, st);
+      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist1,
+                                         (const int *)cur1, (const int *)list1, keys, st);
       if (rc) return rc;
     }
     {
       ProfileScope prof("fallback", st);
-      const long long fb_ctas = std::min<long long>(L.nb, (long long)device_sms() * 8);
-      cull_fallback<<<(unsigned)fb_ctas, kFallbackWarps * 32, 0, st>>>(
-          poses, perm, P, L.nb, scene->d_tiles, scene->n_tiles, F.radius, L.words, bits, keys,
-          items2, ctr);
+      const int fsplits = std::max(1, std::min(L.splits, (T + 63) / 64));
+      dim3 fg(pb, (unsigned)fsplits);
+      fb_pairs<false><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
+                                          prop, hist2, cur2, list2, flags, ctr);
+      tiles_scan<<<1, 1024, 0, st>>>(hist2, T, cur2, &ctr->n_fb);
+      fb_pairs<true><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
+                                         prop, hist2, cur2, list2, flags, ctr);
+      tiles_scan<<<1, 1024, 0, st>>>(hist2, T, cur2, &ctr->n_fb);
     }
     {
       ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<CullEvalCall>(m, F, pk, poses, (const int *)perm, (long long)P, scene,
-                                         (const int2 *)items2, (const int *)&ctr->n_items2,
-                                         keys, eval_grid, st);
+      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist2,
+                                         (const int *)cur2, (const int *)list2, keys, st);
       if (rc) return rc;
     }
   }
@@ -1065,8 +992,8 @@ extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cu
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(cull counters)");
   stats->pose_blocks = 0;
   stats->tiles = 0;
-  stats->proposed_items = c.n_items1;
-  stats->fallback_items = c.n_items2;
+  stats->proposed_items = c.n_prop;
+  stats->fallback_items = c.n_fb;
   stats->fallback_poses = c.fallback_poses;
   if (c.err) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out");
   return PSDF_OK;
