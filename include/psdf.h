@@ -97,10 +97,11 @@ const char *psdf_last_error(void);
 int psdf_version(void);
 
 /* ---- scene preparation (Alg. 1 EncodeEdges + upload, Sec. IV-A.2) -------
- * Validates the edge set, sorts obstacles along a Morton curve of their
- * centroids, packs them into tiles of at most `tile_edges` edges (no obstacle
- * straddles a tile; 0 selects 256), precomputes per-edge constants and
- * uploads everything to the current device (synchronously, on `stream`).
+ * Validates the edge set, packs the obstacles into tiles of at most
+ * `tile_edges` edges (0 selects 256; no obstacle straddles a tile) by
+ * sort-tile-recursive order of their centroids (vertical slices along x,
+ * each ordered along y), precomputes per-edge constants and uploads
+ * everything to the current device (synchronously, on `stream`).
  *
  * psdf_scene_create_csr: edges HOST float[E][4] rows (Ax, Ay, Bx, By) in the
  * world frame; offsets HOST int32[M+1], obstacle i owns rows

@@ -55,7 +55,8 @@ struct CullCounters {
 };
 
 struct CullLayout {
-  size_t keys, prop, flags, cand_s, cand_i, hist1, cur1, hist2, cur2, list1, list2, total;
+  size_t keys, prop, flags, cand_s, cand_i, hist1, cur1, uoff1, hist2, cur2, uoff2, list1, list2,
+      total;
   int splits;
 };
 
@@ -85,8 +86,10 @@ static CullLayout cull_layout(long long P, int n_tiles)
   L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
   L.hist1 = o; o = align256(o + 4 * Tz);
   L.cur1 = o; o = align256(o + 4 * Tz);
+  L.uoff1 = o; o = align256(o + 4 * (Tz + 1));
   L.hist2 = o; o = align256(o + 4 * Tz);
   L.cur2 = o; o = align256(o + 4 * Tz);
+  L.uoff2 = o; o = align256(o + 4 * (Tz + 1));
   L.list1 = o; o = align256(o + 4 * Pz * kMaxK);
   L.list2 = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
@@ -428,43 +431,75 @@ __global__ void merge_emit(long long P, int splits, const float *__restrict__ ca
   for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
 }
 
-// Exclusive prefix sum of per-tile counts (one CTA of 1024 threads, each a
-// run of consecutive tiles); cur[t] = off[t] (the scatter cursor), and the
-// total goes to *total.
-__global__ void __launch_bounds__(1024) tiles_scan(const int *__restrict__ hist, int T,
-                                                   int *__restrict__ off, int *total)
+// Lanes of a tile's work: its cnt poses are split over S obstacle ranges
+// each, so that cnt * S lanes fill about one 128-thread unit when few poses
+// need the tile.
+__device__ __forceinline__ int tile_split(int cnt, int n_obs)
 {
-  __shared__ int warp_sum[32];
+  return max(1, min(kListThreads / max(cnt, 1), n_obs));
+}
+
+__device__ __forceinline__ int tile_units(int cnt, int n_obs)
+{
+  return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
+}
+
+// Exclusive prefix sums over tiles (one CTA of 1024 threads, each a run of
+// consecutive tiles) of the pose counts -> off[t] (the list offsets), and of
+// the work units -> uoff[t] (uoff[T] = the total).  *total = sum of counts.
+__global__ void __launch_bounds__(1024)
+    tiles_scan(const int *__restrict__ hist, const TileHdr *__restrict__ tiles, int T,
+               int *__restrict__ off, int *__restrict__ uoff, int *total)
+{
+  __shared__ int warp_sum[2][32];
   const int tid = threadIdx.x;
   const int per = (T + 1023) / 1024;
   const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
-  int s = 0;
-  for (int i = b0; i < b1; ++i) s += hist[i];
-  int incl = s;
+  int s = 0, su = 0;
+  for (int i = b0; i < b1; ++i) {
+    s += hist[i];
+    su += tile_units(hist[i], tiles[i].n_obs);
+  }
+  int incl = s, inclu = su;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int n = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((tid & 31) >= o) incl += n;
+    const int nu = __shfl_up_sync(0xffffffffu, inclu, o);
+    if ((tid & 31) >= o) {
+      incl += n;
+      inclu += nu;
+    }
   }
-  if ((tid & 31) == 31) warp_sum[tid >> 5] = incl;
+  if ((tid & 31) == 31) {
+    warp_sum[0][tid >> 5] = incl;
+    warp_sum[1][tid >> 5] = inclu;
+  }
   __syncthreads();
   if (tid < 32) {
-    const int w = warp_sum[tid];
-    int wi = w;
+    for (int k = 0; k < 2; ++k) {
+      const int w = warp_sum[k][tid];
+      int wi = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_up_sync(0xffffffffu, wi, o);
-      if (tid >= o) wi += n;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, wi, o);
+        if (tid >= o) wi += n;
+      }
+      warp_sum[k][tid] = wi - w;
     }
-    warp_sum[tid] = wi - w;
   }
   __syncthreads();
-  int base = warp_sum[tid >> 5] + incl - s;
+  int base = warp_sum[0][tid >> 5] + incl - s;
+  int ubase = warp_sum[1][tid >> 5] + inclu - su;
   for (int i = b0; i < b1; ++i) {
     off[i] = base;
+    uoff[i] = ubase;
     base += hist[i];
+    ubase += tile_units(hist[i], tiles[i].n_obs);
   }
-  if (tid == 1023) *total = base;
+  if (tid == 1023) {
+    *total = base;
+    uoff[T] = ubase;
+  }
 }
 
 // Lists of poses per tile for the proposals.
@@ -496,50 +531,60 @@ __device__ __forceinline__ void cp_async_wait_all()
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// One CTA per tile.  The tile's blob is copied into shared memory (16-byte
-// cp.async per thread).  The tile's cnt poses are split over S obstacle
-// ranges each, S = clamp(128 / cnt, 1, n_obs), so that cnt * S lanes (about
-// one CTA's worth when few poses need the tile) share the work; lane l
-// evaluates pose list[l / S] against obstacle range l % S and merges its
-// minimum into the pose's key.
+// Persistent CTAs over work units.  Unit u belongs to tile t with
+// uoff[t] <= u < uoff[t + 1] (binary search) and covers lanes
+// [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane l evaluates
+// pose list[off[t] + l / S] against obstacle range l % S of the tile and
+// merges its minimum into the pose's key.  The tile's blob is staged in
+// shared memory (16-byte cp.async per thread) once per unit.
 template <int M>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float *__restrict__ poses,
-               const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob,
+               const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
                const int *__restrict__ hist, const int *__restrict__ off,
-               const int *__restrict__ list, unsigned long long *__restrict__ keys)
+               const int *__restrict__ uoff, const int *__restrict__ list,
+               unsigned long long *__restrict__ keys)
 {
   extern __shared__ __align__(16) unsigned char tsm[];
-  const int t = blockIdx.x;
-  const int cnt = hist[t];
-  if (cnt == 0) return;  // uniform over the CTA
-  const TileHdr h = tiles[t];
-  const unsigned char *src = blob + h.blob_off;
-  for (int o = 16 * threadIdx.x; o < h.blob_bytes; o += 16 * kListThreads)
-    cp_async16(tsm + o, src + o);
-  const int S = max(1, min(kListThreads / cnt, h.n_obs));
-  const long long L = (long long)cnt * S;
-  const int base = off[t];
-  cp_async_wait_all();
-  __syncthreads();
-  const int4 *ob = reinterpret_cast<const int4 *>(tsm);
-  const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
-  for (long long l = threadIdx.x; l < L; l += kListThreads) {
-    const int pi = (int)(l / S), part = (int)(l % S);
-    const long long p = list[base + pi];
-    const float px = poses[3 * p], py = poses[3 * p + 1];
-    float s, c;
-    sincosf(poses[3 * p + 2], &s, &c);
-    const int o0 = (int)((long long)h.n_obs * part / S);
-    const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
-    unsigned long long best = ~0ull;
-    for (int o = o0; o < o1; ++o) {
-      const int4 rec = ob[o];
-      const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
-      const unsigned long long key = pack_key(v, rec.z);
-      best = key < best ? key : best;
+  const int U = uoff[T];
+  for (int u = blockIdx.x; u < U; u += gridDim.x) {
+    int lo = 0, hi = T - 1;  // largest t with uoff[t] <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (uoff[mid] <= u) lo = mid;
+      else hi = mid - 1;
     }
-    if (best != ~0ull) atomicMin(&keys[p], best);
+    const int t = lo;
+    const TileHdr h = tiles[t];
+    const int cnt = hist[t];
+    const int S = tile_split(cnt, h.n_obs);
+    const long long L = (long long)cnt * S;
+    const long long l = (long long)(u - uoff[t]) * kListThreads + threadIdx.x;
+    const unsigned char *src = blob + h.blob_off;
+    __syncthreads();  // the previous unit's reads of the staged tile are done
+    for (int o = 16 * threadIdx.x; o < h.blob_bytes; o += 16 * kListThreads)
+      cp_async16(tsm + o, src + o);
+    cp_async_wait_all();
+    __syncthreads();
+    if (l < L) {
+      const int4 *ob = reinterpret_cast<const int4 *>(tsm);
+      const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
+      const int pi = (int)(l / S), part = (int)(l % S);
+      const long long p = list[off[t] + pi];
+      const float px = poses[3 * p], py = poses[3 * p + 1];
+      float s, c;
+      sincosf(poses[3 * p + 2], &s, &c);
+      const int o0 = (int)((long long)h.n_obs * part / S);
+      const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
+      unsigned long long best = ~0ull;
+      for (int o = o0; o < o1; ++o) {
+        const int4 rec = ob[o];
+        const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
+        const unsigned long long key = pack_key(v, rec.z);
+        best = key < best ? key : best;
+      }
+      if (best != ~0ull) atomicMin(&keys[p], best);
+    }
   }
 }
 
@@ -690,8 +735,8 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 template <int M>
 struct ListEvalCall {
   static int run(const FootprintK &F, const ParamsK &pk, const float *poses,
-                 const psdf_scene *sc, const int *hist, const int *off, const int *list,
-                 unsigned long long *keys, cudaStream_t st)
+                 const psdf_scene *sc, const int *hist, const int *off, const int *uoff,
+                 const int *list, unsigned long long *keys, cudaStream_t st)
   {
     const size_t smem = (size_t)(sc->max_blob_bytes + 15) / 16 * 16;
     if (smem > 48 * 1024) {
@@ -700,8 +745,9 @@ struct ListEvalCall {
                                            (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
-    eval_lists<M><<<sc->n_tiles, kListThreads, smem, st>>>(F, pk, poses, sc->d_tiles,
-                                                          sc->d_blob, hist, off, list, keys);
+    const int grid = device_sms() * 8;
+    eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, poses, sc->d_tiles, sc->n_tiles,
+                                                   sc->d_blob, hist, off, uoff, list, keys);
     return PSDF_OK;
   }
 };
@@ -915,8 +961,10 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
   int *hist1 = reinterpret_cast<int *>(ws + L.hist1);
   int *cur1 = reinterpret_cast<int *>(ws + L.cur1);
+  int *uoff1 = reinterpret_cast<int *>(ws + L.uoff1);
   int *hist2 = reinterpret_cast<int *>(ws + L.hist2);
   int *cur2 = reinterpret_cast<int *>(ws + L.cur2);
+  int *uoff2 = reinterpret_cast<int *>(ws + L.uoff2);
   int *list1 = reinterpret_cast<int *>(ws + L.list1);
   int *list2 = reinterpret_cast<int *>(ws + L.list2);
   ParamsK pk{params->eps_sat, params->eta};
@@ -946,16 +994,17 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
         default: PSDF_PROPOSE(4) break;
       }
 #undef PSDF_PROPOSE
-      tiles_scan<<<1, 1024, 0, st>>>(hist1, T, cur1, &ctr->n_prop);
+      tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, cur1, uoff1, &ctr->n_prop);
       scatter_prop<<<pb, 128, 0, st>>>(P, prop, cur1, list1);
     }
     // after scatter_prop, cur1[t] = off1[t] + hist1[t]; the lists start at
     // cur1[t] - hist1[t] -- recompute the offsets into cur1 for the evaluation
-    tiles_scan<<<1, 1024, 0, st>>>(hist1, T, cur1, &ctr->n_prop);
+    tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, cur1, uoff1, &ctr->n_prop);
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist1,
-                                         (const int *)cur1, (const int *)list1, keys, st);
+                                         (const int *)cur1, (const int *)uoff1,
+                                         (const int *)list1, keys, st);
       if (rc) return rc;
     }
     {
@@ -964,15 +1013,16 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
       dim3 fg(pb, (unsigned)fsplits);
       fb_pairs<false><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
                                           prop, hist2, cur2, list2, flags, ctr);
-      tiles_scan<<<1, 1024, 0, st>>>(hist2, T, cur2, &ctr->n_fb);
+      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, cur2, uoff2, &ctr->n_fb);
       fb_pairs<true><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
                                          prop, hist2, cur2, list2, flags, ctr);
-      tiles_scan<<<1, 1024, 0, st>>>(hist2, T, cur2, &ctr->n_fb);
+      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, cur2, uoff2, &ctr->n_fb);
     }
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist2,
-                                         (const int *)cur2, (const int *)list2, keys, st);
+                                         (const int *)cur2, (const int *)uoff2,
+                                         (const int *)list2, keys, st);
       if (rc) return rc;
     }
   }

