@@ -65,6 +65,10 @@ extern "C" {
 #define PSDF_PAIR_NONE 0xFFFFFFFFu
 #define PSDF_MAX_FOOTPRINT 16
 #define PSDF_MAX_OBSTACLE_EDGES 256
+/* OR into tile_edges of psdf_scene_create_*: pack tiles greedily along a
+ * Morton (Z-order) curve of the obstacle centroids instead of the default
+ * sort-tile-recursive order (tiles then follow the curve and may be long) */
+#define PSDF_TILE_MORTON 0x10000
 
 typedef struct psdf_scene psdf_scene; /* opaque: owns the device copy of E  */
 

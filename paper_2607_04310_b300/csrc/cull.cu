@@ -55,7 +55,7 @@ struct CullCounters {
 };
 
 struct CullLayout {
-  size_t keys, prop, flags, cand_s, cand_i, hist1, cur1, uoff1, hist2, cur2, uoff2, list1, list2,
+  size_t keys, pose4, flags, cand_s, cand_i, hist1, uoff1, hist2, uoff2, prop, list1, list2,
       total;
   int splits;
 };
@@ -72,6 +72,8 @@ static int score_splits(long long P, int n_tiles)
   return (int)std::max<long long>(1, std::min<long long>(sp, 64));
 }
 
+// Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]),
+// so that proposals and fallback pairs are appended in one pass.
 static CullLayout cull_layout(long long P, int n_tiles)
 {
   CullLayout L;
@@ -80,17 +82,16 @@ static CullLayout cull_layout(long long P, int n_tiles)
   L.splits = score_splits(P, n_tiles);
   size_t o = 256;
   L.keys = o; o = align256(o + 8 * Pz);
-  L.prop = o; o = align256(o + 4 * Pz * kMaxK);
+  L.pose4 = o; o = align256(o + 16 * Pz);
   L.flags = o; o = align256(o + 4 * Pz);
+  L.prop = o; o = align256(o + 4 * Pz * kMaxK);
   L.cand_s = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
   L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
   L.hist1 = o; o = align256(o + 4 * Tz);
-  L.cur1 = o; o = align256(o + 4 * Tz);
   L.uoff1 = o; o = align256(o + 4 * (Tz + 1));
   L.hist2 = o; o = align256(o + 4 * Tz);
-  L.cur2 = o; o = align256(o + 4 * Tz);
   L.uoff2 = o; o = align256(o + 4 * (Tz + 1));
-  L.list1 = o; o = align256(o + 4 * Pz * kMaxK);
+  L.list1 = o; o = align256(o + 4 * Pz * Tz);
   L.list2 = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
   return L;
@@ -285,13 +286,19 @@ __device__ __forceinline__ void stage_tiles(const TileHdr *__restrict__ tiles, i
   }
 }
 
-__global__ void cull_init(unsigned long long *keys, int *flags, long long P, int *hist1,
-                          int *hist2, int T, CullCounters *ctr)
+// keys = +inf, flags and per-tile counters cleared, and every pose's
+// (x, y, cos theta, sin theta) computed once.
+__global__ void cull_init(const float *__restrict__ poses, unsigned long long *keys,
+                          float4 *pose4, int *flags, long long P, int *hist1, int *hist2, int T,
+                          CullCounters *ctr)
 {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P) {
     keys[i] = ~0ull;
     flags[i] = 0;
+    float s, c;
+    sincosf(poses[3 * i + 2], &s, &c);
+    pose4[i] = make_float4(poses[3 * i], poses[3 * i + 1], c, s);
   }
   if (i < T) {
     hist1[i] = 0;
@@ -308,7 +315,7 @@ __global__ void cull_init(unsigned long long *keys, int *flags, long long P, int
 // Bound proposal scores: thread = pose, blockIdx.y = tile split.
 template <int K>
 __global__ void __launch_bounds__(kScoreWarps * 32)
-    score_bound(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+    score_bound(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
                 int n_tiles, int splits, float rfoot, float *__restrict__ cand_s,
                 int *__restrict__ cand_i)
 {
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
   __syncthreads();
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const float px = poses[3 * p], py = poses[3 * p + 1];
+  const float px = pose4[p].x, py = pose4[p].y;
   float sc[K];
   int id[K];
 #pragma unroll
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
 // tensor-core tile), blockIdx.y = tile split; two tiles in flight per step.
 template <int K>
 __global__ void __launch_bounds__(kScoreWarps * 32)
-    score_mlp(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+    score_mlp(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
               int n_tiles, int splits, float rfoot, const uint32_t *__restrict__ frag, float b2,
               float *__restrict__ cand_s, int *__restrict__ cand_i)
 {
@@ -358,14 +365,12 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
   const long long pa = group * 16 + g, pb = group * 16 + g + 8;
   float pxa = 0.f, pya = 0.f, ca = 1.f, sa = 0.f, pxb = 0.f, pyb = 0.f, cb = 1.f, sb = 0.f;
   if (pa < P) {
-    pxa = poses[3 * pa];
-    pya = poses[3 * pa + 1];
-    sincosf(poses[3 * pa + 2], &sa, &ca);
+    const float4 q4 = pose4[pa];
+    pxa = q4.x; pya = q4.y; ca = q4.z; sa = q4.w;
   }
   if (pb < P) {
-    pxb = poses[3 * pb];
-    pyb = poses[3 * pb + 1];
-    sincosf(poses[3 * pb + 2], &sb, &cb);
+    const float4 q4 = pose4[pb];
+    pxb = q4.x; pyb = q4.y; cb = q4.z; sb = q4.w;
   }
   MlpFrags w;
   load_frags(frag, lane, w);
@@ -400,11 +405,12 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
   }
 }
 
-// Per pose: its K best tiles over the splits -> prop[p * K + i], counted per tile.
+// Per pose: its K best tiles over the splits -> prop[p * kMaxK + i], and the
+// pose appended to each of those tiles' lists.
 template <int K>
 __global__ void merge_emit(long long P, int splits, const float *__restrict__ cand_s,
                            const int *__restrict__ cand_i, int *__restrict__ prop,
-                           int *__restrict__ hist)
+                           int *__restrict__ hist, int *__restrict__ list, CullCounters *ctr)
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
@@ -422,21 +428,27 @@ __global__ void merge_emit(long long P, int splits, const float *__restrict__ ca
       const int t = cand_i[c];
       if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
     }
+  int n = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     prop[p * kMaxK + i] = id[i];
-    if (id[i] >= 0) atomicAdd(&hist[id[i]], 1);
+    if (id[i] >= 0) {
+      list[(long long)id[i] * P + atomicAdd(&hist[id[i]], 1)] = (int)p;
+      ++n;
+    }
   }
 #pragma unroll
   for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
+  atomicAdd(&ctr->n_prop, n);
 }
 
 // Lanes of a tile's work: its cnt poses are split over S obstacle ranges
-// each, so that cnt * S lanes fill about one 128-thread unit when few poses
-// need the tile.
+// each, so that cnt * S lanes fill about two 128-thread units when few poses
+// need the tile (short per-lane chains, many warps in flight).
+constexpr int kTargetLanes = 2 * kListThreads;
 __device__ __forceinline__ int tile_split(int cnt, int n_obs)
 {
-  return max(1, min(kListThreads / max(cnt, 1), n_obs));
+  return max(1, min(kTargetLanes / max(cnt, 1), n_obs));
 }
 
 __device__ __forceinline__ int tile_units(int cnt, int n_obs)
@@ -444,75 +456,43 @@ __device__ __forceinline__ int tile_units(int cnt, int n_obs)
   return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
 }
 
-// Exclusive prefix sums over tiles (one CTA of 1024 threads, each a run of
-// consecutive tiles) of the pose counts -> off[t] (the list offsets), and of
-// the work units -> uoff[t] (uoff[T] = the total).  *total = sum of counts.
+// Exclusive prefix sum over tiles of the work units -> uoff[t], uoff[T] =
+// total (one CTA of 1024 threads, each a run of consecutive tiles).
 __global__ void __launch_bounds__(1024)
     tiles_scan(const int *__restrict__ hist, const TileHdr *__restrict__ tiles, int T,
-               int *__restrict__ off, int *__restrict__ uoff, int *total)
+               int *__restrict__ uoff)
 {
-  __shared__ int warp_sum[2][32];
+  __shared__ int warp_sum[32];
   const int tid = threadIdx.x;
   const int per = (T + 1023) / 1024;
   const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
-  int s = 0, su = 0;
-  for (int i = b0; i < b1; ++i) {
-    s += hist[i];
-    su += tile_units(hist[i], tiles[i].n_obs);
-  }
-  int incl = s, inclu = su;
+  int su = 0;
+  for (int i = b0; i < b1; ++i) su += tile_units(hist[i], tiles[i].n_obs);
+  int incl = su;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int n = __shfl_up_sync(0xffffffffu, incl, o);
-    const int nu = __shfl_up_sync(0xffffffffu, inclu, o);
-    if ((tid & 31) >= o) {
-      incl += n;
-      inclu += nu;
-    }
+    if ((tid & 31) >= o) incl += n;
   }
-  if ((tid & 31) == 31) {
-    warp_sum[0][tid >> 5] = incl;
-    warp_sum[1][tid >> 5] = inclu;
-  }
+  if ((tid & 31) == 31) warp_sum[tid >> 5] = incl;
   __syncthreads();
   if (tid < 32) {
-    for (int k = 0; k < 2; ++k) {
-      const int w = warp_sum[k][tid];
-      int wi = w;
+    const int w = warp_sum[tid];
+    int wi = w;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, wi, o);
-        if (tid >= o) wi += n;
-      }
-      warp_sum[k][tid] = wi - w;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, wi, o);
+      if (tid >= o) wi += n;
     }
+    warp_sum[tid] = wi - w;
   }
   __syncthreads();
-  int base = warp_sum[0][tid >> 5] + incl - s;
-  int ubase = warp_sum[1][tid >> 5] + inclu - su;
+  int ubase = warp_sum[tid >> 5] + incl - su;
   for (int i = b0; i < b1; ++i) {
-    off[i] = base;
     uoff[i] = ubase;
-    base += hist[i];
     ubase += tile_units(hist[i], tiles[i].n_obs);
   }
-  if (tid == 1023) {
-    *total = base;
-    uoff[T] = ubase;
-  }
-}
-
-// Lists of poses per tile for the proposals.
-__global__ void scatter_prop(long long P, const int *__restrict__ prop, int *__restrict__ cur,
-                             int *__restrict__ list)
-{
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-#pragma unroll
-  for (int i = 0; i < kMaxK; ++i) {
-    const int t = prop[p * kMaxK + i];
-    if (t >= 0) list[atomicAdd(&cur[t], 1)] = (int)p;
-  }
+  if (tid == 1023) uoff[T] = ubase;
 }
 
 // ---------------------------------------------------------------------------
@@ -534,16 +514,15 @@ __device__ __forceinline__ void cp_async_wait_all()
 // Persistent CTAs over work units.  Unit u belongs to tile t with
 // uoff[t] <= u < uoff[t + 1] (binary search) and covers lanes
 // [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane l evaluates
-// pose list[off[t] + l / S] against obstacle range l % S of the tile and
+// pose list[t * P + l / S] against obstacle range l % S of the tile and
 // merges its minimum into the pose's key.  The tile's blob is staged in
 // shared memory (16-byte cp.async per thread) once per unit.
 template <int M>
 __global__ void __launch_bounds__(kListThreads)
-    eval_lists(FootprintK F, ParamsK prm, const float *__restrict__ poses,
+    eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
                const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
-               const int *__restrict__ hist, const int *__restrict__ off,
-               const int *__restrict__ uoff, const int *__restrict__ list,
-               unsigned long long *__restrict__ keys)
+               const int *__restrict__ hist, const int *__restrict__ uoff,
+               const int *__restrict__ list, unsigned long long *__restrict__ keys)
 {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int U = uoff[T];
@@ -570,10 +549,9 @@ __global__ void __launch_bounds__(kListThreads)
       const int4 *ob = reinterpret_cast<const int4 *>(tsm);
       const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
       const int pi = (int)(l / S), part = (int)(l % S);
-      const long long p = list[off[t] + pi];
-      const float px = poses[3 * p], py = poses[3 * p + 1];
-      float s, c;
-      sincosf(poses[3 * p + 2], &s, &c);
+      const long long p = list[(long long)t * P + pi];
+      const float4 q4 = pose4[p];
+      const float px = q4.x, py = q4.y, c = q4.z, s = q4.w;
       const int o0 = (int)((long long)h.n_obs * part / S);
       const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
       unsigned long long best = ~0ull;
@@ -600,14 +578,13 @@ __device__ __forceinline__ bool fb_need(const float *ab, float px, float py, flo
   return !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
 }
 
-// SCATTER = false: count the pairs per tile and flag the poses; SCATTER =
-// true: write them into the per-tile lists (same decisions).
-template <bool SCATTER>
+// Every (pose, tile) pair of a pose's unproposed tiles whose bound does not
+// exceed the pose's current minimum is appended to the tile's list.
 __global__ void __launch_bounds__(128)
-    fb_pairs(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+    fb_pairs(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
              int n_tiles, int splits, float rfoot, const unsigned long long *__restrict__ keys,
-             const int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ cur,
-             int *__restrict__ list, int *__restrict__ flags, CullCounters *ctr)
+             const int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ list,
+             int *__restrict__ flags, CullCounters *ctr)
 {
   __shared__ float4 ab_s[kMaxSplitTiles];
   const int split = blockIdx.y;
@@ -617,23 +594,25 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const float px = poses[3 * p], py = poses[3 * p + 1];
+  const float4 q4 = pose4[p];
   const unsigned long long key = keys[p];
   const float best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
   int pr[kMaxK];
 #pragma unroll
   for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
-  bool any = false;
+  int n = 0;
   for (int i = 0; i < t1 - t0; ++i) {
     const float4 a4 = ab_s[i];
     const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-    if (fb_need(ab, px, py, rfoot, best, t0 + i, pr)) {
-      any = true;
-      if (SCATTER) list[atomicAdd(&cur[t0 + i], 1)] = (int)p;
-      else atomicAdd(&hist[t0 + i], 1);
+    if (fb_need(ab, q4.x, q4.y, rfoot, best, t0 + i, pr)) {
+      list[(long long)(t0 + i) * P + atomicAdd(&hist[t0 + i], 1)] = (int)p;
+      ++n;
     }
   }
-  if (!SCATTER && any && atomicExch(&flags[p], 1) == 0) atomicAdd(&ctr->fallback_poses, 1);
+  if (n) {
+    atomicAdd(&ctr->n_fb, n);
+    if (atomicExch(&flags[p], 1) == 0) atomicAdd(&ctr->fallback_poses, 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -734,9 +713,9 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 // ---------------------------------------------------------------------------
 template <int M>
 struct ListEvalCall {
-  static int run(const FootprintK &F, const ParamsK &pk, const float *poses,
-                 const psdf_scene *sc, const int *hist, const int *off, const int *uoff,
-                 const int *list, unsigned long long *keys, cudaStream_t st)
+  static int run(const FootprintK &F, const ParamsK &pk, const float4 *pose4, long long P,
+                 const psdf_scene *sc, const int *hist, const int *uoff, const int *list,
+                 unsigned long long *keys, cudaStream_t st)
   {
     const size_t smem = (size_t)(sc->max_blob_bytes + 15) / 16 * 16;
     if (smem > 48 * 1024) {
@@ -746,8 +725,8 @@ struct ListEvalCall {
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
     const int grid = device_sms() * 8;
-    eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, poses, sc->d_tiles, sc->n_tiles,
-                                                   sc->d_blob, hist, off, uoff, list, keys);
+    eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, pose4, P, sc->d_tiles, sc->n_tiles,
+                                                   sc->d_blob, hist, uoff, list, keys);
     return PSDF_OK;
   }
 };
@@ -955,38 +934,38 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
   CullCounters *ctr = reinterpret_cast<CullCounters *>(ws);
   unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
-  int *prop = reinterpret_cast<int *>(ws + L.prop);
+  float4 *pose4 = reinterpret_cast<float4 *>(ws + L.pose4);
   int *flags = reinterpret_cast<int *>(ws + L.flags);
+  int *prop = reinterpret_cast<int *>(ws + L.prop);
   float *cand_s = reinterpret_cast<float *>(ws + L.cand_s);
   int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
   int *hist1 = reinterpret_cast<int *>(ws + L.hist1);
-  int *cur1 = reinterpret_cast<int *>(ws + L.cur1);
   int *uoff1 = reinterpret_cast<int *>(ws + L.uoff1);
   int *hist2 = reinterpret_cast<int *>(ws + L.hist2);
-  int *cur2 = reinterpret_cast<int *>(ws + L.cur2);
   int *uoff2 = reinterpret_cast<int *>(ws + L.uoff2);
   int *list1 = reinterpret_cast<int *>(ws + L.list1);
   int *list2 = reinterpret_cast<int *>(ws + L.list2);
   ParamsK pk{params->eps_sat, params->eta};
   const int init_n = (int)std::max<long long>(P, T);
-  cull_init<<<(init_n + 255) / 256, 256, 0, st>>>(keys, flags, P, hist1, hist2, T, ctr);
+  cull_init<<<(init_n + 255) / 256, 256, 0, st>>>(poses, keys, pose4, flags, P, hist1, hist2, T,
+                                                  ctr);
   if (T > 0) {
     const int K = opts->k;
     const bool net = opts->mode == PSDF_PROPOSE_MLP;
     const unsigned pb = (unsigned)((P + 127) / 128);
     {
       ProfileScope prof("propose", st);
-      const long long warps = net ? (P + 15) / 16 : (P + 31) / 32;
+      const long long warps = (P + 15) / 16;
       dim3 sg(net ? (unsigned)((warps + kScoreWarps - 1) / kScoreWarps) : pb, (unsigned)L.splits);
 #define PSDF_PROPOSE(KK)                                                                      \
   if (net)                                                                                    \
-    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(poses, P, scene->d_tiles, T, L.splits,     \
+    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits,     \
                                                    F.radius, mlp->d_frag, mlp->b2, cand_s,    \
                                                    cand_i);                                   \
   else                                                                                        \
-    score_bound<KK><<<sg, 128, 0, st>>>(poses, P, scene->d_tiles, T, L.splits, F.radius,      \
+    score_bound<KK><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,      \
                                         cand_s, cand_i);                                      \
-  merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1);
+  merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1, list1, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -994,16 +973,12 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
         default: PSDF_PROPOSE(4) break;
       }
 #undef PSDF_PROPOSE
-      tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, cur1, uoff1, &ctr->n_prop);
-      scatter_prop<<<pb, 128, 0, st>>>(P, prop, cur1, list1);
+      tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, uoff1);
     }
-    // after scatter_prop, cur1[t] = off1[t] + hist1[t]; the lists start at
-    // cur1[t] - hist1[t] -- recompute the offsets into cur1 for the evaluation
-    tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, cur1, uoff1, &ctr->n_prop);
     {
       ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist1,
-                                         (const int *)cur1, (const int *)uoff1,
+      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
+                                         (const int *)hist1, (const int *)uoff1,
                                          (const int *)list1, keys, st);
       if (rc) return rc;
     }
@@ -1011,17 +986,14 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
       ProfileScope prof("fallback", st);
       const int fsplits = std::max(1, std::min(L.splits, (T + 63) / 64));
       dim3 fg(pb, (unsigned)fsplits);
-      fb_pairs<false><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
-                                          prop, hist2, cur2, list2, flags, ctr);
-      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, cur2, uoff2, &ctr->n_fb);
-      fb_pairs<true><<<fg, 128, 0, st>>>(poses, P, scene->d_tiles, T, fsplits, F.radius, keys,
-                                         prop, hist2, cur2, list2, flags, ctr);
-      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, cur2, uoff2, &ctr->n_fb);
+      fb_pairs<<<fg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, fsplits, F.radius, keys, prop,
+                                   hist2, list2, flags, ctr);
+      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, uoff2);
     }
     {
       ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, poses, scene, (const int *)hist2,
-                                         (const int *)cur2, (const int *)uoff2,
+      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
+                                         (const int *)hist2, (const int *)uoff2,
                                          (const int *)list2, keys, st);
       if (rc) return rc;
     }

@@ -506,7 +506,7 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   }
   {
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<init_blocks, 256, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
+    epilogue_kernel<M><<<(int)((P + 63) / 64), 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
                                                     sc->d_vtx, sc->d_far, sc->d_row2obs, keys,
                                                     err, phi, dphi, active);
   }
@@ -520,9 +520,9 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
                            long long P, const unsigned *active, const float *grad_phi,
                            float *grad_pose, float *grad_edges, cudaStream_t st)
 {
-  const int blocks = (int)((P + 255) / 256);
+  const int blocks = (int)((P + 63) / 64);
   ProfileScope prof("backward", st);
-  backward_kernel<M><<<blocks, 256, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_obs, sc->d_vtx,
+  backward_kernel<M><<<blocks, 64, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_obs, sc->d_vtx,
                                              sc->d_far, sc->d_row2obs, sc->rows_total, active,
                                              grad_phi, grad_pose, grad_edges);
   cudaError_t e = cudaGetLastError();
@@ -569,9 +569,9 @@ struct EpilogueCall {
                  const ParamsK &pk, const unsigned long long *keys, const int *err, float *phi,
                  float *dphi, unsigned *active, cudaStream_t st)
   {
-    const int blocks = (int)((P + 255) / 256);
+    const int blocks = (int)((P + 63) / 64);
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<blocks, 256, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
+    epilogue_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
                                                sc->d_vtx, sc->d_far, sc->d_row2obs, keys, err,
                                                phi, dphi, active);
     cudaError_t e = cudaGetLastError();

@@ -13,6 +13,18 @@ namespace psdf {
 
 namespace {
 
+uint32_t spread_bits(uint32_t x)
+{
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+uint32_t morton2(uint32_t x, uint32_t y) { return spread_bits(x) | (spread_bits(y) << 1); }
+
 struct ObsIn {
   int64_t first_row;  // caller's row of the first edge
   int n;              // edges
@@ -94,6 +106,8 @@ void free_scene(psdf_scene *s)
 int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
                 int tile_edges, const psdf_params *prm, cudaStream_t st, psdf_scene **out)
 {
+  const bool morton = (tile_edges & PSDF_TILE_MORTON) != 0;
+  tile_edges &= ~PSDF_TILE_MORTON;
   if (tile_edges == 0) tile_edges = kDefaultTileEdges;
   if (tile_edges < 1 || tile_edges > kMaxTileEdges)
     return fail(PSDF_ERR_ARG, "tile_edges must be in [1, " + std::to_string(kMaxTileEdges) + "]");
@@ -133,39 +147,61 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
     cx[i] = sx / (2.0 * obs[i].n);
     cy[i] = sy / (2.0 * obs[i].n);
   }
-  // Sort-tile-recursive packing: vertical slices of about equal edge count
-  // along x, each slice ordered along y and cut greedily into tiles of at
-  // most tile_edges edges.  Tiles come out close to square, which keeps their
-  // AABBs (and the cull's lower bounds) tight.
   std::vector<int> order(M);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cx[a] < cx[b]; });
-  const long long t_target = std::max<long long>(1, (n_edges + tile_edges - 1) / tile_edges);
-  const int slices = std::max(1, (int)std::lround(std::sqrt((double)t_target)));
-  const double per_slice = (double)n_edges / slices;
   std::vector<int> tile_first;  // first sorted obstacle of each tile
-  {
-    int s0 = 0;
-    long long acc_edges = 0;
-    for (int sl = 0; sl < slices && s0 < M; ++sl) {
-      int s1 = s0;
-      const double limit = per_slice * (sl + 1);
-      while (s1 < M && (acc_edges + obs[order[s1]].n <= limit || s1 == s0 || sl == slices - 1)) {
-        acc_edges += obs[order[s1]].n;
-        ++s1;
+  if (morton) {
+    // greedy packing along a Morton (Z-order) curve of the centroids
+    std::vector<uint32_t> code(M);
+    double span = std::max((double)bb[2] - bb[0], (double)bb[3] - bb[1]);
+    if (!(span > 0)) span = 1.0;
+    for (int i = 0; i < M; ++i) {
+      uint32_t qx = (uint32_t)std::min(65535.0, std::max(0.0, (cx[i] - bb[0]) / span * 65535.0));
+      uint32_t qy = (uint32_t)std::min(65535.0, std::max(0.0, (cy[i] - bb[1]) / span * 65535.0));
+      code[i] = morton2(qx, qy);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return code[a] < code[b]; });
+    int acc = 0;
+    for (int s = 0; s < M; ++s) {
+      const int n = obs[order[s]].n;
+      if (s == 0 || acc + n > tile_edges) {
+        tile_first.push_back(s);
+        acc = 0;
       }
-      std::stable_sort(order.begin() + s0, order.begin() + s1,
-                       [&](int a, int b) { return cy[a] < cy[b]; });
-      int acc = 0;
-      for (int s = s0; s < s1; ++s) {
-        const int n = obs[order[s]].n;
-        if (s == s0 || acc + n > tile_edges) {
-          tile_first.push_back(s);
-          acc = 0;
+      acc += n;
+    }
+  } else {
+    // Sort-tile-recursive packing: vertical slices of about equal edge count
+    // along x, each slice ordered along y and cut greedily into tiles of at
+    // most tile_edges edges.  Tiles come out close to square, which keeps their
+    // AABBs (and the cull's lower bounds) tight.
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cx[a] < cx[b]; });
+    const long long t_target = std::max<long long>(1, (n_edges + tile_edges - 1) / tile_edges);
+    const int slices = std::max(1, (int)std::lround(std::sqrt((double)t_target)));
+    const double per_slice = (double)n_edges / slices;
+    {
+      int s0 = 0;
+      long long acc_edges = 0;
+      for (int sl = 0; sl < slices && s0 < M; ++sl) {
+        int s1 = s0;
+        const double limit = per_slice * (sl + 1);
+        while (s1 < M && (acc_edges + obs[order[s1]].n <= limit || s1 == s0 || sl == slices - 1)) {
+          acc_edges += obs[order[s1]].n;
+          ++s1;
         }
-        acc += n;
+        std::stable_sort(order.begin() + s0, order.begin() + s1,
+                         [&](int a, int b) { return cy[a] < cy[b]; });
+        int acc = 0;
+        for (int s = s0; s < s1; ++s) {
+          const int n = obs[order[s]].n;
+          if (s == s0 || acc + n > tile_edges) {
+            tile_first.push_back(s);
+            acc = 0;
+          }
+          acc += n;
+        }
+        s0 = s1;
       }
-      s0 = s1;
     }
   }
   const int T = (int)tile_first.size();

@@ -34,7 +34,9 @@ TARGET_LO, TARGET_HI = -0.5, 5.0
 CKPT_FORMAT = "psdf-tile-mlp-checkpoint-v1"
 WEIGHTS_FORMAT = "psdf-tile-mlp-weights-v1"
 HERE = os.path.dirname(os.path.abspath(__file__))
-DEFAULT_WEIGHTS = os.path.join(HERE, "data", "tile_mlp.json")
+DEFAULT_WEIGHTS = os.path.join(HERE, "data", "tile_mlp.json")            # STR tiles
+MORTON_WEIGHTS = os.path.join(HERE, "data", "tile_mlp_morton.json")      # Morton tiles
+TILE_MORTON = 0x10000  # PSDF_TILE_MORTON
 
 
 def init_weights(seed: int) -> Tuple[np.ndarray, np.ndarray, float]:
@@ -163,14 +165,15 @@ def load_weights(path: str = DEFAULT_WEIGHTS):
 # --------------------------------------------------------------------------
 # data
 # --------------------------------------------------------------------------
-def build_dataset(n_scenes: int, first: int = 0, device="cuda", log=None):
-    """(X [R, 16], y [R]) on the device for training scenes first..first+n-1."""
+def build_dataset(n_scenes: int, first: int = 0, device="cuda", log=None, tile_flags: int = 0):
+    """(X [R, 16], y [R]) on the device for training scenes first..first+n-1
+    (tile_flags: 0 = sort-tile-recursive tiles, TILE_MORTON = Morton tiles)."""
     import torch
     Xs, ys = [], []
     t0 = time.time()
     for i in range(n_scenes):
         w = sg.training_scene(first + i)
-        scene = psdf.Scene.from_csr(w.edges, w.offsets)
+        scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=tile_flags)
         T = scene.info().n_tiles
         poses = torch.as_tensor(w.poses, device=device)
         feats = torch.empty((w.P, T, 16), dtype=torch.float32, device=device)
@@ -237,13 +240,14 @@ def resume(path: str, X, y, log=None) -> Trainer:
 # --------------------------------------------------------------------------
 # evaluation: how often the proposal's first tile holds the nearest obstacle
 # --------------------------------------------------------------------------
-def evaluate(W1, w2, b2, n_scenes: int = 100, first: int = 20000, device="cuda"):
+def evaluate(W1, w2, b2, n_scenes: int = 100, first: int = 20000, device="cuda",
+             tile_flags: int = 0):
     import torch
     mlp = psdf.Mlp(W1, w2, b2)
     hit_mlp = hit_lb = total = 0
     for i in range(n_scenes):
         w = sg.training_scene(first + i)
-        scene = psdf.Scene.from_csr(w.edges, w.offsets)
+        scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=tile_flags)
         T = scene.info().n_tiles
         poses = torch.as_tensor(w.poses, device=device)
         vals = torch.empty((w.P, T), device=device)
@@ -271,21 +275,24 @@ def main():
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--eval-scenes", type=int, default=200)
+    ap.add_argument("--morton", action="store_true", help="train for Morton-packed tiles")
     a = ap.parse_args()
+    flags = TILE_MORTON if a.morton else 0
     torch.cuda.init()
     log = lambda s: print(s, flush=True)
     t0 = time.time()
-    X, y = build_dataset(a.scenes, log=log)
+    X, y = build_dataset(a.scenes, log=log, tile_flags=flags)
     log("dataset: %d rows in %.1f s" % (X.shape[0], time.time() - t0))
     t1 = time.time()
     tr = train(X, y, a.epochs, a.batch, a.lr, a.seed, checkpoint=a.checkpoint, log=log)
     torch.cuda.synchronize()
     log("training: %.1f s" % (time.time() - t1))
     W1, w2, b2 = split_params(tr.get_state()["params"])
-    ev = evaluate(W1, w2, b2, a.eval_scenes)
+    ev = evaluate(W1, w2, b2, a.eval_scenes, tile_flags=flags)
     log("held-out: %s" % json.dumps(ev))
     save_weights(a.out, W1, w2, b2, {"scenes": a.scenes, "epochs": a.epochs, "batch": a.batch,
                                      "lr": a.lr, "seed": a.seed, "heldout": ev,
+                                     "tiles": "morton" if a.morton else "sort-tile-recursive",
                                      "target_clamp": [TARGET_LO, TARGET_HI]})
     log("wrote %s" % a.out)
 
