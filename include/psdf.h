@@ -187,9 +187,9 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
 /* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
  * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
  * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
- * tile-proposal network's predicted signed distance (PSDF_PROPOSE_MLP) or by
- * the conservative bound below (PSDF_PROPOSE_BOUND) -- and those pairs are
- * evaluated exactly.  Then, for every tile the pose did not propose, a
+ * conservative bound below (PSDF_PROPOSE_BOUND), or (PSDF_PROPOSE_MLP) by the
+ * tile-proposal network's predicted signed distance among the 8 tiles with
+ * the smallest bounds -- and those pairs are evaluated exactly.  Then, for every tile the pose did not propose, a
  * conservative lower bound
  *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
  * on the signed distance of every obstacle in the tile is compared with the

@@ -2,21 +2,21 @@
 //
 // Work is organised as (pose, tile) pairs, bucketed by tile:
 //   1. cull_init       keys = +inf, per-tile counters and flags cleared
-//   2. score_*         every pose ranks all tiles (tile-proposal network on
-//                      tensor cores, or the conservative bound); K best per
-//                      tile split
-//   3. merge_emit      per pose: its K best tiles over all splits; count them
-//                      per tile
-//   4. tiles_scan      per-tile offsets (exclusive prefix sum)
-//   5. scatter_prop    per-tile lists of the poses that proposed the tile
-//   6. eval_lists      one CTA per tile: the tile's blob staged in shared
+//   2. score_bound     every pose ranks all tiles by the conservative bound;
+//                      best candidates per tile split
+//   3. merge_emit      per pose: its K best tiles by the bound; or
+//      rerank_mlp      per pose: its 8 best tiles by the bound re-ranked by the
+//                      tile-proposal network on tensor cores, K best kept;
+//                      the pose is appended to each proposed tile's list
+//   4. tiles_scan      per-tile work units (exclusive prefix sum)
+//   5. eval_lists      persistent CTAs over units: the tile's blob staged in shared
 //                      memory, lanes = (pose, obstacle range) pairs so that
 //                      warps stay full, exact evaluation, one atomicMin per
 //                      lane into the pose's 64-bit key
-//   7. fb_count / tiles_scan / fb_scatter / eval_lists
+//   6. fb_pairs / tiles_scan / eval_lists
 //                      fallback: every tile a pose did not propose whose
 //                      lower bound does not exceed the pose's current minimum
-//   8. epilogue        as for the full scan
+//   7. epilogue        as for the full scan
 // A skipped (pose, tile) pair holds only values strictly above the pose's
 // minimum, and the minimum over 64-bit keys does not depend on evaluation
 // order, so the result equals the full scan's bit for bit.
@@ -39,6 +39,7 @@ struct psdf_mlp {
 namespace psdf {
 
 constexpr int kMaxK = PSDF_CULL_MAX_K;
+constexpr int kPre = 8;  // bound-ranked candidates the network re-ranks per pose
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
 constexpr int kScoreWarps = 4;
@@ -85,8 +86,8 @@ static CullLayout cull_layout(long long P, int n_tiles)
   L.pose4 = o; o = align256(o + 16 * Pz);
   L.flags = o; o = align256(o + 4 * Pz);
   L.prop = o; o = align256(o + 4 * Pz * kMaxK);
-  L.cand_s = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
-  L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kMaxK);
+  L.cand_s = o; o = align256(o + 4 * Pz * L.splits * kPre);
+  L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kPre);
   L.hist1 = o; o = align256(o + 4 * Tz);
   L.uoff1 = o; o = align256(o + 4 * (Tz + 1));
   L.hist2 = o; o = align256(o + 4 * Tz);
@@ -207,6 +208,40 @@ __device__ __forceinline__ void load_frags(const uint32_t *frag, int lane, MlpFr
     w.b2[j][0] = frag[kFrag1Words + (j * 32 + lane) * 2];
     w.b2[j][1] = frag[kFrag1Words + (j * 32 + lane) * 2 + 1];
   }
+}
+
+// Scores of 16 rows whose rows g and g + 8 each have their own pose and tile
+// (the network re-ranking candidate tiles); same arithmetic as mlp_rows.
+__device__ __forceinline__ void mlp_rows_pair(const MlpFrags &w, int q, const float *aba,
+                                              float efa, float pxa, float pya, float ca,
+                                              float sa, const float *abb, float efb, float pxb,
+                                              float pyb, float cb, float sb, float rfoot,
+                                              float &sc_a, float &sc_b)
+{
+  float fa0, fa1, fb0, fb1, ga0, ga1, gb0, gb1;
+  feat_corner(aba, q, pxa, pya, ca, sa, fa0, fa1);
+  feat_corner(abb, q, pxb, pyb, cb, sb, fb0, fb1);
+  feat_rest(aba, q, pxa, pya, rfoot, efa, ga0, ga1);
+  feat_rest(abb, q, pxb, pyb, rfoot, efb, gb0, gb1);
+  const uint32_t a0 = pack_f16x2(fa0, fa1), a1 = pack_f16x2(fb0, fb1);
+  const uint32_t a2 = pack_f16x2(ga0, ga1), a3 = pack_f16x2(gb0, gb1);
+  float h[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    h[j][0] = h[j][1] = h[j][2] = h[j][3] = 0.f;
+    mma16816(h[j], a0, a1, a2, a3, w.b1[j][0], w.b1[j][1]);
+  }
+  float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int s2 = 0; s2 < 4; ++s2) {
+    const uint32_t c0 = pack_relu_f16x2(h[2 * s2][0], h[2 * s2][1]);
+    const uint32_t c1 = pack_relu_f16x2(h[2 * s2][2], h[2 * s2][3]);
+    const uint32_t c2 = pack_relu_f16x2(h[2 * s2 + 1][0], h[2 * s2 + 1][1]);
+    const uint32_t c3 = pack_relu_f16x2(h[2 * s2 + 1][2], h[2 * s2 + 1][3]);
+    mma16816(o, c0, c1, c2, c3, w.b2[s2][0], w.b2[s2][1]);
+  }
+  sc_a = o[0];
+  sc_b = o[2];
 }
 
 // Scores of 16 rows (rows g and g + 8 belong to this lane's quad g = lane/4)
@@ -343,68 +378,6 @@ __global__ void __launch_bounds__(kScoreWarps * 32)
   store_cand<K>(cand_s, cand_i, p, split, splits, sc, id);
 }
 
-// Network proposal scores: warp = 16 poses (the 16 rows of every
-// tensor-core tile), blockIdx.y = tile split; two tiles in flight per step.
-template <int K>
-__global__ void __launch_bounds__(kScoreWarps * 32)
-    score_mlp(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
-              int n_tiles, int splits, float rfoot, const uint32_t *__restrict__ frag, float b2,
-              float *__restrict__ cand_s, int *__restrict__ cand_i)
-{
-  __shared__ float4 ab_s[kMaxSplitTiles];
-  __shared__ float ef_s[kMaxSplitTiles];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int split = blockIdx.y;
-  const int t0 = (int)((long long)n_tiles * split / splits);
-  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
-  stage_tiles(tiles, t0, t1, ab_s, ef_s);
-  __syncthreads();
-  const long long group = (long long)blockIdx.x * kScoreWarps + warp;
-  if (group * 16 >= P) return;  // uniform over the warp
-  const int g = lane >> 2, q = lane & 3;
-  const long long pa = group * 16 + g, pb = group * 16 + g + 8;
-  float pxa = 0.f, pya = 0.f, ca = 1.f, sa = 0.f, pxb = 0.f, pyb = 0.f, cb = 1.f, sb = 0.f;
-  if (pa < P) {
-    const float4 q4 = pose4[pa];
-    pxa = q4.x; pya = q4.y; ca = q4.z; sa = q4.w;
-  }
-  if (pb < P) {
-    const float4 q4 = pose4[pb];
-    pxb = q4.x; pyb = q4.y; cb = q4.z; sb = q4.w;
-  }
-  MlpFrags w;
-  load_frags(frag, lane, w);
-  float sca[K], scb[K];
-  int ida[K], idb[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    sca[i] = scb[i] = kInf;
-    ida[i] = idb[i] = -1;
-  }
-  const int n = t1 - t0;
-  for (int i = 0; i < n; i += 2) {
-    const int j = min(i + 1, n - 1);
-    const float4 a4 = ab_s[i], b4 = ab_s[j];
-    const float ab0[4] = {a4.x, a4.y, a4.z, a4.w};
-    const float ab1[4] = {b4.x, b4.y, b4.z, b4.w};
-    float s0a, s0b, s1a, s1b;
-    mlp_rows(w, ab0, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[i], s0a, s0b);
-    mlp_rows(w, ab1, q, pxa, pya, ca, sa, pxb, pyb, cb, sb, rfoot, ef_s[j], s1a, s1b);
-    if (q == 0) {
-      topk_insert<K>(sca, ida, s0a + b2, t0 + i);
-      topk_insert<K>(scb, idb, s0b + b2, t0 + i);
-      if (j != i) {
-        topk_insert<K>(sca, ida, s1a + b2, t0 + j);
-        topk_insert<K>(scb, idb, s1b + b2, t0 + j);
-      }
-    }
-  }
-  if (q == 0) {
-    if (pa < P) store_cand<K>(cand_s, cand_i, pa, split, splits, sca, ida);
-    if (pb < P) store_cand<K>(cand_s, cand_i, pb, split, splits, scb, idb);
-  }
-}
-
 // Per pose: its K best tiles over the splits -> prop[p * kMaxK + i], and the
 // pose appended to each of those tiles' lists.
 template <int K>
@@ -428,6 +401,102 @@ __global__ void merge_emit(long long P, int splits, const float *__restrict__ ca
       const int t = cand_i[c];
       if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
     }
+  int n = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    prop[p * kMaxK + i] = id[i];
+    if (id[i] >= 0) {
+      list[(long long)id[i] * P + atomicAdd(&hist[id[i]], 1)] = (int)p;
+      ++n;
+    }
+  }
+#pragma unroll
+  for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
+  atomicAdd(&ctr->n_prop, n);
+}
+
+// Learned proposal: warp = 32 poses, lane = pose.  Each pose merges its
+// bound-ranked candidates over the splits into the kPre tiles with the
+// smallest bounds; the network then scores those kPre (pose, tile) rows on
+// the tensor cores (16 rows = 2 poses x 8 candidates per mma tile) and the
+// pose proposes its K best by predicted signed distance.
+template <int K>
+__global__ void __launch_bounds__(128)
+    rerank_mlp(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
+               int splits, float rfoot, const uint32_t *__restrict__ frag, float b2,
+               const float *__restrict__ cand_s, const int *__restrict__ cand_i,
+               int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ list,
+               CullCounters *ctr)
+{
+  __shared__ int ct_s[4][32][kPre];
+  __shared__ float sc_s[4][32][kPre];
+  __shared__ float4 ps_s[4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long p = ((long long)blockIdx.x * 4 + warp) * 32 + lane;
+  const long long pbase = ((long long)blockIdx.x * 4 + warp) * 32;
+  if (pbase >= P) return;  // uniform over the warp
+  const bool valid = p < P;
+  {
+    float sc[kPre];
+    int id[kPre];
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      sc[i] = kInf;
+      id[i] = -1;
+    }
+    if (valid)
+      for (int sp = 0; sp < splits; ++sp)
+        for (int i = 0; i < kPre; ++i) {
+          const long long c = (p * splits + sp) * kPre + i;
+          const int t = cand_i[c];
+          if (t >= 0) topk_insert<kPre>(sc, id, cand_s[c], t);
+        }
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) ct_s[warp][lane][i] = id[i];
+    ps_s[warp][lane] = valid ? pose4[p] : make_float4(0.f, 0.f, 1.f, 0.f);
+  }
+  __syncwarp();
+  MlpFrags w;
+  load_frags(frag, lane, w);
+  const int g = lane >> 2, q = lane & 3;
+  for (int j = 0; j < 16; ++j) {
+    const int pa = 2 * j, pb = 2 * j + 1;
+    const int ta = ct_s[warp][pa][g], tb = ct_s[warp][pb][g];
+    float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
+    float efa = 0.f, efb = 0.f;
+    if (ta >= 0) {
+      const TileHdr h = tiles[ta];
+      aba[0] = h.aabb[0]; aba[1] = h.aabb[1]; aba[2] = h.aabb[2]; aba[3] = h.aabb[3];
+      efa = (float)h.n_vtx * (1.f / 256.f);
+    }
+    if (tb >= 0) {
+      const TileHdr h = tiles[tb];
+      abb[0] = h.aabb[0]; abb[1] = h.aabb[1]; abb[2] = h.aabb[2]; abb[3] = h.aabb[3];
+      efb = (float)h.n_vtx * (1.f / 256.f);
+    }
+    const float4 qa = ps_s[warp][pa], qb = ps_s[warp][pb];
+    float s_a, s_b;
+    mlp_rows_pair(w, q, aba, efa, qa.x, qa.y, qa.z, qa.w, abb, efb, qb.x, qb.y, qb.z, qb.w,
+                  rfoot, s_a, s_b);
+    if (q == 0) {
+      sc_s[warp][pa][g] = ta >= 0 ? s_a + b2 : kInf;
+      sc_s[warp][pb][g] = tb >= 0 ? s_b + b2 : kInf;
+    }
+  }
+  __syncwarp();
+  if (!valid) return;
+  float sc[K];
+  int id[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    sc[i] = kInf;
+    id[i] = -1;
+  }
+#pragma unroll
+  for (int i = 0; i < kPre; ++i) {
+    const int t = ct_s[warp][lane][i];
+    if (t >= 0) topk_insert<K>(sc, id, sc_s[warp][lane][i], t);
+  }
   int n = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -955,17 +1024,20 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     const unsigned pb = (unsigned)((P + 127) / 128);
     {
       ProfileScope prof("propose", st);
-      const long long warps = (P + 15) / 16;
-      dim3 sg(net ? (unsigned)((warps + kScoreWarps - 1) / kScoreWarps) : pb, (unsigned)L.splits);
+      dim3 sg(pb, (unsigned)L.splits);
+      const unsigned rb = (unsigned)((P + 127) / 128);
 #define PSDF_PROPOSE(KK)                                                                      \
-  if (net)                                                                                    \
-    score_mlp<KK><<<sg, kScoreWarps * 32, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits,     \
-                                                   F.radius, mlp->d_frag, mlp->b2, cand_s,    \
-                                                   cand_i);                                   \
-  else                                                                                        \
+  if (net) {                                                                                  \
+    score_bound<kPre><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,    \
+                                          cand_s, cand_i);                                    \
+    rerank_mlp<KK><<<rb, 128, 0, st>>>(pose4, P, scene->d_tiles, L.splits, F.radius,          \
+                                       mlp->d_frag, mlp->b2, cand_s, cand_i, prop, hist1,     \
+                                       list1, ctr);                                           \
+  } else {                                                                                    \
     score_bound<KK><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,      \
                                         cand_s, cand_i);                                      \
-  merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1, list1, ctr);
+    merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1, list1, ctr); \
+  }
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
