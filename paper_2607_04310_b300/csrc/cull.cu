@@ -415,10 +415,10 @@ __global__ void merge_emit(long long P, int splits, const float *__restrict__ ca
   atomicAdd(&ctr->n_prop, n);
 }
 
-// Learned proposal: warp = 32 poses, lane = pose.  Each pose merges its
-// bound-ranked candidates over the splits into the kPre tiles with the
-// smallest bounds; the network then scores those kPre (pose, tile) rows on
-// the tensor cores (16 rows = 2 poses x 8 candidates per mma tile) and the
+// Learned proposal: one warp = 2 poses (one 16-row tensor-core tile: rows
+// 0-7 are pose a's candidates, rows 8-15 pose b's).  16 lanes per pose merge
+// its bound-ranked candidates over the splits into the kPre tiles with the
+// smallest bounds; the network scores those kPre (pose, tile) rows and the
 // pose proposes its K best by predicted signed distance.
 template <int K>
 __global__ void __launch_bounds__(128)
@@ -428,81 +428,105 @@ __global__ void __launch_bounds__(128)
                int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ list,
                CullCounters *ctr)
 {
-  __shared__ int ct_s[4][32][kPre];
-  __shared__ float sc_s[4][32][kPre];
-  __shared__ float4 ps_s[4][32];
+  __shared__ int ct_s[4][2][kPre];
+  __shared__ float sc_s[4][2][kPre];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long p = ((long long)blockIdx.x * 4 + warp) * 32 + lane;
-  const long long pbase = ((long long)blockIdx.x * 4 + warp) * 32;
-  if (pbase >= P) return;  // uniform over the warp
+  const long long pw = ((long long)blockIdx.x * 4 + warp) * 2;  // first pose of the warp
+  if (pw >= P) return;                                           // uniform over the warp
+  const int half = lane >> 4, hl = lane & 15;                    // pose of this lane, index in it
+  const long long p = pw + half;
   const bool valid = p < P;
-  {
-    float sc[kPre];
-    int id[kPre];
+  // 1. each lane keeps the kPre best of its share of the candidates
+  float sc[kPre];
+  int id[kPre];
 #pragma unroll
-    for (int i = 0; i < kPre; ++i) {
-      sc[i] = kInf;
-      id[i] = -1;
-    }
-    if (valid)
-      for (int sp = 0; sp < splits; ++sp)
-        for (int i = 0; i < kPre; ++i) {
-          const long long c = (p * splits + sp) * kPre + i;
-          const int t = cand_i[c];
-          if (t >= 0) topk_insert<kPre>(sc, id, cand_s[c], t);
-        }
-#pragma unroll
-    for (int i = 0; i < kPre; ++i) ct_s[warp][lane][i] = id[i];
-    ps_s[warp][lane] = valid ? pose4[p] : make_float4(0.f, 0.f, 1.f, 0.f);
-  }
-  __syncwarp();
-  MlpFrags w;
-  load_frags(frag, lane, w);
-  const int g = lane >> 2, q = lane & 3;
-  for (int j = 0; j < 16; ++j) {
-    const int pa = 2 * j, pb = 2 * j + 1;
-    const int ta = ct_s[warp][pa][g], tb = ct_s[warp][pb][g];
-    float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
-    float efa = 0.f, efb = 0.f;
-    if (ta >= 0) {
-      const TileHdr h = tiles[ta];
-      aba[0] = h.aabb[0]; aba[1] = h.aabb[1]; aba[2] = h.aabb[2]; aba[3] = h.aabb[3];
-      efa = (float)h.n_vtx * (1.f / 256.f);
-    }
-    if (tb >= 0) {
-      const TileHdr h = tiles[tb];
-      abb[0] = h.aabb[0]; abb[1] = h.aabb[1]; abb[2] = h.aabb[2]; abb[3] = h.aabb[3];
-      efb = (float)h.n_vtx * (1.f / 256.f);
-    }
-    const float4 qa = ps_s[warp][pa], qb = ps_s[warp][pb];
-    float s_a, s_b;
-    mlp_rows_pair(w, q, aba, efa, qa.x, qa.y, qa.z, qa.w, abb, efb, qb.x, qb.y, qb.z, qb.w,
-                  rfoot, s_a, s_b);
-    if (q == 0) {
-      sc_s[warp][pa][g] = ta >= 0 ? s_a + b2 : kInf;
-      sc_s[warp][pb][g] = tb >= 0 ? s_b + b2 : kInf;
-    }
-  }
-  __syncwarp();
-  if (!valid) return;
-  float sc[K];
-  int id[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
+  for (int i = 0; i < kPre; ++i) {
     sc[i] = kInf;
     id[i] = -1;
   }
+  const int nc = splits * kPre;
+  if (valid)
+    for (int c = hl; c < nc; c += 16) {
+      const int t = cand_i[p * nc + c];
+      if (t >= 0) topk_insert<kPre>(sc, id, cand_s[p * nc + c], t);
+    }
+  // 2. kPre rounds of a 16-lane argmin: the pose's kPre smallest bounds
+  int head = 0;
+  for (int r = 0; r < kPre; ++r) {
+    float v = head < kPre ? sc[0] : kInf;
+    int t = head < kPre ? id[0] : -1;
+    int who = hl;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int t2 = __shfl_xor_sync(0xffffffffu, t, o);
+      const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+      if (v2 < v || (v2 == v && t2 < t && t2 >= 0) || (t < 0 && t2 >= 0)) {
+        v = v2;
+        t = t2;
+        who = w2;
+      }
+    }
+    if (hl == 0) ct_s[warp][half][r] = t;
+    if (who == hl && t >= 0) {  // pop the winner's head
+#pragma unroll
+      for (int i = 0; i < kPre - 1; ++i) {
+        sc[i] = sc[i + 1];
+        id[i] = id[i + 1];
+      }
+      sc[kPre - 1] = kInf;
+      id[kPre - 1] = -1;
+      ++head;
+    }
+  }
+  __syncwarp();
+  // 3. the network on the 16 rows
+  MlpFrags w;
+  load_frags(frag, lane, w);
+  const int g = lane >> 2, q = lane & 3;
+  const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
+  float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
+  float efa = 0.f, efb = 0.f;
+  if (ta >= 0) {
+    const TileHdr h = tiles[ta];
+    aba[0] = h.aabb[0]; aba[1] = h.aabb[1]; aba[2] = h.aabb[2]; aba[3] = h.aabb[3];
+    efa = (float)h.n_vtx * (1.f / 256.f);
+  }
+  if (tb >= 0) {
+    const TileHdr h = tiles[tb];
+    abb[0] = h.aabb[0]; abb[1] = h.aabb[1]; abb[2] = h.aabb[2]; abb[3] = h.aabb[3];
+    efb = (float)h.n_vtx * (1.f / 256.f);
+  }
+  const float4 qa = pose4[pw];
+  const float4 qb = (pw + 1 < P) ? pose4[pw + 1] : make_float4(0.f, 0.f, 1.f, 0.f);
+  float s_a, s_b;
+  mlp_rows_pair(w, q, aba, efa, qa.x, qa.y, qa.z, qa.w, abb, efb, qb.x, qb.y, qb.z, qb.w, rfoot,
+                s_a, s_b);
+  if (q == 0) {
+    sc_s[warp][0][g] = ta >= 0 ? s_a + b2 : kInf;
+    sc_s[warp][1][g] = tb >= 0 ? s_b + b2 : kInf;
+  }
+  __syncwarp();
+  // 4. lanes 0 and 16: the pose's K best by predicted signed distance
+  if (hl != 0 || !valid) return;
+  float bs[K];
+  int bi[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    bs[i] = kInf;
+    bi[i] = -1;
+  }
 #pragma unroll
   for (int i = 0; i < kPre; ++i) {
-    const int t = ct_s[warp][lane][i];
-    if (t >= 0) topk_insert<K>(sc, id, sc_s[warp][lane][i], t);
+    const int t = ct_s[warp][half][i];
+    if (t >= 0) topk_insert<K>(bs, bi, sc_s[warp][half][i], t);
   }
   int n = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    prop[p * kMaxK + i] = id[i];
-    if (id[i] >= 0) {
-      list[(long long)id[i] * P + atomicAdd(&hist[id[i]], 1)] = (int)p;
+    prop[p * kMaxK + i] = bi[i];
+    if (bi[i] >= 0) {
+      list[(long long)bi[i] * P + atomicAdd(&hist[bi[i]], 1)] = (int)p;
       ++n;
     }
   }
@@ -1025,7 +1049,7 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     {
       ProfileScope prof("propose", st);
       dim3 sg(pb, (unsigned)L.splits);
-      const unsigned rb = (unsigned)((P + 127) / 128);
+      const unsigned rb = (unsigned)((P + 7) / 8);  // 4 warps x 2 poses per CTA
 #define PSDF_PROPOSE(KK)                                                                      \
   if (net) {                                                                                  \
     score_bound<kPre><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,    \
