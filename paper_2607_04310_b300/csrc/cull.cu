@@ -1,22 +1,22 @@
 // Exact tile cull with a proposal (psdf_eval_culled and its helpers).
 //
 // Work is organised as (pose, tile) pairs, bucketed by tile:
-//   1. cull_init       keys = +inf, per-tile counters and flags cleared
-//   2. score_bound     every pose ranks all tiles by the conservative bound;
-//                      best candidates per tile split
-//   3. merge_emit      per pose: its K best tiles by the bound; or
-//      rerank_mlp      per pose: its 8 best tiles by the bound re-ranked by the
-//                      tile-proposal network on tensor cores, K best kept;
-//                      the pose is appended to each proposed tile's list
-//   4. tiles_scan      per-tile work units (exclusive prefix sum)
-//   5. eval_lists      persistent CTAs over units: the tile's blob staged in shared
+//   0. memset          per-tile counters and the pipeline counters cleared
+//   1. propose         16 lanes per pose rank every tile by the conservative
+//                      bound; the pose keeps its K best, or its 8 best
+//                      re-ranked by the tile-proposal network on tensor cores
+//                      (K best kept); the pose is appended to each proposed
+//                      tile's list.  The CTA that finishes last turns the
+//                      per-tile counts into work units (prefix sum + unit map)
+//   2. eval_lists      persistent CTAs over units: the tile's blob staged in shared
 //                      memory, lanes = (pose, obstacle range) pairs so that
 //                      warps stay full, exact evaluation, one atomicMin per
 //                      lane into the pose's 64-bit key
-//   6. fb_pairs / tiles_scan / eval_lists
-//                      fallback: every tile a pose did not propose whose
-//                      lower bound does not exceed the pose's current minimum
-//   7. epilogue        as for the full scan
+//   3. fallback        16 lanes per pose append every tile the pose did not
+//                      propose whose lower bound does not exceed the pose's
+//                      current minimum; the last CTA builds the work units
+//   4. eval_lists      as 2, over the fallback pairs
+//   5. epilogue        as for the full scan
 // A skipped (pose, tile) pair holds only values strictly above the pose's
 // minimum, and the minimum over 64-bit keys does not depend on evaluation
 // order, so the result equals the full scan's bit for bit.
@@ -42,9 +42,8 @@ constexpr int kMaxK = PSDF_CULL_MAX_K;
 constexpr int kPre = 8;  // bound-ranked candidates the network re-ranks per pose
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
-constexpr int kScoreWarps = 4;
-constexpr int kMaxSplitTiles = 1024;  // tiles per split staged in shared memory
-constexpr int kListThreads = 128;     // threads of an eval_lists CTA
+constexpr int kPoseThreads = 128;  // 4 warps x 2 poses per propose / fallback CTA
+constexpr int kListThreads = 128;  // threads of an eval_lists CTA
 constexpr int kMaxScanTiles = 1024 * 64;
 
 // counters at the start of the workspace
@@ -53,45 +52,46 @@ struct CullCounters {
   int n_prop;          // proposed (pose, tile) pairs
   int n_fb;            // fallback (pose, tile) pairs
   int fallback_poses;  // poses with at least one fallback pair
+  unsigned done1;      // CTAs of the propose kernel that finished
+  unsigned done2;      // CTAs of the fallback kernel that finished
 };
 
 struct CullLayout {
-  size_t keys, pose4, flags, cand_s, cand_i, hist1, uoff1, hist2, uoff2, prop, list1, list2,
-      total;
-  int splits;
+  size_t hist1, hist2, clear_bytes, keys, pose4, prop, uoff1, utile1, uoff2, utile2, list1,
+      list2, total;
+  long long cap1, cap2;  // capacity of the unit maps
 };
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Tile splits of the proposal scoring: enough (group, split) warps to fill
-// the GPU, at most 1024 tiles per split staged in shared memory.
-static int score_splits(long long P, int n_tiles)
+// Work units of a tile with cnt listed poses: at most 2 while cnt <= 256,
+// else ceil(cnt / 128); over all tiles at most 3 T + items / 128.
+static long long unit_capacity(long long items, int n_tiles)
 {
-  const long long groups = std::max<long long>(1, (P + 15) / 16);
-  long long sp = (2048 + groups - 1) / groups;
-  sp = std::max<long long>(sp, (n_tiles + kMaxSplitTiles - 1) / kMaxSplitTiles);
-  return (int)std::max<long long>(1, std::min<long long>(sp, 64));
+  return 3LL * n_tiles + items / 128 + 1;
 }
 
 // Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]),
-// so that proposals and fallback pairs are appended in one pass.
+// so that proposals and fallback pairs are appended in one pass.  The
+// counters and both per-tile histograms are contiguous (one memset).
 static CullLayout cull_layout(long long P, int n_tiles)
 {
   CullLayout L;
   const size_t Pz = (size_t)std::max<long long>(P, 1);
   const size_t Tz = (size_t)std::max(n_tiles, 1);
-  L.splits = score_splits(P, n_tiles);
+  L.cap1 = unit_capacity((long long)Pz * kMaxK, (int)Tz);
+  L.cap2 = unit_capacity((long long)Pz * Tz, (int)Tz);
   size_t o = 256;
+  L.hist1 = o; o = align256(o + 4 * Tz);
+  L.hist2 = o; o = align256(o + 4 * Tz);
+  L.clear_bytes = o;
   L.keys = o; o = align256(o + 8 * Pz);
   L.pose4 = o; o = align256(o + 16 * Pz);
-  L.flags = o; o = align256(o + 4 * Pz);
   L.prop = o; o = align256(o + 4 * Pz * kMaxK);
-  L.cand_s = o; o = align256(o + 4 * Pz * L.splits * kPre);
-  L.cand_i = o; o = align256(o + 4 * Pz * L.splits * kPre);
-  L.hist1 = o; o = align256(o + 4 * Tz);
   L.uoff1 = o; o = align256(o + 4 * (Tz + 1));
-  L.hist2 = o; o = align256(o + 4 * Tz);
+  L.utile1 = o; o = align256(o + 4 * (size_t)L.cap1);
   L.uoff2 = o; o = align256(o + 4 * (Tz + 1));
+  L.utile2 = o; o = align256(o + 4 * (size_t)L.cap2);
   L.list1 = o; o = align256(o + 4 * Pz * Tz);
   L.list2 = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
@@ -278,6 +278,79 @@ __device__ __forceinline__ void mlp_rows(const MlpFrags &w, const float *ab, int
 }
 
 // ---------------------------------------------------------------------------
+// per-tile work units
+// ---------------------------------------------------------------------------
+// Lanes of a tile's work: its cnt poses are split over S obstacle ranges
+// each, so that cnt * S lanes fill about two 128-thread units when few poses
+// need the tile (short per-lane chains, many warps in flight).
+constexpr int kTargetLanes = 2 * kListThreads;
+__device__ __forceinline__ int tile_split(int cnt, int n_obs)
+{
+  return max(1, min(kTargetLanes / max(cnt, 1), n_obs));
+}
+
+__device__ __forceinline__ int tile_units(int cnt, int n_obs)
+{
+  return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
+}
+
+// Run by one whole CTA of kPoseThreads threads once every append to hist is
+// done: exclusive prefix sum of the tiles' units -> uoff[t] (uoff[T] = total),
+// the unit -> tile map utile[u], and the number of listed pairs -> *items.
+// hist was written by atomics of other CTAs: read through L2.
+__device__ void build_units(const int *hist, const TileHdr *__restrict__ tiles, int T,
+                            int *__restrict__ uoff, int *__restrict__ utile, int *items)
+{
+  __shared__ int w_units[kPoseThreads / 32], w_items[kPoseThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (T + kPoseThreads - 1) / kPoseThreads;
+  const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
+  int su = 0, si = 0;
+  for (int i = b0; i < b1; ++i) {
+    const int c = __ldcg(hist + i);
+    su += tile_units(c, tiles[i].n_obs);
+    si += c;
+  }
+  int incl = su, isum = si;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+    isum += __shfl_xor_sync(0xffffffffu, isum, o);
+  }
+  if (lane == 31) w_units[warp] = incl;
+  if (lane == 0) w_items[warp] = isum;
+  __syncthreads();
+  int ubase = incl - su, total_items = 0;
+#pragma unroll
+  for (int w = 0; w < kPoseThreads / 32; ++w) {
+    if (w < warp) ubase += w_units[w];
+    total_items += w_items[w];
+  }
+  for (int i = b0; i < b1; ++i) {
+    const int nu = tile_units(__ldcg(hist + i), tiles[i].n_obs);
+    uoff[i] = ubase;
+    for (int k = 0; k < nu; ++k) utile[ubase + k] = i;
+    ubase += nu;
+  }
+  if (tid == kPoseThreads - 1) uoff[T] = ubase;
+  if (tid == 0) *items = total_items;
+}
+
+// True in every thread of the CTA that finished last (all other CTAs'
+// appends are then visible); the counter is cleared before the launch.
+__device__ __forceinline__ bool last_cta(unsigned *done)
+{
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// ---------------------------------------------------------------------------
 // proposals
 // ---------------------------------------------------------------------------
 template <int K>
@@ -299,293 +372,144 @@ __device__ __forceinline__ void topk_insert(float (&sc)[K], int (&id)[K], float 
   }
 }
 
-template <int K>
-__device__ __forceinline__ void store_cand(float *cand_s, int *cand_i, long long p, int split,
-                                           int splits, const float (&sc)[K], const int (&id)[K])
+__device__ __forceinline__ float4 tile_aabb(const TileHdr *__restrict__ tiles, int t)
 {
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    cand_s[(p * splits + split) * K + i] = sc[i];
-    cand_i[(p * splits + split) * K + i] = id[i];
-  }
+  return __ldg(reinterpret_cast<const float4 *>(tiles + t) + 1);
 }
 
-// Stage the AABBs (and edge fractions) of tiles [t0, t1) in shared memory.
-__device__ __forceinline__ void stage_tiles(const TileHdr *__restrict__ tiles, int t0, int t1,
-                                            float4 *ab_s, float *ef_s)
+// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).  Each
+// lane ranks tiles hl, hl + 16, ... by the bound and keeps its R best; R
+// rounds of a 16-lane argmin over the lanes' heads give the pose's R
+// smallest (bound, tile) pairs in order, written to cand[r] (uniform over
+// the pose's 16 lanes).  With NET the 16 rows (2 poses x kPre candidates)
+// are scored by the network and the pose keeps its K best scores; else its
+// K best bounds.  Lane 0 of each pose appends the pose to its proposed tiles.
+template <int K, bool NET>
+__global__ void __launch_bounds__(kPoseThreads)
+    propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
+            int T, float rfoot, const uint32_t *__restrict__ frag, float b2,
+            unsigned long long *__restrict__ keys, float4 *__restrict__ pose4,
+            int *__restrict__ prop, int *hist, int *__restrict__ list, int *__restrict__ uoff,
+            int *__restrict__ utile, CullCounters *ctr)
 {
-  for (int i = threadIdx.x; i < t1 - t0; i += blockDim.x) {
-    const TileHdr h = tiles[t0 + i];
-    ab_s[i] = make_float4(h.aabb[0], h.aabb[1], h.aabb[2], h.aabb[3]);
-    if (ef_s) ef_s[i] = (float)h.n_vtx * (1.f / 256.f);
-  }
-}
-
-// keys = +inf, flags and per-tile counters cleared, and every pose's
-// (x, y, cos theta, sin theta) computed once.
-__global__ void cull_init(const float *__restrict__ poses, unsigned long long *keys,
-                          float4 *pose4, int *flags, long long P, int *hist1, int *hist2, int T,
-                          CullCounters *ctr)
-{
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P) {
-    keys[i] = ~0ull;
-    flags[i] = 0;
-    float s, c;
-    sincosf(poses[3 * i + 2], &s, &c);
-    pose4[i] = make_float4(poses[3 * i], poses[3 * i + 1], c, s);
-  }
-  if (i < T) {
-    hist1[i] = 0;
-    hist2[i] = 0;
-  }
-  if (i == 0) {
-    ctr->err = 0;
-    ctr->n_prop = 0;
-    ctr->n_fb = 0;
-    ctr->fallback_poses = 0;
-  }
-}
-
-// Bound proposal scores: thread = pose, blockIdx.y = tile split.
-template <int K>
-__global__ void __launch_bounds__(kScoreWarps * 32)
-    score_bound(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
-                int n_tiles, int splits, float rfoot, float *__restrict__ cand_s,
-                int *__restrict__ cand_i)
-{
-  __shared__ float4 ab_s[kMaxSplitTiles];
-  const int split = blockIdx.y;
-  const int t0 = (int)((long long)n_tiles * split / splits);
-  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
-  stage_tiles(tiles, t0, t1, ab_s, nullptr);
-  __syncthreads();
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const float px = pose4[p].x, py = pose4[p].y;
-  float sc[K];
-  int id[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    sc[i] = kInf;
-    id[i] = -1;
-  }
-  for (int i = 0; i < t1 - t0; ++i) {
-    const float4 a4 = ab_s[i];
-    const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-    topk_insert<K>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
-  }
-  store_cand<K>(cand_s, cand_i, p, split, splits, sc, id);
-}
-
-// Per pose: its K best tiles over the splits -> prop[p * kMaxK + i], and the
-// pose appended to each of those tiles' lists.
-template <int K>
-__global__ void merge_emit(long long P, int splits, const float *__restrict__ cand_s,
-                           const int *__restrict__ cand_i, int *__restrict__ prop,
-                           int *__restrict__ hist, int *__restrict__ list, CullCounters *ctr)
-{
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  float sc[K];
-  int id[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    sc[i] = kInf;
-    id[i] = -1;
-  }
-  for (int sp = 0; sp < splits; ++sp)
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      const long long c = (p * splits + sp) * K + i;
-      const int t = cand_i[c];
-      if (t >= 0) topk_insert<K>(sc, id, cand_s[c], t);
-    }
-  int n = 0;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    prop[p * kMaxK + i] = id[i];
-    if (id[i] >= 0) {
-      list[(long long)id[i] * P + atomicAdd(&hist[id[i]], 1)] = (int)p;
-      ++n;
-    }
-  }
-#pragma unroll
-  for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
-  atomicAdd(&ctr->n_prop, n);
-}
-
-// Learned proposal: one warp = 2 poses (one 16-row tensor-core tile: rows
-// 0-7 are pose a's candidates, rows 8-15 pose b's).  16 lanes per pose merge
-// its bound-ranked candidates over the splits into the kPre tiles with the
-// smallest bounds; the network scores those kPre (pose, tile) rows and the
-// pose proposes its K best by predicted signed distance.
-template <int K>
-__global__ void __launch_bounds__(128)
-    rerank_mlp(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
-               int splits, float rfoot, const uint32_t *__restrict__ frag, float b2,
-               const float *__restrict__ cand_s, const int *__restrict__ cand_i,
-               int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ list,
-               CullCounters *ctr)
-{
-  __shared__ int ct_s[4][2][kPre];
-  __shared__ float sc_s[4][2][kPre];
+  constexpr int R = NET ? kPre : K;
+  __shared__ int ct_s[kPoseThreads / 32][2][kPre];
+  __shared__ float sc_s[kPoseThreads / 32][2][kPre];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long pw = ((long long)blockIdx.x * 4 + warp) * 2;  // first pose of the warp
-  if (pw >= P) return;                                           // uniform over the warp
-  const int half = lane >> 4, hl = lane & 15;                    // pose of this lane, index in it
-  const long long p = pw + half;
-  const bool valid = p < P;
-  // 1. each lane keeps the kPre best of its share of the candidates
-  float sc[kPre];
-  int id[kPre];
-#pragma unroll
-  for (int i = 0; i < kPre; ++i) {
-    sc[i] = kInf;
-    id[i] = -1;
-  }
-  const int nc = splits * kPre;
-  if (valid)
-    for (int c = hl; c < nc; c += 16) {
-      const int t = cand_i[p * nc + c];
-      if (t >= 0) topk_insert<kPre>(sc, id, cand_s[p * nc + c], t);
-    }
-  // 2. kPre rounds of a 16-lane argmin: the pose's kPre smallest bounds
-  int head = 0;
-  for (int r = 0; r < kPre; ++r) {
-    float v = head < kPre ? sc[0] : kInf;
-    int t = head < kPre ? id[0] : -1;
-    int who = hl;
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-      const int t2 = __shfl_xor_sync(0xffffffffu, t, o);
-      const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
-      if (v2 < v || (v2 == v && t2 < t && t2 >= 0) || (t < 0 && t2 >= 0)) {
-        v = v2;
-        t = t2;
-        who = w2;
+  const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
+  if (pw < P) {  // uniform over the warp
+    const int half = lane >> 4, hl = lane & 15;
+    const long long p = pw + half;
+    const bool valid = p < P;
+    float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
+    if (valid) {
+      px = poses[3 * p];
+      py = poses[3 * p + 1];
+      sincosf(poses[3 * p + 2], &s, &c);
+      if (hl == 0) {
+        keys[p] = ~0ull;
+        pose4[p] = make_float4(px, py, c, s);
       }
     }
-    if (hl == 0) ct_s[warp][half][r] = t;
-    if (who == hl && t >= 0) {  // pop the winner's head
+    float sc[R];
+    int id[R];
 #pragma unroll
-      for (int i = 0; i < kPre - 1; ++i) {
-        sc[i] = sc[i + 1];
-        id[i] = id[i + 1];
+    for (int i = 0; i < R; ++i) {
+      sc[i] = kInf;
+      id[i] = -1;
+    }
+    if (valid)
+      for (int t = hl; t < T; t += 16) {
+        const float4 a4 = tile_aabb(tiles, t);
+        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+        topk_insert<R>(sc, id, tile_lb(ab, px, py, rfoot), t);
       }
-      sc[kPre - 1] = kInf;
-      id[kPre - 1] = -1;
-      ++head;
+    // R rounds of a 16-lane argmin with pop
+    int cand[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float v = sc[0];
+      int t = id[0], who = hl;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int t2 = __shfl_xor_sync(0xffffffffu, t, o);
+        const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+        if (t2 >= 0 && (t < 0 || v2 < v || (v2 == v && t2 < t))) {
+          v = v2;
+          t = t2;
+          who = w2;
+        }
+      }
+      cand[r] = t;
+      if (who == hl && t >= 0) {
+#pragma unroll
+        for (int i = 0; i < R - 1; ++i) {
+          sc[i] = sc[i + 1];
+          id[i] = id[i + 1];
+        }
+        sc[R - 1] = kInf;
+        id[R - 1] = -1;
+      }
+    }
+    int best[K];
+    if constexpr (NET) {
+      if (hl == 0)
+#pragma unroll
+        for (int r = 0; r < kPre; ++r) ct_s[warp][half][r] = cand[r];
+      __syncwarp();
+      MlpFrags w;
+      load_frags(frag, lane, w);
+      const int g = lane >> 2, q = lane & 3;
+      const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
+      float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
+      float efa = 0.f, efb = 0.f;
+      if (ta >= 0) {
+        const float4 a4 = tile_aabb(tiles, ta);
+        aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
+        efa = (float)tiles[ta].n_vtx * (1.f / 256.f);
+      }
+      if (tb >= 0) {
+        const float4 a4 = tile_aabb(tiles, tb);
+        abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
+        efb = (float)tiles[tb].n_vtx * (1.f / 256.f);
+      }
+      // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
+      const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
+      const float ca = __shfl_sync(0xffffffffu, c, 0), sa = __shfl_sync(0xffffffffu, s, 0);
+      const float pxb = __shfl_sync(0xffffffffu, px, 16), pyb = __shfl_sync(0xffffffffu, py, 16);
+      const float cb = __shfl_sync(0xffffffffu, c, 16), sb = __shfl_sync(0xffffffffu, s, 16);
+      float s_a, s_b;
+      mlp_rows_pair(w, q, aba, efa, pxa, pya, ca, sa, abb, efb, pxb, pyb, cb, sb, rfoot, s_a, s_b);
+      if (q == 0) {
+        sc_s[warp][0][g] = ta >= 0 ? s_a + b2 : kInf;
+        sc_s[warp][1][g] = tb >= 0 ? s_b + b2 : kInf;
+      }
+      __syncwarp();
+      float bs[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        bs[i] = kInf;
+        best[i] = -1;
+      }
+#pragma unroll
+      for (int i = 0; i < kPre; ++i)
+        if (cand[i] >= 0) topk_insert<K>(bs, best, sc_s[warp][half][i], cand[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < K; ++i) best[i] = cand[i];
+    }
+    if (valid && hl == 0) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        prop[p * kMaxK + i] = best[i];
+        if (best[i] >= 0) list[(long long)best[i] * P + atomicAdd(&hist[best[i]], 1)] = (int)p;
+      }
+#pragma unroll
+      for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
     }
   }
-  __syncwarp();
-  // 3. the network on the 16 rows
-  MlpFrags w;
-  load_frags(frag, lane, w);
-  const int g = lane >> 2, q = lane & 3;
-  const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
-  float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
-  float efa = 0.f, efb = 0.f;
-  if (ta >= 0) {
-    const TileHdr h = tiles[ta];
-    aba[0] = h.aabb[0]; aba[1] = h.aabb[1]; aba[2] = h.aabb[2]; aba[3] = h.aabb[3];
-    efa = (float)h.n_vtx * (1.f / 256.f);
-  }
-  if (tb >= 0) {
-    const TileHdr h = tiles[tb];
-    abb[0] = h.aabb[0]; abb[1] = h.aabb[1]; abb[2] = h.aabb[2]; abb[3] = h.aabb[3];
-    efb = (float)h.n_vtx * (1.f / 256.f);
-  }
-  const float4 qa = pose4[pw];
-  const float4 qb = (pw + 1 < P) ? pose4[pw + 1] : make_float4(0.f, 0.f, 1.f, 0.f);
-  float s_a, s_b;
-  mlp_rows_pair(w, q, aba, efa, qa.x, qa.y, qa.z, qa.w, abb, efb, qb.x, qb.y, qb.z, qb.w, rfoot,
-                s_a, s_b);
-  if (q == 0) {
-    sc_s[warp][0][g] = ta >= 0 ? s_a + b2 : kInf;
-    sc_s[warp][1][g] = tb >= 0 ? s_b + b2 : kInf;
-  }
-  __syncwarp();
-  // 4. lanes 0 and 16: the pose's K best by predicted signed distance
-  if (hl != 0 || !valid) return;
-  float bs[K];
-  int bi[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    bs[i] = kInf;
-    bi[i] = -1;
-  }
-#pragma unroll
-  for (int i = 0; i < kPre; ++i) {
-    const int t = ct_s[warp][half][i];
-    if (t >= 0) topk_insert<K>(bs, bi, sc_s[warp][half][i], t);
-  }
-  int n = 0;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    prop[p * kMaxK + i] = bi[i];
-    if (bi[i] >= 0) {
-      list[(long long)bi[i] * P + atomicAdd(&hist[bi[i]], 1)] = (int)p;
-      ++n;
-    }
-  }
-#pragma unroll
-  for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
-  atomicAdd(&ctr->n_prop, n);
-}
-
-// Lanes of a tile's work: its cnt poses are split over S obstacle ranges
-// each, so that cnt * S lanes fill about two 128-thread units when few poses
-// need the tile (short per-lane chains, many warps in flight).
-constexpr int kTargetLanes = 2 * kListThreads;
-__device__ __forceinline__ int tile_split(int cnt, int n_obs)
-{
-  return max(1, min(kTargetLanes / max(cnt, 1), n_obs));
-}
-
-__device__ __forceinline__ int tile_units(int cnt, int n_obs)
-{
-  return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
-}
-
-// Exclusive prefix sum over tiles of the work units -> uoff[t], uoff[T] =
-// total (one CTA of 1024 threads, each a run of consecutive tiles).
-__global__ void __launch_bounds__(1024)
-    tiles_scan(const int *__restrict__ hist, const TileHdr *__restrict__ tiles, int T,
-               int *__restrict__ uoff)
-{
-  __shared__ int warp_sum[32];
-  const int tid = threadIdx.x;
-  const int per = (T + 1023) / 1024;
-  const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
-  int su = 0;
-  for (int i = b0; i < b1; ++i) su += tile_units(hist[i], tiles[i].n_obs);
-  int incl = su;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((tid & 31) >= o) incl += n;
-  }
-  if ((tid & 31) == 31) warp_sum[tid >> 5] = incl;
-  __syncthreads();
-  if (tid < 32) {
-    const int w = warp_sum[tid];
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_up_sync(0xffffffffu, wi, o);
-      if (tid >= o) wi += n;
-    }
-    warp_sum[tid] = wi - w;
-  }
-  __syncthreads();
-  int ubase = warp_sum[tid >> 5] + incl - su;
-  for (int i = b0; i < b1; ++i) {
-    uoff[i] = ubase;
-    ubase += tile_units(hist[i], tiles[i].n_obs);
-  }
-  if (tid == 1023) uoff[T] = ubase;
+  if (last_cta(&ctr->done1)) build_units(hist, tiles, T, uoff, utile, &ctr->n_prop);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,29 +528,23 @@ __device__ __forceinline__ void cp_async_wait_all()
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Persistent CTAs over work units.  Unit u belongs to tile t with
-// uoff[t] <= u < uoff[t + 1] (binary search) and covers lanes
-// [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane l evaluates
-// pose list[t * P + l / S] against obstacle range l % S of the tile and
-// merges its minimum into the pose's key.  The tile's blob is staged in
-// shared memory (16-byte cp.async per thread) once per unit.
+// Persistent CTAs over work units.  Unit u belongs to tile t = utile[u] and
+// covers lanes [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane
+// l evaluates pose list[t * P + l / S] against obstacle range l % S of the
+// tile and merges its minimum into the pose's key.  The tile's blob is
+// staged in shared memory (16-byte cp.async per thread) once per unit.
 template <int M>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
                const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
                const int *__restrict__ hist, const int *__restrict__ uoff,
-               const int *__restrict__ list, unsigned long long *__restrict__ keys)
+               const int *__restrict__ utile, long long cap, const int *__restrict__ list,
+               unsigned long long *__restrict__ keys)
 {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int U = uoff[T];
-  for (int u = blockIdx.x; u < U; u += gridDim.x) {
-    int lo = 0, hi = T - 1;  // largest t with uoff[t] <= u
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (uoff[mid] <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    const int t = lo;
+  for (int u = blockIdx.x; u < U && u < cap; u += gridDim.x) {
+    const int t = utile[u];
     const TileHdr h = tiles[t];
     const int cnt = hist[t];
     const int S = tile_split(cnt, h.n_obs);
@@ -636,13 +554,14 @@ __global__ void __launch_bounds__(kListThreads)
     __syncthreads();  // the previous unit's reads of the staged tile are done
     for (int o = 16 * threadIdx.x; o < h.blob_bytes; o += 16 * kListThreads)
       cp_async16(tsm + o, src + o);
+    long long p = -1;
+    if (l < L) p = list[(long long)t * P + l / S];
     cp_async_wait_all();
     __syncthreads();
-    if (l < L) {
+    if (p >= 0) {
       const int4 *ob = reinterpret_cast<const int4 *>(tsm);
       const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
-      const int pi = (int)(l / S), part = (int)(l % S);
-      const long long p = list[(long long)t * P + pi];
+      const int part = (int)(l % S);
       const float4 q4 = pose4[p];
       const float px = q4.x, py = q4.y, c = q4.z, s = q4.w;
       const int o0 = (int)((long long)h.n_obs * part / S);
@@ -671,41 +590,47 @@ __device__ __forceinline__ bool fb_need(const float *ab, float px, float py, flo
   return !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
 }
 
-// Every (pose, tile) pair of a pose's unproposed tiles whose bound does not
-// exceed the pose's current minimum is appended to the tile's list.
-__global__ void __launch_bounds__(128)
-    fb_pairs(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
-             int n_tiles, int splits, float rfoot, const unsigned long long *__restrict__ keys,
-             const int *__restrict__ prop, int *__restrict__ hist, int *__restrict__ list,
-             int *__restrict__ flags, CullCounters *ctr)
+// 16 lanes per pose (two poses per warp) over the tiles: every unproposed
+// tile whose bound does not exceed the pose's current minimum gets the pose
+// appended to its list.  The last CTA builds the work units.
+__global__ void __launch_bounds__(kPoseThreads)
+    fallback(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
+             int T, float rfoot, const unsigned long long *__restrict__ keys,
+             const int *__restrict__ prop, int *hist, int *__restrict__ list,
+             int *__restrict__ uoff, int *__restrict__ utile, CullCounters *ctr)
 {
-  __shared__ float4 ab_s[kMaxSplitTiles];
-  const int split = blockIdx.y;
-  const int t0 = (int)((long long)n_tiles * split / splits);
-  const int t1 = (int)((long long)n_tiles * (split + 1) / splits);
-  stage_tiles(tiles, t0, t1, ab_s, nullptr);
+  __shared__ int n_poses;
+  if (threadIdx.x == 0) n_poses = 0;
   __syncthreads();
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const float4 q4 = pose4[p];
-  const unsigned long long key = keys[p];
-  const float best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
-  int pr[kMaxK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
+  if (pw < P) {  // uniform over the warp
+    const int hl = lane & 15;
+    const long long p = pw + (lane >> 4);
+    int n = 0;
+    if (p < P) {
+      const float4 q4 = pose4[p];
+      const unsigned long long key = keys[p];
+      const float best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
+      int pr[kMaxK];
 #pragma unroll
-  for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
-  int n = 0;
-  for (int i = 0; i < t1 - t0; ++i) {
-    const float4 a4 = ab_s[i];
-    const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-    if (fb_need(ab, q4.x, q4.y, rfoot, best, t0 + i, pr)) {
-      list[(long long)(t0 + i) * P + atomicAdd(&hist[t0 + i], 1)] = (int)p;
-      ++n;
+      for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
+      for (int t = hl; t < T; t += 16) {
+        const float4 a4 = tile_aabb(tiles, t);
+        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+        if (fb_need(ab, q4.x, q4.y, rfoot, best, t, pr)) {
+          list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
+          ++n;
+        }
+      }
     }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (hl == 0 && n > 0) atomicAdd(&n_poses, 1);
   }
-  if (n) {
-    atomicAdd(&ctr->n_fb, n);
-    if (atomicExch(&flags[p], 1) == 0) atomicAdd(&ctr->fallback_poses, 1);
-  }
+  __syncthreads();
+  if (threadIdx.x == 0 && n_poses) atomicAdd(&ctr->fallback_poses, n_poses);
+  if (last_cta(&ctr->done2)) build_units(hist, tiles, T, uoff, utile, &ctr->n_fb);
 }
 
 // ---------------------------------------------------------------------------
@@ -807,8 +732,8 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 template <int M>
 struct ListEvalCall {
   static int run(const FootprintK &F, const ParamsK &pk, const float4 *pose4, long long P,
-                 const psdf_scene *sc, const int *hist, const int *uoff, const int *list,
-                 unsigned long long *keys, cudaStream_t st)
+                 const psdf_scene *sc, const int *hist, const int *uoff, const int *utile,
+                 long long cap, const int *list, unsigned long long *keys, cudaStream_t st)
   {
     const size_t smem = (size_t)(sc->max_blob_bytes + 15) / 16 * 16;
     if (smem > 48 * 1024) {
@@ -819,7 +744,8 @@ struct ListEvalCall {
     }
     const int grid = device_sms() * 8;
     eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, pose4, P, sc->d_tiles, sc->n_tiles,
-                                                   sc->d_blob, hist, uoff, list, keys);
+                                                   sc->d_blob, hist, uoff, utile, cap, list,
+                                                   keys);
     return PSDF_OK;
   }
 };
@@ -1028,40 +954,38 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   CullCounters *ctr = reinterpret_cast<CullCounters *>(ws);
   unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
   float4 *pose4 = reinterpret_cast<float4 *>(ws + L.pose4);
-  int *flags = reinterpret_cast<int *>(ws + L.flags);
   int *prop = reinterpret_cast<int *>(ws + L.prop);
-  float *cand_s = reinterpret_cast<float *>(ws + L.cand_s);
-  int *cand_i = reinterpret_cast<int *>(ws + L.cand_i);
   int *hist1 = reinterpret_cast<int *>(ws + L.hist1);
-  int *uoff1 = reinterpret_cast<int *>(ws + L.uoff1);
   int *hist2 = reinterpret_cast<int *>(ws + L.hist2);
+  int *uoff1 = reinterpret_cast<int *>(ws + L.uoff1);
   int *uoff2 = reinterpret_cast<int *>(ws + L.uoff2);
+  int *utile1 = reinterpret_cast<int *>(ws + L.utile1);
+  int *utile2 = reinterpret_cast<int *>(ws + L.utile2);
   int *list1 = reinterpret_cast<int *>(ws + L.list1);
   int *list2 = reinterpret_cast<int *>(ws + L.list2);
   ParamsK pk{params->eps_sat, params->eta};
-  const int init_n = (int)std::max<long long>(P, T);
-  cull_init<<<(init_n + 255) / 256, 256, 0, st>>>(poses, keys, pose4, flags, P, hist1, hist2, T,
-                                                  ctr);
-  if (T > 0) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.clear_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(cull counters)");
+  if (T == 0) {
+    e = cudaMemsetAsync(keys, 0xff, 8 * (size_t)P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(keys)");
+  } else {
     const int K = opts->k;
     const bool net = opts->mode == PSDF_PROPOSE_MLP;
-    const unsigned pb = (unsigned)((P + 127) / 128);
+    const unsigned pb = (unsigned)((P + 7) / 8);  // 4 warps x 2 poses per CTA
+    const uint32_t *frag = net ? mlp->d_frag : nullptr;
+    const float b2 = net ? mlp->b2 : 0.f;
     {
       ProfileScope prof("propose", st);
-      dim3 sg(pb, (unsigned)L.splits);
-      const unsigned rb = (unsigned)((P + 7) / 8);  // 4 warps x 2 poses per CTA
-#define PSDF_PROPOSE(KK)                                                                      \
-  if (net) {                                                                                  \
-    score_bound<kPre><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,    \
-                                          cand_s, cand_i);                                    \
-    rerank_mlp<KK><<<rb, 128, 0, st>>>(pose4, P, scene->d_tiles, L.splits, F.radius,          \
-                                       mlp->d_frag, mlp->b2, cand_s, cand_i, prop, hist1,     \
-                                       list1, ctr);                                           \
-  } else {                                                                                    \
-    score_bound<KK><<<sg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, L.splits, F.radius,      \
-                                        cand_s, cand_i);                                      \
-    merge_emit<KK><<<pb, 128, 0, st>>>(P, L.splits, cand_s, cand_i, prop, hist1, list1, ctr); \
-  }
+#define PSDF_PROPOSE(KK)                                                                       \
+  if (net)                                                                                     \
+    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,      \
+                                                   frag, b2, keys, pose4, prop, hist1, list1,  \
+                                                   uoff1, utile1, ctr);                        \
+  else                                                                                         \
+    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,     \
+                                                    frag, b2, keys, pose4, prop, hist1, list1, \
+                                                    uoff1, utile1, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -1069,34 +993,32 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
         default: PSDF_PROPOSE(4) break;
       }
 #undef PSDF_PROPOSE
-      tiles_scan<<<1, 1024, 0, st>>>(hist1, scene->d_tiles, T, uoff1);
     }
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
                                          (const int *)hist1, (const int *)uoff1,
-                                         (const int *)list1, keys, st);
+                                         (const int *)utile1, L.cap1, (const int *)list1, keys,
+                                         st);
       if (rc) return rc;
     }
     {
       ProfileScope prof("fallback", st);
-      const int fsplits = std::max(1, std::min(L.splits, (T + 63) / 64));
-      dim3 fg(pb, (unsigned)fsplits);
-      fb_pairs<<<fg, 128, 0, st>>>(pose4, P, scene->d_tiles, T, fsplits, F.radius, keys, prop,
-                                   hist2, list2, flags, ctr);
-      tiles_scan<<<1, 1024, 0, st>>>(hist2, scene->d_tiles, T, uoff2);
+      fallback<<<pb, kPoseThreads, 0, st>>>(pose4, P, scene->d_tiles, T, F.radius, keys, prop,
+                                            hist2, list2, uoff2, utile2, ctr);
     }
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
                                          (const int *)hist2, (const int *)uoff2,
-                                         (const int *)list2, keys, st);
+                                         (const int *)utile2, L.cap2, (const int *)list2, keys,
+                                         st);
       if (rc) return rc;
     }
   }
   rc = launch_epilogue(F, scene, poses, P, pk, keys, &ctr->err, phi, dphi, active, st);
   if (rc) return rc;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch");
 }
 

@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
 template <int M>
 __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float *__restrict__ poses, long long P,
-                                const ObsRec *__restrict__ obs, const float4 *__restrict__ vtx,
-                                const int *__restrict__ far, const int *__restrict__ row2obs,
+                                const ObsRec *__restrict__ row_obs,
+                                const float4 *__restrict__ vtx, const int *__restrict__ far,
                                 const unsigned long long *__restrict__ keys,
                                 const int *__restrict__ err, float *__restrict__ phi,
                                 float *__restrict__ dphi, unsigned *__restrict__ active)
@@ -230,8 +230,7 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
   float s, c;
   sincosf(poses[3 * p + 2], &s, &c);
   const int rank = (int)(unsigned)(key & 0xffffffffu);
-  const int sidx = row2obs[rank];
-  const ObsRec o = obs[sidx];
+  const ObsRec o = row_obs[rank];
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
   const Active a = obstacle_detail<M>(F, px, py, c, s, vt, o.n, o.orig_first, prm.eps_sat);
   phi[p] = a.separated ? sqrtf(a.val) : a.val;
@@ -320,9 +319,9 @@ __device__ float active_t(const FootprintK &F, float px, float py, float c, floa
 
 template <int M>
 __global__ void backward_kernel(FootprintK F, float eps_axis, const float *__restrict__ poses,
-                                long long P, const ObsRec *__restrict__ obs,
+                                long long P, const ObsRec *__restrict__ row_obs,
                                 const float4 *__restrict__ vtx, const int *__restrict__ far,
-                                const int *__restrict__ row2obs, long long rows_total,
+                                long long rows_total,
                                 const unsigned *__restrict__ active,
                                 const float *__restrict__ grad_phi, float *__restrict__ grad_pose,
                                 float *__restrict__ grad_edges)
@@ -334,14 +333,13 @@ __global__ void backward_kernel(FootprintK F, float eps_axis, const float *__res
   const long long row = pid >> kPairShiftEdge;
   const int kind = (pid >> kPairShiftKind) & 0xF;
   const int l = pid & 0xF;
-  int sidx = -1;
+  ObsRec o{0, 0, 0, -1};
   if (pid != PSDF_PAIR_NONE && row < rows_total && l < F.m && kind <= kOAxisRMax)
-    sidx = row2obs[row];
-  if (sidx < 0) {
+    o = row_obs[row];
+  if (o.n == 0) {
     if (grad_pose) grad_pose[3 * p] = grad_pose[3 * p + 1] = grad_pose[3 * p + 2] = 0.f;
     return;
   }
-  const ObsRec o = obs[sidx];
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
   int k = (int)(row - o.orig_first);
   if (kind == kObsBRobotEdge || kind == kRAxisOMaxB || kind == kRAxisRMaxB) k = 0;
@@ -506,8 +504,8 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   }
   {
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<(int)((P + 63) / 64), 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
-                                                    sc->d_vtx, sc->d_far, sc->d_row2obs, keys,
+    epilogue_kernel<M><<<(int)((P + 63) / 64), 64, 0, st>>>(F, pk, sc->eps_axis, poses, P,
+                                                    sc->d_row_obs, sc->d_vtx, sc->d_far, keys,
                                                     err, phi, dphi, active);
   }
   cudaError_t e = cudaGetLastError();
@@ -522,8 +520,8 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
 {
   const int blocks = (int)((P + 63) / 64);
   ProfileScope prof("backward", st);
-  backward_kernel<M><<<blocks, 64, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_obs, sc->d_vtx,
-                                             sc->d_far, sc->d_row2obs, sc->rows_total, active,
+  backward_kernel<M><<<blocks, 64, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_row_obs,
+                                             sc->d_vtx, sc->d_far, sc->rows_total, active,
                                              grad_phi, grad_pose, grad_edges);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -571,8 +569,8 @@ struct EpilogueCall {
   {
     const int blocks = (int)((P + 63) / 64);
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_obs,
-                                               sc->d_vtx, sc->d_far, sc->d_row2obs, keys, err,
+    epilogue_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+                                               sc->d_vtx, sc->d_far, keys, err,
                                                phi, dphi, active);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

@@ -65,8 +65,10 @@ struct TileHdr {
   float aabb[4];   // xmin, ymin, xmax, ymax of the tile's endpoints
 };
 
-// Obstacle record in sorted (tile) order, for the per-pose epilogue and the
-// backward: vertex records live at vtx[2 * (vtx_global + k)].
+// Obstacle record of a caller row (one per row, so that the per-pose
+// epilogue and the backward reach it from a row index in one load): vertex
+// records live at vtx[2 * (vtx_global + k)]; n = 0 marks a row outside every
+// obstacle.
 struct ObsRec {
   int vtx_global;  // first vertex record (sorted order)
   int n;           // edges (1 = segment)
@@ -86,10 +88,9 @@ struct psdf_scene {
   // device arrays
   psdf::TileHdr *d_tiles = nullptr;
   unsigned char *d_blob = nullptr;
-  psdf::ObsRec *d_obs = nullptr;   // [M] sorted
-  float4 *d_vtx = nullptr;         // [2 * n_edges] sorted vertex records
-  int *d_far = nullptr;            // [n_edges] far vertex index within its obstacle
-  int *d_row2obs = nullptr;        // [rows_total] caller row -> sorted obstacle (-1: none)
+  psdf::ObsRec *d_row_obs = nullptr;  // [rows_total] obstacle record of each caller row
+  float4 *d_vtx = nullptr;            // [2 * n_edges] sorted vertex records
+  int *d_far = nullptr;               // [n_edges] far vertex index within its obstacle
   size_t device_bytes = 0;
   // host copies used for launch configuration
   int max_blob_bytes = 0;

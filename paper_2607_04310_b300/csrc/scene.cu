@@ -95,10 +95,9 @@ void free_scene(psdf_scene *s)
   if (!s) return;
   cudaFree(s->d_tiles);
   cudaFree(s->d_blob);
-  cudaFree(s->d_obs);
   cudaFree(s->d_vtx);
   cudaFree(s->d_far);
-  cudaFree(s->d_row2obs);
+  cudaFree(s->d_row_obs);
   delete s;
 }
 
@@ -208,10 +207,9 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   tile_first.push_back(M);
 
   std::vector<TileHdr> tiles(T);
-  std::vector<ObsRec> orec(M);
   std::vector<float4> vtx(2 * (size_t)n_edges);
   std::vector<int> far(n_edges);
-  std::vector<int> row2obs(std::max<int64_t>(rows_total, 0), -1);
+  std::vector<ObsRec> row_obs(std::max<int64_t>(rows_total, 0), ObsRec{0, 0, 0, -1});
   std::vector<unsigned char> blob;
   int64_t vglob = 0;
   int max_blob = 0;
@@ -235,8 +233,8 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
       const ObsIn &o = obs[order[s]];
       const float *e = rows + 4 * o.first_row;
       ob[s - s0] = make_int4(vloc, o.n, (int)o.first_row, s);
-      orec[s] = ObsRec{(int)vglob, o.n, (int)o.first_row, t};
-      for (int k = 0; k < o.n; ++k) row2obs[o.first_row + k] = s;
+      for (int k = 0; k < o.n; ++k)
+        row_obs[o.first_row + k] = ObsRec{(int)vglob, o.n, (int)o.first_row, t};
       // obstacle vertex set: A of every edge, plus B for a segment
       const int nw = (o.n == 1) ? 2 : o.n;
       for (int k = 0; k < o.n; ++k) {
@@ -292,10 +290,9 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   int rc = PSDF_OK;
   if (!rc) rc = dev_upload(&s->d_tiles, tiles, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_blob, blob, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_obs, orec, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_vtx, vtx, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_far, far, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_row2obs, row2obs, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_row_obs, row_obs, st, &s->device_bytes);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "scene upload");
