@@ -297,57 +297,87 @@ __device__ __forceinline__ int tile_units(int cnt, int n_obs)
 // Run by one whole CTA of kPoseThreads threads once every append to hist is
 // done: exclusive prefix sum of the tiles' units -> uoff[t] (uoff[T] = total),
 // the unit -> tile map utile[u], and the number of listed pairs -> *items.
-// hist was written by atomics of other CTAs: read through L2.
+// Chunks of kPoseThreads x 8 tiles, each thread a run of 8 (its loads issued
+// together).  hist was written by atomics of other CTAs: read through L2.
 __device__ void build_units(const int *hist, const TileHdr *__restrict__ tiles, int T,
                             int *__restrict__ uoff, int *__restrict__ utile, int *items)
 {
-  __shared__ int w_units[kPoseThreads / 32], w_items[kPoseThreads / 32];
+  constexpr int kRun = 8, kWarps = kPoseThreads / 32;
+  __shared__ int w_units[kWarps], w_items[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (T + kPoseThreads - 1) / kPoseThreads;
-  const int b0 = min(T, tid * per), b1 = min(T, b0 + per);
-  int su = 0, si = 0;
-  for (int i = b0; i < b1; ++i) {
-    const int c = __ldcg(hist + i);
-    su += tile_units(c, tiles[i].n_obs);
-    si += c;
-  }
-  int incl = su, isum = si;
+  int carry = 0, items_total = 0;
+  for (int c0 = 0; c0 < T; c0 += kPoseThreads * kRun) {
+    const int b0 = c0 + tid * kRun;
+    int cnt[kRun], nob[kRun];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
-    isum += __shfl_xor_sync(0xffffffffu, isum, o);
-  }
-  if (lane == 31) w_units[warp] = incl;
-  if (lane == 0) w_items[warp] = isum;
-  __syncthreads();
-  int ubase = incl - su, total_items = 0;
+    for (int i = 0; i < kRun; ++i) {
+      cnt[i] = (b0 + i < T) ? __ldcg(hist + b0 + i) : 0;
+      nob[i] = (b0 + i < T) ? tiles[b0 + i].n_obs : 1;
+    }
+    int su = 0, si = 0;
 #pragma unroll
-  for (int w = 0; w < kPoseThreads / 32; ++w) {
-    if (w < warp) ubase += w_units[w];
-    total_items += w_items[w];
+    for (int i = 0; i < kRun; ++i) {
+      su += tile_units(cnt[i], nob[i]);
+      si += cnt[i];
+    }
+    int incl = su, isum = si;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += n;
+      isum += __shfl_xor_sync(0xffffffffu, isum, o);
+    }
+    if (lane == 31) w_units[warp] = incl;
+    if (lane == 0) w_items[warp] = isum;
+    __syncthreads();
+    int ubase = carry + incl - su;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      if (w < warp) ubase += w_units[w];
+      carry += w_units[w];
+      items_total += w_items[w];
+    }
+#pragma unroll
+    for (int i = 0; i < kRun; ++i) {
+      if (b0 + i < T) {
+        const int nu = tile_units(cnt[i], nob[i]);
+        uoff[b0 + i] = ubase;
+        for (int k = 0; k < nu; ++k) utile[ubase + k] = b0 + i;
+        ubase += nu;
+      }
+    }
+    __syncthreads();  // w_units / w_items are reused by the next chunk
   }
-  for (int i = b0; i < b1; ++i) {
-    const int nu = tile_units(__ldcg(hist + i), tiles[i].n_obs);
-    uoff[i] = ubase;
-    for (int k = 0; k < nu; ++k) utile[ubase + k] = i;
-    ubase += nu;
+  if (tid == 0) {
+    uoff[T] = carry;
+    *items = items_total;
   }
-  if (tid == kPoseThreads - 1) uoff[T] = ubase;
-  if (tid == 0) *items = total_items;
 }
 
-// True in every thread of the CTA that finished last (all other CTAs'
-// appends are then visible); the counter is cleared before the launch.
+// True in every thread of the CTA that finished last; the counter is
+// cleared before the launch.  Thread 0's device-scope fence after the
+// barrier orders the whole CTA's earlier writes before its ticket; the last
+// CTA's fence after reading the final ticket orders its later reads.
 __device__ __forceinline__ bool last_cta(unsigned *done)
 {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (last) __threadfence();
   return last;
+}
+
+// Tile AABBs [t0, t0 + n) -> shared memory (independent loads, one latency).
+constexpr int kStageTiles = 2048;
+__device__ __forceinline__ void stage_aabbs(const TileHdr *__restrict__ tiles, int t0, int n,
+                                            float4 *ab_s)
+{
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    ab_s[i] = __ldg(reinterpret_cast<const float4 *>(tiles + t0 + i) + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -395,35 +425,46 @@ __global__ void __launch_bounds__(kPoseThreads)
   constexpr int R = NET ? kPre : K;
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
+  __shared__ float4 ab_s[kStageTiles];
+  __shared__ float ef_s[NET ? kStageTiles : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
-  if (pw < P) {  // uniform over the warp
-    const int half = lane >> 4, hl = lane & 15;
-    const long long p = pw + half;
-    const bool valid = p < P;
-    float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
-    if (valid) {
-      px = poses[3 * p];
-      py = poses[3 * p + 1];
-      sincosf(poses[3 * p + 2], &s, &c);
-      if (hl == 0) {
-        keys[p] = ~0ull;
-        pose4[p] = make_float4(px, py, c, s);
-      }
+  const int half = lane >> 4, hl = lane & 15;
+  const long long p = pw + half;
+  const bool valid = p < P;
+  float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
+  if (valid) {
+    px = poses[3 * p];
+    py = poses[3 * p + 1];
+    sincosf(poses[3 * p + 2], &s, &c);
+    if (hl == 0) {
+      keys[p] = ~0ull;
+      pose4[p] = make_float4(px, py, c, s);
     }
-    float sc[R];
-    int id[R];
+  }
+  float sc[R];
+  int id[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-      sc[i] = kInf;
-      id[i] = -1;
-    }
+  for (int i = 0; i < R; ++i) {
+    sc[i] = kInf;
+    id[i] = -1;
+  }
+  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
+    const int n = min(kStageTiles, T - t0);
+    __syncthreads();
+    stage_aabbs(tiles, t0, n, ab_s);
+    if constexpr (NET)
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        ef_s[i] = (float)tiles[t0 + i].n_vtx * (1.f / 256.f);
+    __syncthreads();
     if (valid)
-      for (int t = hl; t < T; t += 16) {
-        const float4 a4 = tile_aabb(tiles, t);
+      for (int i = hl; i < n; i += 16) {
+        const float4 a4 = ab_s[i];
         const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        topk_insert<R>(sc, id, tile_lb(ab, px, py, rfoot), t);
+        topk_insert<R>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
       }
+  }
+  if (pw < P) {  // uniform over the warp
     // R rounds of a 16-lane argmin with pop
     int cand[R];
 #pragma unroll
@@ -464,15 +505,18 @@ __global__ void __launch_bounds__(kPoseThreads)
       const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
       float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
       float efa = 0.f, efb = 0.f;
+      // the candidates' AABBs and edge fractions: from shared memory when
+      // every tile was staged at once
+      const bool staged = T <= kStageTiles;
       if (ta >= 0) {
-        const float4 a4 = tile_aabb(tiles, ta);
+        const float4 a4 = staged ? ab_s[ta] : tile_aabb(tiles, ta);
         aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
-        efa = (float)tiles[ta].n_vtx * (1.f / 256.f);
+        efa = staged ? ef_s[ta] : (float)tiles[ta].n_vtx * (1.f / 256.f);
       }
       if (tb >= 0) {
-        const float4 a4 = tile_aabb(tiles, tb);
+        const float4 a4 = staged ? ab_s[tb] : tile_aabb(tiles, tb);
         abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
-        efb = (float)tiles[tb].n_vtx * (1.f / 256.f);
+        efb = staged ? ef_s[tb] : (float)tiles[tb].n_vtx * (1.f / 256.f);
       }
       // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
       const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
@@ -600,34 +644,44 @@ __global__ void __launch_bounds__(kPoseThreads)
              int *__restrict__ uoff, int *__restrict__ utile, CullCounters *ctr)
 {
   __shared__ int n_poses;
+  __shared__ float4 ab_s[kStageTiles];
   if (threadIdx.x == 0) n_poses = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
-  if (pw < P) {  // uniform over the warp
-    const int hl = lane & 15;
-    const long long p = pw + (lane >> 4);
-    int n = 0;
-    if (p < P) {
-      const float4 q4 = pose4[p];
-      const unsigned long long key = keys[p];
-      const float best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
-      int pr[kMaxK];
+  const int hl = lane & 15;
+  const long long p = pw + (lane >> 4);
+  const bool valid = p < P;
+  float4 q4 = make_float4(0.f, 0.f, 1.f, 0.f);
+  float best = kInf;
+  int pr[kMaxK];
 #pragma unroll
-      for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
-      for (int t = hl; t < T; t += 16) {
-        const float4 a4 = tile_aabb(tiles, t);
+  for (int i = 0; i < kMaxK; ++i) pr[i] = -1;
+  if (valid) {
+    q4 = pose4[p];
+    const unsigned long long key = keys[p];
+    best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
+  }
+  int n = 0;
+  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
+    const int nt = min(kStageTiles, T - t0);
+    __syncthreads();
+    stage_aabbs(tiles, t0, nt, ab_s);
+    __syncthreads();
+    if (valid)
+      for (int i = hl; i < nt; i += 16) {
+        const float4 a4 = ab_s[i];
         const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        if (fb_need(ab, q4.x, q4.y, rfoot, best, t, pr)) {
-          list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
+        if (fb_need(ab, q4.x, q4.y, rfoot, best, t0 + i, pr)) {
+          list[(long long)(t0 + i) * P + atomicAdd(&hist[t0 + i], 1)] = (int)p;
           ++n;
         }
       }
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if (hl == 0 && n > 0) atomicAdd(&n_poses, 1);
   }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if (valid && hl == 0 && n > 0) atomicAdd(&n_poses, 1);
   __syncthreads();
   if (threadIdx.x == 0 && n_poses) atomicAdd(&ctr->fallback_poses, n_poses);
   if (last_cta(&ctr->done2)) build_units(hist, tiles, T, uoff, utile, &ctr->n_fb);
