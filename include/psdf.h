@@ -296,6 +296,97 @@ int psdf_trainer_get(const psdf_trainer *trainer, float *params, float *m, float
 int psdf_trainer_set(psdf_trainer *trainer, const float *params, const float *m, const float *v,
                      int64_t step);
 
+/* ---- batched plan: many instances in one persistent launch ---------------
+ * Batching of MPC instances, SQP iterates and rollouts (Sec. IV-B, the
+ * horizon stacked into one tensor, and Sec. V: per-stage edge sets E_{k+s}):
+ * an INSTANCE is one footprint, one obstacle edge set of its own and a run of
+ * poses.  Instances may differ in footprint size (3..16), edge count and
+ * number of poses.  psdf_plan_create prepares every instance's scene once
+ * (as psdf_scene_create_csr does) and lays all of them out in one device
+ * image; psdf_eval_batched then evaluates every pose of every instance
+ * against its own instance's edges (value, active pair, gradient -- the same
+ * results psdf_eval_grad gives per instance, bit for bit) in ONE persistent
+ * kernel launch: CTAs take work items (instance, block of its poses, run of
+ * its edge tiles) from an atomic queue, largest first, and the CTA that
+ * finishes the last item of a pose block runs that block's epilogue.
+ *
+ * Layout (all HOST pointers, copied at creation):
+ *   footprints  float[sum m_i][2], instance i's footprint at vertex
+ *               fp_offsets[i] .. fp_offsets[i+1]-1 (CCW, 3..16 vertices)
+ *   edges       float[R][4] edge rows of all instances (Ax, Ay, Bx, By)
+ *   obs_offsets int32[n_obs+1], CSR over the rows: obstacle q has rows
+ *               obs_offsets[q] .. obs_offsets[q+1]-1 (1 edge = segment, >= 3
+ *               = closed CCW convex polygon, as for psdf_scene_create_csr)
+ *   inst_obs    int32[n_inst+1]: instance i owns obstacles inst_obs[i] ..
+ *               inst_obs[i+1]-1, i.e. rows obs_offsets[inst_obs[i]] ..
+ *               obs_offsets[inst_obs[i+1]]-1 (may be none)
+ *   pose_offsets int64[n_inst+1]: instance i owns poses pose_offsets[i] ..
+ *               pose_offsets[i+1]-1 of the pose array given to each call
+ *   tile_edges  edges per tile (0 = 256; PSDF_TILE_MORTON selects Morton
+ *               packing), as for scenes.
+ * Active pair ids use the row index WITHIN the instance (row minus the
+ * instance's first row).  eta must be 0 (hard minimum).
+ *
+ * The plan owns its device memory (scene image, work queue, per-pose keys).
+ * psdf_eval_batched allocates nothing and never synchronizes: it issues two
+ * memsets and one kernel on `stream`, so it can be captured in a CUDA graph.
+ * Calls on one plan whose kernels overlap on the GPU race on its workspace
+ * and must be serialized by the caller.
+ *
+ * Tile shapes: `threads` (CTA size 128 or 256; a pose block holds at most
+ * `threads` poses, whose lanes split the tile's obstacles when fewer poses
+ * than lanes are given) and `tiles_per_item` (edge tiles per work item,
+ * 1..64).  psdf_plan_autotune times a grid of candidates on the caller's
+ * poses (it synchronizes and allocates scratch: never call it during
+ * capture), keeps the fastest, and caches the choice per plan shape (the
+ * instances' pose, tile and footprint sizes on the current device) for the
+ * life of the process; *from_cache (optional) reports a cache hit. */
+typedef struct psdf_plan psdf_plan;
+
+typedef struct {
+  int32_t threads;
+  int32_t tiles_per_item;
+} psdf_plan_config;
+
+typedef struct {
+  int32_t n_inst;
+  int32_t n_tiles;     /* edge tiles over all instances */
+  int64_t n_poses;
+  int64_t n_rows;      /* edge rows over all instances */
+  int32_t n_items;     /* work items of the current configuration */
+  int32_t n_blocks;    /* pose blocks of the current configuration */
+  int32_t grid;        /* persistent CTAs launched */
+  int32_t reserved;
+  psdf_plan_config config;
+  size_t device_bytes;
+} psdf_plan_info;
+
+int psdf_plan_create(int32_t n_inst, const float *footprints, const int32_t *fp_offsets,
+                     const float *edges, const int32_t *obs_offsets, const int32_t *inst_obs,
+                     const int64_t *pose_offsets, int32_t tile_edges, const psdf_params *params,
+                     void *stream, psdf_plan **out);
+int psdf_plan_destroy(psdf_plan *plan);
+int psdf_plan_get_info(const psdf_plan *plan, psdf_plan_info *info);
+/* Rebuilds the work queue for `config` (synchronizes the stream). */
+int psdf_plan_set_config(psdf_plan *plan, const psdf_plan_config *config, void *stream);
+int psdf_plan_autotune(psdf_plan *plan, const float *poses, int32_t reps, void *stream,
+                       psdf_plan_config *chosen, int32_t *from_cache);
+/* phi float[n_poses]; dphi float[n_poses][3] or NULL; active uint32[n_poses]
+ * or NULL.  A bounded device wait that ran out turns the outputs of the pose
+ * blocks finished after it into NaN; psdf_plan_status then reports
+ * PSDF_ERR_TIMEOUT. */
+int psdf_eval_batched(psdf_plan *plan, const float *poses, float *phi, float *dphi,
+                      uint32_t *active, void *stream);
+/* Synchronizes the stream and reports whether the last psdf_eval_batched
+ * met a timed-out wait. */
+int psdf_plan_status(const psdf_plan *plan, void *stream);
+/* Vector-Jacobian product through each pose's active pair, as psdf_backward
+ * per instance: grad_pose float[n_poses][3] (written, or NULL), grad_edges
+ * float[R][4] over all instances' rows (accumulated with atomics, or NULL). */
+int psdf_backward_batched(const psdf_plan *plan, const float *poses, const uint32_t *active,
+                          const float *grad_phi, float *grad_pose, float *grad_edges,
+                          void *stream);
+
 /* ---- value + gradient without any device allocation ---------------------
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory while they run -- a control loop with a hard period (an

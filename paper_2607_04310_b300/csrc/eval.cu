@@ -19,6 +19,7 @@
 #include "profile.h"
 #include "psdf_device.cuh"
 #include "psdf_internal.h"
+#include "tma.cuh"
 
 namespace psdf {
 
@@ -41,72 +42,7 @@ int cuda_fail(cudaError_t e, const char *what)
   return PSDF_ERR_CUDA;
 }
 
-// ---------------------------------------------------------------------------
-// TMA bulk copy + mbarrier helpers (inline PTX)
-// ---------------------------------------------------------------------------
 constexpr int kScanThreads = 128;
-constexpr unsigned kWaitLimit = 1u << 22;  // try_wait polls before giving up
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
-{
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// global -> shared bulk copy completing on an mbarrier; dst/src 16-byte
-// aligned and bytes a multiple of 16 (guaranteed by the tile layout)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         uint64_t *bar)
-{
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
-{
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false if the phase did not complete within kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
-{
-  for (unsigned it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -212,109 +148,20 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const unsigned long long key = keys[p];
+  PoseOut r;
   if (*err) {
-    const float nan = __int_as_float(0x7fc00000);
-    phi[p] = nan;
-    if (active) active[p] = PSDF_PAIR_NONE;
-    if (dphi) dphi[3 * p] = dphi[3 * p + 1] = dphi[3 * p + 2] = nan;
-    return;
+    r = pose_out_failed();
+  } else {
+    r = epilogue_pose<M>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
+                         poses[3 * p + 2], keys[p], row_obs, vtx, far, dphi != nullptr);
   }
-  if (key == ~0ull) {  // no obstacle at all
-    phi[p] = kInf;
-    if (active) active[p] = PSDF_PAIR_NONE;
-    if (dphi) dphi[3 * p] = dphi[3 * p + 1] = dphi[3 * p + 2] = 0.f;
-    return;
-  }
-  const float px = poses[3 * p], py = poses[3 * p + 1];
-  float s, c;
-  sincosf(poses[3 * p + 2], &s, &c);
-  const int rank = (int)(unsigned)(key & 0xffffffffu);
-  const ObsRec o = row_obs[rank];
-  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
-  const Active a = obstacle_detail<M>(F, px, py, c, s, vt, o.n, o.orig_first, prm.eps_sat);
-  phi[p] = a.separated ? sqrtf(a.val) : a.val;
-  if (active) active[p] = a.pid;
+  phi[p] = r.phi;
+  if (active) active[p] = r.pid;
   if (dphi) {
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (a.separated || a.dlt > 0.f) {
-      const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n,
-                                    o.orig_first, a.kind, a.l, a.k, a.t, eps_axis);
-      g0 = g.gp[0];
-      g1 = g.gp[1];
-      g2 = g.gp[2];
-    }
-    dphi[3 * p] = g0;
-    dphi[3 * p + 1] = g1;
-    dphi[3 * p + 2] = g2;
+    dphi[3 * p] = r.g[0];
+    dphi[3 * p + 1] = r.g[1];
+    dphi[3 * p + 2] = r.g[2];
   }
-}
-
-// Overlap of a penetration-kind active pair (to find the flat branch of
-// max(delta, 0)); same arithmetic as the scan.
-template <int M>
-__device__ float active_overlap(const FootprintK &F, float px, float py, float c, float s,
-                                const float4 *vt, int n, int kind, int l, int k)
-{
-  const bool seg = (n == 1);
-  if (kind >= kRAxisOMax && kind <= kRAxisRMaxB) {
-    const bool isB = (kind == kRAxisOMaxB || kind == kRAxisRMaxB);
-    const float4 a = vt[2 * k], b = vt[1];
-    const V2 X = isB ? to_local(b.z, b.w, px, py, c, s) : to_local(a.x, a.y, px, py, c, s);
-    float nx = 0.f, ny = 0.f, lo = 0.f, hi = 0.f;
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-      if (q == l) { nx = F.nx[q]; ny = F.ny[q]; lo = F.alo[q]; hi = F.ahi[q]; }
-    const float pr = __fmaf_rn(X.x, nx, __fmul_rn(X.y, ny));
-    return (kind == kRAxisOMax || kind == kRAxisOMaxB) ? __fsub_rn(pr, lo) : __fsub_rn(hi, pr);
-  }
-  const float4 ak = vt[2 * k], bk = vt[2 * k + 1];
-  const V2 A = to_local(ak.x, ak.y, px, py, c, s);
-  V2 B;
-  if (seg) B = to_local(bk.z, bk.w, px, py, c, s);
-  else {
-    const float4 an = vt[2 * ((k + 1) % n)];
-    B = to_local(an.x, an.y, px, py, c, s);
-  }
-  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
-  float smin = kInf, smax = -kInf;
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    const float wx = __fsub_rn(F.vx[q], A.x), wy = __fsub_rn(F.vy[q], A.y);
-    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
-    smin = fminf(smin, sl);
-    smax = fmaxf(smax, sl);
-  }
-  return (kind == kOAxisOMax) ? __fmaf_rn(-smin, ak.w, bk.y) : __fmaf_rn(smax, ak.w, -bk.x);
-}
-
-// Recomputes the projection parameter of a distance-kind active pair.
-template <int M>
-__device__ float active_t(const FootprintK &F, float px, float py, float c, float s,
-                          const float4 *vt, int n, int kind, int l, int k)
-{
-  float vx = 0.f, vy = 0.f, ex = 0.f, ey = 0.f, ie = 0.f;
-#pragma unroll
-  for (int q = 0; q < M; ++q)
-    if (q == l) { vx = F.vx[q]; vy = F.vy[q]; ex = F.ex[q]; ey = F.ey[q]; ie = F.inv_e2[q]; }
-  const bool seg = (n == 1);
-  if (kind == kVertEdge) {
-    const float4 ak = vt[2 * k];
-    const V2 A = to_local(ak.x, ak.y, px, py, c, s);
-    V2 B;
-    if (seg) B = to_local(vt[1].z, vt[1].w, px, py, c, s);
-    else {
-      const float4 an = vt[2 * ((k + 1) % n)];
-      B = to_local(an.x, an.y, px, py, c, s);
-    }
-    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
-    const float wx = __fsub_rn(vx, A.x), wy = __fsub_rn(vy, A.y);
-    return __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak.z));
-  }
-  const V2 X = (kind == kObsVRobotEdge) ? to_local(vt[2 * k].x, vt[2 * k].y, px, py, c, s)
-                                        : to_local(vt[1].z, vt[1].w, px, py, c, s);
-  const float wx = __fsub_rn(vx, X.x), wy = __fsub_rn(vy, X.y);
-  return __fmul_rn(-__fmaf_rn(wx, ex, __fmul_rn(wy, ey)), ie);
 }
 
 template <int M>
@@ -328,43 +175,17 @@ __global__ void backward_kernel(FootprintK F, float eps_axis, const float *__res
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const unsigned pid = active[p];
   const float gphi = grad_phi[p];
-  const long long row = pid >> kPairShiftEdge;
-  const int kind = (pid >> kPairShiftKind) & 0xF;
-  const int l = pid & 0xF;
-  ObsRec o{0, 0, 0, -1};
-  if (pid != PSDF_PAIR_NONE && row < rows_total && l < F.m && kind <= kOAxisRMax)
-    o = row_obs[row];
-  if (o.n == 0) {
-    if (grad_pose) grad_pose[3 * p] = grad_pose[3 * p + 1] = grad_pose[3 * p + 2] = 0.f;
-    return;
-  }
-  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
-  int k = (int)(row - o.orig_first);
-  if (kind == kObsBRobotEdge || kind == kRAxisOMaxB || kind == kRAxisRMaxB) k = 0;
-  const float px = poses[3 * p], py = poses[3 * p + 1];
-  float s, c;
-  sincosf(poses[3 * p + 2], &s, &c);
-  float t = 0.f;
-  bool flat = false;
-  if (kind <= kObsBRobotEdge) {
-    t = active_t<M>(F, px, py, c, s, vt, o.n, kind, l, k);
-  } else {
-    flat = !(active_overlap<M>(F, px, py, c, s, vt, o.n, kind, l, k) > 0.f);
-  }
-  if (flat) {
-    if (grad_pose) grad_pose[3 * p] = grad_pose[3 * p + 1] = grad_pose[3 * p + 2] = 0.f;
-    return;
-  }
-  const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first,
-                                kind, l, k, t, eps_axis);
+  Grad g;
+  const bool has = backward_pose<M>(F, eps_axis, poses[3 * p], poses[3 * p + 1],
+                                    poses[3 * p + 2], active[p], row_obs, rows_total, vtx, far,
+                                    g);
   if (grad_pose) {
-    grad_pose[3 * p] = gphi * g.gp[0];
-    grad_pose[3 * p + 1] = gphi * g.gp[1];
-    grad_pose[3 * p + 2] = gphi * g.gp[2];
+    grad_pose[3 * p] = has ? gphi * g.gp[0] : 0.f;
+    grad_pose[3 * p + 1] = has ? gphi * g.gp[1] : 0.f;
+    grad_pose[3 * p + 2] = has ? gphi * g.gp[2] : 0.f;
   }
-  if (grad_edges) {
+  if (has && grad_edges) {
     for (int i = 0; i < g.nrow; ++i) {
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]], gphi * g.gx[i]);
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1], gphi * g.gy[i]);

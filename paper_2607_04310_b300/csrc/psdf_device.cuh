@@ -76,14 +76,74 @@ __device__ __forceinline__ float synth_value(float d2min, float dmin_axes, float
 }
 
 // ---------------------------------------------------------------------------
+// footprint access
+// ---------------------------------------------------------------------------
+// The constants one edge step reads for robot vertex l.
+struct RobotL {
+  float vx, vy, ex, ey, inv_e2, nx, ny;
+};
+
+// A footprint passed by value as a kernel parameter: the loads below become
+// constant-bank operands of the arithmetic.
+__device__ __forceinline__ RobotL robot_l(const FootprintK &F, int l)
+{
+  return RobotL{F.vx[l], F.vy[l], F.ex[l], F.ey[l], F.inv_e2[l], F.nx[l], F.ny[l]};
+}
+
+__device__ __forceinline__ float2 robot_interval(const FootprintK &F, int l)
+{
+  return make_float2(F.alo[l], F.ahi[l]);
+}
+
+// A footprint staged in shared memory as records (one per robot vertex:
+// {vx, vy, ex, ey}, {inv_e2, nx, ny, 0}; intervals {alo, ahi}), for kernels
+// whose CTAs change footprint from one work item to the next.  The loads are
+// volatile, so they are re-issued at every use (two 16-byte broadcasts per
+// robot vertex and edge) instead of the compiler holding all constants of a
+// large footprint in registers across the obstacle loop.
+struct FootprintS {
+  const float4 *rec;  // [2 * m]
+  const float2 *ivl;  // [m]
+};
+
+__device__ __forceinline__ float4 lds_f4(const float4 *p)
+{
+  float4 r;
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return r;
+}
+
+__device__ __forceinline__ float2 lds_f2(const float2 *p)
+{
+  float2 r;
+  asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];"
+               : "=f"(r.x), "=f"(r.y)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return r;
+}
+
+__device__ __forceinline__ RobotL robot_l(const FootprintS &F, int l)
+{
+  const float4 a = lds_f4(F.rec + 2 * l), b = lds_f4(F.rec + 2 * l + 1);
+  return RobotL{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+}
+
+__device__ __forceinline__ float2 robot_interval(const FootprintS &F, int l)
+{
+  return lds_f2(F.ivl + l);
+}
+
+// ---------------------------------------------------------------------------
 // value-only evaluation of one obstacle (the scan's inner loop)
 // ---------------------------------------------------------------------------
 // One edge of a closed polygon, from A (= vertex k, local) to B (= vertex
 // k+1, local).  Accumulates: d2min (squared separation, Sec. IV-B), the
 // obstacle's projections on the robot axes (pmax/pmin, Sec. IV-C) and the
 // overlap on this edge's own axis.
-template <int M, bool SEG>
-__device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float inv_len2,
+template <int M, bool SEG, class FP>
+__device__ __forceinline__ void edge_step(const FP &F, V2 A, V2 B, float inv_len2,
                                           float inv_len, float alpha_p, float beta_p,
                                           float (&pmax)[M], float (&pmin)[M], float &d2min,
                                           float &dlt)
@@ -92,14 +152,15 @@ __device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float
   float smin = kInf, smax = -kInf;
 #pragma unroll
   for (int l = 0; l < M; ++l) {
+    const RobotL r = robot_l(F, l);
     // robot vertex l -> obstacle edge: t = clamp((v - A).u / (|u|^2 + eps))
-    const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
+    const float wx = __fsub_rn(r.vx, A.x), wy = __fsub_rn(r.vy, A.y);
     const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), inv_len2));
     float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
     if (SEG) {
       // a segment's far endpoint is its own vertex: use it exactly
-      rx = (t == 1.0f) ? __fsub_rn(F.vx[l], B.x) : rx;
-      ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
+      rx = (t == 1.0f) ? __fsub_rn(r.vx, B.x) : rx;
+      ry = (t == 1.0f) ? __fsub_rn(r.vy, B.y) : ry;
     }
     const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
     // robot vertex projected on rot90(u), measured from A (obstacle axis)
@@ -107,13 +168,12 @@ __device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float
     smin = fminf(smin, sl);
     smax = fmaxf(smax, sl);
     // obstacle vertex A -> robot edge l, t' = clamp((A - v).e / (|e|^2 + eps))
-    const float tp =
-        __saturatef(__fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]));
-    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const float tp = __saturatef(__fmul_rn(-__fmaf_rn(wx, r.ex, __fmul_rn(wy, r.ey)), r.inv_e2));
+    const float qx = __fmaf_rn(tp, r.ex, wx), qy = __fmaf_rn(tp, r.ey, wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
     d2min = fminf(d2min, fminf(d2, d2p));
     // obstacle vertex A on the robot axis n_l
-    const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
+    const float pr = __fmaf_rn(A.x, r.nx, __fmul_rn(A.y, r.ny));
     pmax[l] = fmaxf(pmax[l], pr);
     pmin[l] = fminf(pmin[l], pr);
   }
@@ -126,40 +186,41 @@ __device__ __forceinline__ void edge_step(const FootprintK &F, V2 A, V2 B, float
 
 // A segment's B endpoint as an extra obstacle vertex: robot-edge distances
 // and robot-axis projections.
-template <int M>
-__device__ __forceinline__ void extra_vertex(const FootprintK &F, V2 X, float (&pmax)[M],
+template <int M, class FP>
+__device__ __forceinline__ void extra_vertex(const FP &F, V2 X, float (&pmax)[M],
                                              float (&pmin)[M], float &d2min)
 {
 #pragma unroll
   for (int l = 0; l < M; ++l) {
-    const float wx = __fsub_rn(F.vx[l], X.x), wy = __fsub_rn(F.vy[l], X.y);
-    const float tp =
-        __saturatef(__fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]));
-    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const RobotL r = robot_l(F, l);
+    const float wx = __fsub_rn(r.vx, X.x), wy = __fsub_rn(r.vy, X.y);
+    const float tp = __saturatef(__fmul_rn(-__fmaf_rn(wx, r.ex, __fmul_rn(wy, r.ey)), r.inv_e2));
+    const float qx = __fmaf_rn(tp, r.ex, wx), qy = __fmaf_rn(tp, r.ey, wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
     d2min = fminf(d2min, d2p);
-    const float pr = __fmaf_rn(X.x, F.nx[l], __fmul_rn(X.y, F.ny[l]));
+    const float pr = __fmaf_rn(X.x, r.nx, __fmul_rn(X.y, r.ny));
     pmax[l] = fmaxf(pmax[l], pr);
     pmin[l] = fminf(pmin[l], pr);
   }
 }
 
-template <int M>
-__device__ __forceinline__ float robot_axes_min(const FootprintK &F, const float (&pmax)[M],
+template <int M, class FP>
+__device__ __forceinline__ float robot_axes_min(const FP &F, const float (&pmax)[M],
                                                 const float (&pmin)[M], float dlt)
 {
 #pragma unroll
   for (int l = 0; l < M; ++l) {
-    const float da = __fsub_rn(pmax[l], F.alo[l]);
-    const float db = __fsub_rn(F.ahi[l], pmin[l]);
+    const float2 iv = robot_interval(F, l);
+    const float da = __fsub_rn(pmax[l], iv.x);
+    const float db = __fsub_rn(iv.y, pmin[l]);
     dlt = fminf(dlt, fminf(da, db));
   }
   return dlt;
 }
 
 // Value of one obstacle whose vertex records start at vt (2 float4 per vertex).
-template <int M>
-__device__ __forceinline__ float obstacle_value(const FootprintK &F, float px, float py,
+template <int M, class FP>
+__device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
                                                 float c, float s, const float4 *vt, int n,
                                                 float eps_sat)
 {
@@ -356,8 +417,8 @@ __device__ __forceinline__ void add_row(Grad &g, int row, int col, float gx, flo
 {
   for (int i = 0; i < g.nrow; ++i)
     if (g.row[i] == row && g.col[i] == col) {
-      g.gx[i] += gx;
-      g.gy[i] += gy;
+      g.gx[i] = __fadd_rn(g.gx[i], gx);
+      g.gy[i] = __fadd_rn(g.gy[i], gy);
       return;
     }
   g.row[g.nrow] = row;
@@ -398,28 +459,39 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
   for (int q = 0; q < M; ++q)
     if (q == l) { lvx = vx[q]; lvy = vy[q]; lex = F.ex[q]; ley = F.ey[q]; lnx = F.nx[q]; lny = F.ny[q]; }
 
+  // every operation rounded explicitly (no contraction), so the gradient has
+  // the same bits in every kernel that inlines this function
+  const auto mul = [](float x, float y) { return __fmul_rn(x, y); };
+  const auto add = [](float x, float y) { return __fadd_rn(x, y); };
+  const auto sub = [](float x, float y) { return __fsub_rn(x, y); };
+  const auto unit = [&](float rx, float ry, float &hx, float &hy) {
+    const float d = __fsqrt_rn(__fmaf_rn(rx, rx, mul(ry, ry)));
+    hx = d > 0.f ? __fdiv_rn(rx, d) : 0.f;
+    hy = d > 0.f ? __fdiv_rn(ry, d) : 0.f;
+  };
   if (kind == kVertEdge) {
     const V2 Aw = worldA(k), Bw = worldB(k);
     const V2 A = to_local(Aw.x, Aw.y, px, py, c, s), B = to_local(Bw.x, Bw.y, px, py, c, s);
-    const float ux = B.x - A.x, uy = B.y - A.y;
+    const float ux = sub(B.x, A.x), uy = sub(B.y, A.y);
     float rx, ry;
-    if (t == 1.0f) { rx = lvx - B.x; ry = lvy - B.y; }
-    else { rx = (lvx - A.x) - t * ux; ry = (lvy - A.y) - t * uy; }
-    const float d = sqrtf(rx * rx + ry * ry);
-    const float hx = d > 0.f ? rx / d : 0.f, hy = d > 0.f ? ry / d : 0.f;
-    const float wx = c * hx - s * hy, wy = s * hx + c * hy;  // R r^
-    g.gp[0] = wx; g.gp[1] = wy; g.gp[2] = -hx * lvy + hy * lvx;  // r^ . (J v)
-    add_row(g, orig_first + k, 0, -(1.f - t) * wx, -(1.f - t) * wy);
-    add_row(g, rowB(k), colB, -t * wx, -t * wy);
+    if (t == 1.0f) { rx = sub(lvx, B.x); ry = sub(lvy, B.y); }
+    else { rx = sub(sub(lvx, A.x), mul(t, ux)); ry = sub(sub(lvy, A.y), mul(t, uy)); }
+    float hx, hy;
+    unit(rx, ry, hx, hy);
+    const float wx = sub(mul(c, hx), mul(s, hy)), wy = add(mul(s, hx), mul(c, hy));  // R r^
+    g.gp[0] = wx; g.gp[1] = wy; g.gp[2] = sub(mul(hy, lvx), mul(hx, lvy));  // r^ . (J v)
+    const float omt = sub(1.f, t);
+    add_row(g, orig_first + k, 0, -mul(omt, wx), -mul(omt, wy));
+    add_row(g, rowB(k), colB, -mul(t, wx), -mul(t, wy));
   } else if (kind == kObsVRobotEdge || kind == kObsBRobotEdge) {
     const V2 Xw = (kind == kObsVRobotEdge) ? worldA(k) : worldB(0);
     const V2 X = to_local(Xw.x, Xw.y, px, py, c, s);
-    const float qx = lvx + t * lex, qy = lvy + t * ley;
-    const float rx = X.x - qx, ry = X.y - qy;
-    const float d = sqrtf(rx * rx + ry * ry);
-    const float hx = d > 0.f ? rx / d : 0.f, hy = d > 0.f ? ry / d : 0.f;
-    const float wx = c * hx - s * hy, wy = s * hx + c * hy;
-    g.gp[0] = -wx; g.gp[1] = -wy; g.gp[2] = -(-hx * qy + hy * qx);  // -r^ . (J q)
+    const float qx = __fmaf_rn(t, lex, lvx), qy = __fmaf_rn(t, ley, lvy);
+    const float rx = sub(X.x, qx), ry = sub(X.y, qy);
+    float hx, hy;
+    unit(rx, ry, hx, hy);
+    const float wx = sub(mul(c, hx), mul(s, hy)), wy = add(mul(s, hx), mul(c, hy));
+    g.gp[0] = -wx; g.gp[1] = -wy; g.gp[2] = -sub(mul(hy, qx), mul(hx, qy));  // -r^ . (J q)
     if (kind == kObsVRobotEdge) add_row(g, orig_first + k, 0, wx, wy);
     else add_row(g, orig_first, 2, wx, wy);
   } else if (kind >= kRAxisOMax && kind <= kRAxisRMaxB) {
@@ -427,39 +499,185 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
     const bool isB = (kind == kRAxisOMaxB || kind == kRAxisRMaxB);
     const V2 Xw = isB ? worldB(0) : worldA(k);
     const V2 X = to_local(Xw.x, Xw.y, px, py, c, s);
-    const float sg = sideA ? 1.f : -1.f;
-    const float Rnx = c * lnx - s * lny, Rny = s * lnx + c * lny;
-    const float Jnx = -lny, Jny = lnx;
-    g.gp[0] = sg * Rnx; g.gp[1] = sg * Rny; g.gp[2] = -sg * (X.x * Jnx + X.y * Jny);
-    if (isB) add_row(g, orig_first, 2, -sg * Rnx, -sg * Rny);
-    else add_row(g, orig_first + k, 0, -sg * Rnx, -sg * Rny);
+    const float Rnx = sub(mul(c, lnx), mul(s, lny)), Rny = add(mul(s, lnx), mul(c, lny));
+    const float XJn = sub(mul(X.y, lnx), mul(X.x, lny));  // X . (J n), J n = (-ny, nx)
+    const float gx = sideA ? Rnx : -Rnx, gy = sideA ? Rny : -Rny;
+    g.gp[0] = gx; g.gp[1] = gy; g.gp[2] = sideA ? -XJn : XJn;
+    if (isB) add_row(g, orig_first, 2, -gx, -gy);
+    else add_row(g, orig_first + k, 0, -gx, -gy);
   } else if (kind == kOAxisOMax || kind == kOAxisRMax) {
     const bool sideA = (kind == kOAxisOMax);
     const V2 Aw = worldA(k), Bw = worldB(k);
-    const float ux = Bw.x - Aw.x, uy = Bw.y - Aw.y;
-    const float len = sqrtf(ux * ux + uy * uy);
-    const float gd = 1.f / (len + eps_axis);
-    const float npx = -uy * gd, npy = ux * gd;           // n' (world)
-    const float ntx = c * npx + s * npy, nty = -s * npx + c * npy;  // R^T n'
-    const float Rvx = c * lvx - s * lvy, Rvy = s * lvx + c * lvy;
-    const float Jvx = -lvy, Jvy = lvx;
-    const int xk = sideA ? (seg ? 0 : far[k]) : k;        // vertex receiving d/dX
+    const float ux = sub(Bw.x, Aw.x), uy = sub(Bw.y, Aw.y);
+    const float len = __fsqrt_rn(__fmaf_rn(ux, ux, mul(uy, uy)));
+    const float gd = __fdiv_rn(1.f, add(len, eps_axis));
+    const float npx = mul(-uy, gd), npy = mul(ux, gd);                          // n' (world)
+    const float ntx = add(mul(c, npx), mul(s, npy)), nty = sub(mul(c, npy), mul(s, npx));  // R^T n'
+    const float Rvx = sub(mul(c, lvx), mul(s, lvy)), Rvy = add(mul(s, lvx), mul(c, lvy));
+    const int xk = sideA ? (seg ? 0 : far[k]) : k;  // vertex receiving d/dX
     const V2 Xw = worldA(xk);
-    const float sgn = sideA ? 1.f : -1.f;                 // delta = sgn <X - p - R v*, n'>
-    const float Dx = sgn * (Xw.x - px - Rvx), Dy = sgn * (Xw.y - py - Rvy);
-    // sd = -delta
-    g.gp[0] = sgn * npx; g.gp[1] = sgn * npy; g.gp[2] = sgn * (Jvx * ntx + Jvy * nty);
-    add_row(g, orig_first + xk, 0, -sgn * npx, -sgn * npy);
-    const float uhx = ux / len, uhy = uy / len;
-    const float JtDx = Dy, JtDy = -Dx;
-    const float JuD = -uy * Dx + ux * Dy;
-    const float gpr = -gd * gd;
-    const float dux = gd * JtDx + gpr * uhx * JuD, duy = gd * JtDy + gpr * uhy * JuD;
-    // d delta / dA = -du, d delta / dB = du; sd = -delta
+    // delta = sgn <X - p - R v*, n'>, sd = -delta
+    const float Ex = sub(sub(Xw.x, px), Rvx), Ey = sub(sub(Xw.y, py), Rvy);
+    const float Dx = sideA ? Ex : -Ex, Dy = sideA ? Ey : -Ey;
+    const float JvNt = sub(mul(lvx, nty), mul(lvy, ntx));  // (J v*) . R^T n'
+    g.gp[0] = sideA ? npx : -npx; g.gp[1] = sideA ? npy : -npy; g.gp[2] = sideA ? JvNt : -JvNt;
+    add_row(g, orig_first + xk, 0, -g.gp[0], -g.gp[1]);
+    const float uhx = __fdiv_rn(ux, len), uhy = __fdiv_rn(uy, len);
+    const float JuD = sub(mul(ux, Dy), mul(uy, Dx));
+    const float gpr = -mul(gd, gd);
+    // d delta / dA = -du, d delta / dB = du with du = gd J^T D + gpr u^ (J u . D)
+    const float dux = add(mul(gd, Dy), mul(mul(gpr, uhx), JuD));
+    const float duy = add(mul(gd, -Dx), mul(mul(gpr, uhy), JuD));
     add_row(g, orig_first + k, 0, dux, duy);
     add_row(g, rowB(k), colB, -dux, -duy);
   }
   return g;
+}
+
+// Overlap of a penetration-kind active pair (to find the flat branch of
+// max(delta, 0)); same arithmetic as the scan.
+template <int M>
+__device__ __forceinline__ float active_overlap(const FootprintK &F, float px, float py, float c, float s,
+                                const float4 *vt, int n, int kind, int l, int k)
+{
+  const bool seg = (n == 1);
+  if (kind >= kRAxisOMax && kind <= kRAxisRMaxB) {
+    const bool isB = (kind == kRAxisOMaxB || kind == kRAxisRMaxB);
+    const float4 a = vt[2 * k], b = vt[1];
+    const V2 X = isB ? to_local(b.z, b.w, px, py, c, s) : to_local(a.x, a.y, px, py, c, s);
+    float nx = 0.f, ny = 0.f, lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+      if (q == l) { nx = F.nx[q]; ny = F.ny[q]; lo = F.alo[q]; hi = F.ahi[q]; }
+    const float pr = __fmaf_rn(X.x, nx, __fmul_rn(X.y, ny));
+    return (kind == kRAxisOMax || kind == kRAxisOMaxB) ? __fsub_rn(pr, lo) : __fsub_rn(hi, pr);
+  }
+  const float4 ak = vt[2 * k], bk = vt[2 * k + 1];
+  const V2 A = to_local(ak.x, ak.y, px, py, c, s);
+  V2 B;
+  if (seg) B = to_local(bk.z, bk.w, px, py, c, s);
+  else {
+    const float4 an = vt[2 * ((k + 1) % n)];
+    B = to_local(an.x, an.y, px, py, c, s);
+  }
+  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+  float smin = kInf, smax = -kInf;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const float wx = __fsub_rn(F.vx[q], A.x), wy = __fsub_rn(F.vy[q], A.y);
+    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+    smin = fminf(smin, sl);
+    smax = fmaxf(smax, sl);
+  }
+  return (kind == kOAxisOMax) ? __fmaf_rn(-smin, ak.w, bk.y) : __fmaf_rn(smax, ak.w, -bk.x);
+}
+
+// Recomputes the projection parameter of a distance-kind active pair.
+template <int M>
+__device__ __forceinline__ float active_t(const FootprintK &F, float px, float py, float c, float s,
+                          const float4 *vt, int n, int kind, int l, int k)
+{
+  float vx = 0.f, vy = 0.f, ex = 0.f, ey = 0.f, ie = 0.f;
+#pragma unroll
+  for (int q = 0; q < M; ++q)
+    if (q == l) { vx = F.vx[q]; vy = F.vy[q]; ex = F.ex[q]; ey = F.ey[q]; ie = F.inv_e2[q]; }
+  const bool seg = (n == 1);
+  if (kind == kVertEdge) {
+    const float4 ak = vt[2 * k];
+    const V2 A = to_local(ak.x, ak.y, px, py, c, s);
+    V2 B;
+    if (seg) B = to_local(vt[1].z, vt[1].w, px, py, c, s);
+    else {
+      const float4 an = vt[2 * ((k + 1) % n)];
+      B = to_local(an.x, an.y, px, py, c, s);
+    }
+    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const float wx = __fsub_rn(vx, A.x), wy = __fsub_rn(vy, A.y);
+    return __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak.z));
+  }
+  const V2 X = (kind == kObsVRobotEdge) ? to_local(vt[2 * k].x, vt[2 * k].y, px, py, c, s)
+                                        : to_local(vt[1].z, vt[1].w, px, py, c, s);
+  const float wx = __fsub_rn(vx, X.x), wy = __fsub_rn(vy, X.y);
+  return __fmul_rn(-__fmaf_rn(wx, ex, __fmul_rn(wy, ey)), ie);
+}
+
+// Result of the per-pose epilogue.
+struct PoseOut {
+  float phi;
+  float g[3];  // d phi / d (x, y, theta)
+  unsigned pid;
+};
+
+__device__ __forceinline__ PoseOut pose_out_failed()
+{
+  const float nan = __int_as_float(0x7fc00000);
+  return PoseOut{nan, {nan, nan, nan}, PSDF_PAIR_NONE};
+}
+
+// Value, active pair and (if want_grad) pose gradient of one pose from its
+// 64-bit min-key: the winning obstacle is re-evaluated with its exact
+// candidate sets and the closed-form gradient of the active pair is taken
+// (Alg. 1, value + gradient).  row_obs is indexed by the key's rank (a caller
+// row of the pose's scene).
+template <int M>
+__device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_sat,
+                                                 float eps_axis, float px, float py, float theta,
+                                                 unsigned long long key,
+                                                 const ObsRec *__restrict__ row_obs,
+                                                 const float4 *__restrict__ vtx,
+                                                 const int *__restrict__ far, bool want_grad)
+{
+  PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
+  if (key == ~0ull) return r;  // no obstacle at all
+  float s, c;
+  sincosf(theta, &s, &c);
+  const int rank = (int)(unsigned)(key & 0xffffffffu);
+  const ObsRec o = row_obs[rank];
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  const Active a = obstacle_detail<M>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat);
+  r.phi = a.separated ? sqrtf(a.val) : a.val;
+  r.pid = a.pid;
+  if (want_grad && (a.separated || a.dlt > 0.f)) {
+    const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first,
+                                  a.kind, a.l, a.k, a.t, eps_axis);
+    r.g[0] = g.gp[0];
+    r.g[1] = g.gp[1];
+    r.g[2] = g.gp[2];
+  }
+  return r;
+}
+
+// Closed-form gradient of one pose's active pair (pid) w.r.t. the pose and
+// the stored edge endpoints (rows of the pose's scene).  False when the pair
+// is none, out of range, or on the flat branch of max(delta, 0).
+template <int M>
+__device__ __forceinline__ bool backward_pose(const FootprintK &F, float eps_axis, float px,
+                                              float py, float theta, unsigned pid,
+                                              const ObsRec *__restrict__ row_obs,
+                                              long long rows_total,
+                                              const float4 *__restrict__ vtx,
+                                              const int *__restrict__ far, Grad &g)
+{
+  const long long row = pid >> kPairShiftEdge;
+  const int kind = (pid >> kPairShiftKind) & 0xF;
+  const int l = pid & 0xF;
+  if (pid == PSDF_PAIR_NONE || row >= rows_total || l >= F.m || kind > kOAxisRMax) return false;
+  const ObsRec o = row_obs[row];
+  if (o.n == 0) return false;
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  int k = (int)(row - o.orig_first);
+  if (kind == kObsBRobotEdge || kind == kRAxisOMaxB || kind == kRAxisRMaxB) k = 0;
+  float s, c;
+  sincosf(theta, &s, &c);
+  float t = 0.f;
+  if (kind <= kObsBRobotEdge) {
+    t = active_t<M>(F, px, py, c, s, vt, o.n, kind, l, k);
+  } else if (!(active_overlap<M>(F, px, py, c, s, vt, o.n, kind, l, k) > 0.f)) {
+    return false;
+  }
+  g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first, kind, l, k, t,
+                     eps_axis);
+  return true;
 }
 
 }  // namespace psdf

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/psdf.h"
 
@@ -97,6 +99,46 @@ struct psdf_scene {
 };
 
 namespace psdf {
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// one obstacle of the caller's layout
+struct ObsIn {
+  int64_t first_row;  // caller's row of the first edge
+  int n;              // edges
+};
+
+// Host image of a prepared scene (scene.cu), before upload: a scene of its
+// own (psdf_scene) or one instance of a batched plan.
+struct HostScene {
+  int64_t rows_total = 0, n_edges = 0;
+  int M = 0, T = 0, tile_edges = 0, max_n = 0, max_blob = 0;
+  float bb[4] = {0, 0, 0, 0};
+  double eps_seg = 0, eps_axis = 0;
+  std::vector<TileHdr> tiles;
+  std::vector<unsigned char> blob;
+  std::vector<float4> vtx;
+  std::vector<int> far;
+  std::vector<ObsRec> row_obs;
+};
+int build_host_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
+                     int tile_edges, const psdf_params *prm, HostScene *hs);
+
+template <class T>
+int dev_upload(T **dst, const std::vector<T> &src, cudaStream_t st, size_t *bytes)
+{
+  size_t nb = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void **)dst, nb);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  *bytes += nb;
+  if (!src.empty()) {
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(host -> device)");
+  }
+  return PSDF_OK;
+}
+
 // shared host helpers (eval.cu)
 int device_sms();
 int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F);
@@ -110,7 +152,4 @@ int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *pose
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,
                 void *ws, size_t ws_bytes, void *stream);
-void set_error(const std::string &msg);
-int fail(int code, const std::string &msg);
-int cuda_fail(cudaError_t e, const char *what);
 }  // namespace psdf

@@ -25,11 +25,6 @@ uint32_t spread_bits(uint32_t x)
 
 uint32_t morton2(uint32_t x, uint32_t y) { return spread_bits(x) | (spread_bits(y) << 1); }
 
-struct ObsIn {
-  int64_t first_row;  // caller's row of the first edge
-  int n;              // edges
-};
-
 // Check one obstacle against Assumption 1 and the layout rules.
 int validate_obstacle(const float *rows, const ObsIn &o, int64_t idx)
 {
@@ -74,20 +69,6 @@ int validate_obstacle(const float *rows, const ObsIn &o, int64_t idx)
   return PSDF_OK;
 }
 
-template <class T>
-int dev_upload(T **dst, const std::vector<T> &src, cudaStream_t st, size_t *bytes)
-{
-  size_t nb = std::max<size_t>(src.size(), 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void **)dst, nb);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scene)");
-  *bytes += nb;
-  if (!src.empty()) {
-    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(scene)");
-  }
-  return PSDF_OK;
-}
-
 }  // namespace
 
 void free_scene(psdf_scene *s)
@@ -102,8 +83,8 @@ void free_scene(psdf_scene *s)
 }
 
 // rows: caller's edge rows [rows_total][4]; obstacles in caller order.
-int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
-                int tile_edges, const psdf_params *prm, cudaStream_t st, psdf_scene **out)
+int build_host_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
+                     int tile_edges, const psdf_params *prm, HostScene *hs)
 {
   const bool morton = (tile_edges & PSDF_TILE_MORTON) != 0;
   tile_edges &= ~PSDF_TILE_MORTON;
@@ -274,25 +255,48 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
     max_blob = std::max(max_blob, bytes);
   }
 
+  hs->rows_total = rows_total;
+  hs->M = M;
+  hs->T = T;
+  hs->tile_edges = tile_edges;
+  hs->max_n = max_n;
+  hs->n_edges = n_edges;
+  std::memcpy(hs->bb, bb, sizeof(bb));
+  if (M == 0) { hs->bb[0] = hs->bb[1] = hs->bb[2] = hs->bb[3] = 0.f; }
+  hs->eps_seg = eps_seg;
+  hs->eps_axis = eps_axis;
+  hs->max_blob = max_blob;
+  hs->tiles.swap(tiles);
+  hs->blob.swap(blob);
+  hs->vtx.swap(vtx);
+  hs->far.swap(far);
+  hs->row_obs.swap(row_obs);
+  return PSDF_OK;
+}
+
+int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
+                int tile_edges, const psdf_params *prm, cudaStream_t st, psdf_scene **out)
+{
+  HostScene hs;
+  int rc = build_host_scene(rows, rows_total, obs, tile_edges, prm, &hs);
+  if (rc) return rc;
   psdf_scene *s = new psdf_scene();
-  s->rows_total = rows_total;
-  s->M = M;
-  s->n_tiles = T;
-  s->tile_edges = tile_edges;
-  s->max_obs_edges = max_n;
-  s->n_edges = n_edges;
-  std::memcpy(s->bbox, bb, sizeof(bb));
-  if (M == 0) { s->bbox[0] = s->bbox[1] = s->bbox[2] = s->bbox[3] = 0.f; }
-  s->eps_seg = (float)eps_seg;
-  s->eps_axis = (float)eps_axis;
-  s->max_blob_bytes = max_blob;
+  s->rows_total = hs.rows_total;
+  s->M = hs.M;
+  s->n_tiles = hs.T;
+  s->tile_edges = hs.tile_edges;
+  s->max_obs_edges = hs.max_n;
+  s->n_edges = hs.n_edges;
+  std::memcpy(s->bbox, hs.bb, sizeof(hs.bb));
+  s->eps_seg = (float)hs.eps_seg;
+  s->eps_axis = (float)hs.eps_axis;
+  s->max_blob_bytes = hs.max_blob;
   cudaGetDevice(&s->device);
-  int rc = PSDF_OK;
-  if (!rc) rc = dev_upload(&s->d_tiles, tiles, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_blob, blob, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_vtx, vtx, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_far, far, st, &s->device_bytes);
-  if (!rc) rc = dev_upload(&s->d_row_obs, row_obs, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_tiles, hs.tiles, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_blob, hs.blob, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_vtx, hs.vtx, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_far, hs.far, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_row_obs, hs.row_obs, st, &s->device_bytes);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "scene upload");

@@ -52,6 +52,18 @@ class SceneInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class PlanConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("tiles_per_item", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_inst", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
+                ("n_poses", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("n_items", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("config", PlanConfig), ("device_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _SIGS = {
@@ -96,6 +108,17 @@ _SIGS = {
     "psdf_trainer_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
     "psdf_trainer_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "psdf_trainer_set": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64]),
+    "psdf_plan_create": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                        ctypes.c_int32, _vp, _vp, ctypes.POINTER(_vp)]),
+    "psdf_plan_destroy": (ctypes.c_int, [_vp]),
+    "psdf_plan_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    "psdf_plan_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(PlanConfig), _vp]),
+    "psdf_plan_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp,
+                                          ctypes.POINTER(PlanConfig),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "psdf_eval_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "psdf_plan_status": (ctypes.c_int, [_vp, _vp]),
+    "psdf_backward_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -400,3 +423,107 @@ def pair_ids(active) -> np.ndarray:
     """uint32 pair ids from the int32 tensor the helpers return."""
     a = active.detach().cpu().numpy() if hasattr(active, "detach") else np.asarray(active)
     return a.view(np.uint32) if a.dtype == np.int32 else a.astype(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# batched plan
+# --------------------------------------------------------------------------
+class Plan:
+    """Owns a psdf_plan: many instances (footprint, own edge set, run of poses)
+    evaluated by one persistent launch.  `instances` is a sequence of
+    (footprint [m][2], edges [E][4], offsets [M+1], n_poses)."""
+
+    def __init__(self, instances, tile_edges: int = 0, params: Optional[Params] = None,
+                 stream=None):
+        fps, fpo, edges, obs_off, inst_obs, pose_off = [], [0], [], [0], [0], [0]
+        row = 0
+        for fp, e, off, n in instances:
+            fp = np.asarray(fp, dtype=np.float32).reshape(-1, 2)
+            e = np.asarray(e, dtype=np.float32).reshape(-1, 4)
+            off = np.asarray(off, dtype=np.int64)
+            fps.append(fp)
+            fpo.append(fpo[-1] + fp.shape[0])
+            edges.append(e)
+            obs_off.extend((row + off[1:]).tolist())
+            inst_obs.append(inst_obs[-1] + len(off) - 1)
+            pose_off.append(pose_off[-1] + int(n))
+            row += e.shape[0]
+        self.footprints = np.ascontiguousarray(np.concatenate(fps) if fps else
+                                               np.zeros((0, 2), np.float32))
+        self.fp_offsets = np.asarray(fpo, dtype=np.int32)
+        self.edges = np.ascontiguousarray(np.concatenate(edges) if edges else
+                                          np.zeros((0, 4), np.float32))
+        self.obs_offsets = np.asarray(obs_off, dtype=np.int32)
+        self.inst_obs = np.asarray(inst_obs, dtype=np.int32)
+        self.pose_offsets = np.asarray(pose_off, dtype=np.int64)
+        self.row_offsets = np.concatenate([[0], np.cumsum([e.shape[0] for e in edges])]).astype(
+            np.int64) if edges else np.zeros(1, np.int64)
+        self.params = params or Params()
+        out = ctypes.c_void_p()
+        _check(load().psdf_plan_create(len(instances), _ptr(self.footprints),
+                                       _ptr(self.fp_offsets), _ptr(self.edges),
+                                       _ptr(self.obs_offsets), _ptr(self.inst_obs),
+                                       _ptr(self.pose_offsets), tile_edges,
+                                       ctypes.byref(self.params), _stream(stream),
+                                       ctypes.byref(out)))
+        self.handle = ctypes.c_void_p(out.value)
+
+    @property
+    def n_poses(self) -> int:
+        return int(self.pose_offsets[-1])
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(load().psdf_plan_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def close(self) -> None:
+        if self.handle and self.handle.value:
+            load().psdf_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psdf_plan_set_config(plan: Plan, threads: int, tiles_per_item: int, stream=None) -> None:
+    cfg = PlanConfig(threads, tiles_per_item)
+    _check(load().psdf_plan_set_config(plan.handle, ctypes.byref(cfg), _stream(stream)))
+
+
+def psdf_plan_autotune(plan: Plan, poses, reps: int = 3, stream=None) -> Tuple[PlanConfig, bool]:
+    cfg = PlanConfig()
+    hit = ctypes.c_int32(0)
+    _check(load().psdf_plan_autotune(plan.handle, _ptr(poses), reps, _stream(stream),
+                                     ctypes.byref(cfg), ctypes.byref(hit)))
+    return cfg, bool(hit.value)
+
+
+def psdf_eval_batched(plan: Plan, poses, phi, dphi=None, active=None, stream=None) -> None:
+    _check(load().psdf_eval_batched(plan.handle, _ptr(poses), _ptr(phi), _ptr(dphi),
+                                    _ptr(active), _stream(stream)))
+
+
+def psdf_plan_status(plan: Plan, stream=None) -> int:
+    return int(load().psdf_plan_status(plan.handle, _stream(stream)))
+
+
+def psdf_backward_batched(plan: Plan, poses, active, grad_phi, grad_pose=None, grad_edges=None,
+                          stream=None) -> None:
+    _check(load().psdf_backward_batched(plan.handle, _ptr(poses), _ptr(active), _ptr(grad_phi),
+                                        _ptr(grad_pose), _ptr(grad_edges), _stream(stream)))
+
+
+def eval_batched(plan: Plan, poses, stream=None):
+    """phi, dphi, active for every pose of the plan (allocates the outputs)."""
+    import torch
+    P = plan.n_poses
+    dev = poses.device
+    phi = torch.empty(P, device=dev)
+    dphi = torch.empty((P, 3), device=dev)
+    act = torch.empty(P, dtype=torch.int32, device=dev)
+    psdf_eval_batched(plan, poses, phi, dphi, act, stream)
+    return phi, dphi, act
