@@ -50,6 +50,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched uneven-instances measurement")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched uneven-instances measurement (profiling runs)")
     return ap.parse_args()
 
 
@@ -249,10 +253,106 @@ def _graph(step):
     return g.replay, g
 
 
+def _bench_batched(a, dev, flush, stream, peak):
+    """Batched uneven instances (1,024 instances, horizons 10..100, 16..65,536
+    edges, 4..12-vertex footprints): the plan's autotuned persistent launch as
+    one CUDA graph, against one psdf_eval_grad call per instance (also one
+    graph)."""
+    import torch
+    from paper_2607_04310_b300 import psdf, roofline
+    from paper_2607_04310_b300 import scenegen as sg
+    insts = sg.uneven_instances(2)
+    plan = psdf.Plan([(w.footprint, w.edges, w.offsets, w.poses.shape[0]) for w in insts])
+    poses = torch.as_tensor(np.concatenate([w.poses for w in insts]), device=dev).contiguous()
+    P = plan.n_poses
+    pairs = float(sum(w.poses.shape[0] * w.edges.shape[0] for w in insts))
+    flops = float(sum(w.poses.shape[0] * roofline.flops_per_pose(w.footprint.shape[0], w.offsets)
+                      for w in insts))
+    cfg, _ = psdf.psdf_plan_autotune(plan, poses, reps=3)
+    phi = torch.empty(P, device=dev)
+    dphi = torch.empty((P, 3), device=dev)
+    act = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def step_plan():
+        psdf.psdf_eval_batched(plan, poses, phi, dphi, act)
+
+    # per-kernel device time of the eager launch
+    for _ in range(3):
+        step_plan()
+    torch.cuda.synchronize()
+    psdf.psdf_profile_reset()
+    psdf.psdf_profile_enable(True)
+    for _ in range(a.steps):
+        flush.zero_()
+        step_plan()
+    torch.cuda.synchronize()
+    psdf.psdf_profile_enable(False)
+    n_k, k_ms = psdf.psdf_profile_read("batched")
+    n_e, e_ms = psdf.psdf_profile_read("batched_epilogue")
+    psdf.psdf_profile_reset()
+    replay, g = _graph(step_plan)
+    for _ in range(max(a.warmup, 3)):
+        replay()
+    ms = sum(_time_steps(replay, a.steps, flush, stream)) / a.steps
+    ref = (phi.clone(), dphi.clone(), act.clone())
+
+    # one psdf_eval_grad per instance
+    scenes = [psdf.Scene.from_csr(w.edges, w.offsets) for w in insts]
+    nmax = max(w.poses.shape[0] for w in insts)
+    ws = psdf.workspace(nmax, dev)
+    prm = psdf.make_params()
+    offs = np.concatenate([[0], np.cumsum([w.poses.shape[0] for w in insts])])
+
+    def step_each():
+        for i, w in enumerate(insts):
+            s0, s1 = int(offs[i]), int(offs[i + 1])
+            psdf.psdf_eval_grad(w.footprint, scenes[i], poses[s0:s1], prm, phi[s0:s1],
+                                dphi[s0:s1], act[s0:s1], ws)
+
+    replay_each, g_each = _graph(step_each)
+    for _ in range(3):
+        replay_each()
+    each_ms = sum(_time_steps(replay_each, a.steps, flush, stream)) / a.steps
+    same = bool(torch.equal(ref[0].view(torch.int32), phi.view(torch.int32)) and
+                torch.equal(ref[1].view(torch.int32), dphi.view(torch.int32)) and
+                torch.equal(ref[2], act))
+    kern_ms = k_ms / max(n_k, 1)
+    achieved = flops / (kern_ms / 1000.0) / 1e12
+    info = plan.info()
+    return {
+        "workload": "uneven instances: 1024 instances, horizons 10..100, 16..65536 edges "
+                    "(log-uniform, random-yaw rectangles), 4..12-vertex footprints",
+        "poses": int(P), "edges": int(plan.edges.shape[0]), "pair_evals": pairs,
+        "value": pairs / (ms / 1000.0), "unit": "pair-evals/s", "ms_per_step": ms,
+        "launch": "one CUDA graph: 2 memsets + persistent work-queue kernel + epilogue kernel",
+        "gpu_launches_per_step": 2,
+        "autotuned": {"threads": int(cfg.threads), "tiles_per_item": int(cfg.tiles_per_item),
+                      "items": int(info.n_items), "grid": int(info.grid)},
+        "per_instance_calls": {"ms_per_step": each_ms, "value": pairs / (each_ms / 1000.0),
+                               "launches": 3 * len(insts)},
+        "speedup_vs_per_instance_calls": each_ms / ms,
+        "bitwise_equal_to_per_instance_calls": same,
+        "kernels_ms_per_step": {"persistent": kern_ms, "epilogue": e_ms / max(n_e, 1)},
+        "roofline": {"bound": "alu", "kernel": "batched persistent kernel",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "flops_per_step": flops},
+    }
+
+
 def run_b300(a, rank, world, local):
     import torch
     from paper_2607_04310_b300 import psdf, roofline
     from paper_2607_04310_b300 import train_cull
+
+    if a.only_batched:
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        props = torch.cuda.get_device_properties(dev)
+        peak = roofline.fp32_peak_tflops(props.multi_processor_count,
+                                         float(_measured_peaks().get("sm_max_mhz", 2032.0)))
+        print(json.dumps(_bench_batched(a, dev, flush, torch.cuda.current_stream(dev), peak)))
+        return 0
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -433,6 +533,8 @@ def run_b300(a, rank, world, local):
         "gpu_launches": launches_per_step * a.steps,
         "clocks": clk.summary(),
     }
+    if not a.no_batched and world == 1:
+        line["batched_uneven"] = _bench_batched(a, dev, flush, stream, peak)
     if not a.no_cpu_baseline and world == 1:
         import oracle
         rate, n, dt = _oracle_rate(w, a.cpu_seconds)
