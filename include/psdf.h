@@ -74,9 +74,16 @@ typedef struct psdf_scene psdf_scene; /* opaque: owns the device copy of E  */
 
 /* Tolerances of Sec. IV-B / IV-C.  eps_seg: epsilon added to |v|^2 in the
  * projection factor u; eps_axis: epsilon added to |u| in the obstacle-axis
- * normal; eps_sat: the separating-axis tolerance.  eta <= 0 selects the hard
+ * normal; eps_sat: the separating-axis tolerance.  eta = 0 selects the hard
  * minimum of the overlaps (the exact penetration depth, Sec. IV-C); eta > 0
- * the log-sum-exp soft minimum of Eq. penetration_depth. */
+ * the log-sum-exp soft minimum of Eq. penetration_depth over all of an
+ * obstacle's axes (psdf_eval, psdf_eval_grad, psdf_backward and the
+ * no-allocation call; the cull, the tile helpers and batched plans take the
+ * hard minimum only and reject eta > 0).  With eta > 0 a non-separated
+ * obstacle's sd = -pen_soft (which is positive for shallow overlaps), its
+ * gradient is the softmax-weighted sum over its axes with delta > 0, and the
+ * active pair id still names the hard minimum's pair.  eta must be finite
+ * and >= 0 (PSDF_ERR_ARG otherwise). */
 typedef struct {
   float eps_seg;
   float eps_axis;

@@ -966,6 +966,8 @@ extern "C" int psdf_tile_values(const float *footprint, int32_t m, const psdf_sc
   if (rc) return rc;
   if (P == 0 || scene->n_tiles == 0) return PSDF_OK;
   if (scene->n_tiles > 65535) return fail(PSDF_ERR_CAPACITY, "more than 65535 tiles");
+  if (params->eta > 0.f)
+    return fail(PSDF_ERR_ARG, "tile values use the hard minimum only (eta must be 0)");
   ParamsK pk{params->eps_sat, params->eta};
   rc = dispatch_m_cull<TileValuesCall>(m, F, pk, poses, (long long)P, scene, values,
                                        (cudaStream_t)stream);
@@ -984,6 +986,8 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
                            (size_t)-1);
   if (rc) return rc;
   if (!opts) return fail(PSDF_ERR_ARG, "opts is NULL");
+  if (params->eta > 0.f)
+    return fail(PSDF_ERR_ARG, "the cull evaluates the hard minimum only (eta must be 0)");
   if (opts->k < 1 || opts->k > kMaxK) return fail(PSDF_ERR_ARG, "k must be in [1, 4]");
   if (opts->mode != PSDF_PROPOSE_BOUND && opts->mode != PSDF_PROPOSE_MLP)
     return fail(PSDF_ERR_ARG, "unknown proposal mode");

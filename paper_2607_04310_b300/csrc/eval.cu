@@ -55,7 +55,7 @@ __global__ void init_keys_kernel(unsigned long long *keys, long long P, int *err
 }
 
 // Full scan: each CTA = kScanThreads poses x tiles [t0, t1).
-template <int M>
+template <int M, bool SOFT = false>
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     FootprintK F, ParamsK prm, const float *__restrict__ poses, long long P,
     const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob, int n_tiles,
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     const float4 *vt = reinterpret_cast<const float4 *>(tb + 16 * h.n_obs);
     for (int o = 0; o < h.n_obs; ++o) {
       const int4 rec = ob[o];
-      const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
+      const float v = obstacle_value<M, FootprintK, SOFT>(F, px, py, c, s, vt + 2 * rec.x, rec.y,
+                                                          prm.eps_sat, prm.eta);
       const unsigned long long key = pack_key(v, rec.z);
       best = key < best ? key : best;
     }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
 }
 
 // Per-pose epilogue: value, active pair, optional pose gradient.
-template <int M>
+template <int M, bool SOFT = false>
 __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float *__restrict__ poses, long long P,
                                 const ObsRec *__restrict__ row_obs,
@@ -152,8 +153,9 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
   if (*err) {
     r = pose_out_failed();
   } else {
-    r = epilogue_pose<M>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
-                         poses[3 * p + 2], keys[p], row_obs, vtx, far, dphi != nullptr);
+    r = epilogue_pose<M, SOFT>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
+                               poses[3 * p + 2], keys[p], row_obs, vtx, far, dphi != nullptr,
+                               prm.eta);
   }
   phi[p] = r.phi;
   if (active) active[p] = r.pid;
@@ -164,9 +166,10 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
   }
 }
 
-template <int M>
-__global__ void backward_kernel(FootprintK F, float eps_axis, const float *__restrict__ poses,
-                                long long P, const ObsRec *__restrict__ row_obs,
+template <int M, bool SOFT = false>
+__global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
+                                const float *__restrict__ poses, long long P,
+                                const ObsRec *__restrict__ row_obs,
                                 const float4 *__restrict__ vtx, const int *__restrict__ far,
                                 long long rows_total,
                                 const unsigned *__restrict__ active,
@@ -176,9 +179,50 @@ __global__ void backward_kernel(FootprintK F, float eps_axis, const float *__res
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const float gphi = grad_phi[p];
+  const float px = poses[3 * p], py = poses[3 * p + 1], th = poses[3 * p + 2];
+  const unsigned pid = active[p];
+  if (SOFT) {
+    // a penetration pair names a non-separated obstacle: its gradient is the
+    // softmax-weighted sum over the obstacle's axes
+    const long long row = pid >> kPairShiftEdge;
+    const int kind = (pid >> kPairShiftKind) & 0xF;
+    if (pid != PSDF_PAIR_NONE && row < rows_total && kind >= kRAxisOMax && kind <= kOAxisRMax) {
+      const ObsRec o = row_obs[row];
+      if (o.n > 0) {
+        float s, c;
+        sincosf(th, &s, &c);
+        const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+        const Active a = obstacle_detail<M, true>(F, px, py, c, s, vt, o.n, o.orig_first,
+                                                  prm.eps_sat, prm.eta);
+        if (!a.separated) {
+          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+          soft_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first, eps_axis,
+                       prm.eta, a.pen, [&](float w, const Grad &g) {
+                         g0 = __fmaf_rn(w, g.gp[0], g0);
+                         g1 = __fmaf_rn(w, g.gp[1], g1);
+                         g2 = __fmaf_rn(w, g.gp[2], g2);
+                         if (grad_edges) {
+                           const float sc = gphi * w;
+                           for (int i = 0; i < g.nrow; ++i) {
+                             atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]],
+                                       sc * g.gx[i]);
+                             atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1],
+                                       sc * g.gy[i]);
+                           }
+                         }
+                       });
+          if (grad_pose) {
+            grad_pose[3 * p] = gphi * g0;
+            grad_pose[3 * p + 1] = gphi * g1;
+            grad_pose[3 * p + 2] = gphi * g2;
+          }
+          return;
+        }
+      }
+    }
+  }
   Grad g;
-  const bool has = backward_pose<M>(F, eps_axis, poses[3 * p], poses[3 * p + 1],
-                                    poses[3 * p + 2], active[p], row_obs, rows_total, vtx, far,
+  const bool has = backward_pose<M>(F, eps_axis, px, py, th, pid, row_obs, rows_total, vtx, far,
                                     g);
   if (grad_pose) {
     grad_pose[3 * p] = has ? gphi * g.gp[0] : 0.f;
@@ -280,7 +324,8 @@ int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
     return fail(PSDF_ERR_ARG,
                 "params eps_seg/eps_axis differ from the values the scene was prepared with");
   if (!(params->eps_sat >= 0.f)) return fail(PSDF_ERR_ARG, "eps_sat must be >= 0");
-  if (params->eta > 0.f) return fail(PSDF_ERR_ARG, "soft-min penetration (eta > 0) is not available in this build");
+  if (!(params->eta >= 0.f) || !std::isfinite(params->eta))
+    return fail(PSDF_ERR_ARG, "eta must be finite and >= 0 (0 = hard minimum)");
   if (P > 0) {
     if (!workspace) return fail(PSDF_ERR_ARG, "workspace is NULL");
     if (((uintptr_t)workspace & 255u) != 0) return fail(PSDF_ERR_ARG, "workspace must be 256-byte aligned");
@@ -320,14 +365,23 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     const size_t smem = 128 + 2 * (size_t)blob_cap;
     dim3 grid((unsigned)pose_blocks, (unsigned)chunks);
     ProfileScope prof("scan", st);
-    scan_kernel<M><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, sc->d_tiles, sc->d_blob,
-                                                     sc->n_tiles, (int)tpc, blob_cap, keys, err);
+    if (pk.eta > 0.f)
+      scan_kernel<M, true><<<grid, kScanThreads, smem, st>>>(
+          F, pk, poses, P, sc->d_tiles, sc->d_blob, sc->n_tiles, (int)tpc, blob_cap, keys, err);
+    else
+      scan_kernel<M><<<grid, kScanThreads, smem, st>>>(
+          F, pk, poses, P, sc->d_tiles, sc->d_blob, sc->n_tiles, (int)tpc, blob_cap, keys, err);
   }
   {
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<(int)((P + 63) / 64), 64, 0, st>>>(F, pk, sc->eps_axis, poses, P,
-                                                    sc->d_row_obs, sc->d_vtx, sc->d_far, keys,
-                                                    err, phi, dphi, active);
+    const int eb = (int)((P + 63) / 64);
+    if (pk.eta > 0.f)
+      epilogue_kernel<M, true><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+                                                   sc->d_vtx, sc->d_far, keys, err, phi, dphi,
+                                                   active);
+    else
+      epilogue_kernel<M><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+                                             sc->d_vtx, sc->d_far, keys, err, phi, dphi, active);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -336,14 +390,21 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
 
 template <int M>
 static int launch_backward(const FootprintK &F, const psdf_scene *sc, const float *poses,
-                           long long P, const unsigned *active, const float *grad_phi,
-                           float *grad_pose, float *grad_edges, cudaStream_t st)
+                           long long P, const ParamsK &pk, const unsigned *active,
+                           const float *grad_phi, float *grad_pose, float *grad_edges,
+                           cudaStream_t st)
 {
   const int blocks = (int)((P + 63) / 64);
   ProfileScope prof("backward", st);
-  backward_kernel<M><<<blocks, 64, 0, st>>>(F, sc->eps_axis, poses, P, sc->d_row_obs,
-                                             sc->d_vtx, sc->d_far, sc->rows_total, active,
-                                             grad_phi, grad_pose, grad_edges);
+  if (pk.eta > 0.f)
+    backward_kernel<M, true><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P,
+                                                     sc->d_row_obs, sc->d_vtx, sc->d_far,
+                                                     sc->rows_total, active, grad_phi,
+                                                     grad_pose, grad_edges);
+  else
+    backward_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+                                               sc->d_vtx, sc->d_far, sc->rows_total, active,
+                                               grad_phi, grad_pose, grad_edges);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return PSDF_OK;
@@ -402,10 +463,10 @@ struct EpilogueCall {
 template <int M>
 struct BackwardCall {
   static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
-                 const unsigned *active, const float *grad_phi, float *grad_pose,
-                 float *grad_edges, cudaStream_t st)
+                 const ParamsK &pk, const unsigned *active, const float *grad_phi,
+                 float *grad_pose, float *grad_edges, cudaStream_t st)
   {
-    return launch_backward<M>(F, sc, poses, P, active, grad_phi, grad_pose, grad_edges, st);
+    return launch_backward<M>(F, sc, poses, P, pk, active, grad_phi, grad_pose, grad_edges, st);
   }
 };
 
@@ -465,8 +526,9 @@ extern "C" int psdf_backward(const float *footprint, int32_t m, const psdf_scene
   rc = make_footprint(footprint, m, scene->eps_seg, &F);
   if (rc) return rc;
   if (P == 0) return PSDF_OK;
-  return dispatch_m<BackwardCall>(m, F, scene, poses, (long long)P, active, grad_phi, grad_pose,
-                                  grad_edges, (cudaStream_t)stream);
+  const ParamsK pk{params->eps_sat, params->eta};
+  return dispatch_m<BackwardCall>(m, F, scene, poses, (long long)P, pk, active, grad_phi,
+                                  grad_pose, grad_edges, (cudaStream_t)stream);
 }
 
 extern "C" const char *psdf_last_error(void) { return g_err.c_str(); }

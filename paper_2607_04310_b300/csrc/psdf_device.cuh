@@ -75,6 +75,38 @@ __device__ __forceinline__ float synth_value(float d2min, float dmin_axes, float
   return separated ? d2min : -fmaxf(dmin_axes, 0.0f);
 }
 
+// Soft minimum of Eq. penetration_depth over an obstacle's axes,
+// pen = -(1/eta) log sum_n exp(-eta delta_+(n)), accumulated one axis at a
+// time around the running minimum mu of delta_+ (every term <= 1):
+// S = sum exp(-eta (delta_+ - mu)), pen = mu - log(S) / eta.  Explicit
+// rounding, so the scan and the epilogue reach the same bits when they add
+// the axes in the same order.
+struct SoftAcc {
+  float mu = kInf, S = 0.f;
+  __device__ __forceinline__ void add(float delta, float eta)
+  {
+    const float x = fmaxf(delta, 0.f);
+    if (x < mu) {
+      S = __fmaf_rn(S, expf(__fmul_rn(-eta, __fsub_rn(mu, x))), 1.f);
+      mu = x;
+    } else {
+      S = __fadd_rn(S, expf(__fmul_rn(-eta, __fsub_rn(x, mu))));
+    }
+  }
+  __device__ __forceinline__ float pen(float eta) const
+  {
+    return __fsub_rn(mu, __fdiv_rn(logf(S), eta));
+  }
+};
+
+// A non-separated soft value sd = -pen can be positive (shallow overlaps,
+// Sec. IV-D); mapped like the squared separation so that one ordering holds
+// across separated (d^2) and non-separated obstacles.
+__device__ __forceinline__ float soft_key(float sd)
+{
+  return sd > 0.f ? __fmul_rn(sd, sd) : sd;
+}
+
 // ---------------------------------------------------------------------------
 // footprint access
 // ---------------------------------------------------------------------------
@@ -143,10 +175,9 @@ __device__ __forceinline__ float2 robot_interval(const FootprintS &F, int l)
 // obstacle's projections on the robot axes (pmax/pmin, Sec. IV-C) and the
 // overlap on this edge's own axis.
 template <int M, bool SEG, class FP>
-__device__ __forceinline__ void edge_step(const FP &F, V2 A, V2 B, float inv_len2,
-                                          float inv_len, float alpha_p, float beta_p,
-                                          float (&pmax)[M], float (&pmin)[M], float &d2min,
-                                          float &dlt)
+__device__ __forceinline__ float edge_step(const FP &F, V2 A, V2 B, float inv_len2,
+                                           float inv_len, float alpha_p, float beta_p,
+                                           float (&pmax)[M], float (&pmin)[M], float &d2min)
 {
   const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
   float smin = kInf, smax = -kInf;
@@ -181,7 +212,7 @@ __device__ __forceinline__ void edge_step(const FP &F, V2 A, V2 B, float inv_len
   // robot interval [smin, smax] / (|u| + eps)
   const float da = __fmaf_rn(-smin, inv_len, beta_p);
   const float db = __fmaf_rn(smax, inv_len, -alpha_p);
-  dlt = fminf(dlt, fminf(da, db));
+  return fminf(da, db);
 }
 
 // A segment's B endpoint as an extra obstacle vertex: robot-edge distances
@@ -204,25 +235,15 @@ __device__ __forceinline__ void extra_vertex(const FP &F, V2 X, float (&pmax)[M]
   }
 }
 
-template <int M, class FP>
-__device__ __forceinline__ float robot_axes_min(const FP &F, const float (&pmax)[M],
-                                                const float (&pmin)[M], float dlt)
-{
-#pragma unroll
-  for (int l = 0; l < M; ++l) {
-    const float2 iv = robot_interval(F, l);
-    const float da = __fsub_rn(pmax[l], iv.x);
-    const float db = __fsub_rn(iv.y, pmin[l]);
-    dlt = fminf(dlt, fminf(da, db));
-  }
-  return dlt;
-}
-
-// Value of one obstacle whose vertex records start at vt (2 float4 per vertex).
-template <int M, class FP>
+// Value of one obstacle whose vertex records start at vt (2 float4 per vertex),
+// in the min-key domain: d^2 when separated, else -pen (hard: the minimum
+// of max(delta, 0); SOFT: Eq. penetration_depth with sharpness eta, through
+// soft_key).  Axes are visited in a fixed order: each edge's own axis, then
+// the robot axes.
+template <int M, class FP, bool SOFT = false>
 __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
                                                 float c, float s, const float4 *vt, int n,
-                                                float eps_sat)
+                                                float eps_sat, float eta = 0.f)
 {
   float pmax[M], pmin[M];
 #pragma unroll
@@ -231,11 +252,14 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
     pmin[l] = kInf;
   }
   float d2min = kInf, dlt = kInf;
+  SoftAcc acc;
   const float4 a0 = vt[0], b0 = vt[1];
   const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
   if (n == 1) {
     const V2 B0 = to_local(b0.z, b0.w, px, py, c, s);
-    edge_step<M, true>(F, A0, B0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min, dlt);
+    const float de = edge_step<M, true>(F, A0, B0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min);
+    dlt = fminf(dlt, de);
+    if (SOFT) acc.add(de, eta);
     extra_vertex<M>(F, B0, pmax, pmin, d2min);
   } else {
     V2 Acur = A0;
@@ -248,21 +272,33 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
         bnx = vt[2 * (k + 1) + 1];
         Anx = to_local(anx.x, anx.y, px, py, c, s);
       }
-      edge_step<M, false>(F, Acur, Anx, acur.z, acur.w, bcur.x, bcur.y, pmax, pmin, d2min, dlt);
+      const float de =
+          edge_step<M, false>(F, Acur, Anx, acur.z, acur.w, bcur.x, bcur.y, pmax, pmin, d2min);
+      dlt = fminf(dlt, de);
+      if (SOFT) acc.add(de, eta);
       Acur = Anx;
       acur = anx;
       bcur = bnx;
     }
   }
-  dlt = robot_axes_min<M>(F, pmax, pmin, dlt);
-  return synth_value(d2min, dlt, eps_sat);
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float2 iv = robot_interval(F, l);
+    const float dl = fminf(__fsub_rn(pmax[l], iv.x), __fsub_rn(iv.y, pmin[l]));
+    dlt = fminf(dlt, dl);
+    if (SOFT) acc.add(dl, eta);
+  }
+  if (!SOFT) return synth_value(d2min, dlt, eps_sat);
+  if (dlt < -eps_sat) return d2min;
+  return soft_key(-acc.pen(eta));
 }
 
 // ---------------------------------------------------------------------------
 // detail of one obstacle: active pair (lowest (value, pair id)) + gradient
 // ---------------------------------------------------------------------------
 struct Active {
-  float val;      // the obstacle's min-key value (d^2 or -pen)
+  float val;      // the obstacle's min-key value (d^2, -pen, or soft_key(-pen_soft))
+  float pen;      // soft penetration depth (SOFT, non-separated)
   float d2min;    // squared separation
   float dlt;      // min overlap over all axes
   bool separated;
@@ -276,11 +312,13 @@ __device__ __forceinline__ bool better(float v, unsigned pid, float bv, unsigned
   return v < bv || (v == bv && pid < bpid);
 }
 
-template <int M>
+template <int M, bool SOFT = false>
 __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px, float py,
                                                   float c, float s, const float4 *vt, int n,
-                                                  int orig_first, float eps_sat)
+                                                  int orig_first, float eps_sat,
+                                                  float eta = 0.f)
 {
+  SoftAcc acc;
   const bool seg = (n == 1);
   float pmax[M], pmin[M];
   int kmax[M], kmin[M];
@@ -349,6 +387,7 @@ __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px,
     const float da = __fmaf_rn(-smin, ak4.w, bk4.y);
     const float db = __fmaf_rn(smax, ak4.w, -bk4.x);
     dlt = fminf(dlt, fminf(da, db));
+    if (SOFT) acc.add(fminf(da, db), eta);
     {
       const unsigned pid = make_pid(edge, kOAxisOMax, lsmin);
       if (better(da, pid, ba, pa)) { ba = da; pa = pid; akind = kOAxisOMax; al = lsmin; ak = k; }
@@ -383,6 +422,7 @@ __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px,
     const float da = __fsub_rn(pmax[l], F.alo[l]);
     const float db = __fsub_rn(F.ahi[l], pmin[l]);
     dlt = fminf(dlt, fminf(da, db));
+    if (SOFT) acc.add(fminf(da, db), eta);
     const bool bA = seg && kmax[l] == 1, bB = seg && kmin[l] == 1;
     const int eA = seg ? orig_first : orig_first + kmax[l];
     const int eB = seg ? orig_first : orig_first + kmin[l];
@@ -396,6 +436,11 @@ __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px,
   r.dlt = dlt;
   r.separated = dlt < -eps_sat;
   r.val = synth_value(d2min, dlt, eps_sat);
+  r.pen = 0.f;
+  if (SOFT && !r.separated) {
+    r.pen = acc.pen(eta);
+    r.val = soft_key(-r.pen);
+  }
   if (r.separated) {
     r.pid = pd; r.kind = dkind; r.l = dl; r.k = dk; r.t = dt_;
   } else {
@@ -601,6 +646,94 @@ __device__ __forceinline__ float active_t(const FootprintK &F, float px, float p
   return __fmul_rn(-__fmaf_rn(wx, ex, __fmul_rn(wy, ey)), ie);
 }
 
+// Gradient of the soft penetration (Eq. penetration_depth) of a
+// non-separated obstacle: sd = -pen, d sd = sum over axes with delta > 0 of
+// w_a d(-delta_a), w_a = exp(-eta (delta_a - pen)) (the softmax weights).
+// Each axis contributes the closed-form gradient of its smaller side (ties by
+// pair id), exactly as the active pair does in the hard case; emit(w, grad)
+// is called once per contributing axis, edge axes in edge order first.
+template <int M, class Emit>
+__device__ __forceinline__ void soft_grad(const FootprintK &F, float px, float py, float c,
+                                          float s, const float4 *vt, const int *far, int n,
+                                          int orig_first, float eps_axis, float eta, float pen,
+                                          Emit &&emit)
+{
+  const bool seg = (n == 1);
+  float pmax[M], pmin[M];
+  int kmax[M], kmin[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    pmax[l] = -kInf;
+    pmin[l] = kInf;
+    kmax[l] = 0;
+    kmin[l] = 0;
+  }
+  const float4 a0 = vt[0], b0 = vt[1];
+  const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
+  for (int k = 0; k < n; ++k) {
+    const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
+    const V2 A = (k == 0) ? A0 : to_local(ak4.x, ak4.y, px, py, c, s);
+    V2 B;
+    if (seg) {
+      B = to_local(b0.z, b0.w, px, py, c, s);
+    } else if (k + 1 < n) {
+      const float4 an = vt[2 * (k + 1)];
+      B = to_local(an.x, an.y, px, py, c, s);
+    } else {
+      B = A0;
+    }
+    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    float smin = kInf, smax = -kInf;
+    int lsmin = 0, lsmax = 0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
+      const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+      if (sl < smin) { smin = sl; lsmin = l; }
+      if (sl > smax) { smax = sl; lsmax = l; }
+      const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
+      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = k; }
+      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = k; }
+    }
+    const float da = __fmaf_rn(-smin, ak4.w, bk4.y);
+    const float db = __fmaf_rn(smax, ak4.w, -bk4.x);
+    const float dn = fminf(da, db);
+    if (dn > 0.f) {
+      const int edge = orig_first + k;
+      const bool sideA =
+          better(da, make_pid(edge, kOAxisOMax, lsmin), db, make_pid(edge, kOAxisRMax, lsmax));
+      const float w = expf(__fmul_rn(-eta, __fsub_rn(dn, pen)));
+      emit(w, active_grad<M>(F, px, py, c, s, vt, far, n, orig_first,
+                             sideA ? kOAxisOMax : kOAxisRMax, sideA ? lsmin : lsmax, k, 0.f,
+                             eps_axis));
+    }
+  }
+  if (seg) {
+    const V2 Bv = to_local(b0.z, b0.w, px, py, c, s);
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const float pr = __fmaf_rn(Bv.x, F.nx[l], __fmul_rn(Bv.y, F.ny[l]));
+      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = 1; }
+      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = 1; }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float da = __fsub_rn(pmax[l], F.alo[l]);
+    const float db = __fsub_rn(F.ahi[l], pmin[l]);
+    const float dn = fminf(da, db);
+    if (!(dn > 0.f)) continue;
+    const bool bA = seg && kmax[l] == 1, bB = seg && kmin[l] == 1;
+    const int kindA = bA ? kRAxisOMaxB : kRAxisOMax, kindB = bB ? kRAxisRMaxB : kRAxisRMax;
+    const int eA = seg ? orig_first : orig_first + kmax[l];
+    const int eB = seg ? orig_first : orig_first + kmin[l];
+    const bool sideA = better(da, make_pid(eA, kindA, l), db, make_pid(eB, kindB, l));
+    const float w = expf(__fmul_rn(-eta, __fsub_rn(dn, pen)));
+    emit(w, active_grad<M>(F, px, py, c, s, vt, far, n, orig_first, sideA ? kindA : kindB, l,
+                           sideA ? kmax[l] : kmin[l], 0.f, eps_axis));
+  }
+}
+
 // Result of the per-pose epilogue.
 struct PoseOut {
   float phi;
@@ -619,13 +752,14 @@ __device__ __forceinline__ PoseOut pose_out_failed()
 // candidate sets and the closed-form gradient of the active pair is taken
 // (Alg. 1, value + gradient).  row_obs is indexed by the key's rank (a caller
 // row of the pose's scene).
-template <int M>
+template <int M, bool SOFT = false>
 __device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_sat,
                                                  float eps_axis, float px, float py, float theta,
                                                  unsigned long long key,
                                                  const ObsRec *__restrict__ row_obs,
                                                  const float4 *__restrict__ vtx,
-                                                 const int *__restrict__ far, bool want_grad)
+                                                 const int *__restrict__ far, bool want_grad,
+                                                 float eta = 0.f)
 {
   PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
   if (key == ~0ull) return r;  // no obstacle at all
@@ -634,9 +768,20 @@ __device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_
   const int rank = (int)(unsigned)(key & 0xffffffffu);
   const ObsRec o = row_obs[rank];
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
-  const Active a = obstacle_detail<M>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat);
-  r.phi = a.separated ? sqrtf(a.val) : a.val;
+  const Active a = obstacle_detail<M, SOFT>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat, eta);
   r.pid = a.pid;
+  if (SOFT && !a.separated) {
+    r.phi = -a.pen;
+    if (want_grad)
+      soft_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first, eps_axis, eta,
+                   a.pen, [&](float w, const Grad &g) {
+                     r.g[0] = __fmaf_rn(w, g.gp[0], r.g[0]);
+                     r.g[1] = __fmaf_rn(w, g.gp[1], r.g[1]);
+                     r.g[2] = __fmaf_rn(w, g.gp[2], r.g[2]);
+                   });
+    return r;
+  }
+  r.phi = a.separated ? sqrtf(a.val) : a.val;
   if (want_grad && (a.separated || a.dlt > 0.f)) {
     const Grad g = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first,
                                   a.kind, a.l, a.k, a.t, eps_axis);
