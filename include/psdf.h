@@ -171,6 +171,19 @@ int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scene *scene,
                    float *dphi, uint32_t *active, void *workspace, size_t workspace_bytes,
                    void *stream);
 
+/* ---- SQP-RTI stage parameters (Alg. 1, PSDF-MPC pipeline) ---------------
+ * The affine safety constraint of every prediction stage, J_g dx <= h, from
+ * the linearization of h = phi - d_min at the nominal pose (Sec. V-A):
+ * stage float[P][4] = {h, J_g} with h = phi - d_min and J_g = -d phi / d x
+ * (x = (px, py, theta)); active (optional) as for psdf_eval.  The same
+ * kernels as psdf_eval_grad with the conversion fused into the per-pose
+ * epilogue (phi and the gradient are not stored separately); d_min must be
+ * finite.  Asynchronous, no allocation (graph-capturable). */
+int psdf_stage_params(const float *footprint, int32_t m, const psdf_scene *scene,
+                      const float *poses, int64_t P, const psdf_params *params, float d_min,
+                      float *stage, uint32_t *active, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
 /* ---- backward (vector-Jacobian product of phi, Sec. IV-D) ----------------
  * Given the active pair ids of a previous psdf_eval / psdf_eval_grad with the
  * same footprint, scene, poses and params, and an upstream gradient
@@ -384,6 +397,17 @@ int psdf_plan_autotune(psdf_plan *plan, const float *poses, int32_t reps, void *
  * PSDF_ERR_TIMEOUT. */
 int psdf_eval_batched(psdf_plan *plan, const float *poses, float *phi, float *dphi,
                       uint32_t *active, void *stream);
+/* Stage parameters of every pose of a plan (time-varying edge sets: one
+ * instance per stage, each with its own edges), as psdf_stage_params:
+ * stage float[n_poses][4] = {phi - d_min, -d phi / d x}. */
+int psdf_stage_params_batched(psdf_plan *plan, const float *poses, float d_min, float *stage,
+                              uint32_t *active, void *stream);
+/* Debug builds of the library (compiled with PSDF_DEBUG_CHECKS) check every
+ * index the batched kernels take from their data before using it, record
+ * the first violation as (site << 48 | index) and skip the access; this
+ * returns that record (0 = none) and *enabled = 1.  Release builds return
+ * *enabled = 0 and *violation = 0. */
+int psdf_plan_debug_read(uint64_t *violation, int32_t *enabled);
 /* Synchronizes the stream and reports whether the last psdf_eval_batched
  * met a timed-out wait. */
 int psdf_plan_status(const psdf_plan *plan, void *stream);

@@ -3,7 +3,9 @@
     python -m paper_2607_04310_b300.build [--force]
 
 nvcc cross-compiles without a GPU.  Objects are compiled in parallel into
-``_build/`` and linked into ``paper_2607_04310_b300/libpsdf_b300.so``.
+``_build/`` and linked into ``paper_2607_04310_b300/libpsdf_b300.so``.  With
+PSDF_DEBUG=1 in the environment the objects go to ``_build_debug/`` and are
+compiled with PSDF_DEBUG_CHECKS (index checks in the batched kernels).
 """
 from __future__ import annotations
 
@@ -16,12 +18,13 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(ROOT, "_build")
+DEBUG = os.environ.get("PSDF_DEBUG", "0") not in ("", "0")
+BUILD = os.path.join(ROOT, "_build_debug" if DEBUG else "_build")
 LIB = os.path.join(HERE, "libpsdf_b300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr"] + (["-DPSDF_DEBUG_CHECKS"] if DEBUG else [])
 
 
 def _nvcc() -> str:

@@ -21,6 +21,7 @@
 // Autotuner: a grid of (threads, tiles per item) is timed on the caller's
 // poses; the fastest is kept and cached per plan shape for the process.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -69,6 +70,29 @@ struct PlanInst {
 // counters: [0] work queue, [1] a timed-out wait
 constexpr int kCtrWords = 2;
 
+// Sizes of the plan's device arrays, for the index checks of a debug build.
+struct PlanBounds {
+  long long n_poses, n_rows, n_vtx, blob_bytes;
+  int n_items, n_blocks, n_inst, n_tiles;
+};
+
+// Debug builds (PSDF_DEBUG_CHECKS) check every index a batched kernel takes
+// from its data before using it: the first violation (site << 48 | index)
+// is recorded and the access skipped.  Release builds compile the checks out.
+#ifdef PSDF_DEBUG_CHECKS
+static __device__ unsigned long long g_plan_debug;
+__device__ __forceinline__ bool dbg_ok(bool cond, int site, long long idx)
+{
+  if (cond) return true;
+  atomicCAS(&g_plan_debug, 0ull,
+            ((unsigned long long)(site & 0xffff) << 48) | ((unsigned long long)idx & 0xffffffffffffull));
+  return false;
+}
+#define PSDF_DBG(cond, site, idx) dbg_ok((cond), (site), (long long)(idx))
+#else
+#define PSDF_DBG(cond, site, idx) true
+#endif
+
 // ---------------------------------------------------------------------------
 // device
 // ---------------------------------------------------------------------------
@@ -79,9 +103,19 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
                           long long pose0, int npose, const TileHdr *__restrict__ tiles,
                           const unsigned char *__restrict__ blob, int tile0, int ntile,
                           unsigned char *buf0, int blob_cap, uint64_t *bars, unsigned &phase,
-                          unsigned long long *keys)
+                          unsigned long long *keys, const PlanBounds &bnd)
 {
   if (ntile == 0) return true;
+#ifdef PSDF_DEBUG_CHECKS
+  for (int k = 0; k < ntile; ++k) {
+    const TileHdr h = tiles[tile0 + k];
+    const bool good = h.blob_off >= 0 && h.blob_off % 16 == 0 && h.blob_bytes >= 16 &&
+                      h.blob_bytes % 16 == 0 && h.blob_bytes <= blob_cap &&
+                      (long long)h.blob_off + h.blob_bytes <= bnd.blob_bytes &&
+                      h.blob_bytes == 16 * h.n_obs + 32 * h.n_vtx;
+    if (!PSDF_DBG(good, 6, tile0 + k)) return true;
+  }
+#endif
   const int S = max(1, (int)blockDim.x / npose);
   const int j = threadIdx.x % npose, part = threadIdx.x / npose;
   const bool live = part < S;
@@ -129,6 +163,10 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
       const int o0 = h.n_obs * part / S, o1 = h.n_obs * (part + 1) / S;
       for (int o = o0; o < o1; ++o) {
         const int4 rec = ob[o];
+        if (!PSDF_DBG(rec.x >= 0 && rec.y >= 1 && rec.y <= kMaxObsEdges &&
+                          rec.x + (rec.y == 1 ? 1 : rec.y) <= h.n_vtx,
+                      7, tile0 + k))
+          continue;
         const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, eps_sat);
         const unsigned long long key = pack_key(v, rec.z);
         best = key < best ? key : best;
@@ -156,7 +194,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads)
                    float eps_sat, const float *__restrict__ poses,
                    const TileHdr *__restrict__ tiles,
                    const unsigned char *__restrict__ blob, int blob_cap,
-                   unsigned long long *keys, unsigned *ctr)
+                   unsigned long long *keys, unsigned *ctr, PlanBounds bnd)
 {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -178,7 +216,15 @@ __global__ void __launch_bounds__(kPlanMaxThreads)
     const int it = s_item;
     if (it >= n_items) break;
     const PlanItem I = items[it];
+    if (!PSDF_DBG(I.block >= 0 && I.block < bnd.n_blocks, 1, it)) continue;
     const PlanBlock B = blocks[I.block];
+    if (!PSDF_DBG(B.inst >= 0 && B.inst < bnd.n_inst, 2, I.block)) continue;
+    if (!PSDF_DBG(B.npose >= 1 && B.npose <= (int)blockDim.x && B.pose0 >= 0 &&
+                      B.pose0 + B.npose <= bnd.n_poses,
+                  3, I.block))
+      continue;
+    if (!PSDF_DBG(I.ntile >= 0 && I.tile0 >= 0 && I.tile0 + I.ntile <= bnd.n_tiles, 4, it))
+      continue;
     if (B.inst != cur_inst) {
       const int *src = reinterpret_cast<const int *>(fps + B.inst);
       int *dst = reinterpret_cast<int *>(Fs);
@@ -192,11 +238,13 @@ __global__ void __launch_bounds__(kPlanMaxThreads)
 #define PSDF_SCAN_CASE(MM)                                                                    \
   case MM:                                                                                    \
     ok = scan_item<MM>(Fv, eps_sat, poses, B.pose0, B.npose, tiles, blob, I.tile0, I.ntile, \
-                       buf0, blob_cap, bars, phase, keys);                                    \
+                       buf0, blob_cap, bars, phase, keys, bnd);                               \
     break;
       PSDF_FOR_EACH_M(PSDF_SCAN_CASE)
 #undef PSDF_SCAN_CASE
-      default: break;
+      default:
+        (void)PSDF_DBG(false, 5, B.inst);
+        break;
     }
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(&ctr[1], 1u);
@@ -218,34 +266,53 @@ __global__ void batched_epilogue_kernel(const int *__restrict__ pose_inst, long 
                                         const unsigned long long *__restrict__ keys,
                                         const unsigned *__restrict__ ctr,
                                         float *__restrict__ phi, float *__restrict__ dphi,
-                                        unsigned *__restrict__ active)
+                                        unsigned *__restrict__ active,
+                                        float *__restrict__ stage, float d_min, PlanBounds bnd)
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const int i = pose_inst[p];
-  const FootprintK &F = fps[i];
   PoseOut r = pose_out_failed();
-  if (ctr[1] == 0u) {
+  if (!PSDF_DBG(i >= 0 && i < bnd.n_inst, 10, p)) {
+    write_pose_out(r, p, phi, dphi, active, stage, d_min);
+    return;
+  }
+  const FootprintK &F = fps[i];
+  bool checked = true;
+#ifdef PSDF_DEBUG_CHECKS
+  {
+    const unsigned long long key = keys[p];
+    if (key != ~0ull) {
+      const long long rank = (long long)(key & 0xffffffffu);
+      const PlanInst in = inst[i];
+      checked = PSDF_DBG(rank < in.rows && in.row0 + rank < bnd.n_rows, 11, p);
+      if (checked) {
+        const ObsRec o = row_obs[in.row0 + rank];
+        checked = PSDF_DBG(o.n >= 1 && o.n <= kMaxObsEdges && o.vtx_global >= 0 &&
+                               (long long)o.vtx_global + o.n <= bnd.n_vtx,
+                           12, p);
+      }
+    }
+    checked = checked && PSDF_DBG(F.m >= 3 && F.m <= kMaxM, 13, p);
+  }
+#endif
+  if (checked && ctr[1] == 0u) {
     const ObsRec *ro = row_obs + inst[i].row0;
     switch (F.m) {
 #define PSDF_EPI_CASE(MM)                                                                  \
   case MM:                                                                                 \
     r = epilogue_pose<MM>(F, eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],            \
-                          poses[3 * p + 2], keys[p], ro, vtx, far, dphi != nullptr);       \
+                          poses[3 * p + 2], keys[p], ro, vtx, far,                         \
+                          dphi != nullptr || stage != nullptr);                            \
     break;
       PSDF_FOR_EACH_M(PSDF_EPI_CASE)
 #undef PSDF_EPI_CASE
       default: break;
     }
   }
-  phi[p] = r.phi;
-  if (active) active[p] = r.pid;
-  if (dphi) {
-    dphi[3 * p] = r.g[0];
-    dphi[3 * p + 1] = r.g[1];
-    dphi[3 * p + 2] = r.g[2];
-  }
+  write_pose_out(r, p, phi, dphi, active, stage, d_min);
 }
+
 // Backward: one thread per pose, the instance's footprint read from global
 // memory (poses of one instance are contiguous, so warps rarely mix sizes).
 __global__ void batched_backward_kernel(const int *__restrict__ pose_inst, long long P,
@@ -302,6 +369,7 @@ struct psdf_plan {
   int n_inst = 0;
   long long n_poses = 0, n_rows = 0;
   int n_tiles = 0, blob_cap = 16;
+  long long n_vtx = 0, blob_total = 0;
   float eps_sat = 0.f, eps_axis = 0.f;
   std::vector<long long> inst_pose0, inst_npose;
   std::vector<int> inst_tile0, inst_ntile, inst_m;
@@ -443,8 +511,22 @@ int apply_config(psdf_plan *pl, const psdf_plan_config &cfg, cudaStream_t st)
   return PSDF_OK;
 }
 
+PlanBounds plan_bounds(const psdf_plan *pl)
+{
+  PlanBounds b;
+  b.n_poses = pl->n_poses;
+  b.n_rows = pl->n_rows;
+  b.n_vtx = pl->n_vtx;
+  b.blob_bytes = pl->blob_total;
+  b.n_items = pl->n_items;
+  b.n_blocks = pl->n_blocks;
+  b.n_inst = pl->n_inst;
+  b.n_tiles = pl->n_tiles;
+  return b;
+}
+
 int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *dphi,
-                   unsigned *active, cudaStream_t st)
+                   unsigned *active, cudaStream_t st, const StageOut &so = StageOut())
 {
   if (pl->n_items == 0) return PSDF_OK;
   cudaError_t e = cudaMemsetAsync(pl->d_ctr, 0, kCtrWords * sizeof(unsigned), st);
@@ -454,7 +536,7 @@ int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *d
     ProfileScope prof("batched", st);
     batched_kernel<<<pl->grid, pl->cfg.threads, pl->smem, st>>>(
         pl->d_items, pl->n_items, pl->d_blocks, pl->d_fprec, pl->eps_sat, poses, pl->d_tiles,
-        pl->d_blob, pl->blob_cap, pl->d_keys, pl->d_ctr);
+        pl->d_blob, pl->blob_cap, pl->d_keys, pl->d_ctr, plan_bounds(pl));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch (batched)");
   }
@@ -463,7 +545,8 @@ int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *d
     const long long P = pl->n_poses;
     batched_epilogue_kernel<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
         pl->d_pose_inst, P, pl->d_fp, pl->d_inst, pl->eps_sat, pl->eps_axis, poses,
-        pl->d_row_obs, pl->d_vtx, pl->d_far, pl->d_keys, pl->d_ctr, phi, dphi, active);
+        pl->d_row_obs, pl->d_vtx, pl->d_far, pl->d_keys, pl->d_ctr, phi, dphi, active,
+        so.stage, so.d_min, plan_bounds(pl));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch (batched epilogue)");
   }
@@ -598,6 +681,8 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
     return rc;
   }
   pl->n_tiles = (int)tiles.size();
+  pl->n_vtx = (long long)vtx.size() / 2;
+  pl->blob_total = (long long)blob.size();
   pl->blob_cap = std::max(16, (max_blob + 15) / 16 * 16);
   // capacity: the configuration with the most items and blocks
   size_t icap = 0, bcap = 0;
@@ -659,6 +744,22 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
   return PSDF_OK;
 }
 
+extern "C" int psdf_plan_debug_read(uint64_t *violation, int32_t *enabled)
+{
+  if (!violation || !enabled) return fail(PSDF_ERR_ARG, "NULL argument");
+  *violation = 0;
+#ifdef PSDF_DEBUG_CHECKS
+  *enabled = 1;
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_plan_debug, sizeof(v));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyFromSymbol(debug word)");
+  *violation = v;
+#else
+  *enabled = 0;
+#endif
+  return PSDF_OK;
+}
+
 extern "C" int psdf_plan_destroy(psdf_plan *plan)
 {
   free_plan(plan);
@@ -694,6 +795,18 @@ extern "C" int psdf_eval_batched(psdf_plan *plan, const float *poses, float *phi
   if (!plan) return fail(PSDF_ERR_ARG, "plan is NULL");
   if (plan->n_poses > 0 && (!poses || !phi)) return fail(PSDF_ERR_ARG, "poses or phi is NULL");
   return launch_batched(plan, poses, phi, dphi, active, (cudaStream_t)stream);
+}
+
+extern "C" int psdf_stage_params_batched(psdf_plan *plan, const float *poses, float d_min,
+                                         float *stage, uint32_t *active, void *stream)
+{
+  if (!plan) return fail(PSDF_ERR_ARG, "plan is NULL");
+  if (plan->n_poses > 0 && (!poses || !stage)) return fail(PSDF_ERR_ARG, "poses or stage is NULL");
+  if (!std::isfinite(d_min)) return fail(PSDF_ERR_ARG, "d_min must be finite");
+  StageOut so;
+  so.stage = stage;
+  so.d_min = d_min;
+  return launch_batched(plan, poses, nullptr, nullptr, active, (cudaStream_t)stream, so);
 }
 
 extern "C" int psdf_plan_status(const psdf_plan *plan, void *stream)

@@ -11,6 +11,7 @@
 // CTAs with one atomicMin per pose per CTA.  A per-pose epilogue re-derives
 // the active pair of the winning obstacle and its closed-form gradient.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -145,7 +146,8 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float4 *__restrict__ vtx, const int *__restrict__ far,
                                 const unsigned long long *__restrict__ keys,
                                 const int *__restrict__ err, float *__restrict__ phi,
-                                float *__restrict__ dphi, unsigned *__restrict__ active)
+                                float *__restrict__ dphi, unsigned *__restrict__ active,
+                                float *__restrict__ stage, float d_min)
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
@@ -154,16 +156,10 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
     r = pose_out_failed();
   } else {
     r = epilogue_pose<M, SOFT>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
-                               poses[3 * p + 2], keys[p], row_obs, vtx, far, dphi != nullptr,
-                               prm.eta);
+                               poses[3 * p + 2], keys[p], row_obs, vtx, far,
+                               dphi != nullptr || stage != nullptr, prm.eta);
   }
-  phi[p] = r.phi;
-  if (active) active[p] = r.pid;
-  if (dphi) {
-    dphi[3 * p] = r.g[0];
-    dphi[3 * p + 1] = r.g[1];
-    dphi[3 * p + 2] = r.g[2];
-  }
+  write_pose_out(r, p, phi, dphi, active, stage, d_min);
 }
 
 template <int M, bool SOFT = false>
@@ -343,7 +339,7 @@ int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
 template <int M>
 static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                        const psdf_params *prm, float *phi, float *dphi, unsigned *active,
-                       void *ws, cudaStream_t st)
+                       void *ws, const StageOut &so, cudaStream_t st)
 {
   int *err = reinterpret_cast<int *>(ws);
   unsigned long long *keys =
@@ -378,10 +374,11 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     if (pk.eta > 0.f)
       epilogue_kernel<M, true><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
                                                    sc->d_vtx, sc->d_far, keys, err, phi, dphi,
-                                                   active);
+                                                   active, so.stage, so.d_min);
     else
       epilogue_kernel<M><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
-                                             sc->d_vtx, sc->d_far, keys, err, phi, dphi, active);
+                                             sc->d_vtx, sc->d_far, keys, err, phi, dphi, active,
+                                             so.stage, so.d_min);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -437,9 +434,9 @@ template <int M>
 struct EvalCall {
   static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                  const psdf_params *prm, float *phi, float *dphi, unsigned *active, void *ws,
-                 cudaStream_t st)
+                 const StageOut &so, cudaStream_t st)
   {
-    return launch_eval<M>(F, sc, poses, P, prm, phi, dphi, active, ws, st);
+    return launch_eval<M>(F, sc, poses, P, prm, phi, dphi, active, ws, so, st);
   }
 };
 
@@ -453,7 +450,7 @@ struct EpilogueCall {
     ProfileScope prof("epilogue", st);
     epilogue_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
                                                sc->d_vtx, sc->d_far, keys, err,
-                                               phi, dphi, active);
+                                               phi, dphi, active, nullptr, 0.f);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PSDF_OK;
@@ -479,17 +476,17 @@ int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *pose
 
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,
-                void *ws, size_t ws_bytes, void *stream)
+                void *ws, size_t ws_bytes, void *stream, const StageOut &so)
 {
   int rc = check_eval_args(scene, poses, P, params, ws, ws_bytes);
   if (rc) return rc;
-  if (P > 0 && !phi) return fail(PSDF_ERR_ARG, "phi is NULL");
+  if (P > 0 && !phi && !so.stage) return fail(PSDF_ERR_ARG, "phi is NULL");
   FootprintK F;
   rc = make_footprint(footprint, m, scene->eps_seg, &F);
   if (rc) return rc;
   if (P == 0) return PSDF_OK;
   return dispatch_m<EvalCall>(m, F, scene, poses, (long long)P, params, phi, dphi, active, ws,
-                              (cudaStream_t)stream);
+                              so, (cudaStream_t)stream);
 }
 
 }  // namespace psdf
@@ -512,6 +509,20 @@ extern "C" int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scen
   if (P > 0 && !dphi) return fail(PSDF_ERR_ARG, "dphi is NULL");
   return eval_common(footprint, m, scene, poses, P, params, phi, dphi, active, workspace,
                      workspace_bytes, stream);
+}
+
+extern "C" int psdf_stage_params(const float *footprint, int32_t m, const psdf_scene *scene,
+                                 const float *poses, int64_t P, const psdf_params *params,
+                                 float d_min, float *stage, uint32_t *active, void *workspace,
+                                 size_t workspace_bytes, void *stream)
+{
+  if (P > 0 && !stage) return fail(PSDF_ERR_ARG, "stage is NULL");
+  if (!std::isfinite(d_min)) return fail(PSDF_ERR_ARG, "d_min must be finite");
+  StageOut so;
+  so.stage = stage;
+  so.d_min = d_min;
+  return eval_common(footprint, m, scene, poses, P, params, nullptr, nullptr, active, workspace,
+                     workspace_bytes, stream, so);
 }
 
 extern "C" int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,

@@ -747,6 +747,26 @@ __device__ __forceinline__ PoseOut pose_out_failed()
   return PoseOut{nan, {nan, nan, nan}, PSDF_PAIR_NONE};
 }
 
+// Stores one pose's epilogue results; every output is optional.  stage (if
+// given) receives the SQP-RTI stage parameters h = phi - d_min and
+// J_g = -d phi / d x (Alg. 1).
+__device__ __forceinline__ void write_pose_out(const PoseOut &r, long long p, float *phi,
+                                               float *dphi, unsigned *active, float *stage,
+                                               float d_min)
+{
+  if (phi) phi[p] = r.phi;
+  if (active) active[p] = r.pid;
+  if (dphi) {
+    dphi[3 * p] = r.g[0];
+    dphi[3 * p + 1] = r.g[1];
+    dphi[3 * p + 2] = r.g[2];
+  }
+  if (stage) {
+    reinterpret_cast<float4 *>(stage)[p] =
+        make_float4(__fsub_rn(r.phi, d_min), -r.g[0], -r.g[1], -r.g[2]);
+  }
+}
+
 // Value, active pair and (if want_grad) pose gradient of one pose from its
 // 64-bit min-key: the winning obstacle is re-evaluated with its exact
 // candidate sets and the closed-form gradient of the active pair is taken

@@ -139,6 +139,14 @@ int dev_upload(T **dst, const std::vector<T> &src, cudaStream_t st, size_t *byte
   return PSDF_OK;
 }
 
+// Optional SQP-RTI stage parameters written by an epilogue (Alg. 1, PSDF-MPC
+// pipeline): stage[4 p] = phi - d_min (h), stage[4 p + 1 .. 3] = -d phi / d x
+// (J_g).
+struct StageOut {
+  float *stage = nullptr;
+  float d_min = 0.f;
+};
+
 // shared host helpers (eval.cu)
 int device_sms();
 int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F);
@@ -151,5 +159,5 @@ int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *pose
 // value (+ gradient if dphi) evaluation with a given workspace (eval.cu)
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,
-                void *ws, size_t ws_bytes, void *stream);
+                void *ws, size_t ws_bytes, void *stream, const StageOut &so = StageOut());
 }  // namespace psdf

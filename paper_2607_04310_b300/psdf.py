@@ -83,6 +83,9 @@ _SIGS = {
                                       _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_backward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                      _vp, _vp, _vp, _vp]),
+    "psdf_stage_params": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                         ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "psdf_stage_params_batched": (ctypes.c_int, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
     "psdf_eval_grad_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64,
                                               _vp, _vp, _vp, _vp, _vp]),
     "psdf_mlp_create": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.POINTER(_vp)]),
@@ -118,6 +121,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int32)]),
     "psdf_eval_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "psdf_plan_status": (ctypes.c_int, [_vp, _vp]),
+    "psdf_plan_debug_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_int32)]),
     "psdf_backward_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
@@ -257,6 +262,15 @@ def psdf_eval_grad(footprint: np.ndarray, scene: Scene, poses, params: Params, p
                                  poses.shape[0], ctypes.byref(params), _ptr(phi), _ptr(dphi),
                                  _ptr(active), _ptr(workspace), workspace.numel(),
                                  _stream(stream)))
+
+
+def psdf_stage_params(footprint: np.ndarray, scene: Scene, poses, params: Params, d_min: float,
+                      stage, active, workspace, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_stage_params(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                    poses.shape[0], ctypes.byref(params), float(d_min),
+                                    _ptr(stage), _ptr(active), _ptr(workspace), workspace.numel(),
+                                    _stream(stream)))
 
 
 def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, active, grad_phi,
@@ -505,6 +519,20 @@ def psdf_plan_autotune(plan: Plan, poses, reps: int = 3, stream=None) -> Tuple[P
 def psdf_eval_batched(plan: Plan, poses, phi, dphi=None, active=None, stream=None) -> None:
     _check(load().psdf_eval_batched(plan.handle, _ptr(poses), _ptr(phi), _ptr(dphi),
                                     _ptr(active), _stream(stream)))
+
+
+def psdf_stage_params_batched(plan: Plan, poses, d_min: float, stage, active=None,
+                              stream=None) -> None:
+    _check(load().psdf_stage_params_batched(plan.handle, _ptr(poses), float(d_min), _ptr(stage),
+                                            _ptr(active), _stream(stream)))
+
+
+def psdf_plan_debug_read() -> Tuple[int, bool]:
+    """(first recorded index violation, whether this is a debug build)."""
+    v = ctypes.c_uint64(0)
+    en = ctypes.c_int32(0)
+    _check(load().psdf_plan_debug_read(ctypes.byref(v), ctypes.byref(en)))
+    return int(v.value), bool(en.value)
 
 
 def psdf_plan_status(plan: Plan, stream=None) -> int:

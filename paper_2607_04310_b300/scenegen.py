@@ -330,3 +330,31 @@ def training_scene(index: int, n_rects: int = 1024, n_poses: int = 64,
     poses = poses_uniform(g, n_poses, 0.0, side)
     return Workload("training scene %d" % index, fp, edges, offs, poses,
                     {"seed": 1000 + index, "field": side})
+
+
+def moving_obstacle_stages(seed: int = 5, n_mpc: int = 64, horizon: int = 15,
+                           n_rects: int = 200, field: float = 30.0, dt: float = 0.1,
+                           speed: float = 1.0) -> List[Instance]:
+    """Time-varying per-stage edge sets: n_mpc MPC problems, each a horizon
+    of `horizon` stages; stage s sees its own edge set (random-yaw rectangles
+    translated by velocity * s * dt, velocities uniform in direction with
+    |v| <= speed) and the nominal pose of that stage.  One instance per
+    (problem, stage), one pose each.  Translations are added in FP64 and
+    rounded once, so polygon closure stays exact."""
+    g = rng(seed)
+    fp = footprint_rect(0.6, 0.4)
+    out = []
+    for _ in range(n_mpc):
+        edges, offs = rects(g, n_rects, 0.2, 2.0, 0.0, field)
+        n = n_rects
+        ang = g.uniform(-math.pi, math.pi, size=n)
+        vel = g.uniform(0.0, speed, size=n)[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1)
+        path = poses_paths(g, 1, horizon, 0.0, field, step=0.1, dtheta=0.1)
+        base = edges.astype(np.float64).reshape(n, 4, 4)
+        for s_ in range(horizon):
+            d = vel * (s_ * dt)                               # [n, 2]
+            e = base.copy()
+            e[:, :, 0:2] += d[:, None, :]
+            e[:, :, 2:4] += d[:, None, :]
+            out.append(Instance(fp, e.reshape(4 * n, 4).astype(F32), offs, path[s_:s_ + 1]))
+    return out
