@@ -339,6 +339,103 @@ def _bench_batched(a, dev, flush, stream, peak):
     }
 
 
+def _bench_table1(dev, reps: int = 200):
+    """Latency grid of the paper's Table I: M in {1, 10, 100} random-yaw
+    rectangles x B in {1, 10, 100} poses, rectangle footprint.  Three views:
+    the autograd forward and backward as a PyTorch user calls them (host
+    wall clock, synchronized, mean and std -- the paper's measurement; the
+    backward includes PyTorch's autograd engine), the C ABI called directly
+    (psdf_eval_grad, psdf_backward; median host wall clock, synchronized),
+    and the device time of value + gradient + backward replayed as one CUDA
+    graph."""
+    import torch
+    from paper_2607_04310_b300 import psdf
+    from paper_2607_04310_b300 import scenegen as sg
+    from paper_2607_04310_b300.autograd import PSDF
+    g = np.random.default_rng(6)
+    fp = sg.footprint_rect(0.6, 0.4)
+    keys = ("autograd_forward_ms", "autograd_forward_std_ms", "autograd_backward_ms",
+            "autograd_backward_std_ms", "cabi_forward_ms", "cabi_backward_ms", "graph_step_ms")
+    res = {"M": [1, 10, 100], "B": [1, 10, 100]}
+    for k in keys:
+        res[k] = []
+    for M in res["M"]:
+        edges, offs = sg.rects(g, M, 0.2, 2.0, 0.0, 20.0)
+        mod = PSDF(edges, offs, fp)
+        prm = mod.scene.params
+        rows = {k: [] for k in keys}
+        for B in res["B"]:
+            poses = torch.as_tensor(sg.poses_uniform(g, B, 0.0, 20.0), device=dev)
+            pr = poses.clone().requires_grad_(True)
+            for _ in range(10):
+                mod(pr).sum().backward()
+            torch.cuda.synchronize()
+            tf, tb = [], []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                phi = mod(pr)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                loss = phi.sum()
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                loss.backward()
+                torch.cuda.synchronize()
+                t3 = time.perf_counter()
+                tf.append(1e3 * (t1 - t0))
+                tb.append(1e3 * (t3 - t2))
+            rows["autograd_forward_ms"].append(float(np.mean(tf)))
+            rows["autograd_forward_std_ms"].append(float(np.std(tf)))
+            rows["autograd_backward_ms"].append(float(np.mean(tb)))
+            rows["autograd_backward_std_ms"].append(float(np.std(tb)))
+            # the C ABI directly, preallocated buffers
+            phi_o = torch.empty(B, device=dev)
+            dphi_o = torch.empty((B, 3), device=dev)
+            act_o = torch.empty(B, dtype=torch.int32, device=dev)
+            gphi = torch.ones(B, device=dev)
+            gpose = torch.empty((B, 3), device=dev)
+            ws = psdf.workspace(B, dev)
+
+            def fwd():
+                psdf.psdf_eval_grad(fp, mod.scene, poses, prm, phi_o, dphi_o, act_o, ws)
+
+            def bwd():
+                psdf.psdf_backward(fp, mod.scene, poses, prm, act_o, gphi, gpose, None)
+
+            for name, fn in (("cabi_forward_ms", fwd), ("cabi_backward_ms", bwd)):
+                for _ in range(10):
+                    fn()
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    fn()
+                    torch.cuda.synchronize()
+                    ts.append(1e3 * (time.perf_counter() - t0))
+                rows[name].append(float(np.median(ts)))
+
+            def step():
+                fwd()
+                bwd()
+
+            replay, _g = _graph(step)
+            for _ in range(5):
+                replay()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                replay()
+            e1.record()
+            torch.cuda.synchronize()
+            rows["graph_step_ms"].append(e0.elapsed_time(e1) / reps)
+        for k in keys:
+            res[k].append(rows[k])
+    res["note"] = ("rows M, columns B; paper (RTX 4090, PyTorch autograd): forward 0.580-0.614 "
+                   "ms, backward 2.021-2.238 ms (context, other hardware)")
+    return res
+
+
 def run_b300(a, rank, world, local):
     import torch
     from paper_2607_04310_b300 import psdf, roofline
@@ -535,6 +632,7 @@ def run_b300(a, rank, world, local):
     }
     if not a.no_batched and world == 1:
         line["batched_uneven"] = _bench_batched(a, dev, flush, stream, peak)
+        line["table1_latency"] = _bench_table1(dev)
     if not a.no_cpu_baseline and world == 1:
         import oracle
         rate, n, dt = _oracle_rate(w, a.cpu_seconds)

@@ -55,10 +55,14 @@ __global__ void init_keys_kernel(unsigned long long *keys, long long P, int *err
   if (i == 0) *err = 0;
 }
 
-// Full scan: each CTA = kScanThreads poses x tiles [t0, t1).
+// Full scan: each CTA = a block of npb poses x tiles [t0, t1).  With npb =
+// kScanThreads every lane owns one pose; a smaller batch (npb < kScanThreads)
+// splits each tile's obstacles over S = kScanThreads / npb lanes per pose
+// (lane l: pose l % npb, obstacle range l / npb), so that a short horizon
+// still fills the CTA and each lane's chain stays short.
 template <int M, bool SOFT = false>
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(
-    FootprintK F, ParamsK prm, const float *__restrict__ poses, long long P,
+    FootprintK F, ParamsK prm, const float *__restrict__ poses, long long P, int npb,
     const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob, int n_tiles,
     int tiles_per_chunk, int blob_cap, unsigned long long *__restrict__ keys,
     int *__restrict__ err)
@@ -71,8 +75,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
   const int t1 = min(n_tiles, t0 + tiles_per_chunk);
   if (t0 >= t1) return;  // uniform over the CTA
 
-  const long long p = (long long)blockIdx.x * kScanThreads + threadIdx.x;
-  const bool live = p < P;
+  const int S = kScanThreads / npb;
+  const int part = threadIdx.x / npb;
+  const long long p = (long long)blockIdx.x * npb + threadIdx.x % npb;
+  const bool live = p < P && part < S;
   float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
   if (live) {
     px = poses[3 * p];
@@ -118,7 +124,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     const unsigned char *tb = buf0 + b * blob_cap;
     const int4 *ob = reinterpret_cast<const int4 *>(tb);
     const float4 *vt = reinterpret_cast<const float4 *>(tb + 16 * h.n_obs);
-    for (int o = 0; o < h.n_obs; ++o) {
+    // lanes beyond the S ranges (part >= S) take an empty range
+    const int o0 = part >= S ? 0 : (S == 1 ? 0 : h.n_obs * part / S);
+    const int o1 = part >= S ? 0 : (S == 1 ? h.n_obs : h.n_obs * (part + 1) / S);
+    for (int o = o0; o < o1; ++o) {
       const int4 rec = ob[o];
       const float v = obstacle_value<M, FootprintK, SOFT>(F, px, py, c, s, vt + 2 * rec.x, rec.y,
                                                           prm.eps_sat, prm.eta);
@@ -349,7 +358,9 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   init_keys_kernel<<<init_blocks, 256, 0, st>>>(keys, P, err);
   if (sc->n_tiles > 0) {
     const DeviceInfo di = device_info_impl();
-    const long long pose_blocks = (P + kScanThreads - 1) / kScanThreads;
+    // a batch smaller than one CTA splits each tile's obstacles over lanes
+    const int npb = P < kScanThreads ? (int)P : kScanThreads;
+    const long long pose_blocks = (P + npb - 1) / npb;
     if (pose_blocks > 2147483647LL) return fail(PSDF_ERR_CAPACITY, "too many poses for one launch");
     // aim for about 32 CTAs per SM in total (several waves of resident CTAs)
     const long long target = (long long)di.sms * 32;
@@ -362,11 +373,13 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     dim3 grid((unsigned)pose_blocks, (unsigned)chunks);
     ProfileScope prof("scan", st);
     if (pk.eta > 0.f)
-      scan_kernel<M, true><<<grid, kScanThreads, smem, st>>>(
-          F, pk, poses, P, sc->d_tiles, sc->d_blob, sc->n_tiles, (int)tpc, blob_cap, keys, err);
+      scan_kernel<M, true><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, npb, sc->d_tiles,
+                                                             sc->d_blob, sc->n_tiles, (int)tpc,
+                                                             blob_cap, keys, err);
     else
-      scan_kernel<M><<<grid, kScanThreads, smem, st>>>(
-          F, pk, poses, P, sc->d_tiles, sc->d_blob, sc->n_tiles, (int)tpc, blob_cap, keys, err);
+      scan_kernel<M><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, npb, sc->d_tiles,
+                                                       sc->d_blob, sc->n_tiles, (int)tpc,
+                                                       blob_cap, keys, err);
   }
   {
     ProfileScope prof("epilogue", st);
