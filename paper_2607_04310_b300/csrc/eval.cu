@@ -358,8 +358,11 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   init_keys_kernel<<<init_blocks, 256, 0, st>>>(keys, P, err);
   if (sc->n_tiles > 0) {
     const DeviceInfo di = device_info_impl();
-    // a batch smaller than one CTA splits each tile's obstacles over lanes
-    const int npb = P < kScanThreads ? (int)P : kScanThreads;
+    // a small launch (fewer pose blocks x tiles than SMs) splits each tile's
+    // obstacles over more lanes per pose: halve the poses per CTA (down to 8)
+    // until the grid covers the GPU
+    int npb = P < kScanThreads ? (int)P : kScanThreads;
+    while (npb > 8 && ((P + npb - 1) / npb) * sc->n_tiles < di.sms) npb = (npb + 1) / 2;
     const long long pose_blocks = (P + npb - 1) / npb;
     if (pose_blocks > 2147483647LL) return fail(PSDF_ERR_CAPACITY, "too many poses for one launch");
     // aim for about 32 CTAs per SM in total (several waves of resident CTAs)
