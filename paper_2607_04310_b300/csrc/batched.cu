@@ -39,8 +39,9 @@ constexpr int kPlanMaxThreads = 256;
 constexpr int kPlanMaxTilesPerItem = 64;
 // A footprint laid out as the shared-memory records of FootprintS.
 struct FootprintRec {
-  float4 rec[2 * kMaxM];  // {vx, vy, ex, ey}, {inv_e2, nx, ny, 0} per robot vertex
-  float2 ivl[kMaxM];      // {alo, ahi}
+  float4 rec[2 * kMaxM];        // {vx, vy, ex, ey}, {inv_e2, nx, ny, 0} per robot vertex
+  float4 pair[4 * (kMaxM / 2)];  // vertex pairs for the paired edge step (FootprintS)
+  float2 ivl[kMaxM];            // {alo, ahi}
   int m;
   int pad[3];
 };
@@ -188,7 +189,7 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
 #define PSDF_FOR_EACH_M(X) \
   X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
-__global__ void __launch_bounds__(kPlanMaxThreads)
+__global__ void __launch_bounds__(kPlanMaxThreads, 2)
     batched_kernel(const PlanItem *__restrict__ items, int n_items,
                    const PlanBlock *__restrict__ blocks, const FootprintRec *__restrict__ fps,
                    float eps_sat, const float *__restrict__ poses,
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   FootprintRec *Fs = reinterpret_cast<FootprintRec *>(smem + kPlanSmemHead);
-  const FootprintS Fv{Fs->rec, Fs->ivl};
+  const FootprintS Fv{Fs->rec, Fs->ivl, Fs->pair};
   unsigned char *buf0 = smem + kPlanSmemHead + kFpBytes;
   __shared__ int s_item;
   if (threadIdx.x == 0) {
@@ -708,6 +709,13 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
       r.rec[2 * l] = make_float4(F.vx[l], F.vy[l], F.ex[l], F.ey[l]);
       r.rec[2 * l + 1] = make_float4(F.inv_e2[l], F.nx[l], F.ny[l], 0.f);
       r.ivl[l] = make_float2(F.alo[l], F.ahi[l]);
+    }
+    for (int q = 0; q < F.m / 2; ++q) {
+      const int a = 2 * q, b = 2 * q + 1;
+      r.pair[4 * q] = make_float4(F.vx[a], F.vx[b], F.vy[a], F.vy[b]);
+      r.pair[4 * q + 1] = make_float4(F.ex[a], F.ex[b], F.ey[a], F.ey[b]);
+      r.pair[4 * q + 2] = make_float4(-F.inv_e2[a], -F.inv_e2[b], F.nx[a], F.nx[b]);
+      r.pair[4 * q + 3] = make_float4(F.ny[a], F.ny[b], 0.f, 0.f);
     }
     r.m = F.m;
   }

@@ -127,6 +127,21 @@ __device__ __forceinline__ float2 robot_interval(const FootprintK &F, int l)
   return make_float2(F.alo[l], F.ahi[l]);
 }
 
+// The constants of robot vertices 2q and 2q + 1 as pairs, for the paired
+// FP32 instructions of the edge step (inv_e2 negated).
+struct RobotL2 {
+  float2 vx, vy, ex, ey, nie, nx, ny;
+};
+
+__device__ __forceinline__ RobotL2 robot_l2(const FootprintK &F, int q)
+{
+  const int a = 2 * q, b = 2 * q + 1;
+  return RobotL2{make_float2(F.vx[a], F.vx[b]),          make_float2(F.vy[a], F.vy[b]),
+                 make_float2(F.ex[a], F.ex[b]),          make_float2(F.ey[a], F.ey[b]),
+                 make_float2(-F.inv_e2[a], -F.inv_e2[b]), make_float2(F.nx[a], F.nx[b]),
+                 make_float2(F.ny[a], F.ny[b])};
+}
+
 // A footprint staged in shared memory as records (one per robot vertex:
 // {vx, vy, ex, ey}, {inv_e2, nx, ny, 0}; intervals {alo, ahi}), for kernels
 // whose CTAs change footprint from one work item to the next.  The loads are
@@ -134,8 +149,10 @@ __device__ __forceinline__ float2 robot_interval(const FootprintK &F, int l)
 // robot vertex and edge) instead of the compiler holding all constants of a
 // large footprint in registers across the obstacle loop.
 struct FootprintS {
-  const float4 *rec;  // [2 * m]
-  const float2 *ivl;  // [m]
+  const float4 *rec;   // [2 * m]
+  const float2 *ivl;   // [m]
+  const float4 *pair;  // [4 * (m / 2)]: {vx, vx', vy, vy'}, {ex, ex', ey, ey'},
+                       // {-inv_e2, -inv_e2', nx, nx'}, {ny, ny', 0, 0}
 };
 
 __device__ __forceinline__ float4 lds_f4(const float4 *p)
@@ -167,13 +184,61 @@ __device__ __forceinline__ float2 robot_interval(const FootprintS &F, int l)
   return lds_f2(F.ivl + l);
 }
 
+__device__ __forceinline__ RobotL2 robot_l2(const FootprintS &F, int q)
+{
+  const float4 a = lds_f4(F.pair + 4 * q), b = lds_f4(F.pair + 4 * q + 1);
+  const float4 c = lds_f4(F.pair + 4 * q + 2), d = lds_f4(F.pair + 4 * q + 3);
+  return RobotL2{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                 make_float2(b.z, b.w), make_float2(c.x, c.y), make_float2(c.z, c.w),
+                 make_float2(d.x, d.y)};
+}
+
 // ---------------------------------------------------------------------------
 // value-only evaluation of one obstacle (the scan's inner loop)
 // ---------------------------------------------------------------------------
+// One robot vertex against the edge A -> B (local frame): the distance from
+// the vertex to the edge (Sec. IV-B d_v), from the edge's start vertex A to
+// the robot edge (d_e), the vertex's offset on the edge axis (smin/smax)
+// and A's projection on the robot axis (pmax/pmin).
+template <bool SEG>
+__device__ __forceinline__ void vertex_step(const RobotL &r, V2 A, V2 B, float ux, float uy,
+                                            float inv_len2, float &smin, float &smax,
+                                            float &d2min, float &pmax_l, float &pmin_l)
+{
+  // robot vertex l -> obstacle edge: t = clamp((v - A).u / (|u|^2 + eps))
+  const float wx = __fsub_rn(r.vx, A.x), wy = __fsub_rn(r.vy, A.y);
+  const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), inv_len2));
+  float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
+  if (SEG) {
+    // a segment's far endpoint is its own vertex: use it exactly
+    rx = (t == 1.0f) ? __fsub_rn(r.vx, B.x) : rx;
+    ry = (t == 1.0f) ? __fsub_rn(r.vy, B.y) : ry;
+  }
+  const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+  // robot vertex projected on rot90(u), measured from A (obstacle axis)
+  const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+  smin = fminf(smin, sl);
+  smax = fmaxf(smax, sl);
+  // obstacle vertex A -> robot edge l, t' = clamp((A - v).e / (|e|^2 + eps))
+  const float tp = __saturatef(__fmul_rn(-__fmaf_rn(wx, r.ex, __fmul_rn(wy, r.ey)), r.inv_e2));
+  const float qx = __fmaf_rn(tp, r.ex, wx), qy = __fmaf_rn(tp, r.ey, wy);
+  const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+  d2min = fminf(d2min, fminf(d2, d2p));
+  // obstacle vertex A on the robot axis n_l
+  const float pr = __fmaf_rn(A.x, r.nx, __fmul_rn(A.y, r.ny));
+  pmax_l = fmaxf(pmax_l, pr);
+  pmin_l = fminf(pmin_l, pr);
+}
+
 // One edge of a closed polygon, from A (= vertex k, local) to B (= vertex
 // k+1, local).  Accumulates: d2min (squared separation, Sec. IV-B), the
-// obstacle's projections on the robot axes (pmax/pmin, Sec. IV-C) and the
-// overlap on this edge's own axis.
+// obstacle's projections on the robot axes (pmax/pmin, Sec. IV-C) and
+// returns the overlap on this edge's own axis.  Robot vertices are taken in
+// pairs on Blackwell's paired FP32 instructions (fma/add/mul .f32x2: two
+// operations per issue slot; the clamps and minima stay scalar).  Every
+// paired operation is the single-vertex operation with the same operands
+// (a - b as a + (-b), -x * y as x * (-y)), so the results carry the same bits
+// as vertex_step.
 template <int M, bool SEG, class FP>
 __device__ __forceinline__ float edge_step(const FP &F, V2 A, V2 B, float inv_len2,
                                            float inv_len, float alpha_p, float beta_p,
@@ -181,33 +246,44 @@ __device__ __forceinline__ float edge_step(const FP &F, V2 A, V2 B, float inv_le
 {
   const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
   float smin = kInf, smax = -kInf;
+  const float2 nax = make_float2(-A.x, -A.x), nay = make_float2(-A.y, -A.y);
+  const float2 ax2 = make_float2(A.x, A.x), ay2 = make_float2(A.y, A.y);
+  const float2 ux2 = make_float2(ux, ux), uy2 = make_float2(uy, uy);
+  const float2 nux2 = make_float2(-ux, -ux), nuy2 = make_float2(-uy, -uy);
+  const float2 il2 = make_float2(inv_len2, inv_len2);
 #pragma unroll
-  for (int l = 0; l < M; ++l) {
-    const RobotL r = robot_l(F, l);
-    // robot vertex l -> obstacle edge: t = clamp((v - A).u / (|u|^2 + eps))
-    const float wx = __fsub_rn(r.vx, A.x), wy = __fsub_rn(r.vy, A.y);
-    const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), inv_len2));
-    float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
+  for (int q = 0; q < M / 2; ++q) {
+    const RobotL2 r = robot_l2(F, q);
+    const float2 wx = __fadd2_rn(r.vx, nax), wy = __fadd2_rn(r.vy, nay);
+    const float2 tt = __fmul2_rn(__ffma2_rn(wx, ux2, __fmul2_rn(wy, uy2)), il2);
+    const float2 t = make_float2(__saturatef(tt.x), __saturatef(tt.y));
+    float2 rx = __ffma2_rn(t, nux2, wx), ry = __ffma2_rn(t, nuy2, wy);
     if (SEG) {
-      // a segment's far endpoint is its own vertex: use it exactly
-      rx = (t == 1.0f) ? __fsub_rn(r.vx, B.x) : rx;
-      ry = (t == 1.0f) ? __fsub_rn(r.vy, B.y) : ry;
+      const float2 bx = __fadd2_rn(r.vx, make_float2(-B.x, -B.x));
+      const float2 by = __fadd2_rn(r.vy, make_float2(-B.y, -B.y));
+      rx.x = (t.x == 1.0f) ? bx.x : rx.x;
+      rx.y = (t.y == 1.0f) ? bx.y : rx.y;
+      ry.x = (t.x == 1.0f) ? by.x : ry.x;
+      ry.y = (t.y == 1.0f) ? by.y : ry.y;
     }
-    const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
-    // robot vertex projected on rot90(u), measured from A (obstacle axis)
-    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
-    smin = fminf(smin, sl);
-    smax = fmaxf(smax, sl);
-    // obstacle vertex A -> robot edge l, t' = clamp((A - v).e / (|e|^2 + eps))
-    const float tp = __saturatef(__fmul_rn(-__fmaf_rn(wx, r.ex, __fmul_rn(wy, r.ey)), r.inv_e2));
-    const float qx = __fmaf_rn(tp, r.ex, wx), qy = __fmaf_rn(tp, r.ey, wy);
-    const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
-    d2min = fminf(d2min, fminf(d2, d2p));
-    // obstacle vertex A on the robot axis n_l
-    const float pr = __fmaf_rn(A.x, r.nx, __fmul_rn(A.y, r.ny));
-    pmax[l] = fmaxf(pmax[l], pr);
-    pmin[l] = fminf(pmin[l], pr);
+    const float2 d2 = __ffma2_rn(rx, rx, __fmul2_rn(ry, ry));
+    const float2 sl = __ffma2_rn(wy, ux2, __fmul2_rn(wx, nuy2));
+    smin = fminf(smin, fminf(sl.x, sl.y));
+    smax = fmaxf(smax, fmaxf(sl.x, sl.y));
+    const float2 tq = __fmul2_rn(__ffma2_rn(wx, r.ex, __fmul2_rn(wy, r.ey)), r.nie);
+    const float2 tp = make_float2(__saturatef(tq.x), __saturatef(tq.y));
+    const float2 qx = __ffma2_rn(tp, r.ex, wx), qy = __ffma2_rn(tp, r.ey, wy);
+    const float2 d2p = __ffma2_rn(qx, qx, __fmul2_rn(qy, qy));
+    d2min = fminf(d2min, fminf(fminf(d2.x, d2p.x), fminf(d2.y, d2p.y)));
+    const float2 pr = __ffma2_rn(ax2, r.nx, __fmul2_rn(ay2, r.ny));
+    pmax[2 * q] = fmaxf(pmax[2 * q], pr.x);
+    pmax[2 * q + 1] = fmaxf(pmax[2 * q + 1], pr.y);
+    pmin[2 * q] = fminf(pmin[2 * q], pr.x);
+    pmin[2 * q + 1] = fminf(pmin[2 * q + 1], pr.y);
   }
+  if (M & 1)
+    vertex_step<SEG>(robot_l(F, M - 1), A, B, ux, uy, inv_len2, smin, smax, d2min, pmax[M - 1],
+                     pmin[M - 1]);
   // overlap on this edge's axis: obstacle interval [alpha', beta'] vs the
   // robot interval [smin, smax] / (|u| + eps)
   const float da = __fmaf_rn(-smin, inv_len, beta_p);
