@@ -90,6 +90,15 @@ def _csr_from_polygons(polys: Sequence[np.ndarray]) -> Tuple[np.ndarray, np.ndar
     return edges, offs
 
 
+def regular_polygons(centres: Sequence[Tuple[float, float]], ks: Sequence[int],
+                     radii: Sequence[float]) -> Tuple[np.ndarray, np.ndarray]:
+    """Regular k-gons (CCW) at the given centres, as CSR edges; closure is
+    exact (B of an edge is the next edge's A bit for bit)."""
+    polys = [(footprint_regular(k, r).astype(np.float64) + np.asarray(c)).astype(F32)
+             for c, k, r in zip(centres, ks, radii)]
+    return _csr_from_polygons(polys)
+
+
 def rects(g: np.random.Generator, n: int, side_lo: float, side_hi: float,
           field_lo: float, field_hi: float,
           field_hi_y: Optional[float] = None) -> Tuple[np.ndarray, np.ndarray]:
