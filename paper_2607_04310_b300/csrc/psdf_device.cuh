@@ -41,6 +41,20 @@ __device__ __forceinline__ V2 to_local(float X, float Y, float px, float py, flo
   return r;
 }
 
+// Edge vector B - A in the robot frame, rotated from the world-frame
+// difference (exact or nearly so in FP32 for the endpoints of one edge)
+// instead of taken between the two rotated endpoints: their rounding, about
+// an ulp of their distance from the pose, would otherwise dominate the
+// direction of a short edge (and the obstacle-axis overlaps built on it).
+__device__ __forceinline__ V2 local_edge(float ax, float ay, float bx, float by, float c, float s)
+{
+  const float dx = __fsub_rn(bx, ax), dy = __fsub_rn(by, ay);
+  V2 r;
+  r.x = __fmaf_rn(c, dx, __fmul_rn(s, dy));
+  r.y = __fmaf_rn(c, dy, -__fmul_rn(s, dx));
+  return r;
+}
+
 // Total order on float values as unsigned bits (-0 is folded onto +0 first
 // so that the order matches IEEE comparison).
 __device__ __forceinline__ uint32_t ordered_bits(float v)
@@ -240,11 +254,11 @@ __device__ __forceinline__ void vertex_step(const RobotL &r, V2 A, V2 B, float u
 // (a - b as a + (-b), -x * y as x * (-y)), so the results carry the same bits
 // as vertex_step.
 template <int M, bool SEG, class FP>
-__device__ __forceinline__ float edge_step(const FP &F, V2 A, V2 B, float inv_len2,
+__device__ __forceinline__ float edge_step(const FP &F, V2 A, V2 B, V2 U, float inv_len2,
                                            float inv_len, float alpha_p, float beta_p,
                                            float (&pmax)[M], float (&pmin)[M], float &d2min)
 {
-  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+  const float ux = U.x, uy = U.y;
   float smin = kInf, smax = -kInf;
   const float2 nax = make_float2(-A.x, -A.x), nay = make_float2(-A.y, -A.y);
   const float2 ax2 = make_float2(A.x, A.x), ay2 = make_float2(A.y, A.y);
@@ -333,7 +347,9 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
   const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
   if (n == 1) {
     const V2 B0 = to_local(b0.z, b0.w, px, py, c, s);
-    const float de = edge_step<M, true>(F, A0, B0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min);
+    const V2 U0 = local_edge(a0.x, a0.y, b0.z, b0.w, c, s);
+    const float de =
+        edge_step<M, true>(F, A0, B0, U0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min);
     dlt = fminf(dlt, de);
     if (SOFT) acc.add(de, eta);
     extra_vertex<M>(F, B0, pmax, pmin, d2min);
@@ -348,8 +364,9 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
         bnx = vt[2 * (k + 1) + 1];
         Anx = to_local(anx.x, anx.y, px, py, c, s);
       }
-      const float de =
-          edge_step<M, false>(F, Acur, Anx, acur.z, acur.w, bcur.x, bcur.y, pmax, pmin, d2min);
+      const V2 U = local_edge(acur.x, acur.y, anx.x, anx.y, c, s);
+      const float de = edge_step<M, false>(F, Acur, Anx, U, acur.z, acur.w, bcur.x, bcur.y, pmax,
+                                           pmin, d2min);
       dlt = fminf(dlt, de);
       if (SOFT) acc.add(de, eta);
       Acur = Anx;
@@ -418,15 +435,23 @@ __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px,
     const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
     const V2 A = (k == 0) ? A0 : to_local(ak4.x, ak4.y, px, py, c, s);
     V2 B;
+    float bwx, bwy;  // world B
     if (seg) {
+      bwx = b0.z;
+      bwy = b0.w;
       B = to_local(b0.z, b0.w, px, py, c, s);
     } else if (k + 1 < n) {
       const float4 an = vt[2 * (k + 1)];
+      bwx = an.x;
+      bwy = an.y;
       B = to_local(an.x, an.y, px, py, c, s);
     } else {
+      bwx = a0.x;
+      bwy = a0.y;
       B = A0;
     }
-    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const V2 U = local_edge(ak4.x, ak4.y, bwx, bwy, c, s);
+    const float ux = U.x, uy = U.y;
     const int edge = orig_first + k;
     float smin = kInf, smax = -kInf;
     int lsmin = 0, lsmax = 0;
@@ -593,7 +618,8 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
   if (kind == kVertEdge) {
     const V2 Aw = worldA(k), Bw = worldB(k);
     const V2 A = to_local(Aw.x, Aw.y, px, py, c, s), B = to_local(Bw.x, Bw.y, px, py, c, s);
-    const float ux = sub(B.x, A.x), uy = sub(B.y, A.y);
+    const V2 U = local_edge(Aw.x, Aw.y, Bw.x, Bw.y, c, s);
+    const float ux = U.x, uy = U.y;
     float rx, ry;
     if (t == 1.0f) { rx = sub(lvx, B.x); ry = sub(lvy, B.y); }
     else { rx = sub(sub(lvx, A.x), mul(t, ux)); ry = sub(sub(lvy, A.y), mul(t, uy)); }
@@ -675,13 +701,14 @@ __device__ __forceinline__ float active_overlap(const FootprintK &F, float px, f
   }
   const float4 ak = vt[2 * k], bk = vt[2 * k + 1];
   const V2 A = to_local(ak.x, ak.y, px, py, c, s);
-  V2 B;
-  if (seg) B = to_local(bk.z, bk.w, px, py, c, s);
-  else {
+  float bwx = bk.z, bwy = bk.w;
+  if (!seg) {
     const float4 an = vt[2 * ((k + 1) % n)];
-    B = to_local(an.x, an.y, px, py, c, s);
+    bwx = an.x;
+    bwy = an.y;
   }
-  const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+  const V2 U = local_edge(ak.x, ak.y, bwx, bwy, c, s);
+  const float ux = U.x, uy = U.y;
   float smin = kInf, smax = -kInf;
 #pragma unroll
   for (int q = 0; q < M; ++q) {
@@ -706,13 +733,14 @@ __device__ __forceinline__ float active_t(const FootprintK &F, float px, float p
   if (kind == kVertEdge) {
     const float4 ak = vt[2 * k];
     const V2 A = to_local(ak.x, ak.y, px, py, c, s);
-    V2 B;
-    if (seg) B = to_local(vt[1].z, vt[1].w, px, py, c, s);
-    else {
+    float bwx = vt[1].z, bwy = vt[1].w;
+    if (!seg) {
       const float4 an = vt[2 * ((k + 1) % n)];
-      B = to_local(an.x, an.y, px, py, c, s);
+      bwx = an.x;
+      bwy = an.y;
     }
-    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const V2 U = local_edge(ak.x, ak.y, bwx, bwy, c, s);
+    const float ux = U.x, uy = U.y;
     const float wx = __fsub_rn(vx, A.x), wy = __fsub_rn(vy, A.y);
     return __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak.z));
   }
@@ -750,15 +778,23 @@ __device__ __forceinline__ void soft_grad(const FootprintK &F, float px, float p
     const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
     const V2 A = (k == 0) ? A0 : to_local(ak4.x, ak4.y, px, py, c, s);
     V2 B;
+    float bwx, bwy;  // world B
     if (seg) {
+      bwx = b0.z;
+      bwy = b0.w;
       B = to_local(b0.z, b0.w, px, py, c, s);
     } else if (k + 1 < n) {
       const float4 an = vt[2 * (k + 1)];
+      bwx = an.x;
+      bwy = an.y;
       B = to_local(an.x, an.y, px, py, c, s);
     } else {
+      bwx = a0.x;
+      bwy = a0.y;
       B = A0;
     }
-    const float ux = __fsub_rn(B.x, A.x), uy = __fsub_rn(B.y, A.y);
+    const V2 U = local_edge(ak4.x, ak4.y, bwx, bwy, c, s);
+    const float ux = U.x, uy = U.y;
     float smin = kInf, smax = -kInf;
     int lsmin = 0, lsmax = 0;
 #pragma unroll
