@@ -6,10 +6,12 @@
 One step = one pass of the value+gradient path over the dense-clutter
 workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
 100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
-the exact tile cull with the learned proposal (spatial pose sort, network
-scores on tensor cores, exact evaluation of the proposed tiles, lower-bound
-fallback, epilogue with the pose gradient) followed by PSDF_Backward (pose
-and edge-endpoint gradients of sum(phi)).  The metric counts pose x edge
+the exact tile cull with the learned proposal (bound ranking, network
+re-rank on tensor cores, an upper bound from the proposed tiles' obstacle
+circles, every tile whose lower bound does not exceed it listed, one exact
+pass over the listed pairs skipping obstacles by their circle bound, the
+epilogue with the pose gradient) followed by PSDF_Backward (pose and
+edge-endpoint gradients of sum(phi)).  The metric counts pose x edge
 pairs of the whole scene per second (the cull's results equal the full
 scan's bit for bit, checked in the run); the full scan and the bound-ordered
 cull are timed on the same GPU for the speedup.
@@ -516,7 +518,7 @@ def run_b300(a, rank, world, local):
     torch.cuda.synchronize()
     psdf.psdf_profile_enable(False)
     prof = {k: psdf.psdf_profile_read(k) for k in
-            ("propose", "cull_eval", "fallback", "epilogue", "backward")}
+            ("propose", "cull_eval", "epilogue", "backward")}
     psdf.psdf_profile_reset()
     st = psdf.psdf_cull_stats_read(cws, stream)
 
@@ -584,13 +586,13 @@ def run_b300(a, rank, world, local):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = roofline.fp32_peak_tflops(props.multi_processor_count, sm_max)
     items = int(st.proposed_items + st.fallback_items)
-    flops_pose_all_tiles = roofline.flops_per_pose(m, w.offsets)
-    flops_step = items * flops_pose_all_tiles / T
+    # the obstacles the cull evaluated exactly (circle-bound skips excluded)
+    flops_step = roofline.flops_evaluated(m, st.evaluated_edges, st.evaluated_obstacles)
     n_ev, ev_ms = prof["cull_eval"]
     achieved = flops_step * a.steps / (ev_ms / 1000.0) / 1e12  # prof covers a.steps eager steps
-    evaluated_pairs = items * (w.E / T)
-    # init, score, re-rank, scan, eval, fallback pairs, scan, eval, epilogue, backward
-    launches_per_step = 10
+    evaluated_pairs = float(st.evaluated_edges)  # pose x edge pairs evaluated exactly
+    # propose, eval_lists, epilogue, backward (plus one memset node)
+    launches_per_step = 4
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -610,6 +612,8 @@ def run_b300(a, rank, world, local):
                        "fallback_rate": st_bound.fallback_poses / P},
         "cull": {"candidate_fraction": st.proposed_items / (P * T),
                  "evaluated_fraction": items / (P * T),
+                 "evaluated_obstacles": int(st.evaluated_obstacles),
+                 "evaluated_edges": int(st.evaluated_edges),
                  "fallback_rate": st.fallback_poses / P,
                  "proposed_pairs": int(st.proposed_items),
                  "fallback_pairs": int(st.fallback_items),

@@ -209,15 +209,17 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
  * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
  * conservative bound below (PSDF_PROPOSE_BOUND), or (PSDF_PROPOSE_MLP) by the
  * tile-proposal network's predicted signed distance among the 8 tiles with
- * the smallest bounds -- and those pairs are evaluated exactly.  Then, for every tile the pose did not propose, a
+ * the smallest bounds.  The circles containing the proposed tiles'
+ * obstacles give an upper bound UB >= phi; every other tile whose
  * conservative lower bound
  *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
- * on the signed distance of every obstacle in the tile is compared with the
- * pose's current minimum; the pair is evaluated ("fallback") unless LB
- * exceeds it.  No skipped pair can hold a smaller value or a tie, so phi,
- * the active pair and the gradient equal the full scan's.  The network only
- * changes how much work the exact part does.  Pairs are bucketed by tile and
- * each tile is evaluated once for all the poses that need it. */
+ * does not exceed UB is added ("fallback" pairs).  All listed pairs are
+ * evaluated exactly in one pass, skipping obstacles whose circle bound
+ * exceeds the smaller of UB and the values already found.  No skipped tile
+ * or obstacle can hold a smaller value or a tie, so phi, the active pair and
+ * the gradient equal the full scan's.  The network only changes how much
+ * work the exact part does.  Pairs are bucketed by tile and each tile is
+ * staged once for all the poses that need it. */
 typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
 
 #define PSDF_MLP_IN 16
@@ -232,11 +234,11 @@ typedef struct {
 } psdf_cull_opts;
 
 typedef struct {
-  int64_t pose_blocks;    /* reserved (0)                                        */
-  int64_t tiles;          /* reserved (0)                                        */
-  int64_t proposed_items; /* (pose, tile) pairs evaluated from the proposals     */
-  int64_t fallback_items; /* (pose, tile) pairs added by the lower-bound check   */
-  int64_t fallback_poses; /* poses needing at least one tile beyond the proposal */
+  int64_t evaluated_obstacles; /* obstacles evaluated exactly (not skipped)       */
+  int64_t evaluated_edges;     /* their edges                                     */
+  int64_t proposed_items;      /* (pose, tile) pairs listed from the proposals    */
+  int64_t fallback_items;      /* (pose, tile) pairs added by the bound check     */
+  int64_t fallback_poses;      /* poses with at least one tile beyond the proposal */
 } psdf_cull_stats;
 
 /* Tile-proposal network: 16 inputs -> 64 ReLU units -> 1 output, FP16 weights

@@ -5,21 +5,22 @@
 //   1. propose         16 lanes per pose rank every tile by the conservative
 //                      bound; the pose keeps its K best, or its 8 best
 //                      re-ranked by the tile-proposal network on tensor cores
-//                      (K best kept); the pose is appended to each proposed
-//                      tile's list.  The CTA that finishes last turns the
-//                      per-tile counts into work units (prefix sum + unit map)
+//                      (K best kept).  From the circles of the proposed tiles'
+//                      obstacles the lanes take an upper bound UB on phi and
+//                      list the pose for the proposed tiles and for every other
+//                      tile whose lower bound does not exceed UB.  The CTA that
+//                      finishes last turns the per-tile counts into work units
 //   2. eval_lists      persistent CTAs over units: the tile's blob staged in shared
 //                      memory, lanes = (pose, obstacle range) pairs so that
-//                      warps stay full, exact evaluation, one atomicMin per
-//                      lane into the pose's 64-bit key
-//   3. fallback        16 lanes per pose append every tile the pose did not
-//                      propose whose lower bound does not exceed the pose's
-//                      current minimum; the last CTA builds the work units
-//   4. eval_lists      as 2, over the fallback pairs
-//   5. epilogue        as for the full scan
-// A skipped (pose, tile) pair holds only values strictly above the pose's
-// minimum, and the minimum over 64-bit keys does not depend on evaluation
-// order, so the result equals the full scan's bit for bit.
+//                      warps stay full; an obstacle whose circle bound exceeds
+//                      the lane's threshold (UB, then the smallest value seen)
+//                      is skipped, the others are evaluated exactly; one
+//                      atomicMin per lane into the pose's 64-bit key
+//   3. epilogue        as for the full scan
+// Every tile holding a value at or below phi has a lower bound <= phi <= UB,
+// so it is listed; every obstacle skipped has a value above the threshold,
+// which is never below phi.  The minimum over 64-bit keys does not depend on
+// evaluation order, so the result equals the full scan's bit for bit.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -50,16 +51,17 @@ constexpr int kMaxScanTiles = 1024 * 64;
 struct CullCounters {
   int err;
   int n_prop;          // proposed (pose, tile) pairs
-  int n_fb;            // fallback (pose, tile) pairs
-  int fallback_poses;  // poses with at least one fallback pair
+  int n_fb;            // (pose, tile) pairs added by the bound check
+  int fallback_poses;  // poses with at least one such pair
   unsigned done1;      // CTAs of the propose kernel that finished
-  unsigned done2;      // CTAs of the fallback kernel that finished
+  int n_items;         // all listed (pose, tile) pairs
+  unsigned long long n_obs_eval;   // obstacles evaluated exactly
+  unsigned long long n_edge_eval;  // edges of those obstacles
 };
 
 struct CullLayout {
-  size_t hist1, hist2, clear_bytes, keys, pose4, prop, uoff1, utile1, uoff2, utile2, list1,
-      list2, total;
-  long long cap1, cap2;  // capacity of the unit maps
+  size_t hist, clear_bytes, keys, pose4, ub, prop, uoff, utile, list, total;
+  long long cap;  // capacity of the unit map
 };
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -71,29 +73,24 @@ static long long unit_capacity(long long items, int n_tiles)
   return 3LL * n_tiles + items / 128 + 1;
 }
 
-// Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]),
-// so that proposals and fallback pairs are appended in one pass.  The
-// counters and both per-tile histograms are contiguous (one memset).
+// Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]).
+// The counters and the per-tile histogram are contiguous (one memset).
 static CullLayout cull_layout(long long P, int n_tiles)
 {
   CullLayout L;
   const size_t Pz = (size_t)std::max<long long>(P, 1);
   const size_t Tz = (size_t)std::max(n_tiles, 1);
-  L.cap1 = unit_capacity((long long)Pz * kMaxK, (int)Tz);
-  L.cap2 = unit_capacity((long long)Pz * Tz, (int)Tz);
+  L.cap = unit_capacity((long long)Pz * Tz, (int)Tz);
   size_t o = 256;
-  L.hist1 = o; o = align256(o + 4 * Tz);
-  L.hist2 = o; o = align256(o + 4 * Tz);
+  L.hist = o; o = align256(o + 4 * Tz);
   L.clear_bytes = o;
   L.keys = o; o = align256(o + 8 * Pz);
   L.pose4 = o; o = align256(o + 16 * Pz);
+  L.ub = o; o = align256(o + 4 * Pz);
   L.prop = o; o = align256(o + 4 * Pz * kMaxK);
-  L.uoff1 = o; o = align256(o + 4 * (Tz + 1));
-  L.utile1 = o; o = align256(o + 4 * (size_t)L.cap1);
-  L.uoff2 = o; o = align256(o + 4 * (Tz + 1));
-  L.utile2 = o; o = align256(o + 4 * (size_t)L.cap2);
-  L.list1 = o; o = align256(o + 4 * Pz * Tz);
-  L.list2 = o; o = align256(o + 4 * Pz * Tz);
+  L.uoff = o; o = align256(o + 4 * (Tz + 1));
+  L.utile = o; o = align256(o + 4 * (size_t)L.cap);
+  L.list = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
   return L;
 }
@@ -115,12 +112,29 @@ __device__ __forceinline__ float tile_lb(const float *ab, float px, float py, fl
   return (d - rfoot) - (1e-4f + 1e-5f * d);
 }
 
-// The same bound in the min-key value domain (squared separation, or -inf
-// when the tile may touch the footprint).
-__device__ __forceinline__ float tile_lb_value(const float *ab, float px, float py, float rfoot)
+// Bounds from an obstacle's circle {cx, cy, r}: its signed distance to the
+// posed footprint lies in [|p - C| - r - r_foot, |p - C| + r + r_foot]
+// (every footprint point is within r_foot of p, every obstacle point within r
+// of C), each widened by the bound's margin.
+__device__ __forceinline__ float circle_ub(float4 cc, float px, float py, float rfoot)
 {
-  const float lb = tile_lb(ab, px, py, rfoot);
+  const float dx = cc.x - px, dy = cc.y - py;
+  const float d = sqrtf(dx * dx + dy * dy);
+  return (d + cc.z + rfoot) + (1e-4f + 1e-5f * d);
+}
+
+__device__ __forceinline__ float circle_lb_value(float4 cc, float px, float py, float rfoot)
+{
+  const float dx = cc.x - px, dy = cc.y - py;
+  const float d = sqrtf(dx * dx + dy * dy);
+  const float lb = (d - cc.z - rfoot) - (1e-4f + 1e-5f * d);
   return lb > 0.f ? lb * lb * (1.f - 1e-6f) : -kInf;
+}
+
+// An upper bound (metres) in the min-key value domain (d^2 when positive).
+__device__ __forceinline__ float ub_value(float ub)
+{
+  return ub > 0.f ? ub * ub * (1.f + 1e-6f) : ub;
 }
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi)
@@ -414,19 +428,25 @@ __device__ __forceinline__ float4 tile_aabb(const TileHdr *__restrict__ tiles, i
 // the pose's 16 lanes).  With NET the 16 rows (2 poses x kPre candidates)
 // are scored by the network and the pose keeps its K best scores; else its
 // K best bounds.  Lane 0 of each pose appends the pose to its proposed tiles.
+// The pose's 16 lanes then take an upper bound on phi from the circles of
+// the proposed tiles' obstacles, and append the pose to every other tile
+// whose bound does not exceed it; the CTA that finishes last builds the work
+// units of all listed pairs.
 template <int K, bool NET>
 __global__ void __launch_bounds__(kPoseThreads)
     propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
-            int T, float rfoot, const uint32_t *__restrict__ frag, float b2,
-            unsigned long long *__restrict__ keys, float4 *__restrict__ pose4,
-            int *__restrict__ prop, int *hist, int *__restrict__ list, int *__restrict__ uoff,
-            int *__restrict__ utile, CullCounters *ctr)
+            int T, float rfoot, const unsigned char *__restrict__ blob,
+            const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
+            float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
+            int *hist, int *__restrict__ list, int *__restrict__ uoff, int *__restrict__ utile,
+            CullCounters *ctr)
 {
   constexpr int R = NET ? kPre : K;
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
   __shared__ float4 ab_s[kStageTiles];
   __shared__ float ef_s[NET ? kStageTiles : 1];
+  __shared__ int s_prop, s_fb, s_fbp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
   const int half = lane >> 4, hl = lane & 15;
@@ -449,6 +469,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     sc[i] = kInf;
     id[i] = -1;
   }
+  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = 0;
   for (int t0 = 0; t0 < T; t0 += kStageTiles) {
     const int n = min(kStageTiles, T - t0);
     __syncthreads();
@@ -464,6 +485,10 @@ __global__ void __launch_bounds__(kPoseThreads)
         topk_insert<R>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
       }
   }
+  int best[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) best[i] = -1;
+  float ubp = kInf;  // upper bound (metres) on the pose's phi
   if (pw < P) {  // uniform over the warp
     // R rounds of a 16-lane argmin with pop
     int cand[R];
@@ -493,7 +518,6 @@ __global__ void __launch_bounds__(kPoseThreads)
         id[R - 1] = -1;
       }
     }
-    int best[K];
     if constexpr (NET) {
       if (hl == 0)
 #pragma unroll
@@ -544,16 +568,69 @@ __global__ void __launch_bounds__(kPoseThreads)
       for (int i = 0; i < K; ++i) best[i] = cand[i];
     }
     if (valid && hl == 0) {
+      int n = 0;
 #pragma unroll
       for (int i = 0; i < K; ++i) {
         prop[p * kMaxK + i] = best[i];
-        if (best[i] >= 0) list[(long long)best[i] * P + atomicAdd(&hist[best[i]], 1)] = (int)p;
+        if (best[i] >= 0) {
+          list[(long long)best[i] * P + atomicAdd(&hist[best[i]], 1)] = (int)p;
+          ++n;
+        }
       }
 #pragma unroll
       for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
+      atomicAdd(&s_prop, n);
     }
+    // upper bound on phi from the proposed tiles' obstacle circles (16 lanes)
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if (best[i] < 0) continue;  // uniform over the pose's lanes
+      const TileHdr h = tiles[best[i]];
+      const float4 *circ = reinterpret_cast<const float4 *>(blob + h.blob_off + h.blob_bytes);
+      for (int o = hl; o < h.n_obs; o += 16)
+        ubp = fminf(ubp, circle_ub(__ldg(circ + o), px, py, rfoot));
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) ubp = fminf(ubp, __shfl_xor_sync(0xffffffffu, ubp, o));
+    if (valid && hl == 0) ub_out[p] = ubp;
   }
-  if (last_cta(&ctr->done1)) build_units(hist, tiles, T, uoff, utile, &ctr->n_prop);
+  // every unproposed tile whose bound does not exceed the upper bound is
+  // listed too: no other tile can hold a value at or below phi
+  int ncand = 0;
+  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
+    const int n = min(kStageTiles, T - t0);
+    if (T > kStageTiles) {  // uniform: restage this chunk
+      __syncthreads();
+      stage_aabbs(tiles, t0, n, ab_s);
+      __syncthreads();
+    }
+    if (valid)
+      for (int i = hl; i < n; i += 16) {
+        const int t = t0 + i;
+        bool proposed = false;
+#pragma unroll
+        for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
+        const float4 a4 = ab_s[i];
+        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
+        if (!proposed && tile_lb(ab, px, py, rfoot) <= ubp) {
+          list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
+          ++ncand;
+        }
+      }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+  if (valid && hl == 0 && ncand > 0) {
+    atomicAdd(&s_fb, ncand);
+    atomicAdd(&s_fbp, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctr->n_prop, s_prop);
+    atomicAdd(&ctr->n_fb, s_fb);
+    atomicAdd(&ctr->fallback_poses, s_fbp);
+  }
+  if (last_cta(&ctr->done1)) build_units(hist, tiles, T, uoff, utile, &ctr->n_items);
 }
 
 // ---------------------------------------------------------------------------
@@ -575,18 +652,23 @@ __device__ __forceinline__ void cp_async_wait_all()
 // Persistent CTAs over work units.  Unit u belongs to tile t = utile[u] and
 // covers lanes [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane
 // l evaluates pose list[t * P + l / S] against obstacle range l % S of the
-// tile and merges its minimum into the pose's key.  The tile's blob is
-// staged in shared memory (16-byte cp.async per thread) once per unit.
+// tile and merges its minimum into the pose's key.  The tile's blob and its
+// obstacle circles are staged in shared memory (16-byte cp.async per thread)
+// once per unit.  An obstacle whose circle bound exceeds the lane's running
+// threshold -- the pose's upper bound, then the smallest value the lane has
+// evaluated -- cannot reach the pose's minimum and is skipped.
 template <int M>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
                const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
                const int *__restrict__ hist, const int *__restrict__ uoff,
                const int *__restrict__ utile, long long cap, const int *__restrict__ list,
-               unsigned long long *__restrict__ keys)
+               const float *__restrict__ ub, unsigned long long *__restrict__ keys,
+               CullCounters *ctr)
 {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int U = uoff[T];
+  unsigned long long n_obs = 0, n_edge = 0;
   for (int u = blockIdx.x; u < U && u < cap; u += gridDim.x) {
     const int t = utile[u];
     const TileHdr h = tiles[t];
@@ -595,8 +677,9 @@ __global__ void __launch_bounds__(kListThreads)
     const long long L = (long long)cnt * S;
     const long long l = (long long)(u - uoff[t]) * kListThreads + threadIdx.x;
     const unsigned char *src = blob + h.blob_off;
+    const int bytes = h.blob_bytes + 16 * h.n_obs;  // records + circles
     __syncthreads();  // the previous unit's reads of the staged tile are done
-    for (int o = 16 * threadIdx.x; o < h.blob_bytes; o += 16 * kListThreads)
+    for (int o = 16 * threadIdx.x; o < bytes; o += 16 * kListThreads)
       cp_async16(tsm + o, src + o);
     long long p = -1;
     if (l < L) p = list[(long long)t * P + l / S];
@@ -605,86 +688,37 @@ __global__ void __launch_bounds__(kListThreads)
     if (p >= 0) {
       const int4 *ob = reinterpret_cast<const int4 *>(tsm);
       const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
+      const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
       const int part = (int)(l % S);
       const float4 q4 = pose4[p];
       const float px = q4.x, py = q4.y, c = q4.z, s = q4.w;
+      float thr = ub_value(ub[p]);
       const int o0 = (int)((long long)h.n_obs * part / S);
       const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
       unsigned long long best = ~0ull;
       for (int o = o0; o < o1; ++o) {
+        if (circle_lb_value(circ[o], px, py, F.radius) > thr) continue;
         const int4 rec = ob[o];
         const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
         const unsigned long long key = pack_key(v, rec.z);
         best = key < best ? key : best;
+        thr = fminf(thr, v);
+        ++n_obs;
+        n_edge += rec.y;
       }
       if (best != ~0ull) atomicMin(&keys[p], best);
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// fallback: (pose, tile) pairs whose bound does not exceed the pose's minimum
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool fb_need(const float *ab, float px, float py, float rfoot,
-                                        float best, int t, const int (&pr)[kMaxK])
-{
-  bool proposed = false;
+  // evaluated obstacles and edges (the roofline's work count)
 #pragma unroll
-  for (int i = 0; i < kMaxK; ++i) proposed |= (pr[i] == t);
-  return !proposed && !(tile_lb_value(ab, px, py, rfoot) > best);
-}
-
-// 16 lanes per pose (two poses per warp) over the tiles: every unproposed
-// tile whose bound does not exceed the pose's current minimum gets the pose
-// appended to its list.  The last CTA builds the work units.
-__global__ void __launch_bounds__(kPoseThreads)
-    fallback(const float4 *__restrict__ pose4, long long P, const TileHdr *__restrict__ tiles,
-             int T, float rfoot, const unsigned long long *__restrict__ keys,
-             const int *__restrict__ prop, int *hist, int *__restrict__ list,
-             int *__restrict__ uoff, int *__restrict__ utile, CullCounters *ctr)
-{
-  __shared__ int n_poses;
-  __shared__ float4 ab_s[kStageTiles];
-  if (threadIdx.x == 0) n_poses = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
-  const int hl = lane & 15;
-  const long long p = pw + (lane >> 4);
-  const bool valid = p < P;
-  float4 q4 = make_float4(0.f, 0.f, 1.f, 0.f);
-  float best = kInf;
-  int pr[kMaxK];
-#pragma unroll
-  for (int i = 0; i < kMaxK; ++i) pr[i] = -1;
-  if (valid) {
-    q4 = pose4[p];
-    const unsigned long long key = keys[p];
-    best = (key == ~0ull) ? kInf : from_ordered_bits((uint32_t)(key >> 32));
-#pragma unroll
-    for (int i = 0; i < kMaxK; ++i) pr[i] = prop[p * kMaxK + i];
+  for (int o = 16; o > 0; o >>= 1) {
+    n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
+    n_edge += __shfl_xor_sync(0xffffffffu, n_edge, o);
   }
-  int n = 0;
-  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
-    const int nt = min(kStageTiles, T - t0);
-    __syncthreads();
-    stage_aabbs(tiles, t0, nt, ab_s);
-    __syncthreads();
-    if (valid)
-      for (int i = hl; i < nt; i += 16) {
-        const float4 a4 = ab_s[i];
-        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        if (fb_need(ab, q4.x, q4.y, rfoot, best, t0 + i, pr)) {
-          list[(long long)(t0 + i) * P + atomicAdd(&hist[t0 + i], 1)] = (int)p;
-          ++n;
-        }
-      }
+  if ((threadIdx.x & 31) == 0 && n_obs) {
+    atomicAdd(&ctr->n_obs_eval, n_obs);
+    atomicAdd(&ctr->n_edge_eval, n_edge);
   }
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-  if (valid && hl == 0 && n > 0) atomicAdd(&n_poses, 1);
-  __syncthreads();
-  if (threadIdx.x == 0 && n_poses) atomicAdd(&ctr->fallback_poses, n_poses);
-  if (last_cta(&ctr->done2)) build_units(hist, tiles, T, uoff, utile, &ctr->n_fb);
 }
 
 // ---------------------------------------------------------------------------
@@ -787,9 +821,10 @@ template <int M>
 struct ListEvalCall {
   static int run(const FootprintK &F, const ParamsK &pk, const float4 *pose4, long long P,
                  const psdf_scene *sc, const int *hist, const int *uoff, const int *utile,
-                 long long cap, const int *list, unsigned long long *keys, cudaStream_t st)
+                 long long cap, const int *list, const float *ub, unsigned long long *keys,
+                 CullCounters *ctr, cudaStream_t st)
   {
-    const size_t smem = (size_t)(sc->max_blob_bytes + 15) / 16 * 16;
+    const size_t smem = (size_t)(sc->max_blob_ext_bytes + 15) / 16 * 16;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(eval_lists<M>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -798,8 +833,8 @@ struct ListEvalCall {
     }
     const int grid = device_sms() * 8;
     eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, pose4, P, sc->d_tiles, sc->n_tiles,
-                                                   sc->d_blob, hist, uoff, utile, cap, list,
-                                                   keys);
+                                                   sc->d_blob, hist, uoff, utile, cap, list, ub,
+                                                   keys, ctr);
     return PSDF_OK;
   }
 };
@@ -1012,15 +1047,12 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   CullCounters *ctr = reinterpret_cast<CullCounters *>(ws);
   unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
   float4 *pose4 = reinterpret_cast<float4 *>(ws + L.pose4);
+  float *ub = reinterpret_cast<float *>(ws + L.ub);
   int *prop = reinterpret_cast<int *>(ws + L.prop);
-  int *hist1 = reinterpret_cast<int *>(ws + L.hist1);
-  int *hist2 = reinterpret_cast<int *>(ws + L.hist2);
-  int *uoff1 = reinterpret_cast<int *>(ws + L.uoff1);
-  int *uoff2 = reinterpret_cast<int *>(ws + L.uoff2);
-  int *utile1 = reinterpret_cast<int *>(ws + L.utile1);
-  int *utile2 = reinterpret_cast<int *>(ws + L.utile2);
-  int *list1 = reinterpret_cast<int *>(ws + L.list1);
-  int *list2 = reinterpret_cast<int *>(ws + L.list2);
+  int *hist = reinterpret_cast<int *>(ws + L.hist);
+  int *uoff = reinterpret_cast<int *>(ws + L.uoff);
+  int *utile = reinterpret_cast<int *>(ws + L.utile);
+  int *list = reinterpret_cast<int *>(ws + L.list);
   ParamsK pk{params->eps_sat, params->eta};
   cudaError_t e = cudaMemsetAsync(ws, 0, L.clear_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(cull counters)");
@@ -1035,15 +1067,15 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     const float b2 = net ? mlp->b2 : 0.f;
     {
       ProfileScope prof("propose", st);
-#define PSDF_PROPOSE(KK)                                                                       \
-  if (net)                                                                                     \
-    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,      \
-                                                   frag, b2, keys, pose4, prop, hist1, list1,  \
-                                                   uoff1, utile1, ctr);                        \
-  else                                                                                         \
-    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,     \
-                                                    frag, b2, keys, pose4, prop, hist1, list1, \
-                                                    uoff1, utile1, ctr);
+#define PSDF_PROPOSE(KK)                                                                     \
+  if (net)                                                                                   \
+    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,    \
+                                                   scene->d_blob, frag, b2, keys, pose4, ub, \
+                                                   prop, hist, list, uoff, utile, ctr);      \
+  else                                                                                       \
+    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,   \
+                                                    scene->d_blob, frag, b2, keys, pose4,    \
+                                                    ub, prop, hist, list, uoff, utile, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -1055,22 +1087,9 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
-                                         (const int *)hist1, (const int *)uoff1,
-                                         (const int *)utile1, L.cap1, (const int *)list1, keys,
-                                         st);
-      if (rc) return rc;
-    }
-    {
-      ProfileScope prof("fallback", st);
-      fallback<<<pb, kPoseThreads, 0, st>>>(pose4, P, scene->d_tiles, T, F.radius, keys, prop,
-                                            hist2, list2, uoff2, utile2, ctr);
-    }
-    {
-      ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
-                                         (const int *)hist2, (const int *)uoff2,
-                                         (const int *)utile2, L.cap2, (const int *)list2, keys,
-                                         st);
+                                         (const int *)hist, (const int *)uoff,
+                                         (const int *)utile, L.cap, (const int *)list,
+                                         (const float *)ub, keys, ctr, st);
       if (rc) return rc;
     }
   }
@@ -1088,8 +1107,8 @@ extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cu
   CullCounters c;
   e = cudaMemcpy(&c, workspace, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(cull counters)");
-  stats->pose_blocks = 0;
-  stats->tiles = 0;
+  stats->evaluated_obstacles = (int64_t)c.n_obs_eval;
+  stats->evaluated_edges = (int64_t)c.n_edge_eval;
   stats->proposed_items = c.n_prop;
   stats->fallback_items = c.n_fb;
   stats->fallback_poses = c.fallback_poses;

@@ -59,6 +59,9 @@ struct ParamsK {
 //                            b = {alpha', beta', Bx, By}
 // alpha', beta': the obstacle's interval on its own edge normal
 // rot90(u)/(|u|+eps_axis), measured from the edge's start A (pose-invariant).
+// blob_bytes covers these two parts; right after them follow
+//   float4 circ[n_obs]       {cx, cy, r, 0}: a circle containing the obstacle
+// which only the cull reads (blob_off of the next tile skips them).
 struct TileHdr {
   int blob_off;    // byte offset of the blob (16-byte aligned)
   int blob_bytes;  // multiple of 16
@@ -95,7 +98,8 @@ struct psdf_scene {
   int *d_far = nullptr;               // [n_edges] far vertex index within its obstacle
   size_t device_bytes = 0;
   // host copies used for launch configuration
-  int max_blob_bytes = 0;
+  int max_blob_bytes = 0;      // largest tile blob (obstacle + vertex records)
+  int max_blob_ext_bytes = 0;  // the same with the tile's obstacle circles
 };
 
 namespace psdf {
@@ -113,7 +117,7 @@ struct ObsIn {
 // own (psdf_scene) or one instance of a batched plan.
 struct HostScene {
   int64_t rows_total = 0, n_edges = 0;
-  int M = 0, T = 0, tile_edges = 0, max_n = 0, max_blob = 0;
+  int M = 0, T = 0, tile_edges = 0, max_n = 0, max_blob = 0, max_blob_ext = 0;
   float bb[4] = {0, 0, 0, 0};
   double eps_seg = 0, eps_axis = 0;
   std::vector<TileHdr> tiles;

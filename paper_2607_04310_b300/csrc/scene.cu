@@ -193,7 +193,7 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
   std::vector<ObsRec> row_obs(std::max<int64_t>(rows_total, 0), ObsRec{0, 0, 0, -1});
   std::vector<unsigned char> blob;
   int64_t vglob = 0;
-  int max_blob = 0;
+  int max_blob = 0, max_blob_ext = 0;
   for (int t = 0; t < T; ++t) {
     int s0 = tile_first[t], s1 = tile_first[t + 1];
     int nv = 0;
@@ -206,7 +206,9 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
     h.n_obs = nobs;
     h.n_vtx = nv;
     float ab[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
-    blob.resize(blob.size() + bytes);
+    // the blob, then one bounding circle per obstacle (read by the cull only)
+    blob.resize(blob.size() + bytes + 16 * nobs);
+    float4 *circ = (float4 *)(blob.data() + h.blob_off + bytes);
     int4 *ob = (int4 *)(blob.data() + h.blob_off);
     float4 *vb = (float4 *)(blob.data() + h.blob_off + 16 * nobs);
     int vloc = 0;
@@ -218,6 +220,24 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
         row_obs[o.first_row + k] = ObsRec{(int)vglob, o.n, (int)o.first_row, t};
       // obstacle vertex set: A of every edge, plus B for a segment
       const int nw = (o.n == 1) ? 2 : o.n;
+      {
+        // bounding circle: centre = vertex mean rounded to float, radius =
+        // farthest vertex from that centre (FP64), rounded up
+        double sx = 0.0, sy = 0.0;
+        for (int q = 0; q < nw; ++q) {
+          sx += (o.n == 1 && q == 1) ? (double)e[2] : (double)e[4 * q];
+          sy += (o.n == 1 && q == 1) ? (double)e[3] : (double)e[4 * q + 1];
+        }
+        const float cxf = (float)(sx / nw), cyf = (float)(sy / nw);
+        double r2 = 0.0;
+        for (int q = 0; q < nw; ++q) {
+          const double wx = ((o.n == 1 && q == 1) ? (double)e[2] : (double)e[4 * q]) - cxf;
+          const double wy = ((o.n == 1 && q == 1) ? (double)e[3] : (double)e[4 * q + 1]) - cyf;
+          r2 = std::max(r2, wx * wx + wy * wy);
+        }
+        const float rf = std::nextafter((float)std::sqrt(r2), INFINITY);
+        circ[s - s0] = make_float4(cxf, cyf, rf, 0.f);
+      }
       for (int k = 0; k < o.n; ++k) {
         double ax = e[4 * k], ay = e[4 * k + 1], bx = e[4 * k + 2], by = e[4 * k + 3];
         double ux = bx - ax, uy = by - ay;
@@ -253,6 +273,7 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
     std::memcpy(h.aabb, ab, sizeof(ab));
     tiles[t] = h;
     max_blob = std::max(max_blob, bytes);
+    max_blob_ext = std::max(max_blob_ext, bytes + 16 * nobs);
   }
 
   hs->rows_total = rows_total;
@@ -266,6 +287,7 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
   hs->eps_seg = eps_seg;
   hs->eps_axis = eps_axis;
   hs->max_blob = max_blob;
+  hs->max_blob_ext = max_blob_ext;
   hs->tiles.swap(tiles);
   hs->blob.swap(blob);
   hs->vtx.swap(vtx);
@@ -291,6 +313,7 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   s->eps_seg = (float)hs.eps_seg;
   s->eps_axis = (float)hs.eps_axis;
   s->max_blob_bytes = hs.max_blob;
+  s->max_blob_ext_bytes = hs.max_blob_ext;
   cudaGetDevice(&s->device);
   if (!rc) rc = dev_upload(&s->d_tiles, hs.tiles, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_blob, hs.blob, st, &s->device_bytes);

@@ -292,7 +292,7 @@ class CullOpts(ctypes.Structure):
 
 
 class CullStats(ctypes.Structure):
-    _fields_ = [("pose_blocks", ctypes.c_int64), ("tiles", ctypes.c_int64),
+    _fields_ = [("evaluated_obstacles", ctypes.c_int64), ("evaluated_edges", ctypes.c_int64),
                 ("proposed_items", ctypes.c_int64), ("fallback_items", ctypes.c_int64),
                 ("fallback_poses", ctypes.c_int64)]
 

@@ -36,6 +36,12 @@ def flops_per_pose(m: int, offsets) -> float:
     return f
 
 
+def flops_evaluated(m: int, n_edges: int, n_obstacles: int) -> float:
+    """Flops of the obstacles a cull evaluated exactly (closed polygons):
+    14 + 30 m per edge plus 2 m per obstacle."""
+    return float(n_edges) * (14 + 30 * m) + float(n_obstacles) * 2 * m
+
+
 def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
     """Dense FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sms * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12

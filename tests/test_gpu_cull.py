@@ -54,6 +54,10 @@ def test_cull_equals_full_scan_dense_clutter(mode, k):
         # the bound-ordered cull skips almost all (pose, tile) pairs; an
         # untrained network may propose badly (more fallback) but stays exact
         assert st.proposed_items + st.fallback_items < 0.05 * w.P * T
+    # inside the listed tiles most obstacles are skipped by their circle bound
+    obs_per_tile = w.M / T
+    assert 0 < st.evaluated_obstacles < 0.5 * (st.proposed_items + st.fallback_items) * obs_per_tile
+    assert st.evaluated_edges == 4 * st.evaluated_obstacles  # rectangles
 
 
 def test_cull_equals_full_scan_octagon_lidar_and_ragged():
