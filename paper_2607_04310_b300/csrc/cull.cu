@@ -385,13 +385,35 @@ __device__ __forceinline__ bool last_cta(unsigned *done)
   return last;
 }
 
-// Tile AABBs [t0, t0 + n) -> shared memory (independent loads, one latency).
-constexpr int kStageTiles = 2048;
+// Tile AABBs [t0, t0 + n) -> shared memory (independent loads, one latency);
+// with hdr_s also the first half of each header {blob_off, blob_bytes,
+// n_obs, n_vtx}.
+constexpr int kStageTiles = 1024;
 __device__ __forceinline__ void stage_aabbs(const TileHdr *__restrict__ tiles, int t0, int n,
-                                            float4 *ab_s)
+                                            float4 *ab_s, int4 *hdr_s = nullptr)
 {
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     ab_s[i] = __ldg(reinterpret_cast<const float4 *>(tiles + t0 + i) + 1);
+    if (hdr_s) hdr_s[i] = __ldg(reinterpret_cast<const int4 *>(tiles + t0 + i));
+  }
+}
+
+// Squared distance from p to a tile's AABB: the bound's ranking key (the
+// bound is increasing in the distance, so no square root is needed to rank).
+__device__ __forceinline__ float aabb_d2(float4 a4, float px, float py)
+{
+  const float dx = fmaxf(fmaxf(a4.x - px, px - a4.z), 0.f);
+  const float dy = fmaxf(fmaxf(a4.y - py, py - a4.w), 0.f);
+  return dx * dx + dy * dy;
+}
+
+// A distance D' such that every tile whose bound does not exceed ub lies
+// within D' of p: lb <= ub  <=>  d (1 - 1e-5) <= ub + r_foot + 1e-4, widened
+// by far more than the rounding of either side.  Negative: no tile.
+__device__ __forceinline__ float cand_radius(float ub, float rfoot)
+{
+  const float D = (ub + rfoot + 1e-4f) / (1.f - 1e-5f);
+  return D * (1.f + 1e-5f) + 1e-6f;
 }
 
 // ---------------------------------------------------------------------------
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(kPoseThreads)
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
   __shared__ float4 ab_s[kStageTiles];
-  __shared__ float ef_s[NET ? kStageTiles : 1];
+  __shared__ int4 hdr_s[kStageTiles];
   __shared__ int s_prop, s_fb, s_fbp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
@@ -473,17 +495,10 @@ __global__ void __launch_bounds__(kPoseThreads)
   for (int t0 = 0; t0 < T; t0 += kStageTiles) {
     const int n = min(kStageTiles, T - t0);
     __syncthreads();
-    stage_aabbs(tiles, t0, n, ab_s);
-    if constexpr (NET)
-      for (int i = threadIdx.x; i < n; i += blockDim.x)
-        ef_s[i] = (float)tiles[t0 + i].n_vtx * (1.f / 256.f);
+    stage_aabbs(tiles, t0, n, ab_s, hdr_s);
     __syncthreads();
     if (valid)
-      for (int i = hl; i < n; i += 16) {
-        const float4 a4 = ab_s[i];
-        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        topk_insert<R>(sc, id, tile_lb(ab, px, py, rfoot), t0 + i);
-      }
+      for (int i = hl; i < n; i += 16) topk_insert<R>(sc, id, aabb_d2(ab_s[i], px, py), t0 + i);
   }
   int best[K];
 #pragma unroll
@@ -535,12 +550,12 @@ __global__ void __launch_bounds__(kPoseThreads)
       if (ta >= 0) {
         const float4 a4 = staged ? ab_s[ta] : tile_aabb(tiles, ta);
         aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
-        efa = staged ? ef_s[ta] : (float)tiles[ta].n_vtx * (1.f / 256.f);
+        efa = (float)(staged ? hdr_s[ta].w : tiles[ta].n_vtx) * (1.f / 256.f);
       }
       if (tb >= 0) {
         const float4 a4 = staged ? ab_s[tb] : tile_aabb(tiles, tb);
         abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
-        efb = staged ? ef_s[tb] : (float)tiles[tb].n_vtx * (1.f / 256.f);
+        efb = (float)(staged ? hdr_s[tb].w : tiles[tb].n_vtx) * (1.f / 256.f);
       }
       // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
       const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
@@ -582,12 +597,14 @@ __global__ void __launch_bounds__(kPoseThreads)
       atomicAdd(&s_prop, n);
     }
     // upper bound on phi from the proposed tiles' obstacle circles (16 lanes)
+    const bool staged = T <= kStageTiles;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       if (best[i] < 0) continue;  // uniform over the pose's lanes
-      const TileHdr h = tiles[best[i]];
-      const float4 *circ = reinterpret_cast<const float4 *>(blob + h.blob_off + h.blob_bytes);
-      for (int o = hl; o < h.n_obs; o += 16)
+      const int4 h = staged ? hdr_s[best[i]]
+                            : __ldg(reinterpret_cast<const int4 *>(tiles + best[i]));
+      const float4 *circ = reinterpret_cast<const float4 *>(blob + h.x + h.y);
+      for (int o = hl; o < h.z; o += 16)
         ubp = fminf(ubp, circle_ub(__ldg(circ + o), px, py, rfoot));
     }
 #pragma unroll
@@ -595,8 +612,13 @@ __global__ void __launch_bounds__(kPoseThreads)
     if (valid && hl == 0) ub_out[p] = ubp;
   }
   // every unproposed tile whose bound does not exceed the upper bound is
-  // listed too: no other tile can hold a value at or below phi
-  int ncand = 0;
+  // listed too: no other tile can hold a value at or below phi.  A lane's
+  // first few tiles are appended after its loop (their atomics in flight
+  // together), further ones at once.
+  constexpr int kDefer = 4;
+  int ncand = 0, defer[kDefer];
+  const float Dc = cand_radius(ubp, rfoot);
+  const float Dc2 = Dc >= 0.f ? Dc * Dc : -1.f;
   for (int t0 = 0; t0 < T; t0 += kStageTiles) {
     const int n = min(kStageTiles, T - t0);
     if (T > kStageTiles) {  // uniform: restage this chunk
@@ -610,14 +632,21 @@ __global__ void __launch_bounds__(kPoseThreads)
         bool proposed = false;
 #pragma unroll
         for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
-        const float4 a4 = ab_s[i];
-        const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
-        if (!proposed && tile_lb(ab, px, py, rfoot) <= ubp) {
-          list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
+        if (!proposed && aabb_d2(ab_s[i], px, py) <= Dc2) {
+          if (ncand < kDefer) {
+#pragma unroll
+            for (int q = 0; q < kDefer; ++q)
+              if (q == ncand) defer[q] = t;
+          } else {
+            list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
+          }
           ++ncand;
         }
       }
   }
+#pragma unroll
+  for (int q = 0; q < kDefer; ++q)
+    if (q < ncand) list[(long long)defer[q] * P + atomicAdd(&hist[defer[q]], 1)] = (int)p;
 #pragma unroll
   for (int o = 8; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
   if (valid && hl == 0 && ncand > 0) {
