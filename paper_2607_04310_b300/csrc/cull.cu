@@ -680,12 +680,40 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // Persistent CTAs over work units.  Unit u belongs to tile t = utile[u] and
 // covers lanes [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane
-// l evaluates pose list[t * P + l / S] against obstacle range l % S of the
-// tile and merges its minimum into the pose's key.  The tile's blob and its
-// obstacle circles are staged in shared memory (16-byte cp.async per thread)
-// once per unit.  An obstacle whose circle bound exceeds the lane's running
-// threshold -- the pose's upper bound, then the smallest value the lane has
-// evaluated -- cannot reach the pose's minimum and is skipped.
+// l takes pose list[t * P + l / S] and obstacle range l % S of the tile.  The
+// tile's blob and its obstacle circles are staged in shared memory (16-byte
+// cp.async per thread) once per unit.  Each lane tests its obstacles'
+// circle bounds against the pose's upper bound; the survivors of the warp's
+// 32 lanes are compacted (ballot) into a per-warp queue and evaluated 32 at
+// a time, one (pose, obstacle) item per lane, so that lanes whose obstacles
+// were skipped do not idle through their neighbours' evaluations.  Every
+// evaluated obstacle merges its key into the pose's by atomicMin.
+constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
+
+template <int M>
+__device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
+                                           const int *qw, int n_items, int lane, float px,
+                                           float py, float c, float s, long long p,
+                                           const int4 *ob, const float4 *vt,
+                                           unsigned long long *__restrict__ keys,
+                                           unsigned long long &n_obs,
+                                           unsigned long long &n_edge)
+{
+  const int item = lane < n_items ? qw[lane] : 0;
+  const int src = item >> 16, o = item & 0xffff;
+  // the item's pose from the lane that found it (every lane takes part)
+  const float ipx = __shfl_sync(0xffffffffu, px, src), ipy = __shfl_sync(0xffffffffu, py, src);
+  const float ic = __shfl_sync(0xffffffffu, c, src), is = __shfl_sync(0xffffffffu, s, src);
+  const long long ip = __shfl_sync(0xffffffffu, p, src);
+  if (lane < n_items) {
+    const int4 rec = ob[o];
+    const float v = obstacle_value<M>(F, ipx, ipy, ic, is, vt + 2 * rec.x, rec.y, prm.eps_sat);
+    atomicMin(&keys[ip], pack_key(v, rec.z));
+    ++n_obs;
+    n_edge += rec.y;
+  }
+}
+
 template <int M>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
@@ -696,6 +724,9 @@ __global__ void __launch_bounds__(kListThreads)
                CullCounters *ctr)
 {
   extern __shared__ __align__(16) unsigned char tsm[];
+  __shared__ int queue[kListThreads / 32][kQueue];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int *qw = queue[warp];
   const int U = uoff[T];
   unsigned long long n_obs = 0, n_edge = 0;
   for (int u = blockIdx.x; u < U && u < cap; u += gridDim.x) {
@@ -714,28 +745,44 @@ __global__ void __launch_bounds__(kListThreads)
     if (l < L) p = list[(long long)t * P + l / S];
     cp_async_wait_all();
     __syncthreads();
+    const int4 *ob = reinterpret_cast<const int4 *>(tsm);
+    const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
+    const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
+    float px = 0.f, py = 0.f, c = 1.f, s = 0.f, thr = -kInf;
+    int o0 = 0, o1 = 0;
     if (p >= 0) {
-      const int4 *ob = reinterpret_cast<const int4 *>(tsm);
-      const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
-      const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
-      const int part = (int)(l % S);
       const float4 q4 = pose4[p];
-      const float px = q4.x, py = q4.y, c = q4.z, s = q4.w;
-      float thr = ub_value(ub[p]);
-      const int o0 = (int)((long long)h.n_obs * part / S);
-      const int o1 = (int)((long long)h.n_obs * (part + 1) / S);
-      unsigned long long best = ~0ull;
-      for (int o = o0; o < o1; ++o) {
-        if (circle_lb_value(circ[o], px, py, F.radius) > thr) continue;
-        const int4 rec = ob[o];
-        const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, prm.eps_sat);
-        const unsigned long long key = pack_key(v, rec.z);
-        best = key < best ? key : best;
-        thr = fminf(thr, v);
-        ++n_obs;
-        n_edge += rec.y;
+      px = q4.x;
+      py = q4.y;
+      c = q4.z;
+      s = q4.w;
+      thr = ub_value(ub[p]);
+      const int part = (int)(l % S);
+      o0 = (int)((long long)h.n_obs * part / S);
+      o1 = (int)((long long)h.n_obs * (part + 1) / S);
+    }
+    int span = o1 - o0;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, k));
+    int nq = 0;
+    for (int k = 0; k < span; ++k) {
+      const int o = o0 + k;
+      const bool keep = o < o1 && !(circle_lb_value(circ[o], px, py, F.radius) > thr);
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (keep) qw[nq + __popc(mask & ((1u << lane) - 1u))] = (lane << 16) | o;
+      nq += __popc(mask);
+      if (nq >= 32) {  // uniform: a full batch
+        __syncwarp();
+        eval_items<M>(F, prm, qw, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
+        __syncwarp();
+        if (lane < nq - 32) qw[lane] = qw[32 + lane];
+        __syncwarp();
+        nq -= 32;
       }
-      if (best != ~0ull) atomicMin(&keys[p], best);
+    }
+    if (nq > 0) {
+      __syncwarp();
+      eval_items<M>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
     }
   }
   // evaluated obstacles and edges (the roofline's work count)
@@ -744,7 +791,7 @@ __global__ void __launch_bounds__(kListThreads)
     n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
     n_edge += __shfl_xor_sync(0xffffffffu, n_edge, o);
   }
-  if ((threadIdx.x & 31) == 0 && n_obs) {
+  if (lane == 0 && n_obs) {
     atomicAdd(&ctr->n_obs_eval, n_obs);
     atomicAdd(&ctr->n_edge_eval, n_edge);
   }
