@@ -463,7 +463,8 @@ __global__ void __launch_bounds__(kPoseThreads)
             int *hist, int *__restrict__ list, int *__restrict__ uoff, int *__restrict__ utile,
             CullCounters *ctr)
 {
-  constexpr int R = NET ? kPre : K;
+  constexpr int R = NET ? kPre : K;  // candidates merged per pose
+  constexpr int RL = NET ? 4 : K;    // best tiles each lane keeps
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
   __shared__ float4 ab_s[kStageTiles];
@@ -484,10 +485,10 @@ __global__ void __launch_bounds__(kPoseThreads)
       pose4[p] = make_float4(px, py, c, s);
     }
   }
-  float sc[R];
-  int id[R];
+  float sc[RL];
+  int id[RL];
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
+  for (int i = 0; i < RL; ++i) {
     sc[i] = kInf;
     id[i] = -1;
   }
@@ -498,40 +499,36 @@ __global__ void __launch_bounds__(kPoseThreads)
     stage_aabbs(tiles, t0, n, ab_s, hdr_s);
     __syncthreads();
     if (valid)
-      for (int i = hl; i < n; i += 16) topk_insert<R>(sc, id, aabb_d2(ab_s[i], px, py), t0 + i);
+      for (int i = hl; i < n; i += 16) topk_insert<RL>(sc, id, aabb_d2(ab_s[i], px, py), t0 + i);
   }
   int best[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) best[i] = -1;
   float ubp = kInf;  // upper bound (metres) on the pose's phi
   if (pw < P) {  // uniform over the warp
-    // R rounds of a 16-lane argmin with pop
+    // R rounds of a 16-lane minimum over the lanes' heads, as 64-bit keys
+    // (squared distance bits << 32 | tile; the squared distance is not
+    // negative, so its bits order like the value).  Lane hl holds the tiles
+    // t = hl (mod 16), so a key's tile names the lane that pops it.  A lane
+    // keeps only its RL best, so with the network the 8 candidates are the
+    // pose's 8 smallest bounds unless one lane held more than RL of them.
     int cand[R];
+    int head = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float v = sc[0];
-      int t = id[0], who = hl;
+      unsigned long long key = ~0ull;
+#pragma unroll
+      for (int i = 0; i < RL; ++i)
+        if (i == head && id[i] >= 0)
+          key = ((unsigned long long)__float_as_uint(sc[i]) << 32) | (unsigned)id[i];
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
-        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int t2 = __shfl_xor_sync(0xffffffffu, t, o);
-        const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
-        if (t2 >= 0 && (t < 0 || v2 < v || (v2 == v && t2 < t))) {
-          v = v2;
-          t = t2;
-          who = w2;
-        }
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        key = k2 < key ? k2 : key;
       }
+      const int t = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
       cand[r] = t;
-      if (who == hl && t >= 0) {
-#pragma unroll
-        for (int i = 0; i < R - 1; ++i) {
-          sc[i] = sc[i + 1];
-          id[i] = id[i + 1];
-        }
-        sc[R - 1] = kInf;
-        id[R - 1] = -1;
-      }
+      if (t >= 0 && (t & 15) == hl) ++head;
     }
     if constexpr (NET) {
       if (hl == 0)
