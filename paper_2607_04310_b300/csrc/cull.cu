@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     if (valid)
       for (int i = hl; i < n; i += 16) topk_insert<RL>(sc, id, aabb_d2(ab_s[i], px, py), t0 + i);
   }
+  pdl_wait();  // no-op: the proposal kernel follows a memset
   int best[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) best[i] = -1;
@@ -656,6 +657,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     atomicAdd(&ctr->n_fb, s_fb);
     atomicAdd(&ctr->fallback_poses, s_fbp);
   }
+  pdl_trigger();  // the evaluation kernel may launch; it waits for this grid
   if (last_cta(&ctr->done1)) build_units(hist, tiles, T, uoff, utile, &ctr->n_items);
 }
 
@@ -724,6 +726,7 @@ __global__ void __launch_bounds__(kListThreads)
   __shared__ int queue[kListThreads / 32][kQueue];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int *qw = queue[warp];
+  pdl_wait();  // the proposal kernel's lists and units
   const int U = uoff[T];
   unsigned long long n_obs = 0, n_edge = 0;
   for (int u = blockIdx.x; u < U && u < cap; u += gridDim.x) {
@@ -782,6 +785,7 @@ __global__ void __launch_bounds__(kListThreads)
       eval_items<M>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
     }
   }
+  pdl_trigger();  // the epilogue may launch; it waits for this grid
   // evaluated obstacles and edges (the roofline's work count)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -905,10 +909,12 @@ struct ListEvalCall {
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
     const int grid = device_sms() * 8;
-    eval_lists<M><<<grid, kListThreads, smem, st>>>(F, pk, pose4, P, sc->d_tiles, sc->n_tiles,
-                                                   sc->d_blob, hist, uoff, utile, cap, list, ub,
-                                                   keys, ctr);
-    return PSDF_OK;
+    // follows the proposal kernel: may start while it finishes
+    cudaError_t e = launch_pdl(eval_lists<M>, dim3(grid), dim3(kListThreads), smem, st, F, pk,
+                               pose4, P, (const TileHdr *)sc->d_tiles, sc->n_tiles,
+                               (const unsigned char *)sc->d_blob, hist, uoff, utile, cap, list,
+                               ub, keys, ctr);
+    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (eval_lists)");
   }
 };
 

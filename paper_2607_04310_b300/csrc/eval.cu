@@ -158,6 +158,7 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 float *__restrict__ dphi, unsigned *__restrict__ active,
                                 float *__restrict__ stage, float d_min)
 {
+  pdl_wait();
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   PoseOut r;
@@ -181,6 +182,7 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float *__restrict__ grad_phi, float *__restrict__ grad_pose,
                                 float *__restrict__ grad_edges)
 {
+  pdl_wait();
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const float gphi = grad_phi[p];
@@ -409,15 +411,19 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
 {
   const int blocks = (int)((P + 63) / 64);
   ProfileScope prof("backward", st);
+  // usually follows an epilogue on the stream: may start while it finishes
+  cudaError_t le;
   if (pk.eta > 0.f)
-    backward_kernel<M, true><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P,
-                                                     sc->d_row_obs, sc->d_vtx, sc->d_far,
-                                                     sc->rows_total, active, grad_phi,
-                                                     grad_pose, grad_edges);
+    le = launch_pdl(backward_kernel<M, true>, dim3(blocks), dim3(64), 0, st, F, pk, sc->eps_axis,
+                    poses, P, (const ObsRec *)sc->d_row_obs, (const float4 *)sc->d_vtx,
+                    (const int *)sc->d_far, (long long)sc->rows_total, active, grad_phi,
+                    grad_pose, grad_edges);
   else
-    backward_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
-                                               sc->d_vtx, sc->d_far, sc->rows_total, active,
-                                               grad_phi, grad_pose, grad_edges);
+    le = launch_pdl(backward_kernel<M, false>, dim3(blocks), dim3(64), 0, st, F, pk,
+                    sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
+                    (const float4 *)sc->d_vtx, (const int *)sc->d_far,
+                    (long long)sc->rows_total, active, grad_phi, grad_pose, grad_edges);
+  if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return PSDF_OK;
@@ -464,10 +470,12 @@ struct EpilogueCall {
   {
     const int blocks = (int)((P + 63) / 64);
     ProfileScope prof("epilogue", st);
-    epilogue_kernel<M><<<blocks, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
-                                               sc->d_vtx, sc->d_far, keys, err,
-                                               phi, dphi, active, nullptr, 0.f);
-    cudaError_t e = cudaGetLastError();
+    // after the cull's evaluation kernel: may start while it finishes
+    cudaError_t e = launch_pdl(epilogue_kernel<M, false>, dim3(blocks), dim3(64), 0, st, F, pk,
+                               sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
+                               (const float4 *)sc->d_vtx, (const int *)sc->d_far, keys, err,
+                               phi, dphi, active, (float *)nullptr, 0.f);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PSDF_OK;
   }

@@ -55,6 +55,18 @@ __device__ __forceinline__ V2 local_edge(float ax, float ay, float bx, float by,
   return r;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor finishes;
+// pdl_wait() blocks until the predecessor grid has completed and its memory is
+// visible (a no-op for a kernel launched without the attribute), and
+// pdl_trigger() lets the successor's launch begin once every CTA of this grid
+// has passed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Total order on float values as unsigned bits (-0 is folded onto +0 first
 // so that the order matches IEEE comparison).
 __device__ __forceinline__ uint32_t ordered_bits(float v)

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -150,6 +151,27 @@ struct StageOut {
   float *stage = nullptr;
   float d_min = 0.f;
 };
+
+// Launch with programmatic stream serialization (see pdl_wait in
+// psdf_device.cuh): the kernel may begin while the previous kernel on the
+// stream finishes; it must call pdl_wait() before touching that kernel's
+// outputs.
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args &&...args)
+{
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // shared host helpers (eval.cu)
 int device_sms();
