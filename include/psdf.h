@@ -209,11 +209,14 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
  * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
  * conservative bound below (PSDF_PROPOSE_BOUND), or (PSDF_PROPOSE_MLP) by the
  * tile-proposal network's predicted signed distance among the 8 tiles with
- * the smallest bounds.  The circles containing the proposed tiles'
+ * the smallest bounds, among the tiles of the pose's cell in the scene's
+ * cull grid (every tile within one cell size of the pose; all tiles for a
+ * pose outside the grid).  The circles containing the proposed tiles'
  * obstacles give an upper bound UB >= phi; every other tile whose
  * conservative lower bound
  *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
- * does not exceed UB is added ("fallback" pairs).  All listed pairs are
+ * does not exceed UB is added ("fallback" pairs), taken from the cell's list
+ * when those tiles all lie within its reach, else from all tiles.  All listed pairs are
  * evaluated exactly in one pass, skipping obstacles whose circle bound
  * exceeds the smaller of UB and the values already found.  No skipped tile
  * or obstacle can hold a smaller value or a tie, so phi, the active pair and
@@ -221,6 +224,20 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
  * work the exact part does.  Pairs are bucketed by tile and each tile is
  * staged once for all the poses that need it. */
 typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
+
+/* The cull grid of a scene: a uniform grid of nx x ny square cells of side
+ * `cell` metres from (x0, y0), built with the scene; each cell lists every
+ * tile whose AABB comes within `cell` of it (`entries` list entries in all).
+ * A pose uses its cell's list while the tiles it needs lie within `reach`
+ * metres.  nx = ny = 0: no grid (a scene without tiles, or one whose tiles'
+ * AABBs are so large that the lists would exceed 64 entries per tile); the
+ * cull then scans all tiles.  Diagnostic only. */
+typedef struct {
+  int32_t nx, ny;
+  int64_t entries;
+  float x0, y0, cell, reach;
+} psdf_cull_grid_info;
+int psdf_scene_cull_grid(const psdf_scene *scene, psdf_cull_grid_info *info);
 
 #define PSDF_MLP_IN 16
 #define PSDF_MLP_HIDDEN 64

@@ -2,13 +2,17 @@
 //
 // Work is organised as (pose, tile) pairs, bucketed by tile:
 //   0. memset          per-tile counters and the pipeline counters cleared
-//   1. propose         16 lanes per pose rank every tile by the conservative
+//   1. propose         16 lanes per pose rank the tiles of the pose's cell in a
+//                      uniform grid (every tile within one cell size; all
+//                      tiles for a pose outside the grid) by the conservative
 //                      bound; the pose keeps its K best, or its 8 best
 //                      re-ranked by the tile-proposal network on tensor cores
 //                      (K best kept).  From the circles of the proposed tiles'
 //                      obstacles the lanes take an upper bound UB on phi and
 //                      list the pose for the proposed tiles and for every other
-//                      tile whose lower bound does not exceed UB.  The CTA that
+//                      tile whose lower bound does not exceed UB (the cell's
+//                      list holds them all when UB's reach is within the
+//                      cell's; else every tile is tested).  The CTA that
 //                      finishes last turns the per-tile counts into work units
 //   2. eval_lists      persistent CTAs over units: the tile's blob staged in shared
 //                      memory, lanes = (pose, obstacle range) pairs so that
@@ -385,19 +389,6 @@ __device__ __forceinline__ bool last_cta(unsigned *done)
   return last;
 }
 
-// Tile AABBs [t0, t0 + n) -> shared memory (independent loads, one latency);
-// with hdr_s also the first half of each header {blob_off, blob_bytes,
-// n_obs, n_vtx}.
-constexpr int kStageTiles = 1024;
-__device__ __forceinline__ void stage_aabbs(const TileHdr *__restrict__ tiles, int t0, int n,
-                                            float4 *ab_s, int4 *hdr_s = nullptr)
-{
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    ab_s[i] = __ldg(reinterpret_cast<const float4 *>(tiles + t0 + i) + 1);
-    if (hdr_s) hdr_s[i] = __ldg(reinterpret_cast<const int4 *>(tiles + t0 + i));
-  }
-}
-
 // Squared distance from p to a tile's AABB: the bound's ranking key (the
 // bound is increasing in the distance, so no square root is needed to rank).
 __device__ __forceinline__ float aabb_d2(float4 a4, float px, float py)
@@ -443,21 +434,35 @@ __device__ __forceinline__ float4 tile_aabb(const TileHdr *__restrict__ tiles, i
   return __ldg(reinterpret_cast<const float4 *>(tiles + t) + 1);
 }
 
-// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).  Each
-// lane ranks tiles hl, hl + 16, ... by the bound and keeps its R best; R
-// rounds of a 16-lane argmin over the lanes' heads give the pose's R
-// smallest (bound, tile) pairs in order, written to cand[r] (uniform over
-// the pose's 16 lanes).  With NET the 16 rows (2 poses x kPre candidates)
-// are scored by the network and the pose keeps its K best scores; else its
-// K best bounds.  Lane 0 of each pose appends the pose to its proposed tiles.
-// The pose's 16 lanes then take an upper bound on phi from the circles of
-// the proposed tiles' obstacles, and append the pose to every other tile
-// whose bound does not exceed it; the CTA that finishes last builds the work
-// units of all listed pairs.
+// The pose's cell in the cull grid, or -1 (no grid, or the pose outside it:
+// every lookup then scans all tiles).
+__device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
+{
+  if (g.nx == 0) return -1;
+  const float fx = __fmul_rn(__fsub_rn(px, g.x0), g.inv_cs);
+  const float fy = __fmul_rn(__fsub_rn(py, g.y0), g.inv_cs);
+  if (!(fx >= 0.f && fx < (float)g.nx && fy >= 0.f && fy < (float)g.ny)) return -1;
+  return (int)fy * g.nx + (int)fx;
+}
+
+// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).  The
+// tiles a pose looks at are its grid cell's list (every tile within one
+// cell size of the pose), else all tiles; lane hl takes entries hl, hl + 16,
+// ... and keeps its RL best bounds.  R rounds of a 16-lane argmin over the
+// lanes' heads give the pose's R smallest (bound, tile) pairs in order,
+// written to cand[r] (uniform over the pose's 16 lanes).  With NET the 16
+// rows (2 poses x kPre candidates) are scored by the network and the pose
+// keeps its K best scores; else its K best bounds.  Lane 0 of each pose
+// appends the pose to its proposed tiles.  The pose's 16 lanes then take an
+// upper bound on phi from the circles of the proposed tiles' obstacles, and
+// append the pose to every other tile whose bound does not exceed it: from
+// the cell's list when the bound's reach is within the grid's, else from
+// all tiles.  The CTA that finishes last builds the work units of all listed
+// pairs.
 template <int K, bool NET>
 __global__ void __launch_bounds__(kPoseThreads)
     propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
-            int T, float rfoot, const unsigned char *__restrict__ blob,
+            int T, const CullGrid grid, float rfoot, const unsigned char *__restrict__ blob,
             const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
             float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
             int *hist, int *__restrict__ list, int *__restrict__ uoff, int *__restrict__ utile,
@@ -467,19 +472,25 @@ __global__ void __launch_bounds__(kPoseThreads)
   constexpr int RL = NET ? 4 : K;    // best tiles each lane keeps
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
-  __shared__ float4 ab_s[kStageTiles];
-  __shared__ int4 hdr_s[kStageTiles];
   __shared__ int s_prop, s_fb, s_fbp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
   const int half = lane >> 4, hl = lane & 15;
   const long long p = pw + half;
   const bool valid = p < P;
+  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = 0;
   float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
+  int e0 = 0, e1 = 0;  // the cell's list, or all tiles (cell < 0)
+  int cell = -1;
   if (valid) {
     px = poses[3 * p];
     py = poses[3 * p + 1];
     sincosf(poses[3 * p + 2], &s, &c);
+    cell = grid_cell(grid, px, py);
+    if (cell >= 0) {
+      e0 = __ldg(grid.off + cell);
+      e1 = __ldg(grid.off + cell + 1);
+    }
     if (hl == 0) {
       keys[p] = ~0ull;
       pose4[p] = make_float4(px, py, c, s);
@@ -492,27 +503,25 @@ __global__ void __launch_bounds__(kPoseThreads)
     sc[i] = kInf;
     id[i] = -1;
   }
-  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = 0;
-  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
-    const int n = min(kStageTiles, T - t0);
-    __syncthreads();
-    stage_aabbs(tiles, t0, n, ab_s, hdr_s);
-    __syncthreads();
-    if (valid)
-      for (int i = hl; i < n; i += 16) topk_insert<RL>(sc, id, aabb_d2(ab_s[i], px, py), t0 + i);
+  // entries i of the cell's list (tile grid.tl[i]) or tiles i
+  const int lo = (cell >= 0 ? e0 : 0) + hl, hi = valid ? (cell >= 0 ? e1 : T) : 0;
+  for (int i = lo; i < hi; i += 16) {
+    const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
+    topk_insert<RL>(sc, id, aabb_d2(tile_aabb(tiles, t), px, py), t);
   }
   pdl_wait();  // no-op: the proposal kernel follows a memset
+  __syncthreads();  // s_prop, s_fb, s_fbp initialised
   int best[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) best[i] = -1;
   float ubp = kInf;  // upper bound (metres) on the pose's phi
   if (pw < P) {  // uniform over the warp
     // R rounds of a 16-lane minimum over the lanes' heads, as 64-bit keys
-    // (squared distance bits << 32 | tile; the squared distance is not
-    // negative, so its bits order like the value).  Lane hl holds the tiles
-    // t = hl (mod 16), so a key's tile names the lane that pops it.  A lane
-    // keeps only its RL best, so with the network the 8 candidates are the
-    // pose's 8 smallest bounds unless one lane held more than RL of them.
+    // (squared distance bits << 32 | tile << 4 | lane; the squared distance
+    // is not negative, so its bits order like the value, and a tile sits in
+    // one lane only).  A lane keeps only its RL best, so with the network
+    // the 8 candidates are the 8 smallest bounds it looked at unless one
+    // lane held more than RL of them.
     int cand[R];
     int head = 0;
 #pragma unroll
@@ -521,15 +530,16 @@ __global__ void __launch_bounds__(kPoseThreads)
 #pragma unroll
       for (int i = 0; i < RL; ++i)
         if (i == head && id[i] >= 0)
-          key = ((unsigned long long)__float_as_uint(sc[i]) << 32) | (unsigned)id[i];
+          key = ((unsigned long long)__float_as_uint(sc[i]) << 32) |
+                ((unsigned)id[i] << 4) | (unsigned)hl;
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
         key = k2 < key ? k2 : key;
       }
-      const int t = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
-      cand[r] = t;
-      if (t >= 0 && (t & 15) == hl) ++head;
+      const bool any = key != ~0ull;
+      cand[r] = any ? (int)((unsigned)(key & 0xffffffffu) >> 4) : -1;
+      if (any && (int)(key & 15u) == hl) ++head;
     }
     if constexpr (NET) {
       if (hl == 0)
@@ -542,18 +552,16 @@ __global__ void __launch_bounds__(kPoseThreads)
       const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
       float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
       float efa = 0.f, efb = 0.f;
-      // the candidates' AABBs and edge fractions: from shared memory when
-      // every tile was staged at once
-      const bool staged = T <= kStageTiles;
+      // the candidates' AABBs and edge fractions
       if (ta >= 0) {
-        const float4 a4 = staged ? ab_s[ta] : tile_aabb(tiles, ta);
+        const float4 a4 = tile_aabb(tiles, ta);
         aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
-        efa = (float)(staged ? hdr_s[ta].w : tiles[ta].n_vtx) * (1.f / 256.f);
+        efa = (float)__ldg(&tiles[ta].n_vtx) * (1.f / 256.f);
       }
       if (tb >= 0) {
-        const float4 a4 = staged ? ab_s[tb] : tile_aabb(tiles, tb);
+        const float4 a4 = tile_aabb(tiles, tb);
         abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
-        efb = (float)(staged ? hdr_s[tb].w : tiles[tb].n_vtx) * (1.f / 256.f);
+        efb = (float)__ldg(&tiles[tb].n_vtx) * (1.f / 256.f);
       }
       // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
       const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
@@ -594,16 +602,22 @@ __global__ void __launch_bounds__(kPoseThreads)
       for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
       atomicAdd(&s_prop, n);
     }
-    // upper bound on phi from the proposed tiles' obstacle circles (16 lanes)
-    const bool staged = T <= kStageTiles;
+    // upper bound on phi from the proposed tiles' obstacle circles (16
+    // lanes, four circles a lane per round, their loads issued together)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       if (best[i] < 0) continue;  // uniform over the pose's lanes
-      const int4 h = staged ? hdr_s[best[i]]
-                            : __ldg(reinterpret_cast<const int4 *>(tiles + best[i]));
+      const int4 h = __ldg(reinterpret_cast<const int4 *>(tiles + best[i]));
       const float4 *circ = reinterpret_cast<const float4 *>(blob + h.x + h.y);
-      for (int o = hl; o < h.z; o += 16)
-        ubp = fminf(ubp, circle_ub(__ldg(circ + o), px, py, rfoot));
+      for (int o = hl; o < h.z; o += 64) {
+        float4 cc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (o + 16 * q < h.z) cc[q] = __ldg(circ + o + 16 * q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (o + 16 * q < h.z) ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot));
+      }
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) ubp = fminf(ubp, __shfl_xor_sync(0xffffffffu, ubp, o));
@@ -617,30 +631,23 @@ __global__ void __launch_bounds__(kPoseThreads)
   int ncand = 0, defer[kDefer];
   const float Dc = cand_radius(ubp, rfoot);
   const float Dc2 = Dc >= 0.f ? Dc * Dc : -1.f;
-  for (int t0 = 0; t0 < T; t0 += kStageTiles) {
-    const int n = min(kStageTiles, T - t0);
-    if (T > kStageTiles) {  // uniform: restage this chunk
-      __syncthreads();
-      stage_aabbs(tiles, t0, n, ab_s);
-      __syncthreads();
-    }
-    if (valid)
-      for (int i = hl; i < n; i += 16) {
-        const int t = t0 + i;
-        bool proposed = false;
+  const bool in_cell = cell >= 0 && Dc <= grid.reach_q;
+  const int clo = (in_cell ? e0 : 0) + hl, chi = valid ? (in_cell ? e1 : T) : 0;
+  for (int i = clo; i < chi; i += 16) {
+    const int t = in_cell ? __ldg(grid.tl + i) : i;
+    bool proposed = false;
 #pragma unroll
-        for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
-        if (!proposed && aabb_d2(ab_s[i], px, py) <= Dc2) {
-          if (ncand < kDefer) {
+    for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
+    if (!proposed && aabb_d2(tile_aabb(tiles, t), px, py) <= Dc2) {
+      if (ncand < kDefer) {
 #pragma unroll
-            for (int q = 0; q < kDefer; ++q)
-              if (q == ncand) defer[q] = t;
-          } else {
-            list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
-          }
-          ++ncand;
-        }
+        for (int q = 0; q < kDefer; ++q)
+          if (q == ncand) defer[q] = t;
+      } else {
+        list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
       }
+      ++ncand;
+    }
   }
 #pragma unroll
   for (int q = 0; q < kDefer; ++q)
@@ -1148,13 +1155,15 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
       ProfileScope prof("propose", st);
 #define PSDF_PROPOSE(KK)                                                                     \
   if (net)                                                                                   \
-    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,    \
-                                                   scene->d_blob, frag, b2, keys, pose4, ub, \
-                                                   prop, hist, list, uoff, utile, ctr);      \
-  else                                                                                       \
-    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, F.radius,   \
-                                                    scene->d_blob, frag, b2, keys, pose4,    \
-                                                    ub, prop, hist, list, uoff, utile, ctr);
+    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid, \
+                                                   F.radius, scene->d_blob, frag, b2, keys,     \
+                                                   pose4, ub, prop, hist, list, uoff, utile,    \
+                                                   ctr);                                        \
+  else                                                                                          \
+    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid,   \
+                                                    F.radius, scene->d_blob, frag, b2, keys,    \
+                                                    pose4, ub, prop, hist, list, uoff, utile,   \
+                                                    ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;

@@ -82,6 +82,21 @@ struct ObsRec {
   int tile;
 };
 
+// Uniform grid over a scene's bounding box for the cull's tile lookups.
+// Cell (i, j) covers [x0 + i cs, x0 + (i + 1) cs) x [y0 + j cs, y0 + (j + 1) cs)
+// and lists, in increasing tile order, every tile whose AABB comes within
+// `reach` of the cell in the L-infinity sense (so every tile within Euclidean
+// distance reach as well).  A pose whose computed cell is (i, j) finds in
+// that one list every tile within reach_q of itself: reach_q is reach less
+// a margin for the rounding of the pose's cell index.  nx = 0: no grid, every
+// lookup scans all tiles.
+struct CullGrid {
+  float x0 = 0.f, y0 = 0.f, inv_cs = 0.f, reach_q = -1.f;
+  int nx = 0, ny = 0;
+  const int *off = nullptr;  // [nx * ny + 1] list offsets (device)
+  const int *tl = nullptr;   // tile lists (device)
+};
+
 }  // namespace psdf
 
 struct psdf_scene {
@@ -97,6 +112,10 @@ struct psdf_scene {
   psdf::ObsRec *d_row_obs = nullptr;  // [rows_total] obstacle record of each caller row
   float4 *d_vtx = nullptr;            // [2 * n_edges] sorted vertex records
   int *d_far = nullptr;               // [n_edges] far vertex index within its obstacle
+  psdf::CullGrid grid;                // the cull's cell -> tile lists
+  float grid_cell = 0.f;              // cell side (m)
+  int64_t grid_entries = 0;
+  int *d_cell_off = nullptr, *d_cell_tiles = nullptr;
   size_t device_bytes = 0;
   // host copies used for launch configuration
   int max_blob_bytes = 0;      // largest tile blob (obstacle + vertex records)

@@ -79,6 +79,8 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_vtx);
   cudaFree(s->d_far);
   cudaFree(s->d_row_obs);
+  cudaFree(s->d_cell_off);
+  cudaFree(s->d_cell_tiles);
   delete s;
 }
 
@@ -296,6 +298,67 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
   return PSDF_OK;
 }
 
+// The cull's uniform grid (see CullGrid): cells about the size of a tile,
+// reach one cell.  Host arithmetic in FP64; every tile is listed in each cell
+// its AABB, widened by reach plus a margin, overlaps.  The margin covers the
+// device's FP32 rounding of a pose's cell (relative error of a few 1e-7 of
+// the coordinates' magnitude, plus that of 1/cs); reach_q takes it off twice.
+// No grid when the lists would grow far beyond the tile count (strongly
+// uneven tiles): lookups then scan all tiles.
+void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<int> *off,
+                     std::vector<int> *tl)
+{
+  *g = CullGrid();
+  *cell = 0.f;
+  off->clear();
+  tl->clear();
+  const int T = hs.T;
+  if (T == 0) return;
+  const double x0 = hs.bb[0], y0 = hs.bb[1];
+  const double W = (double)hs.bb[2] - x0, H = (double)hs.bb[3] - y0;
+  double cs = std::sqrt(W * H / T);
+  cs = std::max({cs, std::max(W, H) / 1000.0, 1e-3});
+  const int nx = (int)std::floor(W / cs) + 1, ny = (int)std::floor(H / cs) + 1;
+  const double reach = cs;
+  const double mag = std::fabs(x0) + std::fabs(y0) + (nx + ny) * cs;
+  const double margin = 1e-3 * cs + 1e-6 * mag;
+  auto span = [&](double lo, double hi, int n, int *i0, int *i1) {
+    *i0 = std::max(0, (int)std::floor((lo - reach - margin) / cs));
+    *i1 = std::min(n - 1, (int)std::floor((hi + reach + margin) / cs));
+  };
+  std::vector<int> cnt((size_t)nx * ny + 1, 0);
+  long long total = 0;
+  for (int t = 0; t < T; ++t) {
+    const float *a = hs.tiles[t].aabb;
+    int i0, i1, j0, j1;
+    span(a[0] - x0, a[2] - x0, nx, &i0, &i1);
+    span(a[1] - y0, a[3] - y0, ny, &j0, &j1);
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) ++cnt[(size_t)j * nx + i];
+    total += (long long)std::max(0, i1 - i0 + 1) * std::max(0, j1 - j0 + 1);
+  }
+  if (total > 64LL * T + 65536) return;
+  off->assign((size_t)nx * ny + 1, 0);
+  for (size_t c = 0; c < (size_t)nx * ny; ++c) (*off)[c + 1] = (*off)[c] + cnt[c];
+  tl->assign((size_t)total, 0);
+  std::vector<int> cur(off->begin(), off->end() - 1);
+  for (int t = 0; t < T; ++t) {  // increasing t: every list sorted
+    const float *a = hs.tiles[t].aabb;
+    int i0, i1, j0, j1;
+    span(a[0] - x0, a[2] - x0, nx, &i0, &i1);
+    span(a[1] - y0, a[3] - y0, ny, &j0, &j1);
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) (*tl)[cur[(size_t)j * nx + i]++] = t;
+  }
+  g->x0 = hs.bb[0];
+  g->y0 = hs.bb[1];
+  g->inv_cs = (float)(1.0 / cs);
+  g->reach_q = (float)(reach - 2.0 * margin);
+  g->nx = nx;
+  g->ny = ny;
+  *cell = (float)cs;
+}
+
 int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
                 int tile_edges, const psdf_params *prm, cudaStream_t st, psdf_scene **out)
 {
@@ -320,6 +383,15 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   if (!rc) rc = dev_upload(&s->d_vtx, hs.vtx, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_far, hs.far, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_row_obs, hs.row_obs, st, &s->device_bytes);
+  std::vector<int> cell_off, cell_tiles;
+  build_cull_grid(hs, &s->grid, &s->grid_cell, &cell_off, &cell_tiles);
+  s->grid_entries = (int64_t)cell_tiles.size();
+  if (!rc && s->grid.nx > 0) {
+    rc = dev_upload(&s->d_cell_off, cell_off, st, &s->device_bytes);
+    if (!rc) rc = dev_upload(&s->d_cell_tiles, cell_tiles, st, &s->device_bytes);
+    s->grid.off = s->d_cell_off;
+    s->grid.tl = s->d_cell_tiles;
+  }
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "scene upload");
@@ -392,6 +464,19 @@ extern "C" int psdf_scene_create_padded(const float *A, const float *B, const ui
 extern "C" int psdf_scene_destroy(psdf_scene *scene)
 {
   free_scene(scene);
+  return PSDF_OK;
+}
+
+extern "C" int psdf_scene_cull_grid(const psdf_scene *s, psdf_cull_grid_info *info)
+{
+  if (!s || !info) return fail(PSDF_ERR_ARG, "scene or info is NULL");
+  info->nx = s->grid.nx;
+  info->ny = s->grid.ny;
+  info->entries = s->grid.nx > 0 ? s->grid_entries : 0;
+  info->x0 = s->grid.x0;
+  info->y0 = s->grid.y0;
+  info->cell = s->grid.nx > 0 ? s->grid_cell : 0.f;
+  info->reach = s->grid.nx > 0 ? s->grid.reach_q : 0.f;
   return PSDF_OK;
 }
 

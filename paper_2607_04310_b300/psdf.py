@@ -45,6 +45,12 @@ class Params(ctypes.Structure):
                 ("eps_sat", ctypes.c_float), ("eta", ctypes.c_float)]
 
 
+class CullGridInfo(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("entries", ctypes.c_int64),
+                ("x0", ctypes.c_float), ("y0", ctypes.c_float), ("cell", ctypes.c_float),
+                ("reach", ctypes.c_float)]
+
+
 class SceneInfo(ctypes.Structure):
     _fields_ = [("n_edges", ctypes.c_int64), ("n_obstacles", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int32), ("tile_edges", ctypes.c_int32),
@@ -75,6 +81,7 @@ _SIGS = {
                                                 ctypes.c_int32, _vp, _vp, ctypes.POINTER(_vp)]),
     "psdf_scene_destroy": (ctypes.c_int, [_vp]),
     "psdf_scene_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(SceneInfo)]),
+    "psdf_scene_cull_grid": (ctypes.c_int, [_vp, ctypes.POINTER(CullGridInfo)]),
     "psdf_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "psdf_workspace_status": (ctypes.c_int, [_vp, _vp]),
     "psdf_eval": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
@@ -222,6 +229,11 @@ class Scene:
     def info(self) -> SceneInfo:
         inf = SceneInfo()
         _check(load().psdf_scene_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def cull_grid(self) -> CullGridInfo:
+        inf = CullGridInfo()
+        _check(load().psdf_scene_cull_grid(self.handle, ctypes.byref(inf)))
         return inf
 
     def close(self) -> None:

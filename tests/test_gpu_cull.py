@@ -94,6 +94,72 @@ def test_cull_far_poses_and_empty_scene():
     assert torch.all(torch.isinf(phi))
 
 
+def _csr_subset(edges, offs, keep):
+    """The obstacles of a CSR edge set whose mask entry is True."""
+    rows, new_offs = [], [0]
+    for i in np.flatnonzero(keep):
+        rows.append(edges[offs[i]:offs[i + 1]])
+        new_offs.append(new_offs[-1] + offs[i + 1] - offs[i])
+    return np.concatenate(rows).astype(np.float32), np.asarray(new_offs, dtype=np.int32)
+
+
+def test_cull_grid_cells_holes_and_outside_poses():
+    """Dense clutter with an empty disc of radius 25 m: poses in the hole have
+    an upper bound beyond one cell (every tile tested), poses in the clutter
+    use their cell's list, poses on cell borders, on the bounding box and
+    outside it scan all tiles; every output bit equals the full scan."""
+    g = np.random.default_rng(11)
+    edges, offs = sg.rects(g, 12000, 0.2, 1.0, 0.0, 120.0)
+    cen = edges[offs[:-1], 0:2]
+    keep = np.hypot(cen[:, 0] - 60.0, cen[:, 1] - 60.0) > 25.0
+    edges, offs = _csr_subset(edges, offs, keep)
+    scene = psdf.Scene.from_csr(edges, offs)
+    x0, y0 = float(edges[:, 0::2].min()), float(edges[:, 1::2].min())
+    x1, y1 = float(edges[:, 0::2].max()), float(edges[:, 1::2].max())
+    grid = scene.cull_grid()
+    assert grid.nx > 0 and grid.entries > 0 and 0 < grid.reach < grid.cell
+    assert grid.x0 == np.float32(x0) and grid.y0 == np.float32(y0)
+    cs = float(grid.cell)
+    n = 1500
+    pts = [g.uniform(0.0, 120.0, size=(n, 2)),                       # clutter and hole
+           60.0 + g.normal(size=(200, 2)) * 8.0,                     # the hole
+           np.stack([x0 + cs * g.integers(0, 12, 300),               # cell borders
+                     g.uniform(y0, y1, 300)], axis=1),
+           np.stack([g.uniform(x0, x1, 100), np.full(100, y1)], axis=1),   # on the box
+           np.stack([np.full(100, x1), g.uniform(y0, y1, 100)], axis=1),
+           np.stack([g.uniform(-30.0, 150.0, 200), np.full(200, -0.5)], axis=1),  # outside
+           np.array([[x0, y0], [x1, y1], [x0 - 1e-3, y0], [x1 + 1e-3, y1]])]
+    xy = np.concatenate(pts).astype(np.float32)
+    poses_np = np.concatenate([xy, g.uniform(-math.pi, math.pi, size=(len(xy), 1))],
+                              axis=1).astype(np.float32)
+    w = sg.Workload("clutter_with_hole", sg.footprint_rect(), edges, offs, poses_np)
+    poses = torch.as_tensor(poses_np, device="cuda")
+    for mlp, k in ((None, 1), (None, 3), (_random_mlp(5), 1), (_random_mlp(6), 2)):
+        _compare_cull(w, scene, poses, mlp=mlp, k=k)
+
+
+def test_cull_without_grid_long_segments():
+    """Segments 1 km long, one per tile: every tile's AABB spans most of the
+    field, so the scene gets no grid and every lookup scans all tiles."""
+    g = np.random.default_rng(12)
+    n = 400
+    a = g.uniform(0.0, 100.0, size=(n, 2))
+    ang = math.pi / 4 + g.uniform(-0.1, 0.1, size=n)
+    b = a + 1000.0 * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    edges = np.concatenate([a, b], axis=1).astype(np.float32)
+    offs = np.arange(n + 1, dtype=np.int32)
+    scene = psdf.Scene.from_csr(edges, offs, tile_edges=1)
+    assert scene.info().n_tiles == n
+    assert scene.cull_grid().nx == 0
+    poses_np = np.concatenate([g.uniform(-50.0, 850.0, size=(700, 2)),
+                               g.uniform(-math.pi, math.pi, size=(700, 1))], axis=1)
+    w = sg.Workload("long_segments", sg.footprint_rect(), edges, offs,
+                    poses_np.astype(np.float32))
+    poses = torch.as_tensor(w.poses, device="cuda")
+    _compare_cull(w, scene, poses, k=1)
+    _compare_cull(w, scene, poses, mlp=_random_mlp(9), k=2)
+
+
 def test_lower_bound_is_below_every_tile_value():
     w = sg.dense_clutter(4, n_rects=4000, n_poses=512, field_side=80.0)
     scene = psdf.Scene.from_csr(w.edges, w.offsets)
