@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
   if (live && best != ~0ull) atomicMin(&keys[p], best);
 }
 
+constexpr int kEpiLanes = 4;  // lanes sharing one pose's epilogue (hard minimum)
+
 // Per-pose epilogue: value, active pair, optional pose gradient.
 template <int M, bool SOFT = false>
 __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
@@ -159,18 +161,47 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 float *__restrict__ stage, float d_min)
 {
   pdl_wait();
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  PoseOut r;
-  if (*err) {
-    r = pose_out_failed();
+  pdl_trigger();  // a following backward may launch now; it waits for this grid
+  const bool want_grad = dphi != nullptr || stage != nullptr;
+  if constexpr (SOFT) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    PoseOut r;
+    if (*err) {
+      r = pose_out_failed();
+    } else {
+      r = epilogue_pose<M, true>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
+                                 poses[3 * p + 2], keys[p], row_obs, vtx, far, want_grad,
+                                 prm.eta);
+    }
+    write_pose_out(r, p, phi, dphi, active, stage, d_min);
   } else {
-    r = epilogue_pose<M, SOFT>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],
-                               poses[3 * p + 2], keys[p], row_obs, vtx, far,
-                               dphi != nullptr || stage != nullptr, prm.eta);
+    // kEpiLanes lanes per pose, every lane of the block through the shared
+    // detail (no early exit before it)
+    const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kEpiLanes;
+    const int g = (int)(threadIdx.x % kEpiLanes);
+    const bool valid = p < P;
+    PoseOut r;
+    if (*err) {
+      r = pose_out_failed();
+    } else {
+      const long long q = valid ? p : 0;
+      r = epilogue_pose_coop<M, kEpiLanes>(F, prm.eps_sat, eps_axis, poses[3 * q],
+                                           poses[3 * q + 1], poses[3 * q + 2],
+                                           valid ? keys[p] : ~0ull, row_obs, vtx, far,
+                                           want_grad, g);
+    }
+    if (valid && g == 0) write_pose_out(r, p, phi, dphi, active, stage, d_min);
   }
-  write_pose_out(r, p, phi, dphi, active, stage, d_min);
 }
+
+// Launch shape of the epilogue: hard minimum kEpiLanes lanes per pose in
+// blocks of 128, soft minimum one thread per pose in blocks of 64.
+inline dim3 epilogue_blocks(long long P, bool soft)
+{
+  return soft ? dim3((unsigned)((P + 63) / 64)) : dim3((unsigned)((P * kEpiLanes + 127) / 128));
+}
+inline dim3 epilogue_threads(bool soft) { return soft ? dim3(64) : dim3(128); }
 
 template <int M, bool SOFT = false>
 __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
@@ -388,13 +419,14 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
   }
   {
     ProfileScope prof("epilogue", st);
-    const int eb = (int)((P + 63) / 64);
-    if (pk.eta > 0.f)
-      epilogue_kernel<M, true><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+    const bool soft = pk.eta > 0.f;
+    const dim3 eb = epilogue_blocks(P, soft), et = epilogue_threads(soft);
+    if (soft)
+      epilogue_kernel<M, true><<<eb, et, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
                                                    sc->d_vtx, sc->d_far, keys, err, phi, dphi,
                                                    active, so.stage, so.d_min);
     else
-      epilogue_kernel<M><<<eb, 64, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
+      epilogue_kernel<M><<<eb, et, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
                                              sc->d_vtx, sc->d_far, keys, err, phi, dphi, active,
                                              so.stage, so.d_min);
   }
@@ -468,10 +500,10 @@ struct EpilogueCall {
                  const ParamsK &pk, const unsigned long long *keys, const int *err, float *phi,
                  float *dphi, unsigned *active, cudaStream_t st)
   {
-    const int blocks = (int)((P + 63) / 64);
     ProfileScope prof("epilogue", st);
     // after the cull's evaluation kernel: may start while it finishes
-    cudaError_t e = launch_pdl(epilogue_kernel<M, false>, dim3(blocks), dim3(64), 0, st, F, pk,
+    cudaError_t e = launch_pdl(epilogue_kernel<M, false>, epilogue_blocks(P, false),
+                               epilogue_threads(false), 0, st, F, pk,
                                sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                                (const float4 *)sc->d_vtx, (const int *)sc->d_far, keys, err,
                                phi, dphi, active, (float *)nullptr, 0.f);

@@ -67,6 +67,17 @@ __device__ __forceinline__ void pdl_trigger()
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Requests every 128-byte line of [p, p + bytes) into L1 (at most 16 lines),
+// so that the loads that follow, issued one after another by a dependent
+// chain, hit L1 after a single memory latency.
+__device__ __forceinline__ void prefetch_lines(const void *p, int bytes)
+{
+  const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)127, a1 = (uintptr_t)p + (uintptr_t)bytes;
+  int n = 0;
+  for (uintptr_t a = a0; a < a1 && n < 16; a += 128, ++n)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+
 // Total order on float values as unsigned bits (-0 is folded onto +0 first
 // so that the order matches IEEE comparison).
 __device__ __forceinline__ uint32_t ordered_bits(float v)
@@ -417,6 +428,175 @@ __device__ __forceinline__ bool better(float v, unsigned pid, float bv, unsigned
   return v < bv || (v == bv && pid < bpid);
 }
 
+// Running state of an obstacle's detail: per robot axis the obstacle's
+// extreme projections (first vertex reaching each), the best distance and
+// best obstacle-axis candidates as (value, pair id), and the minima.
+template <int M>
+struct DetailAcc {
+  float pmax[M], pmin[M];
+  int kmax[M], kmin[M];
+  float d2min, dlt, bd, ba, dt;
+  unsigned pd, pa;
+  __device__ __forceinline__ DetailAcc()
+  {
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      pmax[l] = -kInf;
+      pmin[l] = kInf;
+      kmax[l] = 0;
+      kmin[l] = 0;
+    }
+    d2min = kInf;
+    dlt = kInf;
+    bd = kInf;
+    ba = kInf;
+    dt = 0.f;
+    pd = PSDF_PAIR_NONE;
+    pa = PSDF_PAIR_NONE;
+  }
+};
+
+// Edge k of an obstacle (vt, n) into the detail state: its distance pairs
+// with every robot vertex and vertex k's with every robot edge, its own
+// axis, and vertex k's projections on the robot axes.
+template <int M, bool SOFT>
+__device__ __forceinline__ void detail_edge(const FootprintK &F, float px, float py, float c,
+                                            float s, const float4 *vt, int n, int k,
+                                            int orig_first, DetailAcc<M> &q, SoftAcc &acc,
+                                            float eta)
+{
+  const bool seg = (n == 1);
+  const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
+  float bwx, bwy;  // world B
+  if (seg) {
+    bwx = bk4.z;
+    bwy = bk4.w;
+  } else {
+    const float4 an = vt[2 * (k + 1 < n ? k + 1 : 0)];
+    bwx = an.x;
+    bwy = an.y;
+  }
+  const V2 A = to_local(ak4.x, ak4.y, px, py, c, s);
+  const V2 B = to_local(bwx, bwy, px, py, c, s);
+  const V2 U = local_edge(ak4.x, ak4.y, bwx, bwy, c, s);
+  const float ux = U.x, uy = U.y;
+  const int edge = orig_first + k;
+  float smin = kInf, smax = -kInf;
+  int lsmin = 0, lsmax = 0;
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
+    const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak4.z));
+    float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
+    if (seg) {
+      rx = (t == 1.0f) ? __fsub_rn(F.vx[l], B.x) : rx;
+      ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
+    }
+    const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+    if (seg || t < 1.0f) {
+      q.d2min = fminf(q.d2min, d2);
+      const unsigned pid = make_pid(edge, kVertEdge, l);
+      if (better(d2, pid, q.bd, q.pd)) { q.bd = d2; q.pd = pid; q.dt = t; }
+    }
+    const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
+    if (sl < smin) { smin = sl; lsmin = l; }
+    if (sl > smax) { smax = sl; lsmax = l; }
+    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    if (tp > 0.0f && tp < 1.0f) {
+      q.d2min = fminf(q.d2min, d2p);
+      const unsigned pid = make_pid(edge, kObsVRobotEdge, l);
+      if (better(d2p, pid, q.bd, q.pd)) { q.bd = d2p; q.pd = pid; q.dt = tp; }
+    }
+    const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
+    if (pr > q.pmax[l]) { q.pmax[l] = pr; q.kmax[l] = k; }
+    if (pr < q.pmin[l]) { q.pmin[l] = pr; q.kmin[l] = k; }
+  }
+  const float da = __fmaf_rn(-smin, ak4.w, bk4.y);
+  const float db = __fmaf_rn(smax, ak4.w, -bk4.x);
+  q.dlt = fminf(q.dlt, fminf(da, db));
+  if (SOFT) acc.add(fminf(da, db), eta);
+  {
+    const unsigned pid = make_pid(edge, kOAxisOMax, lsmin);
+    if (better(da, pid, q.ba, q.pa)) { q.ba = da; q.pa = pid; }
+  }
+  {
+    const unsigned pid = make_pid(edge, kOAxisRMax, lsmax);
+    if (better(db, pid, q.ba, q.pa)) { q.ba = db; q.pa = pid; }
+  }
+}
+
+// A segment's B endpoint: its distances to the robot edges and its
+// projections on the robot axes (vertex index 1).
+template <int M>
+__device__ __forceinline__ void detail_seg_b(const FootprintK &F, float px, float py, float c,
+                                             float s, const float4 *vt, int orig_first,
+                                             DetailAcc<M> &q)
+{
+  const float4 b0 = vt[1];
+  const V2 Bv = to_local(b0.z, b0.w, px, py, c, s);
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float wx = __fsub_rn(F.vx[l], Bv.x), wy = __fsub_rn(F.vy[l], Bv.y);
+    const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
+    const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
+    const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    if (tp > 0.0f && tp < 1.0f) {
+      q.d2min = fminf(q.d2min, d2p);
+      const unsigned pid = make_pid(orig_first, kObsBRobotEdge, l);
+      if (better(d2p, pid, q.bd, q.pd)) { q.bd = d2p; q.pd = pid; q.dt = tp; }
+    }
+    const float pr = __fmaf_rn(Bv.x, F.nx[l], __fmul_rn(Bv.y, F.ny[l]));
+    if (pr > q.pmax[l]) { q.pmax[l] = pr; q.kmax[l] = 1; }
+    if (pr < q.pmin[l]) { q.pmin[l] = pr; q.kmin[l] = 1; }
+  }
+}
+
+// Robot axes, then the obstacle's value and active pair (kind, l, k and t
+// re-derived from the winning pair id).
+template <int M, bool SOFT>
+__device__ __forceinline__ Active detail_finish(const FootprintK &F, int n, int orig_first,
+                                                float eps_sat, DetailAcc<M> &q, SoftAcc &acc,
+                                                float eta)
+{
+  const bool seg = (n == 1);
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float da = __fsub_rn(q.pmax[l], F.alo[l]);
+    const float db = __fsub_rn(F.ahi[l], q.pmin[l]);
+    q.dlt = fminf(q.dlt, fminf(da, db));
+    if (SOFT) acc.add(fminf(da, db), eta);
+    const bool bA = seg && q.kmax[l] == 1, bB = seg && q.kmin[l] == 1;
+    const int eA = seg ? orig_first : orig_first + q.kmax[l];
+    const int eB = seg ? orig_first : orig_first + q.kmin[l];
+    const unsigned pidA = make_pid(eA, bA ? kRAxisOMaxB : kRAxisOMax, l);
+    const unsigned pidB = make_pid(eB, bB ? kRAxisRMaxB : kRAxisRMax, l);
+    if (better(da, pidA, q.ba, q.pa)) { q.ba = da; q.pa = pidA; }
+    if (better(db, pidB, q.ba, q.pa)) { q.ba = db; q.pa = pidB; }
+  }
+  Active r;
+  r.d2min = q.d2min;
+  r.dlt = q.dlt;
+  r.separated = q.dlt < -eps_sat;
+  r.val = synth_value(q.d2min, q.dlt, eps_sat);
+  r.pen = 0.f;
+  if (SOFT && !r.separated) {
+    r.pen = acc.pen(eta);
+    r.val = soft_key(-r.pen);
+  }
+  r.pid = r.separated ? q.pd : q.pa;
+  r.kind = (int)((r.pid >> kPairShiftKind) & 0xF);
+  r.l = (int)(r.pid & 0xF);
+  const int e = (int)(r.pid >> kPairShiftEdge) - orig_first;
+  // the segment's B endpoint is vertex 1 of a robot-axis pair and vertex 0
+  // (edge 0) of a robot-edge pair
+  r.k = (r.kind == kRAxisOMaxB || r.kind == kRAxisRMaxB) ? 1 : e;
+  r.t = r.separated ? q.dt : 0.f;
+  if (r.pid == PSDF_PAIR_NONE) { r.kind = 0; r.l = 0; r.k = 0; }
+  return r;
+}
+
 template <int M, bool SOFT = false>
 __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px, float py,
                                                   float c, float s, const float4 *vt, int n,
@@ -424,142 +604,50 @@ __device__ __forceinline__ Active obstacle_detail(const FootprintK &F, float px,
                                                   float eta = 0.f)
 {
   SoftAcc acc;
-  const bool seg = (n == 1);
-  float pmax[M], pmin[M];
-  int kmax[M], kmin[M];
+  DetailAcc<M> q;
+  for (int k = 0; k < n; ++k) detail_edge<M, SOFT>(F, px, py, c, s, vt, n, k, orig_first, q, acc, eta);
+  if (n == 1) detail_seg_b<M>(F, px, py, c, s, vt, orig_first, q);
+  return detail_finish<M, SOFT>(F, n, orig_first, eps_sat, q, acc, eta);
+}
+
+// The same detail by G lanes (G divides 32, groups aligned): lane g of the
+// group takes edges g, g + G, ...; the states are merged by shuffles with
+// the serial loop's tie rules (the lowest (value, pair id); the first vertex
+// reaching an extreme projection), so every lane returns the serial
+// result bit for bit.  Hard minimum only.  Every lane of the warp must call
+// it (n = 0 for a lane group without an obstacle).
+template <int M, int G>
+__device__ __forceinline__ Active obstacle_detail_coop(const FootprintK &F, float px, float py,
+                                                       float c, float s, const float4 *vt,
+                                                       int n, int orig_first, float eps_sat,
+                                                       int g)
+{
+  SoftAcc acc;
+  DetailAcc<M> q;
+  for (int k = g; k < n; k += G) detail_edge<M, false>(F, px, py, c, s, vt, n, k, orig_first, q, acc, 0.f);
+  if (n == 1 && g == 0) detail_seg_b<M>(F, px, py, c, s, vt, orig_first, q);
 #pragma unroll
-  for (int l = 0; l < M; ++l) {
-    pmax[l] = -kInf;
-    pmin[l] = kInf;
-    kmax[l] = 0;
-    kmin[l] = 0;
-  }
-  float d2min = kInf, dlt = kInf;
-  // best distance candidate and best axis candidate
-  float bd = kInf, ba = kInf;
-  unsigned pd = PSDF_PAIR_NONE, pa = PSDF_PAIR_NONE;
-  int dk = 0, dl = 0, dkind = 0, ak = 0, al = 0, akind = 0;
-  float dt_ = 0.f;
-  const float4 a0 = vt[0], b0 = vt[1];
-  const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
-  const int nv = seg ? 2 : n;  // vertex set size
-  for (int k = 0; k < n; ++k) {
-    const float4 ak4 = vt[2 * k], bk4 = vt[2 * k + 1];
-    const V2 A = (k == 0) ? A0 : to_local(ak4.x, ak4.y, px, py, c, s);
-    V2 B;
-    float bwx, bwy;  // world B
-    if (seg) {
-      bwx = b0.z;
-      bwy = b0.w;
-      B = to_local(b0.z, b0.w, px, py, c, s);
-    } else if (k + 1 < n) {
-      const float4 an = vt[2 * (k + 1)];
-      bwx = an.x;
-      bwy = an.y;
-      B = to_local(an.x, an.y, px, py, c, s);
-    } else {
-      bwx = a0.x;
-      bwy = a0.y;
-      B = A0;
-    }
-    const V2 U = local_edge(ak4.x, ak4.y, bwx, bwy, c, s);
-    const float ux = U.x, uy = U.y;
-    const int edge = orig_first + k;
-    float smin = kInf, smax = -kInf;
-    int lsmin = 0, lsmax = 0;
+  for (int o = 1; o < G; o <<= 1) {
+    q.d2min = fminf(q.d2min, __shfl_xor_sync(0xffffffffu, q.d2min, o));
+    q.dlt = fminf(q.dlt, __shfl_xor_sync(0xffffffffu, q.dlt, o));
+    const float bd = __shfl_xor_sync(0xffffffffu, q.bd, o);
+    const unsigned pd = __shfl_xor_sync(0xffffffffu, q.pd, o);
+    const float dt = __shfl_xor_sync(0xffffffffu, q.dt, o);
+    if (better(bd, pd, q.bd, q.pd)) { q.bd = bd; q.pd = pd; q.dt = dt; }
+    const float ba = __shfl_xor_sync(0xffffffffu, q.ba, o);
+    const unsigned pa = __shfl_xor_sync(0xffffffffu, q.pa, o);
+    if (better(ba, pa, q.ba, q.pa)) { q.ba = ba; q.pa = pa; }
 #pragma unroll
     for (int l = 0; l < M; ++l) {
-      const float wx = __fsub_rn(F.vx[l], A.x), wy = __fsub_rn(F.vy[l], A.y);
-      const float t = __saturatef(__fmul_rn(__fmaf_rn(wx, ux, __fmul_rn(wy, uy)), ak4.z));
-      float rx = __fmaf_rn(-t, ux, wx), ry = __fmaf_rn(-t, uy, wy);
-      if (seg) {
-        rx = (t == 1.0f) ? __fsub_rn(F.vx[l], B.x) : rx;
-        ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
-      }
-      const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
-      if (seg || t < 1.0f) {
-        d2min = fminf(d2min, d2);
-        const unsigned pid = make_pid(edge, kVertEdge, l);
-        if (better(d2, pid, bd, pd)) { bd = d2; pd = pid; dkind = kVertEdge; dl = l; dk = k; dt_ = t; }
-      }
-      const float sl = __fmaf_rn(wy, ux, -__fmul_rn(wx, uy));
-      if (sl < smin) { smin = sl; lsmin = l; }
-      if (sl > smax) { smax = sl; lsmax = l; }
-      const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
-      const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
-      const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
-      if (tp > 0.0f && tp < 1.0f) {
-        d2min = fminf(d2min, d2p);
-        const unsigned pid = make_pid(edge, kObsVRobotEdge, l);
-        if (better(d2p, pid, bd, pd)) { bd = d2p; pd = pid; dkind = kObsVRobotEdge; dl = l; dk = k; dt_ = tp; }
-      }
-      const float pr = __fmaf_rn(A.x, F.nx[l], __fmul_rn(A.y, F.ny[l]));
-      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = k; }
-      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = k; }
-    }
-    const float da = __fmaf_rn(-smin, ak4.w, bk4.y);
-    const float db = __fmaf_rn(smax, ak4.w, -bk4.x);
-    dlt = fminf(dlt, fminf(da, db));
-    if (SOFT) acc.add(fminf(da, db), eta);
-    {
-      const unsigned pid = make_pid(edge, kOAxisOMax, lsmin);
-      if (better(da, pid, ba, pa)) { ba = da; pa = pid; akind = kOAxisOMax; al = lsmin; ak = k; }
-    }
-    {
-      const unsigned pid = make_pid(edge, kOAxisRMax, lsmax);
-      if (better(db, pid, ba, pa)) { ba = db; pa = pid; akind = kOAxisRMax; al = lsmax; ak = k; }
+      const float vmx = __shfl_xor_sync(0xffffffffu, q.pmax[l], o);
+      const int kmx = __shfl_xor_sync(0xffffffffu, q.kmax[l], o);
+      if (vmx > q.pmax[l] || (vmx == q.pmax[l] && kmx < q.kmax[l])) { q.pmax[l] = vmx; q.kmax[l] = kmx; }
+      const float vmn = __shfl_xor_sync(0xffffffffu, q.pmin[l], o);
+      const int kmn = __shfl_xor_sync(0xffffffffu, q.kmin[l], o);
+      if (vmn < q.pmin[l] || (vmn == q.pmin[l] && kmn < q.kmin[l])) { q.pmin[l] = vmn; q.kmin[l] = kmn; }
     }
   }
-  if (seg) {
-    // the segment's B endpoint: robot-edge distances and axis projections
-    const V2 Bv = to_local(b0.z, b0.w, px, py, c, s);
-#pragma unroll
-    for (int l = 0; l < M; ++l) {
-      const float wx = __fsub_rn(F.vx[l], Bv.x), wy = __fsub_rn(F.vy[l], Bv.y);
-      const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
-      const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
-      const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
-      if (tp > 0.0f && tp < 1.0f) {
-        d2min = fminf(d2min, d2p);
-        const unsigned pid = make_pid(orig_first, kObsBRobotEdge, l);
-        if (better(d2p, pid, bd, pd)) { bd = d2p; pd = pid; dkind = kObsBRobotEdge; dl = l; dk = 0; dt_ = tp; }
-      }
-      const float pr = __fmaf_rn(Bv.x, F.nx[l], __fmul_rn(Bv.y, F.ny[l]));
-      if (pr > pmax[l]) { pmax[l] = pr; kmax[l] = 1; }
-      if (pr < pmin[l]) { pmin[l] = pr; kmin[l] = 1; }
-    }
-  }
-  (void)nv;
-#pragma unroll
-  for (int l = 0; l < M; ++l) {
-    const float da = __fsub_rn(pmax[l], F.alo[l]);
-    const float db = __fsub_rn(F.ahi[l], pmin[l]);
-    dlt = fminf(dlt, fminf(da, db));
-    if (SOFT) acc.add(fminf(da, db), eta);
-    const bool bA = seg && kmax[l] == 1, bB = seg && kmin[l] == 1;
-    const int eA = seg ? orig_first : orig_first + kmax[l];
-    const int eB = seg ? orig_first : orig_first + kmin[l];
-    const unsigned pidA = make_pid(eA, bA ? kRAxisOMaxB : kRAxisOMax, l);
-    const unsigned pidB = make_pid(eB, bB ? kRAxisRMaxB : kRAxisRMax, l);
-    if (better(da, pidA, ba, pa)) { ba = da; pa = pidA; akind = bA ? kRAxisOMaxB : kRAxisOMax; al = l; ak = kmax[l]; }
-    if (better(db, pidB, ba, pa)) { ba = db; pa = pidB; akind = bB ? kRAxisRMaxB : kRAxisRMax; al = l; ak = kmin[l]; }
-  }
-  Active r;
-  r.d2min = d2min;
-  r.dlt = dlt;
-  r.separated = dlt < -eps_sat;
-  r.val = synth_value(d2min, dlt, eps_sat);
-  r.pen = 0.f;
-  if (SOFT && !r.separated) {
-    r.pen = acc.pen(eta);
-    r.val = soft_key(-r.pen);
-  }
-  if (r.separated) {
-    r.pid = pd; r.kind = dkind; r.l = dl; r.k = dk; r.t = dt_;
-  } else {
-    r.pid = pa; r.kind = akind; r.l = al; r.k = ak; r.t = 0.f;
-  }
-  return r;
+  return detail_finish<M, false>(F, n, orig_first, eps_sat, q, acc, 0.f);
 }
 
 // Pose gradient and edge-gradient contributions of one active pair
@@ -912,6 +1000,8 @@ __device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_
   const int rank = (int)(unsigned)(key & 0xffffffffu);
   const ObsRec o = row_obs[rank];
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  prefetch_lines(vt, 32 * o.n);
+  if (want_grad) prefetch_lines(far + o.vtx_global, 4 * o.n);
   const Active a = obstacle_detail<M, SOFT>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat, eta);
   r.pid = a.pid;
   if (SOFT && !a.separated) {
@@ -936,6 +1026,40 @@ __device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_
   return r;
 }
 
+// epilogue_pose of the hard minimum by G lanes per pose (lane g of the
+// group; see obstacle_detail_coop): the detail is shared out over the
+// obstacle's edges, the gradient is taken by lane 0 of the group alone (the
+// other lanes return it as zero).  Every lane of the warp must call it.
+template <int M, int G>
+__device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float eps_sat,
+                                                      float eps_axis, float px, float py,
+                                                      float theta, unsigned long long key,
+                                                      const ObsRec *__restrict__ row_obs,
+                                                      const float4 *__restrict__ vtx,
+                                                      const int *__restrict__ far,
+                                                      bool want_grad, int g)
+{
+  PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
+  const bool none = key == ~0ull;
+  ObsRec o{0, 0, 0, 0};
+  if (!none) o = row_obs[(int)(unsigned)(key & 0xffffffffu)];
+  float s, c;
+  sincosf(theta, &s, &c);
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  const Active a = obstacle_detail_coop<M, G>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat, g);
+  if (none) return r;
+  r.pid = a.pid;
+  r.phi = a.separated ? sqrtf(a.val) : a.val;
+  if (want_grad && g == 0 && (a.separated || a.dlt > 0.f)) {
+    const Grad gr = active_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first,
+                                   a.kind, a.l, a.k, a.t, eps_axis);
+    r.g[0] = gr.gp[0];
+    r.g[1] = gr.gp[1];
+    r.g[2] = gr.gp[2];
+  }
+  return r;
+}
+
 // Closed-form gradient of one pose's active pair (pid) w.r.t. the pose and
 // the stored edge endpoints (rows of the pose's scene).  False when the pair
 // is none, out of range, or on the flat branch of max(delta, 0).
@@ -954,6 +1078,8 @@ __device__ __forceinline__ bool backward_pose(const FootprintK &F, float eps_axi
   const ObsRec o = row_obs[row];
   if (o.n == 0) return false;
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  prefetch_lines(vt, 32 * o.n);
+  prefetch_lines(far + o.vtx_global, 4 * o.n);
   int k = (int)(row - o.orig_first);
   if (kind == kObsBRobotEdge || kind == kRAxisOMaxB || kind == kRAxisRMaxB) k = 0;
   float s, c;
