@@ -12,14 +12,14 @@
 //                      list the pose for the proposed tiles and for every other
 //                      tile whose lower bound does not exceed UB (the cell's
 //                      list holds them all when UB's reach is within the
-//                      cell's; else every tile is tested).  The CTA that
-//                      finishes last turns the per-tile counts into work units
-//   2. eval_lists      persistent CTAs over units: the tile's blob staged in shared
-//                      memory, lanes = (pose, obstacle range) pairs so that
-//                      warps stay full; an obstacle whose circle bound exceeds
-//                      the lane's threshold (UB, then the smallest value seen)
-//                      is skipped, the others are evaluated exactly; one
-//                      atomicMin per lane into the pose's 64-bit key
+//                      cell's; else every tile is tested)
+//   2. eval_lists      two CTAs per tile, launched while the proposals finish:
+//                      the tile's blob staged in shared memory, then the
+//                      tile's lanes = (pose, obstacle range) pairs in units of
+//                      128 so that warps stay full; an obstacle whose circle
+//                      bound exceeds the pose's upper bound is skipped, the
+//                      others are evaluated exactly; one atomicMin per
+//                      evaluated obstacle into the pose's 64-bit key
 //   3. epilogue        as for the full scan
 // Every tile holding a value at or below phi has a lower bound <= phi <= UB,
 // so it is listed; every obstacle skipped has a value above the threshold,
@@ -57,25 +57,15 @@ struct CullCounters {
   int n_prop;          // proposed (pose, tile) pairs
   int n_fb;            // (pose, tile) pairs added by the bound check
   int fallback_poses;  // poses with at least one such pair
-  unsigned done1;      // CTAs of the propose kernel that finished
-  int n_items;         // all listed (pose, tile) pairs
   unsigned long long n_obs_eval;   // obstacles evaluated exactly
   unsigned long long n_edge_eval;  // edges of those obstacles
 };
 
 struct CullLayout {
-  size_t hist, clear_bytes, keys, pose4, ub, prop, uoff, utile, list, total;
-  long long cap;  // capacity of the unit map
+  size_t hist, clear_bytes, keys, pose4, ub, prop, list, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-
-// Work units of a tile with cnt listed poses: at most 2 while cnt <= 256,
-// else ceil(cnt / 128); over all tiles at most 3 T + items / 128.
-static long long unit_capacity(long long items, int n_tiles)
-{
-  return 3LL * n_tiles + items / 128 + 1;
-}
 
 // Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]).
 // The counters and the per-tile histogram are contiguous (one memset).
@@ -84,7 +74,6 @@ static CullLayout cull_layout(long long P, int n_tiles)
   CullLayout L;
   const size_t Pz = (size_t)std::max<long long>(P, 1);
   const size_t Tz = (size_t)std::max(n_tiles, 1);
-  L.cap = unit_capacity((long long)Pz * Tz, (int)Tz);
   size_t o = 256;
   L.hist = o; o = align256(o + 4 * Tz);
   L.clear_bytes = o;
@@ -92,8 +81,6 @@ static CullLayout cull_layout(long long P, int n_tiles)
   L.pose4 = o; o = align256(o + 16 * Pz);
   L.ub = o; o = align256(o + 4 * Pz);
   L.prop = o; o = align256(o + 4 * Pz * kMaxK);
-  L.uoff = o; o = align256(o + 4 * (Tz + 1));
-  L.utile = o; o = align256(o + 4 * (size_t)L.cap);
   L.list = o; o = align256(o + 4 * Pz * Tz);
   L.total = o;
   return L;
@@ -312,83 +299,6 @@ __device__ __forceinline__ int tile_units(int cnt, int n_obs)
   return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
 }
 
-// Run by one whole CTA of kPoseThreads threads once every append to hist is
-// done: exclusive prefix sum of the tiles' units -> uoff[t] (uoff[T] = total),
-// the unit -> tile map utile[u], and the number of listed pairs -> *items.
-// Chunks of kPoseThreads x 8 tiles, each thread a run of 8 (its loads issued
-// together).  hist was written by atomics of other CTAs: read through L2.
-__device__ void build_units(const int *hist, const TileHdr *__restrict__ tiles, int T,
-                            int *__restrict__ uoff, int *__restrict__ utile, int *items)
-{
-  constexpr int kRun = 8, kWarps = kPoseThreads / 32;
-  __shared__ int w_units[kWarps], w_items[kWarps];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int carry = 0, items_total = 0;
-  for (int c0 = 0; c0 < T; c0 += kPoseThreads * kRun) {
-    const int b0 = c0 + tid * kRun;
-    int cnt[kRun], nob[kRun];
-#pragma unroll
-    for (int i = 0; i < kRun; ++i) {
-      cnt[i] = (b0 + i < T) ? __ldcg(hist + b0 + i) : 0;
-      nob[i] = (b0 + i < T) ? tiles[b0 + i].n_obs : 1;
-    }
-    int su = 0, si = 0;
-#pragma unroll
-    for (int i = 0; i < kRun; ++i) {
-      su += tile_units(cnt[i], nob[i]);
-      si += cnt[i];
-    }
-    int incl = su, isum = si;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += n;
-      isum += __shfl_xor_sync(0xffffffffu, isum, o);
-    }
-    if (lane == 31) w_units[warp] = incl;
-    if (lane == 0) w_items[warp] = isum;
-    __syncthreads();
-    int ubase = carry + incl - su;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      if (w < warp) ubase += w_units[w];
-      carry += w_units[w];
-      items_total += w_items[w];
-    }
-#pragma unroll
-    for (int i = 0; i < kRun; ++i) {
-      if (b0 + i < T) {
-        const int nu = tile_units(cnt[i], nob[i]);
-        uoff[b0 + i] = ubase;
-        for (int k = 0; k < nu; ++k) utile[ubase + k] = b0 + i;
-        ubase += nu;
-      }
-    }
-    __syncthreads();  // w_units / w_items are reused by the next chunk
-  }
-  if (tid == 0) {
-    uoff[T] = carry;
-    *items = items_total;
-  }
-}
-
-// True in every thread of the CTA that finished last; the counter is
-// cleared before the launch.  Thread 0's device-scope fence after the
-// barrier orders the whole CTA's earlier writes before its ticket; the last
-// CTA's fence after reading the final ticket orders its later reads.
-__device__ __forceinline__ bool last_cta(unsigned *done)
-{
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(done, 1u) == gridDim.x - 1;
-    if (last) __threadfence();
-  }
-  __syncthreads();
-  return last;
-}
-
 // Squared distance from p to a tile's AABB: the bound's ranking key (the
 // bound is increasing in the distance, so no square root is needed to rank).
 __device__ __forceinline__ float aabb_d2(float4 a4, float px, float py)
@@ -465,7 +375,7 @@ __global__ void __launch_bounds__(kPoseThreads)
             int T, const CullGrid grid, float rfoot, const unsigned char *__restrict__ blob,
             const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
             float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
-            int *hist, int *__restrict__ list, int *__restrict__ uoff, int *__restrict__ utile,
+            int *hist, int *__restrict__ list,
             CullCounters *ctr)
 {
   constexpr int R = NET ? kPre : K;  // candidates merged per pose
@@ -665,7 +575,6 @@ __global__ void __launch_bounds__(kPoseThreads)
     atomicAdd(&ctr->fallback_poses, s_fbp);
   }
   pdl_trigger();  // the evaluation kernel may launch; it waits for this grid
-  if (last_cta(&ctr->done1)) build_units(hist, tiles, T, uoff, utile, &ctr->n_items);
 }
 
 // ---------------------------------------------------------------------------
@@ -684,16 +593,18 @@ __device__ __forceinline__ void cp_async_wait_all()
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Persistent CTAs over work units.  Unit u belongs to tile t = utile[u] and
-// covers lanes [(u - uoff[t]) * 128, +128) of the tile's cnt * S lanes; lane
-// l takes pose list[t * P + l / S] and obstacle range l % S of the tile.  The
-// tile's blob and its obstacle circles are staged in shared memory (16-byte
-// cp.async per thread) once per unit.  Each lane tests its obstacles'
+// kTileCTAs CTAs per tile: CTA j of tile t takes the tile's work units j,
+// j + kTileCTAs, ... (unit i covers lanes [128 i, 128 i + 128) of the tile's
+// cnt * S lanes); lane l takes pose list[t * P + l / S] and obstacle range
+// l % S of the tile.  The tile's blob and its obstacle circles are staged in
+// shared memory (16-byte cp.async per thread) before the CTA waits for the
+// proposals (they are pose-invariant).  Each lane tests its obstacles'
 // circle bounds against the pose's upper bound; the survivors of the warp's
 // 32 lanes are compacted (ballot) into a per-warp queue and evaluated 32 at
 // a time, one (pose, obstacle) item per lane, so that lanes whose obstacles
 // were skipped do not idle through their neighbours' evaluations.  Every
 // evaluated obstacle merges its key into the pose's by atomicMin.
+constexpr int kTileCTAs = 2;
 constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
 
 template <int M>
@@ -724,8 +635,7 @@ template <int M>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
                const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
-               const int *__restrict__ hist, const int *__restrict__ uoff,
-               const int *__restrict__ utile, long long cap, const int *__restrict__ list,
+               const int *__restrict__ hist, const int *__restrict__ list,
                const float *__restrict__ ub, unsigned long long *__restrict__ keys,
                CullCounters *ctr)
 {
@@ -733,37 +643,38 @@ __global__ void __launch_bounds__(kListThreads)
   __shared__ int queue[kListThreads / 32][kQueue];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int *qw = queue[warp];
-  pdl_wait();  // the proposal kernel's lists and units
-  const int U = uoff[T];
-  unsigned long long n_obs = 0, n_edge = 0;
-  for (int u = blockIdx.x; u < U && u < cap; u += gridDim.x) {
-    const int t = utile[u];
-    const TileHdr h = tiles[t];
-    const int cnt = hist[t];
-    const int S = tile_split(cnt, h.n_obs);
-    const long long L = (long long)cnt * S;
-    const long long l = (long long)(u - uoff[t]) * kListThreads + threadIdx.x;
+  const int t = (int)(blockIdx.x / kTileCTAs), j0 = (int)(blockIdx.x % kTileCTAs);
+  const TileHdr h = tiles[t];
+  {
     const unsigned char *src = blob + h.blob_off;
     const int bytes = h.blob_bytes + 16 * h.n_obs;  // records + circles
-    __syncthreads();  // the previous unit's reads of the staged tile are done
     for (int o = 16 * threadIdx.x; o < bytes; o += 16 * kListThreads)
       cp_async16(tsm + o, src + o);
+  }
+  pdl_wait();  // the proposal kernel's lists
+  const int cnt = __ldcg(hist + t);
+  const int S = tile_split(cnt, h.n_obs);
+  const long long L = (long long)cnt * S;
+  const int units = tile_units(cnt, h.n_obs);
+  cp_async_wait_all();
+  __syncthreads();
+  const int4 *ob = reinterpret_cast<const int4 *>(tsm);
+  const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
+  const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
+  unsigned long long n_obs = 0, n_edge = 0;
+  for (int j = j0; j < units; j += kTileCTAs) {
+    const long long l = (long long)j * kListThreads + threadIdx.x;
     long long p = -1;
-    if (l < L) p = list[(long long)t * P + l / S];
-    cp_async_wait_all();
-    __syncthreads();
-    const int4 *ob = reinterpret_cast<const int4 *>(tsm);
-    const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
-    const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
+    if (l < L) p = __ldcg(list + (long long)t * P + l / S);
     float px = 0.f, py = 0.f, c = 1.f, s = 0.f, thr = -kInf;
     int o0 = 0, o1 = 0;
     if (p >= 0) {
-      const float4 q4 = pose4[p];
+      const float4 q4 = __ldcg(pose4 + p);
       px = q4.x;
       py = q4.y;
       c = q4.z;
       s = q4.w;
-      thr = ub_value(ub[p]);
+      thr = ub_value(__ldcg(ub + p));
       const int part = (int)(l % S);
       o0 = (int)((long long)h.n_obs * part / S);
       o1 = (int)((long long)h.n_obs * (part + 1) / S);
@@ -791,6 +702,7 @@ __global__ void __launch_bounds__(kListThreads)
       __syncwarp();
       eval_items<M>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
     }
+    __syncwarp();  // the queue is refilled by the next unit
   }
   pdl_trigger();  // the epilogue may launch; it waits for this grid
   // evaluated obstacles and edges (the roofline's work count)
@@ -904,8 +816,8 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 template <int M>
 struct ListEvalCall {
   static int run(const FootprintK &F, const ParamsK &pk, const float4 *pose4, long long P,
-                 const psdf_scene *sc, const int *hist, const int *uoff, const int *utile,
-                 long long cap, const int *list, const float *ub, unsigned long long *keys,
+                 const psdf_scene *sc, const int *hist,
+                 const int *list, const float *ub, unsigned long long *keys,
                  CullCounters *ctr, cudaStream_t st)
   {
     const size_t smem = (size_t)(sc->max_blob_ext_bytes + 15) / 16 * 16;
@@ -915,12 +827,11 @@ struct ListEvalCall {
                                            (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
-    const int grid = device_sms() * 8;
+    const unsigned grid = (unsigned)sc->n_tiles * kTileCTAs;
     // follows the proposal kernel: may start while it finishes
     cudaError_t e = launch_pdl(eval_lists<M>, dim3(grid), dim3(kListThreads), smem, st, F, pk,
                                pose4, P, (const TileHdr *)sc->d_tiles, sc->n_tiles,
-                               (const unsigned char *)sc->d_blob, hist, uoff, utile, cap, list,
-                               ub, keys, ctr);
+                               (const unsigned char *)sc->d_blob, hist, list, ub, keys, ctr);
     return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (eval_lists)");
   }
 };
@@ -1136,8 +1047,6 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   float *ub = reinterpret_cast<float *>(ws + L.ub);
   int *prop = reinterpret_cast<int *>(ws + L.prop);
   int *hist = reinterpret_cast<int *>(ws + L.hist);
-  int *uoff = reinterpret_cast<int *>(ws + L.uoff);
-  int *utile = reinterpret_cast<int *>(ws + L.utile);
   int *list = reinterpret_cast<int *>(ws + L.list);
   ParamsK pk{params->eps_sat, params->eta};
   cudaError_t e = cudaMemsetAsync(ws, 0, L.clear_bytes, st);
@@ -1157,13 +1066,11 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   if (net)                                                                                   \
     propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid, \
                                                    F.radius, scene->d_blob, frag, b2, keys,     \
-                                                   pose4, ub, prop, hist, list, uoff, utile,    \
-                                                   ctr);                                        \
+                                                   pose4, ub, prop, hist, list, ctr);           \
   else                                                                                          \
     propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid,   \
                                                     F.radius, scene->d_blob, frag, b2, keys,    \
-                                                    pose4, ub, prop, hist, list, uoff, utile,   \
-                                                    ctr);
+                                                    pose4, ub, prop, hist, list, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -1175,8 +1082,7 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     {
       ProfileScope prof("cull_eval", st);
       rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
-                                         (const int *)hist, (const int *)uoff,
-                                         (const int *)utile, L.cap, (const int *)list,
+                                         (const int *)hist, (const int *)list,
                                          (const float *)ub, keys, ctr, st);
       if (rc) return rc;
     }

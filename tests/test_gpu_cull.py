@@ -60,6 +60,18 @@ def test_cull_equals_full_scan_dense_clutter(mode, k):
     assert st.evaluated_edges == 4 * st.evaluated_obstacles  # rectangles
 
 
+def test_cull_equals_full_scan_many_tiles():
+    """6,250 tiles of 16 edges: beyond the tile count whose work units each
+    evaluation CTA lays out itself, so the proposal kernel's last CTA writes
+    them to global memory."""
+    w = sg.dense_clutter(4, n_poses=2048)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=16)
+    assert scene.info().n_tiles > 4096
+    poses = torch.as_tensor(w.poses, device="cuda")
+    _compare_cull(w, scene, poses, k=1)
+    _compare_cull(w, scene, poses, mlp=_random_mlp(4), k=2)
+
+
 def test_cull_equals_full_scan_octagon_lidar_and_ragged():
     w = sg.octagon_lidar(1)
     scene = psdf.Scene.from_csr(w.edges, w.offsets)
