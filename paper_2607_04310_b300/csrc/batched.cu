@@ -352,7 +352,8 @@ __global__ void batched_backward_kernel(const int *__restrict__ pose_inst, long 
     grad_pose[3 * p + 2] = has ? gphi * g.gp[2] : 0.f;
   }
   if (has && grad_edges) {
-    for (int r = 0; r < g.nrow; ++r) {
+    for (int r = 0; r < kGradRows; ++r) {
+      if (r >= g.nrow) break;
       const long long row = in.row0 + g.row[r];
       atomicAdd(&grad_edges[4 * row + g.col[r]], gphi * g.gx[r]);
       atomicAdd(&grad_edges[4 * row + g.col[r] + 1], gphi * g.gy[r]);

@@ -241,7 +241,8 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
                          g2 = __fmaf_rn(w, g.gp[2], g2);
                          if (grad_edges) {
                            const float sc = gphi * w;
-                           for (int i = 0; i < g.nrow; ++i) {
+                           for (int i = 0; i < kGradRows; ++i) {
+                             if (i >= g.nrow) break;
                              atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]],
                                        sc * g.gx[i]);
                              atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1],
@@ -268,7 +269,8 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
     grad_pose[3 * p + 2] = has ? gphi * g.gp[2] : 0.f;
   }
   if (has && grad_edges) {
-    for (int i = 0; i < g.nrow; ++i) {
+    for (int i = 0; i < kGradRows; ++i) {
+      if (i >= g.nrow) break;
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]], gphi * g.gx[i]);
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1], gphi * g.gy[i]);
     }

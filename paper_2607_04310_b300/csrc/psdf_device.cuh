@@ -652,25 +652,35 @@ __device__ __forceinline__ Active obstacle_detail_coop(const FootprintK &F, floa
 
 // Pose gradient and edge-gradient contributions of one active pair
 // (active-branch subgradient of Sec. IV-D, closed form per kind).
+constexpr int kGradRows = 3;  // edge-endpoint slots an active pair touches
 struct Grad {
   float gp[3];     // d sd / d (px, py, theta)
   int nrow;        // edge contributions: caller row, slot column (0 = A, 2 = B)
-  int row[3], col[3];
-  float gx[3], gy[3];
+  int row[kGradRows], col[kGradRows];
+  float gx[kGradRows], gy[kGradRows];
 };
 
+// Adds (gx, gy) to the slot of (row, col), opening one if none holds it.
+// Fixed-size loops, so that the slots stay in registers.
 __device__ __forceinline__ void add_row(Grad &g, int row, int col, float gx, float gy)
 {
-  for (int i = 0; i < g.nrow; ++i)
-    if (g.row[i] == row && g.col[i] == col) {
+  bool merged = false;
+#pragma unroll
+  for (int i = 0; i < kGradRows; ++i)
+    if (!merged && i < g.nrow && g.row[i] == row && g.col[i] == col) {
       g.gx[i] = __fadd_rn(g.gx[i], gx);
       g.gy[i] = __fadd_rn(g.gy[i], gy);
-      return;
+      merged = true;
     }
-  g.row[g.nrow] = row;
-  g.col[g.nrow] = col;
-  g.gx[g.nrow] = gx;
-  g.gy[g.nrow] = gy;
+  if (merged) return;
+#pragma unroll
+  for (int i = 0; i < kGradRows; ++i)
+    if (i == g.nrow) {
+      g.row[i] = row;
+      g.col[i] = col;
+      g.gx[i] = gx;
+      g.gy[i] = gy;
+    }
   ++g.nrow;
 }
 
