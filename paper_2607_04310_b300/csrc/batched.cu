@@ -8,15 +8,14 @@
 // concatenated, so each instance's results equal psdf_eval_grad's bit for bit.
 //
 // Work: an item is (pose block, run of the instance's tiles).  A pose block
-// holds up to `threads` poses of one instance; when it holds fewer poses than
-// lanes, lane l takes pose l % n and obstacle range l / n of each tile, so a
-// short horizon still fills the CTA.  Items are sorted by decreasing work and
+// holds up to `threads` poses of one instance; the (pose, obstacle) pairs of
+// each tile are dealt round-robin over the lanes, so a short horizon still
+// fills the CTA evenly.  Items are sorted by decreasing work and
 // taken from an atomic queue by persistent CTAs; tiles stream through shared
-// memory by TMA bulk copies (double-buffered, bounded waits).  Each lane merges
-// its 64-bit min-key into the pose's key with one atomicMin per item, and the
-// CTA that completes the last item of a pose block (counter per block, device
-// fence before the ticket) runs the block's epilogue: value, active pair and
-// closed-form gradient.  No CTA ever waits for another.
+// memory by TMA bulk copies (double-buffered, bounded waits).  Pair keys are
+// merged per pose in shared memory and into the pose's global 64-bit key with
+// one atomicMin per pose per item; an epilogue kernel then writes value,
+// active pair and closed-form gradient.  No CTA ever waits for another.
 //
 // Autotuner: a grid of (threads, tiles per item) is timed on the caller's
 // poses; the fastest is kept and cached per plan shape for the process.
@@ -97,14 +96,18 @@ __device__ __forceinline__ bool dbg_ok(bool cond, int site, long long idx)
 // ---------------------------------------------------------------------------
 // device
 // ---------------------------------------------------------------------------
-// One item: lanes (pose l % npose, obstacle range l / npose) over the item's
-// tiles.  False when a bounded wait ran out (uniform over the CTA).
+// One item: for each of the item's tiles the npose x n_obs (pose, obstacle)
+// pairs are dealt round-robin over all lanes, so that every lane has the
+// same share whatever the horizon; a pair's key goes into the pose's key in
+// shared memory, and the block's keys into global memory once per item.
+// False when a bounded wait ran out (uniform over the CTA).
 template <int M>
 __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__restrict__ poses,
                           long long pose0, int npose, const TileHdr *__restrict__ tiles,
                           const unsigned char *__restrict__ blob, int tile0, int ntile,
                           unsigned char *buf0, int blob_cap, uint64_t *bars, unsigned &phase,
-                          unsigned long long *keys, const PlanBounds &bnd)
+                          float4 *spose, unsigned long long *skey, unsigned long long *keys,
+                          const PlanBounds &bnd)
 {
   if (ntile == 0) return true;
 #ifdef PSDF_DEBUG_CHECKS
@@ -117,15 +120,16 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
     if (!PSDF_DBG(good, 6, tile0 + k)) return true;
   }
 #endif
-  const int S = max(1, (int)blockDim.x / npose);
-  const int j = threadIdx.x % npose, part = threadIdx.x / npose;
-  const bool live = part < S;
-  float px = 0.f, py = 0.f, c = 1.f, s = 0.f;
-  if (live) {
+  // pair i = pose i % npose, obstacle i / npose: a stride of blockDim.x
+  // pairs moves the pose by dj and the obstacle by do_ (plus a carry)
+  const int dj = (int)blockDim.x % npose, do_ = (int)blockDim.x / npose;
+  // the block's poses (x, y, cos, sin) and their keys for this item
+  for (int j = threadIdx.x; j < npose; j += blockDim.x) {
     const long long p = pose0 + j;
-    px = poses[3 * p];
-    py = poses[3 * p + 1];
-    sincosf(poses[3 * p + 2], &s, &c);
+    float sn, cs;
+    sincosf(poses[3 * p + 2], &sn, &cs);
+    spose[j] = make_float4(poses[3 * p], poses[3 * p + 1], cs, sn);
+    skey[j] = ~0ull;
   }
   if (threadIdx.x == 0) {
     const TileHdr h = tiles[tile0];
@@ -134,7 +138,6 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
     bulk_g2s(buf0, blob + h.blob_off, (unsigned)h.blob_bytes, &bars[0]);
   }
   unsigned pending = 1u;
-  unsigned long long best = ~0ull;
   bool ok = true;
   for (int k = 0; k < ntile; ++k) {
     const int b = k & 1;
@@ -160,19 +163,37 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
     const unsigned char *tb = buf0 + b * blob_cap;
     const int4 *ob = reinterpret_cast<const int4 *>(tb);
     const float4 *vt = reinterpret_cast<const float4 *>(tb + 16 * h.n_obs);
-    if (live) {
-      const int o0 = h.n_obs * part / S, o1 = h.n_obs * (part + 1) / S;
-      for (int o = o0; o < o1; ++o) {
-        const int4 rec = ob[o];
-        if (!PSDF_DBG(rec.x >= 0 && rec.y >= 1 && rec.y <= kMaxObsEdges &&
-                          rec.x + (rec.y == 1 ? 1 : rec.y) <= h.n_vtx,
-                      7, tile0 + k))
-          continue;
-        const float v = obstacle_value<M>(F, px, py, c, s, vt + 2 * rec.x, rec.y, eps_sat);
+    // (pose, obstacle) pairs of the tile dealt round-robin over all lanes:
+    // pair i = pose i % npose, obstacle i / npose
+    // (the lane's pose advances by dj and its obstacle by do_ per pair; a
+    // lane keeps its best key while its pose stays the same)
+    const int n_obs = h.n_obs;
+    int j = (int)threadIdx.x % npose, o = (int)threadIdx.x / npose;
+    int cur = -1;
+    unsigned long long best = ~0ull;
+    for (; o < n_obs; o += do_) {
+      const int4 rec = ob[o];
+      if (PSDF_DBG(rec.x >= 0 && rec.y >= 1 && rec.y <= kMaxObsEdges &&
+                       rec.x + (rec.y == 1 ? 1 : rec.y) <= h.n_vtx,
+                   7, tile0 + k)) {
+        const float4 q = spose[j];
+        const float v = obstacle_value<M>(F, q.x, q.y, q.z, q.w, vt + 2 * rec.x, rec.y, eps_sat);
         const unsigned long long key = pack_key(v, rec.z);
-        best = key < best ? key : best;
+        if (j != cur) {
+          if (cur >= 0) atomicMin(&skey[cur], best);
+          cur = j;
+          best = key;
+        } else {
+          best = key < best ? key : best;
+        }
+      }
+      j += dj;
+      if (j >= npose) {
+        j -= npose;
+        ++o;
       }
     }
+    if (cur >= 0) atomicMin(&skey[cur], best);
     __syncthreads();
   }
   if (!ok) {
@@ -182,7 +203,8 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
       if ((pending >> q) & 1u) (void)mbar_wait_bounded(&bars[q], (phase >> q) & 1u);
     return false;
   }
-  if (live && best != ~0ull) atomicMin(&keys[pose0 + j], best);
+  for (int j = threadIdx.x; j < npose; j += blockDim.x)
+    if (skey[j] != ~0ull) atomicMin(&keys[pose0 + j], skey[j]);
   return true;
 }
 
@@ -203,6 +225,8 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
   const FootprintS Fv{Fs->rec, Fs->ivl, Fs->pair};
   unsigned char *buf0 = smem + kPlanSmemHead + kFpBytes;
   __shared__ int s_item;
+  __shared__ float4 spose[kPlanMaxThreads];
+  __shared__ unsigned long long skey[kPlanMaxThreads];
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -239,7 +263,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
 #define PSDF_SCAN_CASE(MM)                                                                    \
   case MM:                                                                                    \
     ok = scan_item<MM>(Fv, eps_sat, poses, B.pose0, B.npose, tiles, blob, I.tile0, I.ntile, \
-                       buf0, blob_cap, bars, phase, keys, bnd);                               \
+                       buf0, blob_cap, bars, phase, spose, skey, keys, bnd);                  \
     break;
       PSDF_FOR_EACH_M(PSDF_SCAN_CASE)
 #undef PSDF_SCAN_CASE
