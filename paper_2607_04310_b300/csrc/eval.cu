@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
 }
 
 constexpr int kEpiLanes = 4;  // lanes sharing one pose's epilogue (hard minimum)
+constexpr int kBwdSpread = 4;  // lanes per pose in the backward (one of them works)
 
 // Per-pose epilogue: value, active pair, optional pose gradient.
 template <int M, bool SOFT = false>
@@ -214,7 +215,11 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 float *__restrict__ grad_edges)
 {
   pdl_wait();
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // one pose per kBwdSpread lanes: fewer poses (and active-pair kinds, whose
+  // gradient branches a warp runs one after another) per warp
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid % kBwdSpread) return;
+  const long long p = gid / kBwdSpread;
   if (p >= P) return;
   const float gphi = grad_phi[p];
   const float px = poses[3 * p], py = poses[3 * p + 1], th = poses[3 * p + 2];
@@ -443,17 +448,17 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
                            const float *grad_phi, float *grad_pose, float *grad_edges,
                            cudaStream_t st)
 {
-  const int blocks = (int)((P + 63) / 64);
+  const unsigned blocks = (unsigned)((P * kBwdSpread + 127) / 128);
   ProfileScope prof("backward", st);
   // usually follows an epilogue on the stream: may start while it finishes
   cudaError_t le;
   if (pk.eta > 0.f)
-    le = launch_pdl(backward_kernel<M, true>, dim3(blocks), dim3(64), 0, st, F, pk, sc->eps_axis,
+    le = launch_pdl(backward_kernel<M, true>, dim3(blocks), dim3(128), 0, st, F, pk, sc->eps_axis,
                     poses, P, (const ObsRec *)sc->d_row_obs, (const float4 *)sc->d_vtx,
                     (const int *)sc->d_far, (long long)sc->rows_total, active, grad_phi,
                     grad_pose, grad_edges);
   else
-    le = launch_pdl(backward_kernel<M, false>, dim3(blocks), dim3(64), 0, st, F, pk,
+    le = launch_pdl(backward_kernel<M, false>, dim3(blocks), dim3(128), 0, st, F, pk,
                     sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                     (const float4 *)sc->d_vtx, (const int *)sc->d_far,
                     (long long)sc->rows_total, active, grad_phi, grad_pose, grad_edges);
