@@ -586,12 +586,11 @@ def run_b300(a, rank, world, local):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = roofline.fp32_peak_tflops(props.multi_processor_count, sm_max)
     items = int(st.proposed_items + st.fallback_items)
-    obs_per_tile = w.M / T
     work = {
         # the obstacles the cull evaluated exactly (circle-bound skips excluded)
         "cull_eval": roofline.flops_evaluated(m, st.evaluated_edges, st.evaluated_obstacles),
-        # two passes of AABB distances over every (pose, tile) + circle upper bounds
-        "propose": roofline.flops_propose(P, T, CULL_K * obs_per_tile),
+        # the tile bounds and obstacle circles the proposals computed (kernel counts)
+        "propose": roofline.flops_propose(st.bound_evaluations, st.circle_evaluations),
     }
     kroof = {}
     for k, f in work.items():
@@ -628,6 +627,8 @@ def run_b300(a, rank, world, local):
                  "fallback_rate": st.fallback_poses / P,
                  "proposed_pairs": int(st.proposed_items),
                  "fallback_pairs": int(st.fallback_items),
+                 "bound_evaluations": int(st.bound_evaluations),
+                 "circle_evaluations": int(st.circle_evaluations),
                  "evaluated_pair_evals_per_s": evaluated_pairs / (ms_step / 1000.0),
                  "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp")},
         "roofline": {"bound": "alu", "kernel": kname[dom],

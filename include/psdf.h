@@ -256,6 +256,8 @@ typedef struct {
   int64_t proposed_items;      /* (pose, tile) pairs listed from the proposals    */
   int64_t fallback_items;      /* (pose, tile) pairs added by the bound check     */
   int64_t fallback_poses;      /* poses with at least one tile beyond the proposal */
+  int64_t bound_evaluations;   /* tile lower bounds computed by the proposals     */
+  int64_t circle_evaluations;  /* obstacle circles behind the upper bounds        */
 } psdf_cull_stats;
 
 /* Tile-proposal network: 16 inputs -> 64 ReLU units -> 1 output, FP16 weights

@@ -59,6 +59,8 @@ struct CullCounters {
   int fallback_poses;  // poses with at least one such pair
   unsigned long long n_obs_eval;   // obstacles evaluated exactly
   unsigned long long n_edge_eval;  // edges of those obstacles
+  unsigned long long n_bound;      // tile bounds the proposals computed
+  unsigned long long n_circ;       // obstacle circles of the proposals' upper bounds
 };
 
 struct CullLayout {
@@ -383,12 +385,14 @@ __global__ void __launch_bounds__(kPoseThreads)
   __shared__ int ct_s[kPoseThreads / 32][2][kPre];
   __shared__ float sc_s[kPoseThreads / 32][2][kPre];
   __shared__ int s_prop, s_fb, s_fbp;
+  __shared__ unsigned s_bound, s_circ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
   const int half = lane >> 4, hl = lane & 15;
   const long long p = pw + half;
   const bool valid = p < P;
-  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = 0;
+  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = s_bound = s_circ = 0;
+  unsigned n_bound = 0, n_circ = 0;  // this lane's tile bounds and circles
   float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
   int e0 = 0, e1 = 0;  // the cell's list, or all tiles (cell < 0)
   int cell = -1;
@@ -418,6 +422,7 @@ __global__ void __launch_bounds__(kPoseThreads)
   for (int i = lo; i < hi; i += 16) {
     const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
     topk_insert<RL>(sc, id, aabb_d2(tile_aabb(tiles, t), px, py), t);
+    ++n_bound;
   }
   pdl_wait();  // no-op: the proposal kernel follows a memset
   __syncthreads();  // s_prop, s_fb, s_fbp initialised
@@ -526,7 +531,10 @@ __global__ void __launch_bounds__(kPoseThreads)
           if (o + 16 * q < h.z) cc[q] = __ldg(circ + o + 16 * q);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (o + 16 * q < h.z) ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot));
+          if (o + 16 * q < h.z) {
+            ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot));
+            ++n_circ;
+          }
       }
     }
 #pragma unroll
@@ -548,6 +556,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     bool proposed = false;
 #pragma unroll
     for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
+    ++n_bound;
     if (!proposed && aabb_d2(tile_aabb(tiles, t), px, py) <= Dc2) {
       if (ncand < kDefer) {
 #pragma unroll
@@ -568,11 +577,22 @@ __global__ void __launch_bounds__(kPoseThreads)
     atomicAdd(&s_fb, ncand);
     atomicAdd(&s_fbp, 1);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_bound += __shfl_xor_sync(0xffffffffu, n_bound, o);
+    n_circ += __shfl_xor_sync(0xffffffffu, n_circ, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&s_bound, n_bound);
+    atomicAdd(&s_circ, n_circ);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(&ctr->n_prop, s_prop);
     atomicAdd(&ctr->n_fb, s_fb);
     atomicAdd(&ctr->fallback_poses, s_fbp);
+    atomicAdd(&ctr->n_bound, (unsigned long long)s_bound);
+    atomicAdd(&ctr->n_circ, (unsigned long long)s_circ);
   }
   pdl_trigger();  // the evaluation kernel may launch; it waits for this grid
 }
@@ -1106,6 +1126,8 @@ extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cu
   stats->proposed_items = c.n_prop;
   stats->fallback_items = c.n_fb;
   stats->fallback_poses = c.fallback_poses;
+  stats->bound_evaluations = (int64_t)c.n_bound;
+  stats->circle_evaluations = (int64_t)c.n_circ;
   if (c.err) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out");
   return PSDF_OK;
 }

@@ -306,7 +306,8 @@ class CullOpts(ctypes.Structure):
 class CullStats(ctypes.Structure):
     _fields_ = [("evaluated_obstacles", ctypes.c_int64), ("evaluated_edges", ctypes.c_int64),
                 ("proposed_items", ctypes.c_int64), ("fallback_items", ctypes.c_int64),
-                ("fallback_poses", ctypes.c_int64)]
+                ("fallback_poses", ctypes.c_int64), ("bound_evaluations", ctypes.c_int64),
+                ("circle_evaluations", ctypes.c_int64)]
 
 
 class Mlp:

@@ -42,12 +42,13 @@ def flops_evaluated(m: int, n_edges: int, n_obstacles: int) -> float:
     return float(n_edges) * (14 + 30 * m) + float(n_obstacles) * 2 * m
 
 
-def flops_propose(P: int, T: int, circles_per_pose: float) -> float:
-    """FP32 flops of the cull's proposal kernel: two passes of the squared
-    distance to every tile's AABB (4 sub, mul, fma = 7 per pass) and one
-    circle upper bound (2 sub, mul, fma, sqrt, 3 add, fma = 10) per obstacle
-    of the proposed tiles.  The network's tensor-core flops are not FP32."""
-    return 14.0 * P * T + 10.0 * P * circles_per_pose
+def flops_propose(bound_evaluations: int, circle_evaluations: int) -> float:
+    """FP32 flops of the cull's proposal kernel: the squared distance to a
+    tile's AABB (4 sub, 2 max, mul, fma: 7 counted) per tile bound it
+    computed (both passes, as counted by the kernel) and one circle upper
+    bound (2 sub, mul, fma, sqrt, 3 add, fma = 10) per obstacle circle of
+    the proposed tiles.  The network's tensor-core flops are not FP32."""
+    return 7.0 * bound_evaluations + 10.0 * circle_evaluations
 
 
 def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:

@@ -54,6 +54,13 @@ def test_cull_equals_full_scan_dense_clutter(mode, k):
         # the bound-ordered cull skips almost all (pose, tile) pairs; an
         # untrained network may propose badly (more fallback) but stays exact
         assert st.proposed_items + st.fallback_items < 0.05 * w.P * T
+    # the proposals rank only the tiles of each pose's grid cell (and, for
+    # the bound order, test only them: an untrained network's far proposals
+    # leave upper bounds beyond the cell's reach, then every tile is tested)
+    assert 0 < st.bound_evaluations <= 2 * w.P * T
+    if mode == "bound":
+        assert st.bound_evaluations < 0.1 * 2 * w.P * T
+    assert st.circle_evaluations >= st.proposed_items
     # inside the listed tiles most obstacles are skipped by their circle bound
     obs_per_tile = w.M / T
     assert 0 < st.evaluated_obstacles < 0.5 * (st.proposed_items + st.fallback_items) * obs_per_tile
@@ -168,8 +175,13 @@ def test_cull_without_grid_long_segments():
     w = sg.Workload("long_segments", sg.footprint_rect(), edges, offs,
                     poses_np.astype(np.float32))
     poses = torch.as_tensor(w.poses, device="cuda")
-    _compare_cull(w, scene, poses, k=1)
-    _compare_cull(w, scene, poses, mlp=_random_mlp(9), k=2)
+    st = _compare_cull(w, scene, poses, k=1)
+    # both passes of every pose over all tiles; one circle per proposed tile
+    assert st.bound_evaluations == 2 * w.P * n
+    assert st.circle_evaluations == w.P
+    st = _compare_cull(w, scene, poses, mlp=_random_mlp(9), k=2)
+    assert st.bound_evaluations == 2 * w.P * n
+    assert st.circle_evaluations == 2 * w.P
 
 
 def test_lower_bound_is_below_every_tile_value():
