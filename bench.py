@@ -341,6 +341,56 @@ def _bench_batched(a, dev, flush, stream, peak):
     }
 
 
+def _bench_scan_configs(dev, flush, stream, peak, steps: int = 20):
+    """Full-scan throughput on the two other single-scene workloads: the
+    octagon footprint over rectangles and LiDAR segments (3,200 poses x
+    20,000 edges, value + gradient) and the backward workload (10,240 poses x
+    10,000 edges, value + gradient + backward).  One CUDA graph per step, L2
+    flushed before each; FP32 roofline of the step from the algorithmic flops
+    of every (pose, edge) pair."""
+    import torch
+    from paper_2607_04310_b300 import psdf, roofline
+    from paper_2607_04310_b300 import scenegen as sg
+    out = {}
+    for name, w, with_bwd in (("octagon_lidar", sg.octagon_lidar(1), False),
+                              ("backward_rects", sg.backward_rects(3), True)):
+        scene = psdf.Scene.from_csr(w.edges, w.offsets)
+        prm = scene.params
+        P = w.P
+        poses = torch.as_tensor(w.poses, device=dev).contiguous()
+        phi = torch.empty(P, device=dev)
+        dphi = torch.empty((P, 3), device=dev)
+        act = torch.empty(P, dtype=torch.int32, device=dev)
+        ws = psdf.workspace(P, dev)
+        gphi = torch.ones(P, device=dev)
+        gpose = torch.empty((P, 3), device=dev)
+        gedges = torch.zeros((w.E, 4), device=dev)
+
+        def step():
+            psdf.psdf_eval_grad(w.footprint, scene, poses, prm, phi, dphi, act, ws)
+            if with_bwd:
+                psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges)
+
+        replay, _g = _graph(step)
+        for _ in range(3):
+            replay()
+        ms = float(np.median(_time_steps(replay, steps, flush, stream)))
+        m = w.footprint.shape[0]
+        flops = roofline.flops_per_pose(m, w.offsets) * P
+        pairs = float(P) * w.E
+        out[name] = {"workload": w.name, "poses": P, "edges": w.E, "footprint_vertices": m,
+                     "path": "full scan + pose gradient" + (" + backward" if with_bwd else ""),
+                     "ms_per_step": ms, "value": pairs / (ms / 1000.0),
+                     "unit": "pair-evals/s",
+                     "roofline": {"bound": "alu", "achieved": flops / (ms / 1000.0) / 1e12,
+                                  "peak": peak, "unit": "TFLOP/s",
+                                  "frac": flops / (ms / 1000.0) / 1e12 / peak,
+                                  "flops_per_step": flops,
+                                  "note": "whole step (scan, epilogue%s)"
+                                          % (", backward" if with_bwd else "")}}
+    return out
+
+
 def _bench_table1(dev, reps: int = 200):
     """Latency grid of the paper's Table I: M in {1, 10, 100} random-yaw
     rectangles x B in {1, 10, 100} poses, rectangle footprint.  Three views:
@@ -616,7 +666,10 @@ def run_b300(a, rank, world, local):
         "speedup_vs_full_scan": full_ms / ms_step,
         "launch": "one CUDA graph per step (eager launches: %.4f ms/step)" % eager_ms,
         "exact_vs_full_scan": exact,
-        "full_scan": {"value": pairs / (full_ms / 1000.0), "ms_per_step": full_ms},
+        "full_scan": {"value": pairs / (full_ms / 1000.0), "ms_per_step": full_ms,
+                      "roofline_frac": roofline.flops_per_pose(m, w.offsets) * P
+                      / (full_ms / 1000.0) / 1e12 / peak,
+                      "note": "scan + epilogue + backward, FP32 flops of every pair"},
         "bound_cull": {"value": pairs / (bound_ms / 1000.0), "ms_per_step": bound_ms,
                        "evaluated_fraction": (st_bound.proposed_items + st_bound.fallback_items) / (P * T),
                        "fallback_rate": st_bound.fallback_poses / P},
@@ -652,6 +705,7 @@ def run_b300(a, rank, world, local):
     if not a.no_batched and world == 1:
         line["batched_uneven"] = _bench_batched(a, dev, flush, stream, peak)
         line["table1_latency"] = _bench_table1(dev)
+        line["full_scan_configs"] = _bench_scan_configs(dev, flush, stream, peak)
     if not a.no_cpu_baseline and world == 1:
         import oracle
         rate, n, dt = _oracle_rate(w, a.cpu_seconds)
