@@ -520,9 +520,12 @@ def run_b300(a, rank, world, local):
     prm = psdf.make_params()
     P = w.P
     poses = torch.as_tensor(w.poses, device=dev).contiguous()
-    phi = torch.empty(P, device=dev)
-    dphi = torch.empty((P, 3), device=dev)
-    act = torch.empty(P, dtype=torch.int32, device=dev)
+    # phi, dphi and the active pair as views of one buffer, so that the
+    # end-to-end leg reads the step's result back with one copy
+    out = torch.empty(5 * P, device=dev)
+    phi = out[:P]
+    dphi = out[P:4 * P].view(P, 3)
+    act = out[4 * P:].view(torch.int32)
     ws = psdf.workspace(P, dev)
     cws = torch.empty(psdf.psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8, device=dev)
     gphi = torch.ones(P, device=dev)
@@ -600,17 +603,13 @@ def run_b300(a, rank, world, local):
     e2e_step_ms = float("nan")
     if not a.no_e2e:
         h_poses = torch.as_tensor(w.poses).pin_memory()
-        h_phi = torch.empty(P).pin_memory()
-        h_dphi = torch.empty((P, 3)).pin_memory()
-        h_act = torch.empty(P, dtype=torch.int32).pin_memory()
+        h_out = torch.empty(5 * P).pin_memory()
         d_poses = torch.empty_like(poses)
 
         def e2e_step():
             d_poses.copy_(h_poses, non_blocking=True)
             step_learned(d_poses)
-            h_phi.copy_(phi, non_blocking=True)
-            h_dphi.copy_(dphi, non_blocking=True)
-            h_act.copy_(act, non_blocking=True)
+            h_out.copy_(out, non_blocking=True)  # phi, dphi, active
 
         replay_e2e, g_e2e = _graph(e2e_step)
         for _ in range(3):
