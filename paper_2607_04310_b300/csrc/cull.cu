@@ -288,8 +288,9 @@ __device__ __forceinline__ void mlp_rows(const MlpFrags &w, const float *ab, int
 // per-tile work units
 // ---------------------------------------------------------------------------
 // Lanes of a tile's work: its cnt poses are split over S obstacle ranges
-// each, so that cnt * S lanes fill about two 128-thread units when few poses
-// need the tile (short per-lane chains, many warps in flight).
+// each, so that cnt * S lanes fill about two 128-thread units (one per CTA of
+// the tile) when few poses need the tile (short per-lane chains, many warps
+// in flight).
 constexpr int kTargetLanes = 2 * kListThreads;
 __device__ __forceinline__ int tile_split(int cnt, int n_obs)
 {
@@ -369,8 +370,7 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
 // upper bound on phi from the circles of the proposed tiles' obstacles, and
 // append the pose to every other tile whose bound does not exceed it: from
 // the cell's list when the bound's reach is within the grid's, else from
-// all tiles.  The CTA that finishes last builds the work units of all listed
-// pairs.
+// all tiles.
 template <int K, bool NET>
 __global__ void __launch_bounds__(kPoseThreads)
     propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
