@@ -700,12 +700,12 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
   auto worldB = [&](int kk) {
     V2 r;
     if (seg) { const float4 b = vt[1]; r.x = b.z; r.y = b.w; }
-    else { const float4 a = vt[2 * ((kk + 1) % n)]; r.x = a.x; r.y = a.y; }
+    else { const float4 a = vt[2 * (kk + 1 < n ? kk + 1 : 0)]; r.x = a.x; r.y = a.y; }
     return r;
   };
   // gradient of edge k's B endpoint goes to the next vertex's A slot for a
   // closed polygon, to the B slot for a segment
-  auto rowB = [&](int kk) { return seg ? orig_first : orig_first + (kk + 1) % n; };
+  auto rowB = [&](int kk) { return seg ? orig_first : orig_first + (kk + 1 < n ? kk + 1 : 0); };
   const int colB = seg ? 2 : 0;
   float vx[M], vy[M];
 #pragma unroll
@@ -721,9 +721,12 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
   const auto add = [](float x, float y) { return __fadd_rn(x, y); };
   const auto sub = [](float x, float y) { return __fsub_rn(x, y); };
   const auto unit = [&](float rx, float ry, float &hx, float &hy) {
-    const float d = __fsqrt_rn(__fmaf_rn(rx, rx, mul(ry, ry)));
-    hx = d > 0.f ? __fdiv_rn(rx, d) : 0.f;
-    hy = d > 0.f ? __fdiv_rn(ry, d) : 0.f;
+    // 1/|r| from the hardware reciprocal square root (a few ulp, the same
+    // bits in every kernel)
+    const float d2 = __fmaf_rn(rx, rx, mul(ry, ry));
+    const float inv = d2 > 0.f ? rsqrtf(d2) : 0.f;
+    hx = mul(rx, inv);
+    hy = mul(ry, inv);
   };
   if (kind == kVertEdge) {
     const V2 Aw = worldA(k), Bw = worldB(k);
@@ -766,7 +769,9 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
     const bool sideA = (kind == kOAxisOMax);
     const V2 Aw = worldA(k), Bw = worldB(k);
     const float ux = sub(Bw.x, Aw.x), uy = sub(Bw.y, Aw.y);
-    const float len = __fsqrt_rn(__fmaf_rn(ux, ux, mul(uy, uy)));
+    const float len2 = __fmaf_rn(ux, ux, mul(uy, uy));
+    const float inv_len = rsqrtf(len2);  // edges are at least 1e-6 m long
+    const float len = mul(len2, inv_len);
     const float gd = __fdiv_rn(1.f, add(len, eps_axis));
     const float npx = mul(-uy, gd), npy = mul(ux, gd);                          // n' (world)
     const float ntx = add(mul(c, npx), mul(s, npy)), nty = sub(mul(c, npy), mul(s, npx));  // R^T n'
@@ -779,7 +784,7 @@ __device__ Grad active_grad(const FootprintK &F, float px, float py, float c, fl
     const float JvNt = sub(mul(lvx, nty), mul(lvy, ntx));  // (J v*) . R^T n'
     g.gp[0] = sideA ? npx : -npx; g.gp[1] = sideA ? npy : -npy; g.gp[2] = sideA ? JvNt : -JvNt;
     add_row(g, orig_first + xk, 0, -g.gp[0], -g.gp[1]);
-    const float uhx = __fdiv_rn(ux, len), uhy = __fdiv_rn(uy, len);
+    const float uhx = mul(ux, inv_len), uhy = mul(uy, inv_len);
     const float JuD = sub(mul(ux, Dy), mul(uy, Dx));
     const float gpr = -mul(gd, gd);
     // d delta / dA = -du, d delta / dB = du with du = gd J^T D + gpr u^ (J u . D)
@@ -813,7 +818,7 @@ __device__ __forceinline__ float active_overlap(const FootprintK &F, float px, f
   const V2 A = to_local(ak.x, ak.y, px, py, c, s);
   float bwx = bk.z, bwy = bk.w;
   if (!seg) {
-    const float4 an = vt[2 * ((k + 1) % n)];
+    const float4 an = vt[2 * (k + 1 < n ? k + 1 : 0)];
     bwx = an.x;
     bwy = an.y;
   }
@@ -845,7 +850,7 @@ __device__ __forceinline__ float active_t(const FootprintK &F, float px, float p
     const V2 A = to_local(ak.x, ak.y, px, py, c, s);
     float bwx = vt[1].z, bwy = vt[1].w;
     if (!seg) {
-      const float4 an = vt[2 * ((k + 1) % n)];
+      const float4 an = vt[2 * (k + 1 < n ? k + 1 : 0)];
       bwx = an.x;
       bwy = an.y;
     }
