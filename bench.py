@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -188,7 +188,7 @@ def run_reference(a, rank, world):
     import oracle
     w = _workload(0)
     cores = oracle.max_threads()
-    per_step = max(1.0, 60.0 / max(a.steps + a.warmup, 1))
+    per_step = max(0.3, 60.0 / max(a.steps + a.warmup, 1))
     rate, n, dt = _oracle_rate(w, min(per_step, 10.0))
     # each step: the oracle on a bounded sample of the same workload
     times = []
