@@ -148,7 +148,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
 }
 
 constexpr int kEpiLanes = 4;  // lanes sharing one pose's epilogue (hard minimum)
-constexpr int kBwdSpread = 4;  // lanes per pose in the backward (one of them works)
+// Lanes per pose in the backward (one of them works): a whole warp per pose
+// while the launch stays within about two waves of the GPU's threads (the
+// kernel is a chain of dependent loads and a per-kind branch, so fewer poses
+// per warp shorten it), fewer lanes for larger batches.
+inline int backward_spread_shift(long long P)
+{
+  const long long budget = 2LL * device_sms() * 2048;
+  int shift = 5;
+  while (shift > 0 && (P << shift) > budget) --shift;
+  return shift;
+}
 
 // Per-pose epilogue: value, active pair, optional pose gradient.
 template <int M, bool SOFT = false>
@@ -212,14 +222,14 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 long long rows_total,
                                 const unsigned *__restrict__ active,
                                 const float *__restrict__ grad_phi, float *__restrict__ grad_pose,
-                                float *__restrict__ grad_edges)
+                                float *__restrict__ grad_edges, int spread)
 {
   pdl_wait();
-  // one pose per kBwdSpread lanes: fewer poses (and active-pair kinds, whose
+  // one pose per 2^spread lanes: fewer poses (and active-pair kinds, whose
   // gradient branches a warp runs one after another) per warp
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid % kBwdSpread) return;
-  const long long p = gid / kBwdSpread;
+  if (gid & ((1LL << spread) - 1)) return;
+  const long long p = gid >> spread;
   if (p >= P) return;
   const float gphi = grad_phi[p];
   const float px = poses[3 * p], py = poses[3 * p + 1], th = poses[3 * p + 2];
@@ -448,7 +458,8 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
                            const float *grad_phi, float *grad_pose, float *grad_edges,
                            cudaStream_t st)
 {
-  const unsigned blocks = (unsigned)((P * kBwdSpread + 127) / 128);
+  const int spread = backward_spread_shift(P);
+  const unsigned blocks = (unsigned)(((P << spread) + 127) / 128);
   ProfileScope prof("backward", st);
   // usually follows an epilogue on the stream: may start while it finishes
   cudaError_t le;
@@ -456,12 +467,12 @@ static int launch_backward(const FootprintK &F, const psdf_scene *sc, const floa
     le = launch_pdl(backward_kernel<M, true>, dim3(blocks), dim3(128), 0, st, F, pk, sc->eps_axis,
                     poses, P, (const ObsRec *)sc->d_row_obs, (const float4 *)sc->d_vtx,
                     (const int *)sc->d_far, (long long)sc->rows_total, active, grad_phi,
-                    grad_pose, grad_edges);
+                    grad_pose, grad_edges, spread);
   else
     le = launch_pdl(backward_kernel<M, false>, dim3(blocks), dim3(128), 0, st, F, pk,
                     sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                     (const float4 *)sc->d_vtx, (const int *)sc->d_far,
-                    (long long)sc->rows_total, active, grad_phi, grad_pose, grad_edges);
+                    (long long)sc->rows_total, active, grad_phi, grad_pose, grad_edges, spread);
   if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
