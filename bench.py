@@ -650,8 +650,8 @@ def run_b300(a, rank, world, local):
     dom = max(kroof, key=lambda k: kroof[k]["avg_launch_ms"])
     kname = {"cull_eval": "eval_lists", "propose": "propose"}
     evaluated_pairs = float(st.evaluated_edges)  # pose x edge pairs evaluated exactly
-    # propose, eval_lists, epilogue, backward (plus one memset node)
-    launches_per_step = 4
+    # clear_words, propose, eval_lists, epilogue, backward
+    launches_per_step = 5
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -1,7 +1,7 @@
 // Exact tile cull with a proposal (psdf_eval_culled and its helpers).
 //
 // Work is organised as (pose, tile) pairs, bucketed by tile:
-//   0. memset          per-tile counters and the pipeline counters cleared
+//   0. clear_words     per-tile counters and the pipeline counters cleared
 //   1. propose         16 lanes per pose rank the tiles of the pose's cell in a
 //                      uniform grid (every tile within one cell size; all
 //                      tiles for a pose outside the grid) by the conservative
@@ -70,7 +70,7 @@ struct CullLayout {
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]).
-// The counters and the per-tile histogram are contiguous (one memset).
+// The counters and the per-tile histogram are contiguous (cleared by one kernel).
 static CullLayout cull_layout(long long P, int n_tiles)
 {
   CullLayout L;
@@ -320,6 +320,16 @@ __device__ __forceinline__ float cand_radius(float ub, float rfoot)
   return D * (1.f + 1e-5f) + 1e-6f;
 }
 
+// Zeroes the counters and per-tile counts of a cull workspace; the proposal
+// kernel, launched after it with programmatic stream serialization, ranks
+// its tiles meanwhile and waits for it before its first append.
+__global__ void clear_words(unsigned *__restrict__ w, int n)
+{
+  pdl_trigger();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    w[i] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // proposals
 // ---------------------------------------------------------------------------
@@ -424,7 +434,6 @@ __global__ void __launch_bounds__(kPoseThreads)
     topk_insert<RL>(sc, id, aabb_d2(tile_aabb(tiles, t), px, py), t);
     ++n_bound;
   }
-  pdl_wait();  // no-op: the proposal kernel follows a memset
   __syncthreads();  // s_prop, s_fb, s_fbp initialised
   int best[K];
 #pragma unroll
@@ -503,6 +512,9 @@ __global__ void __launch_bounds__(kPoseThreads)
 #pragma unroll
       for (int i = 0; i < K; ++i) best[i] = cand[i];
     }
+    // the per-tile counts and the counters are cleared by the kernel before
+    // this one: wait for it before the first append
+    pdl_wait();
     if (valid && hl == 0) {
       int n = 0;
 #pragma unroll
@@ -586,6 +598,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     atomicAdd(&s_bound, n_bound);
     atomicAdd(&s_circ, n_circ);
   }
+  pdl_wait();  // (warps of poses beyond P reach the counters without appending)
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(&ctr->n_prop, s_prop);
@@ -1069,8 +1082,14 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   int *hist = reinterpret_cast<int *>(ws + L.hist);
   int *list = reinterpret_cast<int *>(ws + L.list);
   ParamsK pk{params->eps_sat, params->eta};
-  cudaError_t e = cudaMemsetAsync(ws, 0, L.clear_bytes, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(cull counters)");
+  cudaError_t e;
+  {
+    const int words = (int)(L.clear_bytes / 4);
+    clear_words<<<std::min((words + 255) / 256, 64), 256, 0, st>>>(
+        reinterpret_cast<unsigned *>(ws), words);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch (clear)");
+  }
   if (T == 0) {
     e = cudaMemsetAsync(keys, 0xff, 8 * (size_t)P, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(keys)");
@@ -1082,15 +1101,11 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
     const float b2 = net ? mlp->b2 : 0.f;
     {
       ProfileScope prof("propose", st);
-#define PSDF_PROPOSE(KK)                                                                     \
-  if (net)                                                                                   \
-    propose<KK, true><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid, \
-                                                   F.radius, scene->d_blob, frag, b2, keys,     \
-                                                   pose4, ub, prop, hist, list, ctr);           \
-  else                                                                                          \
-    propose<KK, false><<<pb, kPoseThreads, 0, st>>>(poses, P, scene->d_tiles, T, scene->grid,   \
-                                                    F.radius, scene->d_blob, frag, b2, keys,    \
-                                                    pose4, ub, prop, hist, list, ctr);
+#define PSDF_PROPOSE(KK)                                                                      \
+  e = launch_pdl(net ? propose<KK, true> : propose<KK, false>, dim3(pb), dim3(kPoseThreads), 0, \
+                 st, poses, (long long)P, (const TileHdr *)scene->d_tiles, T, scene->grid,      \
+                 F.radius, (const unsigned char *)scene->d_blob, frag, b2, keys, pose4, ub,     \
+                 prop, hist, list, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;
         case 2: PSDF_PROPOSE(2) break;
@@ -1098,6 +1113,7 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
         default: PSDF_PROPOSE(4) break;
       }
 #undef PSDF_PROPOSE
+      if (e != cudaSuccess) return cuda_fail(e, "kernel launch (propose)");
     }
     {
       ProfileScope prof("cull_eval", st);
