@@ -171,6 +171,17 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 float *__restrict__ dphi, unsigned *__restrict__ active,
                                 float *__restrict__ stage, float d_min)
 {
+  // the pose (an input of the call, not an output of the kernel before) is
+  // read before the wait
+  float px = 0.f, py = 0.f, th = 0.f;
+  if (!SOFT) {
+    const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kEpiLanes;
+    if (p < P) {
+      px = poses[3 * p];
+      py = poses[3 * p + 1];
+      th = poses[3 * p + 2];
+    }
+  }
   pdl_wait();
   pdl_trigger();  // a following backward may launch now; it waits for this grid
   const bool want_grad = dphi != nullptr || stage != nullptr;
@@ -196,9 +207,7 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
     if (*err) {
       r = pose_out_failed();
     } else {
-      const long long q = valid ? p : 0;
-      r = epilogue_pose_coop<M, kEpiLanes>(F, prm.eps_sat, eps_axis, poses[3 * q],
-                                           poses[3 * q + 1], poses[3 * q + 2],
+      r = epilogue_pose_coop<M, kEpiLanes>(F, prm.eps_sat, eps_axis, px, py, th,
                                            valid ? keys[p] : ~0ull, row_obs, vtx, far,
                                            want_grad, g);
     }
@@ -224,15 +233,18 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float *__restrict__ grad_phi, float *__restrict__ grad_pose,
                                 float *__restrict__ grad_edges, int spread)
 {
-  pdl_wait();
   // one pose per 2^spread lanes: fewer poses (and active-pair kinds, whose
   // gradient branches a warp runs one after another) per warp
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid & ((1LL << spread) - 1)) return;
   const long long p = gid >> spread;
   if (p >= P) return;
-  const float gphi = grad_phi[p];
+  // the pose is read before the wait: it is an input of the call, never an
+  // output of the epilogue that usually precedes this kernel (the active
+  // pair and the incoming gradient may be, so they are read after it)
   const float px = poses[3 * p], py = poses[3 * p + 1], th = poses[3 * p + 2];
+  pdl_wait();
+  const float gphi = grad_phi[p];
   const unsigned pid = active[p];
   if (SOFT) {
     // a penetration pair names a non-separated obstacle: its gradient is the
