@@ -167,14 +167,14 @@ def _measured_peaks():
 # --------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # --------------------------------------------------------------------------
-def _oracle_rate(w, seconds: float, seed: int = 0):
+def _oracle_rate(w, seconds: float, seed: int = 0, nthreads: int = 0):
     import oracle
     g = np.random.default_rng(seed)
     n = 4
     while True:
         idx = g.choice(w.P, size=min(n, w.P), replace=False)
         t0 = time.perf_counter()
-        oracle.psdf_eval(w.footprint, w.edges, w.offsets, w.poses[idx])
+        oracle.psdf_eval(w.footprint, w.edges, w.offsets, w.poses[idx], nthreads=nthreads)
         dt = time.perf_counter() - t0
         if dt >= seconds or n >= w.P:
             break
@@ -708,9 +708,12 @@ def run_b300(a, rank, world, local):
     if not a.no_cpu_baseline and world == 1:
         import oracle
         rate, n, dt = _oracle_rate(w, a.cpu_seconds)
+        rate1, n1, dt1 = _oracle_rate(w, min(4.0, a.cpu_seconds / 3), seed=1, nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(),
                                 "kind": "oracle",
-                                "sample": "%d of 4096 poses x 100000 edges, %.1f s" % (n, dt)}
+                                "sample": "%d of 4096 poses x 100000 edges, %.1f s" % (n, dt),
+                                "one_core": {"value": rate1, "cores": 1,
+                                             "sample": "%d poses, %.1f s" % (n1, dt1)}}
     print(json.dumps(line))
     if pg:
         pg.destroy_process_group()
