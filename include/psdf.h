@@ -77,9 +77,9 @@ typedef struct psdf_scene psdf_scene; /* opaque: owns the device copy of E  */
  * normal; eps_sat: the separating-axis tolerance.  eta = 0 selects the hard
  * minimum of the overlaps (the exact penetration depth, Sec. IV-C); eta > 0
  * the log-sum-exp soft minimum of Eq. penetration_depth over all of an
- * obstacle's axes (psdf_eval, psdf_eval_grad, psdf_backward and the
- * no-allocation call; the cull, the tile helpers and batched plans take the
- * hard minimum only and reject eta > 0).  With eta > 0 a non-separated
+ * obstacle's axes (psdf_eval, psdf_eval_grad, psdf_backward, the
+ * no-allocation call and psdf_eval_culled; the tile helpers and batched plans
+ * take the hard minimum only and reject eta > 0).  With eta > 0 a non-separated
  * obstacle's sd = -pen_soft (which is positive for shallow overlaps), its
  * gradient is the softmax-weighted sum over its axes with delta > 0, and the
  * active pair id still names the hard minimum's pair.  eta must be finite

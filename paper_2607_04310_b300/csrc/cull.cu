@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -384,7 +385,8 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
 template <int K, bool NET>
 __global__ void __launch_bounds__(kPoseThreads)
     propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
-            int T, const CullGrid grid, float rfoot, const unsigned char *__restrict__ blob,
+            int T, const CullGrid grid, float rfoot, float ub_pad,
+            const unsigned char *__restrict__ blob,
             const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
             float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
             int *hist, int *__restrict__ list,
@@ -551,6 +553,7 @@ __global__ void __launch_bounds__(kPoseThreads)
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) ubp = fminf(ubp, __shfl_xor_sync(0xffffffffu, ubp, o));
+    ubp += ub_pad;  // soft minimum: a penetrating obstacle's value reaches up to log(K) / eta
     if (valid && hl == 0) ub_out[p] = ubp;
   }
   // every unproposed tile whose bound does not exceed the upper bound is
@@ -640,7 +643,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 constexpr int kTileCTAs = 2;
 constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
 
-template <int M>
+template <int M, bool SOFT>
 __device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
                                            const int *qw, int n_items, int lane, float px,
                                            float py, float c, float s, long long p,
@@ -657,14 +660,15 @@ __device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &p
   const long long ip = __shfl_sync(0xffffffffu, p, src);
   if (lane < n_items) {
     const int4 rec = ob[o];
-    const float v = obstacle_value<M>(F, ipx, ipy, ic, is, vt + 2 * rec.x, rec.y, prm.eps_sat);
+    const float v = obstacle_value<M, FootprintK, SOFT>(F, ipx, ipy, ic, is, vt + 2 * rec.x,
+                                                        rec.y, prm.eps_sat, prm.eta);
     atomicMin(&keys[ip], pack_key(v, rec.z));
     ++n_obs;
     n_edge += rec.y;
   }
 }
 
-template <int M>
+template <int M, bool SOFT>
 __global__ void __launch_bounds__(kListThreads)
     eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
                const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(kListThreads)
       nq += __popc(mask);
       if (nq >= 32) {  // uniform: a full batch
         __syncwarp();
-        eval_items<M>(F, prm, qw, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
+        eval_items<M, SOFT>(F, prm, qw, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
         __syncwarp();
         if (lane < nq - 32) qw[lane] = qw[32 + lane];
         __syncwarp();
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(kListThreads)
     }
     if (nq > 0) {
       __syncwarp();
-      eval_items<M>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
+      eval_items<M, SOFT>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
     }
     __syncwarp();  // the queue is refilled by the next unit
   }
@@ -854,15 +858,17 @@ struct ListEvalCall {
                  CullCounters *ctr, cudaStream_t st)
   {
     const size_t smem = (size_t)(sc->max_blob_ext_bytes + 15) / 16 * 16;
+    const bool soft = pk.eta > 0.f;
+    auto kern = soft ? eval_lists<M, true> : eval_lists<M, false>;
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(eval_lists<M>,
+      cudaError_t e = cudaFuncSetAttribute(kern,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
     }
     const unsigned grid = (unsigned)sc->n_tiles * kTileCTAs;
     // follows the proposal kernel: may start while it finishes
-    cudaError_t e = launch_pdl(eval_lists<M>, dim3(grid), dim3(kListThreads), smem, st, F, pk,
+    cudaError_t e = launch_pdl(kern, dim3(grid), dim3(kListThreads), smem, st, F, pk,
                                pose4, P, (const TileHdr *)sc->d_tiles, sc->n_tiles,
                                (const unsigned char *)sc->d_blob, hist, list, ub, keys, ctr);
     return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (eval_lists)");
@@ -1051,8 +1057,6 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
                            (size_t)-1);
   if (rc) return rc;
   if (!opts) return fail(PSDF_ERR_ARG, "opts is NULL");
-  if (params->eta > 0.f)
-    return fail(PSDF_ERR_ARG, "the cull evaluates the hard minimum only (eta must be 0)");
   if (opts->k < 1 || opts->k > kMaxK) return fail(PSDF_ERR_ARG, "k must be in [1, 4]");
   if (opts->mode != PSDF_PROPOSE_BOUND && opts->mode != PSDF_PROPOSE_MLP)
     return fail(PSDF_ERR_ARG, "unknown proposal mode");
@@ -1096,6 +1100,13 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
   } else {
     const int K = opts->k;
     const bool net = opts->mode == PSDF_PROPOSE_MLP;
+    // soft minimum: an obstacle's value lies below its hard distance when it
+    // is separated and at most log(K) / eta (K axes) when it penetrates, so
+    // the upper bound taken from distances is raised by that much
+    float ub_pad = 0.f;
+    if (params->eta > 0.f)
+      ub_pad = (float)(std::log((double)(m + scene->max_obs_edges)) / params->eta * (1.0 + 1e-5) +
+                       1e-6);
     const unsigned pb = (unsigned)((P + 7) / 8);  // 4 warps x 2 poses per CTA
     const uint32_t *frag = net ? mlp->d_frag : nullptr;
     const float b2 = net ? mlp->b2 : 0.f;
@@ -1104,7 +1115,8 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
 #define PSDF_PROPOSE(KK)                                                                      \
   e = launch_pdl(net ? propose<KK, true> : propose<KK, false>, dim3(pb), dim3(kPoseThreads), 0, \
                  st, poses, (long long)P, (const TileHdr *)scene->d_tiles, T, scene->grid,      \
-                 F.radius, (const unsigned char *)scene->d_blob, frag, b2, keys, pose4, ub,     \
+                 F.radius, ub_pad, (const unsigned char *)scene->d_blob, frag, b2, keys, pose4, \
+                 ub,                                                                            \
                  prop, hist, list, ctr);
       switch (K) {
         case 1: PSDF_PROPOSE(1) break;

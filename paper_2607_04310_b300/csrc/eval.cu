@@ -532,8 +532,9 @@ struct EpilogueCall {
   {
     ProfileScope prof("epilogue", st);
     // after the cull's evaluation kernel: may start while it finishes
-    cudaError_t e = launch_pdl(epilogue_kernel<M, false>, epilogue_blocks(P, false),
-                               epilogue_threads(false), 0, st, F, pk,
+    const bool soft = pk.eta > 0.f;
+    cudaError_t e = launch_pdl(soft ? epilogue_kernel<M, true> : epilogue_kernel<M, false>,
+                               epilogue_blocks(P, soft), epilogue_threads(soft), 0, st, F, pk,
                                sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                                (const float4 *)sc->d_vtx, (const int *)sc->d_far, keys, err,
                                phi, dphi, active, (float *)nullptr, 0.f);

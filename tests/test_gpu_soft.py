@@ -110,8 +110,10 @@ def test_soft_rejected_where_unsupported():
     prm = psdf.make_params(eta=100.0)
     sc = psdf.Scene.from_csr(w.edges, w.offsets, params=prm)
     ps = torch.as_tensor(w.poses, device="cuda")
+    n_tiles = sc.info().n_tiles
     with pytest.raises(psdf.PsdfError) as ei:
-        psdf.eval_culled(sc, w.footprint, ps, k=1, params=prm)
+        psdf.psdf_tile_values(w.footprint, sc, ps, prm,
+                              torch.empty((w.P, n_tiles), device="cuda"))
     assert ei.value.code == psdf.PSDF_ERR_ARG
     with pytest.raises(psdf.PsdfError) as ei:
         psdf.Plan([(w.footprint, w.edges, w.offsets, w.P)], params=prm)
@@ -119,3 +121,34 @@ def test_soft_rejected_where_unsupported():
     with pytest.raises(psdf.PsdfError) as ei:
         psdf.eval_grad(sc, w.footprint, ps, params=psdf.make_params(eta=float("nan")))
     assert ei.value.code == psdf.PSDF_ERR_ARG
+
+
+def _bits(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("eta", [1.0, 50.0, 1000.0])
+def test_soft_cull_equals_full_scan(eta):
+    """The exact tile cull with the soft minimum (its upper bound raised by
+    log(K) / eta, the most a penetrating obstacle's soft value can exceed
+    zero): every output bit equal to the full scan's soft evaluation, with
+    half of the poses penetrating, for two tilings and two proposal sizes."""
+    w = sg.dense_clutter(4, n_rects=4000, n_poses=1024, field_side=80.0)
+    poses = torch.as_tensor(_penetrating(w, 7, frac=0.5, spread=0.2), device="cuda")
+    prm = psdf.make_params(eta=eta)
+    hard_phi = None
+    for te in (0, 32):
+        scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=te)
+        phi0, dphi0, act0 = psdf.eval_grad(scene, w.footprint, poses, params=prm)
+        if hard_phi is None:
+            hard_phi = psdf.eval_grad(scene, w.footprint, poses)[0]
+        for k in (1, 3):
+            phi1, dphi1, act1, _ws = psdf.eval_culled(scene, w.footprint, poses, k=k, params=prm)
+            torch.cuda.synchronize()
+            assert np.array_equal(_bits(phi0), _bits(phi1)), (te, k)
+            assert np.array_equal(_bits(act0), _bits(act1)), (te, k)
+            assert np.array_equal(_bits(dphi0), _bits(dphi1)), (te, k)
+    # the soft minimum changes the penetrating poses' values
+    pen = (hard_phi < 0).cpu().numpy()
+    assert pen.sum() >= 100
+    assert np.any(_bits(phi0)[pen] != _bits(hard_phi)[pen])
