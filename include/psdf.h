@@ -236,8 +236,16 @@ typedef struct {
   int32_t nx, ny;
   int64_t entries;
   float x0, y0, cell, reach;
+  float inv_cell; /* the FP32 1 / cell the kernels scale coordinates by */
 } psdf_cull_grid_info;
 int psdf_scene_cull_grid(const psdf_scene *scene, psdf_cull_grid_info *info);
+
+/* Copies the cull grid's lists to the host (synchronous): offsets HOST
+ * int32[nx * ny + 1] (cell c lists tiles[offsets[c] .. offsets[c + 1])),
+ * tiles HOST int32[entries]; and every tile's AABB, aabbs HOST
+ * float[n_tiles][4] (xmin, ymin, xmax, ymax), nullable.  Diagnostic only. */
+int psdf_scene_cull_grid_copy(const psdf_scene *scene, int32_t *offsets, int32_t *tiles,
+                              float *aabbs);
 
 #define PSDF_MLP_IN 16
 #define PSDF_MLP_HIDDEN 64

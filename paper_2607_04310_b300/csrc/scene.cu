@@ -477,7 +477,29 @@ extern "C" int psdf_scene_cull_grid(const psdf_scene *s, psdf_cull_grid_info *in
   info->y0 = s->grid.y0;
   info->cell = s->grid.nx > 0 ? s->grid_cell : 0.f;
   info->reach = s->grid.nx > 0 ? s->grid.reach_q : 0.f;
+  info->inv_cell = s->grid.inv_cs;
   return PSDF_OK;
+}
+
+extern "C" int psdf_scene_cull_grid_copy(const psdf_scene *s, int32_t *offsets, int32_t *tiles,
+                                         float *aabbs)
+{
+  if (!s) return fail(PSDF_ERR_ARG, "scene is NULL");
+  cudaError_t e = cudaSuccess;
+  if (s->grid.nx > 0) {
+    if (!offsets || !tiles) return fail(PSDF_ERR_ARG, "offsets or tiles is NULL");
+    const size_t cells = (size_t)s->grid.nx * s->grid.ny + 1;
+    e = cudaMemcpy(offsets, s->d_cell_off, 4 * cells, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && s->grid_entries > 0)
+      e = cudaMemcpy(tiles, s->d_cell_tiles, 4 * (size_t)s->grid_entries, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess && aabbs && s->n_tiles > 0) {
+    std::vector<TileHdr> h(s->n_tiles);
+    e = cudaMemcpy(h.data(), s->d_tiles, sizeof(TileHdr) * h.size(), cudaMemcpyDeviceToHost);
+    for (size_t t = 0; e == cudaSuccess && t < h.size(); ++t)
+      std::memcpy(aabbs + 4 * t, h[t].aabb, sizeof(h[t].aabb));
+  }
+  return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "cudaMemcpy(cull grid)");
 }
 
 extern "C" int psdf_scene_get_info(const psdf_scene *s, psdf_scene_info *info)

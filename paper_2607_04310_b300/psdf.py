@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
 class CullGridInfo(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("entries", ctypes.c_int64),
                 ("x0", ctypes.c_float), ("y0", ctypes.c_float), ("cell", ctypes.c_float),
-                ("reach", ctypes.c_float)]
+                ("reach", ctypes.c_float), ("inv_cell", ctypes.c_float)]
 
 
 class SceneInfo(ctypes.Structure):
@@ -82,6 +82,7 @@ _SIGS = {
     "psdf_scene_destroy": (ctypes.c_int, [_vp]),
     "psdf_scene_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(SceneInfo)]),
     "psdf_scene_cull_grid": (ctypes.c_int, [_vp, ctypes.POINTER(CullGridInfo)]),
+    "psdf_scene_cull_grid_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "psdf_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "psdf_workspace_status": (ctypes.c_int, [_vp, _vp]),
     "psdf_eval": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp,
@@ -235,6 +236,17 @@ class Scene:
         inf = CullGridInfo()
         _check(load().psdf_scene_cull_grid(self.handle, ctypes.byref(inf)))
         return inf
+
+    def cull_grid_lists(self):
+        """(offsets [nx*ny+1], tiles [entries], tile AABBs [T,4]) on the host."""
+        g = self.cull_grid()
+        T = self.info().n_tiles
+        off = np.zeros(max(g.nx * g.ny + 1, 1), dtype=np.int32)
+        tl = np.zeros(max(int(g.entries), 1), dtype=np.int32)
+        ab = np.zeros((max(T, 1), 4), dtype=np.float32)
+        _check(load().psdf_scene_cull_grid_copy(self.handle, off.ctypes.data, tl.ctypes.data,
+                                                ab.ctypes.data))
+        return off[:g.nx * g.ny + 1], tl[:int(g.entries)], ab[:T]
 
     def close(self) -> None:
         if self.handle and self.handle.value:

@@ -280,3 +280,56 @@ def test_features_match_numpy_definition():
     rf = float(np.max(np.hypot(w.footprint[:, 0], w.footprint[:, 1])))
     ref = omlp.tile_features(aabb, counts, w.poses, rf)
     assert np.max(np.abs(feats.cpu().numpy() - ref)) <= 2e-5
+
+
+def test_cull_grid_lists_cover_the_reach():
+    """Direct check of the grid invariant: a point whose cell, computed in
+    FP32 as the proposal kernel does, is c finds in c's list every tile whose
+    AABB lies within the grid's reach (FP64 distance), on uniform clutter
+    (sort-tile-recursive and Morton tiles) and on two uneven clusters of
+    polygons; random points and points on and next to every cell border."""
+    g0 = np.random.default_rng(21)
+    e1, o1 = sg.rects(g0, 3000, 0.2, 1.0, 0.0, 80.0)
+    e2, o2 = sg.convex_polygons(g0, 600, 3, 9, 0.3, 1.5, 0.0, 20.0)
+    e3, o3 = sg.convex_polygons(g0, 300, 3, 9, 0.3, 3.0, 60.0, 120.0)
+    scenes = [psdf.Scene.from_csr(e1, o1), psdf.Scene.from_csr(*sg.concat((e2, o2), (e3, o3))),
+              psdf.Scene.from_csr(e1, o1, tile_edges=0x10000)]  # Morton tiles
+    checked = 0
+    for scene in scenes:
+        g = scene.cull_grid()
+        assert g.nx > 0
+        off, tl, ab = scene.cull_grid_lists()
+        assert off[0] == 0 and off[-1] == len(tl) == g.entries
+        assert np.all(np.diff(off) >= 0)
+        cs = float(g.cell)
+        W, H = g.nx * cs, g.ny * cs
+        # random points, points on every cell border, and points a hair inside
+        # and outside of the borders (the FP32 cell index may round either way)
+        pts = [g0.uniform([g.x0, g.y0], [g.x0 + W, g.y0 + H], size=(20000, 2))]
+        for i in range(g.nx + 1):
+            x = g.x0 + i * cs
+            ys = g0.uniform(g.y0, g.y0 + H, size=20)
+            for dx in (-1e-4, 0.0, 1e-4):
+                pts.append(np.stack([np.full(20, x + dx), ys], axis=1))
+        pts = np.concatenate(pts)
+        f32 = np.float32
+        # the kernel's cell index: (p - x0) * (1 / cell) in FP32
+        inv = f32(g.inv_cell)
+        fx = (pts[:, 0].astype(f32) - f32(g.x0)) * inv
+        fy = (pts[:, 1].astype(f32) - f32(g.y0)) * inv
+        inside = (fx >= 0) & (fx < g.nx) & (fy >= 0) & (fy < g.ny)
+        cell = fy[inside].astype(np.int64) * g.nx + fx[inside].astype(np.int64)
+        p = pts[inside].astype(np.float32).astype(np.float64)
+        a = ab.astype(np.float64)
+        for k in range(0, len(p), 2000):
+            q = p[k:k + 2000]
+            dx = np.maximum(np.maximum(a[None, :, 0] - q[:, None, 0], q[:, None, 0] - a[None, :, 2]), 0)
+            dy = np.maximum(np.maximum(a[None, :, 1] - q[:, None, 1], q[:, None, 1] - a[None, :, 3]), 0)
+            need = np.hypot(dx, dy) <= float(g.reach)
+            for r in range(len(q)):
+                c = cell[k + r]
+                lst = set(tl[off[c]:off[c + 1]].tolist())
+                miss = set(np.flatnonzero(need[r]).tolist()) - lst
+                assert not miss, (c, sorted(miss)[:5])
+        checked += int(inside.sum())
+    assert checked > 50000
