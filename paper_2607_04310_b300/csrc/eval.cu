@@ -50,6 +50,7 @@ constexpr int kScanThreads = 128;
 // ---------------------------------------------------------------------------
 __global__ void init_keys_kernel(unsigned long long *keys, long long P, int *err)
 {
+  pdl_trigger();  // the scan may launch now; it waits for this grid before its atomics
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P) keys[i] = ~0ull;
   if (i == 0) *err = 0;
@@ -136,6 +137,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     }
     __syncthreads();
   }
+  // the keys and the error word are initialised by the kernel before this
+  // one (launched programmatically behind it): wait for it before merging
+  pdl_wait();
+  pdl_trigger();  // the epilogue may launch; it waits for this grid
   if (!ok) {
     // record the failure, then give copies still in flight a bounded chance
     // to land before the CTA's shared memory is released
@@ -437,27 +442,24 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     const size_t smem = 128 + 2 * (size_t)blob_cap;
     dim3 grid((unsigned)pose_blocks, (unsigned)chunks);
     ProfileScope prof("scan", st);
-    if (pk.eta > 0.f)
-      scan_kernel<M, true><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, npb, sc->d_tiles,
-                                                             sc->d_blob, sc->n_tiles, (int)tpc,
-                                                             blob_cap, keys, err);
-    else
-      scan_kernel<M><<<grid, kScanThreads, smem, st>>>(F, pk, poses, P, npb, sc->d_tiles,
-                                                       sc->d_blob, sc->n_tiles, (int)tpc,
-                                                       blob_cap, keys, err);
+    // behind the key initialisation: the scan runs while it finishes
+    cudaError_t le = launch_pdl(pk.eta > 0.f ? scan_kernel<M, true> : scan_kernel<M, false>,
+                                grid, dim3(kScanThreads), smem, st, F, pk, poses, P, npb,
+                                (const TileHdr *)sc->d_tiles, (const unsigned char *)sc->d_blob,
+                                sc->n_tiles, (int)tpc, blob_cap, keys, err);
+    if (le != cudaSuccess) return cuda_fail(le, "kernel launch (scan)");
   }
   {
     ProfileScope prof("epilogue", st);
     const bool soft = pk.eta > 0.f;
-    const dim3 eb = epilogue_blocks(P, soft), et = epilogue_threads(soft);
-    if (soft)
-      epilogue_kernel<M, true><<<eb, et, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
-                                                   sc->d_vtx, sc->d_far, keys, err, phi, dphi,
-                                                   active, so.stage, so.d_min);
-    else
-      epilogue_kernel<M><<<eb, et, 0, st>>>(F, pk, sc->eps_axis, poses, P, sc->d_row_obs,
-                                             sc->d_vtx, sc->d_far, keys, err, phi, dphi, active,
-                                             so.stage, so.d_min);
+    // behind the scan: its CTAs are resident when the scan completes
+    cudaError_t le = launch_pdl(soft ? epilogue_kernel<M, true> : epilogue_kernel<M, false>,
+                                epilogue_blocks(P, soft), epilogue_threads(soft), 0, st, F, pk,
+                                sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
+                                (const float4 *)sc->d_vtx, (const int *)sc->d_far,
+                                (const unsigned long long *)keys, (const int *)err, phi, dphi,
+                                active, so.stage, so.d_min);
+    if (le != cudaSuccess) return cuda_fail(le, "kernel launch (epilogue)");
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
