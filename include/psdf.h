@@ -78,8 +78,8 @@ typedef struct psdf_scene psdf_scene; /* opaque: owns the device copy of E  */
  * minimum of the overlaps (the exact penetration depth, Sec. IV-C); eta > 0
  * the log-sum-exp soft minimum of Eq. penetration_depth over all of an
  * obstacle's axes (psdf_eval, psdf_eval_grad, psdf_backward, the
- * no-allocation call and psdf_eval_culled; the tile helpers and batched plans
- * take the hard minimum only and reject eta > 0).  With eta > 0 a non-separated
+ * no-allocation call, psdf_eval_culled and the batched plans; the tile
+ * helpers take the hard minimum only and reject eta > 0).  With eta > 0 a non-separated
  * obstacle's sd = -pen_soft (which is positive for shallow overlaps), its
  * gradient is the softmax-weighted sum over its axes with delta > 0, and the
  * active pair id still names the hard minimum's pair.  eta must be finite
@@ -374,7 +374,8 @@ int psdf_trainer_set(psdf_trainer *trainer, const float *params, const float *m,
  *   tile_edges  edges per tile (0 = 256; PSDF_TILE_MORTON selects Morton
  *               packing), as for scenes.
  * Active pair ids use the row index WITHIN the instance (row minus the
- * instance's first row).  eta must be 0 (hard minimum).
+ * instance's first row).  params->eta > 0 selects the soft minimum for the
+ * whole plan (evaluation, stage parameters and backward).
  *
  * The plan owns its device memory (scene image, work queue, per-pose keys).
  * psdf_eval_batched allocates nothing and never synchronizes: it issues two

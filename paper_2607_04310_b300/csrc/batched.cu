@@ -101,8 +101,8 @@ __device__ __forceinline__ bool dbg_ok(bool cond, int site, long long idx)
 // same share whatever the horizon; a pair's key goes into the pose's key in
 // shared memory, and the block's keys into global memory once per item.
 // False when a bounded wait ran out (uniform over the CTA).
-template <int M>
-__device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__restrict__ poses,
+template <int M, bool SOFT>
+__device__ bool scan_item(const FootprintS &F, ParamsK prm, const float *__restrict__ poses,
                           long long pose0, int npose, const TileHdr *__restrict__ tiles,
                           const unsigned char *__restrict__ blob, int tile0, int ntile,
                           unsigned char *buf0, int blob_cap, uint64_t *bars, unsigned &phase,
@@ -177,7 +177,8 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
                        rec.x + (rec.y == 1 ? 1 : rec.y) <= h.n_vtx,
                    7, tile0 + k)) {
         const float4 q = spose[j];
-        const float v = obstacle_value<M>(F, q.x, q.y, q.z, q.w, vt + 2 * rec.x, rec.y, eps_sat);
+        const float v = obstacle_value<M, FootprintS, SOFT>(F, q.x, q.y, q.z, q.w, vt + 2 * rec.x,
+                                                            rec.y, prm.eps_sat, prm.eta);
         const unsigned long long key = pack_key(v, rec.z);
         if (j != cur) {
           if (cur >= 0) atomicMin(&skey[cur], best);
@@ -211,10 +212,11 @@ __device__ bool scan_item(const FootprintS &F, float eps_sat, const float *__res
 #define PSDF_FOR_EACH_M(X) \
   X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
+template <bool SOFT>
 __global__ void __launch_bounds__(kPlanMaxThreads, 2)
     batched_kernel(const PlanItem *__restrict__ items, int n_items,
                    const PlanBlock *__restrict__ blocks, const FootprintRec *__restrict__ fps,
-                   float eps_sat, const float *__restrict__ poses,
+                   ParamsK prm, const float *__restrict__ poses,
                    const TileHdr *__restrict__ tiles,
                    const unsigned char *__restrict__ blob, int blob_cap,
                    unsigned long long *keys, unsigned *ctr, PlanBounds bnd)
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
     switch (Fs->m) {
 #define PSDF_SCAN_CASE(MM)                                                                    \
   case MM:                                                                                    \
-    ok = scan_item<MM>(Fv, eps_sat, poses, B.pose0, B.npose, tiles, blob, I.tile0, I.ntile, \
+    ok = scan_item<MM, SOFT>(Fv, prm, poses, B.pose0, B.npose, tiles, blob, I.tile0, I.ntile, \
                        buf0, blob_cap, bars, phase, spose, skey, keys, bnd);                  \
     break;
       PSDF_FOR_EACH_M(PSDF_SCAN_CASE)
@@ -281,9 +283,10 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
 // Per-pose epilogue of the plan: one thread per pose, its instance's
 // footprint read from global memory (an instance's poses are contiguous, so a
 // warp rarely mixes footprint sizes).
+template <bool SOFT>
 __global__ void batched_epilogue_kernel(const int *__restrict__ pose_inst, long long P,
                                         const FootprintK *__restrict__ fps,
-                                        const PlanInst *__restrict__ inst, float eps_sat,
+                                        const PlanInst *__restrict__ inst, ParamsK prm,
                                         float eps_axis, const float *__restrict__ poses,
                                         const ObsRec *__restrict__ row_obs,
                                         const float4 *__restrict__ vtx,
@@ -326,9 +329,9 @@ __global__ void batched_epilogue_kernel(const int *__restrict__ pose_inst, long 
     switch (F.m) {
 #define PSDF_EPI_CASE(MM)                                                                  \
   case MM:                                                                                 \
-    r = epilogue_pose<MM>(F, eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],            \
-                          poses[3 * p + 2], keys[p], ro, vtx, far,                         \
-                          dphi != nullptr || stage != nullptr);                            \
+    r = epilogue_pose<MM, SOFT>(F, prm.eps_sat, eps_axis, poses[3 * p], poses[3 * p + 1],  \
+                                poses[3 * p + 2], keys[p], ro, vtx, far,                   \
+                                dphi != nullptr || stage != nullptr, prm.eta);             \
     break;
       PSDF_FOR_EACH_M(PSDF_EPI_CASE)
 #undef PSDF_EPI_CASE
@@ -340,9 +343,11 @@ __global__ void batched_epilogue_kernel(const int *__restrict__ pose_inst, long 
 
 // Backward: one thread per pose, the instance's footprint read from global
 // memory (poses of one instance are contiguous, so warps rarely mix sizes).
+template <bool SOFT>
 __global__ void batched_backward_kernel(const int *__restrict__ pose_inst, long long P,
                                         const FootprintK *__restrict__ fps,
-                                        const PlanInst *__restrict__ inst, float eps_axis,
+                                        const PlanInst *__restrict__ inst, ParamsK prm,
+                                        float eps_axis,
                                         const float *__restrict__ poses,
                                         const ObsRec *__restrict__ row_obs,
                                         const float4 *__restrict__ vtx,
@@ -358,6 +363,41 @@ __global__ void batched_backward_kernel(const int *__restrict__ pose_inst, long 
   const FootprintK &F = fps[i];
   const PlanInst in = inst[i];
   const float gphi = grad_phi[p];
+  if (SOFT) {
+    // a penetration pair names a non-separated obstacle: the softmax-weighted
+    // sum over the obstacle's axes
+    float gp[3];
+    bool soft = false;
+    const auto edge = [&](float w, const Grad &g) {
+      if (!grad_edges) return;
+      const float sc = gphi * w;
+      for (int r = 0; r < kGradRows; ++r) {
+        if (r >= g.nrow) break;
+        const long long row = in.row0 + g.row[r];
+        atomicAdd(&grad_edges[4 * row + g.col[r]], sc * g.gx[r]);
+        atomicAdd(&grad_edges[4 * row + g.col[r] + 1], sc * g.gy[r]);
+      }
+    };
+    switch (F.m) {
+#define PSDF_SOFT_BWD_CASE(MM)                                                                \
+  case MM:                                                                                    \
+    soft = soft_backward_pose<MM>(F, prm.eps_sat, prm.eta, eps_axis, poses[3 * p],            \
+                                  poses[3 * p + 1], poses[3 * p + 2], active[p],              \
+                                  row_obs + in.row0, in.rows, vtx, far, gp, edge);            \
+    break;
+      PSDF_FOR_EACH_M(PSDF_SOFT_BWD_CASE)
+#undef PSDF_SOFT_BWD_CASE
+      default: break;
+    }
+    if (soft) {
+      if (grad_pose) {
+        grad_pose[3 * p] = gphi * gp[0];
+        grad_pose[3 * p + 1] = gphi * gp[1];
+        grad_pose[3 * p + 2] = gphi * gp[2];
+      }
+      return;
+    }
+  }
   Grad g;
   bool has = false;
   switch (F.m) {
@@ -396,7 +436,7 @@ struct psdf_plan {
   long long n_poses = 0, n_rows = 0;
   int n_tiles = 0, blob_cap = 16;
   long long n_vtx = 0, blob_total = 0;
-  float eps_sat = 0.f, eps_axis = 0.f;
+  float eps_sat = 0.f, eps_axis = 0.f, eta = 0.f;
   std::vector<long long> inst_pose0, inst_npose;
   std::vector<int> inst_tile0, inst_ntile, inst_m;
   std::vector<int> tile_vtx;  // edges of each tile (work estimate)
@@ -520,12 +560,14 @@ int apply_config(psdf_plan *pl, const psdf_plan_config &cfg, cudaStream_t st)
   if (e != cudaSuccess) return cuda_fail(e, "plan work queue upload");
   const size_t smem = kPlanSmemHead + kFpBytes + 2 * (size_t)pl->blob_cap;
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batched_kernel)");
+    for (auto k : {batched_kernel<false>, batched_kernel<true>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batched_kernel)");
+    }
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, cfg.threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, pl->eta > 0.f ? batched_kernel<true> : batched_kernel<false>, cfg.threads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   per_sm = std::max(per_sm, 1);
   pl->cfg = cfg;
@@ -560,8 +602,10 @@ int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *d
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(plan workspace)");
   {
     ProfileScope prof("batched", st);
-    batched_kernel<<<pl->grid, pl->cfg.threads, pl->smem, st>>>(
-        pl->d_items, pl->n_items, pl->d_blocks, pl->d_fprec, pl->eps_sat, poses, pl->d_tiles,
+    const ParamsK pk{pl->eps_sat, pl->eta};
+    (pl->eta > 0.f ? batched_kernel<true> : batched_kernel<false>)<<<pl->grid, pl->cfg.threads,
+                                                                      pl->smem, st>>>(
+        pl->d_items, pl->n_items, pl->d_blocks, pl->d_fprec, pk, poses, pl->d_tiles,
         pl->d_blob, pl->blob_cap, pl->d_keys, pl->d_ctr, plan_bounds(pl));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch (batched)");
@@ -569,8 +613,10 @@ int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *d
   {
     ProfileScope prof("batched_epilogue", st);
     const long long P = pl->n_poses;
-    batched_epilogue_kernel<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
-        pl->d_pose_inst, P, pl->d_fp, pl->d_inst, pl->eps_sat, pl->eps_axis, poses,
+    const ParamsK pk{pl->eps_sat, pl->eta};
+    (pl->eta > 0.f ? batched_epilogue_kernel<true>
+                   : batched_epilogue_kernel<false>)<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
+        pl->d_pose_inst, P, pl->d_fp, pl->d_inst, pk, pl->eps_axis, poses,
         pl->d_row_obs, pl->d_vtx, pl->d_far, pl->d_keys, pl->d_ctr, phi, dphi, active,
         so.stage, so.d_min, plan_bounds(pl));
     e = cudaGetLastError();
@@ -606,8 +652,8 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
   *out = nullptr;
   if (n_inst < 0) return fail(PSDF_ERR_ARG, "n_inst < 0");
   if (!params) return fail(PSDF_ERR_ARG, "params is NULL");
-  if (params->eta > 0.f)
-    return fail(PSDF_ERR_ARG, "soft-min penetration (eta > 0) is not available in a plan");
+  if (!(params->eta >= 0.f) || !std::isfinite(params->eta))
+    return fail(PSDF_ERR_ARG, "eta must be finite and >= 0");
   if (!(params->eps_sat >= 0.f)) return fail(PSDF_ERR_ARG, "eps_sat must be >= 0");
   if (n_inst > 0 && (!footprints || !fp_offsets || !obs_offsets || !inst_obs || !pose_offsets))
     return fail(PSDF_ERR_ARG, "NULL array");
@@ -636,6 +682,7 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
   cudaGetDevice(&pl->device);
   pl->n_inst = n_inst;
   pl->eps_sat = params->eps_sat;
+  pl->eta = params->eta;
   pl->eps_axis = params->eps_axis;
   pl->n_poses = n_inst > 0 ? pose_offsets[n_inst] : 0;
   pl->n_rows = R;
@@ -760,6 +807,7 @@ extern "C" int psdf_plan_create(int32_t n_inst, const float *footprints,
     uint64_t h = 1469598103934665603ull;
     h = fnv(h, (uint64_t)device_sms());
     h = fnv(h, (uint64_t)n_inst);
+    h = fnv(h, (uint64_t)(pl->eta > 0.f));  // the soft minimum's kernel times differently
     for (int i = 0; i < n_inst; ++i) {
       h = fnv(h, (uint64_t)pl->inst_npose[i]);
       h = fnv(h, (uint64_t)pl->inst_ntile[i]);
@@ -932,8 +980,10 @@ extern "C" int psdf_backward_batched(const psdf_plan *plan, const float *poses,
   cudaStream_t st = (cudaStream_t)stream;
   ProfileScope prof("batched_backward", st);
   const long long P = plan->n_poses;
-  batched_backward_kernel<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
-      plan->d_pose_inst, P, plan->d_fp, plan->d_inst, plan->eps_axis, poses, plan->d_row_obs,
+  const ParamsK pk{plan->eps_sat, plan->eta};
+  (plan->eta > 0.f ? batched_backward_kernel<true>
+                   : batched_backward_kernel<false>)<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
+      plan->d_pose_inst, P, plan->d_fp, plan->d_inst, pk, plan->eps_axis, poses, plan->d_row_obs,
       plan->d_vtx, plan->d_far, active, grad_phi, grad_pose, grad_edges);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (batched backward)");

@@ -254,42 +254,25 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
   if (SOFT) {
     // a penetration pair names a non-separated obstacle: its gradient is the
     // softmax-weighted sum over the obstacle's axes
-    const long long row = pid >> kPairShiftEdge;
-    const int kind = (pid >> kPairShiftKind) & 0xF;
-    if (pid != PSDF_PAIR_NONE && row < rows_total && kind >= kRAxisOMax && kind <= kOAxisRMax) {
-      const ObsRec o = row_obs[row];
-      if (o.n > 0) {
-        float s, c;
-        sincosf(th, &s, &c);
-        const float4 *vt = vtx + 2 * (long long)o.vtx_global;
-        const Active a = obstacle_detail<M, true>(F, px, py, c, s, vt, o.n, o.orig_first,
-                                                  prm.eps_sat, prm.eta);
-        if (!a.separated) {
-          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-          soft_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first, eps_axis,
-                       prm.eta, a.pen, [&](float w, const Grad &g) {
-                         g0 = __fmaf_rn(w, g.gp[0], g0);
-                         g1 = __fmaf_rn(w, g.gp[1], g1);
-                         g2 = __fmaf_rn(w, g.gp[2], g2);
-                         if (grad_edges) {
-                           const float sc = gphi * w;
-                           for (int i = 0; i < kGradRows; ++i) {
-                             if (i >= g.nrow) break;
-                             atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]],
-                                       sc * g.gx[i]);
-                             atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1],
-                                       sc * g.gy[i]);
-                           }
-                         }
-                       });
-          if (grad_pose) {
-            grad_pose[3 * p] = gphi * g0;
-            grad_pose[3 * p + 1] = gphi * g1;
-            grad_pose[3 * p + 2] = gphi * g2;
-          }
-          return;
-        }
+    float gp[3];
+    if (soft_backward_pose<M>(F, prm.eps_sat, prm.eta, eps_axis, px, py, th, pid, row_obs,
+                              rows_total, vtx, far, gp, [&](float w, const Grad &g) {
+                                if (!grad_edges) return;
+                                const float sc = gphi * w;
+                                for (int i = 0; i < kGradRows; ++i) {
+                                  if (i >= g.nrow) break;
+                                  atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]],
+                                            sc * g.gx[i]);
+                                  atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1],
+                                            sc * g.gy[i]);
+                                }
+                              })) {
+      if (grad_pose) {
+        grad_pose[3 * p] = gphi * gp[0];
+        grad_pose[3 * p + 1] = gphi * gp[1];
+        grad_pose[3 * p + 2] = gphi * gp[2];
       }
+      return;
     }
   }
   Grad g;

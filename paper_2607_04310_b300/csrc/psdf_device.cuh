@@ -1075,6 +1075,44 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
   return r;
 }
 
+// Soft-minimum backward of one pose: when its active pair names a
+// penetration axis of an obstacle that is not separated, the pose gradient
+// is the softmax-weighted sum over the obstacle's axes (written to gp) and
+// every axis's edge-endpoint rows go to edge(w, Grad); false otherwise (the
+// hard closed form of backward_pose then applies).  row_obs / rows_total
+// are those of the pose's scene.
+template <int M, class Edge>
+__device__ __forceinline__ bool soft_backward_pose(const FootprintK &F, float eps_sat,
+                                                   float eta, float eps_axis, float px,
+                                                   float py, float theta, unsigned pid,
+                                                   const ObsRec *__restrict__ row_obs,
+                                                   long long rows_total,
+                                                   const float4 *__restrict__ vtx,
+                                                   const int *__restrict__ far, float (&gp)[3],
+                                                   Edge edge)
+{
+  const long long row = pid >> kPairShiftEdge;
+  const int kind = (pid >> kPairShiftKind) & 0xF;
+  if (pid == PSDF_PAIR_NONE || row >= rows_total || kind < kRAxisOMax || kind > kOAxisRMax)
+    return false;
+  const ObsRec o = row_obs[row];
+  if (o.n == 0) return false;
+  float s, c;
+  sincosf(theta, &s, &c);
+  const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  const Active a = obstacle_detail<M, true>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat, eta);
+  if (a.separated) return false;
+  gp[0] = gp[1] = gp[2] = 0.f;
+  soft_grad<M>(F, px, py, c, s, vt, far + o.vtx_global, o.n, o.orig_first, eps_axis, eta, a.pen,
+               [&](float w, const Grad &g) {
+                 gp[0] = __fmaf_rn(w, g.gp[0], gp[0]);
+                 gp[1] = __fmaf_rn(w, g.gp[1], gp[1]);
+                 gp[2] = __fmaf_rn(w, g.gp[2], gp[2]);
+                 edge(w, g);
+               });
+  return true;
+}
+
 // Closed-form gradient of one pose's active pair (pid) w.r.t. the pose and
 // the stored edge endpoints (rows of the pose's scene).  False when the pair
 // is none, out of range, or on the flat branch of max(delta, 0).

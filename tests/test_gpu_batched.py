@@ -230,3 +230,46 @@ def test_uneven_instances_full_size_against_oracle():
         compare(got, ref)
         p0 += n
     assert p0 == plan.n_poses
+
+
+@pytest.mark.parametrize("eta", [20.0, 500.0])
+def test_soft_plan_matches_single_scene(eta):
+    """The soft minimum through a plan: values, pairs and pose gradients bit
+    for bit equal to one psdf_eval_grad per instance, and the backward's pose
+    gradients too (edge gradients to float-atomic order), with half of every
+    instance's poses moved onto obstacle vertices (penetrations)."""
+    insts = [w for w in _mixed_instances(23, n_inst=18) if w.poses.shape[0] and w.edges.shape[0]]
+    g = np.random.default_rng(24)
+    for w in insts:
+        n = w.poses.shape[0] // 2
+        idx = g.integers(0, w.edges.shape[0], size=n)
+        w.poses[:n, 0:2] = (w.edges[idx, 0:2] + g.normal(size=(n, 2)) * 0.2).astype(np.float32)
+    prm = psdf.make_params(eta=eta)
+    plan = _plan(insts, params=prm)
+    poses = _poses(insts)
+    phi, dphi, act = psdf.eval_batched(plan, poses)
+    P = plan.n_poses
+    gphi = torch.linspace(0.5, 1.5, P, device="cuda")
+    gpose = torch.empty((P, 3), device="cuda")
+    gedges = torch.zeros((plan.edges.shape[0], 4), device="cuda")
+    psdf.psdf_backward_batched(plan, poses, act, gphi, gpose, gedges)
+    torch.cuda.synchronize()
+    p0, r0, n_pen = 0, 0, 0
+    for w in insts:
+        n, E = w.poses.shape[0], w.edges.shape[0]
+        sc = psdf.Scene.from_csr(w.edges, w.offsets)
+        ps = poses[p0:p0 + n].contiguous()
+        rphi, rdphi, ract = psdf.eval_grad(sc, w.footprint, ps, params=prm)
+        ga = torch.empty((n, 3), device="cuda")
+        ge = torch.zeros((E, 4), device="cuda")
+        psdf.psdf_backward(w.footprint, sc, ps, prm, ract, gphi[p0:p0 + n].contiguous(), ga, ge)
+        torch.cuda.synchronize()
+        assert np.array_equal(_bits(phi[p0:p0 + n]), _bits(rphi))
+        assert np.array_equal(_bits(act[p0:p0 + n]), _bits(ract))
+        assert np.array_equal(_bits(dphi[p0:p0 + n]), _bits(rdphi))
+        assert np.array_equal(_bits(gpose[p0:p0 + n]), _bits(ga))
+        assert torch.allclose(gedges[r0:r0 + E], ge, rtol=1e-5, atol=1e-6)
+        n_pen += int((rphi < 0).sum())
+        p0 += n
+        r0 += E
+    assert n_pen >= 50

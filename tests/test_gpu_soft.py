@@ -116,7 +116,8 @@ def test_soft_rejected_where_unsupported():
                               torch.empty((w.P, n_tiles), device="cuda"))
     assert ei.value.code == psdf.PSDF_ERR_ARG
     with pytest.raises(psdf.PsdfError) as ei:
-        psdf.Plan([(w.footprint, w.edges, w.offsets, w.P)], params=prm)
+        psdf.Plan([(w.footprint, w.edges, w.offsets, w.P)],
+                  params=psdf.make_params(eta=float("inf")))
     assert ei.value.code == psdf.PSDF_ERR_ARG
     with pytest.raises(psdf.PsdfError) as ei:
         psdf.eval_grad(sc, w.footprint, ps, params=psdf.make_params(eta=float("nan")))
