@@ -273,3 +273,13 @@ def test_soft_plan_matches_single_scene(eta):
         p0 += n
         r0 += E
     assert n_pen >= 50
+
+
+def test_zz_no_index_violation_recorded():
+    """Run last in this module: a debug build (PSDF_DEBUG=1) checks every
+    index the batched kernels take from their data and records the first
+    violation; none may have been seen by the tests above."""
+    v, enabled = psdf.psdf_plan_debug_read()
+    if not enabled:
+        pytest.skip("release build: the index checks are compiled out")
+    assert v == 0, "site %d, index %d" % (v >> 48, v & ((1 << 48) - 1))
