@@ -110,11 +110,16 @@ __device__ __forceinline__ float tile_lb(const float *ab, float px, float py, fl
 // posed footprint lies in [|p - C| - r - r_foot, |p - C| + r + r_foot]
 // (every footprint point is within r_foot of p, every obstacle point within r
 // of C), each widened by the bound's margin.
-__device__ __forceinline__ float circle_ub(float4 cc, float px, float py, float rfoot)
+__device__ __forceinline__ float circle_ub(float4 cc, float px, float py, float rfoot,
+                                           float rin)
 {
   const float dx = cc.x - px, dy = cc.y - py;
   const float d = sqrtf(dx * dx + dy * dy);
-  return (d + cc.z + rfoot) + (1e-4f + 1e-5f * d);
+  // the circle's centre lies in the obstacle; with a disc of radius rin about
+  // the pose inside the footprint the two come within d - rin of each other,
+  // else within d + r + r_foot
+  const float b = rin >= 0.f ? fmaxf(d - rin, 0.f) : (d + cc.z + rfoot);
+  return b + (1e-4f + 1e-5f * d);
 }
 
 __device__ __forceinline__ float circle_lb_value(float4 cc, float px, float py, float rfoot)
@@ -385,7 +390,7 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
 template <int K, bool NET>
 __global__ void __launch_bounds__(kPoseThreads)
     propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
-            int T, const CullGrid grid, float rfoot, float ub_pad,
+            int T, const CullGrid grid, float rfoot, float rin, float ub_pad,
             const unsigned char *__restrict__ blob,
             const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
             float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
@@ -546,7 +551,7 @@ __global__ void __launch_bounds__(kPoseThreads)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (o + 16 * q < h.z) {
-            ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot));
+            ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot, rin));
             ++n_circ;
           }
       }
@@ -1115,7 +1120,8 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
 #define PSDF_PROPOSE(KK)                                                                      \
   e = launch_pdl(net ? propose<KK, true> : propose<KK, false>, dim3(pb), dim3(kPoseThreads), 0, \
                  st, poses, (long long)P, (const TileHdr *)scene->d_tiles, T, scene->grid,      \
-                 F.radius, ub_pad, (const unsigned char *)scene->d_blob, frag, b2, keys, pose4, \
+                 F.radius, F.inner, ub_pad, (const unsigned char *)scene->d_blob, frag, b2,     \
+                 keys, pose4,                                                                   \
                  ub,                                                                            \
                  prop, hist, list, ctr);
       switch (K) {

@@ -364,6 +364,13 @@ int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F)
     F->ahi[l] = (float)hi;
   }
   F->radius = (float)(rad * (1.0 + 1e-6));
+  // the largest disc about the pose inside the footprint: the smallest
+  // distance from the pose to an edge line (all positive iff the pose lies
+  // inside), rounded down
+  double inner = INFINITY;
+  for (int l = 0; l < m; ++l)
+    inner = std::min(inner, (double)F->vx[l] * F->nx[l] + (double)F->vy[l] * F->ny[l]);
+  F->inner = inner > 1e-6 ? (float)(inner * (1.0 - 1e-5) - 1e-7) : -1.f;
   return PSDF_OK;
 }
 

@@ -44,6 +44,8 @@ struct FootprintK {
   float nx[kMaxM], ny[kMaxM];    // outward unit normals n_l
   float alo[kMaxM], ahi[kMaxM];  // robot interval on n_l: [alpha_P, beta_P]
   float radius;                  // max_l |v_l| (bounding radius about the pose)
+  float inner;                   // radius of a disc about the pose inside the footprint,
+                                 // or -1 when the pose lies outside it
   int m;
 };
 
