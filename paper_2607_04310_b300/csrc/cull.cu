@@ -115,10 +115,10 @@ __device__ __forceinline__ float circle_ub(float4 cc, float px, float py, float 
 {
   const float dx = cc.x - px, dy = cc.y - py;
   const float d = sqrtf(dx * dx + dy * dy);
-  // the circle's centre lies in the obstacle; with a disc of radius rin about
-  // the pose inside the footprint the two come within d - rin of each other,
-  // else within d + r + r_foot
-  const float b = rin >= 0.f ? fmaxf(d - rin, 0.f) : (d + cc.z + rfoot);
+  // a disc of radius cc.w about the circle's centre lies in the obstacle;
+  // with a disc of radius rin about the pose inside the footprint the two
+  // come within d - rin - cc.w of each other, else within d + r + r_foot
+  const float b = rin >= 0.f ? fmaxf(d - rin - cc.w, 0.f) : (d + cc.z + rfoot);
   return b + (1e-4f + 1e-5f * d);
 }
 

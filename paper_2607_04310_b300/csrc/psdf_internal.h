@@ -63,7 +63,8 @@ struct ParamsK {
 // alpha', beta': the obstacle's interval on its own edge normal
 // rot90(u)/(|u|+eps_axis), measured from the edge's start A (pose-invariant).
 // blob_bytes covers these two parts; right after them follow
-//   float4 circ[n_obs]       {cx, cy, r, 0}: a circle containing the obstacle
+//   float4 circ[n_obs]       {cx, cy, r, rin}: a circle containing the obstacle
+//                            and the radius of a disc about its centre inside it
 // which only the cull reads (blob_off of the next tile skips them).
 struct TileHdr {
   int blob_off;    // byte offset of the blob (16-byte aligned)

@@ -238,7 +238,17 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
           r2 = std::max(r2, wx * wx + wy * wy);
         }
         const float rf = std::nextafter((float)std::sqrt(r2), INFINITY);
-        circ[s - s0] = make_float4(cxf, cyf, rf, 0.f);
+        // inner radius: the disc about the centre inside a closed polygon (its
+        // distance to the nearest edge line), rounded down; 0 for a segment
+        double rin = o.n >= 3 ? INFINITY : 0.0;
+        for (int k = 0; k < o.n && o.n >= 3; ++k) {
+          const double ax = e[4 * k], ay = e[4 * k + 1];
+          const double ux = (double)e[4 * k + 2] - ax, uy = (double)e[4 * k + 3] - ay;
+          const double dist = (ux * (cyf - ay) - uy * (cxf - ax)) / std::sqrt(ux * ux + uy * uy);
+          rin = std::min(rin, dist);
+        }
+        const float rinf = rin > 1e-6 ? (float)(rin * (1.0 - 1e-5) - 1e-7) : 0.f;
+        circ[s - s0] = make_float4(cxf, cyf, rf, rinf);
       }
       for (int k = 0; k < o.n; ++k) {
         double ax = e[4 * k], ay = e[4 * k + 1], bx = e[4 * k + 2], by = e[4 * k + 3];
