@@ -447,30 +447,26 @@ __global__ void __launch_bounds__(kPoseThreads)
   for (int i = 0; i < K; ++i) best[i] = -1;
   float ubp = kInf;  // upper bound (metres) on the pose's phi
   if (pw < P) {  // uniform over the warp
-    // R rounds of a 16-lane minimum over the lanes' heads, as 64-bit keys
-    // (squared distance bits << 32 | tile << 4 | lane; the squared distance
-    // is not negative, so its bits order like the value, and a tile sits in
-    // one lane only).  A lane keeps only its RL best, so with the network
-    // the 8 candidates are the 8 smallest bounds it looked at unless one
-    // lane held more than RL of them.
+    // R rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys
+    // (the top 16 bits of the squared distance -- not negative, so its bits
+    // order like the value, to 1/128 -- over the tile's 16 bits; a tile sits
+    // in one lane only, so the lane whose head won pops it).  A lane keeps
+    // only its RL best, so with the network the 8 candidates are the 8
+    // smallest bounds it looked at unless one lane held more than RL of them.
     int cand[R];
     int head = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      unsigned long long key = ~0ull;
+      unsigned mine = ~0u;
 #pragma unroll
       for (int i = 0; i < RL; ++i)
-        if (i == head && id[i] >= 0)
-          key = ((unsigned long long)__float_as_uint(sc[i]) << 32) |
-                ((unsigned)id[i] << 4) | (unsigned)hl;
+        if (i == head && id[i] >= 0) mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
+      unsigned key = mine;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        key = k2 < key ? k2 : key;
-      }
-      const bool any = key != ~0ull;
-      cand[r] = any ? (int)((unsigned)(key & 0xffffffffu) >> 4) : -1;
-      if (any && (int)(key & 15u) == hl) ++head;
+      for (int o = 8; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+      const bool any = key != ~0u;
+      cand[r] = any ? (int)(key & 0xffffu) : -1;
+      if (any && key == mine) ++head;
     }
     if constexpr (NET) {
       if (hl == 0)
