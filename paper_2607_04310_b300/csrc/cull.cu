@@ -644,6 +644,10 @@ __device__ __forceinline__ void cp_async_wait_all()
 constexpr int kTileCTAs = 2;
 constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
 
+// The first n_items queued (lane, obstacle) items of the warp, kItemLanes
+// lanes per item (the obstacle's edges shared out, see obstacle_value_coop),
+// 32 / kItemLanes items a round; every lane takes part in every round.
+constexpr int kItemLanes = 4;
 template <int M, bool SOFT>
 __device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
                                            const int *qw, int n_items, int lane, float px,
@@ -653,19 +657,25 @@ __device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &p
                                            unsigned long long &n_obs,
                                            unsigned long long &n_edge)
 {
-  const int item = lane < n_items ? qw[lane] : 0;
-  const int src = item >> 16, o = item & 0xffff;
-  // the item's pose from the lane that found it (every lane takes part)
-  const float ipx = __shfl_sync(0xffffffffu, px, src), ipy = __shfl_sync(0xffffffffu, py, src);
-  const float ic = __shfl_sync(0xffffffffu, c, src), is = __shfl_sync(0xffffffffu, s, src);
-  const long long ip = __shfl_sync(0xffffffffu, p, src);
-  if (lane < n_items) {
-    const int4 rec = ob[o];
-    const float v = obstacle_value<M, FootprintK, SOFT>(F, ipx, ipy, ic, is, vt + 2 * rec.x,
-                                                        rec.y, prm.eps_sat, prm.eta);
-    atomicMin(&keys[ip], pack_key(v, rec.z));
-    ++n_obs;
-    n_edge += rec.y;
+  constexpr int B = 32 / kItemLanes;
+  const int g = lane % kItemLanes;
+  for (int r0 = 0; r0 < n_items; r0 += B) {
+    const int slot = r0 + lane / kItemLanes;
+    const bool live = slot < n_items;
+    const int item = live ? qw[slot] : 0;
+    const int src = item >> 16, o = item & 0xffff;
+    // the item's pose from the lane that found it
+    const float ipx = __shfl_sync(0xffffffffu, px, src), ipy = __shfl_sync(0xffffffffu, py, src);
+    const float ic = __shfl_sync(0xffffffffu, c, src), is = __shfl_sync(0xffffffffu, s, src);
+    const long long ip = __shfl_sync(0xffffffffu, p, src);
+    const int4 rec = live ? ob[o] : make_int4(0, 0, 0, 0);
+    const float v = obstacle_value_coop<M, kItemLanes, SOFT>(F, ipx, ipy, ic, is, vt + 2 * rec.x,
+                                                             rec.y, prm.eps_sat, prm.eta, g);
+    if (live && g == 0) {
+      atomicMin(&keys[ip], pack_key(v, rec.z));
+      ++n_obs;
+      n_edge += rec.y;
+    }
   }
 }
 

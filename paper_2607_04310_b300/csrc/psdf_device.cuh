@@ -409,6 +409,69 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
   return soft_key(-acc.pen(eta));
 }
 
+// obstacle_value of the hard minimum or the soft minimum by G lanes (G
+// divides 32, groups aligned): lane g of the group takes edges g, g + G, ...
+// (a segment: lane 0 alone); the minima and the extreme projections are
+// merged by shuffles, which are exact, so for the hard minimum every lane
+// returns the serial value bit for bit.  The soft minimum accumulates its
+// axes in a fixed order, so it stays serial (SOFT: lane 0 of the group
+// evaluates the obstacle alone).  Every lane of the warp must call it (n = 0
+// for a group without an obstacle: no loads, the value is then meaningless).
+template <int M, int G, bool SOFT, class FP>
+__device__ __forceinline__ float obstacle_value_coop(const FP &F, float px, float py, float c,
+                                                     float s, const float4 *vt, int n,
+                                                     float eps_sat, float eta, int g)
+{
+  if (SOFT) {
+    float v = kInf;
+    if (g == 0 && n > 0) v = obstacle_value<M, FP, true>(F, px, py, c, s, vt, n, eps_sat, eta);
+    return v;
+  }
+  float pmax[M], pmin[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    pmax[l] = -kInf;
+    pmin[l] = kInf;
+  }
+  float d2min = kInf, dlt = kInf;
+  if (n == 1) {
+    if (g == 0) {
+      const float4 a0 = vt[0], b0 = vt[1];
+      const V2 A0 = to_local(a0.x, a0.y, px, py, c, s);
+      const V2 B0 = to_local(b0.z, b0.w, px, py, c, s);
+      const V2 U0 = local_edge(a0.x, a0.y, b0.z, b0.w, c, s);
+      dlt = edge_step<M, true>(F, A0, B0, U0, a0.z, a0.w, b0.x, b0.y, pmax, pmin, d2min);
+      extra_vertex<M>(F, B0, pmax, pmin, d2min);
+    }
+  } else {
+    for (int k = g; k < n; k += G) {
+      const float4 ak = vt[2 * k], bk = vt[2 * k + 1];
+      const float4 an = vt[2 * (k + 1 < n ? k + 1 : 0)];
+      const V2 A = to_local(ak.x, ak.y, px, py, c, s);
+      const V2 An = to_local(an.x, an.y, px, py, c, s);
+      const V2 U = local_edge(ak.x, ak.y, an.x, an.y, c, s);
+      dlt = fminf(dlt, edge_step<M, false>(F, A, An, U, ak.z, ak.w, bk.x, bk.y, pmax, pmin,
+                                           d2min));
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    d2min = fminf(d2min, __shfl_xor_sync(0xffffffffu, d2min, o));
+    dlt = fminf(dlt, __shfl_xor_sync(0xffffffffu, dlt, o));
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      pmax[l] = fmaxf(pmax[l], __shfl_xor_sync(0xffffffffu, pmax[l], o));
+      pmin[l] = fminf(pmin[l], __shfl_xor_sync(0xffffffffu, pmin[l], o));
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < M; ++l) {
+    const float2 iv = robot_interval(F, l);
+    dlt = fminf(dlt, fminf(__fsub_rn(pmax[l], iv.x), __fsub_rn(iv.y, pmin[l])));
+  }
+  return synth_value(d2min, dlt, eps_sat);
+}
+
 // ---------------------------------------------------------------------------
 // detail of one obstacle: active pair (lowest (value, pair id)) + gradient
 // ---------------------------------------------------------------------------
