@@ -637,9 +637,9 @@ __device__ __forceinline__ void cp_async_wait_all()
 // shared memory (16-byte cp.async per thread) before the CTA waits for the
 // proposals (they are pose-invariant).  Each lane tests its obstacles'
 // circle bounds against the pose's upper bound; the survivors of the warp's
-// 32 lanes are compacted (ballot) into a per-warp queue and evaluated 32 at
-// a time, one (pose, obstacle) item per lane, so that lanes whose obstacles
-// were skipped do not idle through their neighbours' evaluations.  Every
+// 32 lanes are compacted (ballot) into a per-warp queue and evaluated a few
+// at a time, kItemLanes lanes per (pose, obstacle) item, so that lanes whose
+// obstacles were skipped do not idle through their neighbours' evaluations.  Every
 // evaluated obstacle merges its key into the pose's by atomicMin.
 constexpr int kTileCTAs = 2;
 constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
