@@ -702,7 +702,8 @@ __global__ void __launch_bounds__(kListThreads)
   pdl_wait();  // the proposal kernel's lists
   const int cnt = __ldcg(hist + t);
   const int S = tile_split(cnt, h.n_obs);
-  const long long L = (long long)cnt * S;
+  // lane counts fit 32 bits: cnt * S <= max(cnt, 2 * kListThreads) and cnt <= P < 2^31
+  const unsigned L = (unsigned)cnt * (unsigned)S;
   const int units = tile_units(cnt, h.n_obs);
   cp_async_wait_all();
   __syncthreads();
@@ -711,9 +712,9 @@ __global__ void __launch_bounds__(kListThreads)
   const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
   unsigned long long n_obs = 0, n_edge = 0;
   for (int j = j0; j < units; j += kTileCTAs) {
-    const long long l = (long long)j * kListThreads + threadIdx.x;
+    const unsigned l = (unsigned)j * kListThreads + threadIdx.x;
     long long p = -1;
-    if (l < L) p = __ldcg(list + (long long)t * P + l / S);
+    if (l < L) p = __ldcg(list + (long long)t * P + l / (unsigned)S);
     float px = 0.f, py = 0.f, c = 1.f, s = 0.f, thr = -kInf;
     int o0 = 0, o1 = 0;
     if (p >= 0) {
@@ -723,9 +724,9 @@ __global__ void __launch_bounds__(kListThreads)
       c = q4.z;
       s = q4.w;
       thr = ub_value(__ldcg(ub + p));
-      const int part = (int)(l % S);
-      o0 = (int)((long long)h.n_obs * part / S);
-      o1 = (int)((long long)h.n_obs * (part + 1) / S);
+      const int part = (int)(l % (unsigned)S);
+      o0 = h.n_obs * part / S;  // n_obs <= 256 and part < S <= 256
+      o1 = h.n_obs * (part + 1) / S;
     }
     int span = o1 - o0;
 #pragma unroll

@@ -417,16 +417,11 @@ __device__ __forceinline__ float obstacle_value(const FP &F, float px, float py,
 // axes in a fixed order, so it stays serial (SOFT: lane 0 of the group
 // evaluates the obstacle alone).  Every lane of the warp must call it (n = 0
 // for a group without an obstacle: no loads, the value is then meaningless).
-template <int M, int G, bool SOFT, class FP>
-__device__ __forceinline__ float obstacle_value_coop(const FP &F, float px, float py, float c,
-                                                     float s, const float4 *vt, int n,
-                                                     float eps_sat, float eta, int g)
+template <int M, int G, class FP>
+__device__ __forceinline__ float obstacle_value_coop_hard(const FP &F, float px, float py,
+                                                          float c, float s, const float4 *vt,
+                                                          int n, float eps_sat, int g)
 {
-  if (SOFT) {
-    float v = kInf;
-    if (g == 0 && n > 0) v = obstacle_value<M, FP, true>(F, px, py, c, s, vt, n, eps_sat, eta);
-    return v;
-  }
   float pmax[M], pmin[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) {
@@ -470,6 +465,20 @@ __device__ __forceinline__ float obstacle_value_coop(const FP &F, float px, floa
     dlt = fminf(dlt, fminf(__fsub_rn(pmax[l], iv.x), __fsub_rn(iv.y, pmin[l])));
   }
   return synth_value(d2min, dlt, eps_sat);
+}
+
+template <int M, int G, bool SOFT, class FP>
+__device__ __forceinline__ float obstacle_value_coop(const FP &F, float px, float py, float c,
+                                                     float s, const float4 *vt, int n,
+                                                     float eps_sat, float eta, int g)
+{
+  if constexpr (SOFT) {
+    float v = kInf;
+    if (g == 0 && n > 0) v = obstacle_value<M, FP, true>(F, px, py, c, s, vt, n, eps_sat, eta);
+    return v;
+  } else {
+    return obstacle_value_coop_hard<M, G>(F, px, py, c, s, vt, n, eps_sat, g);
+  }
 }
 
 // ---------------------------------------------------------------------------
