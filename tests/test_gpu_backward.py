@@ -135,3 +135,25 @@ def test_backward_matches_fd_of_oracle():
                 fd = (oracle.psdf_eval(fp, ep, offs, poses[q:q + 1])["phi"][0]
                       - oracle.psdf_eval(fp, em, offs, poses[q:q + 1])["phi"][0]) / (2 * h)
                 assert abs(ge[e0 + v, c] - fd) <= 1e-4 * max(1.0, abs(fd)), (q, v, c, ge[e0 + v, c], fd)
+
+
+def test_backward_pose_gradient_equals_forward_at_every_batch_size():
+    """The backward's pose gradient with a unit upstream gradient is the
+    forward's d phi / d pose bit for bit, for batch sizes that give the
+    backward launch every spread of lanes per pose (a warp per pose for
+    small batches, down to a thread per pose above about 600 K poses) and a
+    ragged tail."""
+    w = sg.backward_rects(3, n_inst=8, horizon=8, n_rects=400)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    g = np.random.default_rng(31)
+    dev = torch.device("cuda")
+    for P in (1, 37, 4096, 25_001, 75_003, 700_001):
+        poses = torch.as_tensor(np.concatenate(
+            [g.uniform(0.0, 40.0, size=(P, 2)), g.uniform(-math.pi, math.pi, size=(P, 1))],
+            axis=1).astype(np.float32), device=dev)
+        phi, dphi, act = psdf.eval_grad(scene, w.footprint, poses)
+        gpose = torch.empty((P, 3), device=dev)
+        psdf.psdf_backward(w.footprint, scene, poses, scene.params, act,
+                           torch.ones(P, device=dev), gpose, None)
+        torch.cuda.synchronize()
+        assert torch.equal(gpose.view(torch.int32), dphi.view(torch.int32)), P
