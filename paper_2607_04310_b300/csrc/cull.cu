@@ -53,15 +53,20 @@ constexpr int kListThreads = 128;  // threads of an eval_lists CTA
 constexpr int kMaxScanTiles = 1024 * 64;
 
 // counters at the start of the workspace
+// Pipeline counters, each spread over kCtrSlots words (CTA b adds to slot
+// b % kCtrSlots, so that a few thousand CTAs do not queue on one address);
+// psdf_cull_stats_read sums the slots.
+constexpr int kCtrSlots = 16;
 struct CullCounters {
   int err;
-  int n_prop;          // proposed (pose, tile) pairs
-  int n_fb;            // (pose, tile) pairs added by the bound check
-  int fallback_poses;  // poses with at least one such pair
-  unsigned long long n_obs_eval;   // obstacles evaluated exactly
-  unsigned long long n_edge_eval;  // edges of those obstacles
-  unsigned long long n_bound;      // tile bounds the proposals computed
-  unsigned long long n_circ;       // obstacle circles of the proposals' upper bounds
+  int pad;
+  unsigned long long n_prop[kCtrSlots];       // proposed (pose, tile) pairs
+  unsigned long long n_fb[kCtrSlots];         // (pose, tile) pairs added by the bound check
+  unsigned long long fallback_poses[kCtrSlots];  // poses with at least one such pair
+  unsigned long long n_obs_eval[kCtrSlots];   // obstacles evaluated exactly
+  unsigned long long n_edge_eval[kCtrSlots];  // edges of those obstacles
+  unsigned long long n_bound[kCtrSlots];      // tile bounds the proposals computed
+  unsigned long long n_circ[kCtrSlots];       // obstacle circles of the proposals' upper bounds
 };
 
 struct CullLayout {
@@ -77,7 +82,7 @@ static CullLayout cull_layout(long long P, int n_tiles)
   CullLayout L;
   const size_t Pz = (size_t)std::max<long long>(P, 1);
   const size_t Tz = (size_t)std::max(n_tiles, 1);
-  size_t o = 256;
+  size_t o = align256(sizeof(CullCounters));
   L.hist = o; o = align256(o + 4 * Tz);
   L.clear_bytes = o;
   L.keys = o; o = align256(o + 8 * Pz);
@@ -605,11 +610,12 @@ __global__ void __launch_bounds__(kPoseThreads)
   pdl_wait();  // (warps of poses beyond P reach the counters without appending)
   __syncthreads();
   if (threadIdx.x == 0) {
-    atomicAdd(&ctr->n_prop, s_prop);
-    atomicAdd(&ctr->n_fb, s_fb);
-    atomicAdd(&ctr->fallback_poses, s_fbp);
-    atomicAdd(&ctr->n_bound, (unsigned long long)s_bound);
-    atomicAdd(&ctr->n_circ, (unsigned long long)s_circ);
+    const int slot = blockIdx.x % kCtrSlots;
+    atomicAdd(&ctr->n_prop[slot], (unsigned long long)s_prop);
+    atomicAdd(&ctr->n_fb[slot], (unsigned long long)s_fb);
+    atomicAdd(&ctr->fallback_poses[slot], (unsigned long long)s_fbp);
+    atomicAdd(&ctr->n_bound[slot], (unsigned long long)s_bound);
+    atomicAdd(&ctr->n_circ[slot], (unsigned long long)s_circ);
   }
   pdl_trigger();  // the evaluation kernel may launch; it waits for this grid
 }
@@ -760,9 +766,18 @@ __global__ void __launch_bounds__(kListThreads)
     n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
     n_edge += __shfl_xor_sync(0xffffffffu, n_edge, o);
   }
+  __shared__ unsigned long long s_cnt[2];
+  if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0ull;
+  __syncthreads();
   if (lane == 0 && n_obs) {
-    atomicAdd(&ctr->n_obs_eval, n_obs);
-    atomicAdd(&ctr->n_edge_eval, n_edge);
+    atomicAdd(&s_cnt[0], n_obs);
+    atomicAdd(&s_cnt[1], n_edge);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_cnt[0]) {
+    const int slot = blockIdx.x % kCtrSlots;
+    atomicAdd(&ctr->n_obs_eval[slot], s_cnt[0]);
+    atomicAdd(&ctr->n_edge_eval[slot], s_cnt[1]);
   }
 }
 
@@ -1162,13 +1177,18 @@ extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cu
   CullCounters c;
   e = cudaMemcpy(&c, workspace, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(cull counters)");
-  stats->evaluated_obstacles = (int64_t)c.n_obs_eval;
-  stats->evaluated_edges = (int64_t)c.n_edge_eval;
-  stats->proposed_items = c.n_prop;
-  stats->fallback_items = c.n_fb;
-  stats->fallback_poses = c.fallback_poses;
-  stats->bound_evaluations = (int64_t)c.n_bound;
-  stats->circle_evaluations = (int64_t)c.n_circ;
+  auto sum = [](const unsigned long long (&v)[kCtrSlots]) {
+    unsigned long long t = 0;
+    for (int i = 0; i < kCtrSlots; ++i) t += v[i];
+    return (int64_t)t;
+  };
+  stats->evaluated_obstacles = sum(c.n_obs_eval);
+  stats->evaluated_edges = sum(c.n_edge_eval);
+  stats->proposed_items = sum(c.n_prop);
+  stats->fallback_items = sum(c.n_fb);
+  stats->fallback_poses = sum(c.fallback_poses);
+  stats->bound_evaluations = sum(c.n_bound);
+  stats->circle_evaluations = sum(c.n_circ);
   if (c.err) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out");
   return PSDF_OK;
 }
