@@ -49,6 +49,7 @@ constexpr int kPre = 8;  // bound-ranked candidates the network re-ranks per pos
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
 constexpr int kPoseThreads = 128;  // 4 warps x 2 poses per propose / fallback CTA
+constexpr int kKeep = 2;  // cell entries a propose lane keeps from its ranking pass
 constexpr int kListThreads = 128;  // threads of an eval_lists CTA
 constexpr int kMaxScanTiles = 1024 * 64;
 
@@ -439,11 +440,29 @@ __global__ void __launch_bounds__(kPoseThreads)
     sc[i] = kInf;
     id[i] = -1;
   }
-  // entries i of the cell's list (tile grid.tl[i]) or tiles i
+  // entries i of the cell's list (tile grid.tl[i], its AABB grid.ab[i]) or
+  // tiles i; a lane's first kKeep cell entries stay in registers for the
+  // candidate pass below
   const int lo = (cell >= 0 ? e0 : 0) + hl, hi = valid ? (cell >= 0 ? e1 : T) : 0;
-  for (int i = lo; i < hi; i += 16) {
+  int kt[kKeep];
+  float kd2[kKeep];
+  int i = lo;
+#pragma unroll
+  for (int q = 0; q < kKeep; ++q, i += 16) {
+    kt[q] = -1;
+    kd2[q] = kInf;
+    if (i < hi) {
+      const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
+      const float d2 = aabb_d2(cell >= 0 ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py);
+      topk_insert<RL>(sc, id, d2, t);
+      kt[q] = t;
+      kd2[q] = d2;
+      ++n_bound;
+    }
+  }
+  for (; i < hi; i += 16) {
     const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
-    topk_insert<RL>(sc, id, aabb_d2(tile_aabb(tiles, t), px, py), t);
+    topk_insert<RL>(sc, id, aabb_d2(cell >= 0 ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py), t);
     ++n_bound;
   }
   __syncthreads();  // s_prop, s_fb, s_fbp initialised
@@ -572,13 +591,11 @@ __global__ void __launch_bounds__(kPoseThreads)
   const float Dc2 = Dc >= 0.f ? Dc * Dc : -1.f;
   const bool in_cell = cell >= 0 && Dc <= grid.reach_q;
   const int clo = (in_cell ? e0 : 0) + hl, chi = valid ? (in_cell ? e1 : T) : 0;
-  for (int i = clo; i < chi; i += 16) {
-    const int t = in_cell ? __ldg(grid.tl + i) : i;
+  auto consider = [&](int t, float d2) {
     bool proposed = false;
 #pragma unroll
     for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
-    ++n_bound;
-    if (!proposed && aabb_d2(tile_aabb(tiles, t), px, py) <= Dc2) {
+    if (!proposed && d2 <= Dc2) {
       if (ncand < kDefer) {
 #pragma unroll
         for (int q = 0; q < kDefer; ++q)
@@ -588,6 +605,17 @@ __global__ void __launch_bounds__(kPoseThreads)
       }
       ++ncand;
     }
+  };
+  i = clo;
+  if (in_cell) {  // the same entries as the ranking pass: its first ones kept
+#pragma unroll
+    for (int q = 0; q < kKeep; ++q, i += 16)
+      if (i < chi) consider(kt[q], kd2[q]);
+  }
+  for (; i < chi; i += 16) {
+    const int t = in_cell ? __ldg(grid.tl + i) : i;
+    consider(t, aabb_d2(in_cell ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py));
+    ++n_bound;
   }
 #pragma unroll
   for (int q = 0; q < kDefer; ++q)

@@ -96,8 +96,9 @@ struct ObsRec {
 struct CullGrid {
   float x0 = 0.f, y0 = 0.f, inv_cs = 0.f, reach_q = -1.f;
   int nx = 0, ny = 0;
-  const int *off = nullptr;  // [nx * ny + 1] list offsets (device)
-  const int *tl = nullptr;   // tile lists (device)
+  const int *off = nullptr;    // [nx * ny + 1] list offsets (device)
+  const int *tl = nullptr;     // tile lists (device)
+  const float4 *ab = nullptr;  // [entries] AABB of tile tl[i], beside it (device)
 };
 
 }  // namespace psdf
@@ -119,6 +120,7 @@ struct psdf_scene {
   float grid_cell = 0.f;              // cell side (m)
   int64_t grid_entries = 0;
   int *d_cell_off = nullptr, *d_cell_tiles = nullptr;
+  float4 *d_cell_aabbs = nullptr;
   size_t device_bytes = 0;
   // host copies used for launch configuration
   int max_blob_bytes = 0;      // largest tile blob (obstacle + vertex records)

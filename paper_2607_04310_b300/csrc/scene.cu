@@ -81,6 +81,7 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_row_obs);
   cudaFree(s->d_cell_off);
   cudaFree(s->d_cell_tiles);
+  cudaFree(s->d_cell_aabbs);
   delete s;
 }
 
@@ -316,12 +317,13 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
 // No grid when the lists would grow far beyond the tile count (strongly
 // uneven tiles): lookups then scan all tiles.
 void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<int> *off,
-                     std::vector<int> *tl)
+                     std::vector<int> *tl, std::vector<float4> *ab)
 {
   *g = CullGrid();
   *cell = 0.f;
   off->clear();
   tl->clear();
+  ab->clear();
   const int T = hs.T;
   if (T == 0) return;
   const double x0 = hs.bb[0], y0 = hs.bb[1];
@@ -351,6 +353,7 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
   off->assign((size_t)nx * ny + 1, 0);
   for (size_t c = 0; c < (size_t)nx * ny; ++c) (*off)[c + 1] = (*off)[c] + cnt[c];
   tl->assign((size_t)total, 0);
+  ab->assign((size_t)total, make_float4(0.f, 0.f, 0.f, 0.f));
   std::vector<int> cur(off->begin(), off->end() - 1);
   for (int t = 0; t < T; ++t) {  // increasing t: every list sorted
     const float *a = hs.tiles[t].aabb;
@@ -358,7 +361,11 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
     span(a[0] - x0, a[2] - x0, nx, &i0, &i1);
     span(a[1] - y0, a[3] - y0, ny, &j0, &j1);
     for (int j = j0; j <= j1; ++j)
-      for (int i = i0; i <= i1; ++i) (*tl)[cur[(size_t)j * nx + i]++] = t;
+      for (int i = i0; i <= i1; ++i) {
+        const int e = cur[(size_t)j * nx + i]++;
+        (*tl)[e] = t;
+        (*ab)[e] = make_float4(a[0], a[1], a[2], a[3]);
+      }
   }
   g->x0 = hs.bb[0];
   g->y0 = hs.bb[1];
@@ -394,13 +401,16 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   if (!rc) rc = dev_upload(&s->d_far, hs.far, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_row_obs, hs.row_obs, st, &s->device_bytes);
   std::vector<int> cell_off, cell_tiles;
-  build_cull_grid(hs, &s->grid, &s->grid_cell, &cell_off, &cell_tiles);
+  std::vector<float4> cell_aabbs;
+  build_cull_grid(hs, &s->grid, &s->grid_cell, &cell_off, &cell_tiles, &cell_aabbs);
   s->grid_entries = (int64_t)cell_tiles.size();
   if (!rc && s->grid.nx > 0) {
     rc = dev_upload(&s->d_cell_off, cell_off, st, &s->device_bytes);
     if (!rc) rc = dev_upload(&s->d_cell_tiles, cell_tiles, st, &s->device_bytes);
+    if (!rc) rc = dev_upload(&s->d_cell_aabbs, cell_aabbs, st, &s->device_bytes);
     s->grid.off = s->d_cell_off;
     s->grid.tl = s->d_cell_tiles;
+    s->grid.ab = s->d_cell_aabbs;
   }
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
