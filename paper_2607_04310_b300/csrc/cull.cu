@@ -676,7 +676,8 @@ __device__ __forceinline__ void cp_async_wait_all()
 // obstacles were skipped do not idle through their neighbours' evaluations.  Every
 // evaluated obstacle merges its key into the pose's by atomicMin.
 constexpr int kTileCTAs = 2;
-constexpr int kQueue = 64;  // per-warp queue of (lane, obstacle) items
+constexpr int kFilt = 4;    // circle bounds a lane tests between two queue appends
+constexpr int kQueue = 31 + 32 * kFilt;  // per-warp queue of (lane, obstacle) items
 
 // The first n_items queued (lane, obstacle) items of the warp, kItemLanes
 // lanes per item (the obstacle's edges shared out, see obstacle_value_coop),
@@ -739,6 +740,21 @@ __global__ void __launch_bounds__(kListThreads)
   // lane counts fit 32 bits: cnt * S <= max(cnt, 2 * kListThreads) and cnt <= P < 2^31
   const unsigned L = (unsigned)cnt * (unsigned)S;
   const int units = tile_units(cnt, h.n_obs);
+  // a unit lane's pose, its frame and upper bound; the first unit's are read
+  // while the tile is still being staged, each next one at the end of a unit
+  long long pn = -1;
+  float4 qn = make_float4(0.f, 0.f, 1.f, 0.f);
+  float ubn = -kInf;
+  auto fetch = [&](int j) {
+    const unsigned l = (unsigned)j * kListThreads + threadIdx.x;
+    pn = -1;
+    if (j < units && l < L) pn = __ldcg(list + (long long)t * P + l / (unsigned)S);
+    if (pn >= 0) {
+      qn = __ldcg(pose4 + pn);
+      ubn = __ldcg(ub + pn);
+    }
+  };
+  fetch(j0);
   cp_async_wait_all();
   __syncthreads();
   const int4 *ob = reinterpret_cast<const int4 *>(tsm);
@@ -747,17 +763,15 @@ __global__ void __launch_bounds__(kListThreads)
   unsigned long long n_obs = 0, n_edge = 0;
   for (int j = j0; j < units; j += kTileCTAs) {
     const unsigned l = (unsigned)j * kListThreads + threadIdx.x;
-    long long p = -1;
-    if (l < L) p = __ldcg(list + (long long)t * P + l / (unsigned)S);
+    const long long p = pn;
     float px = 0.f, py = 0.f, c = 1.f, s = 0.f, thr = -kInf;
     int o0 = 0, o1 = 0;
     if (p >= 0) {
-      const float4 q4 = __ldcg(pose4 + p);
-      px = q4.x;
-      py = q4.y;
-      c = q4.z;
-      s = q4.w;
-      thr = ub_value(__ldcg(ub + p));
+      px = qn.x;
+      py = qn.y;
+      c = qn.z;
+      s = qn.w;
+      thr = ub_value(ubn);
       const int part = (int)(l % (unsigned)S);
       o0 = h.n_obs * part / S;  // n_obs <= 256 and part < S <= 256
       o1 = h.n_obs * (part + 1) / S;
@@ -765,20 +779,35 @@ __global__ void __launch_bounds__(kListThreads)
     int span = o1 - o0;
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, k));
+    // kFilt circle bounds at a time (independent), then their survivors
+    // appended in obstacle order; whole batches of 32 evaluated at once
     int nq = 0;
-    for (int k = 0; k < span; ++k) {
-      const int o = o0 + k;
-      const bool keep = o < o1 && !(circle_lb_value(circ[o], px, py, F.radius) > thr);
-      const unsigned mask = __ballot_sync(0xffffffffu, keep);
-      if (keep) qw[nq + __popc(mask & ((1u << lane) - 1u))] = (lane << 16) | o;
-      nq += __popc(mask);
-      if (nq >= 32) {  // uniform: a full batch
+    for (int k0 = 0; k0 < span; k0 += kFilt) {
+      bool keep[kFilt];
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        const int o = o0 + k0 + q;
+        keep[q] = false;
+        if (o < o1) keep[q] = !(circle_lb_value(circ[o], px, py, F.radius) > thr);
+      }
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        const unsigned mask = __ballot_sync(0xffffffffu, keep[q]);
+        if (keep[q]) qw[nq + __popc(mask & ((1u << lane) - 1u))] = (lane << 16) | (o0 + k0 + q);
+        nq += __popc(mask);
+      }
+      if (nq >= 32) {  // uniform: whole batches, the rest (< 32) moved to the front
         __syncwarp();
-        eval_items<M, SOFT>(F, prm, qw, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
+        int head = 0;
+        for (; nq - head >= 32; head += 32)
+          eval_items<M, SOFT>(F, prm, qw + head, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs,
+                              n_edge);
+        const int rest = nq - head;
+        const int v = lane < rest ? qw[head + lane] : 0;
         __syncwarp();
-        if (lane < nq - 32) qw[lane] = qw[32 + lane];
+        if (lane < rest) qw[lane] = v;
         __syncwarp();
-        nq -= 32;
+        nq = rest;
       }
     }
     if (nq > 0) {
@@ -786,6 +815,7 @@ __global__ void __launch_bounds__(kListThreads)
       eval_items<M, SOFT>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
     }
     __syncwarp();  // the queue is refilled by the next unit
+    fetch(j + kTileCTAs);
   }
   pdl_trigger();  // the epilogue may launch; it waits for this grid
   // evaluated obstacles and edges (the roofline's work count)
