@@ -217,15 +217,18 @@ struct MlpFrags {
 
 __device__ __forceinline__ void load_frags(const uint32_t *frag, int lane, MlpFrags &w)
 {
+  const uint2 *f2 = reinterpret_cast<const uint2 *>(frag);
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    w.b1[j][0] = frag[(j * 32 + lane) * 2];
-    w.b1[j][1] = frag[(j * 32 + lane) * 2 + 1];
+    const uint2 v = __ldg(f2 + j * 32 + lane);
+    w.b1[j][0] = v.x;
+    w.b1[j][1] = v.y;
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    w.b2[j][0] = frag[kFrag1Words + (j * 32 + lane) * 2];
-    w.b2[j][1] = frag[kFrag1Words + (j * 32 + lane) * 2 + 1];
+    const uint2 v = __ldg(f2 + kFrag1Words / 2 + j * 32 + lane);
+    w.b2[j][0] = v.x;
+    w.b2[j][1] = v.y;
   }
 }
 
@@ -419,6 +422,8 @@ __global__ void __launch_bounds__(kPoseThreads)
   float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
   int e0 = 0, e1 = 0;  // the cell's list, or all tiles (cell < 0)
   int cell = -1;
+  MlpFrags w;  // the network's weights (pose-invariant: read first)
+  if constexpr (NET) load_frags(frag, lane, w);
   if (valid) {
     px = poses[3 * p];
     py = poses[3 * p + 1];
@@ -479,15 +484,19 @@ __global__ void __launch_bounds__(kPoseThreads)
     // smallest bounds it looked at unless one lane held more than RL of them.
     int cand[R];
     int head = 0;
+    // tile headers of the candidates {blob_off, blob_bytes, n_obs, n_vtx}:
+    // with the network lane 4 g holds candidate g's of pose a (hda) and of
+    // pose b (hdb); without it lane r of a pose's half holds candidate r's
+    int4 hda = make_int4(0, 0, 0, 0), hdb = hda;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       unsigned mine = ~0u;
 #pragma unroll
       for (int i = 0; i < RL; ++i)
         if (i == head && id[i] >= 0) mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
-      unsigned key = mine;
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+      const unsigned k0 = __reduce_min_sync(0xffffffffu, half == 0 ? mine : ~0u);
+      const unsigned k1 = __reduce_min_sync(0xffffffffu, half == 1 ? mine : ~0u);
+      const unsigned key = half ? k1 : k0;
       const bool any = key != ~0u;
       cand[r] = any ? (int)(key & 0xffffu) : -1;
       if (any && key == mine) ++head;
@@ -497,22 +506,22 @@ __global__ void __launch_bounds__(kPoseThreads)
 #pragma unroll
         for (int r = 0; r < kPre; ++r) ct_s[warp][half][r] = cand[r];
       __syncwarp();
-      MlpFrags w;
-      load_frags(frag, lane, w);
       const int g = lane >> 2, q = lane & 3;
       const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
       float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
       float efa = 0.f, efb = 0.f;
       // the candidates' AABBs and edge fractions
       if (ta >= 0) {
+        hda = __ldg(reinterpret_cast<const int4 *>(tiles + ta));
         const float4 a4 = tile_aabb(tiles, ta);
         aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
-        efa = (float)__ldg(&tiles[ta].n_vtx) * (1.f / 256.f);
+        efa = (float)hda.w * (1.f / 256.f);
       }
       if (tb >= 0) {
+        hdb = __ldg(reinterpret_cast<const int4 *>(tiles + tb));
         const float4 a4 = tile_aabb(tiles, tb);
         abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
-        efb = (float)__ldg(&tiles[tb].n_vtx) * (1.f / 256.f);
+        efb = (float)hdb.w * (1.f / 256.f);
       }
       // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
       const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
@@ -537,7 +546,10 @@ __global__ void __launch_bounds__(kPoseThreads)
         if (cand[i] >= 0) topk_insert<K>(bs, best, sc_s[warp][half][i], cand[i]);
     } else {
 #pragma unroll
-      for (int i = 0; i < K; ++i) best[i] = cand[i];
+      for (int i = 0; i < K; ++i) {
+        best[i] = cand[i];
+        if (hl == i && cand[i] >= 0) hda = __ldg(reinterpret_cast<const int4 *>(tiles + cand[i]));
+      }
     }
     // the per-tile counts and the counters are cleared by the kernel before
     // this one: wait for it before the first append
@@ -560,8 +572,26 @@ __global__ void __launch_bounds__(kPoseThreads)
     // lanes, four circles a lane per round, their loads issued together)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
+      // the proposed tile's header from the lane that read it
+      int src = (half << 4) + i;
+      if constexpr (NET) {
+        int r = 0;
+#pragma unroll
+        for (int q = 0; q < kPre; ++q)
+          if (cand[q] == best[i]) r = q;
+        src = 4 * r;
+      }
+      int4 h;
+      h.x = __shfl_sync(0xffffffffu, hda.x, src);
+      h.y = __shfl_sync(0xffffffffu, hda.y, src);
+      h.z = __shfl_sync(0xffffffffu, hda.z, src);
+      if constexpr (NET) {
+        const int bx = __shfl_sync(0xffffffffu, hdb.x, src);
+        const int by = __shfl_sync(0xffffffffu, hdb.y, src);
+        const int bz = __shfl_sync(0xffffffffu, hdb.z, src);
+        if (half) h = make_int4(bx, by, bz, 0);
+      }
       if (best[i] < 0) continue;  // uniform over the pose's lanes
-      const int4 h = __ldg(reinterpret_cast<const int4 *>(tiles + best[i]));
       const float4 *circ = reinterpret_cast<const float4 *>(blob + h.x + h.y);
       for (int o = hl; o < h.z; o += 64) {
         float4 cc[4];
@@ -576,8 +606,12 @@ __global__ void __launch_bounds__(kPoseThreads)
           }
       }
     }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) ubp = fminf(ubp, __shfl_xor_sync(0xffffffffu, ubp, o));
+    {  // 16-lane minimum (ubp >= 0, so its bits order like the value)
+      const unsigned u = __float_as_uint(ubp);
+      const unsigned u0 = __reduce_min_sync(0xffffffffu, half == 0 ? u : ~0u);
+      const unsigned u1 = __reduce_min_sync(0xffffffffu, half == 1 ? u : ~0u);
+      ubp = __uint_as_float(half ? u1 : u0);
+    }
     ubp += ub_pad;  // soft minimum: a penetrating obstacle's value reaches up to log(K) / eta
     if (valid && hl == 0) ub_out[p] = ubp;
   }
