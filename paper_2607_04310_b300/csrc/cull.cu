@@ -13,7 +13,7 @@
 //                      tile whose lower bound does not exceed UB (the cell's
 //                      list holds them all when UB's reach is within the
 //                      cell's; else every tile is tested)
-//   2. eval_lists      two CTAs per tile, launched while the proposals finish:
+//   2. eval_lists      two CTAs per tile, launched as the proposals start:
 //                      the tile's blob staged in shared memory, then the
 //                      tile's lanes = (pose, obstacle range) pairs in units of
 //                      128 so that warps stay full; an obstacle whose circle
@@ -417,6 +417,9 @@ __global__ void __launch_bounds__(kPoseThreads)
   const int half = lane >> 4, hl = lane & 15;
   const long long p = pw + half;
   const bool valid = p < P;
+  // the evaluation kernel may launch at once: its CTAs stage their tiles
+  // while the proposals run, and wait for this grid before reading its lists
+  pdl_trigger();
   if (threadIdx.x == 0) s_prop = s_fb = s_fbp = s_bound = s_circ = 0;
   unsigned n_bound = 0, n_circ = 0;  // this lane's tile bounds and circles
   float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
@@ -679,7 +682,6 @@ __global__ void __launch_bounds__(kPoseThreads)
     atomicAdd(&ctr->n_bound[slot], (unsigned long long)s_bound);
     atomicAdd(&ctr->n_circ[slot], (unsigned long long)s_circ);
   }
-  pdl_trigger();  // the evaluation kernel may launch; it waits for this grid
 }
 
 // ---------------------------------------------------------------------------
