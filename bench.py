@@ -538,26 +538,37 @@ def run_b300(a, rank, world, local):
 
     # every library call launches on the current stream (None), so the same
     # step functions run eagerly or under CUDA-graph capture
+    # every step saves its backward records in the forward (the active pair's
+    # gradient rows, which the epilogue computes anyway) and scatters them
+    saved = torch.empty((P, psdf.SAVED_FLOATS), dtype=torch.float32, device=dev)
+
     def step_learned(ps=poses):
-        psdf.psdf_eval_culled(w.footprint, scene, mlp, learned, ps, prm, phi, dphi, act, cws)
-        psdf.psdf_backward(w.footprint, scene, ps, prm, act, gphi, gpose, gedges)
+        psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, ps, prm, phi, dphi, act,
+                                   saved, cws)
+        psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
+
+    def step_learned_recompute():
+        psdf.psdf_eval_culled(w.footprint, scene, mlp, learned, poses, prm, phi, dphi, act, cws)
+        psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges)
 
     def step_bound():
-        psdf.psdf_eval_culled(w.footprint, scene, None, bound, poses, prm, phi, dphi, act, cws)
-        psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges)
+        psdf.psdf_eval_culled_save(w.footprint, scene, None, bound, poses, prm, phi, dphi, act,
+                                   saved, cws)
+        psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
     def step_full():
-        psdf.psdf_eval_grad(w.footprint, scene, poses, prm, phi, dphi, act, ws)
-        psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges)
+        psdf.psdf_eval_grad_save(w.footprint, scene, poses, prm, phi, dphi, act, saved, ws)
+        psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
     # exactness in this run: learned cull vs full scan, every output bit
     step_full()
-    ref = (phi.clone(), dphi.clone(), act.clone())
+    ref = (phi.clone(), dphi.clone(), act.clone(), gpose.clone())
     step_learned()
     torch.cuda.synchronize()
     exact = bool(torch.equal(ref[0].view(torch.int32), phi.view(torch.int32)) and
                  torch.equal(ref[1].view(torch.int32), dphi.view(torch.int32)) and
-                 torch.equal(ref[2], act))
+                 torch.equal(ref[2], act) and
+                 torch.equal(ref[3].view(torch.int32), gpose.view(torch.int32)))
     for _ in range(max(a.warmup, 3)):
         step_learned()
     torch.cuda.synchronize()
@@ -597,6 +608,10 @@ def run_b300(a, rank, world, local):
         replay_bound()
     bound_ms = sum(_time_steps(replay_bound, a.steps, flush, stream)) / a.steps
     st_bound = psdf.psdf_cull_stats_read(cws, stream)
+    replay_rec, g_rec = _graph(step_learned_recompute)
+    for _ in range(3):
+        replay_rec()
+    recompute_ms = sum(_time_steps(replay_rec, a.steps, flush, stream)) / a.steps
     eager_ms = sum(_time_steps(step_learned, a.steps, flush, stream)) / a.steps
 
     # ---- end to end through the C ABI with host buffers ----------------------
@@ -611,14 +626,14 @@ def run_b300(a, rank, world, local):
             # poses in, the cull step, the result (phi, dphi, active) read
             # back on a side stream while the backward runs
             d_poses.copy_(h_poses, non_blocking=True)
-            psdf.psdf_eval_culled(w.footprint, scene, mlp, learned, d_poses, prm, phi, dphi, act,
-                                  cws)
+            psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, d_poses, prm, phi, dphi,
+                                       act, saved, cws)
             fwd_done = torch.cuda.Event()
             fwd_done.record()
             side.wait_event(fwd_done)
             with torch.cuda.stream(side):
                 h_out.copy_(out, non_blocking=True)
-            psdf.psdf_backward(w.footprint, scene, d_poses, prm, act, gphi, gpose, gedges)
+            psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
             torch.cuda.current_stream().wait_stream(side)
 
         replay_e2e, g_e2e = _graph(e2e_step)
@@ -669,7 +684,8 @@ def run_b300(a, rank, world, local):
         "impl": "b300",
         "config": {"workload": WORKLOAD, "poses_per_gpu": P, "edges": w.E,
                    "obstacles": w.M, "tiles": T, "footprint_vertices": m,
-                   "path": "learned tile cull (k=%d) + pose gradient + backward" % CULL_K,
+                   "path": ("learned tile cull (k=%d) + pose gradient + backward (from the "
+                            "forward's saved rows)" % CULL_K),
                    "pair_count": "effective: poses x edges of the whole scene",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "speedup_vs_full_scan": full_ms / ms_step,
@@ -679,6 +695,11 @@ def run_b300(a, rank, world, local):
                       "roofline_frac": roofline.flops_per_pose(m, w.offsets) * P
                       / (full_ms / 1000.0) / 1e12 / peak,
                       "note": "scan + epilogue + backward, FP32 flops of every pair"},
+        "backward_recompute": {"value": pairs / (recompute_ms / 1000.0),
+                               "ms_per_step": recompute_ms,
+                               "note": "the same step through psdf_eval_culled + psdf_backward "
+                                       "(the backward recomputes the active pair's geometry "
+                                       "instead of reading the forward's saved rows)"},
         "bound_cull": {"value": pairs / (bound_ms / 1000.0), "ms_per_step": bound_ms,
                        "evaluated_fraction": (st_bound.proposed_items + st_bound.fallback_items) / (P * T),
                        "fallback_rate": st_bound.fallback_poses / P},

@@ -204,6 +204,36 @@ int psdf_backward(const float *footprint, int32_t m, const psdf_scene *scene,
                   const uint32_t *active, const float *grad_phi, float *grad_pose,
                   float *grad_edges, void *stream);
 
+/* ---- backward from records saved by the forward (hard minimum) -----------
+ * The forward's epilogue already takes the active pair's gradient (Alg. 1,
+ * value + gradient); these calls keep, per pose, what the backward above
+ * recomputes from the active pair id, so that the backward is a scale and a
+ * scatter.  Record layout, float saved[P][16] (DEVICE, 16-byte aligned,
+ * caller-owned, written by the forward, read by psdf_backward_saved):
+ *   0..2  d phi / d (x, y, theta), the dphi the forward writes
+ *   3     int32 bits: the count (0..3) of edge-endpoint rows below, or -1
+ *         when the pose has no gradient (no obstacle, or touching without
+ *         overlap on the active axis)
+ *   4 + 3i, 5 + 3i, 6 + 3i (i < 3): int32 bits of (caller edge row * 4 +
+ *         column), then d phi / d column, d phi / d (column + 1); column 0 is
+ *         (Ax, Ay), column 2 is (Bx, By), as in grad_edges
+ *   13..15 zero
+ * psdf_eval_grad_save / psdf_eval_culled_save: psdf_eval_grad /
+ * psdf_eval_culled plus the records (dphi and saved required); eta > 0 is
+ * rejected (PSDF_ERR_ARG: the soft backward touches every axis of the
+ * obstacle).  psdf_backward_saved: grad_pose and grad_edges exactly as
+ * psdf_backward computes them from the same forward (grad_pose bit for bit;
+ * grad_edges up to the order of its float atomics); rows outside the
+ * scene's 4 * rows_total columns are skipped.  All three are asynchronous
+ * on `stream` and allocate nothing (graph-capturable). */
+int psdf_eval_grad_save(const float *footprint, int32_t m, const psdf_scene *scene,
+                        const float *poses, int64_t P, const psdf_params *params, float *phi,
+                        float *dphi, uint32_t *active, float *saved, void *workspace,
+                        size_t workspace_bytes, void *stream);
+int psdf_backward_saved(const psdf_scene *scene, const float *saved, int64_t P,
+                        const float *grad_phi, float *grad_pose, float *grad_edges,
+                        void *stream);
+
 /* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
  * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
  * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
@@ -311,6 +341,13 @@ int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
                      const psdf_mlp *mlp, const psdf_cull_opts *opts, const float *poses,
                      int64_t P, const psdf_params *params, float *phi, float *dphi,
                      uint32_t *active, void *workspace, size_t workspace_bytes, void *stream);
+/* The same plus the saved backward records of psdf_backward_saved (see
+ * there; hard minimum only). */
+int psdf_eval_culled_save(const float *footprint, int32_t m, const psdf_scene *scene,
+                          const psdf_mlp *mlp, const psdf_cull_opts *opts, const float *poses,
+                          int64_t P, const psdf_params *params, float *phi, float *dphi,
+                          uint32_t *active, float *saved, void *workspace,
+                          size_t workspace_bytes, void *stream);
 
 /* Synchronizes `stream` and copies the counters of the last psdf_eval_culled
  * that used `workspace` (PSDF_ERR_TIMEOUT if it recorded a device failure). */

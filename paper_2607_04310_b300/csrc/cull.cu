@@ -1168,11 +1168,11 @@ extern "C" int psdf_tile_values(const float *footprint, int32_t m, const psdf_sc
   return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch");
 }
 
-extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
-                                const psdf_mlp *mlp, const psdf_cull_opts *opts,
-                                const float *poses, int64_t P, const psdf_params *params,
-                                float *phi, float *dphi, uint32_t *active, void *workspace,
-                                size_t workspace_bytes, void *stream)
+static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
+                       const psdf_mlp *mlp, const psdf_cull_opts *opts, const float *poses,
+                       int64_t P, const psdf_params *params, float *phi, float *dphi,
+                       uint32_t *active, float4 *saved, void *workspace, size_t workspace_bytes,
+                       void *stream)
 {
   int rc = check_eval_args(scene, poses, P, params, workspace ? workspace : (void *)256,
                            (size_t)-1);
@@ -1257,10 +1257,35 @@ extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_sc
       if (rc) return rc;
     }
   }
-  rc = launch_epilogue(F, scene, poses, P, pk, keys, &ctr->err, phi, dphi, active, st);
+  rc = launch_epilogue(F, scene, poses, P, pk, keys, &ctr->err, phi, dphi, active, st, saved);
   if (rc) return rc;
   e = cudaGetLastError();
   return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch");
+}
+
+extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
+                                const psdf_mlp *mlp, const psdf_cull_opts *opts,
+                                const float *poses, int64_t P, const psdf_params *params,
+                                float *phi, float *dphi, uint32_t *active, void *workspace,
+                                size_t workspace_bytes, void *stream)
+{
+  return eval_culled(footprint, m, scene, mlp, opts, poses, P, params, phi, dphi, active, nullptr,
+                     workspace, workspace_bytes, stream);
+}
+
+extern "C" int psdf_eval_culled_save(const float *footprint, int32_t m,
+                                     const psdf_scene *scene, const psdf_mlp *mlp,
+                                     const psdf_cull_opts *opts, const float *poses, int64_t P,
+                                     const psdf_params *params, float *phi, float *dphi,
+                                     uint32_t *active, float *saved, void *workspace,
+                                     size_t workspace_bytes, void *stream)
+{
+  if (P > 0 && !saved) return fail(PSDF_ERR_ARG, "saved is NULL");
+  if (params && params->eta > 0.f)
+    return fail(PSDF_ERR_ARG, "saved backward records need the hard minimum (eta <= 0)");
+  if (((uintptr_t)saved & 15u) != 0) return fail(PSDF_ERR_ARG, "saved must be 16-byte aligned");
+  return eval_culled(footprint, m, scene, mlp, opts, poses, P, params, phi, dphi, active,
+                     reinterpret_cast<float4 *>(saved), workspace, workspace_bytes, stream);
 }
 
 extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cull_stats *stats)

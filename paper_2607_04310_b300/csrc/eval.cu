@@ -165,8 +165,9 @@ inline int backward_spread_shift(long long P)
   return shift;
 }
 
-// Per-pose epilogue: value, active pair, optional pose gradient.
-template <int M, bool SOFT = false>
+// Per-pose epilogue: value, active pair, optional pose gradient; SAVE (hard
+// minimum) also writes the saved backward records.
+template <int M, bool SOFT = false, bool SAVE = false>
 __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const float *__restrict__ poses, long long P,
                                 const ObsRec *__restrict__ row_obs,
@@ -174,7 +175,8 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
                                 const unsigned long long *__restrict__ keys,
                                 const int *__restrict__ err, float *__restrict__ phi,
                                 float *__restrict__ dphi, unsigned *__restrict__ active,
-                                float *__restrict__ stage, float d_min)
+                                float *__restrict__ stage, float d_min,
+                                float4 *__restrict__ saved)
 {
   // the pose (an input of the call, not an output of the kernel before) is
   // read before the wait
@@ -189,7 +191,7 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
   }
   pdl_wait();
   pdl_trigger();  // a following backward may launch now; it waits for this grid
-  const bool want_grad = dphi != nullptr || stage != nullptr;
+  const bool want_grad = SAVE || dphi != nullptr || stage != nullptr;
   if constexpr (SOFT) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -209,14 +211,19 @@ __global__ void epilogue_kernel(FootprintK F, ParamsK prm, float eps_axis,
     const int g = (int)(threadIdx.x % kEpiLanes);
     const bool valid = p < P;
     PoseOut r;
+    Grad rows;
+    rows.nrow = -1;
     if (*err) {
       r = pose_out_failed();
     } else {
       r = epilogue_pose_coop<M, kEpiLanes>(F, prm.eps_sat, eps_axis, px, py, th,
                                            valid ? keys[p] : ~0ull, row_obs, vtx, far,
-                                           want_grad, g);
+                                           want_grad, g, SAVE ? &rows : nullptr);
     }
-    if (valid && g == 0) write_pose_out(r, p, phi, dphi, active, stage, d_min);
+    if (valid && g == 0) {
+      write_pose_out(r, p, phi, dphi, active, stage, d_min);
+      if constexpr (SAVE) write_saved(saved, p, rows);
+    }
   }
 }
 
@@ -288,6 +295,46 @@ __global__ void backward_kernel(FootprintK F, ParamsK prm, float eps_axis,
       if (i >= g.nrow) break;
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i]], gphi * g.gx[i]);
       atomicAdd(&grad_edges[4 * (long long)g.row[i] + g.col[i] + 1], gphi * g.gy[i]);
+    }
+  }
+}
+
+// Backward from the forward's saved records (psdf_backward_saved): the pose
+// gradient and the edge-endpoint rows scaled by the incoming gradient, the
+// same products the recomputing backward forms.  One thread per pose; a row
+// whose two columns do not both lie in [0, 4 rows_total) is skipped.
+__global__ void backward_saved_kernel(const float4 *__restrict__ saved, long long P,
+                                      long long rows_total, const float *__restrict__ grad_phi,
+                                      float *__restrict__ grad_pose,
+                                      float *__restrict__ grad_edges)
+{
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();  // the records may come from the epilogue just before
+  if (p >= P) return;
+  const float gphi = grad_phi[p];
+  float w[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = saved[4 * p + q];
+    w[4 * q] = v.x;
+    w[4 * q + 1] = v.y;
+    w[4 * q + 2] = v.z;
+    w[4 * q + 3] = v.w;
+  }
+  const int nrow = __float_as_int(w[3]);
+  const bool has = nrow >= 0;
+  if (grad_pose) {
+    grad_pose[3 * p] = has ? gphi * w[0] : 0.f;
+    grad_pose[3 * p + 1] = has ? gphi * w[1] : 0.f;
+    grad_pose[3 * p + 2] = has ? gphi * w[2] : 0.f;
+  }
+  if (!grad_edges) return;
+#pragma unroll
+  for (int i = 0; i < kGradRows; ++i) {
+    const int idx = __float_as_int(w[4 + 3 * i]);
+    if (i < nrow && idx >= 0 && idx + 1 < 4 * rows_total) {
+      atomicAdd(&grad_edges[idx], gphi * w[5 + 3 * i]);
+      atomicAdd(&grad_edges[idx + 1], gphi * w[6 + 3 * i]);
     }
   }
 }
@@ -443,12 +490,14 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     ProfileScope prof("epilogue", st);
     const bool soft = pk.eta > 0.f;
     // behind the scan: its CTAs are resident when the scan completes
-    cudaError_t le = launch_pdl(soft ? epilogue_kernel<M, true> : epilogue_kernel<M, false>,
+    cudaError_t le = launch_pdl(soft       ? epilogue_kernel<M, true>
+                                : so.saved ? epilogue_kernel<M, false, true>
+                                           : epilogue_kernel<M, false>,
                                 epilogue_blocks(P, soft), epilogue_threads(soft), 0, st, F, pk,
                                 sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                                 (const float4 *)sc->d_vtx, (const int *)sc->d_far,
                                 (const unsigned long long *)keys, (const int *)err, phi, dphi,
-                                active, so.stage, so.d_min);
+                                active, so.stage, so.d_min, so.saved);
     if (le != cudaSuccess) return cuda_fail(le, "kernel launch (epilogue)");
   }
   cudaError_t e = cudaGetLastError();
@@ -520,16 +569,18 @@ template <int M>
 struct EpilogueCall {
   static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                  const ParamsK &pk, const unsigned long long *keys, const int *err, float *phi,
-                 float *dphi, unsigned *active, cudaStream_t st)
+                 float *dphi, unsigned *active, float4 *saved, cudaStream_t st)
   {
     ProfileScope prof("epilogue", st);
     // after the cull's evaluation kernel: may start while it finishes
     const bool soft = pk.eta > 0.f;
-    cudaError_t e = launch_pdl(soft ? epilogue_kernel<M, true> : epilogue_kernel<M, false>,
+    cudaError_t e = launch_pdl(soft    ? epilogue_kernel<M, true>
+                               : saved ? epilogue_kernel<M, false, true>
+                                       : epilogue_kernel<M, false>,
                                epilogue_blocks(P, soft), epilogue_threads(soft), 0, st, F, pk,
                                sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
                                (const float4 *)sc->d_vtx, (const int *)sc->d_far, keys, err,
-                               phi, dphi, active, (float *)nullptr, 0.f);
+                               phi, dphi, active, (float *)nullptr, 0.f, saved);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PSDF_OK;
@@ -548,9 +599,10 @@ struct BackwardCall {
 
 int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                     const ParamsK &pk, const unsigned long long *keys, const int *err,
-                    float *phi, float *dphi, unsigned *active, cudaStream_t st)
+                    float *phi, float *dphi, unsigned *active, cudaStream_t st, float4 *saved)
 {
-  return dispatch_m<EpilogueCall>(F.m, F, sc, poses, P, pk, keys, err, phi, dphi, active, st);
+  return dispatch_m<EpilogueCall>(F.m, F, sc, poses, P, pk, keys, err, phi, dphi, active, saved,
+                                  st);
 }
 
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
@@ -588,6 +640,41 @@ extern "C" int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scen
   if (P > 0 && !dphi) return fail(PSDF_ERR_ARG, "dphi is NULL");
   return eval_common(footprint, m, scene, poses, P, params, phi, dphi, active, workspace,
                      workspace_bytes, stream);
+}
+
+extern "C" int psdf_eval_grad_save(const float *footprint, int32_t m, const psdf_scene *scene,
+                                   const float *poses, int64_t P, const psdf_params *params,
+                                   float *phi, float *dphi, uint32_t *active, float *saved,
+                                   void *workspace, size_t workspace_bytes, void *stream)
+{
+  if (P > 0 && (!dphi || !saved)) return fail(PSDF_ERR_ARG, "dphi or saved is NULL");
+  if (params && params->eta > 0.f)
+    return fail(PSDF_ERR_ARG, "saved backward records need the hard minimum (eta <= 0)");
+  if (((uintptr_t)saved & 15u) != 0) return fail(PSDF_ERR_ARG, "saved must be 16-byte aligned");
+  StageOut so;
+  so.saved = reinterpret_cast<float4 *>(saved);
+  return eval_common(footprint, m, scene, poses, P, params, phi, dphi, active, workspace,
+                     workspace_bytes, stream, so);
+}
+
+extern "C" int psdf_backward_saved(const psdf_scene *scene, const float *saved, int64_t P,
+                                   const float *grad_phi, float *grad_pose, float *grad_edges,
+                                   void *stream)
+{
+  if (!scene) return fail(PSDF_ERR_ARG, "scene is NULL");
+  if (P < 0) return fail(PSDF_ERR_ARG, "P < 0");
+  if (P == 0) return PSDF_OK;
+  if (!saved || !grad_phi) return fail(PSDF_ERR_ARG, "saved or grad_phi is NULL");
+  if (((uintptr_t)saved & 15u) != 0) return fail(PSDF_ERR_ARG, "saved must be 16-byte aligned");
+  const unsigned blocks = (unsigned)((P + 127) / 128);
+  ProfileScope prof("backward", (cudaStream_t)stream);
+  // usually follows an epilogue on the stream: may start while it finishes
+  cudaError_t e = launch_pdl(backward_saved_kernel, dim3(blocks), dim3(128), 0,
+                             (cudaStream_t)stream, reinterpret_cast<const float4 *>(saved),
+                             (long long)P, (long long)scene->rows_total, grad_phi, grad_pose,
+                             grad_edges);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (backward_saved)");
 }
 
 extern "C" int psdf_stage_params(const float *footprint, int32_t m, const psdf_scene *scene,

@@ -1124,9 +1124,11 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
                                                       const ObsRec *__restrict__ row_obs,
                                                       const float4 *__restrict__ vtx,
                                                       const int *__restrict__ far,
-                                                      bool want_grad, int g)
+                                                      bool want_grad, int g,
+                                                      Grad *rows = nullptr)
 {
   PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
+  if (rows) rows->nrow = -1;  // no gradient
   const bool none = key == ~0ull;
   ObsRec o{0, 0, 0, 0};
   if (!none) o = row_obs[(int)(unsigned)(key & 0xffffffffu)];
@@ -1143,8 +1145,33 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
     r.g[0] = gr.gp[0];
     r.g[1] = gr.gp[1];
     r.g[2] = gr.gp[2];
+    if (rows) *rows = gr;
   }
   return r;
+}
+
+// Saved backward record of one pose (psdf_saved_grad, 4 float4): the pose
+// gradient of the active pair, its edge-endpoint rows (caller row * 4 +
+// column, d/dx, d/dy), their count, or -1 when the pose has no gradient.
+__device__ __forceinline__ void write_saved(float4 *saved, long long p, const Grad &g)
+{
+  float w[16];
+  w[0] = g.gp[0];
+  w[1] = g.gp[1];
+  w[2] = g.gp[2];
+  w[3] = __int_as_float(g.nrow);
+#pragma unroll
+  for (int i = 0; i < kGradRows; ++i) {
+    const bool on = i < g.nrow;
+    w[4 + 3 * i] = __int_as_float(on ? 4 * g.row[i] + g.col[i] : -1);
+    w[5 + 3 * i] = on ? g.gx[i] : 0.f;
+    w[6 + 3 * i] = on ? g.gy[i] : 0.f;
+  }
+  w[13] = w[14] = w[15] = 0.f;
+  if (g.nrow < 0) w[0] = w[1] = w[2] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    saved[4 * p + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
 // Soft-minimum backward of one pose: when its active pair names a

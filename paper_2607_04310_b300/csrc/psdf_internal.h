@@ -174,6 +174,7 @@ int dev_upload(T **dst, const std::vector<T> &src, cudaStream_t st, size_t *byte
 struct StageOut {
   float *stage = nullptr;
   float d_min = 0.f;
+  float4 *saved = nullptr;  // saved backward records (psdf_saved_grad), hard minimum
 };
 
 // Launch with programmatic stream serialization (see pdl_wait in
@@ -205,7 +206,8 @@ int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
 // per-pose epilogue (value, active pair, optional gradient) from 64-bit keys
 int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                     const ParamsK &pk, const unsigned long long *keys, const int *err,
-                    float *phi, float *dphi, unsigned *active, cudaStream_t st);
+                    float *phi, float *dphi, unsigned *active, cudaStream_t st,
+                    float4 *saved = nullptr);
 // value (+ gradient if dphi) evaluation with a given workspace (eval.cu)
 int eval_common(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
                 int64_t P, const psdf_params *params, float *phi, float *dphi, unsigned *active,

@@ -91,6 +91,9 @@ _SIGS = {
                                       _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_backward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                      _vp, _vp, _vp, _vp]),
+    "psdf_eval_grad_save": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                           _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "psdf_backward_saved": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "psdf_stage_params": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                          ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_stage_params_batched": (ctypes.c_int, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
@@ -110,6 +113,9 @@ _SIGS = {
     "psdf_eval_culled": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                         ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_size_t, _vp]),
+    "psdf_eval_culled_save": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                             ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                             ctypes.c_size_t, _vp]),
     "psdf_cull_stats_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "psdf_trainer_create": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float,
                                            ctypes.POINTER(_vp)]),
@@ -306,6 +312,27 @@ def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, ac
                                 _stream(stream)))
 
 
+# floats per pose of a saved backward record (psdf_eval_grad_save,
+# psdf_eval_culled_save -> psdf_backward_saved)
+SAVED_FLOATS = 16
+
+
+def psdf_eval_grad_save(footprint: np.ndarray, scene: Scene, poses, params: Params, phi, dphi,
+                        active, saved, workspace, stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval_grad_save(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                      poses.shape[0], ctypes.byref(params), _ptr(phi),
+                                      _ptr(dphi), _ptr(active), _ptr(saved), _ptr(workspace),
+                                      workspace.numel(), _stream(stream)))
+
+
+def psdf_backward_saved(scene: Scene, saved, grad_phi, grad_pose, grad_edges,
+                        stream=None) -> None:
+    _check(load().psdf_backward_saved(scene.handle, _ptr(saved), saved.shape[0],
+                                      _ptr(grad_phi), _ptr(grad_pose), _ptr(grad_edges),
+                                      _stream(stream)))
+
+
 NOALLOC_MAX_POSES = 262144
 PROPOSE_BOUND = 1
 PROPOSE_MLP = 2
@@ -382,6 +409,18 @@ def psdf_eval_culled(footprint, scene: Scene, mlp: Optional[Mlp], opts: CullOpts
                                    _ptr(poses), poses.shape[0], ctypes.byref(params), _ptr(phi),
                                    _ptr(dphi), _ptr(active), _ptr(workspace), workspace.numel(),
                                    _stream(stream)))
+
+
+def psdf_eval_culled_save(footprint, scene: Scene, mlp: Optional[Mlp], opts: CullOpts, poses,
+                          params: Params, phi, dphi, active, saved, workspace,
+                          stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval_culled_save(_ptr(fp), fp.shape[0], scene.handle,
+                                        mlp.handle if mlp is not None else None,
+                                        ctypes.byref(opts), _ptr(poses), poses.shape[0],
+                                        ctypes.byref(params), _ptr(phi), _ptr(dphi),
+                                        _ptr(active), _ptr(saved), _ptr(workspace),
+                                        workspace.numel(), _stream(stream)))
 
 
 def psdf_cull_stats_read(workspace, stream=None) -> CullStats:
