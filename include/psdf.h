@@ -17,7 +17,12 @@
  *    Sec. IV-A.1).  The library copies it by value into every launch.
  *  - Poses and all per-pose outputs are DEVICE pointers owned by the caller:
  *    poses float[P][3] = (px, py, theta); phi float[P]; dphi float[P][3];
- *    active uint32[P].  The library never allocates caller outputs.
+ *    active uint32[P].  The library never allocates caller outputs.  Pinned
+ *    host memory mapped into the device's address space at the same address
+ *    (cudaHostAlloc / cudaMallocHost with unified addressing) is accepted as
+ *    well: the kernels then read the poses and write the outputs across the
+ *    host link themselves, with no copy call (zero-copy).  Any other host
+ *    pointer for the poses is rejected (PSDF_ERR_ARG).
  *  - Every evaluation call is asynchronous on `stream` (a cudaStream_t passed
  *    as void*, NULL = the legacy default stream); nothing is read back to the
  *    host and no device memory is allocated, so calls can be captured in a

@@ -441,10 +441,13 @@ int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
     if (ws_bytes < psdf_workspace_bytes(P))
       return fail(PSDF_ERR_CAPACITY, "workspace smaller than psdf_workspace_bytes(P)");
   }
+  // device memory, managed memory, or pinned host memory mapped into the
+  // device's address space at the same address (read across the host link)
   cudaPointerAttributes attr;
   if (P > 0 && cudaPointerGetAttributes(&attr, poses) == cudaSuccess &&
-      attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
-    return fail(PSDF_ERR_ARG, "poses must be a device pointer");
+      attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged &&
+      !(attr.type == cudaMemoryTypeHost && attr.devicePointer == (const void *)poses))
+    return fail(PSDF_ERR_ARG, "poses must be device memory or device-mapped pinned host memory");
   cudaGetLastError();
   return PSDF_OK;
 }

@@ -182,3 +182,33 @@ def test_saved_rows_outside_the_scene_are_skipped():
     assert np.all(g[w.E] == 0)
     assert g[0, 0] == 1.0 and g[0, 1] == 1.0
     assert np.count_nonzero(g) == 2
+
+
+def test_zero_copy_host_buffers_equal_device_buffers():
+    """Poses read and outputs written by the kernels in pinned, device-mapped
+    host memory give the device-buffer results bit for bit; pageable host
+    poses stay rejected."""
+    w = sg.dense_clutter(4, n_rects=4000, n_poses=1024, field_side=80.0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=32)
+    P = w.P
+    poses = torch.as_tensor(w.poses, device=DEV)
+    _, dphi0, act0, saved0 = _forward_save(w, scene, poses)
+    phi0 = psdf.eval_grad(scene, w.footprint, poses)[0]
+    h_poses = torch.as_tensor(w.poses).pin_memory()
+    h_phi = torch.empty(P).pin_memory()
+    h_dphi = torch.empty((P, 3)).pin_memory()
+    h_act = torch.empty(P, dtype=torch.int32).pin_memory()
+    saved = torch.empty((P, psdf.SAVED_FLOATS), device=DEV)
+    ws = torch.empty(psdf.psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8, device=DEV)
+    psdf.psdf_eval_culled_save(w.footprint, scene, None, psdf.CullOpts(psdf.PROPOSE_BOUND, 2),
+                               h_poses, scene.params, h_phi, h_dphi, h_act, saved, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(h_phi.numpy().view(np.uint32), _bits(phi0))
+    assert np.array_equal(h_dphi.numpy().view(np.uint32), _bits(dphi0))
+    assert np.array_equal(h_act.numpy(), act0.cpu().numpy())
+    assert np.array_equal(_bits(saved), _bits(saved0))
+    with pytest.raises(psdf.PsdfError) as ei:  # pageable host poses
+        psdf.psdf_eval_culled_save(w.footprint, scene, None, psdf.CullOpts(psdf.PROPOSE_BOUND, 2),
+                                   torch.as_tensor(w.poses), scene.params, h_phi, h_dphi, h_act,
+                                   saved, ws)
+    assert ei.value.code == psdf.PSDF_ERR_ARG
