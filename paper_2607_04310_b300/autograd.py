@@ -3,9 +3,11 @@
     phi = psdf_phi(poses, edges, scene, footprint)      # [P]
     phi.sum().backward()  ->  poses.grad [P, 3], edges.grad [E, 4]
 
-Forward runs psdf_eval_grad; backward runs the hand-written psdf_backward
-kernel through the active pair of each pose (the active-branch subgradient
-of Sec. IV-D).  `edges` is the caller's [rows, 4] tensor whose values the
+Forward runs psdf_eval_grad_save (the hard minimum: the active pair's
+gradient rows are kept per pose) and backward psdf_backward_saved, which
+scales and scatters them; with the soft minimum forward runs psdf_eval_grad
+and backward the recomputing psdf_backward kernel.  Both give the
+active-branch subgradient of Sec. IV-D.  `edges` is the caller's [rows, 4] tensor whose values the
 scene was built from; it only carries the gradient (its values are read
 from the scene).  A closed polygon's vertex gradient is reported in its A
 slot, its B slots receive zero.
@@ -28,25 +30,37 @@ class PSDFFunction(torch.autograd.Function):
             raise TypeError("poses must be a float32 CUDA tensor [P, 3]")
         poses_c = poses.detach().contiguous()
         prm = params or scene.params
-        phi, dphi, act = psdf.eval_grad(scene, footprint, poses_c, params=prm, grad=True)
         ctx.scene = scene
         ctx.footprint = footprint
         ctx.params = prm
         ctx.n_rows = scene.n_rows
-        ctx.save_for_backward(poses_c, act)
+        if prm.eta > 0:
+            phi, dphi, act = psdf.eval_grad(scene, footprint, poses_c, params=prm, grad=True)
+            ctx.save_for_backward(poses_c, act, None)
+        else:
+            P = poses_c.shape[0]
+            phi = torch.empty(P, dtype=torch.float32, device=poses.device)
+            dphi = torch.empty((P, 3), dtype=torch.float32, device=poses.device)
+            act = torch.empty(P, dtype=torch.int32, device=poses.device)
+            saved = torch.empty((P, psdf.SAVED_FLOATS), dtype=torch.float32, device=poses.device)
+            psdf.psdf_eval_grad_save(footprint, scene, poses_c, prm, phi, dphi, act, saved,
+                                     psdf.workspace(P, poses.device))
+            ctx.save_for_backward(poses_c, act, saved)
         ctx.mark_non_differentiable(act)
         return phi, dphi, act
 
     @staticmethod
     def backward(ctx, grad_phi, _grad_dphi, _grad_act):
-        poses, act = ctx.saved_tensors
+        poses, act, saved = ctx.saved_tensors
         grad_phi = grad_phi.contiguous().float()
         need_pose = ctx.needs_input_grad[0]
         need_edges = ctx.needs_input_grad[1]
         gpose = torch.empty_like(poses) if need_pose else None
         gedges = (torch.zeros((ctx.n_rows, 4), dtype=torch.float32, device=poses.device)
                   if need_edges else None)
-        if need_pose or need_edges:
+        if (need_pose or need_edges) and saved is not None:
+            psdf.psdf_backward_saved(ctx.scene, saved, grad_phi, gpose, gedges)
+        elif need_pose or need_edges:
             psdf.psdf_backward(ctx.footprint, ctx.scene, poses, ctx.params, act, grad_phi,
                                gpose, gedges)
         return gpose, gedges, None, None, None

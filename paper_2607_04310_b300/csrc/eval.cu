@@ -669,10 +669,11 @@ extern "C" int psdf_backward_saved(const psdf_scene *scene, const float *saved, 
   if (P == 0) return PSDF_OK;
   if (!saved || !grad_phi) return fail(PSDF_ERR_ARG, "saved or grad_phi is NULL");
   if (((uintptr_t)saved & 15u) != 0) return fail(PSDF_ERR_ARG, "saved must be 16-byte aligned");
-  const unsigned blocks = (unsigned)((P + 127) / 128);
+  // one warp per CTA: the few thousand poses of a step spread over every SM
+  const unsigned blocks = (unsigned)((P + 31) / 32);
   ProfileScope prof("backward", (cudaStream_t)stream);
   // usually follows an epilogue on the stream: may start while it finishes
-  cudaError_t e = launch_pdl(backward_saved_kernel, dim3(blocks), dim3(128), 0,
+  cudaError_t e = launch_pdl(backward_saved_kernel, dim3(blocks), dim3(32), 0,
                              (cudaStream_t)stream, reinterpret_cast<const float4 *>(saved),
                              (long long)P, (long long)scene->rows_total, grad_phi, grad_pose,
                              grad_edges);

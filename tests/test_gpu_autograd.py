@@ -54,3 +54,32 @@ def test_autograd_pose_only():
     ref = oracle.psdf_eval(w.footprint, w.edges, w.offsets, w.poses)
     ok = (ref["margin"] >= 1e-3) & ((ref["phi"] < 0) | (ref["phi"] >= 1e-2))
     assert np.max(np.abs(p.grad.cpu().numpy()[ok] - ref["grad"][ok])) <= 1e-4
+
+
+def test_autograd_soft_minimum_matches_oracle():
+    """eta > 0: the wrapper's forward and recomputing backward against the
+    oracle's soft mode (the hard mode above goes through the saved rows)."""
+    from paper_2607_04310_b300 import psdf
+    from paper_2607_04310_b300.autograd import psdf_phi
+    g = sg.rng(19)
+    fp = sg.footprint_random_convex(g, 7, 0.3, 0.6, min_gap=0.3)
+    edges, offs = sg.convex_polygons(g, 60, 3, 8, 0.3, 1.0, 0.0, 15.0)
+    n = 600
+    idx = g.integers(0, len(edges), size=n)
+    poses = np.concatenate([edges[idx, 0:2] + g.normal(size=(n, 2)) * 0.3,
+                            g.uniform(-math.pi, math.pi, size=(n, 1))], axis=1).astype(np.float32)
+    eta = 200.0
+    ref = oracle.psdf_eval(fp, edges, offs, poses, eta=eta)
+    keep = (ref["egap"] >= 1e-3) & (ref["twin"] == oracle.PID_NONE) & \
+           ((ref["phi"] < 0) | (ref["phi"] >= 1e-2))
+    poses = poses[keep]
+    prm = psdf.make_params(eta=eta)
+    scene = psdf.Scene.from_csr(edges, offs, params=prm)
+    p = torch.tensor(poses, device="cuda", requires_grad=True)
+    wt = torch.tensor(g.normal(size=len(poses)), dtype=torch.float32, device="cuda")
+    phi = psdf_phi(p, None, scene, fp, prm)
+    (phi * wt).sum().backward()
+    rp, _ = oracle.psdf_backward(fp, edges, offs, poses, wt.double().cpu().numpy(), eta=eta)
+    assert np.sum(ref["phi"][keep] < 0) >= 20
+    assert np.max(np.abs(phi.detach().cpu().numpy() - ref["phi"][keep])) <= 1e-5
+    assert np.max(np.abs(p.grad.cpu().numpy() - rp)) <= 1e-4 * max(1.0, np.abs(rp).max())
