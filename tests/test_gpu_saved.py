@@ -212,3 +212,28 @@ def test_zero_copy_host_buffers_equal_device_buffers():
                                    torch.as_tensor(w.poses), scene.params, h_phi, h_dphi, h_act,
                                    saved, ws)
     assert ei.value.code == psdf.PSDF_ERR_ARG
+
+
+def test_zero_copy_full_scan_and_backward():
+    """The full scan with pinned, device-mapped host poses and outputs, then
+    the saved-row backward: the device-buffer results bit for bit."""
+    w = sg.octagon_lidar(1)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    P = w.P
+    poses = torch.as_tensor(w.poses, device=DEV)
+    phi0, dphi0, act0, saved0 = _forward_save(w, scene, poses)
+    h_poses = torch.as_tensor(w.poses).pin_memory()
+    h_phi = torch.empty(P).pin_memory()
+    h_dphi = torch.empty((P, 3)).pin_memory()
+    h_act = torch.empty(P, dtype=torch.int32).pin_memory()
+    saved = torch.empty((P, psdf.SAVED_FLOATS), device=DEV)
+    psdf.psdf_eval_grad_save(w.footprint, scene, h_poses, scene.params, h_phi, h_dphi, h_act,
+                             saved, psdf.workspace(P, poses.device))
+    gp = torch.empty((P, 3), device=DEV)
+    psdf.psdf_backward_saved(scene, saved, torch.ones(P, device=DEV), gp, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(h_phi.numpy().view(np.uint32), _bits(phi0))
+    assert np.array_equal(h_dphi.numpy().view(np.uint32), _bits(dphi0))
+    assert np.array_equal(h_act.numpy(), act0.cpu().numpy())
+    assert np.array_equal(_bits(saved), _bits(saved0))
+    assert np.array_equal(_bits(gp), _bits(dphi0))
