@@ -1135,6 +1135,8 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
   float s, c;
   sincosf(theta, &s, &c);
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
+  // the far-vertex indices the gradient reads, fetched while the detail runs
+  if (want_grad && g == 0 && !none) prefetch_lines(far + o.vtx_global, 4 * o.n);
   const Active a = obstacle_detail_coop<M, G>(F, px, py, c, s, vt, o.n, o.orig_first, eps_sat, g);
   if (none) return r;
   r.pid = a.pid;
