@@ -503,16 +503,37 @@ int psdf_backward_batched(const psdf_plan *plan, const float *poses, const uint3
  *    GPU that loads the library keeps it until the process exits.  P above
  *    the maximum is rejected with PSDF_ERR_CAPACITY.
  *  - The first call on a device looks up the array's device address (once,
- *    with that device current); make that first call before any stream
- *    capture.
+ *    with that device current, and again after the device's context was
+ *    replaced, e.g. by cudaDeviceReset); make that first call before any
+ *    stream capture.
  *  - Every call shares the one array: calls whose kernels overlap on the GPU
  *    (other streams, other threads) race and must be serialized by the
  *    caller.  Each call re-initializes the scratch it uses, so the previous
- *    call's contents never leak into its results. */
+ *    call's contents never leak into its results.
+ *  - The error word lives in the built-in array, which psdf_workspace_status
+ *    cannot read: a device-side wait that ran out shows only in the outputs
+ *    (phi = NaN, dphi = NaN, active = PSDF_PAIR_NONE for the affected
+ *    poses). */
 #define PSDF_NOALLOC_MAX_POSES 262144
 int psdf_eval_grad_noalloc(const float *footprint, int32_t m, const psdf_scene *scene,
                            const float *poses, int64_t P, const psdf_params *params, float *phi,
                            float *dphi, uint32_t *active, void *stream);
+
+/* ---- failure detection (for tests) ---------------------------------------
+ * The library has no counterpart in the paper here.  Its only device-side
+ * waits are the bounded mbarrier waits for the tile copies of the full scan
+ * (psdf_eval, psdf_eval_grad, psdf_stage_params, the no-allocation call) and
+ * of the batched plans; each gives up after `polls` polls (default 4194304,
+ * i.e. 1 << 22), records the failure (psdf_workspace_status /
+ * psdf_plan_status then report PSDF_ERR_TIMEOUT) and turns the affected
+ * poses' outputs into phi = NaN, dphi = NaN, active = PSDF_PAIR_NONE.  This
+ * sets the limit for every launch issued afterwards in the process (a CUDA
+ * graph keeps the limit it was captured with); 0 makes every such wait give
+ * up at once, which drives that path without any fault or hang: a kernel
+ * whose wait gave up still waits, with the default limit, for the copies it
+ * has issued before it exits.  The exact tile cull has no device-side wait.
+ * *previous (nullable) receives the limit that was in force. */
+int psdf_debug_set_wait_limit(uint32_t polls, uint32_t *previous);
 
 /* ---- tracing -----------------------------------------------------------
  * When enabled, the library brackets each launch of its kernels with CUDA

@@ -107,7 +107,7 @@ __device__ bool scan_item(const FootprintS &F, ParamsK prm, const float *__restr
                           const unsigned char *__restrict__ blob, int tile0, int ntile,
                           unsigned char *buf0, int blob_cap, uint64_t *bars, unsigned &phase,
                           float4 *spose, unsigned long long *skey, unsigned long long *keys,
-                          const PlanBounds &bnd)
+                          const PlanBounds &bnd, unsigned wait_polls)
 {
   if (ntile == 0) return true;
 #ifdef PSDF_DEBUG_CHECKS
@@ -151,7 +151,7 @@ __device__ bool scan_item(const FootprintS &F, ParamsK prm, const float *__restr
       }
       pending |= 1u << (b ^ 1);
     }
-    bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
+    bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, wait_polls);
     got = __syncthreads_and(got);
     if (!got) {
       ok = false;
@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
                    ParamsK prm, const float *__restrict__ poses,
                    const TileHdr *__restrict__ tiles,
                    const unsigned char *__restrict__ blob, int blob_cap,
-                   unsigned long long *keys, unsigned *ctr, PlanBounds bnd)
+                   unsigned long long *keys, unsigned *ctr, PlanBounds bnd,
+                   unsigned wait_polls)
 {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kPlanMaxThreads, 2)
 #define PSDF_SCAN_CASE(MM)                                                                    \
   case MM:                                                                                    \
     ok = scan_item<MM, SOFT>(Fv, prm, poses, B.pose0, B.npose, tiles, blob, I.tile0, I.ntile, \
-                       buf0, blob_cap, bars, phase, spose, skey, keys, bnd);                  \
+                       buf0, blob_cap, bars, phase, spose, skey, keys, bnd, wait_polls);      \
     break;
       PSDF_FOR_EACH_M(PSDF_SCAN_CASE)
 #undef PSDF_SCAN_CASE
@@ -606,7 +607,7 @@ int launch_batched(const psdf_plan *pl, const float *poses, float *phi, float *d
     (pl->eta > 0.f ? batched_kernel<true> : batched_kernel<false>)<<<pl->grid, pl->cfg.threads,
                                                                       pl->smem, st>>>(
         pl->d_items, pl->n_items, pl->d_blocks, pl->d_fprec, pk, poses, pl->d_tiles,
-        pl->d_blob, pl->blob_cap, pl->d_keys, pl->d_ctr, plan_bounds(pl));
+        pl->d_blob, pl->blob_cap, pl->d_keys, pl->d_ctr, plan_bounds(pl), wait_limit());
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch (batched)");
   }

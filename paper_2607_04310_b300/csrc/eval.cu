@@ -11,6 +11,7 @@
 // CTAs with one atomicMin per pose per CTA.  A per-pose epilogue re-derives
 // the active pair of the winning obstacle and its closed-form gradient.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -45,6 +46,9 @@ int cuda_fail(cudaError_t e, const char *what)
 
 constexpr int kScanThreads = 128;
 
+static std::atomic<unsigned> g_wait_limit{kWaitLimit};
+unsigned wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     FootprintK F, ParamsK prm, const float *__restrict__ poses, long long P, int npb,
     const TileHdr *__restrict__ tiles, const unsigned char *__restrict__ blob, int n_tiles,
     int tiles_per_chunk, int blob_cap, unsigned long long *__restrict__ keys,
-    int *__restrict__ err)
+    int *__restrict__ err, unsigned wait_polls)
 {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
       }
       pending |= 1u << (b ^ 1);
     }
-    bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
+    bool got = mbar_wait_bounded(&bars[b], (phase >> b) & 1u, wait_polls);
     got = __syncthreads_and(got);
     if (!got) {
       ok = false;
@@ -486,7 +490,7 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
     cudaError_t le = launch_pdl(pk.eta > 0.f ? scan_kernel<M, true> : scan_kernel<M, false>,
                                 grid, dim3(kScanThreads), smem, st, F, pk, poses, P, npb,
                                 (const TileHdr *)sc->d_tiles, (const unsigned char *)sc->d_blob,
-                                sc->n_tiles, (int)tpc, blob_cap, keys, err);
+                                sc->n_tiles, (int)tpc, blob_cap, keys, err, wait_limit());
     if (le != cudaSuccess) return cuda_fail(le, "kernel launch (scan)");
   }
   {
@@ -715,6 +719,13 @@ extern "C" int psdf_backward(const float *footprint, int32_t m, const psdf_scene
 extern "C" const char *psdf_last_error(void) { return g_err.c_str(); }
 
 extern "C" int psdf_version(void) { return 100; }
+
+extern "C" int psdf_debug_set_wait_limit(uint32_t polls, uint32_t *previous)
+{
+  const unsigned old = g_wait_limit.exchange(polls);
+  if (previous) *previous = old;
+  return PSDF_OK;
+}
 
 extern "C" size_t psdf_workspace_bytes(int64_t P)
 {

@@ -28,8 +28,44 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // context the address belongs to
 
-// Once per device, with that device current: the array's device address.
+// Identity of the context current on this thread (0 = none yet), from the
+// driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime's
+// entry-point query so that the library does not link the driver library.
+// Neither call allocates.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+unsigned long long current_context_id()
+{
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx) return 0;
+  if (get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// The array's device address on the current device: looked up once per
+// device (with that device current) and again whenever the device's context
+// is no longer the one the address was taken in (after cudaDeviceReset the
+// runtime makes a new primary context, and the old address is gone).
 int scratch_address(void **out)
 {
   int dev = 0;
@@ -38,11 +74,14 @@ int scratch_address(void **out)
   if (dev < 0 || dev >= kMaxDevices)
     return fail(PSDF_ERR_CAPACITY, "device index beyond the no-allocation table");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
     g_addr[dev] = p;
+    // the lookup made the device's primary context current if none was
+    g_ctx_id[dev] = id != 0 ? id : current_context_id();
   }
   *out = g_addr[dev];
   return PSDF_OK;

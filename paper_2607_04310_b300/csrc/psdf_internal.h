@@ -200,6 +200,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 
 // shared host helpers (eval.cu)
 int device_sms();
+// polls a bounded device-side wait makes before it gives up (kernel argument
+// of every kernel with such a wait; psdf_debug_set_wait_limit)
+unsigned wait_limit();
 int make_footprint(const float *fp, int m, float eps_seg, FootprintK *F);
 int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
                     const psdf_params *params, void *workspace, size_t ws_bytes);

@@ -62,10 +62,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
   return ok != 0;
 }
 
-// Bounded wait: false if the phase did not complete within kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+// Bounded wait: false if the phase did not complete within `limit` polls
+// (kWaitLimit unless the caller passes the launch's own limit; 0 gives up at
+// once).  A kernel whose wait gave up still drains its copies in flight with
+// the default limit before it exits.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
+                                                  unsigned limit = kWaitLimit)
 {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
+  for (unsigned it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

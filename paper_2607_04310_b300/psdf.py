@@ -138,6 +138,8 @@ _SIGS = {
     "psdf_plan_debug_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_int32)]),
     "psdf_backward_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "psdf_debug_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32,
+                                                 ctypes.POINTER(ctypes.c_uint32)]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -454,6 +456,18 @@ def psdf_eval_grad_noalloc(footprint: np.ndarray, scene: Scene, poses, params: P
     return int(load().psdf_eval_grad_noalloc(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
                                              poses.shape[0], ctypes.byref(params), _ptr(phi),
                                              _ptr(dphi), _ptr(active), _stream(stream)))
+
+
+DEFAULT_WAIT_LIMIT = 1 << 22
+
+
+def psdf_debug_set_wait_limit(polls: int) -> int:
+    """Polls every bounded device-side wait makes before it gives up, for
+    launches issued afterwards (0 = give up at once); returns the previous
+    limit."""
+    prev = ctypes.c_uint32()
+    _check(load().psdf_debug_set_wait_limit(int(polls), ctypes.byref(prev)))
+    return int(prev.value)
 
 
 def psdf_profile_enable(on: bool) -> None:

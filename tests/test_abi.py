@@ -97,3 +97,19 @@ def test_binding_fails_loudly_without_library(tmp_path):
             psdf.load(str(tmp_path / "missing.so"))
     finally:
         psdf._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/psdf.h that the binding mirrors (under
+    its own name or without the PSDF_ prefix) has the same value there."""
+    txt = open(os.path.join(ROOT, "include", "psdf.h")).read()
+    defs = dict(re.findall(r"#define\s+(PSDF_[A-Z0-9_]+)\s+(0x[0-9A-Fa-f]+|\d+)u?\b", txt))
+    assert "PSDF_NOALLOC_MAX_POSES" in defs and "PSDF_ERR_CAPACITY" in defs
+    mirrored = 0
+    for name, val in defs.items():
+        for py in (name, name[len("PSDF_"):]):
+            if hasattr(psdf, py):
+                assert getattr(psdf, py) == int(val, 0), (name, getattr(psdf, py), val)
+                mirrored += 1
+                break
+    assert hasattr(psdf, "NOALLOC_MAX_POSES") and mirrored >= 12, mirrored
