@@ -268,7 +268,11 @@ def _bench_batched(a, dev, flush, stream, peak):
     poses = torch.as_tensor(np.concatenate([w.poses for w in insts]), device=dev).contiguous()
     P = plan.n_poses
     pairs = float(sum(w.poses.shape[0] * w.edges.shape[0] for w in insts))
-    flops = float(sum(w.poses.shape[0] * roofline.flops_per_pose(w.footprint.shape[0], w.offsets)
+    flops_instr = float(sum(w.poses.shape[0] *
+                            roofline.flops_per_pose(w.footprint.shape[0], w.offsets)
+                            for w in insts))
+    flops = float(sum(roofline.flops_fixed(w.footprint.shape[0],
+                                           float(w.poses.shape[0]) * w.edges.shape[0])
                       for w in insts))
     cfg, _ = psdf.psdf_plan_autotune(plan, poses, reps=3)
     phi = torch.empty(P, device=dev)
@@ -337,7 +341,9 @@ def _bench_batched(a, dev, flush, stream, peak):
         "kernels_ms_per_step": {"persistent": kern_ms, "epilogue": e_ms / max(n_e, 1)},
         "roofline": {"bound": "alu", "kernel": "batched persistent kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "flops_per_step": flops},
+                     "frac": achieved / peak, "flops_per_step": flops,
+                     "flop_model": "F(m) = 40 m + 26 per (pose, edge) pair",
+                     "frac_instruction_count": flops_instr / (kern_ms / 1000.0) / 1e12 / peak},
     }
 
 
@@ -376,7 +382,8 @@ def _bench_scan_configs(dev, flush, stream, peak, steps: int = 20):
             replay()
         ms = float(np.median(_time_steps(replay, steps, flush, stream)))
         m = w.footprint.shape[0]
-        flops = roofline.flops_per_pose(m, w.offsets) * P
+        flops = roofline.flops_fixed(m, float(P) * w.E)
+        flops_instr = roofline.flops_per_pose(m, w.offsets) * P
         pairs = float(P) * w.E
         out[name] = {"workload": w.name, "poses": P, "edges": w.E, "footprint_vertices": m,
                      "path": "full scan + pose gradient" + (" + backward" if with_bwd else ""),
@@ -386,6 +393,9 @@ def _bench_scan_configs(dev, flush, stream, peak, steps: int = 20):
                                   "peak": peak, "unit": "TFLOP/s",
                                   "frac": flops / (ms / 1000.0) / 1e12 / peak,
                                   "flops_per_step": flops,
+                                  "flop_model": "F(m) = 40 m + 26 per (pose, edge) pair",
+                                  "frac_instruction_count":
+                                      flops_instr / (ms / 1000.0) / 1e12 / peak,
                                   "note": "whole step (scan, epilogue%s)"
                                           % (", backward" if with_bwd else "")}}
     return out
@@ -488,6 +498,24 @@ def _bench_table1(dev, reps: int = 200):
     return res
 
 
+def _fp32_peak(local: int):
+    """The FP32 roofline's denominator measured on this GPU: the library's
+    FMA microbenchmark (every SM full, 8 independent chains a thread), scalar
+    and paired FFMA (the faster counts), with the SM clock sampled meanwhile."""
+    from paper_2607_04310_b300 import psdf
+    with ClockSampler(local) as clk:
+        t_s, ms_s = psdf.psdf_measure_fp32_peak(False, iters=200000, reps=5)
+        t_p, ms_p = psdf.psdf_measure_fp32_peak(True, iters=200000, reps=5)
+    c = clk.summary()
+    kind = "paired" if t_p >= t_s else "scalar"
+    peak = max(t_s, t_p)
+    return {"peak": peak, "unit": "TFLOP/s", "scalar_ffma": t_s, "paired_ffma": t_p,
+            "clocks": c,
+            "source": "measured: the library's FP32 FMA microbenchmark (%s FFMA, best of 5 "
+                      "launches of about %.0f ms), median SM clock %s MHz"
+                      % (kind, ms_p if kind == "paired" else ms_s, c.get("sm_mhz"))}
+
+
 def run_b300(a, rank, world, local):
     import torch
     from paper_2607_04310_b300 import psdf, roofline
@@ -497,9 +525,7 @@ def run_b300(a, rank, world, local):
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-        props = torch.cuda.get_device_properties(dev)
-        peak = roofline.fp32_peak_tflops(props.multi_processor_count,
-                                         float(_measured_peaks().get("sm_max_mhz", 2032.0)))
+        peak = _fp32_peak(local)["peak"]
         print(json.dumps(_bench_batched(a, dev, flush, torch.cuda.current_stream(dev), peak)))
         return 0
 
@@ -510,6 +536,8 @@ def run_b300(a, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
+    fp32 = _fp32_peak(local)
+    peak = fp32["peak"]
     w = _workload(rank)
     m = w.footprint.shape[0]
     scene = psdf.Scene.from_csr(w.edges, w.offsets)
@@ -581,8 +609,7 @@ def run_b300(a, rank, world, local):
         step_learned()
     torch.cuda.synchronize()
     psdf.psdf_profile_enable(False)
-    prof = {k: psdf.psdf_profile_read(k) for k in
-            ("propose", "cull_eval", "epilogue", "backward")}
+    prof = {k: psdf.psdf_profile_read(k) for k in ("cull", "backward")}
     psdf.psdf_profile_reset()
     st = psdf.psdf_cull_stats_read(cws, stream)
 
@@ -676,29 +703,24 @@ def run_b300(a, rank, world, local):
             pg.destroy_process_group()
         return 0
 
-    # ---- rooflines of the step's kernels; the dominant (largest) one is reported
-    props = torch.cuda.get_device_properties(dev)
+    # ---- roofline of the step's dominant kernel (the fused cull) ----------
     peaks = _measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak = roofline.fp32_peak_tflops(props.multi_processor_count, sm_max)
-    items = int(st.proposed_items + st.fallback_items)
-    work = {
-        # the obstacles the cull evaluated exactly (circle-bound skips excluded)
-        "cull_eval": roofline.flops_evaluated(m, st.evaluated_edges, st.evaluated_obstacles),
-        # the tile bounds and obstacle circles the proposals computed (kernel counts)
-        "propose": roofline.flops_propose(st.bound_evaluations, st.circle_evaluations),
-    }
-    kroof = {}
-    for k, f in work.items():
-        n_k, k_ms = prof[k]
-        ach = f * a.steps / (k_ms / 1000.0) / 1e12  # prof covers a.steps eager steps
-        kroof[k] = {"flops_per_step": f, "avg_launch_ms": k_ms / max(n_k, 1),
-                    "achieved": ach, "frac": ach / peak}
-    dom = max(kroof, key=lambda k: kroof[k]["avg_launch_ms"])
-    kname = {"cull_eval": "eval_lists", "propose": "propose"}
     evaluated_pairs = float(st.evaluated_edges)  # pose x edge pairs evaluated exactly
-    # clear_words, propose, eval_lists, epilogue, backward
-    launches_per_step = 5
+    items = int(st.proposed_items + st.fallback_items)
+    n_k, k_ms = prof["cull"]
+    cull_ms = k_ms / max(n_k, 1)
+    # FP32 work: the evaluated pairs by the fixed per-pair count, plus the
+    # tile bounds and obstacle circles of the proposals
+    f_fixed = roofline.flops_fixed(m, evaluated_pairs) + roofline.flops_propose(
+        st.bound_evaluations, st.circle_evaluations)
+    f_instr = roofline.flops_evaluated(m, st.evaluated_edges, st.evaluated_obstacles) + \
+        roofline.flops_propose(st.bound_evaluations, st.circle_evaluations)
+    f_net = roofline.flops_network(8 * P)  # 8 candidates scored per pose
+    ach = f_fixed / (cull_ms / 1000.0) / 1e12
+    ach_instr = f_instr / (cull_ms / 1000.0) / 1e12
+    bf16 = float(peaks.get("bf16_tflops", 0.0)) or None
+    net_ach = f_net / (cull_ms / 1000.0) / 1e12
+    launches_per_step = 2  # cull_kernel, backward_saved_kernel
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -714,9 +736,12 @@ def run_b300(a, rank, world, local):
         "launch": "one CUDA graph per step (eager launches: %.4f ms/step)" % eager_ms,
         "exact_vs_full_scan": exact,
         "full_scan": {"value": pairs / (full_ms / 1000.0), "ms_per_step": full_ms,
-                      "roofline_frac": roofline.flops_per_pose(m, w.offsets) * P
-                      / (full_ms / 1000.0) / 1e12 / peak,
-                      "note": "scan + epilogue + backward, FP32 flops of every pair"},
+                      "roofline_frac": roofline.flops_fixed(m, float(P) * w.E)
+                      / (full_ms / 1000.0) / 1e12 / fp32["peak"],
+                      "roofline_frac_instruction_count": roofline.flops_per_pose(m, w.offsets) * P
+                      / (full_ms / 1000.0) / 1e12 / fp32["peak"],
+                      "note": "scan + epilogue + backward; FP32 flops of every pair (fixed "
+                              "count F(m) = 40 m + 26; instruction-level count beside it)"},
         "backward_recompute": {"value": pairs / (recompute_ms / 1000.0),
                                "ms_per_step": recompute_ms,
                                "note": "the same step through psdf_eval_culled + psdf_backward "
@@ -736,18 +761,26 @@ def run_b300(a, rank, world, local):
                  "circle_evaluations": int(st.circle_evaluations),
                  "evaluated_pair_evals_per_s": evaluated_pairs / (ms_step / 1000.0),
                  "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp")},
-        "roofline": {"bound": "alu", "kernel": kname[dom],
-                     "achieved": kroof[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
-                     "frac": kroof[dom]["frac"],
-                     "note": "latency-bound: the cull leaves a few thousand work items per step",
-                     "kernels": {kname[k]: v for k, v in kroof.items()},
-                     "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz "
-                                    "(max SM clock in MEASURED_PEAKS.json)"
-                                    % (props.multi_processor_count, sm_max),
-                     "flops_per_step": kroof[dom]["flops_per_step"],
-                     "avg_launch_ms": kroof[dom]["avg_launch_ms"],
-                     "traffic": _traffic(kname[dom], WORKLOAD)},
+        "roofline": {"bound": "alu", "kernel": "cull_kernel",
+                     "achieved": ach, "peak": fp32["peak"], "unit": "TFLOP/s",
+                     "frac": ach / fp32["peak"],
+                     "note": "latency-bound: a few thousand dependent chains of loads per step",
+                     "flop_model": "F(m) = 40 m + 26 per evaluated (pose, edge) pair, plus 7 "
+                                   "per tile bound and 10 per obstacle circle",
+                     "flops_per_step": f_fixed,
+                     "instruction_count": {"flops_per_step": f_instr, "achieved": ach_instr,
+                                           "frac": ach_instr / fp32["peak"],
+                                           "model": "14 + 30 m per edge + 2 m per obstacle"},
+                     "network_tensor": {"flops_per_step": f_net, "achieved": net_ach,
+                                        "peak": bf16, "frac": net_ach / bf16 if bf16 else None,
+                                        "note": "FP16 mma.sync 16x64x1 over 8 candidates per "
+                                                "pose, against the measured dense bf16 rate "
+                                                "(FP16 dense has the same nominal rate)"},
+                     "peak_source": fp32["source"],
+                     "avg_launch_ms": cull_ms,
+                     "traffic": _traffic("cull_kernel", WORKLOAD)},
         "kernels_ms_per_step": {k: v[1] / a.steps for k, v in prof.items()},
+        "fp32_peak": fp32,
         "e2e": {"value": world * pairs / (e2e_step_ms / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 12 * P, "d2h_bytes_per_step": (4 + 12 + 4) * P,
                 "ms_per_step": e2e_step_ms,

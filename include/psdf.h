@@ -535,6 +535,17 @@ int psdf_eval_grad_noalloc(const float *footprint, int32_t m, const psdf_scene *
  * *previous (nullable) receives the limit that was in force. */
 int psdf_debug_set_wait_limit(uint32_t polls, uint32_t *previous);
 
+/* ---- measurement --------------------------------------------------------
+ * No counterpart in the paper: the FP32 roofline's denominator, measured.
+ * Runs an FP32 FMA microbenchmark on the current device (every SM full of
+ * threads running 8 independent multiply-add chains each, `iters` steps,
+ * scalar FMAs or, paired != 0, paired FP32 FMAs on float2) reps + 1 times on
+ * `stream` (the first launch warms up), synchronously, and returns the best
+ * rate in TFLOP/s (2 flops per FMA) and its duration.  It allocates a small
+ * output buffer and synchronizes: never call it during stream capture. */
+int psdf_measure_fp32_peak(int32_t paired, int32_t iters, int32_t reps, double *tflops,
+                           double *best_ms, void *stream);
+
 /* ---- tracing -----------------------------------------------------------
  * When enabled, the library brackets each launch of its kernels with CUDA
  * events recorded on the launch stream (not during stream capture).

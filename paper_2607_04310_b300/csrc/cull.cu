@@ -1,30 +1,25 @@
 // Exact tile cull with a proposal (psdf_eval_culled and its helpers).
 //
-// Work is organised as (pose, tile) pairs, bucketed by tile:
-//   0. clear_words     per-tile counters and the pipeline counters cleared
-//   1. propose         16 lanes per pose rank the tiles of the pose's cell in a
-//                      uniform grid (every tile within one cell size; all
-//                      tiles for a pose outside the grid) by the conservative
-//                      bound; the pose keeps its K best, or its 8 best
-//                      re-ranked by the tile-proposal network on tensor cores
-//                      (K best kept).  From the circles of the proposed tiles'
-//                      obstacles the lanes take an upper bound UB on phi and
-//                      list the pose for the proposed tiles and for every other
-//                      tile whose lower bound does not exceed UB (the cell's
-//                      list holds them all when UB's reach is within the
-//                      cell's; else every tile is tested)
-//   2. eval_lists      two CTAs per tile, launched as the proposals start:
-//                      the tile's blob staged in shared memory, then the
-//                      tile's lanes = (pose, obstacle range) pairs in units of
-//                      128 so that warps stay full; an obstacle whose circle
-//                      bound exceeds the pose's upper bound is skipped, the
-//                      others are evaluated exactly; one atomicMin per
-//                      evaluated obstacle into the pose's 64-bit key
-//   3. epilogue        as for the full scan
-// Every tile holding a value at or below phi has a lower bound <= phi <= UB,
-// so it is listed; every obstacle skipped has a value above the threshold,
-// which is never below phi.  The minimum over 64-bit keys does not depend on
-// evaluation order, so the result equals the full scan's bit for bit.
+// One launch, each pose handled by 16 lanes of its own (cull_kernel):
+//   ranking      the tiles of the pose's cell in a uniform grid (every tile
+//                within one cell size; all tiles for a pose outside the
+//                grid), ordered by their conservative bound; the pose
+//                proposes its K nearest tiles, or the K best of its 8 nearest
+//                re-ranked by the tile-proposal network on tensor cores
+//   pass 1       an upper bound UB >= phi from the circles of the proposed
+//                tiles' obstacles; every obstacle there whose circle bound
+//                does not exceed UB is evaluated exactly: value v1 >= phi
+//   pass 2       every other tile whose bound does not exceed v1 (the cell's
+//                list holds them all while v1's reach is within the cell's;
+//                else every tile is tested); obstacles whose circle bound
+//                exceeds v1 are skipped, the others evaluated exactly
+//   epilogue     as for the full scan, on the winning obstacle
+// The scene's arrays are brought into L2 by bulk prefetches (TMA) at the
+// start of the launch.  Every tile holding a value at or below phi has a
+// bound <= phi <= v1, so it is evaluated; every obstacle skipped has a value
+// above the threshold, which is never below phi.  The minimum over 64-bit
+// keys does not depend on evaluation order, so the result equals the full
+// scan's bit for bit.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -48,52 +43,7 @@ constexpr int kMaxK = PSDF_CULL_MAX_K;
 constexpr int kPre = 8;  // bound-ranked candidates the network re-ranks per pose
 constexpr int kFrag1Words = 8 * 32 * 2;
 constexpr int kFrag2Words = 4 * 32 * 2;
-constexpr int kPoseThreads = 128;  // 4 warps x 2 poses per propose / fallback CTA
-constexpr int kKeep = 2;  // cell entries a propose lane keeps from its ranking pass
-constexpr int kListThreads = 128;  // threads of an eval_lists CTA
 constexpr int kMaxScanTiles = 1024 * 64;
-
-// counters at the start of the workspace
-// Pipeline counters, each spread over kCtrSlots words (CTA b adds to slot
-// b % kCtrSlots, so that a few thousand CTAs do not queue on one address);
-// psdf_cull_stats_read sums the slots.
-constexpr int kCtrSlots = 16;
-struct CullCounters {
-  int err;
-  int pad;
-  unsigned long long n_prop[kCtrSlots];       // proposed (pose, tile) pairs
-  unsigned long long n_fb[kCtrSlots];         // (pose, tile) pairs added by the bound check
-  unsigned long long fallback_poses[kCtrSlots];  // poses with at least one such pair
-  unsigned long long n_obs_eval[kCtrSlots];   // obstacles evaluated exactly
-  unsigned long long n_edge_eval[kCtrSlots];  // edges of those obstacles
-  unsigned long long n_bound[kCtrSlots];      // tile bounds the proposals computed
-  unsigned long long n_circ[kCtrSlots];       // obstacle circles of the proposals' upper bounds
-};
-
-struct CullLayout {
-  size_t hist, clear_bytes, keys, pose4, ub, prop, list, total;
-};
-
-static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-
-// Per-tile pose lists have a fixed capacity of P entries (list[t * P + i]).
-// The counters and the per-tile histogram are contiguous (cleared by one kernel).
-static CullLayout cull_layout(long long P, int n_tiles)
-{
-  CullLayout L;
-  const size_t Pz = (size_t)std::max<long long>(P, 1);
-  const size_t Tz = (size_t)std::max(n_tiles, 1);
-  size_t o = align256(sizeof(CullCounters));
-  L.hist = o; o = align256(o + 4 * Tz);
-  L.clear_bytes = o;
-  L.keys = o; o = align256(o + 8 * Pz);
-  L.pose4 = o; o = align256(o + 16 * Pz);
-  L.ub = o; o = align256(o + 4 * Pz);
-  L.prop = o; o = align256(o + 4 * Pz * kMaxK);
-  L.list = o; o = align256(o + 4 * Pz * Tz);
-  L.total = o;
-  return L;
-}
 
 // ---------------------------------------------------------------------------
 // conservative lower bound and network inputs
@@ -299,24 +249,6 @@ __device__ __forceinline__ void mlp_rows(const MlpFrags &w, const float *ab, int
   sc_b = o[2];
 }
 
-// ---------------------------------------------------------------------------
-// per-tile work units
-// ---------------------------------------------------------------------------
-// Lanes of a tile's work: its cnt poses are split over S obstacle ranges
-// each, so that cnt * S lanes fill about two 128-thread units (one per CTA of
-// the tile) when few poses need the tile (short per-lane chains, many warps
-// in flight).
-constexpr int kTargetLanes = 2 * kListThreads;
-__device__ __forceinline__ int tile_split(int cnt, int n_obs)
-{
-  return max(1, min(kTargetLanes / max(cnt, 1), n_obs));
-}
-
-__device__ __forceinline__ int tile_units(int cnt, int n_obs)
-{
-  return cnt == 0 ? 0 : (int)(((long long)cnt * tile_split(cnt, n_obs) + kListThreads - 1) / kListThreads);
-}
-
 // Squared distance from p to a tile's AABB: the bound's ranking key (the
 // bound is increasing in the distance, so no square root is needed to rank).
 __device__ __forceinline__ float aabb_d2(float4 a4, float px, float py)
@@ -333,16 +265,6 @@ __device__ __forceinline__ float cand_radius(float ub, float rfoot)
 {
   const float D = (ub + rfoot + 1e-4f) / (1.f - 1e-5f);
   return D * (1.f + 1e-5f) + 1e-6f;
-}
-
-// Zeroes the counters and per-tile counts of a cull workspace; the proposal
-// kernel, launched after it with programmatic stream serialization, ranks
-// its tiles meanwhile and waits for it before its first append.
-__global__ void clear_words(unsigned *__restrict__ w, int n)
-{
-  pdl_trigger();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    w[i] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -383,495 +305,594 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
   return (int)fy * g.nx + (int)fx;
 }
 
-// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).  The
-// tiles a pose looks at are its grid cell's list (every tile within one
-// cell size of the pose), else all tiles; lane hl takes entries hl, hl + 16,
-// ... and keeps its RL best bounds.  R rounds of a 16-lane argmin over the
-// lanes' heads give the pose's R smallest (bound, tile) pairs in order,
-// written to cand[r] (uniform over the pose's 16 lanes).  With NET the 16
-// rows (2 poses x kPre candidates) are scored by the network and the pose
-// keeps its K best scores; else its K best bounds.  Lane 0 of each pose
-// appends the pose to its proposed tiles.  The pose's 16 lanes then take an
-// upper bound on phi from the circles of the proposed tiles' obstacles, and
-// append the pose to every other tile whose bound does not exceed it: from
-// the cell's list when the bound's reach is within the grid's, else from
-// all tiles.
-template <int K, bool NET>
-__global__ void __launch_bounds__(kPoseThreads)
-    propose(const float *__restrict__ poses, long long P, const TileHdr *__restrict__ tiles,
-            int T, const CullGrid grid, float rfoot, float rin, float ub_pad,
-            const unsigned char *__restrict__ blob,
-            const uint32_t *__restrict__ frag, float b2, unsigned long long *__restrict__ keys,
-            float4 *__restrict__ pose4, float *__restrict__ ub_out, int *__restrict__ prop,
-            int *hist, int *__restrict__ list,
-            CullCounters *ctr)
+// ---------------------------------------------------------------------------
+// the fused cull: each pose's proposals, exact evaluation and epilogue by
+// its own 16 lanes, in one launch
+// ---------------------------------------------------------------------------
+constexpr int kCullThreads = 128;  // 4 warps x 2 poses
+constexpr int kCullWarps = kCullThreads / 32;
+constexpr int kRL = 4;             // best tiles a lane keeps from its ranking pass
+constexpr int kFilt = 4;           // circle bounds a lane tests per round
+constexpr int kItemLanes = 4;      // lanes per evaluated (pose, obstacle) item
+constexpr int kItemsPerRound = 32 / kItemLanes;
+constexpr int kQueue = 32 * kFilt + kItemsPerRound;  // a round's appends + leftovers
+constexpr int kSegs = 16;          // tiles of one flattened pass (one per lane of a half)
+constexpr int kStatWords = 8;      // counters per CTA in the workspace
+constexpr int kStatBase = 32;      // first counter word (the header is 256 bytes)
+constexpr long long kPrefetchChunk = 16384;  // bytes per bulk L2 prefetch
+constexpr int kMaxPrefetch = 8;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-CTA counters (workspace words kStatBase + kStatWords * CTA + i).
+enum CullStat { kStProp, kStFb, kStFbPoses, kStBound, kStCirc, kStObs, kStEdges, kStCount };
+
+// Scene arrays brought into L2 with bulk prefetches at the start of the
+// launch (every chunk by thread 0 of one CTA, round-robin): a step then pays
+// the scene's bytes once at the HBM bandwidth instead of a chain of
+// dependent HBM round trips per pose.  ptr 16-byte aligned, bytes a multiple
+// of 16.
+struct Prefetch {
+  const unsigned char *ptr[kMaxPrefetch];
+  long long bytes[kMaxPrefetch];
+  long long first[kMaxPrefetch + 1];  // first chunk of each range; first[n] = all chunks
+  int n;
+};
+
+struct CullArgs {
+  const float *poses;
+  long long P;
+  CullGrid grid;
+  const float4 *tile_ab;    // all tiles: poses outside the grid, bounds beyond its reach
+  const int4 *tile_info;
+  int T;
+  int K;                    // proposals per pose
+  const CullObs *obs;
+  const float4 *vtx;
+  const int *far;
+  float ub_pad;             // soft minimum: most a penetrating obstacle's value exceeds 0
+  float eps_axis;
+  const uint32_t *frag;     // network fragments (NET)
+  float b2;
+  float *phi, *dphi;
+  unsigned *active;
+  float4 *saved;            // saved backward records (hard minimum), or NULL
+  unsigned long long *ws;   // {CTAs, error word, ...} then kStatWords per CTA
+  Prefetch pf;
+};
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, unsigned bytes)
 {
-  constexpr int R = NET ? kPre : K;  // candidates merged per pose
-  constexpr int RL = NET ? 4 : K;    // best tiles each lane keeps
-  __shared__ int ct_s[kPoseThreads / 32][2][kPre];
-  __shared__ float sc_s[kPoseThreads / 32][2][kPre];
-  __shared__ int s_prop, s_fb, s_fbp;
-  __shared__ unsigned s_bound, s_circ;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long pw = ((long long)blockIdx.x * (kPoseThreads / 32) + warp) * 2;
-  const int half = lane >> 4, hl = lane & 15;
-  const long long p = pw + half;
-  const bool valid = p < P;
-  // the evaluation kernel may launch at once: its CTAs stage their tiles
-  // while the proposals run, and wait for this grid before reading its lists
-  pdl_trigger();
-  if (threadIdx.x == 0) s_prop = s_fb = s_fbp = s_bound = s_circ = 0;
-  unsigned n_bound = 0, n_circ = 0;  // this lane's tile bounds and circles
-  float px = 0.f, py = 0.f, s = 0.f, c = 1.f;
-  int e0 = 0, e1 = 0;  // the cell's list, or all tiles (cell < 0)
-  int cell = -1;
-  MlpFrags w;  // the network's weights (pose-invariant: read first)
-  if constexpr (NET) load_frags(frag, lane, w);
-  if (valid) {
-    px = poses[3 * p];
-    py = poses[3 * p + 1];
-    sincosf(poses[3 * p + 2], &s, &c);
-    cell = grid_cell(grid, px, py);
-    if (cell >= 0) {
-      e0 = __ldg(grid.off + cell);
-      e1 = __ldg(grid.off + cell + 1);
-    }
-    if (hl == 0) {
-      keys[p] = ~0ull;
-      pose4[p] = make_float4(px, py, c, s);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_scene(const Prefetch &pf)
+{
+  for (long long c = blockIdx.x; c < pf.first[pf.n]; c += gridDim.x) {
+    int i = 0;
+    while (i + 1 < pf.n && c >= pf.first[i + 1]) ++i;
+    const long long off = (c - pf.first[i]) * kPrefetchChunk;
+    const long long rest = pf.bytes[i] - off;
+    const unsigned sz = (unsigned)((rest < kPrefetchChunk ? rest : kPrefetchChunk) & ~15LL);
+    if (sz > 0) bulk_prefetch_l2(pf.ptr[i] + off, sz);
+  }
+}
+
+// The tiles a pose looks at: entries [lo, hi) of its cell's list, or every
+// tile.
+struct Entries {
+  const float4 *ab;
+  const int4 *info;
+  int lo, hi;
+};
+
+__device__ __forceinline__ Entries entries_of(const CullArgs &a, int cell, bool use_cell)
+{
+  if (use_cell)
+    return Entries{a.grid.ab, a.grid.info, __ldg(a.grid.off + cell), __ldg(a.grid.off + cell + 1)};
+  return Entries{a.tile_ab, a.tile_info, 0, a.T};
+}
+
+// The tile bound in the min-key value domain (as circle_lb_value): every
+// obstacle of the tile has a value above it, or -inf (no claim).
+__device__ __forceinline__ float tile_lb_value(float4 ab, float px, float py, float rfoot)
+{
+  const float b[4] = {ab.x, ab.y, ab.z, ab.w};
+  const float lb = tile_lb(b, px, py, rfoot);
+  return lb > 0.f ? lb * lb * (1.f - 1e-6f) : -kInf;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// Obstacle (sorted index) of the flattened position f over a half's tiles:
+// tile j holds positions st[j] .. st[j + 1] - 1, its obstacles from s0[j].
+__device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int nseg, int f)
+{
+  int j = 0;
+  while (j + 1 < nseg && f >= st[j + 1]) ++j;
+  return s0[j] + (f - st[j]);
+}
+
+// Per-lane running minimum of one pose half's keys (and the obstacle).
+struct HalfBest {
+  unsigned long long k0 = ~0ull, k1 = ~0ull;
+  int s0 = 0, s1 = 0;
+  __device__ __forceinline__ void add(int h, unsigned long long k, int s)
+  {
+    if (h == 0) {
+      if (k < k0) { k0 = k; s0 = s; }
+    } else {
+      if (k < k1) { k1 = k; s1 = s; }
     }
   }
-  float sc[RL];
-  int id[RL];
+};
+
+// The first n queued (obstacle << 5 | lane) items of the warp, kItemLanes
+// lanes per item (the obstacle's edges shared out, obstacle_value_coop),
+// kItemsPerRound items a round; every lane takes part in every round.  Each
+// item's pose is the one of the lane that queued it.
+template <int M, bool SOFT>
+__device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
+                                           const CullArgs &a, const int *qw, int n, int lane,
+                                           float px, float py, float c, float s, HalfBest &hb,
+                                           unsigned &n_obs, unsigned &n_edge)
+{
+  const int g = lane % kItemLanes;
+  for (int r0 = 0; r0 < n; r0 += kItemsPerRound) {
+    const int slot = r0 + lane / kItemLanes;
+    const bool live = slot < n;
+    const int item = live ? qw[slot] : 0;
+    const int src = item & 31, so = item >> 5;
+    const float ipx = __shfl_sync(kFull, px, src), ipy = __shfl_sync(kFull, py, src);
+    const float ic = __shfl_sync(kFull, c, src), is = __shfl_sync(kFull, s, src);
+    int4 rec = make_int4(0, 0, 0, 0);
+    if (live) rec = __ldg(&a.obs[so].rec);
+    const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
+        F, ipx, ipy, ic, is, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat, prm.eta, g);
+    if (live && g == 0) {
+      hb.add(src >> 4, pack_key(v, rec.z), so);
+      ++n_obs;
+      n_edge += (unsigned)rec.y;
+    }
+  }
+}
+
+// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).
+//  1. ranking: the tiles of the pose's cell in the cull grid (every tile
+//     within one cell size of it), else all tiles; lane hl takes entries hl,
+//     hl + 16, ... and keeps its 4 smallest AABB distances; rounds of a
+//     16-lane minimum give the pose's smallest ones in order.  The pose
+//     proposes its K nearest tiles, or (NET) the K best network scores among
+//     its 8 nearest (2 poses x 8 candidates = 16 rows of one tensor-core
+//     pass).
+//  2. pass 1: an upper bound UB >= phi from the circles of the proposed
+//     tiles' obstacles; those whose circle bound does not exceed UB are
+//     evaluated exactly.  Their minimum key is phi's first value v1 >= phi.
+//  3. pass 2: every other tile whose bound does not exceed v1 -- from the
+//     cell's list when those all lie within the grid's reach, else from all
+//     tiles -- in chunks of 16 tiles, their obstacles flattened over the 16
+//     lanes; obstacles whose circle bound exceeds v1 are skipped, the others
+//     evaluated exactly.
+//     Both passes queue their surviving (pose, obstacle) items in one
+//     warp-wide queue, evaluated in rounds of 8 items (4 lanes each) at one
+//     place in the code, so that the kernel's instruction footprint stays
+//     small.
+//  4. epilogue of every winning obstacle of the CTA's 8 poses by one warp
+//     (4 lanes per pose, or one for the soft minimum): value, active pair,
+//     gradient, saved backward rows.
+// No skipped tile or obstacle can hold a value at or below phi, and the key
+// minimum does not depend on the order of evaluation, so the outputs equal
+// the full scan's bit for bit.
+template <int M, bool NET, bool SOFT>
+__global__ void __launch_bounds__(kCullThreads, 4)
+    cull_kernel(const FootprintK F, const ParamsK prm, const CullArgs a)
+{
+  constexpr int kPoses = 2 * kCullWarps;  // poses per CTA
+  __shared__ int q_s[kCullWarps][kQueue];
+  __shared__ int seg_s0[kCullWarps][2][kSegs];
+  __shared__ int seg_st[kCullWarps][2][kSegs + 1];
+  __shared__ int cand_s[kCullWarps][2][kPre];
+  __shared__ float score_s[kCullWarps][2][kPre];
+  __shared__ float4 ep_pose[kPoses];
+  __shared__ unsigned long long ep_key[kPoses];
+  __shared__ int ep_obs[kPoses];
+  __shared__ unsigned st_s[kStCount];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, hl = lane & 15;
+  const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+  const long long p = ((long long)blockIdx.x * kCullWarps + warp) * 2 + half;
+  const bool valid = p < a.P;
+  int *qw = q_s[warp];
+  int *sg0 = seg_s0[warp][half], *sgt = seg_st[warp][half];
+  if (threadIdx.x < kStCount) st_s[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) prefetch_scene(a.pf);
+  // a following kernel (the backward) may launch now; it waits for this grid
+  pdl_trigger();
+  float px = 0.f, py = 0.f, th = 0.f;
+  if (valid) {
+    px = a.poses[3 * p];
+    py = a.poses[3 * p + 1];
+    th = a.poses[3 * p + 2];
+  }
+  float s, c;
+  sincosf(th, &s, &c);
+  MlpFrags w;
+  if constexpr (NET) load_frags(a.frag, lane, w);
+  const int K = a.K;
+  unsigned n_bound = 0, n_circ = 0, n_obs = 0, n_edge = 0;
+
+  // ---- 1. ranking and proposals -------------------------------------------
+  const int cell = valid ? grid_cell(a.grid, px, py) : -1;
+  Entries E = entries_of(a, cell, cell >= 0);
+  if (!valid) E.hi = E.lo;
+  float sc[kRL];
+  int id[kRL];
 #pragma unroll
-  for (int i = 0; i < RL; ++i) {
+  for (int i = 0; i < kRL; ++i) {
     sc[i] = kInf;
     id[i] = -1;
   }
-  // entries i of the cell's list (tile grid.tl[i], its AABB grid.ab[i]) or
-  // tiles i; a lane's first kKeep cell entries stay in registers for the
-  // candidate pass below
-  const int lo = (cell >= 0 ? e0 : 0) + hl, hi = valid ? (cell >= 0 ? e1 : T) : 0;
-  int kt[kKeep];
-  float kd2[kKeep];
-  int i = lo;
-#pragma unroll
-  for (int q = 0; q < kKeep; ++q, i += 16) {
-    kt[q] = -1;
-    kd2[q] = kInf;
-    if (i < hi) {
-      const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
-      const float d2 = aabb_d2(cell >= 0 ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py);
-      topk_insert<RL>(sc, id, d2, t);
-      kt[q] = t;
-      kd2[q] = d2;
+  {
+    int i = E.lo + hl;
+    for (; i + 16 < E.hi; i += 32) {
+      const float4 a0 = __ldg(E.ab + i), a1 = __ldg(E.ab + i + 16);
+      topk_insert<kRL>(sc, id, aabb_d2(a0, px, py), i - E.lo);
+      topk_insert<kRL>(sc, id, aabb_d2(a1, px, py), i + 16 - E.lo);
+      n_bound += 2;
+    }
+    if (i < E.hi) {
+      topk_insert<kRL>(sc, id, aabb_d2(__ldg(E.ab + i), px, py), i - E.lo);
       ++n_bound;
     }
   }
-  for (; i < hi; i += 16) {
-    const int t = cell >= 0 ? __ldg(grid.tl + i) : i;
-    topk_insert<RL>(sc, id, aabb_d2(cell >= 0 ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py), t);
-    ++n_bound;
-  }
-  __syncthreads();  // s_prop, s_fb, s_fbp initialised
-  int best[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) best[i] = -1;
-  float ubp = kInf;  // upper bound (metres) on the pose's phi
-  if (pw < P) {  // uniform over the warp
-    // R rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys
-    // (the top 16 bits of the squared distance -- not negative, so its bits
-    // order like the value, to 1/128 -- over the tile's 16 bits; a tile sits
-    // in one lane only, so the lane whose head won pops it).  A lane keeps
-    // only its RL best, so with the network the 8 candidates are the 8
-    // smallest bounds it looked at unless one lane held more than RL of them.
-    int cand[R];
+  // rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys (the
+  // top 16 bits of the squared distance -- not negative, so its bits order
+  // like the value, to 1/128 -- over the entry's 16 bits; an entry sits in
+  // one lane only, so the lane whose head won pops it)
+  const int R = NET ? kPre : K;
+  int cand[kPre];
+  {
     int head = 0;
-    // tile headers of the candidates {blob_off, blob_bytes, n_obs, n_vtx}:
-    // with the network lane 4 g holds candidate g's of pose a (hda) and of
-    // pose b (hdb); without it lane r of a pose's half holds candidate r's
-    int4 hda = make_int4(0, 0, 0, 0), hdb = hda;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      unsigned mine = ~0u;
+    for (int r = 0; r < kPre; ++r) {
+      cand[r] = -1;
+      if (r < R) {  // uniform over the warp
+        unsigned mine = ~0u;
 #pragma unroll
-      for (int i = 0; i < RL; ++i)
-        if (i == head && id[i] >= 0) mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
-      const unsigned k0 = __reduce_min_sync(0xffffffffu, half == 0 ? mine : ~0u);
-      const unsigned k1 = __reduce_min_sync(0xffffffffu, half == 1 ? mine : ~0u);
-      const unsigned key = half ? k1 : k0;
-      const bool any = key != ~0u;
-      cand[r] = any ? (int)(key & 0xffffu) : -1;
-      if (any && key == mine) ++head;
-    }
-    if constexpr (NET) {
-      if (hl == 0)
-#pragma unroll
-        for (int r = 0; r < kPre; ++r) ct_s[warp][half][r] = cand[r];
-      __syncwarp();
-      const int g = lane >> 2, q = lane & 3;
-      const int ta = ct_s[warp][0][g], tb = ct_s[warp][1][g];
-      float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
-      float efa = 0.f, efb = 0.f;
-      // the candidates' AABBs and edge fractions
-      if (ta >= 0) {
-        hda = __ldg(reinterpret_cast<const int4 *>(tiles + ta));
-        const float4 a4 = tile_aabb(tiles, ta);
-        aba[0] = a4.x; aba[1] = a4.y; aba[2] = a4.z; aba[3] = a4.w;
-        efa = (float)hda.w * (1.f / 256.f);
-      }
-      if (tb >= 0) {
-        hdb = __ldg(reinterpret_cast<const int4 *>(tiles + tb));
-        const float4 a4 = tile_aabb(tiles, tb);
-        abb[0] = a4.x; abb[1] = a4.y; abb[2] = a4.z; abb[3] = a4.w;
-        efb = (float)hdb.w * (1.f / 256.f);
-      }
-      // pose a's and pose b's (x, y, cos, sin) from lanes 0 and 16
-      const float pxa = __shfl_sync(0xffffffffu, px, 0), pya = __shfl_sync(0xffffffffu, py, 0);
-      const float ca = __shfl_sync(0xffffffffu, c, 0), sa = __shfl_sync(0xffffffffu, s, 0);
-      const float pxb = __shfl_sync(0xffffffffu, px, 16), pyb = __shfl_sync(0xffffffffu, py, 16);
-      const float cb = __shfl_sync(0xffffffffu, c, 16), sb = __shfl_sync(0xffffffffu, s, 16);
-      float s_a, s_b;
-      mlp_rows_pair(w, q, aba, efa, pxa, pya, ca, sa, abb, efb, pxb, pyb, cb, sb, rfoot, s_a, s_b);
-      if (q == 0) {
-        sc_s[warp][0][g] = ta >= 0 ? s_a + b2 : kInf;
-        sc_s[warp][1][g] = tb >= 0 ? s_b + b2 : kInf;
-      }
-      __syncwarp();
-      float bs[K];
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        bs[i] = kInf;
-        best[i] = -1;
-      }
-#pragma unroll
-      for (int i = 0; i < kPre; ++i)
-        if (cand[i] >= 0) topk_insert<K>(bs, best, sc_s[warp][half][i], cand[i]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        best[i] = cand[i];
-        if (hl == i && cand[i] >= 0) hda = __ldg(reinterpret_cast<const int4 *>(tiles + cand[i]));
+        for (int i = 0; i < kRL; ++i)
+          if (i == head && id[i] >= 0)
+            mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
+        const unsigned k0 = __reduce_min_sync(kFull, half == 0 ? mine : ~0u);
+        const unsigned k1 = __reduce_min_sync(kFull, half == 1 ? mine : ~0u);
+        const unsigned key = half ? k1 : k0;
+        cand[r] = key != ~0u ? (int)(key & 0xffffu) : -1;
+        if (key != ~0u && key == mine) ++head;
       }
     }
-    // the per-tile counts and the counters are cleared by the kernel before
-    // this one: wait for it before the first append
-    pdl_wait();
-    if (valid && hl == 0) {
-      int n = 0;
+  }
+  int best[kMaxK];
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        prop[p * kMaxK + i] = best[i];
-        if (best[i] >= 0) {
-          list[(long long)best[i] * P + atomicAdd(&hist[best[i]], 1)] = (int)p;
-          ++n;
+  for (int i = 0; i < kMaxK; ++i) best[i] = i < K ? cand[i] : -1;
+  if constexpr (NET) {
+    if (hl == 0)
+#pragma unroll
+      for (int r = 0; r < kPre; ++r) cand_s[warp][half][r] = cand[r];
+    __syncwarp();
+    // lane 4 g + q: candidate g of both poses, quarter q of its inputs
+    const int g = lane >> 2, q = lane & 3;
+    const int cellA = __shfl_sync(kFull, cell, 0), cellB = __shfl_sync(kFull, cell, 16);
+    const int loA = __shfl_sync(kFull, E.lo, 0), loB = __shfl_sync(kFull, E.lo, 16);
+    const int ta = cand_s[warp][0][g], tb = cand_s[warp][1][g];
+    float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
+    float efa = 0.f, efb = 0.f;
+    if (ta >= 0) {
+      const float4 v = __ldg((cellA >= 0 ? a.grid.ab : a.tile_ab) + loA + ta);
+      const int4 inf = __ldg((cellA >= 0 ? a.grid.info : a.tile_info) + loA + ta);
+      aba[0] = v.x; aba[1] = v.y; aba[2] = v.z; aba[3] = v.w;
+      efa = (float)inf.z * (1.f / 256.f);
+    }
+    if (tb >= 0) {
+      const float4 v = __ldg((cellB >= 0 ? a.grid.ab : a.tile_ab) + loB + tb);
+      const int4 inf = __ldg((cellB >= 0 ? a.grid.info : a.tile_info) + loB + tb);
+      abb[0] = v.x; abb[1] = v.y; abb[2] = v.z; abb[3] = v.w;
+      efb = (float)inf.z * (1.f / 256.f);
+    }
+    const float pxa = __shfl_sync(kFull, px, 0), pya = __shfl_sync(kFull, py, 0);
+    const float ca = __shfl_sync(kFull, c, 0), sa = __shfl_sync(kFull, s, 0);
+    const float pxb = __shfl_sync(kFull, px, 16), pyb = __shfl_sync(kFull, py, 16);
+    const float cb = __shfl_sync(kFull, c, 16), sb = __shfl_sync(kFull, s, 16);
+    float s_a, s_b;
+    mlp_rows_pair(w, q, aba, efa, pxa, pya, ca, sa, abb, efb, pxb, pyb, cb, sb, F.radius, s_a,
+                  s_b);
+    if (q == 0) {
+      score_s[warp][0][g] = ta >= 0 ? s_a + a.b2 : kInf;
+      score_s[warp][1][g] = tb >= 0 ? s_b + a.b2 : kInf;
+    }
+    __syncwarp();
+    float bsc[kMaxK];
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i) {
+      bsc[i] = kInf;
+      best[i] = -1;
+    }
+#pragma unroll
+    for (int i = 0; i < kPre; ++i)
+      if (cand[i] >= 0) topk_insert<kMaxK>(bsc, best, score_s[warp][half][i], cand[i]);
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i)
+      if (i >= K) best[i] = -1;
+  }
+
+  // ---- 2. pass 1 set-up: the proposed tiles, the upper bound -------------
+  int ptile[kMaxK];
+  int nseg = 0, N = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxK; ++i) {
+    ptile[i] = -1;
+    if (best[i] >= 0) {
+      const int4 inf = __ldg(E.info + E.lo + best[i]);
+      ptile[i] = inf.w;
+      if (hl == 0) {
+        sg0[nseg] = inf.x;
+        sgt[nseg] = N;
+      }
+      N += inf.y;
+      ++nseg;
+    }
+  }
+  if (hl == 0) sgt[nseg] = N;
+  const int n_prop = nseg;
+  __syncwarp();
+  // the circles of the lane's first round stay in registers for the first
+  // round of circle tests below
+  float4 cc0[kFilt];
+  int so0[kFilt];
+  float ubp = kInf;
+  for (int f0 = hl; f0 < N; f0 += 16 * kFilt) {
+    float4 cc[kFilt];
+    int so[kFilt];
+#pragma unroll
+    for (int q = 0; q < kFilt; ++q) {
+      const int f = f0 + 16 * q;
+      so[q] = 0;
+      if (f < N) {
+        so[q] = flat_obstacle(sg0, sgt, nseg, f);
+        cc[q] = __ldg(&a.obs[so[q]].circ);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kFilt; ++q)
+      if (f0 + 16 * q < N) {
+        ubp = fminf(ubp, circle_ub(cc[q], px, py, F.radius, F.inner));
+        ++n_circ;
+      }
+    if (f0 == hl) {
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        cc0[q] = cc[q];
+        so0[q] = so[q];
+      }
+    }
+  }
+  {  // 16-lane minimum (ubp >= 0, so its bits order like the value)
+    const unsigned u = __float_as_uint(ubp);
+    const unsigned u0 = __reduce_min_sync(kFull, half == 0 ? u : ~0u);
+    const unsigned u1 = __reduce_min_sync(kFull, half == 1 ? u : ~0u);
+    ubp = __uint_as_float(half ? u1 : u0);
+  }
+  ubp += a.ub_pad;
+
+  // ---- 2-3. both passes: circle tests, queued items, exact evaluation ----
+  // One loop: each iteration tests one round of circles (kFilt a lane) of
+  // the current run of tiles and evaluates the queue's whole rounds; at the
+  // end of pass 1 (and of the last run) the queue is drained.
+  HalfBest hb;
+  int nq = 0;  // queued items of the warp (uniform)
+  int pass = 1, ch = 0, nch = 0, k0 = 0;
+  float thr = ub_value(ubp), v1 = kInf;
+  Entries E2 = E;
+  int n_fb = 0;
+  int span = N > hl ? (N - hl + 15) / 16 : 0;
+  span = (int)__reduce_max_sync(kFull, (unsigned)span);
+  for (;;) {
+    // one round of circle tests: positions hl + 16 (k0 + q) of the run
+    if (k0 < span) {
+      bool keep[kFilt];
+      int so[kFilt];
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        const int f = hl + 16 * (k0 + q);
+        keep[q] = false;
+        so[q] = 0;
+        if (f < N) {
+          float4 cq;
+          if (pass == 1 && k0 == 0) {
+            so[q] = so0[q];
+            cq = cc0[q];
+          } else {
+            so[q] = flat_obstacle(sg0, sgt, nseg, f);
+            cq = __ldg(&a.obs[so[q]].circ);
+          }
+          keep[q] = !(circle_lb_value(cq, px, py, F.radius) > thr);
         }
       }
 #pragma unroll
-      for (int i = K; i < kMaxK; ++i) prop[p * kMaxK + i] = -1;
-      atomicAdd(&s_prop, n);
-    }
-    // upper bound on phi from the proposed tiles' obstacle circles (16
-    // lanes, four circles a lane per round, their loads issued together)
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      // the proposed tile's header from the lane that read it
-      int src = (half << 4) + i;
-      if constexpr (NET) {
-        int r = 0;
-#pragma unroll
-        for (int q = 0; q < kPre; ++q)
-          if (cand[q] == best[i]) r = q;
-        src = 4 * r;
-      }
-      int4 h;
-      h.x = __shfl_sync(0xffffffffu, hda.x, src);
-      h.y = __shfl_sync(0xffffffffu, hda.y, src);
-      h.z = __shfl_sync(0xffffffffu, hda.z, src);
-      if constexpr (NET) {
-        const int bx = __shfl_sync(0xffffffffu, hdb.x, src);
-        const int by = __shfl_sync(0xffffffffu, hdb.y, src);
-        const int bz = __shfl_sync(0xffffffffu, hdb.z, src);
-        if (half) h = make_int4(bx, by, bz, 0);
-      }
-      if (best[i] < 0) continue;  // uniform over the pose's lanes
-      const float4 *circ = reinterpret_cast<const float4 *>(blob + h.x + h.y);
-      for (int o = hl; o < h.z; o += 64) {
-        float4 cc[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (o + 16 * q < h.z) cc[q] = __ldg(circ + o + 16 * q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (o + 16 * q < h.z) {
-            ubp = fminf(ubp, circle_ub(cc[q], px, py, rfoot, rin));
-            ++n_circ;
-          }
-      }
-    }
-    {  // 16-lane minimum (ubp >= 0, so its bits order like the value)
-      const unsigned u = __float_as_uint(ubp);
-      const unsigned u0 = __reduce_min_sync(0xffffffffu, half == 0 ? u : ~0u);
-      const unsigned u1 = __reduce_min_sync(0xffffffffu, half == 1 ? u : ~0u);
-      ubp = __uint_as_float(half ? u1 : u0);
-    }
-    ubp += ub_pad;  // soft minimum: a penetrating obstacle's value reaches up to log(K) / eta
-    if (valid && hl == 0) ub_out[p] = ubp;
-  }
-  // every unproposed tile whose bound does not exceed the upper bound is
-  // listed too: no other tile can hold a value at or below phi.  A lane's
-  // first few tiles are appended after its loop (their atomics in flight
-  // together), further ones at once.
-  constexpr int kDefer = 4;
-  int ncand = 0, defer[kDefer];
-  const float Dc = cand_radius(ubp, rfoot);
-  const float Dc2 = Dc >= 0.f ? Dc * Dc : -1.f;
-  const bool in_cell = cell >= 0 && Dc <= grid.reach_q;
-  const int clo = (in_cell ? e0 : 0) + hl, chi = valid ? (in_cell ? e1 : T) : 0;
-  auto consider = [&](int t, float d2) {
-    bool proposed = false;
-#pragma unroll
-    for (int q = 0; q < K; ++q) proposed |= (best[q] == t);
-    if (!proposed && d2 <= Dc2) {
-      if (ncand < kDefer) {
-#pragma unroll
-        for (int q = 0; q < kDefer; ++q)
-          if (q == ncand) defer[q] = t;
-      } else {
-        list[(long long)t * P + atomicAdd(&hist[t], 1)] = (int)p;
-      }
-      ++ncand;
-    }
-  };
-  i = clo;
-  if (in_cell) {  // the same entries as the ranking pass: its first ones kept
-#pragma unroll
-    for (int q = 0; q < kKeep; ++q, i += 16)
-      if (i < chi) consider(kt[q], kd2[q]);
-  }
-  for (; i < chi; i += 16) {
-    const int t = in_cell ? __ldg(grid.tl + i) : i;
-    consider(t, aabb_d2(in_cell ? __ldg(grid.ab + i) : tile_aabb(tiles, t), px, py));
-    ++n_bound;
-  }
-#pragma unroll
-  for (int q = 0; q < kDefer; ++q)
-    if (q < ncand) list[(long long)defer[q] * P + atomicAdd(&hist[defer[q]], 1)] = (int)p;
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
-  if (valid && hl == 0 && ncand > 0) {
-    atomicAdd(&s_fb, ncand);
-    atomicAdd(&s_fbp, 1);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    n_bound += __shfl_xor_sync(0xffffffffu, n_bound, o);
-    n_circ += __shfl_xor_sync(0xffffffffu, n_circ, o);
-  }
-  if (lane == 0) {
-    atomicAdd(&s_bound, n_bound);
-    atomicAdd(&s_circ, n_circ);
-  }
-  pdl_wait();  // (warps of poses beyond P reach the counters without appending)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int slot = blockIdx.x % kCtrSlots;
-    atomicAdd(&ctr->n_prop[slot], (unsigned long long)s_prop);
-    atomicAdd(&ctr->n_fb[slot], (unsigned long long)s_fb);
-    atomicAdd(&ctr->fallback_poses[slot], (unsigned long long)s_fbp);
-    atomicAdd(&ctr->n_bound[slot], (unsigned long long)s_bound);
-    atomicAdd(&ctr->n_circ[slot], (unsigned long long)s_circ);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// exact evaluation of the per-tile lists
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(smem_dst)),
-               "l"(gmem_src)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// kTileCTAs CTAs per tile: CTA j of tile t takes the tile's work units j,
-// j + kTileCTAs, ... (unit i covers lanes [128 i, 128 i + 128) of the tile's
-// cnt * S lanes); lane l takes pose list[t * P + l / S] and obstacle range
-// l % S of the tile.  The tile's blob and its obstacle circles are staged in
-// shared memory (16-byte cp.async per thread) before the CTA waits for the
-// proposals (they are pose-invariant).  Each lane tests its obstacles'
-// circle bounds against the pose's upper bound; the survivors of the warp's
-// 32 lanes are compacted (ballot) into a per-warp queue and evaluated a few
-// at a time, kItemLanes lanes per (pose, obstacle) item, so that lanes whose
-// obstacles were skipped do not idle through their neighbours' evaluations.  Every
-// evaluated obstacle merges its key into the pose's by atomicMin.
-constexpr int kTileCTAs = 2;
-constexpr int kFilt = 4;    // circle bounds a lane tests between two queue appends
-constexpr int kQueue = 31 + 32 * kFilt;  // per-warp queue of (lane, obstacle) items
-
-// The first n_items queued (lane, obstacle) items of the warp, kItemLanes
-// lanes per item (the obstacle's edges shared out, see obstacle_value_coop),
-// 32 / kItemLanes items a round; every lane takes part in every round.
-constexpr int kItemLanes = 4;
-template <int M, bool SOFT>
-__device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
-                                           const int *qw, int n_items, int lane, float px,
-                                           float py, float c, float s, long long p,
-                                           const int4 *ob, const float4 *vt,
-                                           unsigned long long *__restrict__ keys,
-                                           unsigned long long &n_obs,
-                                           unsigned long long &n_edge)
-{
-  constexpr int B = 32 / kItemLanes;
-  const int g = lane % kItemLanes;
-  for (int r0 = 0; r0 < n_items; r0 += B) {
-    const int slot = r0 + lane / kItemLanes;
-    const bool live = slot < n_items;
-    const int item = live ? qw[slot] : 0;
-    const int src = item >> 16, o = item & 0xffff;
-    // the item's pose from the lane that found it
-    const float ipx = __shfl_sync(0xffffffffu, px, src), ipy = __shfl_sync(0xffffffffu, py, src);
-    const float ic = __shfl_sync(0xffffffffu, c, src), is = __shfl_sync(0xffffffffu, s, src);
-    const long long ip = __shfl_sync(0xffffffffu, p, src);
-    const int4 rec = live ? ob[o] : make_int4(0, 0, 0, 0);
-    const float v = obstacle_value_coop<M, kItemLanes, SOFT>(F, ipx, ipy, ic, is, vt + 2 * rec.x,
-                                                             rec.y, prm.eps_sat, prm.eta, g);
-    if (live && g == 0) {
-      atomicMin(&keys[ip], pack_key(v, rec.z));
-      ++n_obs;
-      n_edge += rec.y;
-    }
-  }
-}
-
-template <int M, bool SOFT>
-__global__ void __launch_bounds__(kListThreads)
-    eval_lists(FootprintK F, ParamsK prm, const float4 *__restrict__ pose4, long long P,
-               const TileHdr *__restrict__ tiles, int T, const unsigned char *__restrict__ blob,
-               const int *__restrict__ hist, const int *__restrict__ list,
-               const float *__restrict__ ub, unsigned long long *__restrict__ keys,
-               CullCounters *ctr)
-{
-  extern __shared__ __align__(16) unsigned char tsm[];
-  __shared__ int queue[kListThreads / 32][kQueue];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int *qw = queue[warp];
-  const int t = (int)(blockIdx.x / kTileCTAs), j0 = (int)(blockIdx.x % kTileCTAs);
-  const TileHdr h = tiles[t];
-  {
-    const unsigned char *src = blob + h.blob_off;
-    const int bytes = h.blob_bytes + 16 * h.n_obs;  // records + circles
-    for (int o = 16 * threadIdx.x; o < bytes; o += 16 * kListThreads)
-      cp_async16(tsm + o, src + o);
-  }
-  pdl_wait();  // the proposal kernel's lists
-  const int cnt = __ldcg(hist + t);
-  const int S = tile_split(cnt, h.n_obs);
-  // lane counts fit 32 bits: cnt * S <= max(cnt, 2 * kListThreads) and cnt <= P < 2^31
-  const unsigned L = (unsigned)cnt * (unsigned)S;
-  const int units = tile_units(cnt, h.n_obs);
-  // a unit lane's pose, its frame and upper bound; the first unit's are read
-  // while the tile is still being staged, each next one at the end of a unit
-  long long pn = -1;
-  float4 qn = make_float4(0.f, 0.f, 1.f, 0.f);
-  float ubn = -kInf;
-  auto fetch = [&](int j) {
-    const unsigned l = (unsigned)j * kListThreads + threadIdx.x;
-    pn = -1;
-    if (j < units && l < L) pn = __ldcg(list + (long long)t * P + l / (unsigned)S);
-    if (pn >= 0) {
-      qn = __ldcg(pose4 + pn);
-      ubn = __ldcg(ub + pn);
-    }
-  };
-  fetch(j0);
-  cp_async_wait_all();
-  __syncthreads();
-  const int4 *ob = reinterpret_cast<const int4 *>(tsm);
-  const float4 *vt = reinterpret_cast<const float4 *>(tsm + 16 * h.n_obs);
-  const float4 *circ = reinterpret_cast<const float4 *>(tsm + h.blob_bytes);
-  unsigned long long n_obs = 0, n_edge = 0;
-  for (int j = j0; j < units; j += kTileCTAs) {
-    const unsigned l = (unsigned)j * kListThreads + threadIdx.x;
-    const long long p = pn;
-    float px = 0.f, py = 0.f, c = 1.f, s = 0.f, thr = -kInf;
-    int o0 = 0, o1 = 0;
-    if (p >= 0) {
-      px = qn.x;
-      py = qn.y;
-      c = qn.z;
-      s = qn.w;
-      thr = ub_value(ubn);
-      const int part = (int)(l % (unsigned)S);
-      o0 = h.n_obs * part / S;  // n_obs <= 256 and part < S <= 256
-      o1 = h.n_obs * (part + 1) / S;
-    }
-    int span = o1 - o0;
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, k));
-    // kFilt circle bounds at a time (independent), then their survivors
-    // appended in obstacle order; whole batches of 32 evaluated at once
-    int nq = 0;
-    for (int k0 = 0; k0 < span; k0 += kFilt) {
-      bool keep[kFilt];
-#pragma unroll
       for (int q = 0; q < kFilt; ++q) {
-        const int o = o0 + k0 + q;
-        keep[q] = false;
-        if (o < o1) keep[q] = !(circle_lb_value(circ[o], px, py, F.radius) > thr);
+        const unsigned m = __ballot_sync(kFull, keep[q]);
+        if (keep[q]) qw[nq + __popc(m & ((1u << lane) - 1u))] = (so[q] << 5) | lane;
+        nq += __popc(m);
       }
-#pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        const unsigned mask = __ballot_sync(0xffffffffu, keep[q]);
-        if (keep[q]) qw[nq + __popc(mask & ((1u << lane) - 1u))] = (lane << 16) | (o0 + k0 + q);
-        nq += __popc(mask);
-      }
-      if (nq >= 32) {  // uniform: whole batches, the rest (< 32) moved to the front
-        __syncwarp();
-        int head = 0;
-        for (; nq - head >= 32; head += 32)
-          eval_items<M, SOFT>(F, prm, qw + head, 32, lane, px, py, c, s, p, ob, vt, keys, n_obs,
-                              n_edge);
-        const int rest = nq - head;
-        const int v = lane < rest ? qw[head + lane] : 0;
-        __syncwarp();
-        if (lane < rest) qw[lane] = v;
-        __syncwarp();
-        nq = rest;
-      }
+      k0 += kFilt;
     }
-    if (nq > 0) {
+    const bool run_done = k0 >= span;
+    const bool last = run_done && (pass == 1 || ch + 1 >= nch);
+    // evaluate whole rounds; everything when pass 1 or the last run ends
+    const int todo = last ? nq : nq / kItemsPerRound * kItemsPerRound;
+    if (todo > 0) {
       __syncwarp();
-      eval_items<M, SOFT>(F, prm, qw, nq, lane, px, py, c, s, p, ob, vt, keys, n_obs, n_edge);
+      const int g = lane % kItemLanes;
+      for (int r0 = 0; r0 < todo; r0 += kItemsPerRound) {
+        const int slot = r0 + lane / kItemLanes;
+        const bool live = slot < todo;
+        const int item = live ? qw[slot] : 0;
+        const int src = item & 31, so = item >> 5;
+        const float ipx = __shfl_sync(kFull, px, src), ipy = __shfl_sync(kFull, py, src);
+        const float ic = __shfl_sync(kFull, c, src), is = __shfl_sync(kFull, s, src);
+        int4 rec = make_int4(0, 0, 0, 0);
+        if (live) rec = __ldg(&a.obs[so].rec);
+        const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
+            F, ipx, ipy, ic, is, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat, prm.eta, g);
+        if (live && g == 0) {
+          hb.add(src >> 4, pack_key(v, rec.z), so);
+          ++n_obs;
+          n_edge += (unsigned)rec.y;
+        }
+      }
+      const int rest = nq - todo;
+      const int v = lane < rest ? qw[todo + lane] : 0;
+      __syncwarp();
+      if (lane < rest) qw[lane] = v;
+      __syncwarp();
+      nq = rest;
     }
-    __syncwarp();  // the queue is refilled by the next unit
-    fetch(j + kTileCTAs);
-  }
-  pdl_trigger();  // the epilogue may launch; it waits for this grid
-  // evaluated obstacles and edges (the roofline's work count)
+    if (!run_done) continue;
+    if (pass == 2 && ch + 1 >= nch) break;
+    if (pass == 1) {
+      // each pose's first value: the minimum over its evaluated obstacles
+      const unsigned long long b0 = warp_min_u64(hb.k0), b1 = warp_min_u64(hb.k1);
+      const unsigned long long bk = half ? b1 : b0;
+      v1 = bk == ~0ull ? kInf : from_ordered_bits((unsigned)(bk >> 32));
+      // every tile whose bound does not exceed v1 lies within cand_radius of p
+      const float um = v1 > 0.f ? sqrtf(v1) * (1.f + 1e-6f) : 0.f;
+      const bool in_cell = cell >= 0 && cand_radius(um, F.radius) <= a.grid.reach_q;
+      E2 = entries_of(a, cell, in_cell);
+      if (!valid) E2.hi = E2.lo;
+      nch = (E2.hi - E2.lo + 15) / 16;
+      nch = (int)__reduce_max_sync(kFull, (unsigned)nch);
+      pass = 2;
+      ch = 0;
+      thr = v1;
+      if (nch == 0) break;
+    } else {
+      ++ch;
+    }
+    // the next run: chunk ch of pass 2, its passing tiles compacted in lane
+    // order (first obstacles, starts of their obstacle runs)
+    __syncwarp();  // the segment arrays of the previous run are done with
+    {
+      const int i = E2.lo + ch * 16 + hl;
+      bool passing = false;
+      int4 inf = make_int4(0, 0, 0, 0);
+      if (i < E2.hi) {
+        const float4 ab = __ldg(E2.ab + i);
+        inf = __ldg(E2.info + i);
+        ++n_bound;
+        bool proposed = false;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
-    n_edge += __shfl_xor_sync(0xffffffffu, n_edge, o);
+        for (int q = 0; q < kMaxK; ++q) proposed |= ptile[q] == inf.w;
+        passing = !proposed && !(tile_lb_value(ab, px, py, F.radius) > v1);
+      }
+      const unsigned m = __ballot_sync(kFull, passing) & hmask;
+      nseg = __popc(m);
+      int x = passing ? inf.y : 0;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o, 16);
+        if (hl >= o) x += y;
+      }
+      N = __shfl_sync(kFull, x, (half << 4) + 15);
+      if (passing) {
+        const int pos = __popc(m & ((1u << lane) - 1u));
+        sg0[pos] = inf.x;
+        sgt[pos] = x - inf.y;
+      }
+      if (hl == 0) sgt[nseg] = N;
+      n_fb += nseg;
+      __syncwarp();
+    }
+    k0 = 0;
+    span = N > hl ? (N - hl + 15) / 16 : 0;
+    span = (int)__reduce_max_sync(kFull, (unsigned)span);
   }
-  __shared__ unsigned long long s_cnt[2];
-  if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0ull;
-  __syncthreads();
-  if (lane == 0 && n_obs) {
-    atomicAdd(&s_cnt[0], n_obs);
-    atomicAdd(&s_cnt[1], n_edge);
+  unsigned long long bk;
+  int bs;
+  {
+    const unsigned long long k0w = warp_min_u64(hb.k0), k1w = warp_min_u64(hb.k1);
+    const int w0 = __ffs(__ballot_sync(kFull, hb.k0 == k0w)) - 1;
+    const int w1 = __ffs(__ballot_sync(kFull, hb.k1 == k1w)) - 1;
+    const int o0 = __shfl_sync(kFull, hb.s0, w0), o1 = __shfl_sync(kFull, hb.s1, w1);
+    bk = half ? k1w : k0w;
+    bs = half ? o1 : o0;
+  }
+  if (hl == 0) {
+    const int j = 2 * warp + half;
+    ep_pose[j] = make_float4(px, py, c, s);
+    ep_key[j] = valid ? bk : ~0ull;
+    ep_obs[j] = bs;
+  }
+
+  // ---- counters ------------------------------------------------------------
+  unsigned cnt[kStCount];
+  cnt[kStProp] = (valid && hl == 0) ? (unsigned)n_prop : 0u;
+  cnt[kStFb] = (valid && hl == 0) ? (unsigned)n_fb : 0u;
+  cnt[kStFbPoses] = (valid && hl == 0 && n_fb > 0) ? 1u : 0u;
+  cnt[kStBound] = n_bound;
+  cnt[kStCirc] = n_circ;
+  cnt[kStObs] = n_obs;
+  cnt[kStEdges] = n_edge;
+  __syncthreads();  // st_s initialised; the epilogue records written
+#pragma unroll
+  for (int k = 0; k < kStCount; ++k) {
+    const unsigned t = __reduce_add_sync(kFull, cnt[k]);
+    if (lane == 0 && t) atomicAdd(&st_s[k], t);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && s_cnt[0]) {
-    const int slot = blockIdx.x % kCtrSlots;
-    atomicAdd(&ctr->n_obs_eval[slot], s_cnt[0]);
-    atomicAdd(&ctr->n_edge_eval[slot], s_cnt[1]);
+  if (threadIdx.x < kStCount)
+    a.ws[kStatBase + (long long)blockIdx.x * kStatWords + threadIdx.x] = st_s[threadIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ws[0] = gridDim.x;
+    a.ws[1] = 0ull;  // the cull has no device-side wait
+  }
+  if (warp != 0) return;
+
+  // ---- 4. epilogues of the CTA's poses by warp 0 ---------------------------
+  {
+    const int j = lane >> 2;  // pose of the CTA, 4 lanes each
+    const long long pj = (long long)blockIdx.x * kPoses + j;
+    const bool vj = pj < a.P;
+    const float4 q = ep_pose[j];
+    const unsigned long long key = ep_key[j];
+    const bool none = key == ~0ull;
+    ObsRec o{0, 0, 0, 0};
+    if (!none) {
+      const int4 r = __ldg(&a.obs[ep_obs[j]].rec);
+      o = ObsRec{r.x, r.y, r.z, r.w};
+    }
+    const bool save = a.saved != nullptr;
+    const bool want_grad = save || a.dphi != nullptr;
+    PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
+    Grad rows;
+    rows.nrow = -1;
+    if constexpr (SOFT) {
+      if (vj && (lane & 3) == 0)
+        r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w, none, o,
+                                       a.vtx, a.far, want_grad, prm.eta);
+    } else {
+      r = epilogue_obstacle_coop<M, 4>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w,
+                                       none || !vj, o, a.vtx, a.far, want_grad, lane & 3,
+                                       save ? &rows : nullptr);
+    }
+    if (vj && (lane & 3) == 0) {
+      write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
+      if (!SOFT && save) write_saved(a.saved, pj, rows);
+    }
   }
 }
 
@@ -971,28 +992,26 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Cull workspace: a 256-byte header {CTAs of the last launch, error word},
+// then kStatWords counters per CTA (written, never accumulated: nothing to
+// clear before a launch).
+static size_t cull_workspace_bytes(long long P)
+{
+  const long long ctas = (std::max<long long>(P, 0) + 2 * kCullWarps - 1) / (2 * kCullWarps);
+  return 8 * (size_t)kStatBase + 8 * (size_t)kStatWords * (size_t)std::max<long long>(ctas, 1);
+}
+
 template <int M>
-struct ListEvalCall {
-  static int run(const FootprintK &F, const ParamsK &pk, const float4 *pose4, long long P,
-                 const psdf_scene *sc, const int *hist,
-                 const int *list, const float *ub, unsigned long long *keys,
-                 CullCounters *ctr, cudaStream_t st)
+struct CullCall {
+  static int run(const FootprintK &F, const ParamsK &pk, const CullArgs &a, bool net, dim3 grid,
+                 cudaStream_t st)
   {
-    const size_t smem = (size_t)(sc->max_blob_ext_bytes + 15) / 16 * 16;
     const bool soft = pk.eta > 0.f;
-    auto kern = soft ? eval_lists<M, true> : eval_lists<M, false>;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(eval_lists)");
-    }
-    const unsigned grid = (unsigned)sc->n_tiles * kTileCTAs;
-    // follows the proposal kernel: may start while it finishes
-    cudaError_t e = launch_pdl(kern, dim3(grid), dim3(kListThreads), smem, st, F, pk,
-                               pose4, P, (const TileHdr *)sc->d_tiles, sc->n_tiles,
-                               (const unsigned char *)sc->d_blob, hist, list, ub, keys, ctr);
-    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (eval_lists)");
+    auto kern = net ? (soft ? cull_kernel<M, true, true> : cull_kernel<M, true, false>)
+                    : (soft ? cull_kernel<M, false, true> : cull_kernel<M, false, false>);
+    kern<<<grid, kCullThreads, 0, st>>>(F, pk, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (cull)");
   }
 };
 
@@ -1091,7 +1110,8 @@ extern "C" int psdf_mlp_destroy(psdf_mlp *mlp)
 
 extern "C" size_t psdf_cull_workspace_bytes(int64_t P, const psdf_scene *scene)
 {
-  return cull_layout(P, scene ? scene->n_tiles : 1).total;
+  (void)scene;
+  return cull_workspace_bytes(P);
 }
 
 extern "C" int psdf_tile_features(const float *footprint, int32_t m, const psdf_scene *scene,
@@ -1186,81 +1206,79 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   FootprintK F;
   rc = make_footprint(footprint, m, scene->eps_seg, &F);
   if (rc) return rc;
-  if (P == 0) return PSDF_OK;
-  if (P > (1LL << 31) - 1) return fail(PSDF_ERR_CAPACITY, "P too large for the cull");
-  if (scene->n_tiles > kMaxScanTiles) return fail(PSDF_ERR_CAPACITY, "too many tiles for the cull");
-  const int T = scene->n_tiles;
-  if ((long long)P * std::max(T, 1) > (1LL << 31) - 1)
-    return fail(PSDF_ERR_CAPACITY, "poses x tiles too large for the cull's pair lists");
-  const CullLayout L = cull_layout(P, T);
   if (!workspace) return fail(PSDF_ERR_ARG, "workspace is NULL");
   if (((uintptr_t)workspace & 255u) != 0) return fail(PSDF_ERR_ARG, "workspace must be 256-byte aligned");
-  if (workspace_bytes < L.total)
+  if (workspace_bytes < cull_workspace_bytes(P))
     return fail(PSDF_ERR_CAPACITY, "workspace smaller than psdf_cull_workspace_bytes");
+  if (P > (1LL << 31) - 1) return fail(PSDF_ERR_CAPACITY, "P too large for the cull");
+  if (scene->n_tiles > kMaxScanTiles) return fail(PSDF_ERR_CAPACITY, "too many tiles for the cull");
+  if (scene->M >= (1 << 26)) return fail(PSDF_ERR_CAPACITY, "too many obstacles for the cull");
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
-  CullCounters *ctr = reinterpret_cast<CullCounters *>(ws);
-  unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
-  float4 *pose4 = reinterpret_cast<float4 *>(ws + L.pose4);
-  float *ub = reinterpret_cast<float *>(ws + L.ub);
-  int *prop = reinterpret_cast<int *>(ws + L.prop);
-  int *hist = reinterpret_cast<int *>(ws + L.hist);
-  int *list = reinterpret_cast<int *>(ws + L.list);
-  ParamsK pk{params->eps_sat, params->eta};
-  cudaError_t e;
-  {
-    const int words = (int)(L.clear_bytes / 4);
-    clear_words<<<std::min((words + 255) / 256, 64), 256, 0, st>>>(
-        reinterpret_cast<unsigned *>(ws), words);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch (clear)");
+  unsigned long long *ws = reinterpret_cast<unsigned long long *>(workspace);
+  if (P == 0) {  // no launch: the counters read as zero
+    cudaError_t e = cudaMemsetAsync(ws, 0, kStatBase * 8, st);
+    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "cudaMemsetAsync(cull counters)");
   }
-  if (T == 0) {
-    e = cudaMemsetAsync(keys, 0xff, 8 * (size_t)P, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(keys)");
-  } else {
-    const int K = opts->k;
-    const bool net = opts->mode == PSDF_PROPOSE_MLP;
-    // soft minimum: an obstacle's value lies below its hard distance when it
-    // is separated and at most log(K) / eta (K axes) when it penetrates, so
-    // the upper bound taken from distances is raised by that much
-    float ub_pad = 0.f;
-    if (params->eta > 0.f)
-      ub_pad = (float)(std::log((double)(m + scene->max_obs_edges)) / params->eta * (1.0 + 1e-5) +
+  const bool net = opts->mode == PSDF_PROPOSE_MLP;
+  CullArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.poses = poses;
+  a.P = P;
+  a.grid = scene->grid;
+  a.tile_ab = scene->d_tile_ab;
+  a.tile_info = scene->d_tile_info;
+  a.T = scene->n_tiles;
+  a.K = opts->k;
+  a.obs = scene->d_cull_obs;
+  a.vtx = scene->d_vtx;
+  a.far = scene->d_far;
+  // soft minimum: an obstacle's value lies below its hard distance when it
+  // is separated and at most log(K) / eta (K axes) when it penetrates, so
+  // the upper bound taken from distances is raised by that much
+  a.ub_pad = 0.f;
+  if (params->eta > 0.f)
+    a.ub_pad = (float)(std::log((double)(m + scene->max_obs_edges)) / params->eta * (1.0 + 1e-5) +
                        1e-6);
-    const unsigned pb = (unsigned)((P + 7) / 8);  // 4 warps x 2 poses per CTA
-    const uint32_t *frag = net ? mlp->d_frag : nullptr;
-    const float b2 = net ? mlp->b2 : 0.f;
-    {
-      ProfileScope prof("propose", st);
-#define PSDF_PROPOSE(KK)                                                                      \
-  e = launch_pdl(net ? propose<KK, true> : propose<KK, false>, dim3(pb), dim3(kPoseThreads), 0, \
-                 st, poses, (long long)P, (const TileHdr *)scene->d_tiles, T, scene->grid,      \
-                 F.radius, F.inner, ub_pad, (const unsigned char *)scene->d_blob, frag, b2,     \
-                 keys, pose4,                                                                   \
-                 ub,                                                                            \
-                 prop, hist, list, ctr);
-      switch (K) {
-        case 1: PSDF_PROPOSE(1) break;
-        case 2: PSDF_PROPOSE(2) break;
-        case 3: PSDF_PROPOSE(3) break;
-        default: PSDF_PROPOSE(4) break;
+  a.eps_axis = scene->eps_axis;
+  a.frag = net ? mlp->d_frag : nullptr;
+  a.b2 = net ? mlp->b2 : 0.f;
+  a.phi = phi;
+  a.dphi = dphi;
+  a.active = active;
+  a.saved = saved;
+  a.ws = ws;
+  const long long grid = (P + 2 * kCullWarps - 1) / (2 * kCullWarps);
+  // the scene into L2 when the launch reads a good part of it and it fits
+  // well within L2 (a few poses on a huge scene read only what they need)
+  {
+    const size_t scene_bytes = 32 * (size_t)scene->M + 36 * (size_t)scene->n_edges +
+                               32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles;
+    if (P >= 64 && scene_bytes <= (32u << 20)) {
+      auto add = [&](const void *ptr, size_t bytes) {
+        bytes &= ~(size_t)15;
+        if (!ptr || bytes == 0 || a.pf.n >= kMaxPrefetch) return;
+        a.pf.ptr[a.pf.n] = reinterpret_cast<const unsigned char *>(ptr);
+        a.pf.bytes[a.pf.n] = (long long)bytes;
+        a.pf.first[a.pf.n + 1] =
+            a.pf.first[a.pf.n] + ((long long)bytes + kPrefetchChunk - 1) / kPrefetchChunk;
+        ++a.pf.n;
+      };
+      if (scene->grid.nx > 0) {
+        add(scene->d_cell_off, 4 * ((size_t)scene->grid.nx * scene->grid.ny + 1));
+        add(scene->d_cell_aabbs, 16 * (size_t)scene->grid_entries);
+        add(scene->d_cell_info, 16 * (size_t)scene->grid_entries);
+      } else {
+        add(scene->d_tile_ab, 16 * (size_t)scene->n_tiles);
+        add(scene->d_tile_info, 16 * (size_t)scene->n_tiles);
       }
-#undef PSDF_PROPOSE
-      if (e != cudaSuccess) return cuda_fail(e, "kernel launch (propose)");
-    }
-    {
-      ProfileScope prof("cull_eval", st);
-      rc = dispatch_m_cull<ListEvalCall>(m, F, pk, (const float4 *)pose4, (long long)P, scene,
-                                         (const int *)hist, (const int *)list,
-                                         (const float *)ub, keys, ctr, st);
-      if (rc) return rc;
+      add(scene->d_cull_obs, sizeof(CullObs) * (size_t)scene->M);
+      add(scene->d_vtx, 32 * (size_t)scene->n_edges);
+      add(scene->d_far, 4 * (size_t)scene->n_edges);
     }
   }
-  rc = launch_epilogue(F, scene, poses, P, pk, keys, &ctr->err, phi, dphi, active, st, saved);
-  if (rc) return rc;
-  e = cudaGetLastError();
-  return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch");
+  ParamsK pk{params->eps_sat, params->eta};
+  ProfileScope prof("cull", st);
+  return dispatch_m_cull<CullCall>(m, F, pk, a, net, dim3((unsigned)grid), st);
 }
 
 extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
@@ -1293,21 +1311,25 @@ extern "C" int psdf_cull_stats_read(const void *workspace, void *stream, psdf_cu
   if (!workspace || !stats) return fail(PSDF_ERR_ARG, "NULL argument");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  CullCounters c;
-  e = cudaMemcpy(&c, workspace, sizeof(c), cudaMemcpyDeviceToHost);
+  unsigned long long hdr[2];
+  e = cudaMemcpy(hdr, workspace, sizeof(hdr), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(cull counters)");
-  auto sum = [](const unsigned long long (&v)[kCtrSlots]) {
-    unsigned long long t = 0;
-    for (int i = 0; i < kCtrSlots; ++i) t += v[i];
-    return (int64_t)t;
-  };
-  stats->evaluated_obstacles = sum(c.n_obs_eval);
-  stats->evaluated_edges = sum(c.n_edge_eval);
-  stats->proposed_items = sum(c.n_prop);
-  stats->fallback_items = sum(c.n_fb);
-  stats->fallback_poses = sum(c.fallback_poses);
-  stats->bound_evaluations = sum(c.n_bound);
-  stats->circle_evaluations = sum(c.n_circ);
-  if (c.err) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out");
+  std::vector<unsigned long long> w((size_t)hdr[0] * kStatWords);
+  if (!w.empty()) {
+    e = cudaMemcpy(w.data(), reinterpret_cast<const unsigned long long *>(workspace) + kStatBase,
+                   w.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(cull counters)");
+  }
+  unsigned long long sum[kStatWords] = {};
+  for (size_t b = 0; b < (size_t)hdr[0]; ++b)
+    for (int k = 0; k < kStatWords; ++k) sum[k] += w[b * kStatWords + k];
+  stats->evaluated_obstacles = (int64_t)sum[kStObs];
+  stats->evaluated_edges = (int64_t)sum[kStEdges];
+  stats->proposed_items = (int64_t)sum[kStProp];
+  stats->fallback_items = (int64_t)sum[kStFb];
+  stats->fallback_poses = (int64_t)sum[kStFbPoses];
+  stats->bound_evaluations = (int64_t)sum[kStBound];
+  stats->circle_evaluations = (int64_t)sum[kStCirc];
+  if (hdr[1]) return fail(PSDF_ERR_TIMEOUT, "a bounded device-side wait ran out");
   return PSDF_OK;
 }

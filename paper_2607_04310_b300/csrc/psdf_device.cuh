@@ -1066,26 +1066,21 @@ __device__ __forceinline__ void write_pose_out(const PoseOut &r, long long p, fl
   }
 }
 
-// Value, active pair and (if want_grad) pose gradient of one pose from its
-// 64-bit min-key: the winning obstacle is re-evaluated with its exact
-// candidate sets and the closed-form gradient of the active pair is taken
-// (Alg. 1, value + gradient).  row_obs is indexed by the key's rank (a caller
-// row of the pose's scene).
+// Value, active pair and (if want_grad) pose gradient of one pose whose
+// winning obstacle o is known (none: no obstacle at all): the obstacle is
+// re-evaluated with its exact candidate sets and the closed-form gradient of
+// the active pair is taken (Alg. 1, value + gradient).  c, s = cos, sin of
+// the pose's theta as sincosf gives them.
 template <int M, bool SOFT = false>
-__device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_sat,
-                                                 float eps_axis, float px, float py, float theta,
-                                                 unsigned long long key,
-                                                 const ObsRec *__restrict__ row_obs,
-                                                 const float4 *__restrict__ vtx,
-                                                 const int *__restrict__ far, bool want_grad,
-                                                 float eta = 0.f)
+__device__ __forceinline__ PoseOut epilogue_obstacle(const FootprintK &F, float eps_sat,
+                                                     float eps_axis, float px, float py, float c,
+                                                     float s, bool none, const ObsRec &o,
+                                                     const float4 *__restrict__ vtx,
+                                                     const int *__restrict__ far, bool want_grad,
+                                                     float eta = 0.f)
 {
   PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
-  if (key == ~0ull) return r;  // no obstacle at all
-  float s, c;
-  sincosf(theta, &s, &c);
-  const int rank = (int)(unsigned)(key & 0xffffffffu);
-  const ObsRec o = row_obs[rank];
+  if (none) return r;  // no obstacle at all
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
   prefetch_lines(vt, 32 * o.n);
   if (want_grad) prefetch_lines(far + o.vtx_global, 4 * o.n);
@@ -1113,27 +1108,43 @@ __device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_
   return r;
 }
 
-// epilogue_pose of the hard minimum by G lanes per pose (lane g of the
+// The same from the pose's 64-bit min-key: row_obs is indexed by the key's
+// rank (a caller row of the pose's scene).
+template <int M, bool SOFT = false>
+__device__ __forceinline__ PoseOut epilogue_pose(const FootprintK &F, float eps_sat,
+                                                 float eps_axis, float px, float py, float theta,
+                                                 unsigned long long key,
+                                                 const ObsRec *__restrict__ row_obs,
+                                                 const float4 *__restrict__ vtx,
+                                                 const int *__restrict__ far, bool want_grad,
+                                                 float eta = 0.f)
+{
+  if (key == ~0ull) return PoseOut{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
+  float s, c;
+  sincosf(theta, &s, &c);
+  const ObsRec o = row_obs[(int)(unsigned)(key & 0xffffffffu)];
+  return epilogue_obstacle<M, SOFT>(F, eps_sat, eps_axis, px, py, c, s, false, o, vtx, far,
+                                    want_grad, eta);
+}
+
+// epilogue_obstacle of the hard minimum by G lanes per pose (lane g of the
 // group; see obstacle_detail_coop): the detail is shared out over the
 // obstacle's edges, the gradient is taken by lane 0 of the group alone (the
-// other lanes return it as zero).  Every lane of the warp must call it.
+// other lanes return it as zero).  Every lane of the warp must call it (a
+// group without a pose passes none).
 template <int M, int G>
-__device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float eps_sat,
-                                                      float eps_axis, float px, float py,
-                                                      float theta, unsigned long long key,
-                                                      const ObsRec *__restrict__ row_obs,
-                                                      const float4 *__restrict__ vtx,
-                                                      const int *__restrict__ far,
-                                                      bool want_grad, int g,
-                                                      Grad *rows = nullptr)
+__device__ __forceinline__ PoseOut epilogue_obstacle_coop(const FootprintK &F, float eps_sat,
+                                                          float eps_axis, float px, float py,
+                                                          float c, float s, bool none,
+                                                          ObsRec o,
+                                                          const float4 *__restrict__ vtx,
+                                                          const int *__restrict__ far,
+                                                          bool want_grad, int g,
+                                                          Grad *rows = nullptr)
 {
   PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
   if (rows) rows->nrow = -1;  // no gradient
-  const bool none = key == ~0ull;
-  ObsRec o{0, 0, 0, 0};
-  if (!none) o = row_obs[(int)(unsigned)(key & 0xffffffffu)];
-  float s, c;
-  sincosf(theta, &s, &c);
+  if (none) o = ObsRec{0, 0, 0, 0};
   const float4 *vt = vtx + 2 * (long long)o.vtx_global;
   // the far-vertex indices the gradient reads, fetched while the detail runs
   if (want_grad && g == 0 && !none) prefetch_lines(far + o.vtx_global, 4 * o.n);
@@ -1150,6 +1161,27 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
     if (rows) *rows = gr;
   }
   return r;
+}
+
+// epilogue_obstacle_coop from the pose's 64-bit min-key (row_obs indexed by
+// the key's rank).
+template <int M, int G>
+__device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float eps_sat,
+                                                      float eps_axis, float px, float py,
+                                                      float theta, unsigned long long key,
+                                                      const ObsRec *__restrict__ row_obs,
+                                                      const float4 *__restrict__ vtx,
+                                                      const int *__restrict__ far,
+                                                      bool want_grad, int g,
+                                                      Grad *rows = nullptr)
+{
+  const bool none = key == ~0ull;
+  ObsRec o{0, 0, 0, 0};
+  if (!none) o = row_obs[(int)(unsigned)(key & 0xffffffffu)];
+  float s, c;
+  sincosf(theta, &s, &c);
+  return epilogue_obstacle_coop<M, G>(F, eps_sat, eps_axis, px, py, c, s, none, o, vtx, far,
+                                      want_grad, g, rows);
 }
 
 // Saved backward record of one pose (psdf_saved_grad, 4 float4): the pose

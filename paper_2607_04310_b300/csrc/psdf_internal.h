@@ -85,6 +85,18 @@ struct ObsRec {
   int tile;
 };
 
+// Obstacle record of the exact tile cull, one per obstacle in sorted (tile)
+// order: a circle containing the obstacle, the radius of a disc about its
+// centre inside it, and where the obstacle's vertex records are.
+struct CullObs {
+  float4 circ;  // {cx, cy, r, rin}
+  int4 rec;     // {first vertex record (vtx, sorted order), edges, rank, tile}
+};
+
+// What the cull reads of a tile beside its AABB: {first sorted obstacle,
+// obstacles, edges, tile index}.
+using TileInfo = int4;
+
 // Uniform grid over a scene's bounding box for the cull's tile lookups.
 // Cell (i, j) covers [x0 + i cs, x0 + (i + 1) cs) x [y0 + j cs, y0 + (j + 1) cs)
 // and lists, in increasing tile order, every tile whose AABB comes within
@@ -99,6 +111,7 @@ struct CullGrid {
   const int *off = nullptr;    // [nx * ny + 1] list offsets (device)
   const int *tl = nullptr;     // tile lists (device)
   const float4 *ab = nullptr;  // [entries] AABB of tile tl[i], beside it (device)
+  const int4 *info = nullptr;  // [entries] TileInfo of tile tl[i] (device)
 };
 
 }  // namespace psdf
@@ -121,6 +134,10 @@ struct psdf_scene {
   int64_t grid_entries = 0;
   int *d_cell_off = nullptr, *d_cell_tiles = nullptr;
   float4 *d_cell_aabbs = nullptr;
+  int4 *d_cell_info = nullptr;
+  psdf::CullObs *d_cull_obs = nullptr;  // [M] cull records in sorted order
+  float4 *d_tile_ab = nullptr;          // [n_tiles] AABBs
+  int4 *d_tile_info = nullptr;          // [n_tiles] TileInfo
   size_t device_bytes = 0;
   // host copies used for launch configuration
   int max_blob_bytes = 0;      // largest tile blob (obstacle + vertex records)
@@ -150,6 +167,9 @@ struct HostScene {
   std::vector<float4> vtx;
   std::vector<int> far;
   std::vector<ObsRec> row_obs;
+  std::vector<CullObs> cull_obs;  // [M] sorted order
+  std::vector<float4> tile_ab;    // [T]
+  std::vector<int4> tile_info;    // [T]
 };
 int build_host_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> &obs,
                      int tile_edges, const psdf_params *prm, HostScene *hs);

@@ -82,6 +82,10 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_cell_off);
   cudaFree(s->d_cell_tiles);
   cudaFree(s->d_cell_aabbs);
+  cudaFree(s->d_cell_info);
+  cudaFree(s->d_cull_obs);
+  cudaFree(s->d_tile_ab);
+  cudaFree(s->d_tile_info);
   delete s;
 }
 
@@ -195,6 +199,9 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
   std::vector<int> far(n_edges);
   std::vector<ObsRec> row_obs(std::max<int64_t>(rows_total, 0), ObsRec{0, 0, 0, -1});
   std::vector<unsigned char> blob;
+  std::vector<CullObs> cull_obs(M);
+  std::vector<float4> tile_ab(T);
+  std::vector<int4> tile_info(T);
   int64_t vglob = 0;
   int max_blob = 0, max_blob_ext = 0;
   for (int t = 0; t < T; ++t) {
@@ -250,6 +257,8 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
         }
         const float rinf = rin > 1e-6 ? (float)(rin * (1.0 - 1e-5) - 1e-7) : 0.f;
         circ[s - s0] = make_float4(cxf, cyf, rf, rinf);
+        cull_obs[s].circ = circ[s - s0];
+        cull_obs[s].rec = make_int4((int)vglob, o.n, (int)o.first_row, t);
       }
       for (int k = 0; k < o.n; ++k) {
         double ax = e[4 * k], ay = e[4 * k + 1], bx = e[4 * k + 2], by = e[4 * k + 3];
@@ -285,6 +294,8 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
     }
     std::memcpy(h.aabb, ab, sizeof(ab));
     tiles[t] = h;
+    tile_ab[t] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+    tile_info[t] = make_int4(s0, nobs, nv, t);
     max_blob = std::max(max_blob, bytes);
     max_blob_ext = std::max(max_blob_ext, bytes + 16 * nobs);
   }
@@ -306,6 +317,9 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
   hs->vtx.swap(vtx);
   hs->far.swap(far);
   hs->row_obs.swap(row_obs);
+  hs->cull_obs.swap(cull_obs);
+  hs->tile_ab.swap(tile_ab);
+  hs->tile_info.swap(tile_info);
   return PSDF_OK;
 }
 
@@ -317,13 +331,14 @@ int build_host_scene(const float *rows, int64_t rows_total, const std::vector<Ob
 // No grid when the lists would grow far beyond the tile count (strongly
 // uneven tiles): lookups then scan all tiles.
 void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<int> *off,
-                     std::vector<int> *tl, std::vector<float4> *ab)
+                     std::vector<int> *tl, std::vector<float4> *ab, std::vector<int4> *info)
 {
   *g = CullGrid();
   *cell = 0.f;
   off->clear();
   tl->clear();
   ab->clear();
+  info->clear();
   const int T = hs.T;
   if (T == 0) return;
   const double x0 = hs.bb[0], y0 = hs.bb[1];
@@ -354,6 +369,7 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
   for (size_t c = 0; c < (size_t)nx * ny; ++c) (*off)[c + 1] = (*off)[c] + cnt[c];
   tl->assign((size_t)total, 0);
   ab->assign((size_t)total, make_float4(0.f, 0.f, 0.f, 0.f));
+  info->assign((size_t)total, make_int4(0, 0, 0, 0));
   std::vector<int> cur(off->begin(), off->end() - 1);
   for (int t = 0; t < T; ++t) {  // increasing t: every list sorted
     const float *a = hs.tiles[t].aabb;
@@ -365,6 +381,7 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
         const int e = cur[(size_t)j * nx + i]++;
         (*tl)[e] = t;
         (*ab)[e] = make_float4(a[0], a[1], a[2], a[3]);
+        (*info)[e] = hs.tile_info[t];
       }
   }
   g->x0 = hs.bb[0];
@@ -400,17 +417,23 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   if (!rc) rc = dev_upload(&s->d_vtx, hs.vtx, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_far, hs.far, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_row_obs, hs.row_obs, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_cull_obs, hs.cull_obs, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_tile_ab, hs.tile_ab, st, &s->device_bytes);
+  if (!rc) rc = dev_upload(&s->d_tile_info, hs.tile_info, st, &s->device_bytes);
   std::vector<int> cell_off, cell_tiles;
   std::vector<float4> cell_aabbs;
-  build_cull_grid(hs, &s->grid, &s->grid_cell, &cell_off, &cell_tiles, &cell_aabbs);
+  std::vector<int4> cell_info;
+  build_cull_grid(hs, &s->grid, &s->grid_cell, &cell_off, &cell_tiles, &cell_aabbs, &cell_info);
   s->grid_entries = (int64_t)cell_tiles.size();
   if (!rc && s->grid.nx > 0) {
     rc = dev_upload(&s->d_cell_off, cell_off, st, &s->device_bytes);
     if (!rc) rc = dev_upload(&s->d_cell_tiles, cell_tiles, st, &s->device_bytes);
     if (!rc) rc = dev_upload(&s->d_cell_aabbs, cell_aabbs, st, &s->device_bytes);
+    if (!rc) rc = dev_upload(&s->d_cell_info, cell_info, st, &s->device_bytes);
     s->grid.off = s->d_cell_off;
     s->grid.tl = s->d_cell_tiles;
     s->grid.ab = s->d_cell_aabbs;
+    s->grid.info = s->d_cell_info;
   }
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);

@@ -140,6 +140,9 @@ _SIGS = {
     "psdf_backward_batched": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "psdf_debug_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32,
                                                  ctypes.POINTER(ctypes.c_uint32)]),
+    "psdf_measure_fp32_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), _vp]),
     "psdf_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "psdf_profile_reset": (ctypes.c_int, []),
     "psdf_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -456,6 +459,16 @@ def psdf_eval_grad_noalloc(footprint: np.ndarray, scene: Scene, poses, params: P
     return int(load().psdf_eval_grad_noalloc(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
                                              poses.shape[0], ctypes.byref(params), _ptr(phi),
                                              _ptr(dphi), _ptr(active), _stream(stream)))
+
+
+def psdf_measure_fp32_peak(paired: bool, iters: int = 200000, reps: int = 5,
+                           stream=None) -> Tuple[float, float]:
+    """(TFLOP/s, ms) of the library's FP32 FMA microbenchmark (best of reps)."""
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(load().psdf_measure_fp32_peak(1 if paired else 0, int(iters), int(reps),
+                                         ctypes.byref(tf), ctypes.byref(ms), _stream(stream)))
+    return float(tf.value), float(ms.value)
 
 
 DEFAULT_WAIT_LIMIT = 1 << 22

@@ -51,6 +51,30 @@ def flops_propose(bound_evaluations: int, circle_evaluations: int) -> float:
     return 7.0 * bound_evaluations + 10.0 * circle_evaluations
 
 
+def pair_flops_fixed(m: int) -> float:
+    """The fixed per-(pose, edge) flop count of the hot path's stages,
+    independent of any kernel: transform 14, vertex -> edge 16 m, edge
+    vertex -> robot edge 14 m, robot-axis projections 5 m, obstacle-axis
+    interval 5 m + 12; F(m) = 40 m + 26 (186 at m = 4, 346 at m = 8).  It
+    counts work the kernels share across an edge's two ends or skip (the
+    far-end clamps), so it exceeds the instruction-level count above."""
+    return 40.0 * m + 26.0
+
+
+def flops_fixed(m: int, pairs: float) -> float:
+    """Flops of `pairs` evaluated (pose, edge) pairs by the fixed count."""
+    return pair_flops_fixed(m) * float(pairs)
+
+
+MLP_FLOPS_PER_ROW = (16 * 64 + 64 * 1) * 2  # one network score: 2,176 flops
+
+
+def flops_network(rows: float) -> float:
+    """Tensor-core flops of the tile-proposal network for `rows` scored
+    (pose, tile) rows (16 -> 64 -> 1, FP16 operands)."""
+    return MLP_FLOPS_PER_ROW * float(rows)
+
+
 def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
     """Dense FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sms * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
