@@ -6,20 +6,19 @@
 //                grid), ordered by their conservative bound; the pose
 //                proposes its K nearest tiles, or the K best of its 8 nearest
 //                re-ranked by the tile-proposal network on tensor cores
-//   pass 1       an upper bound UB >= phi from the circles of the proposed
-//                tiles' obstacles; every obstacle there whose circle bound
-//                does not exceed UB is evaluated exactly: value v1 >= phi
-//   pass 2       every other tile whose bound does not exceed v1 (the cell's
-//                list holds them all while v1's reach is within the cell's;
-//                else every tile is tested); obstacles whose circle bound
-//                exceeds v1 are skipped, the others evaluated exactly
+//   upper bound  UB >= phi from the circles of the proposed tiles' obstacles
+//   evaluation   every tile whose bound does not exceed UB (the cell's list
+//                holds them all while UB's reach is within the cell's; else
+//                every tile is tested), the proposed ones always; obstacles
+//                whose circle bound exceeds UB are skipped, the others
+//                evaluated exactly
 //   epilogue     as for the full scan, on the winning obstacle
 // The scene's arrays are brought into L2 by bulk prefetches (TMA) at the
 // start of the launch.  Every tile holding a value at or below phi has a
-// bound <= phi <= v1, so it is evaluated; every obstacle skipped has a value
-// above the threshold, which is never below phi.  The minimum over 64-bit
-// keys does not depend on evaluation order, so the result equals the full
-// scan's bit for bit.
+// bound <= phi <= UB, so it is evaluated; every obstacle skipped has a value
+// above UB, which is never below phi.  The minimum over 64-bit keys does not
+// depend on evaluation order, so the result equals the full scan's bit for
+// bit.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -309,14 +308,16 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
 // the fused cull: each pose's proposals, exact evaluation and epilogue by
 // its own 16 lanes, in one launch
 // ---------------------------------------------------------------------------
-constexpr int kCullThreads = 128;  // 4 warps x 2 poses
+constexpr int kCullThreads = 256;  // 8 warps x 2 poses
 constexpr int kCullWarps = kCullThreads / 32;
+constexpr int kPoses = 2 * kCullWarps;  // poses per CTA
 constexpr int kRL = 4;             // best tiles a lane keeps from its ranking pass
-constexpr int kFilt = 4;           // circle bounds a lane tests per round
+constexpr int kFilt = 8;           // circle bounds a thread tests per block
 constexpr int kItemLanes = 4;      // lanes per evaluated (pose, obstacle) item
-constexpr int kItemsPerRound = 32 / kItemLanes;
-constexpr int kQueue = 32 * kFilt + kItemsPerRound;  // a round's appends + leftovers
-constexpr int kSegs = 16;          // tiles of one flattened pass (one per lane of a half)
+constexpr int kGroups = kCullThreads / kItemLanes;  // items evaluated per pass
+constexpr int kSegCap = kPoses * 16;  // segments of one round: 16 tiles per pose
+constexpr int kSegsPerPass = kCullThreads / 8;  // segments whose circles a pass tests
+constexpr int kQCap = 2 * kCullThreads * kFilt;  // queued (pose, obstacle) items: two steps
 constexpr int kStatWords = 8;      // counters per CTA in the workspace
 constexpr int kStatBase = 32;      // first counter word (the header is 256 bytes)
 constexpr long long kPrefetchChunk = 16384;  // bytes per bulk L2 prefetch
@@ -349,6 +350,7 @@ struct CullArgs {
   const CullObs *obs;
   const float4 *vtx;
   const int *far;
+  const ObsRec *row_obs;    // obstacle record of each caller row (the key's rank)
   float ub_pad;             // soft minimum: most a penetrating obstacle's value exceeds 0
   float eps_axis;
   const uint32_t *frag;     // network fragments (NET)
@@ -401,16 +403,6 @@ __device__ __forceinline__ float tile_lb_value(float4 ab, float px, float py, fl
   return lb > 0.f ? lb * lb * (1.f - 1e-6f) : -kInf;
 }
 
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
-{
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
-}
-
 // Obstacle (sorted index) of the flattened position f over a half's tiles:
 // tile j holds positions st[j] .. st[j + 1] - 1, its obstacles from s0[j].
 __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int nseg, int f)
@@ -420,51 +412,8 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
   return s0[j] + (f - st[j]);
 }
 
-// Per-lane running minimum of one pose half's keys (and the obstacle).
-struct HalfBest {
-  unsigned long long k0 = ~0ull, k1 = ~0ull;
-  int s0 = 0, s1 = 0;
-  __device__ __forceinline__ void add(int h, unsigned long long k, int s)
-  {
-    if (h == 0) {
-      if (k < k0) { k0 = k; s0 = s; }
-    } else {
-      if (k < k1) { k1 = k; s1 = s; }
-    }
-  }
-};
-
-// The first n queued (obstacle << 5 | lane) items of the warp, kItemLanes
-// lanes per item (the obstacle's edges shared out, obstacle_value_coop),
-// kItemsPerRound items a round; every lane takes part in every round.  Each
-// item's pose is the one of the lane that queued it.
-template <int M, bool SOFT>
-__device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &prm,
-                                           const CullArgs &a, const int *qw, int n, int lane,
-                                           float px, float py, float c, float s, HalfBest &hb,
-                                           unsigned &n_obs, unsigned &n_edge)
-{
-  const int g = lane % kItemLanes;
-  for (int r0 = 0; r0 < n; r0 += kItemsPerRound) {
-    const int slot = r0 + lane / kItemLanes;
-    const bool live = slot < n;
-    const int item = live ? qw[slot] : 0;
-    const int src = item & 31, so = item >> 5;
-    const float ipx = __shfl_sync(kFull, px, src), ipy = __shfl_sync(kFull, py, src);
-    const float ic = __shfl_sync(kFull, c, src), is = __shfl_sync(kFull, s, src);
-    int4 rec = make_int4(0, 0, 0, 0);
-    if (live) rec = __ldg(&a.obs[so].rec);
-    const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
-        F, ipx, ipy, ic, is, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat, prm.eta, g);
-    if (live && g == 0) {
-      hb.add(src >> 4, pack_key(v, rec.z), so);
-      ++n_obs;
-      n_edge += (unsigned)rec.y;
-    }
-  }
-}
-
-// One warp = 2 poses, 16 lanes each (lanes 0-15 pose a, 16-31 pose b).
+// One CTA = 16 poses; one warp = 2 poses, 16 lanes each (lanes 0-15 pose
+// a, 16-31 pose b) for the per-pose stages:
 //  1. ranking: the tiles of the pose's cell in the cull grid (every tile
 //     within one cell size of it), else all tiles; lane hl takes entries hl,
 //     hl + 16, ... and keeps its 4 smallest AABB distances; rounds of a
@@ -472,47 +421,55 @@ __device__ __forceinline__ void eval_items(const FootprintK &F, const ParamsK &p
 //     proposes its K nearest tiles, or (NET) the K best network scores among
 //     its 8 nearest (2 poses x 8 candidates = 16 rows of one tensor-core
 //     pass).
-//  2. pass 1: an upper bound UB >= phi from the circles of the proposed
-//     tiles' obstacles; those whose circle bound does not exceed UB are
-//     evaluated exactly.  Their minimum key is phi's first value v1 >= phi.
-//  3. pass 2: every other tile whose bound does not exceed v1 -- from the
-//     cell's list when those all lie within the grid's reach, else from all
-//     tiles -- in chunks of 16 tiles, their obstacles flattened over the 16
-//     lanes; obstacles whose circle bound exceeds v1 are skipped, the others
-//     evaluated exactly.
-//     Both passes queue their surviving (pose, obstacle) items in one
-//     warp-wide queue, evaluated in rounds of 8 items (4 lanes each) at one
-//     place in the code, so that the kernel's instruction footprint stays
-//     small.
-//  4. epilogue of every winning obstacle of the CTA's 8 poses by one warp
-//     (4 lanes per pose, or one for the soft minimum): value, active pair,
-//     gradient, saved backward rows.
+//  2. an upper bound UB >= phi from the circles of the proposed tiles'
+//     obstacles.
+// then, by the whole CTA, in rounds over chunks of 16 list entries per pose
+// (the cell's list when every tile whose bound does not exceed UB lies
+// within the grid's reach, else all tiles):
+//  3. each pose's tiles of the chunk whose bound does not exceed its UB (the
+//     proposed ones always) join the round's list of segments (pose, first
+//     obstacle, obstacles);
+//  4. 16 threads per segment test its obstacles' circle bounds against the
+//     pose's UB; the survivors go to one CTA-wide queue, evaluated exactly
+//     by 4 lanes each, and merged into the pose's 64-bit key in shared
+//     memory (atomicMin).  Sharing the work over the CTA's 256 threads keeps
+//     a pose with several nearby tiles from stretching its own warp.
+//  5. epilogue of every pose (4 lanes each, or one for the soft minimum) by
+//     the first two warps: value, active pair, gradient, saved rows.
 // No skipped tile or obstacle can hold a value at or below phi, and the key
 // minimum does not depend on the order of evaluation, so the outputs equal
 // the full scan's bit for bit.
 template <int M, bool NET, bool SOFT>
-__global__ void __launch_bounds__(kCullThreads, 4)
+__global__ void __launch_bounds__(kCullThreads, 2)
     cull_kernel(const FootprintK F, const ParamsK prm, const CullArgs a)
 {
-  constexpr int kPoses = 2 * kCullWarps;  // poses per CTA
-  __shared__ int q_s[kCullWarps][kQueue];
-  __shared__ int seg_s0[kCullWarps][2][kSegs];
-  __shared__ int seg_st[kCullWarps][2][kSegs + 1];
+  __shared__ int ub_s0[kCullWarps][2][kMaxK + 1];  // proposed tiles, flattened
+  __shared__ int ub_st[kCullWarps][2][kMaxK + 1];
   __shared__ int cand_s[kCullWarps][2][kPre];
   __shared__ float score_s[kCullWarps][2][kPre];
-  __shared__ float4 ep_pose[kPoses];
-  __shared__ unsigned long long ep_key[kPoses];
-  __shared__ int ep_obs[kPoses];
+  __shared__ float4 pose_s[kPoses];
+  __shared__ float thr_s[kPoses];
+  __shared__ unsigned long long key_s[kPoses];
+  __shared__ int seg_first[kSegCap], seg_n[kSegCap];
+  __shared__ unsigned char seg_pose[kSegCap];
+  __shared__ int q_s[kQCap];
+  __shared__ int nseg_s, nq_s;
   __shared__ unsigned st_s[kStCount];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int half = lane >> 4, hl = lane & 15;
   const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
-  const long long p = ((long long)blockIdx.x * kCullWarps + warp) * 2 + half;
+  const int j = 2 * warp + half;  // the pose within the CTA
+  const long long p = (long long)blockIdx.x * kPoses + j;
   const bool valid = p < a.P;
-  int *qw = q_s[warp];
-  int *sg0 = seg_s0[warp][half], *sgt = seg_st[warp][half];
-  if (threadIdx.x < kStCount) st_s[threadIdx.x] = 0u;
-  if (threadIdx.x == 0) prefetch_scene(a.pf);
+  int *sg0 = ub_s0[warp][half], *sgt = ub_st[warp][half];
+  if (tid < kStCount) st_s[tid] = 0u;
+  if (tid < kPoses) key_s[tid] = ~0ull;
+  if (tid == 0) {
+    nseg_s = 0;
+    nq_s = 0;
+    prefetch_scene(a.pf);
+  }
   // a following kernel (the backward) may launch now; it waits for this grid
   pdl_trigger();
   float px = 0.f, py = 0.f, th = 0.f;
@@ -539,18 +496,29 @@ __global__ void __launch_bounds__(kCullThreads, 4)
     sc[i] = kInf;
     id[i] = -1;
   }
-  {
-    int i = E.lo + hl;
-    for (; i + 16 < E.hi; i += 32) {
-      const float4 a0 = __ldg(E.ab + i), a1 = __ldg(E.ab + i + 16);
-      topk_insert<kRL>(sc, id, aabb_d2(a0, px, py), i - E.lo);
-      topk_insert<kRL>(sc, id, aabb_d2(a1, px, py), i + 16 - E.lo);
-      n_bound += 2;
-    }
+  // the lane's first two entries (hl, hl + 16) stay in registers for the
+  // tile tests below (cell lists rarely hold more than 32)
+  float4 kab[2];
+  int4 kinf[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int i = E.lo + hl + 16 * q;
+    kab[q] = make_float4(kInf, kInf, -kInf, -kInf);
+    kinf[q] = make_int4(0, 0, 0, -1);
     if (i < E.hi) {
-      topk_insert<kRL>(sc, id, aabb_d2(__ldg(E.ab + i), px, py), i - E.lo);
+      kab[q] = __ldg(E.ab + i);
+      kinf[q] = __ldg(E.info + i);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (E.lo + hl + 16 * q < E.hi) {
+      topk_insert<kRL>(sc, id, aabb_d2(kab[q], px, py), hl + 16 * q);
       ++n_bound;
     }
+  for (int i = E.lo + hl + 32; i < E.hi; i += 16) {
+    topk_insert<kRL>(sc, id, aabb_d2(__ldg(E.ab + i), px, py), i - E.lo);
+    ++n_bound;
   }
   // rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys (the
   // top 16 bits of the squared distance -- not negative, so its bits order
@@ -630,14 +598,23 @@ __global__ void __launch_bounds__(kCullThreads, 4)
       if (i >= K) best[i] = -1;
   }
 
-  // ---- 2. pass 1 set-up: the proposed tiles, the upper bound -------------
+  // ---- 2. the upper bound: circles of the proposed tiles' obstacles -------
   int ptile[kMaxK];
   int nseg = 0, N = 0;
 #pragma unroll
   for (int i = 0; i < kMaxK; ++i) {
+    // entry best[i] of the half: lane best % 16, register slot best / 16
+    // (a load for entries beyond the kept ones)
+    const int b = best[i];
+    const int slot = b >= 0 ? b >> 4 : 0;
+    int4 kept = slot == 0 ? kinf[0] : kinf[1];
+    int4 inf;
+    inf.x = __shfl_sync(kFull, kept.x, (half << 4) + (b & 15));
+    inf.y = __shfl_sync(kFull, kept.y, (half << 4) + (b & 15));
+    inf.w = __shfl_sync(kFull, kept.w, (half << 4) + (b & 15));
+    if (b >= 32) inf = __ldg(E.info + E.lo + b);
     ptile[i] = -1;
-    if (best[i] >= 0) {
-      const int4 inf = __ldg(E.info + E.lo + best[i]);
+    if (b >= 0) {
       ptile[i] = inf.w;
       if (hl == 0) {
         sg0[nseg] = inf.x;
@@ -650,22 +627,13 @@ __global__ void __launch_bounds__(kCullThreads, 4)
   if (hl == 0) sgt[nseg] = N;
   const int n_prop = nseg;
   __syncwarp();
-  // the circles of the lane's first round stay in registers for the first
-  // round of circle tests below
-  float4 cc0[kFilt];
-  int so0[kFilt];
   float ubp = kInf;
   for (int f0 = hl; f0 < N; f0 += 16 * kFilt) {
     float4 cc[kFilt];
-    int so[kFilt];
 #pragma unroll
     for (int q = 0; q < kFilt; ++q) {
       const int f = f0 + 16 * q;
-      so[q] = 0;
-      if (f < N) {
-        so[q] = flat_obstacle(sg0, sgt, nseg, f);
-        cc[q] = __ldg(&a.obs[so[q]].circ);
-      }
+      if (f < N) cc[q] = __ldg(&a.obs[flat_obstacle(sg0, sgt, nseg, f)].circ);
     }
 #pragma unroll
     for (int q = 0; q < kFilt; ++q)
@@ -673,13 +641,6 @@ __global__ void __launch_bounds__(kCullThreads, 4)
         ubp = fminf(ubp, circle_ub(cc[q], px, py, F.radius, F.inner));
         ++n_circ;
       }
-    if (f0 == hl) {
-#pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        cc0[q] = cc[q];
-        so0[q] = so[q];
-      }
-    }
   }
   {  // 16-lane minimum (ubp >= 0, so its bits order like the value)
     const unsigned u = __float_as_uint(ubp);
@@ -688,154 +649,150 @@ __global__ void __launch_bounds__(kCullThreads, 4)
     ubp = __uint_as_float(half ? u1 : u0);
   }
   ubp += a.ub_pad;
-
-  // ---- 2-3. both passes: circle tests, queued items, exact evaluation ----
-  // One loop: each iteration tests one round of circles (kFilt a lane) of
-  // the current run of tiles and evaluates the queue's whole rounds; at the
-  // end of pass 1 (and of the last run) the queue is drained.
-  HalfBest hb;
-  int nq = 0;  // queued items of the warp (uniform)
-  int pass = 1, ch = 0, nch = 0, k0 = 0;
-  float thr = ub_value(ubp), v1 = kInf;
-  Entries E2 = E;
-  int n_fb = 0;
-  int span = N > hl ? (N - hl + 15) / 16 : 0;
-  span = (int)__reduce_max_sync(kFull, (unsigned)span);
-  for (;;) {
-    // one round of circle tests: positions hl + 16 (k0 + q) of the run
-    if (k0 < span) {
-      bool keep[kFilt];
-      int so[kFilt];
-#pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        const int f = hl + 16 * (k0 + q);
-        keep[q] = false;
-        so[q] = 0;
-        if (f < N) {
-          float4 cq;
-          if (pass == 1 && k0 == 0) {
-            so[q] = so0[q];
-            cq = cc0[q];
-          } else {
-            so[q] = flat_obstacle(sg0, sgt, nseg, f);
-            cq = __ldg(&a.obs[so[q]].circ);
-          }
-          keep[q] = !(circle_lb_value(cq, px, py, F.radius) > thr);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        const unsigned m = __ballot_sync(kFull, keep[q]);
-        if (keep[q]) qw[nq + __popc(m & ((1u << lane) - 1u))] = (so[q] << 5) | lane;
-        nq += __popc(m);
-      }
-      k0 += kFilt;
-    }
-    const bool run_done = k0 >= span;
-    const bool last = run_done && (pass == 1 || ch + 1 >= nch);
-    // evaluate whole rounds; everything when pass 1 or the last run ends
-    const int todo = last ? nq : nq / kItemsPerRound * kItemsPerRound;
-    if (todo > 0) {
-      __syncwarp();
-      const int g = lane % kItemLanes;
-      for (int r0 = 0; r0 < todo; r0 += kItemsPerRound) {
-        const int slot = r0 + lane / kItemLanes;
-        const bool live = slot < todo;
-        const int item = live ? qw[slot] : 0;
-        const int src = item & 31, so = item >> 5;
-        const float ipx = __shfl_sync(kFull, px, src), ipy = __shfl_sync(kFull, py, src);
-        const float ic = __shfl_sync(kFull, c, src), is = __shfl_sync(kFull, s, src);
-        int4 rec = make_int4(0, 0, 0, 0);
-        if (live) rec = __ldg(&a.obs[so].rec);
-        const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
-            F, ipx, ipy, ic, is, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat, prm.eta, g);
-        if (live && g == 0) {
-          hb.add(src >> 4, pack_key(v, rec.z), so);
-          ++n_obs;
-          n_edge += (unsigned)rec.y;
-        }
-      }
-      const int rest = nq - todo;
-      const int v = lane < rest ? qw[todo + lane] : 0;
-      __syncwarp();
-      if (lane < rest) qw[lane] = v;
-      __syncwarp();
-      nq = rest;
-    }
-    if (!run_done) continue;
-    if (pass == 2 && ch + 1 >= nch) break;
-    if (pass == 1) {
-      // each pose's first value: the minimum over its evaluated obstacles
-      const unsigned long long b0 = warp_min_u64(hb.k0), b1 = warp_min_u64(hb.k1);
-      const unsigned long long bk = half ? b1 : b0;
-      v1 = bk == ~0ull ? kInf : from_ordered_bits((unsigned)(bk >> 32));
-      // every tile whose bound does not exceed v1 lies within cand_radius of p
-      const float um = v1 > 0.f ? sqrtf(v1) * (1.f + 1e-6f) : 0.f;
-      const bool in_cell = cell >= 0 && cand_radius(um, F.radius) <= a.grid.reach_q;
-      E2 = entries_of(a, cell, in_cell);
-      if (!valid) E2.hi = E2.lo;
-      nch = (E2.hi - E2.lo + 15) / 16;
-      nch = (int)__reduce_max_sync(kFull, (unsigned)nch);
-      pass = 2;
-      ch = 0;
-      thr = v1;
-      if (nch == 0) break;
-    } else {
-      ++ch;
-    }
-    // the next run: chunk ch of pass 2, its passing tiles compacted in lane
-    // order (first obstacles, starts of their obstacle runs)
-    __syncwarp();  // the segment arrays of the previous run are done with
-    {
-      const int i = E2.lo + ch * 16 + hl;
-      bool passing = false;
-      int4 inf = make_int4(0, 0, 0, 0);
-      if (i < E2.hi) {
-        const float4 ab = __ldg(E2.ab + i);
-        inf = __ldg(E2.info + i);
-        ++n_bound;
-        bool proposed = false;
-#pragma unroll
-        for (int q = 0; q < kMaxK; ++q) proposed |= ptile[q] == inf.w;
-        passing = !proposed && !(tile_lb_value(ab, px, py, F.radius) > v1);
-      }
-      const unsigned m = __ballot_sync(kFull, passing) & hmask;
-      nseg = __popc(m);
-      int x = passing ? inf.y : 0;
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o, 16);
-        if (hl >= o) x += y;
-      }
-      N = __shfl_sync(kFull, x, (half << 4) + 15);
-      if (passing) {
-        const int pos = __popc(m & ((1u << lane) - 1u));
-        sg0[pos] = inf.x;
-        sgt[pos] = x - inf.y;
-      }
-      if (hl == 0) sgt[nseg] = N;
-      n_fb += nseg;
-      __syncwarp();
-    }
-    k0 = 0;
-    span = N > hl ? (N - hl + 15) / 16 : 0;
-    span = (int)__reduce_max_sync(kFull, (unsigned)span);
-  }
-  unsigned long long bk;
-  int bs;
-  {
-    const unsigned long long k0w = warp_min_u64(hb.k0), k1w = warp_min_u64(hb.k1);
-    const int w0 = __ffs(__ballot_sync(kFull, hb.k0 == k0w)) - 1;
-    const int w1 = __ffs(__ballot_sync(kFull, hb.k1 == k1w)) - 1;
-    const int o0 = __shfl_sync(kFull, hb.s0, w0), o1 = __shfl_sync(kFull, hb.s1, w1);
-    bk = half ? k1w : k0w;
-    bs = half ? o1 : o0;
-  }
+  // every tile whose bound does not exceed UB lies within cand_radius(UB) of
+  // p: the cell's list holds them all while that is within the grid's reach
+  const float thr = ub_value(ubp);
+  const bool in_cell = cell >= 0 && cand_radius(ubp, F.radius) <= a.grid.reach_q;
+  Entries E2 = entries_of(a, cell, in_cell);
+  if (!valid) E2.hi = E2.lo;
+  const bool same = E2.ab == E.ab && E2.lo == E.lo;  // the ranking's entries
+  const int nch = (E2.hi - E2.lo + 15) / 16;
   if (hl == 0) {
-    const int j = 2 * warp + half;
-    ep_pose[j] = make_float4(px, py, c, s);
-    ep_key[j] = valid ? bk : ~0ull;
-    ep_obs[j] = bs;
+    pose_s[j] = make_float4(px, py, c, s);
+    thr_s[j] = thr;
+  }
+  __syncthreads();  // the CTA's counters and keys initialised
+
+  // ---- 3-4. rounds of tile tests, circle tests and exact evaluations -------
+  // A round collects, for every pose, the passing tiles of its next chunks
+  // of 16 entries while they fit its share of the round's segments (16; a
+  // chunk never holds more, so every round makes progress), then tests the
+  // circles of all collected segments and evaluates the survivors.
+  int n_fb = 0;
+  int ch = 0;  // this pose's next chunk
+  for (;;) {
+    {
+      int used = 0;  // segments this pose added in this round (uniform over the half)
+      for (; ch < nch; ++ch) {
+        const int i = E2.lo + ch * 16 + hl;
+        bool passing = false, proposed = false;
+        int4 inf = make_int4(0, 0, 0, 0);
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < E2.hi) {
+          if (same && ch < 2) {  // the ranking pass's entries, in registers
+            ab = ch == 0 ? kab[0] : kab[1];
+            inf = ch == 0 ? kinf[0] : kinf[1];
+          } else {
+            ab = __ldg(E2.ab + i);
+            inf = __ldg(E2.info + i);
+          }
+#pragma unroll
+          for (int q = 0; q < kMaxK; ++q) proposed |= ptile[q] == inf.w;
+          passing = proposed || !(tile_lb_value(ab, px, py, F.radius) > thr);
+        }
+        const unsigned m = __ballot_sync(hmask, passing) & hmask;
+        if (used + __popc(m) > 16) break;  // the rest next round
+        if (i < E2.hi) ++n_bound;
+        n_fb += __popc(__ballot_sync(hmask, passing && !proposed) & hmask);
+        int base = 0;
+        if (hl == 0 && m) base = atomicAdd(&nseg_s, __popc(m));
+        base = __shfl_sync(hmask, base, half << 4);
+        if (passing) {
+          const int pos = base + __popc(m & ((1u << lane) - 1u));
+          seg_first[pos] = inf.x;
+          seg_n[pos] = inf.y;
+          seg_pose[pos] = (unsigned char)j;
+        }
+        used += __popc(m);
+      }
+    }
+    const bool more = ch < nch;  // this pose has chunks left for later rounds
+    __syncthreads();
+    const int nsg = nseg_s;
+    // circle tests: 8 threads per segment, kSegsPerPass segments a pass;
+    // thread t takes segment t / 8 (+ kSegsPerPass per pass) and, in step b
+    // of the pass, its obstacles 64 b + t % 8 + 8 q (q < kFilt), the loads
+    // of a step independent; survivors are queued, and the queue is
+    // evaluated when the next step could overflow it and at the end
+    const int lt = tid & 7;
+    int sp = 0, b = 0;  // first segment of the pass, step within the pass
+    for (;;) {
+      const int seg = sp + (tid >> 3);
+      const int sn = seg < nsg ? seg_n[seg] : 0;
+      const bool has = b * 8 * kFilt < sn;
+      bool keep[kFilt];
+      int item[kFilt];
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        keep[q] = false;
+        item[q] = 0;
+      }
+      if (has) {
+        const int sf = seg_first[seg];
+        const int jj = seg_pose[seg];
+        const float4 q4 = pose_s[jj];
+        const float tq = thr_s[jj];
+        float4 cq[kFilt];
+#pragma unroll
+        for (int q = 0; q < kFilt; ++q) {
+          const int o = b * 8 * kFilt + lt + 8 * q;
+          if (o < sn) cq[q] = __ldg(&a.obs[sf + o].circ);
+        }
+#pragma unroll
+        for (int q = 0; q < kFilt; ++q) {
+          const int o = b * 8 * kFilt + lt + 8 * q;
+          keep[q] = o < sn && !(circle_lb_value(cq[q], q4.x, q4.y, F.radius) > tq);
+          item[q] = ((sf + o) << 4) | jj;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        const unsigned mk = __ballot_sync(kFull, keep[q]);
+        int base = 0;
+        if (lane == 0 && mk) base = atomicAdd(&nq_s, __popc(mk));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep[q]) q_s[base + __popc(mk & ((1u << lane) - 1u))] = item[q];
+      }
+      // the next step: the next block of this pass's segments, or the next pass
+      const bool more_blocks = __syncthreads_or(has && (b + 1) * 8 * kFilt < sn);
+      bool done = false;
+      if (more_blocks) {
+        ++b;
+      } else {
+        b = 0;
+        sp += kSegsPerPass;
+        done = sp >= nsg;
+      }
+      const int nq = nq_s;
+      if (done || nq > kQCap - kCullThreads * kFilt) {
+        // the queued items, kItemLanes lanes each (the obstacle's edges
+        // shared out, obstacle_value_coop), kGroups items a pass
+        const int g = lane % kItemLanes;
+        for (int b0 = 0; b0 < nq; b0 += kGroups) {
+          const int slot = b0 + tid / kItemLanes;
+          const bool live = slot < nq;
+          const int it = live ? q_s[slot] : 0;
+          const int ij = it & 15, so = it >> 4;
+          const float4 pq = pose_s[ij];
+          int4 rec = make_int4(0, 0, 0, 0);
+          if (live) rec = __ldg(&a.obs[so].rec);
+          const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
+              F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,
+              prm.eta, g);
+          if (live && g == 0) {
+            atomicMin(&key_s[ij], pack_key(v, rec.z));
+            ++n_obs;
+            n_edge += (unsigned)rec.y;
+          }
+        }
+        __syncthreads();  // the queue consumed
+        if (tid == 0) nq_s = 0;
+        __syncthreads();
+      }
+      if (done) break;
+    }
+    if (tid == 0) nseg_s = 0;
+    if (!__syncthreads_or(more)) break;
   }
 
   // ---- counters ------------------------------------------------------------
@@ -847,34 +804,30 @@ __global__ void __launch_bounds__(kCullThreads, 4)
   cnt[kStCirc] = n_circ;
   cnt[kStObs] = n_obs;
   cnt[kStEdges] = n_edge;
-  __syncthreads();  // st_s initialised; the epilogue records written
 #pragma unroll
   for (int k = 0; k < kStCount; ++k) {
     const unsigned t = __reduce_add_sync(kFull, cnt[k]);
     if (lane == 0 && t) atomicAdd(&st_s[k], t);
   }
-  __syncthreads();
-  if (threadIdx.x < kStCount)
-    a.ws[kStatBase + (long long)blockIdx.x * kStatWords + threadIdx.x] = st_s[threadIdx.x];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  __syncthreads();  // every key and counter final
+  if (tid < kStCount)
+    a.ws[kStatBase + (long long)blockIdx.x * kStatWords + tid] = st_s[tid];
+  if (blockIdx.x == 0 && tid == 0) {
     a.ws[0] = gridDim.x;
     a.ws[1] = 0ull;  // the cull has no device-side wait
   }
-  if (warp != 0) return;
+  if (warp >= kPoses / 8) return;
 
-  // ---- 4. epilogues of the CTA's poses by warp 0 ---------------------------
+  // ---- 5. epilogues: 8 poses a warp, 4 lanes each ---------------------------
   {
-    const int j = lane >> 2;  // pose of the CTA, 4 lanes each
-    const long long pj = (long long)blockIdx.x * kPoses + j;
+    const int jj = 8 * warp + (lane >> 2);
+    const long long pj = (long long)blockIdx.x * kPoses + jj;
     const bool vj = pj < a.P;
-    const float4 q = ep_pose[j];
-    const unsigned long long key = ep_key[j];
-    const bool none = key == ~0ull;
+    const float4 q = pose_s[jj];
+    const unsigned long long key = key_s[jj];
+    const bool none = key == ~0ull || !vj;
     ObsRec o{0, 0, 0, 0};
-    if (!none) {
-      const int4 r = __ldg(&a.obs[ep_obs[j]].rec);
-      o = ObsRec{r.x, r.y, r.z, r.w};
-    }
+    if (!none) o = a.row_obs[(int)(unsigned)(key & 0xffffffffu)];
     const bool save = a.saved != nullptr;
     const bool want_grad = save || a.dphi != nullptr;
     PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
@@ -885,8 +838,8 @@ __global__ void __launch_bounds__(kCullThreads, 4)
         r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w, none, o,
                                        a.vtx, a.far, want_grad, prm.eta);
     } else {
-      r = epilogue_obstacle_coop<M, 4>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w,
-                                       none || !vj, o, a.vtx, a.far, want_grad, lane & 3,
+      r = epilogue_obstacle_coop<M, 4>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w, none, o,
+                                       a.vtx, a.far, want_grad, lane & 3,
                                        save ? &rows : nullptr);
     }
     if (vj && (lane & 3) == 0) {
@@ -997,7 +950,7 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 // clear before a launch).
 static size_t cull_workspace_bytes(long long P)
 {
-  const long long ctas = (std::max<long long>(P, 0) + 2 * kCullWarps - 1) / (2 * kCullWarps);
+  const long long ctas = (std::max<long long>(P, 0) + kPoses - 1) / kPoses;
   return 8 * (size_t)kStatBase + 8 * (size_t)kStatWords * (size_t)std::max<long long>(ctas, 1);
 }
 
@@ -1232,6 +1185,7 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   a.obs = scene->d_cull_obs;
   a.vtx = scene->d_vtx;
   a.far = scene->d_far;
+  a.row_obs = scene->d_row_obs;
   // soft minimum: an obstacle's value lies below its hard distance when it
   // is separated and at most log(K) / eta (K axes) when it penetrates, so
   // the upper bound taken from distances is raised by that much
@@ -1247,11 +1201,12 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   a.active = active;
   a.saved = saved;
   a.ws = ws;
-  const long long grid = (P + 2 * kCullWarps - 1) / (2 * kCullWarps);
+  const long long grid = (P + kPoses - 1) / kPoses;
   // the scene into L2 when the launch reads a good part of it and it fits
   // well within L2 (a few poses on a huge scene read only what they need)
   {
     const size_t scene_bytes = 32 * (size_t)scene->M + 36 * (size_t)scene->n_edges +
+                               16 * (size_t)scene->rows_total +
                                32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles;
     if (P >= 64 && scene_bytes <= (32u << 20)) {
       auto add = [&](const void *ptr, size_t bytes) {
@@ -1274,6 +1229,7 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
       add(scene->d_cull_obs, sizeof(CullObs) * (size_t)scene->M);
       add(scene->d_vtx, 32 * (size_t)scene->n_edges);
       add(scene->d_far, 4 * (size_t)scene->n_edges);
+      add(scene->d_row_obs, sizeof(ObsRec) * (size_t)scene->rows_total);
     }
   }
   ParamsK pk{params->eps_sat, params->eta};
