@@ -450,6 +450,8 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   __shared__ float4 pose_s[kPoses];
   __shared__ float thr_s[kPoses];
   __shared__ unsigned long long key_s[kPoses];
+  __shared__ Active det_s[kPoses];  // the winning obstacle's detail (hard minimum)
+  __shared__ int4 drec_s[kPoses];   // and its record
   __shared__ int seg_first[kSegCap], seg_n[kSegCap];
   __shared__ unsigned char seg_pose[kSegCap];
   __shared__ int q_s[kQCap];
@@ -776,11 +778,31 @@ __global__ void __launch_bounds__(kCullThreads, 2)
           const float4 pq = pose_s[ij];
           int4 rec = make_int4(0, 0, 0, 0);
           if (live) rec = __ldg(&a.obs[so].rec);
-          const float v = obstacle_value_coop<M, kItemLanes, SOFT>(
-              F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,
-              prm.eta, g);
+          if constexpr (SOFT) {
+            const float v = obstacle_value_coop<M, kItemLanes, true>(
+                F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,
+                prm.eta, g);
+            if (live && g == 0) atomicMin(&key_s[ij], pack_key(v, rec.z));
+          } else {
+            // the key and the exact detail in one evaluation: the item that
+            // holds its pose's minimum after the pass leaves its detail for
+            // the epilogue
+            float kv;
+            const Active ad = obstacle_scan_detail_coop<M, kItemLanes>(
+                F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, rec.z,
+                prm.eps_sat, g, kv);
+            const unsigned long long key = pack_key(kv, rec.z);
+            if (live && g == 0) {
+              atomicMin(&key_s[ij], key);
+              prefetch_lines(a.far + rec.x, 4 * rec.y);  // the gradient's far indices
+            }
+            __syncthreads();  // the pass's minima are in
+            if (live && g == 0 && key_s[ij] == key) {
+              det_s[ij] = ad;
+              drec_s[ij] = rec;
+            }
+          }
           if (live && g == 0) {
-            atomicMin(&key_s[ij], pack_key(v, rec.z));
             ++n_obs;
             n_edge += (unsigned)rec.y;
           }
@@ -816,36 +838,54 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     a.ws[0] = gridDim.x;
     a.ws[1] = 0ull;  // the cull has no device-side wait
   }
-  if (warp >= kPoses / 8) return;
-
-  // ---- 5. epilogues: 8 poses a warp, 4 lanes each ---------------------------
-  {
+  const bool save = a.saved != nullptr;
+  const bool want_grad = save || a.dphi != nullptr;
+  if constexpr (SOFT) {
+    // ---- 5. soft-minimum epilogues: 8 poses a warp, one lane each ----------
+    if (warp >= kPoses / 8) return;
     const int jj = 8 * warp + (lane >> 2);
     const long long pj = (long long)blockIdx.x * kPoses + jj;
     const bool vj = pj < a.P;
+    if (vj && (lane & 3) == 0) {
+      const float4 q = pose_s[jj];
+      const unsigned long long key = key_s[jj];
+      const bool none = key == ~0ull;
+      ObsRec o{0, 0, 0, 0};
+      if (!none) o = a.row_obs[(int)(unsigned)(key & 0xffffffffu)];
+      const PoseOut r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z,
+                                                   q.w, none, o, a.vtx, a.far, want_grad,
+                                                   prm.eta);
+      write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
+    }
+  } else {
+    // ---- 5. epilogues of the hard minimum: the winners' details are known;
+    // lane 0 of each pose's half takes the active pair's gradient (two poses
+    // a warp: the per-kind branches of at most two pairs run one after the
+    // other) -----------------------------------------------------------------
+    if (hl != 0) return;
+    const int jj = j;
+    const long long pj = (long long)blockIdx.x * kPoses + jj;
+    if (pj >= a.P) return;
     const float4 q = pose_s[jj];
-    const unsigned long long key = key_s[jj];
-    const bool none = key == ~0ull || !vj;
-    ObsRec o{0, 0, 0, 0};
-    if (!none) o = a.row_obs[(int)(unsigned)(key & 0xffffffffu)];
-    const bool save = a.saved != nullptr;
-    const bool want_grad = save || a.dphi != nullptr;
+    const bool none = key_s[jj] == ~0ull;
     PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
     Grad rows;
     rows.nrow = -1;
-    if constexpr (SOFT) {
-      if (vj && (lane & 3) == 0)
-        r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w, none, o,
-                                       a.vtx, a.far, want_grad, prm.eta);
-    } else {
-      r = epilogue_obstacle_coop<M, 4>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z, q.w, none, o,
-                                       a.vtx, a.far, want_grad, lane & 3,
-                                       save ? &rows : nullptr);
+    if (!none) {
+      const Active ad = det_s[jj];
+      const int4 rc = drec_s[jj];
+      r.pid = ad.pid;
+      r.phi = ad.separated ? sqrtf(ad.val) : ad.val;
+      if (want_grad && (ad.separated || ad.dlt > 0.f)) {
+        rows = active_grad<M>(F, q.x, q.y, q.z, q.w, a.vtx + 2 * (long long)rc.x, a.far + rc.x,
+                              rc.y, rc.z, ad.kind, ad.l, ad.k, ad.t, a.eps_axis);
+        r.g[0] = rows.gp[0];
+        r.g[1] = rows.gp[1];
+        r.g[2] = rows.gp[2];
+      }
     }
-    if (vj && (lane & 3) == 0) {
-      write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
-      if (!SOFT && save) write_saved(a.saved, pj, rows);
-    }
+    write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
+    if (save) write_saved(a.saved, pj, rows);
   }
 }
 

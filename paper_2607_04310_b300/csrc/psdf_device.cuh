@@ -508,6 +508,7 @@ struct DetailAcc {
   float pmax[M], pmin[M];
   int kmax[M], kmin[M];
   float d2min, dlt, bd, ba, dt;
+  float d2scan;  // the scan's candidate set (far-end clamps included)
   unsigned pd, pa;
   __device__ __forceinline__ DetailAcc()
   {
@@ -519,6 +520,7 @@ struct DetailAcc {
       kmin[l] = 0;
     }
     d2min = kInf;
+    d2scan = kInf;
     dlt = kInf;
     bd = kInf;
     ba = kInf;
@@ -531,7 +533,11 @@ struct DetailAcc {
 // Edge k of an obstacle (vt, n) into the detail state: its distance pairs
 // with every robot vertex and vertex k's with every robot edge, its own
 // axis, and vertex k's projections on the robot axes.
-template <int M, bool SOFT>
+// SCAN also keeps the minimum over the scan's candidate set in q.d2scan
+// (every clamped point-to-segment candidate, as edge_step takes them), with
+// the same operations, so that synth_value(d2scan, dlt) is the obstacle's
+// min-key value bit for bit.
+template <int M, bool SOFT, bool SCAN = false>
 __device__ __forceinline__ void detail_edge(const FootprintK &F, float px, float py, float c,
                                             float s, const float4 *vt, int n, int k,
                                             int orig_first, DetailAcc<M> &q, SoftAcc &acc,
@@ -565,6 +571,7 @@ __device__ __forceinline__ void detail_edge(const FootprintK &F, float px, float
       ry = (t == 1.0f) ? __fsub_rn(F.vy[l], B.y) : ry;
     }
     const float d2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+    if (SCAN) q.d2scan = fminf(q.d2scan, d2);
     if (seg || t < 1.0f) {
       q.d2min = fminf(q.d2min, d2);
       const unsigned pid = make_pid(edge, kVertEdge, l);
@@ -576,6 +583,11 @@ __device__ __forceinline__ void detail_edge(const FootprintK &F, float px, float
     const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
     const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    if (SCAN) {  // the clamped candidate of the scan
+      const float tc = __saturatef(tp);
+      const float cx = __fmaf_rn(tc, F.ex[l], wx), cy = __fmaf_rn(tc, F.ey[l], wy);
+      q.d2scan = fminf(q.d2scan, __fmaf_rn(cx, cx, __fmul_rn(cy, cy)));
+    }
     if (tp > 0.0f && tp < 1.0f) {
       q.d2min = fminf(q.d2min, d2p);
       const unsigned pid = make_pid(edge, kObsVRobotEdge, l);
@@ -601,7 +613,7 @@ __device__ __forceinline__ void detail_edge(const FootprintK &F, float px, float
 
 // A segment's B endpoint: its distances to the robot edges and its
 // projections on the robot axes (vertex index 1).
-template <int M>
+template <int M, bool SCAN = false>
 __device__ __forceinline__ void detail_seg_b(const FootprintK &F, float px, float py, float c,
                                              float s, const float4 *vt, int orig_first,
                                              DetailAcc<M> &q)
@@ -614,6 +626,11 @@ __device__ __forceinline__ void detail_seg_b(const FootprintK &F, float px, floa
     const float tp = __fmul_rn(-__fmaf_rn(wx, F.ex[l], __fmul_rn(wy, F.ey[l])), F.inv_e2[l]);
     const float qx = __fmaf_rn(tp, F.ex[l], wx), qy = __fmaf_rn(tp, F.ey[l], wy);
     const float d2p = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
+    if (SCAN) {
+      const float tc = __saturatef(tp);
+      const float cx = __fmaf_rn(tc, F.ex[l], wx), cy = __fmaf_rn(tc, F.ey[l], wy);
+      q.d2scan = fminf(q.d2scan, __fmaf_rn(cx, cx, __fmul_rn(cy, cy)));
+    }
     if (tp > 0.0f && tp < 1.0f) {
       q.d2min = fminf(q.d2min, d2p);
       const unsigned pid = make_pid(orig_first, kObsBRobotEdge, l);
@@ -720,6 +737,49 @@ __device__ __forceinline__ Active obstacle_detail_coop(const FootprintK &F, floa
     }
   }
   return detail_finish<M, false>(F, n, orig_first, eps_sat, q, acc, 0.f);
+}
+
+// obstacle_detail_coop that also returns the obstacle's min-key value as the
+// scan computes it (keyval, every lane): the detail's own arithmetic plus
+// the scan's unfiltered candidate minimum, so one evaluation gives both the
+// key and the active pair.  Hard minimum only.
+template <int M, int G>
+__device__ __forceinline__ Active obstacle_scan_detail_coop(const FootprintK &F, float px,
+                                                            float py, float c, float s,
+                                                            const float4 *vt, int n,
+                                                            int orig_first, float eps_sat,
+                                                            int g, float &keyval)
+{
+  SoftAcc acc;
+  DetailAcc<M> q;
+  for (int k = g; k < n; k += G)
+    detail_edge<M, false, true>(F, px, py, c, s, vt, n, k, orig_first, q, acc, 0.f);
+  if (n == 1 && g == 0) detail_seg_b<M, true>(F, px, py, c, s, vt, orig_first, q);
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    q.d2min = fminf(q.d2min, __shfl_xor_sync(0xffffffffu, q.d2min, o));
+    q.d2scan = fminf(q.d2scan, __shfl_xor_sync(0xffffffffu, q.d2scan, o));
+    q.dlt = fminf(q.dlt, __shfl_xor_sync(0xffffffffu, q.dlt, o));
+    const float bd = __shfl_xor_sync(0xffffffffu, q.bd, o);
+    const unsigned pd = __shfl_xor_sync(0xffffffffu, q.pd, o);
+    const float dt = __shfl_xor_sync(0xffffffffu, q.dt, o);
+    if (better(bd, pd, q.bd, q.pd)) { q.bd = bd; q.pd = pd; q.dt = dt; }
+    const float ba = __shfl_xor_sync(0xffffffffu, q.ba, o);
+    const unsigned pa = __shfl_xor_sync(0xffffffffu, q.pa, o);
+    if (better(ba, pa, q.ba, q.pa)) { q.ba = ba; q.pa = pa; }
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const float vmx = __shfl_xor_sync(0xffffffffu, q.pmax[l], o);
+      const int kmx = __shfl_xor_sync(0xffffffffu, q.kmax[l], o);
+      if (vmx > q.pmax[l] || (vmx == q.pmax[l] && kmx < q.kmax[l])) { q.pmax[l] = vmx; q.kmax[l] = kmx; }
+      const float vmn = __shfl_xor_sync(0xffffffffu, q.pmin[l], o);
+      const int kmn = __shfl_xor_sync(0xffffffffu, q.kmin[l], o);
+      if (vmn < q.pmin[l] || (vmn == q.pmin[l] && kmn < q.kmin[l])) { q.pmin[l] = vmn; q.kmin[l] = kmn; }
+    }
+  }
+  const Active a = detail_finish<M, false>(F, n, orig_first, eps_sat, q, acc, 0.f);
+  keyval = synth_value(q.d2scan, a.dlt, eps_sat);
+  return a;
 }
 
 // Pose gradient and edge-gradient contributions of one active pair
