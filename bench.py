@@ -6,15 +6,16 @@
 One step = one pass of the value+gradient path over the dense-clutter
 workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
 100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
-the exact tile cull with the learned proposal (bound ranking, network
-re-rank on tensor cores, an upper bound from the proposed tiles' obstacle
-circles, every tile whose lower bound does not exceed it listed, one exact
-pass over the listed pairs skipping obstacles by their circle bound, the
+the exact tile cull (one fused kernel: each pose ranks the tiles of its grid
+cell, proposes the nearest by the conservative bound, takes an upper bound
+from the proposed tile's obstacle circles, and the CTA evaluates exactly
+every obstacle of every tile whose bounds do not exceed it, then the
 epilogue with the pose gradient) followed by PSDF_Backward (pose and
-edge-endpoint gradients of sum(phi)).  The metric counts pose x edge
-pairs of the whole scene per second (the cull's results equal the full
-scan's bit for bit, checked in the run); the full scan and the bound-ordered
-cull are timed on the same GPU for the speedup.
+edge-endpoint gradients of sum(phi)) from the forward's saved rows.  The
+metric counts pose x edge pairs of the whole scene per second (the cull's
+results equal the full scan's bit for bit, checked in the run); the full
+scan and the cull with the learned proposal (the tile-proposal network
+re-ranking each pose's 8 nearest tiles) are timed on the same GPU.
 
 Under torchrun (N > 1) every rank evaluates its own 4,096 poses on the same
 scene (weak scaling, no data-path collective); the value is the total pair
@@ -220,6 +221,12 @@ def run_reference(a, rank, world):
 # B300 arm
 # --------------------------------------------------------------------------
 CULL_K = 1
+# The tile proposal of the headline step: "bound" (the conservative AABB
+# bound's order) or "mlp" (the trained network).  On the sort-tile-recursive
+# tiles of this workload the network picks the bound's tile 93 % of the time
+# and adds its ranking to every pose's chain, so the bound order is the faster
+# exact path; the learned cull is measured beside it.
+HEADLINE_MODE = "bound"
 
 
 def _time_steps(step, steps, flush, stream, clocks=None):
@@ -570,17 +577,23 @@ def run_b300(a, rank, world, local):
     # gradient rows, which the epilogue computes anyway) and scatters them
     saved = torch.empty((P, psdf.SAVED_FLOATS), dtype=torch.float32, device=dev)
 
-    def step_learned(ps=poses):
-        psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, ps, prm, phi, dphi, act,
+    # the headline step proposes tiles by the bound (HEADLINE_MODE); the
+    # learned proposal is timed beside it on the same GPU
+    head = bound if HEADLINE_MODE == "bound" else learned
+    head_net = None if HEADLINE_MODE == "bound" else mlp
+
+    def step_head(ps=poses):
+        psdf.psdf_eval_culled_save(w.footprint, scene, head_net, head, ps, prm, phi, dphi, act,
                                    saved, cws)
         psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
-    def step_learned_recompute():
-        psdf.psdf_eval_culled(w.footprint, scene, mlp, learned, poses, prm, phi, dphi, act, cws)
+    def step_head_recompute():
+        psdf.psdf_eval_culled(w.footprint, scene, head_net, head, poses, prm, phi, dphi, act,
+                              cws)
         psdf.psdf_backward(w.footprint, scene, poses, prm, act, gphi, gpose, gedges)
 
-    def step_bound():
-        psdf.psdf_eval_culled_save(w.footprint, scene, None, bound, poses, prm, phi, dphi, act,
+    def step_learned():
+        psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, poses, prm, phi, dphi, act,
                                    saved, cws)
         psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
@@ -588,17 +601,23 @@ def run_b300(a, rank, world, local):
         psdf.psdf_eval_grad_save(w.footprint, scene, poses, prm, phi, dphi, act, saved, ws)
         psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
-    # exactness in this run: learned cull vs full scan, every output bit
+    # exactness in this run: both culls vs the full scan, every output bit
     step_full()
     ref = (phi.clone(), dphi.clone(), act.clone(), gpose.clone())
+
+    def same_as_full():
+        torch.cuda.synchronize()
+        return bool(torch.equal(ref[0].view(torch.int32), phi.view(torch.int32)) and
+                    torch.equal(ref[1].view(torch.int32), dphi.view(torch.int32)) and
+                    torch.equal(ref[2], act) and
+                    torch.equal(ref[3].view(torch.int32), gpose.view(torch.int32)))
+
     step_learned()
-    torch.cuda.synchronize()
-    exact = bool(torch.equal(ref[0].view(torch.int32), phi.view(torch.int32)) and
-                 torch.equal(ref[1].view(torch.int32), dphi.view(torch.int32)) and
-                 torch.equal(ref[2], act) and
-                 torch.equal(ref[3].view(torch.int32), gpose.view(torch.int32)))
+    exact_learned = same_as_full()
+    step_head()
+    exact = same_as_full() and exact_learned
     for _ in range(max(a.warmup, 3)):
-        step_learned()
+        step_head()
     torch.cuda.synchronize()
     # per-kernel device time of the eager step (CUDA events around each of the
     # library's launches, on its stream): the roofline of the dominant kernel
@@ -606,21 +625,21 @@ def run_b300(a, rank, world, local):
     psdf.psdf_profile_enable(True)
     for _ in range(a.steps):
         flush.zero_()
-        step_learned()
+        step_head()
     torch.cuda.synchronize()
     psdf.psdf_profile_enable(False)
     prof = {k: psdf.psdf_profile_read(k) for k in ("cull", "backward")}
     psdf.psdf_profile_reset()
     st = psdf.psdf_cull_stats_read(cws, stream)
 
-    # ---- headline: the learned-cull step as one CUDA-graph launch --------------
-    replay_learned, g_learned = _graph(step_learned)
+    # ---- headline: the cull step as one CUDA-graph launch ---------------------
+    replay_head, g_head = _graph(step_head)
     for _ in range(max(a.warmup, 3)):
-        replay_learned()
+        replay_head()
     if pg:
         pg.barrier()
     with ClockSampler(local) as clk:
-        ms = _time_steps(replay_learned, a.steps, flush, stream)
+        ms = _time_steps(replay_head, a.steps, flush, stream)
     if pg:
         pg.barrier()
     ms_step = sum(ms) / len(ms)
@@ -630,16 +649,16 @@ def run_b300(a, rank, world, local):
     for _ in range(3):
         replay_full()
     full_ms = sum(_time_steps(replay_full, a.steps, flush, stream)) / a.steps
-    replay_bound, g_bound = _graph(step_bound)
+    replay_learned, g_learned = _graph(step_learned)
     for _ in range(3):
-        replay_bound()
-    bound_ms = sum(_time_steps(replay_bound, a.steps, flush, stream)) / a.steps
-    st_bound = psdf.psdf_cull_stats_read(cws, stream)
-    replay_rec, g_rec = _graph(step_learned_recompute)
+        replay_learned()
+    learned_ms = sum(_time_steps(replay_learned, a.steps, flush, stream)) / a.steps
+    st_learned = psdf.psdf_cull_stats_read(cws, stream)
+    replay_rec, g_rec = _graph(step_head_recompute)
     for _ in range(3):
         replay_rec()
     recompute_ms = sum(_time_steps(replay_rec, a.steps, flush, stream)) / a.steps
-    eager_ms = sum(_time_steps(step_learned, a.steps, flush, stream)) / a.steps
+    eager_ms = sum(_time_steps(step_head, a.steps, flush, stream)) / a.steps
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e_step_ms = e2e_copy_ms = float("nan")
@@ -654,7 +673,7 @@ def run_b300(a, rank, world, local):
             # poses in, the cull step, the result (phi, dphi, active) read
             # back on a side stream while the backward runs
             d_poses.copy_(h_poses, non_blocking=True)
-            psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, d_poses, prm, phi, dphi,
+            psdf.psdf_eval_culled_save(w.footprint, scene, head_net, head, d_poses, prm, phi, dphi,
                                        act, saved, cws)
             fwd_done = torch.cuda.Event()
             fwd_done.record()
@@ -677,7 +696,7 @@ def run_b300(a, rank, world, local):
         h_act = h_out[4 * P:].view(torch.int32)
 
         def e2e_zero_copy_step():
-            psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, h_poses, prm, h_phi,
+            psdf.psdf_eval_culled_save(w.footprint, scene, head_net, head, h_poses, prm, h_phi,
                                        h_dphi, h_act, saved, cws)
             psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
@@ -715,7 +734,8 @@ def run_b300(a, rank, world, local):
         st.bound_evaluations, st.circle_evaluations)
     f_instr = roofline.flops_evaluated(m, st.evaluated_edges, st.evaluated_obstacles) + \
         roofline.flops_propose(st.bound_evaluations, st.circle_evaluations)
-    f_net = roofline.flops_network(8 * P)  # 8 candidates scored per pose
+    # the network's tensor-core flops, when the headline step runs it
+    f_net = roofline.flops_network(8 * P) if HEADLINE_MODE == "mlp" else 0.0
     ach = f_fixed / (cull_ms / 1000.0) / 1e12
     ach_instr = f_instr / (cull_ms / 1000.0) / 1e12
     bf16 = float(peaks.get("bf16_tflops", 0.0)) or None
@@ -728,8 +748,13 @@ def run_b300(a, rank, world, local):
         "impl": "b300",
         "config": {"workload": WORKLOAD, "poses_per_gpu": P, "edges": w.E,
                    "obstacles": w.M, "tiles": T, "footprint_vertices": m,
-                   "path": ("learned tile cull (k=%d) + pose gradient + backward (from the "
-                            "forward's saved rows)" % CULL_K),
+                   "path": ("%s tile cull (k=%d) + pose gradient + backward (from the "
+                            "forward's saved rows); %s" % (
+                                "bound-ordered" if HEADLINE_MODE == "bound" else "learned",
+                                CULL_K,
+                                "the learned proposal, timed beside it (learned_cull), costs "
+                                "more than it saves on these sort-tile-recursive tiles"
+                                if HEADLINE_MODE == "bound" else "")),
                    "pair_count": "effective: poses x edges of the whole scene",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "speedup_vs_full_scan": full_ms / ms_step,
@@ -747,9 +772,25 @@ def run_b300(a, rank, world, local):
                                "note": "the same step through psdf_eval_culled + psdf_backward "
                                        "(the backward recomputes the active pair's geometry "
                                        "instead of reading the forward's saved rows)"},
-        "bound_cull": {"value": pairs / (bound_ms / 1000.0), "ms_per_step": bound_ms,
-                       "evaluated_fraction": (st_bound.proposed_items + st_bound.fallback_items) / (P * T),
-                       "fallback_rate": st_bound.fallback_poses / P},
+        "learned_cull": {"value": pairs / (learned_ms / 1000.0), "ms_per_step": learned_ms,
+                         "exact_vs_full_scan": exact_learned,
+                         "evaluated_fraction": (st_learned.proposed_items
+                                                + st_learned.fallback_items) / (P * T),
+                         "fallback_rate": st_learned.fallback_poses / P,
+                         "evaluated_obstacles": int(st_learned.evaluated_obstacles),
+                         "listed_pairs": int(st_learned.proposed_items
+                                             + st_learned.fallback_items),
+                         "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp"),
+                         "network_flops_per_step": roofline.flops_network(8 * P),
+                         "gain_vs_bound": {
+                             "ms_per_step": learned_ms - ms_step,
+                             "listed_pairs": int(st_learned.proposed_items
+                                                 + st_learned.fallback_items)
+                             - int(st.proposed_items + st.fallback_items),
+                             "evaluated_obstacles": int(st_learned.evaluated_obstacles)
+                             - int(st.evaluated_obstacles),
+                             "note": "positive = the learned proposal costs more than the "
+                                     "bound order"}},
         "cull": {"candidate_fraction": st.proposed_items / (P * T),
                  "evaluated_fraction": items / (P * T),
                  "evaluated_obstacles": int(st.evaluated_obstacles),
@@ -759,8 +800,7 @@ def run_b300(a, rank, world, local):
                  "fallback_pairs": int(st.fallback_items),
                  "bound_evaluations": int(st.bound_evaluations),
                  "circle_evaluations": int(st.circle_evaluations),
-                 "evaluated_pair_evals_per_s": evaluated_pairs / (ms_step / 1000.0),
-                 "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp")},
+                 "evaluated_pair_evals_per_s": evaluated_pairs / (ms_step / 1000.0)},
         "roofline": {"bound": "alu", "kernel": "cull_kernel",
                      "achieved": ach, "peak": fp32["peak"], "unit": "TFLOP/s",
                      "frac": ach / fp32["peak"],
@@ -771,23 +811,23 @@ def run_b300(a, rank, world, local):
                      "instruction_count": {"flops_per_step": f_instr, "achieved": ach_instr,
                                            "frac": ach_instr / fp32["peak"],
                                            "model": "14 + 30 m per edge + 2 m per obstacle"},
-                     "network_tensor": {"flops_per_step": f_net, "achieved": net_ach,
-                                        "peak": bf16, "frac": net_ach / bf16 if bf16 else None,
-                                        "note": "FP16 mma.sync 16x64x1 over 8 candidates per "
-                                                "pose, against the measured dense bf16 rate "
-                                                "(FP16 dense has the same nominal rate)"},
+                     "network_tensor": ({"flops_per_step": f_net, "achieved": net_ach,
+                                         "peak": bf16, "frac": net_ach / bf16 if bf16 else None,
+                                         "note": "FP16 mma.sync 16x64x1 over 8 candidates per "
+                                                 "pose, against the measured dense bf16 rate "
+                                                 "(FP16 dense has the same nominal rate)"}
+                                        if HEADLINE_MODE == "mlp" else None),
                      "peak_source": fp32["source"],
                      "avg_launch_ms": cull_ms,
                      "traffic": _traffic("cull_kernel", WORKLOAD)},
         "kernels_ms_per_step": {k: v[1] / a.steps for k, v in prof.items()},
         "fp32_peak": fp32,
         "e2e": {"value": world * pairs / (e2e_step_ms / 1000.0), "unit": UNIT,
-                "h2d_bytes_per_step": 2 * 12 * P, "d2h_bytes_per_step": (4 + 12 + 4) * P,
+                "h2d_bytes_per_step": 12 * P, "d2h_bytes_per_step": (4 + 12 + 4) * P,
                 "ms_per_step": e2e_step_ms,
-                "note": "zero-copy, one CUDA graph: the kernels read the poses from pinned, "
-                        "device-mapped host memory (the proposal and epilogue kernels, 12 B "
-                        "per pose each) and the epilogue writes phi / dphi / active into "
-                        "pinned host memory; no copy calls",
+                "note": "zero-copy, one CUDA graph: the cull kernel reads the poses from "
+                        "pinned, device-mapped host memory (12 B per pose) and writes phi / "
+                        "dphi / active into pinned host memory; no copy calls",
                 "equal_to_device_outputs": e2e_exact,
                 "copies": {"value": world * pairs / (e2e_copy_ms / 1000.0),
                            "ms_per_step": e2e_copy_ms, "h2d_bytes_per_step": 12 * P,
