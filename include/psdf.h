@@ -176,6 +176,42 @@ int psdf_eval_grad(const float *footprint, int32_t m, const psdf_scene *scene,
                    float *dphi, uint32_t *active, void *workspace, size_t workspace_bytes,
                    void *stream);
 
+/* ---- scene parts: keys, their minimum, the owner's epilogue --------------
+ * Eq. psdf_value is a minimum over obstacles, so a scene may be split into
+ * parts whose caller rows are consecutive ranges of one numbering (part r a
+ * CSR scene of its own holding the whole scene's rows row_offset_r ..
+ * row_offset_r + rows_r - 1): a static map and each step's moving obstacles
+ * (Sec. V, time-varying edge sets), or an edge set sharded over GPUs.  Each
+ * part yields per-pose 64-bit keys (ordered value << 32 | rank, the rank
+ * being the whole scene's row of the obstacle's first edge), their minimum
+ * is the whole scene's key with its tie-break, and the part that holds the
+ * winning obstacle runs the epilogue: the outputs equal one evaluation of
+ * the whole scene bit for bit.
+ *
+ * psdf_eval_keys: keys[P] (DEVICE uint64, caller-owned, overwritten) of the
+ *   part by the full scan, ranks offset by row_offset; 0xFFFF...F = no
+ *   obstacle.  workspace: DEVICE, >= 256 bytes, 256-byte aligned (only its
+ *   error word is used; psdf_workspace_status reads it).
+ * psdf_merge_keys: b[p] = min(a[p], b[p]) for DEVICE uint64 a, b.  Across
+ *   GPUs the same minimum is one all-reduce: the keys read as int64 with the
+ *   top bit flipped order as the unsigned keys do.
+ * psdf_finish_keys: the epilogue (phi, active pair in the whole scene's row
+ *   numbering, gradient if dphi) of the poses whose merged key names an
+ *   obstacle of this part, and, when own_empty != 0, of the poses whose key
+ *   names none (phi = +inf, active = PSDF_PAIR_NONE); the other poses'
+ *   outputs are not written.  dphi and active are nullable.
+ * All are asynchronous on `stream` and allocate nothing.  row_offset >= 0
+ * and row_offset + the part's rows must fit the pair id's 24-bit edge field
+ * (PSDF_ERR_ARG otherwise). */
+int psdf_eval_keys(const float *footprint, int32_t m, const psdf_scene *scene, const float *poses,
+                   int64_t P, const psdf_params *params, int64_t row_offset, uint64_t *keys,
+                   void *workspace, size_t workspace_bytes, void *stream);
+int psdf_merge_keys(const uint64_t *a, uint64_t *b, int64_t P, void *stream);
+int psdf_finish_keys(const float *footprint, int32_t m, const psdf_scene *scene,
+                     const float *poses, int64_t P, const psdf_params *params,
+                     int64_t row_offset, int32_t own_empty, const uint64_t *keys, float *phi,
+                     float *dphi, uint32_t *active, void *stream);
+
 /* ---- SQP-RTI stage parameters (Alg. 1, PSDF-MPC pipeline) ---------------
  * The affine safety constraint of every prediction stage, J_g dx <= h, from
  * the linearization of h = phi - d_min at the nominal pose (Sec. V-A):

@@ -456,15 +456,84 @@ int check_eval_args(const psdf_scene *scene, const float *poses, int64_t P,
   return PSDF_OK;
 }
 
-template <int M>
-static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
-                       const psdf_params *prm, float *phi, float *dphi, unsigned *active,
-                       void *ws, const StageOut &so, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// scene parts: keys with a row offset, their minimum, the owner's epilogue
+// ---------------------------------------------------------------------------
+// Adds row_offset to the rank of every key that names an obstacle, so that
+// keys of scene parts whose rows are consecutive ranges of one numbering
+// compare as keys of the whole scene.  Waits for the scan (programmatic).
+__global__ void offset_keys_kernel(unsigned long long *keys, long long P, unsigned row_offset)
 {
-  int *err = reinterpret_cast<int *>(ws);
-  unsigned long long *keys =
-      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(ws) + 256);
-  ParamsK pk{prm->eps_sat, prm->eta};
+  pdl_wait();
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P && keys[p] != ~0ull) keys[p] += row_offset;
+}
+
+// b[p] = min(a[p], b[p]).
+__global__ void merge_keys_kernel(const unsigned long long *__restrict__ a,
+                                  unsigned long long *__restrict__ b, long long P)
+{
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) b[p] = a[p] < b[p] ? a[p] : b[p];
+}
+
+// Epilogue of the poses whose (merged) key names an obstacle of this scene
+// part, rows [row_offset, row_offset + rows), or names none when own_empty;
+// the other poses' outputs are left as they are.  The active pair's edge is
+// reported in the whole scene's numbering.  Hard minimum: kEpiLanes lanes a
+// pose (every lane through the shared detail); soft minimum: one thread.
+template <int M, bool SOFT>
+__global__ void finish_keys_kernel(FootprintK F, ParamsK prm, float eps_axis,
+                                   const float *__restrict__ poses, long long P,
+                                   const ObsRec *__restrict__ row_obs,
+                                   const float4 *__restrict__ vtx, const int *__restrict__ far,
+                                   const unsigned long long *__restrict__ keys,
+                                   long long row_offset, long long rows, int own_empty,
+                                   float *__restrict__ phi, float *__restrict__ dphi,
+                                   unsigned *__restrict__ active)
+{
+  const int lanes = SOFT ? 1 : kEpiLanes;
+  const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / lanes;
+  const int g = (int)(threadIdx.x % lanes);
+  bool own = false;
+  unsigned long long key = ~0ull;
+  if (p < P) {
+    key = keys[p];
+    if (key == ~0ull) {
+      own = own_empty != 0;
+    } else {
+      const long long rank = (long long)(key & 0xffffffffull);
+      own = rank >= row_offset && rank < row_offset + rows;
+      key = own ? key - (unsigned long long)row_offset : ~0ull;
+    }
+  }
+  float px = 0.f, py = 0.f, th = 0.f;
+  if (p < P) {
+    px = poses[3 * p];
+    py = poses[3 * p + 1];
+    th = poses[3 * p + 2];
+  }
+  const bool want_grad = dphi != nullptr;
+  PoseOut r;
+  if constexpr (SOFT) {
+    if (!own) return;
+    r = epilogue_pose<M, true>(F, prm.eps_sat, eps_axis, px, py, th, key, row_obs, vtx, far,
+                               want_grad, prm.eta);
+  } else {
+    r = epilogue_pose_coop<M, kEpiLanes>(F, prm.eps_sat, eps_axis, px, py, th,
+                                         own ? key : ~0ull, row_obs, vtx, far, want_grad, g);
+    if (!own || g != 0) return;
+  }
+  if (r.pid != PSDF_PAIR_NONE) r.pid += (unsigned)row_offset << kPairShiftEdge;
+  write_pose_out(r, p, phi, dphi, active, nullptr, 0.f);
+}
+
+// Keys of every pose over the scene's tiles: key initialisation + the full
+// scan (its atomicMin merges into keys[]); err receives a timed-out wait.
+template <int M>
+static int launch_scan(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                       const ParamsK &pk, unsigned long long *keys, int *err, cudaStream_t st)
+{
   const int init_blocks = (int)((P + 255) / 256);
   init_keys_kernel<<<init_blocks, 256, 0, st>>>(keys, P, err);
   if (sc->n_tiles > 0) {
@@ -493,6 +562,20 @@ static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *p
                                 sc->n_tiles, (int)tpc, blob_cap, keys, err, wait_limit());
     if (le != cudaSuccess) return cuda_fail(le, "kernel launch (scan)");
   }
+  return PSDF_OK;
+}
+
+template <int M>
+static int launch_eval(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                       const psdf_params *prm, float *phi, float *dphi, unsigned *active,
+                       void *ws, const StageOut &so, cudaStream_t st)
+{
+  int *err = reinterpret_cast<int *>(ws);
+  unsigned long long *keys =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(ws) + 256);
+  ParamsK pk{prm->eps_sat, prm->eta};
+  int rc = launch_scan<M>(F, sc, poses, P, pk, keys, err, st);
+  if (rc) return rc;
   {
     ProfileScope prof("epilogue", st);
     const bool soft = pk.eta > 0.f;
@@ -604,6 +687,39 @@ struct BackwardCall {
   }
 };
 
+template <int M>
+struct KeysCall {
+  static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                 const ParamsK &pk, unsigned long long *keys, int *err, unsigned row_offset,
+                 cudaStream_t st)
+  {
+    int rc = launch_scan<M>(F, sc, poses, P, pk, keys, err, st);
+    if (rc) return rc;
+    if (row_offset == 0) return PSDF_OK;
+    cudaError_t e = launch_pdl(offset_keys_kernel, dim3((unsigned)((P + 255) / 256)), dim3(256), 0,
+                               st, keys, P, row_offset);
+    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (offset keys)");
+  }
+};
+
+template <int M>
+struct FinishCall {
+  static int run(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
+                 const ParamsK &pk, const unsigned long long *keys, long long row_offset,
+                 int own_empty, float *phi, float *dphi, unsigned *active, cudaStream_t st)
+  {
+    const bool soft = pk.eta > 0.f;
+    const long long threads = soft ? P : P * kEpiLanes;
+    (soft ? finish_keys_kernel<M, true> : finish_keys_kernel<M, false>)
+        <<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+            F, pk, sc->eps_axis, poses, P, (const ObsRec *)sc->d_row_obs,
+            (const float4 *)sc->d_vtx, (const int *)sc->d_far, keys, row_offset,
+            (long long)sc->rows_total, own_empty, phi, dphi, active);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (finish keys)");
+  }
+};
+
 int launch_epilogue(const FootprintK &F, const psdf_scene *sc, const float *poses, long long P,
                     const ParamsK &pk, const unsigned long long *keys, const int *err,
                     float *phi, float *dphi, unsigned *active, cudaStream_t st, float4 *saved)
@@ -683,6 +799,62 @@ extern "C" int psdf_backward_saved(const psdf_scene *scene, const float *saved, 
                              grad_edges);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (backward_saved)");
+}
+
+extern "C" int psdf_eval_keys(const float *footprint, int32_t m, const psdf_scene *scene,
+                              const float *poses, int64_t P, const psdf_params *params,
+                              int64_t row_offset, uint64_t *keys, void *workspace,
+                              size_t workspace_bytes, void *stream)
+{
+  // the workspace holds only the error word here (the keys are the caller's)
+  int rc = check_eval_args(scene, poses, P, params, workspace, (size_t)-1);
+  if (rc) return rc;
+  if (P > 0 && workspace_bytes < 256) return fail(PSDF_ERR_CAPACITY, "workspace below 256 bytes");
+  if (P > 0 && !keys) return fail(PSDF_ERR_ARG, "keys is NULL");
+  if (row_offset < 0 || row_offset + scene->rows_total > (int64_t)kMaxEdgeIndex + 1)
+    return fail(PSDF_ERR_ARG, "row_offset outside the pair id's edge range");
+  FootprintK F;
+  rc = make_footprint(footprint, m, scene->eps_seg, &F);
+  if (rc) return rc;
+  if (P == 0) return PSDF_OK;
+  const ParamsK pk{params->eps_sat, params->eta};
+  return dispatch_m<KeysCall>(m, F, scene, poses, (long long)P, pk,
+                              reinterpret_cast<unsigned long long *>(keys),
+                              reinterpret_cast<int *>(workspace), (unsigned)row_offset,
+                              (cudaStream_t)stream);
+}
+
+extern "C" int psdf_merge_keys(const uint64_t *a, uint64_t *b, int64_t P, void *stream)
+{
+  if (P < 0) return fail(PSDF_ERR_ARG, "P < 0");
+  if (P == 0) return PSDF_OK;
+  if (!a || !b) return fail(PSDF_ERR_ARG, "NULL argument");
+  merge_keys_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const unsigned long long *>(a), reinterpret_cast<unsigned long long *>(b),
+      (long long)P);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (merge keys)");
+}
+
+extern "C" int psdf_finish_keys(const float *footprint, int32_t m, const psdf_scene *scene,
+                                const float *poses, int64_t P, const psdf_params *params,
+                                int64_t row_offset, int32_t own_empty, const uint64_t *keys,
+                                float *phi, float *dphi, uint32_t *active, void *stream)
+{
+  int rc = check_eval_args(scene, poses, P, params, (void *)256, (size_t)-1);
+  if (rc) return rc;
+  if (P > 0 && (!keys || !phi)) return fail(PSDF_ERR_ARG, "keys or phi is NULL");
+  if (row_offset < 0 || row_offset + scene->rows_total > (int64_t)kMaxEdgeIndex + 1)
+    return fail(PSDF_ERR_ARG, "row_offset outside the pair id's edge range");
+  FootprintK F;
+  rc = make_footprint(footprint, m, scene->eps_seg, &F);
+  if (rc) return rc;
+  if (P == 0) return PSDF_OK;
+  const ParamsK pk{params->eps_sat, params->eta};
+  return dispatch_m<FinishCall>(m, F, scene, poses, (long long)P, pk,
+                                reinterpret_cast<const unsigned long long *>(keys),
+                                (long long)row_offset, (int)own_empty, phi, dphi, active,
+                                (cudaStream_t)stream);
 }
 
 extern "C" int psdf_stage_params(const float *footprint, int32_t m, const psdf_scene *scene,

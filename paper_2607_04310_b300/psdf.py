@@ -94,6 +94,12 @@ _SIGS = {
     "psdf_eval_grad_save": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                            _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_backward_saved": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
+    "psdf_eval_keys": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                      ctypes.c_int64, _vp, _vp, ctypes.c_size_t, _vp]),
+    "psdf_merge_keys": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
+    "psdf_finish_keys": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                        ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                        _vp]),
     "psdf_stage_params": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                          ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "psdf_stage_params_batched": (ctypes.c_int, [_vp, _vp, ctypes.c_float, _vp, _vp, _vp]),
@@ -306,6 +312,32 @@ def psdf_stage_params(footprint: np.ndarray, scene: Scene, poses, params: Params
                                     poses.shape[0], ctypes.byref(params), float(d_min),
                                     _ptr(stage), _ptr(active), _ptr(workspace), workspace.numel(),
                                     _stream(stream)))
+
+
+def psdf_eval_keys(footprint: np.ndarray, scene: Scene, poses, params: Params, row_offset: int,
+                   keys, workspace, stream=None) -> None:
+    """Per-pose 64-bit keys of a scene part (keys: int64 tensor holding the
+    unsigned bits), ranks offset by row_offset."""
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_eval_keys(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                 poses.shape[0], ctypes.byref(params), int(row_offset),
+                                 _ptr(keys), _ptr(workspace), workspace.numel(),
+                                 _stream(stream)))
+
+
+def psdf_merge_keys(a, b, stream=None) -> None:
+    """b = min(a, b) over the unsigned key bits."""
+    _check(load().psdf_merge_keys(_ptr(a), _ptr(b), b.numel(), _stream(stream)))
+
+
+def psdf_finish_keys(footprint: np.ndarray, scene: Scene, poses, params: Params,
+                     row_offset: int, own_empty: bool, keys, phi, dphi, active,
+                     stream=None) -> None:
+    fp = np.ascontiguousarray(footprint, dtype=np.float32)
+    _check(load().psdf_finish_keys(_ptr(fp), fp.shape[0], scene.handle, _ptr(poses),
+                                   poses.shape[0], ctypes.byref(params), int(row_offset),
+                                   1 if own_empty else 0, _ptr(keys), _ptr(phi), _ptr(dphi),
+                                   _ptr(active), _stream(stream)))
 
 
 def psdf_backward(footprint: np.ndarray, scene: Scene, poses, params: Params, active, grad_phi,
