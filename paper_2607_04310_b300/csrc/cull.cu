@@ -482,6 +482,10 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   }
   float s, c;
   sincosf(th, &s, &c);
+  // the CTA's counters, keys and lists initialised (early: every warp is
+  // here at about the same time; nothing below waits for another warp
+  // before the tile tests are in)
+  __syncthreads();
   MlpFrags w;
   if constexpr (NET) load_frags(a.frag, lane, w);
   const int K = a.K;
@@ -663,7 +667,6 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     pose_s[j] = make_float4(px, py, c, s);
     thr_s[j] = thr;
   }
-  __syncthreads();  // the CTA's counters and keys initialised
 
   // ---- 3-4. rounds of tile tests, circle tests and exact evaluations -------
   // A round collects, for every pose, the passing tiles of its next chunks
@@ -747,13 +750,22 @@ __global__ void __launch_bounds__(kCullThreads, 2)
           item[q] = ((sf + o) << 4) | jj;
         }
       }
+      {  // the warp's survivors appended with one shared-memory atomic
+        int mine = 0;
 #pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        const unsigned mk = __ballot_sync(kFull, keep[q]);
+        for (int q = 0; q < kFilt; ++q) mine += keep[q] ? 1 : 0;
+        int x = mine;  // inclusive prefix over the warp's lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
         int base = 0;
-        if (lane == 0 && mk) base = atomicAdd(&nq_s, __popc(mk));
-        base = __shfl_sync(kFull, base, 0);
-        if (keep[q]) q_s[base + __popc(mk & ((1u << lane) - 1u))] = item[q];
+        if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
+        base = __shfl_sync(kFull, base, 31) + x - mine;
+#pragma unroll
+        for (int q = 0; q < kFilt; ++q)
+          if (keep[q]) q_s[base++] = item[q];
       }
       // the next step: the next block of this pass's segments, or the next pass
       const bool more_blocks = __syncthreads_or(has && (b + 1) * 8 * kFilt < sn);
