@@ -389,6 +389,8 @@ struct Entries {
 
 __device__ __forceinline__ Entries entries_of(const CullArgs &a, int cell, bool use_cell)
 {
+  if (use_cell && a.grid.cap > 0)  // fixed-capacity lists: no offsets to load
+    return Entries{a.grid.fab, a.grid.finfo, cell * a.grid.cap, (cell + 1) * a.grid.cap};
   if (use_cell)
     return Entries{a.grid.ab, a.grid.info, __ldg(a.grid.off + cell), __ldg(a.grid.off + cell + 1)};
   return Entries{a.tile_ab, a.tile_info, 0, a.T};
@@ -516,14 +518,21 @@ __global__ void __launch_bounds__(kCullThreads, 2)
       kinf[q] = __ldg(E.info + i);
     }
   }
+  {  // a fixed-capacity list's real entries end at its first padding slot
+    const int nreal = __popc(__ballot_sync(kFull, kinf[0].w >= 0) & hmask) +
+                      __popc(__ballot_sync(kFull, kinf[1].w >= 0) & hmask);
+    if (cell >= 0 && a.grid.cap > 0 && nreal < 32) E.hi = E.lo + nreal;
+  }
 #pragma unroll
   for (int q = 0; q < 2; ++q)
-    if (E.lo + hl + 16 * q < E.hi) {
+    if (E.lo + hl + 16 * q < E.hi && kinf[q].w != -2) {
       topk_insert<kRL>(sc, id, aabb_d2(kab[q], px, py), hl + 16 * q);
       ++n_bound;
     }
   for (int i = E.lo + hl + 32; i < E.hi; i += 16) {
-    topk_insert<kRL>(sc, id, aabb_d2(__ldg(E.ab + i), px, py), i - E.lo);
+    const float4 ab = __ldg(E.ab + i);
+    if (!(ab.x <= ab.z)) continue;  // a padding slot (empty AABB)
+    topk_insert<kRL>(sc, id, aabb_d2(ab, px, py), i - E.lo);
     ++n_bound;
   }
   // rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys (the
@@ -561,20 +570,24 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     __syncwarp();
     // lane 4 g + q: candidate g of both poses, quarter q of its inputs
     const int g = lane >> 2, q = lane & 3;
-    const int cellA = __shfl_sync(kFull, cell, 0), cellB = __shfl_sync(kFull, cell, 16);
+    // each pose's entries (its cell's list, or all tiles): pointers of lanes 0 and 16
+    const float4 *abA = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 0);
+    const float4 *abB = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 16);
+    const int4 *infA = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 0);
+    const int4 *infB = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 16);
     const int loA = __shfl_sync(kFull, E.lo, 0), loB = __shfl_sync(kFull, E.lo, 16);
     const int ta = cand_s[warp][0][g], tb = cand_s[warp][1][g];
     float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
     float efa = 0.f, efb = 0.f;
     if (ta >= 0) {
-      const float4 v = __ldg((cellA >= 0 ? a.grid.ab : a.tile_ab) + loA + ta);
-      const int4 inf = __ldg((cellA >= 0 ? a.grid.info : a.tile_info) + loA + ta);
+      const float4 v = __ldg(abA + loA + ta);
+      const int4 inf = __ldg(infA + loA + ta);
       aba[0] = v.x; aba[1] = v.y; aba[2] = v.z; aba[3] = v.w;
       efa = (float)inf.z * (1.f / 256.f);
     }
     if (tb >= 0) {
-      const float4 v = __ldg((cellB >= 0 ? a.grid.ab : a.tile_ab) + loB + tb);
-      const int4 inf = __ldg((cellB >= 0 ? a.grid.info : a.tile_info) + loB + tb);
+      const float4 v = __ldg(abB + loB + tb);
+      const int4 inf = __ldg(infB + loB + tb);
       abb[0] = v.x; abb[1] = v.y; abb[2] = v.z; abb[3] = v.w;
       efb = (float)inf.z * (1.f / 256.f);
     }
@@ -662,6 +675,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   Entries E2 = entries_of(a, cell, in_cell);
   if (!valid) E2.hi = E2.lo;
   const bool same = E2.ab == E.ab && E2.lo == E.lo;  // the ranking's entries
+  if (same) E2.hi = E.hi;
   const int nch = (E2.hi - E2.lo + 15) / 16;
   if (hl == 0) {
     pose_s[j] = make_float4(px, py, c, s);
@@ -694,10 +708,11 @@ __global__ void __launch_bounds__(kCullThreads, 2)
 #pragma unroll
           for (int q = 0; q < kMaxK; ++q) proposed |= ptile[q] == inf.w;
           passing = proposed || !(tile_lb_value(ab, px, py, F.radius) > thr);
+          if (inf.w == -2) passing = false;  // a padding slot
         }
         const unsigned m = __ballot_sync(hmask, passing) & hmask;
         if (used + __popc(m) > 16) break;  // the rest next round
-        if (i < E2.hi) ++n_bound;
+        if (i < E2.hi && inf.w != -2) ++n_bound;
         n_fb += __popc(__ballot_sync(hmask, passing && !proposed) & hmask);
         int base = 0;
         if (hl == 0 && m) base = atomicAdd(&nseg_s, __popc(m));
@@ -1270,7 +1285,11 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
             a.pf.first[a.pf.n] + ((long long)bytes + kPrefetchChunk - 1) / kPrefetchChunk;
         ++a.pf.n;
       };
-      if (scene->grid.nx > 0) {
+      if (scene->grid.nx > 0 && scene->grid.cap > 0) {
+        const size_t slots = (size_t)scene->grid.nx * scene->grid.ny * scene->grid.cap;
+        add(scene->d_cell_fab, 16 * slots);
+        add(scene->d_cell_finfo, 16 * slots);
+      } else if (scene->grid.nx > 0) {
         add(scene->d_cell_off, 4 * ((size_t)scene->grid.nx * scene->grid.ny + 1));
         add(scene->d_cell_aabbs, 16 * (size_t)scene->grid_entries);
         add(scene->d_cell_info, 16 * (size_t)scene->grid_entries);

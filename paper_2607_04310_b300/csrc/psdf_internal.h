@@ -112,6 +112,13 @@ struct CullGrid {
   const int *tl = nullptr;     // tile lists (device)
   const float4 *ab = nullptr;  // [entries] AABB of tile tl[i], beside it (device)
   const int4 *info = nullptr;  // [entries] TileInfo of tile tl[i] (device)
+  // The same lists padded to a fixed capacity per cell (cell c's entries at
+  // c * cap .. c * cap + cap - 1; padding: an empty AABB and tile -2), so
+  // that a pose reaches its entries from its cell index in one load; cap = 0
+  // when some list is too long (the lists above serve then).
+  int cap = 0;
+  const float4 *fab = nullptr;
+  const int4 *finfo = nullptr;
 };
 
 }  // namespace psdf
@@ -135,6 +142,8 @@ struct psdf_scene {
   int *d_cell_off = nullptr, *d_cell_tiles = nullptr;
   float4 *d_cell_aabbs = nullptr;
   int4 *d_cell_info = nullptr;
+  float4 *d_cell_fab = nullptr;  // fixed-capacity lists (grid.cap > 0)
+  int4 *d_cell_finfo = nullptr;
   psdf::CullObs *d_cull_obs = nullptr;  // [M] cull records in sorted order
   float4 *d_tile_ab = nullptr;          // [n_tiles] AABBs
   int4 *d_tile_info = nullptr;          // [n_tiles] TileInfo

@@ -83,6 +83,8 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_cell_tiles);
   cudaFree(s->d_cell_aabbs);
   cudaFree(s->d_cell_info);
+  cudaFree(s->d_cell_fab);
+  cudaFree(s->d_cell_finfo);
   cudaFree(s->d_cull_obs);
   cudaFree(s->d_tile_ab);
   cudaFree(s->d_tile_info);
@@ -434,6 +436,28 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
     s->grid.tl = s->d_cell_tiles;
     s->grid.ab = s->d_cell_aabbs;
     s->grid.info = s->d_cell_info;
+    // fixed-capacity copies when every list is short (a multiple of 16 slots)
+    int longest = 0;
+    for (size_t c = 0; c + 1 < cell_off.size(); ++c)
+      longest = std::max(longest, cell_off[c + 1] - cell_off[c]);
+    const int cap = (longest + 15) / 16 * 16;
+    if (!rc && cap > 0 && cap <= 64) {
+      const size_t cells = cell_off.size() - 1;
+      std::vector<float4> fab(cells * cap, make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY));
+      std::vector<int4> finfo(cells * cap, make_int4(0, 0, 0, -2));
+      for (size_t c = 0; c < cells; ++c)
+        for (int e = cell_off[c]; e < cell_off[c + 1]; ++e) {
+          fab[c * cap + (e - cell_off[c])] = cell_aabbs[e];
+          finfo[c * cap + (e - cell_off[c])] = cell_info[e];
+        }
+      rc = dev_upload(&s->d_cell_fab, fab, st, &s->device_bytes);
+      if (!rc) rc = dev_upload(&s->d_cell_finfo, finfo, st, &s->device_bytes);
+      if (!rc) {
+        s->grid.cap = cap;
+        s->grid.fab = s->d_cell_fab;
+        s->grid.finfo = s->d_cell_finfo;
+      }
+    }
   }
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
