@@ -6,16 +6,17 @@
 One step = one pass of the value+gradient path over the dense-clutter
 workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
 100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
-the exact tile cull (one fused kernel: each pose ranks the tiles of its grid
-cell, proposes the nearest by the conservative bound, takes an upper bound
-from the proposed tile's obstacle circles, and the CTA evaluates exactly
-every obstacle of every tile whose bounds do not exceed it, then the
-epilogue with the pose gradient) followed by PSDF_Backward (pose and
-edge-endpoint gradients of sum(phi)) from the forward's saved rows.  The
-metric counts pose x edge pairs of the whole scene per second (the cull's
-results equal the full scan's bit for bit, checked in the run); the full
-scan and the cull with the learned proposal (the tile-proposal network
-re-ranking each pose's 8 nearest tiles) are timed on the same GPU.
+the exact tile cull (one fused kernel: each pose takes an upper bound from
+the 8 obstacle circles its cell of the scene's upper-bound grid keeps, and
+the CTA evaluates exactly every obstacle of every tile of the pose's cull-grid
+cell whose bounds do not exceed it, then the epilogue with the pose
+gradient) followed by PSDF_Backward (pose and edge-endpoint gradients of
+sum(phi)) from the forward's saved rows.  The metric counts pose x edge
+pairs of the whole scene per second (the cull's results equal the full
+scan's bit for bit, checked in the run); the full scan, the bound-ordered
+cull (upper bound from the tile of smallest AABB bound) and the learned
+cull (the tile-proposal network re-ranking each pose's 8 nearest tiles) are
+timed on the same GPU.
 
 Under torchrun (N > 1) every rank evaluates its own 4,096 poses on the same
 scene (weak scaling, no data-path collective); the value is the total pair
@@ -221,12 +222,14 @@ def run_reference(a, rank, world):
 # B300 arm
 # --------------------------------------------------------------------------
 CULL_K = 1
-# The tile proposal of the headline step: "bound" (the conservative AABB
-# bound's order) or "mlp" (the trained network).  On the sort-tile-recursive
-# tiles of this workload the network picks the bound's tile 93 % of the time
-# and adds its ranking to every pose's chain, so the bound order is the faster
-# exact path; the learned cull is measured beside it.
-HEADLINE_MODE = "bound"
+# Where the headline step's upper bound comes from: "circles" (the scene's
+# upper-bound grid: 8 obstacle circles per cell, no proposal), "bound" (the
+# circles of the tile of smallest AABB bound) or "mlp" (of the trained
+# network's best tile).  On the sort-tile-recursive tiles of this workload the
+# network picks the bound's tile 93 % of the time and adds its ranking to
+# every pose's chain, and the grid needs no ranking at all, so the grid is the
+# fastest exact path; the other two are measured beside it.
+HEADLINE_MODE = "circles"
 
 
 def _time_steps(step, steps, flush, stream, clocks=None):
@@ -570,6 +573,7 @@ def run_b300(a, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     learned = psdf.CullOpts(psdf.PROPOSE_MLP, CULL_K)
     bound = psdf.CullOpts(psdf.PROPOSE_BOUND, CULL_K)
+    circles = psdf.CullOpts(psdf.PROPOSE_CIRCLES, CULL_K)
 
     # every library call launches on the current stream (None), so the same
     # step functions run eagerly or under CUDA-graph capture
@@ -577,10 +581,10 @@ def run_b300(a, rank, world, local):
     # gradient rows, which the epilogue computes anyway) and scatters them
     saved = torch.empty((P, psdf.SAVED_FLOATS), dtype=torch.float32, device=dev)
 
-    # the headline step proposes tiles by the bound (HEADLINE_MODE); the
-    # learned proposal is timed beside it on the same GPU
-    head = bound if HEADLINE_MODE == "bound" else learned
-    head_net = None if HEADLINE_MODE == "bound" else mlp
+    # the headline step's upper bound (HEADLINE_MODE); the bound-ordered and
+    # the learned proposal are timed beside it on the same GPU
+    head = {"circles": circles, "bound": bound, "mlp": learned}[HEADLINE_MODE]
+    head_net = mlp if HEADLINE_MODE == "mlp" else None
 
     def step_head(ps=poses):
         psdf.psdf_eval_culled_save(w.footprint, scene, head_net, head, ps, prm, phi, dphi, act,
@@ -594,6 +598,11 @@ def run_b300(a, rank, world, local):
 
     def step_learned():
         psdf.psdf_eval_culled_save(w.footprint, scene, mlp, learned, poses, prm, phi, dphi, act,
+                                   saved, cws)
+        psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
+
+    def step_bound():
+        psdf.psdf_eval_culled_save(w.footprint, scene, None, bound, poses, prm, phi, dphi, act,
                                    saved, cws)
         psdf.psdf_backward_saved(scene, saved, gphi, gpose, gedges)
 
@@ -614,8 +623,10 @@ def run_b300(a, rank, world, local):
 
     step_learned()
     exact_learned = same_as_full()
+    step_bound()
+    exact_bound = same_as_full()
     step_head()
-    exact = same_as_full() and exact_learned
+    exact = same_as_full() and exact_learned and exact_bound
     for _ in range(max(a.warmup, 3)):
         step_head()
     torch.cuda.synchronize()
@@ -654,6 +665,11 @@ def run_b300(a, rank, world, local):
         replay_learned()
     learned_ms = sum(_time_steps(replay_learned, a.steps, flush, stream)) / a.steps
     st_learned = psdf.psdf_cull_stats_read(cws, stream)
+    replay_bound, g_bound = _graph(step_bound)
+    for _ in range(3):
+        replay_bound()
+    bound_ms = sum(_time_steps(replay_bound, a.steps, flush, stream)) / a.steps
+    st_bound = psdf.psdf_cull_stats_read(cws, stream)
     replay_rec, g_rec = _graph(step_head_recompute)
     for _ in range(3):
         replay_rec()
@@ -748,13 +764,15 @@ def run_b300(a, rank, world, local):
         "impl": "b300",
         "config": {"workload": WORKLOAD, "poses_per_gpu": P, "edges": w.E,
                    "obstacles": w.M, "tiles": T, "footprint_vertices": m,
-                   "path": ("%s tile cull (k=%d) + pose gradient + backward (from the "
-                            "forward's saved rows); %s" % (
-                                "bound-ordered" if HEADLINE_MODE == "bound" else "learned",
-                                CULL_K,
-                                "the learned proposal, timed beside it (learned_cull), costs "
-                                "more than it saves on these sort-tile-recursive tiles"
-                                if HEADLINE_MODE == "bound" else "")),
+                   "path": ("%s + pose gradient + backward (from the forward's saved "
+                            "rows); %s" % (
+                                {"circles": "exact tile cull, upper bound from the scene's "
+                                            "upper-bound grid (8 obstacle circles per cell)",
+                                 "bound": "bound-ordered tile cull (k=%d)" % CULL_K,
+                                 "mlp": "learned tile cull (k=%d)" % CULL_K}[HEADLINE_MODE],
+                                "the bound-ordered cull (bound_cull) and the learned proposal "
+                                "(learned_cull) are timed beside it; the network costs more "
+                                "than it saves on these sort-tile-recursive tiles")),
                    "pair_count": "effective: poses x edges of the whole scene",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "speedup_vs_full_scan": full_ms / ms_step,
@@ -772,6 +790,13 @@ def run_b300(a, rank, world, local):
                                "note": "the same step through psdf_eval_culled + psdf_backward "
                                        "(the backward recomputes the active pair's geometry "
                                        "instead of reading the forward's saved rows)"},
+        "bound_cull": {"value": pairs / (bound_ms / 1000.0), "ms_per_step": bound_ms,
+                       "exact_vs_full_scan": exact_bound,
+                       "evaluated_obstacles": int(st_bound.evaluated_obstacles),
+                       "listed_pairs": int(st_bound.proposed_items + st_bound.fallback_items),
+                       "fallback_rate": st_bound.fallback_poses / P,
+                       "note": "upper bound from the circles of each pose's tile of smallest "
+                               "AABB bound (k = %d)" % CULL_K},
         "learned_cull": {"value": pairs / (learned_ms / 1000.0), "ms_per_step": learned_ms,
                          "exact_vs_full_scan": exact_learned,
                          "evaluated_fraction": (st_learned.proposed_items
@@ -783,12 +808,12 @@ def run_b300(a, rank, world, local):
                          "network_heldout_top1": wmeta.get("heldout", {}).get("top1_mlp"),
                          "network_flops_per_step": roofline.flops_network(8 * P),
                          "gain_vs_bound": {
-                             "ms_per_step": learned_ms - ms_step,
+                             "ms_per_step": learned_ms - bound_ms,
                              "listed_pairs": int(st_learned.proposed_items
                                                  + st_learned.fallback_items)
-                             - int(st.proposed_items + st.fallback_items),
+                             - int(st_bound.proposed_items + st_bound.fallback_items),
                              "evaluated_obstacles": int(st_learned.evaluated_obstacles)
-                             - int(st.evaluated_obstacles),
+                             - int(st_bound.evaluated_obstacles),
                              "note": "positive = the learned proposal costs more than the "
                                      "bound order"}},
         "cull": {"candidate_fraction": st.proposed_items / (P * T),

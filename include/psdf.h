@@ -277,23 +277,27 @@ int psdf_backward_saved(const psdf_scene *scene, const float *saved, int64_t P,
 
 /* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
  * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
- * the (pose, tile) pairs.  Each pose proposes its k best tiles -- by the
- * conservative bound below (PSDF_PROPOSE_BOUND), or (PSDF_PROPOSE_MLP) by the
- * tile-proposal network's predicted signed distance among the 8 tiles with
- * the smallest bounds, among the tiles of the pose's cell in the scene's
+ * the (pose, tile) pairs.  Each pose first takes an upper bound UB >= phi
+ * from obstacle circles (a circle containing the obstacle, and a disc inside
+ * it): under PSDF_PROPOSE_BOUND and PSDF_PROPOSE_MLP from the circles of the
+ * obstacles of its k proposed tiles -- the k tiles of smallest bound (BOUND),
+ * or the network's k tiles of smallest predicted signed distance among the 8
+ * of smallest bound (MLP), among the tiles of the pose's cell in the scene's
  * cull grid (every tile within one cell size of the pose; all tiles for a
- * pose outside the grid).  The circles containing the proposed tiles'
- * obstacles give an upper bound UB >= phi; every other tile whose
- * conservative lower bound
+ * pose outside the grid); under PSDF_PROPOSE_CIRCLES from the 8 circles the
+ * scene keeps for the pose's cell of its upper-bound grid (no proposal: the
+ * circles whose far side is nearest the cell, chosen when the scene is
+ * built).  Then every tile whose conservative lower bound
  *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
- * does not exceed UB is added ("fallback" pairs), taken from the cell's list
- * when those tiles all lie within its reach, else from all tiles.  All listed pairs are
- * evaluated exactly in one pass, skipping obstacles whose circle bound
- * exceeds the smaller of UB and the values already found.  No skipped tile
- * or obstacle can hold a smaller value or a tie, so phi, the active pair and
- * the gradient equal the full scan's.  The network only changes how much
- * work the exact part does.  Pairs are bucketed by tile and each tile is
- * staged once for all the poses that need it. */
+ * does not exceed UB is listed ("fallback" pairs; all listed pairs are
+ * fallback pairs under PSDF_PROPOSE_CIRCLES), taken from the cell's list
+ * when those tiles all lie within its reach, else from all tiles.  The listed
+ * tiles' obstacles whose circle bound exceeds UB are skipped, the rest are
+ * evaluated exactly.  No skipped tile or obstacle can hold a smaller value or
+ * a tie, so phi, the active pair and the gradient equal the full scan's.  The
+ * proposal only changes how much work the exact part does.  One launch: 16
+ * poses a CTA, each pose's ranking and bound by 16 lanes, the tile tests,
+ * circle tests and exact evaluations shared out over the CTA. */
 typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
 
 /* The cull grid of a scene: a uniform grid of nx x ny square cells of side
@@ -322,11 +326,12 @@ int psdf_scene_cull_grid_copy(const psdf_scene *scene, int32_t *offsets, int32_t
 #define PSDF_MLP_HIDDEN 64
 #define PSDF_PROPOSE_BOUND 1
 #define PSDF_PROPOSE_MLP 2
+#define PSDF_PROPOSE_CIRCLES 3
 #define PSDF_CULL_MAX_K 4
 
 typedef struct {
-  int32_t mode; /* PSDF_PROPOSE_BOUND or PSDF_PROPOSE_MLP */
-  int32_t k;    /* proposals per pose, 1..PSDF_CULL_MAX_K */
+  int32_t mode; /* PSDF_PROPOSE_BOUND, PSDF_PROPOSE_MLP or PSDF_PROPOSE_CIRCLES */
+  int32_t k;    /* proposals per pose, 1..PSDF_CULL_MAX_K (unused by PSDF_PROPOSE_CIRCLES) */
 } psdf_cull_opts;
 
 typedef struct {
@@ -377,7 +382,7 @@ int psdf_tile_lower_bounds(const float *footprint, int32_t m, const psdf_scene *
 
 size_t psdf_cull_workspace_bytes(int64_t P, const psdf_scene *scene);
 
-/* dphi and active are nullable; mlp may be NULL for PSDF_PROPOSE_BOUND. */
+/* dphi and active are nullable; mlp may be NULL except for PSDF_PROPOSE_MLP. */
 int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,
                      const psdf_mlp *mlp, const psdf_cull_opts *opts, const float *poses,
                      int64_t P, const psdf_params *params, float *phi, float *dphi,

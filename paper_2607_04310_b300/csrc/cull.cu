@@ -304,6 +304,15 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
   return (int)fy * g.nx + (int)fx;
 }
 
+// The pose's cell in the upper-bound grid, clamped to the grid (a pose
+// outside it takes the nearest cell's circles; any circle is a valid bound).
+__device__ __forceinline__ long long ub_cell(const UbGrid &g, float px, float py)
+{
+  const float fx = fminf(fmaxf((px - g.x0) * g.inv_cs, 0.f), (float)(g.nx - 1));
+  const float fy = fminf(fmaxf((py - g.y0) * g.inv_cs, 0.f), (float)(g.ny - 1));
+  return (long long)(int)fy * g.nx + (int)fx;
+}
+
 // ---------------------------------------------------------------------------
 // the fused cull: each pose's proposals, exact evaluation and epilogue by
 // its own 16 lanes, in one launch
@@ -319,10 +328,16 @@ constexpr int kSegCap = kPoses * 16;  // segments of one round: 16 tiles per pos
 constexpr int kSegsPerPass = kCullThreads / 8;  // segments whose circles a pass tests
 constexpr int kQCap = 2 * kCullThreads * kFilt;  // queued (pose, obstacle) items: two steps
 constexpr int kStatWords = 8;      // counters per CTA in the workspace
+constexpr int kOutSaved = 4;       // out_s: phi, active pair, -, -, the saved record
+constexpr int kOutWords = kOutSaved + 16;
 constexpr int kStatBase = 32;      // first counter word (the header is 256 bytes)
 constexpr long long kPrefetchChunk = 16384;  // bytes per bulk L2 prefetch
 constexpr int kMaxPrefetch = 8;
 constexpr unsigned kFull = 0xffffffffu;
+// where the upper bound comes from
+constexpr int kPropBound = 1;    // the circles of the k tiles of smallest bound
+constexpr int kPropNet = 2;      // the circles of the network's k best tiles
+constexpr int kPropCircles = 3;  // the pose's cell of the upper-bound grid
 
 // Per-CTA counters (workspace words kStatBase + kStatWords * CTA + i).
 enum CullStat { kStProp, kStFb, kStFbPoses, kStBound, kStCirc, kStObs, kStEdges, kStCount };
@@ -343,6 +358,7 @@ struct CullArgs {
   const float *poses;
   long long P;
   CullGrid grid;
+  UbGrid ub;                // upper-bound circles (kPropCircles)
   const float4 *tile_ab;    // all tiles: poses outside the grid, bounds beyond its reach
   const int4 *tile_info;
   int T;
@@ -416,35 +432,42 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
 
 // One CTA = 16 poses; one warp = 2 poses, 16 lanes each (lanes 0-15 pose
 // a, 16-31 pose b) for the per-pose stages:
-//  1. ranking: the tiles of the pose's cell in the cull grid (every tile
-//     within one cell size of it), else all tiles; lane hl takes entries hl,
-//     hl + 16, ... and keeps its 4 smallest AABB distances; rounds of a
-//     16-lane minimum give the pose's smallest ones in order.  The pose
-//     proposes its K nearest tiles, or (NET) the K best network scores among
-//     its 8 nearest (2 poses x 8 candidates = 16 rows of one tensor-core
-//     pass).
+//  1. ranking (PROP = bound or network): the tiles of the pose's cell in the
+//     cull grid (every tile within one cell size of it), else all tiles;
+//     lane hl takes entries hl, hl + 16, ... and keeps its 4 smallest AABB
+//     distances; rounds of a 16-lane minimum give the pose's smallest ones
+//     in order.  The pose proposes its K nearest tiles, or (network) the K
+//     best network scores among its 8 nearest (2 poses x 8 candidates = 16
+//     rows of one tensor-core pass).
 //  2. an upper bound UB >= phi from the circles of the proposed tiles'
-//     obstacles.
+//     obstacles, or (PROP = circles, no stage 1) from the 8 circles of the
+//     pose's cell in the scene's upper-bound grid, one a lane, loaded beside
+//     the cell's tile entries.
 // then, by the whole CTA, in rounds over chunks of 16 list entries per pose
 // (the cell's list when every tile whose bound does not exceed UB lies
 // within the grid's reach, else all tiles):
 //  3. each pose's tiles of the chunk whose bound does not exceed its UB (the
 //     proposed ones always) join the round's list of segments (pose, first
 //     obstacle, obstacles);
-//  4. 16 threads per segment test its obstacles' circle bounds against the
+//  4. 8 threads per segment test its obstacles' circle bounds against the
 //     pose's UB; the survivors go to one CTA-wide queue, evaluated exactly
 //     by 4 lanes each, and merged into the pose's 64-bit key in shared
-//     memory (atomicMin).  Sharing the work over the CTA's 256 threads keeps
+//     memory (atomicMin); the item holding a pose's minimum after a pass
+//     leaves its detail.  Sharing the work over the CTA's 256 threads keeps
 //     a pose with several nearby tiles from stretching its own warp.
-//  5. epilogue of every pose (4 lanes each, or one for the soft minimum) by
-//     the first two warps: value, active pair, gradient, saved rows.
+//  5. epilogue: the hard minimum's gradient by lane 0 of each pose's half
+//     from the winner's detail, the outputs stored by its 16 lanes; the
+//     soft minimum's by one lane a pose in the first two warps.  Each warp
+//     adds its counters to the CTA's workspace words.
 // No skipped tile or obstacle can hold a value at or below phi, and the key
 // minimum does not depend on the order of evaluation, so the outputs equal
 // the full scan's bit for bit.
-template <int M, bool NET, bool SOFT>
+template <int M, int PROP, bool SOFT>
 __global__ void __launch_bounds__(kCullThreads, 2)
     cull_kernel(const FootprintK F, const ParamsK prm, const CullArgs a)
 {
+  constexpr bool NET = PROP == kPropNet;
+  constexpr bool CIRC = PROP == kPropCircles;
   __shared__ int ub_s0[kCullWarps][2][kMaxK + 1];  // proposed tiles, flattened
   __shared__ int ub_st[kCullWarps][2][kMaxK + 1];
   __shared__ int cand_s[kCullWarps][2][kPre];
@@ -452,13 +475,17 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   __shared__ float4 pose_s[kPoses];
   __shared__ float thr_s[kPoses];
   __shared__ unsigned long long key_s[kPoses];
-  __shared__ Active det_s[kPoses];  // the winning obstacle's detail (hard minimum)
-  __shared__ int4 drec_s[kPoses];   // and its record
+  // hard minimum: the winning item's detail and obstacle record, then each
+  // pose's outputs -- phi, the active pair, and the saved record (its first
+  // three words the pose gradient); a pose without obstacles keeps the
+  // initial ones
+  __shared__ Active det_s[kPoses];
+  __shared__ int4 drec_s[kPoses];
+  __shared__ float out_s[kPoses][kOutWords];
   __shared__ int seg_first[kSegCap], seg_n[kSegCap];
   __shared__ unsigned char seg_pose[kSegCap];
   __shared__ int q_s[kQCap];
   __shared__ int nseg_s, nq_s;
-  __shared__ unsigned st_s[kStCount];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int half = lane >> 4, hl = lane & 15;
@@ -466,9 +493,22 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   const int j = 2 * warp + half;  // the pose within the CTA
   const long long p = (long long)blockIdx.x * kPoses + j;
   const bool valid = p < a.P;
+  const bool save = a.saved != nullptr;
+  const bool want_grad = save || a.dphi != nullptr;
   int *sg0 = ub_s0[warp][half], *sgt = ub_st[warp][half];
-  if (tid < kStCount) st_s[tid] = 0u;
-  if (tid < kPoses) key_s[tid] = ~0ull;
+  // the CTA's counters, added to by every warp at the end
+  if (tid < kStatWords) a.ws[kStatBase + (long long)blockIdx.x * kStatWords + tid] = 0ull;
+  if (tid < kPoses) {
+    key_s[tid] = ~0ull;
+    if constexpr (!SOFT) {  // no obstacle: phi = +inf, no pair, no gradient rows
+      out_s[tid][0] = kInf;
+      out_s[tid][1] = __uint_as_float(PSDF_PAIR_NONE);
+      Grad none;
+      none.gp[0] = none.gp[1] = none.gp[2] = 0.f;
+      none.nrow = -1;
+      saved_words(none, &out_s[tid][kOutSaved]);
+    }
+  }
   if (tid == 0) {
     nseg_s = 0;
     nq_s = 0;
@@ -497,12 +537,12 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   const int cell = valid ? grid_cell(a.grid, px, py) : -1;
   Entries E = entries_of(a, cell, cell >= 0);
   if (!valid) E.hi = E.lo;
-  float sc[kRL];
-  int id[kRL];
-#pragma unroll
-  for (int i = 0; i < kRL; ++i) {
-    sc[i] = kInf;
-    id[i] = -1;
+  // (upper-bound grid) the pose's cell's circles, one a lane, loaded beside
+  // the cell's tile entries
+  float4 ubc = make_float4(0.f, 0.f, kInf, -kInf);
+  if constexpr (CIRC) {
+    if (valid && hl < kUbCircles && a.ub.nx > 0)
+      ubc = __ldg(a.ub.circ + ub_cell(a.ub, px, py) * kUbCircles + hl);
   }
   // the lane's first two entries (hl, hl + 16) stay in registers for the
   // tile tests below (cell lists rarely hold more than 32)
@@ -523,144 +563,165 @@ __global__ void __launch_bounds__(kCullThreads, 2)
                       __popc(__ballot_sync(kFull, kinf[1].w >= 0) & hmask);
     if (cell >= 0 && a.grid.cap > 0 && nreal < 32) E.hi = E.lo + nreal;
   }
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-    if (E.lo + hl + 16 * q < E.hi && kinf[q].w != -2) {
-      topk_insert<kRL>(sc, id, aabb_d2(kab[q], px, py), hl + 16 * q);
-      ++n_bound;
-    }
-  for (int i = E.lo + hl + 32; i < E.hi; i += 16) {
-    const float4 ab = __ldg(E.ab + i);
-    if (!(ab.x <= ab.z)) continue;  // a padding slot (empty AABB)
-    topk_insert<kRL>(sc, id, aabb_d2(ab, px, py), i - E.lo);
-    ++n_bound;
-  }
-  // rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys (the
-  // top 16 bits of the squared distance -- not negative, so its bits order
-  // like the value, to 1/128 -- over the entry's 16 bits; an entry sits in
-  // one lane only, so the lane whose head won pops it)
-  const int R = NET ? kPre : K;
-  int cand[kPre];
-  {
-    int head = 0;
-#pragma unroll
-    for (int r = 0; r < kPre; ++r) {
-      cand[r] = -1;
-      if (r < R) {  // uniform over the warp
-        unsigned mine = ~0u;
-#pragma unroll
-        for (int i = 0; i < kRL; ++i)
-          if (i == head && id[i] >= 0)
-            mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
-        const unsigned k0 = __reduce_min_sync(kFull, half == 0 ? mine : ~0u);
-        const unsigned k1 = __reduce_min_sync(kFull, half == 1 ? mine : ~0u);
-        const unsigned key = half ? k1 : k0;
-        cand[r] = key != ~0u ? (int)(key & 0xffffu) : -1;
-        if (key != ~0u && key == mine) ++head;
-      }
-    }
-  }
   int best[kMaxK];
 #pragma unroll
-  for (int i = 0; i < kMaxK; ++i) best[i] = i < K ? cand[i] : -1;
-  if constexpr (NET) {
-    if (hl == 0)
+  for (int i = 0; i < kMaxK; ++i) best[i] = -1;
+  if constexpr (!CIRC) {
+    float sc[kRL];
+    int id[kRL];
 #pragma unroll
-      for (int r = 0; r < kPre; ++r) cand_s[warp][half][r] = cand[r];
-    __syncwarp();
-    // lane 4 g + q: candidate g of both poses, quarter q of its inputs
-    const int g = lane >> 2, q = lane & 3;
-    // each pose's entries (its cell's list, or all tiles): pointers of lanes 0 and 16
-    const float4 *abA = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 0);
-    const float4 *abB = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 16);
-    const int4 *infA = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 0);
-    const int4 *infB = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 16);
-    const int loA = __shfl_sync(kFull, E.lo, 0), loB = __shfl_sync(kFull, E.lo, 16);
-    const int ta = cand_s[warp][0][g], tb = cand_s[warp][1][g];
-    float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
-    float efa = 0.f, efb = 0.f;
-    if (ta >= 0) {
-      const float4 v = __ldg(abA + loA + ta);
-      const int4 inf = __ldg(infA + loA + ta);
-      aba[0] = v.x; aba[1] = v.y; aba[2] = v.z; aba[3] = v.w;
-      efa = (float)inf.z * (1.f / 256.f);
-    }
-    if (tb >= 0) {
-      const float4 v = __ldg(abB + loB + tb);
-      const int4 inf = __ldg(infB + loB + tb);
-      abb[0] = v.x; abb[1] = v.y; abb[2] = v.z; abb[3] = v.w;
-      efb = (float)inf.z * (1.f / 256.f);
-    }
-    const float pxa = __shfl_sync(kFull, px, 0), pya = __shfl_sync(kFull, py, 0);
-    const float ca = __shfl_sync(kFull, c, 0), sa = __shfl_sync(kFull, s, 0);
-    const float pxb = __shfl_sync(kFull, px, 16), pyb = __shfl_sync(kFull, py, 16);
-    const float cb = __shfl_sync(kFull, c, 16), sb = __shfl_sync(kFull, s, 16);
-    float s_a, s_b;
-    mlp_rows_pair(w, q, aba, efa, pxa, pya, ca, sa, abb, efb, pxb, pyb, cb, sb, F.radius, s_a,
-                  s_b);
-    if (q == 0) {
-      score_s[warp][0][g] = ta >= 0 ? s_a + a.b2 : kInf;
-      score_s[warp][1][g] = tb >= 0 ? s_b + a.b2 : kInf;
-    }
-    __syncwarp();
-    float bsc[kMaxK];
-#pragma unroll
-    for (int i = 0; i < kMaxK; ++i) {
-      bsc[i] = kInf;
-      best[i] = -1;
+    for (int i = 0; i < kRL; ++i) {
+      sc[i] = kInf;
+      id[i] = -1;
     }
 #pragma unroll
-    for (int i = 0; i < kPre; ++i)
-      if (cand[i] >= 0) topk_insert<kMaxK>(bsc, best, score_s[warp][half][i], cand[i]);
+    for (int q = 0; q < 2; ++q)
+      if (E.lo + hl + 16 * q < E.hi && kinf[q].w != -2) {
+        topk_insert<kRL>(sc, id, aabb_d2(kab[q], px, py), hl + 16 * q);
+        ++n_bound;
+      }
+    for (int i = E.lo + hl + 32; i < E.hi; i += 16) {
+      const float4 ab = __ldg(E.ab + i);
+      if (!(ab.x <= ab.z)) continue;  // a padding slot (empty AABB)
+      topk_insert<kRL>(sc, id, aabb_d2(ab, px, py), i - E.lo);
+      ++n_bound;
+    }
+    // rounds of a 16-lane minimum over the lanes' heads, as 32-bit keys (the
+    // top 16 bits of the squared distance -- not negative, so its bits order
+    // like the value, to 1/128 -- over the entry's 16 bits; an entry sits in
+    // one lane only, so the lane whose head won pops it)
+    const int R = NET ? kPre : K;
+    int cand[kPre];
+    {
+      int head = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxK; ++i)
-      if (i >= K) best[i] = -1;
-  }
+      for (int r = 0; r < kPre; ++r) {
+        cand[r] = -1;
+        if (r < R) {  // uniform over the warp
+          unsigned mine = ~0u;
+#pragma unroll
+          for (int i = 0; i < kRL; ++i)
+            if (i == head && id[i] >= 0)
+              mine = (__float_as_uint(sc[i]) & 0xffff0000u) | (unsigned)id[i];
+          const unsigned k0 = __reduce_min_sync(kFull, half == 0 ? mine : ~0u);
+          const unsigned k1 = __reduce_min_sync(kFull, half == 1 ? mine : ~0u);
+          const unsigned key = half ? k1 : k0;
+          cand[r] = key != ~0u ? (int)(key & 0xffffu) : -1;
+          if (key != ~0u && key == mine) ++head;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i) best[i] = i < K ? cand[i] : -1;
+    if constexpr (NET) {
+      if (hl == 0)
+#pragma unroll
+        for (int r = 0; r < kPre; ++r) cand_s[warp][half][r] = cand[r];
+      __syncwarp();
+      // lane 4 g + q: candidate g of both poses, quarter q of its inputs
+      const int g = lane >> 2, q = lane & 3;
+      // each pose's entries (its cell's list, or all tiles): pointers of lanes 0 and 16
+      const float4 *abA = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 0);
+      const float4 *abB = (const float4 *)__shfl_sync(kFull, (unsigned long long)E.ab, 16);
+      const int4 *infA = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 0);
+      const int4 *infB = (const int4 *)__shfl_sync(kFull, (unsigned long long)E.info, 16);
+      const int loA = __shfl_sync(kFull, E.lo, 0), loB = __shfl_sync(kFull, E.lo, 16);
+      const int ta = cand_s[warp][0][g], tb = cand_s[warp][1][g];
+      float aba[4] = {0.f, 0.f, 0.f, 0.f}, abb[4] = {0.f, 0.f, 0.f, 0.f};
+      float efa = 0.f, efb = 0.f;
+      if (ta >= 0) {
+        const float4 v = __ldg(abA + loA + ta);
+        const int4 inf = __ldg(infA + loA + ta);
+        aba[0] = v.x; aba[1] = v.y; aba[2] = v.z; aba[3] = v.w;
+        efa = (float)inf.z * (1.f / 256.f);
+      }
+      if (tb >= 0) {
+        const float4 v = __ldg(abB + loB + tb);
+        const int4 inf = __ldg(infB + loB + tb);
+        abb[0] = v.x; abb[1] = v.y; abb[2] = v.z; abb[3] = v.w;
+        efb = (float)inf.z * (1.f / 256.f);
+      }
+      const float pxa = __shfl_sync(kFull, px, 0), pya = __shfl_sync(kFull, py, 0);
+      const float ca = __shfl_sync(kFull, c, 0), sa = __shfl_sync(kFull, s, 0);
+      const float pxb = __shfl_sync(kFull, px, 16), pyb = __shfl_sync(kFull, py, 16);
+      const float cb = __shfl_sync(kFull, c, 16), sb = __shfl_sync(kFull, s, 16);
+      float s_a, s_b;
+      mlp_rows_pair(w, q, aba, efa, pxa, pya, ca, sa, abb, efb, pxb, pyb, cb, sb, F.radius, s_a,
+                    s_b);
+      if (q == 0) {
+        score_s[warp][0][g] = ta >= 0 ? s_a + a.b2 : kInf;
+        score_s[warp][1][g] = tb >= 0 ? s_b + a.b2 : kInf;
+      }
+      __syncwarp();
+      float bsc[kMaxK];
+#pragma unroll
+      for (int i = 0; i < kMaxK; ++i) {
+        bsc[i] = kInf;
+        best[i] = -1;
+      }
+#pragma unroll
+      for (int i = 0; i < kPre; ++i)
+        if (cand[i] >= 0) topk_insert<kMaxK>(bsc, best, score_s[warp][half][i], cand[i]);
+#pragma unroll
+      for (int i = 0; i < kMaxK; ++i)
+        if (i >= K) best[i] = -1;
+    }
+  }  // !CIRC
 
-  // ---- 2. the upper bound: circles of the proposed tiles' obstacles -------
+  // ---- 2. the upper bound: circles of the proposed tiles' obstacles, or of
+  // the pose's upper-bound cell ---------------------------------------------
   int ptile[kMaxK];
   int nseg = 0, N = 0;
-#pragma unroll
-  for (int i = 0; i < kMaxK; ++i) {
-    // entry best[i] of the half: lane best % 16, register slot best / 16
-    // (a load for entries beyond the kept ones)
-    const int b = best[i];
-    const int slot = b >= 0 ? b >> 4 : 0;
-    int4 kept = slot == 0 ? kinf[0] : kinf[1];
-    int4 inf;
-    inf.x = __shfl_sync(kFull, kept.x, (half << 4) + (b & 15));
-    inf.y = __shfl_sync(kFull, kept.y, (half << 4) + (b & 15));
-    inf.w = __shfl_sync(kFull, kept.w, (half << 4) + (b & 15));
-    if (b >= 32) inf = __ldg(E.info + E.lo + b);
-    ptile[i] = -1;
-    if (b >= 0) {
-      ptile[i] = inf.w;
-      if (hl == 0) {
-        sg0[nseg] = inf.x;
-        sgt[nseg] = N;
-      }
-      N += inf.y;
-      ++nseg;
-    }
-  }
-  if (hl == 0) sgt[nseg] = N;
-  const int n_prop = nseg;
-  __syncwarp();
   float ubp = kInf;
-  for (int f0 = hl; f0 < N; f0 += 16 * kFilt) {
-    float4 cc[kFilt];
 #pragma unroll
-    for (int q = 0; q < kFilt; ++q) {
-      const int f = f0 + 16 * q;
-      if (f < N) cc[q] = __ldg(&a.obs[flat_obstacle(sg0, sgt, nseg, f)].circ);
+  for (int i = 0; i < kMaxK; ++i) ptile[i] = -1;
+  if constexpr (CIRC) {
+    if (valid && hl < kUbCircles) {
+      ubp = circle_ub(ubc, px, py, F.radius, F.inner);
+      ++n_circ;
     }
+  } else {
 #pragma unroll
-    for (int q = 0; q < kFilt; ++q)
-      if (f0 + 16 * q < N) {
-        ubp = fminf(ubp, circle_ub(cc[q], px, py, F.radius, F.inner));
-        ++n_circ;
+    for (int i = 0; i < kMaxK; ++i) {
+      // entry best[i] of the half: lane best % 16, register slot best / 16
+      // (a load for entries beyond the kept ones)
+      const int b = best[i];
+      const int slot = b >= 0 ? b >> 4 : 0;
+      int4 kept = slot == 0 ? kinf[0] : kinf[1];
+      int4 inf;
+      inf.x = __shfl_sync(kFull, kept.x, (half << 4) + (b & 15));
+      inf.y = __shfl_sync(kFull, kept.y, (half << 4) + (b & 15));
+      inf.w = __shfl_sync(kFull, kept.w, (half << 4) + (b & 15));
+      if (b >= 32) inf = __ldg(E.info + E.lo + b);
+      ptile[i] = -1;
+      if (b >= 0) {
+        ptile[i] = inf.w;
+        if (hl == 0) {
+          sg0[nseg] = inf.x;
+          sgt[nseg] = N;
+        }
+        N += inf.y;
+        ++nseg;
       }
+    }
+    if (hl == 0) sgt[nseg] = N;
+    __syncwarp();
+    for (int f0 = hl; f0 < N; f0 += 16 * kFilt) {
+      float4 cc[kFilt];
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q) {
+        const int f = f0 + 16 * q;
+        if (f < N) cc[q] = __ldg(&a.obs[flat_obstacle(sg0, sgt, nseg, f)].circ);
+      }
+#pragma unroll
+      for (int q = 0; q < kFilt; ++q)
+        if (f0 + 16 * q < N) {
+          ubp = fminf(ubp, circle_ub(cc[q], px, py, F.radius, F.inner));
+          ++n_circ;
+        }
+    }
   }
+  const int n_prop = nseg;
   {  // 16-lane minimum (ubp >= 0, so its bits order like the value)
     const unsigned u = __float_as_uint(ubp);
     const unsigned u0 = __reduce_min_sync(kFull, half == 0 ? u : ~0u);
@@ -722,6 +783,9 @@ __global__ void __launch_bounds__(kCullThreads, 2)
           seg_first[pos] = inf.x;
           seg_n[pos] = inf.y;
           seg_pose[pos] = (unsigned char)j;
+          // the tile's obstacle records on their way into this SM's L1
+          // while the round's tile tests finish
+
         }
         used += __popc(m);
       }
@@ -764,6 +828,9 @@ __global__ void __launch_bounds__(kCullThreads, 2)
           keep[q] = o < sn && !(circle_lb_value(cq[q], q4.x, q4.y, F.radius) > tq);
           item[q] = ((sf + o) << 4) | jj;
         }
+        // a survivor's vertex records on their way into L1 while the
+        // queue fills
+
       }
       {  // the warp's survivors appended with one shared-memory atomic
         int mine = 0;
@@ -825,6 +892,9 @@ __global__ void __launch_bounds__(kCullThreads, 2)
             }
             __syncthreads();  // the pass's minima are in
             if (live && g == 0 && key_s[ij] == key) {
+              // this item holds its pose's minimum so far: its detail for
+              // the epilogue (a later pass that finds a smaller key
+              // overwrites it)
               det_s[ij] = ad;
               drec_s[ij] = rec;
             }
@@ -844,7 +914,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     if (!__syncthreads_or(more)) break;
   }
 
-  // ---- counters ------------------------------------------------------------
+  // ---- counters: each warp adds its sums to the CTA's words ---------------
   unsigned cnt[kStCount];
   cnt[kStProp] = (valid && hl == 0) ? (unsigned)n_prop : 0u;
   cnt[kStFb] = (valid && hl == 0) ? (unsigned)n_fb : 0u;
@@ -856,17 +926,15 @@ __global__ void __launch_bounds__(kCullThreads, 2)
 #pragma unroll
   for (int k = 0; k < kStCount; ++k) {
     const unsigned t = __reduce_add_sync(kFull, cnt[k]);
-    if (lane == 0 && t) atomicAdd(&st_s[k], t);
+    if (lane == 0 && t)
+      atomicAdd(&a.ws[kStatBase + (long long)blockIdx.x * kStatWords + k],
+                (unsigned long long)t);
   }
-  __syncthreads();  // every key and counter final
-  if (tid < kStCount)
-    a.ws[kStatBase + (long long)blockIdx.x * kStatWords + tid] = st_s[tid];
   if (blockIdx.x == 0 && tid == 0) {
     a.ws[0] = gridDim.x;
     a.ws[1] = 0ull;  // the cull has no device-side wait
   }
-  const bool save = a.saved != nullptr;
-  const bool want_grad = save || a.dphi != nullptr;
+  // (the rounds ended on a barrier: every key and winner's output is final)
   if constexpr (SOFT) {
     // ---- 5. soft-minimum epilogues: 8 poses a warp, one lane each ----------
     if (warp >= kPoses / 8) return;
@@ -885,34 +953,32 @@ __global__ void __launch_bounds__(kCullThreads, 2)
       write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
     }
   } else {
-    // ---- 5. epilogues of the hard minimum: the winners' details are known;
-    // lane 0 of each pose's half takes the active pair's gradient (two poses
-    // a warp: the per-kind branches of at most two pairs run one after the
-    // other) -----------------------------------------------------------------
-    if (hl != 0) return;
-    const int jj = j;
-    const long long pj = (long long)blockIdx.x * kPoses + jj;
+    // ---- 5. hard minimum: lane 0 of the pose's half takes the active pair's
+    // gradient from the winner's detail (the per-kind branches of a warp's
+    // two poses run one after the other), then 16 lanes store the outputs --
+    const long long pj = (long long)blockIdx.x * kPoses + j;
     if (pj >= a.P) return;
-    const float4 q = pose_s[jj];
-    const bool none = key_s[jj] == ~0ull;
-    PoseOut r{kInf, {0.f, 0.f, 0.f}, PSDF_PAIR_NONE};
-    Grad rows;
-    rows.nrow = -1;
-    if (!none) {
-      const Active ad = det_s[jj];
-      const int4 rc = drec_s[jj];
-      r.pid = ad.pid;
-      r.phi = ad.separated ? sqrtf(ad.val) : ad.val;
-      if (want_grad && (ad.separated || ad.dlt > 0.f)) {
-        rows = active_grad<M>(F, q.x, q.y, q.z, q.w, a.vtx + 2 * (long long)rc.x, a.far + rc.x,
-                              rc.y, rc.z, ad.kind, ad.l, ad.k, ad.t, a.eps_axis);
-        r.g[0] = rows.gp[0];
-        r.g[1] = rows.gp[1];
-        r.g[2] = rows.gp[2];
-      }
+    if (hl == 0 && key_s[j] != ~0ull) {
+      const Active ad = det_s[j];
+      const int4 rec = drec_s[j];
+      const float4 pq = pose_s[j];
+      float *o = out_s[j];
+      o[0] = ad.separated ? sqrtf(ad.val) : ad.val;
+      o[1] = __uint_as_float(ad.pid);
+      Grad rows;
+      rows.nrow = -1;
+      if (want_grad && (ad.separated || ad.dlt > 0.f))
+        rows = active_grad<M>(F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x,
+                              a.far + rec.x, rec.y, rec.z, ad.kind, ad.l, ad.k, ad.t,
+                              a.eps_axis);
+      saved_words(rows, &o[kOutSaved]);
     }
-    write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
-    if (save) write_saved(a.saved, pj, rows);
+    __syncwarp(hmask);
+    const float *o = out_s[j];
+    if (save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = o[kOutSaved + hl];
+    if (hl == 0 && a.phi) a.phi[pj] = o[0];
+    if (hl == 1 && a.active) a.active[pj] = __float_as_uint(o[1]);
+    if (hl >= 2 && hl < 5 && a.dphi) a.dphi[3 * pj + hl - 2] = o[kOutSaved + hl - 2];
   }
 }
 
@@ -1023,12 +1089,16 @@ static size_t cull_workspace_bytes(long long P)
 
 template <int M>
 struct CullCall {
-  static int run(const FootprintK &F, const ParamsK &pk, const CullArgs &a, bool net, dim3 grid,
+  static int run(const FootprintK &F, const ParamsK &pk, const CullArgs &a, int prop, dim3 grid,
                  cudaStream_t st)
   {
     const bool soft = pk.eta > 0.f;
-    auto kern = net ? (soft ? cull_kernel<M, true, true> : cull_kernel<M, true, false>)
-                    : (soft ? cull_kernel<M, false, true> : cull_kernel<M, false, false>);
+    auto kern = prop == kPropNet
+                    ? (soft ? cull_kernel<M, kPropNet, true> : cull_kernel<M, kPropNet, false>)
+                : prop == kPropCircles
+                    ? (soft ? cull_kernel<M, kPropCircles, true>
+                            : cull_kernel<M, kPropCircles, false>)
+                    : (soft ? cull_kernel<M, kPropBound, true> : cull_kernel<M, kPropBound, false>);
     kern<<<grid, kCullThreads, 0, st>>>(F, pk, a);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (cull)");
@@ -1219,7 +1289,8 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   if (rc) return rc;
   if (!opts) return fail(PSDF_ERR_ARG, "opts is NULL");
   if (opts->k < 1 || opts->k > kMaxK) return fail(PSDF_ERR_ARG, "k must be in [1, 4]");
-  if (opts->mode != PSDF_PROPOSE_BOUND && opts->mode != PSDF_PROPOSE_MLP)
+  if (opts->mode != PSDF_PROPOSE_BOUND && opts->mode != PSDF_PROPOSE_MLP &&
+      opts->mode != PSDF_PROPOSE_CIRCLES)
     return fail(PSDF_ERR_ARG, "unknown proposal mode");
   if (opts->mode == PSDF_PROPOSE_MLP && !mlp) return fail(PSDF_ERR_ARG, "mlp is NULL");
   if ((rc = check_out(phi, P, "phi"))) return rc;
@@ -1240,11 +1311,13 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
     return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "cudaMemsetAsync(cull counters)");
   }
   const bool net = opts->mode == PSDF_PROPOSE_MLP;
+  const int prop = net ? kPropNet : opts->mode == PSDF_PROPOSE_CIRCLES ? kPropCircles : kPropBound;
   CullArgs a;
   std::memset(&a, 0, sizeof(a));
   a.poses = poses;
   a.P = P;
   a.grid = scene->grid;
+  a.ub = scene->ubgrid;
   a.tile_ab = scene->d_tile_ab;
   a.tile_info = scene->d_tile_info;
   a.T = scene->n_tiles;
@@ -1274,7 +1347,11 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   {
     const size_t scene_bytes = 32 * (size_t)scene->M + 36 * (size_t)scene->n_edges +
                                16 * (size_t)scene->rows_total +
-                               32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles;
+                               32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles +
+                               (prop == kPropCircles ? sizeof(float4) * kUbCircles *
+                                                           (size_t)scene->ubgrid.nx *
+                                                           scene->ubgrid.ny
+                                                     : 0);
     if (P >= 64 && scene_bytes <= (32u << 20)) {
       auto add = [&](const void *ptr, size_t bytes) {
         bytes &= ~(size_t)15;
@@ -1285,6 +1362,9 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
             a.pf.first[a.pf.n] + ((long long)bytes + kPrefetchChunk - 1) / kPrefetchChunk;
         ++a.pf.n;
       };
+      if (prop == kPropCircles && scene->ubgrid.nx > 0)
+        add(scene->d_ub_circ,
+            sizeof(float4) * kUbCircles * (size_t)scene->ubgrid.nx * scene->ubgrid.ny);
       if (scene->grid.nx > 0 && scene->grid.cap > 0) {
         const size_t slots = (size_t)scene->grid.nx * scene->grid.ny * scene->grid.cap;
         add(scene->d_cell_fab, 16 * slots);
@@ -1305,7 +1385,7 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   }
   ParamsK pk{params->eps_sat, params->eta};
   ProfileScope prof("cull", st);
-  return dispatch_m_cull<CullCall>(m, F, pk, a, net, dim3((unsigned)grid), st);
+  return dispatch_m_cull<CullCall>(m, F, pk, a, prop, dim3((unsigned)grid), st);
 }
 
 extern "C" int psdf_eval_culled(const float *footprint, int32_t m, const psdf_scene *scene,

@@ -1247,9 +1247,9 @@ __device__ __forceinline__ PoseOut epilogue_pose_coop(const FootprintK &F, float
 // Saved backward record of one pose (psdf_saved_grad, 4 float4): the pose
 // gradient of the active pair, its edge-endpoint rows (caller row * 4 +
 // column, d/dx, d/dy), their count, or -1 when the pose has no gradient.
-__device__ __forceinline__ void write_saved(float4 *saved, long long p, const Grad &g)
+// The saved backward record of a pose (16 words) from its gradient rows.
+__device__ __forceinline__ void saved_words(const Grad &g, float *w)
 {
-  float w[16];
   w[0] = g.gp[0];
   w[1] = g.gp[1];
   w[2] = g.gp[2];
@@ -1263,6 +1263,12 @@ __device__ __forceinline__ void write_saved(float4 *saved, long long p, const Gr
   }
   w[13] = w[14] = w[15] = 0.f;
   if (g.nrow < 0) w[0] = w[1] = w[2] = 0.f;
+}
+
+__device__ __forceinline__ void write_saved(float4 *saved, long long p, const Grad &g)
+{
+  float w[16];
+  saved_words(g, w);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     saved[4 * p + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);

@@ -121,6 +121,20 @@ struct CullGrid {
   const int4 *finfo = nullptr;
 };
 
+// Upper-bound grid of the cull: a uniform grid of nx x ny square cells of
+// side 1 / inv_cs from (x0, y0); cell c holds kUbCircles obstacle circles
+// (circ[c * kUbCircles + i], the CullObs circle {cx, cy, r, rin}) chosen for
+// the smallest distance from the farthest point of the cell to the far side
+// of the circle.  Any obstacle's circle bounds phi from above at any pose, so
+// which cell a pose computes affects how tight its bound is, never whether it
+// holds.  Padding: r = inf, rin = -inf (no bound).  nx = 0: no grid.
+constexpr int kUbCircles = 8;
+struct UbGrid {
+  float x0 = 0.f, y0 = 0.f, inv_cs = 0.f;
+  int nx = 0, ny = 0;
+  const float4 *circ = nullptr;
+};
+
 }  // namespace psdf
 
 struct psdf_scene {
@@ -144,6 +158,8 @@ struct psdf_scene {
   int4 *d_cell_info = nullptr;
   float4 *d_cell_fab = nullptr;  // fixed-capacity lists (grid.cap > 0)
   int4 *d_cell_finfo = nullptr;
+  psdf::UbGrid ubgrid;                  // the cull's per-cell upper-bound circles
+  float4 *d_ub_circ = nullptr;
   psdf::CullObs *d_cull_obs = nullptr;  // [M] cull records in sorted order
   float4 *d_tile_ab = nullptr;          // [n_tiles] AABBs
   int4 *d_tile_info = nullptr;          // [n_tiles] TileInfo

@@ -373,6 +373,7 @@ def psdf_backward_saved(scene: Scene, saved, grad_phi, grad_pose, grad_edges,
 NOALLOC_MAX_POSES = 262144
 PROPOSE_BOUND = 1
 PROPOSE_MLP = 2
+PROPOSE_CIRCLES = 3
 
 
 class CullOpts(ctypes.Structure):
@@ -467,12 +468,16 @@ def psdf_cull_stats_read(workspace, stream=None) -> CullStats:
 
 
 def eval_culled(scene: Scene, footprint, poses, mlp: Optional[Mlp] = None, k: int = 2,
-                params: Optional[Params] = None, grad: bool = True, ws=None, stream=None):
-    """(phi, dphi or None, active, workspace) through the exact tile cull."""
+                params: Optional[Params] = None, grad: bool = True, ws=None, stream=None,
+                mode: Optional[int] = None):
+    """(phi, dphi or None, active, workspace) through the exact tile cull;
+    mode defaults to PROPOSE_MLP with a network, else PROPOSE_BOUND."""
     import torch
     prm = params or scene.params
     P = poses.shape[0]
-    opts = CullOpts(PROPOSE_MLP if mlp is not None else PROPOSE_BOUND, k)
+    if mode is None:
+        mode = PROPOSE_MLP if mlp is not None else PROPOSE_BOUND
+    opts = CullOpts(mode, k)
     phi = torch.empty(P, dtype=torch.float32, device=poses.device)
     act = torch.empty(P, dtype=torch.int32, device=poses.device)
     dphi = torch.empty((P, 3), dtype=torch.float32, device=poses.device) if grad else None

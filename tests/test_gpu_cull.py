@@ -27,9 +27,9 @@ def _random_mlp(seed):
     return psdf.Mlp(W1.astype(np.float32), w2.astype(np.float32), 0.25)
 
 
-def _compare_cull(w, scene, poses, mlp=None, k=2):
+def _compare_cull(w, scene, poses, mlp=None, k=2, mode=None):
     phi0, dphi0, act0 = psdf.eval_grad(scene, w.footprint, poses)
-    phi1, dphi1, act1, ws = psdf.eval_culled(scene, w.footprint, poses, mlp=mlp, k=k)
+    phi1, dphi1, act1, ws = psdf.eval_culled(scene, w.footprint, poses, mlp=mlp, k=k, mode=mode)
     st = psdf.psdf_cull_stats_read(ws)
     torch.cuda.synchronize()
     assert np.array_equal(_bits(phi0), _bits(phi1))
@@ -39,15 +39,29 @@ def _compare_cull(w, scene, poses, mlp=None, k=2):
 
 
 @pytest.mark.parametrize("mode,k", [("bound", 1), ("bound", 2), ("bound", 4), ("mlp", 1),
-                                    ("mlp", 3)])
+                                    ("mlp", 3), ("circles", 1)])
 def test_cull_equals_full_scan_dense_clutter(mode, k):
     """4,096 poses x 100,000 edges (the bench workload): every output bit equal."""
     w = sg.dense_clutter(4)
     scene = psdf.Scene.from_csr(w.edges, w.offsets)
     poses = torch.as_tensor(w.poses, device="cuda")
     mlp = _random_mlp(7) if mode == "mlp" else None
-    st = _compare_cull(w, scene, poses, mlp=mlp, k=k)
+    st = _compare_cull(w, scene, poses, mlp=mlp, k=k,
+                       mode=psdf.PROPOSE_CIRCLES if mode == "circles" else None)
     T = scene.info().n_tiles
+    if mode == "circles":
+        # no proposals: the 8 circles of the pose's upper-bound cell, every
+        # listed pair a fallback pair, and no more listed than the bound order
+        # (its proposed tile's circles) lists
+        assert st.proposed_items == 0
+        assert st.circle_evaluations >= 8 * w.P
+        stb = _compare_cull(w, scene, poses, k=1)
+        assert st.fallback_items <= stb.proposed_items + stb.fallback_items
+        assert 0 < st.bound_evaluations < 0.1 * 2 * w.P * T
+        obs_per_tile = w.M / T
+        assert 0 < st.evaluated_obstacles < 0.5 * st.fallback_items * obs_per_tile
+        assert st.evaluated_edges == 4 * st.evaluated_obstacles
+        return
     assert 0 < st.proposed_items <= w.P * k
     assert st.proposed_items + st.fallback_items <= w.P * T
     if mode == "bound":
@@ -65,6 +79,50 @@ def test_cull_equals_full_scan_dense_clutter(mode, k):
     obs_per_tile = w.M / T
     assert 0 < st.evaluated_obstacles < 0.5 * (st.proposed_items + st.fallback_items) * obs_per_tile
     assert st.evaluated_edges == 4 * st.evaluated_obstacles  # rectangles
+
+
+def test_circles_cull_equals_full_scan_across_scenes():
+    """The upper-bound-grid cull (PROPOSE_CIRCLES) on every kind of scene the
+    other tests use: octagon footprint with lidar segments and ragged pose
+    counts, penetrating poses on small tiles, far poses and an empty scene,
+    6,250 tiles, and a scene without a cull grid (1 km segments)."""
+    C = psdf.PROPOSE_CIRCLES
+    w = sg.octagon_lidar(1)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    for P in (w.P, 1, 31, 33, 100):
+        _compare_cull(w, scene, torch.as_tensor(w.poses[:P], device="cuda"), mode=C)
+    w = sg.plain_rect_small(0)
+    g = np.random.default_rng(3)
+    idx = g.integers(0, w.E, size=700)
+    poses_np = np.concatenate([w.edges[idx, 0:2] + g.normal(size=(700, 2)) * 0.4,
+                               g.uniform(-math.pi, math.pi, size=(700, 1))], axis=1)
+    poses = torch.as_tensor(poses_np.astype(np.float32), device="cuda")
+    for te in (4, 16, 64):
+        _compare_cull(w, psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=te), poses, mode=C)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    far = torch.tensor([[500.0, -300.0, 0.1], [-1e4, 1e4, 2.0], [10.0, 10.0, 0.0]], device="cuda")
+    _compare_cull(w, scene, far, mode=C)
+    empty = psdf.Scene.from_csr(np.zeros((0, 4), np.float32), np.zeros(1, np.int32))
+    phi, _, _, _ = psdf.eval_culled(empty, w.footprint, far, mode=C)
+    torch.cuda.synchronize()
+    assert torch.all(torch.isinf(phi))
+    w = sg.dense_clutter(4, n_poses=2048)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets, tile_edges=16)
+    _compare_cull(w, scene, torch.as_tensor(w.poses, device="cuda"), mode=C)
+    g = np.random.default_rng(12)
+    a = g.uniform(0.0, 100.0, size=(400, 2))
+    ang = math.pi / 4 + g.uniform(-0.1, 0.1, size=400)
+    b = a + 1000.0 * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    edges = np.concatenate([a, b], axis=1).astype(np.float32)
+    offs = np.arange(401, dtype=np.int32)
+    scene = psdf.Scene.from_csr(edges, offs, tile_edges=1)
+    assert scene.cull_grid().nx == 0
+    poses_np = np.concatenate([g.uniform(-50.0, 850.0, size=(700, 2)),
+                               g.uniform(-math.pi, math.pi, size=(700, 1))], axis=1)
+    w = sg.Workload("long_segments", sg.footprint_rect(), edges, offs,
+                    poses_np.astype(np.float32))
+    st = _compare_cull(w, scene, torch.as_tensor(w.poses, device="cuda"), mode=C)
+    assert st.proposed_items == 0 and st.bound_evaluations == w.P * 400
 
 
 def test_cull_equals_full_scan_many_tiles():
@@ -155,6 +213,7 @@ def test_cull_grid_cells_holes_and_outside_poses():
     poses = torch.as_tensor(poses_np, device="cuda")
     for mlp, k in ((None, 1), (None, 3), (_random_mlp(5), 1), (_random_mlp(6), 2)):
         _compare_cull(w, scene, poses, mlp=mlp, k=k)
+    _compare_cull(w, scene, poses, mode=psdf.PROPOSE_CIRCLES)
 
 
 def test_cull_without_grid_long_segments():

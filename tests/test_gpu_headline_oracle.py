@@ -1,7 +1,8 @@
 """The dense-clutter workload (4,096 poses x 100,000 edges of 25,000
 rectangles in a 200 x 200 m field, rectangle footprint 0.6 x 0.4 m) against
-the FP64 oracle on every pose: the full scan, the bound-ordered cull and the
-learned cull (the shipped network, k = 1), each through the C ABI -- value
+the FP64 oracle on every pose: the full scan, the bound-ordered cull, the
+learned cull (the shipped network, k = 1) and the upper-bound-grid cull,
+each through the C ABI -- value
 within 1e-5 m, active pair bit-exact (or its antiparallel twin) away from
 FP64 ties, pose gradient within 1e-4 relative -- and the backward from the
 culled forward's saved rows against the oracle's backward (Sec. IV-D, Eq.
@@ -36,13 +37,14 @@ def _run(w, scene, mlp, path):
     if path == "full":
         phi, dphi, act = psdf.eval_grad(scene, w.footprint, poses)
     else:
-        phi, dphi, act, _ws = psdf.eval_culled(scene, w.footprint, poses,
-                                               mlp=mlp if path == "learned" else None, k=1)
+        phi, dphi, act, _ws = psdf.eval_culled(
+            scene, w.footprint, poses, mlp=mlp if path == "learned" else None, k=1,
+            mode=psdf.PROPOSE_CIRCLES if path == "circles" else None)
     torch.cuda.synchronize()
     return {"phi": phi.cpu().numpy(), "pair": psdf.pair_ids(act), "grad": dphi.cpu().numpy()}
 
 
-@pytest.mark.parametrize("path", ["full", "bound", "learned"])
+@pytest.mark.parametrize("path", ["full", "bound", "learned", "circles"])
 def test_dense_clutter_every_pose_matches_oracle(headline, path):
     w, ref, scene, mlp = headline
     gpu = _run(w, scene, mlp, path)
@@ -55,7 +57,7 @@ def test_dense_clutter_every_pose_matches_oracle(headline, path):
     assert st["grad_checked"] >= 0.75 * w.P, st
 
 
-@pytest.mark.parametrize("path", ["bound", "learned"])
+@pytest.mark.parametrize("path", ["bound", "learned", "circles"])
 def test_dense_clutter_backward_from_saved_rows_matches_oracle(headline, path):
     w, ref, scene, mlp = headline
     dev = torch.device("cuda")
@@ -73,7 +75,8 @@ def test_dense_clutter_backward_from_saved_rows_matches_oracle(headline, path):
     act = torch.empty(P, dtype=torch.int32, device=dev)
     saved = torch.empty((P, psdf.SAVED_FLOATS), device=dev)
     cws = torch.empty(psdf.psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8, device=dev)
-    opts = psdf.CullOpts(psdf.PROPOSE_MLP if path == "learned" else psdf.PROPOSE_BOUND, 1)
+    opts = psdf.CullOpts({"learned": psdf.PROPOSE_MLP, "bound": psdf.PROPOSE_BOUND,
+                          "circles": psdf.PROPOSE_CIRCLES}[path], 1)
     psdf.psdf_eval_culled_save(w.footprint, scene, mlp if path == "learned" else None, opts,
                                poses, scene.params, phi, dphi, act, saved, cws)
     gpose = torch.empty((P, 3), device=dev)
