@@ -304,13 +304,18 @@ __device__ __forceinline__ int grid_cell(const CullGrid &g, float px, float py)
   return (int)fy * g.nx + (int)fx;
 }
 
-// The pose's cell in the upper-bound grid, clamped to the grid (a pose
-// outside it takes the nearest cell's circles; any circle is a valid bound).
-__device__ __forceinline__ long long ub_cell(const UbGrid &g, float px, float py)
+// The pose's cell in the candidate grid, clamped to the grid (a pose
+// outside it takes the nearest cell's circles for its bound: any circle is a
+// valid one), and whether the pose lies in it (only then may the cell's list
+// stand for the whole scene).
+__device__ __forceinline__ long long cand_cell(const CandGrid &g, float px, float py, bool &in)
 {
-  const float fx = fminf(fmaxf((px - g.x0) * g.inv_cs, 0.f), (float)(g.nx - 1));
-  const float fy = fminf(fmaxf((py - g.y0) * g.inv_cs, 0.f), (float)(g.ny - 1));
-  return (long long)(int)fy * g.nx + (int)fx;
+  const float fx = __fmul_rn(__fsub_rn(px, g.x0), g.inv_cs);
+  const float fy = __fmul_rn(__fsub_rn(py, g.y0), g.inv_cs);
+  in = fx >= 0.f && fx < (float)g.nx && fy >= 0.f && fy < (float)g.ny;
+  const float cx = fminf(fmaxf(fx, 0.f), (float)(g.nx - 1));
+  const float cy = fminf(fmaxf(fy, 0.f), (float)(g.ny - 1));
+  return (long long)(int)cy * g.nx + (int)cx;
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +337,7 @@ constexpr int kOutSaved = 4;       // out_s: phi, active pair, -, -, the saved r
 constexpr int kOutWords = kOutSaved + 16;
 constexpr int kStatBase = 32;      // first counter word (the header is 256 bytes)
 constexpr long long kPrefetchChunk = 16384;  // bytes per bulk L2 prefetch
-constexpr int kMaxPrefetch = 8;
+constexpr int kMaxPrefetch = 10;
 constexpr unsigned kFull = 0xffffffffu;
 // where the upper bound comes from
 constexpr int kPropBound = 1;    // the circles of the k tiles of smallest bound
@@ -358,7 +363,7 @@ struct CullArgs {
   const float *poses;
   long long P;
   CullGrid grid;
-  UbGrid ub;                // upper-bound circles (kPropCircles)
+  CandGrid cand;            // candidate obstacles per cell (kPropCircles)
   const float4 *tile_ab;    // all tiles: poses outside the grid, bounds beyond its reach
   const int4 *tile_info;
   int T;
@@ -537,12 +542,22 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   const int cell = valid ? grid_cell(a.grid, px, py) : -1;
   Entries E = entries_of(a, cell, cell >= 0);
   if (!valid) E.hi = E.lo;
-  // (upper-bound grid) the pose's cell's circles, one a lane, loaded beside
-  // the cell's tile entries
-  float4 ubc = make_float4(0.f, 0.f, kInf, -kInf);
+  // (candidate grid) the pose's cell's kCand candidates, two a lane, and
+  // its completeness radius, loaded beside the cell's tile entries
+  float4 cc[2] = {make_float4(0.f, 0.f, kInf, -kInf), make_float4(0.f, 0.f, kInf, -kInf)};
+  int co[2] = {-1, -1};
+  float crc = -kInf;
+  bool cin = false;
   if constexpr (CIRC) {
-    if (valid && hl < kUbCircles && a.ub.nx > 0)
-      ubc = __ldg(a.ub.circ + ub_cell(a.ub, px, py) * kUbCircles + hl);
+    if (valid && a.cand.nx > 0) {
+      const long long cc0 = cand_cell(a.cand, px, py, cin) * kCand;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        cc[q] = __ldg(a.cand.circ + cc0 + hl + 16 * q);
+        co[q] = __ldg(a.cand.obs + cc0 + hl + 16 * q);
+      }
+      crc = __ldg(a.cand.rc + cc0 / kCand);
+    }
   }
   // the lane's first two entries (hl, hl + 16) stay in registers for the
   // tile tests below (cell lists rarely hold more than 32)
@@ -676,9 +691,10 @@ __global__ void __launch_bounds__(kCullThreads, 2)
 #pragma unroll
   for (int i = 0; i < kMaxK; ++i) ptile[i] = -1;
   if constexpr (CIRC) {
-    if (valid && hl < kUbCircles) {
-      ubp = circle_ub(ubc, px, py, F.radius, F.inner);
-      ++n_circ;
+    if (valid) {
+      ubp = fminf(circle_ub(cc[0], px, py, F.radius, F.inner),
+                  circle_ub(cc[1], px, py, F.radius, F.inner));
+      n_circ += (co[0] >= 0) + (co[1] >= 0);
     }
   } else {
 #pragma unroll
@@ -735,8 +751,35 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   const bool in_cell = cell >= 0 && cand_radius(ubp, F.radius) <= a.grid.reach_q;
   Entries E2 = entries_of(a, cell, in_cell);
   if (!valid) E2.hi = E2.lo;
-  const bool same = E2.ab == E.ab && E2.lo == E.lo;  // the ranking's entries
+  const bool same = E2.ab == E.ab && E2.lo == E.lo;  // the first entries, in registers
   if (same) E2.hi = E.hi;
+  if constexpr (CIRC) {
+    // A pose in its candidate cell whose bound lies within the cell's
+    // completeness radius needs only the cell's candidates: every unlisted
+    // obstacle is farther than r_foot + UB from it, so it is separated from
+    // the footprint by more than UB (with a margin for this test's
+    // rounding).  Their circle bounds are tested here, the survivors queued
+    // for the first evaluation pass, and the pose takes no tiles.
+    const bool direct = cin && crc > (ubp + F.radius) * (1.f + 1e-6f) + 1e-6f;
+    bool keep[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      keep[q] = direct && co[q] >= 0 && !(circle_lb_value(cc[q], px, py, F.radius) > thr);
+    const int mine = (int)keep[0] + (int)keep[1];
+    int x = mine;  // inclusive prefix over the warp's lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    int base = 0;
+    if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
+    base = __shfl_sync(kFull, base, 31) + x - mine;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (keep[q]) q_s[base++] = (co[q] << 4) | j;
+    if (direct) E2.hi = E2.lo;
+  }
   const int nch = (E2.hi - E2.lo + 15) / 16;
   if (hl == 0) {
     pose_s[j] = make_float4(px, py, c, s);
@@ -801,63 +844,67 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     const int lt = tid & 7;
     int sp = 0, b = 0;  // first segment of the pass, step within the pass
     for (;;) {
-      const int seg = sp + (tid >> 3);
-      const int sn = seg < nsg ? seg_n[seg] : 0;
-      const bool has = b * 8 * kFilt < sn;
-      bool keep[kFilt];
-      int item[kFilt];
-#pragma unroll
-      for (int q = 0; q < kFilt; ++q) {
-        keep[q] = false;
-        item[q] = 0;
-      }
-      if (has) {
-        const int sf = seg_first[seg];
-        const int jj = seg_pose[seg];
-        const float4 q4 = pose_s[jj];
-        const float tq = thr_s[jj];
-        float4 cq[kFilt];
+      // (a round without segments evaluates the queued candidates only)
+      bool done = true;
+      if (nsg > 0) {
+        const int seg = sp + (tid >> 3);
+        const int sn = seg < nsg ? seg_n[seg] : 0;
+        const bool has = b * 8 * kFilt < sn;
+        bool keep[kFilt];
+        int item[kFilt];
 #pragma unroll
         for (int q = 0; q < kFilt; ++q) {
-          const int o = b * 8 * kFilt + lt + 8 * q;
-          if (o < sn) cq[q] = __ldg(&a.obs[sf + o].circ);
+          keep[q] = false;
+          item[q] = 0;
         }
+        if (has) {
+          const int sf = seg_first[seg];
+          const int jj = seg_pose[seg];
+          const float4 q4 = pose_s[jj];
+          const float tq = thr_s[jj];
+          float4 cq[kFilt];
 #pragma unroll
-        for (int q = 0; q < kFilt; ++q) {
-          const int o = b * 8 * kFilt + lt + 8 * q;
-          keep[q] = o < sn && !(circle_lb_value(cq[q], q4.x, q4.y, F.radius) > tq);
-          item[q] = ((sf + o) << 4) | jj;
-        }
-        // a survivor's vertex records on their way into L1 while the
-        // queue fills
+          for (int q = 0; q < kFilt; ++q) {
+            const int o = b * 8 * kFilt + lt + 8 * q;
+            if (o < sn) cq[q] = __ldg(&a.obs[sf + o].circ);
+          }
+#pragma unroll
+          for (int q = 0; q < kFilt; ++q) {
+            const int o = b * 8 * kFilt + lt + 8 * q;
+            keep[q] = o < sn && !(circle_lb_value(cq[q], q4.x, q4.y, F.radius) > tq);
+            item[q] = ((sf + o) << 4) | jj;
+          }
+          // a survivor's vertex records on their way into L1 while the
+          // queue fills
 
-      }
-      {  // the warp's survivors appended with one shared-memory atomic
-        int mine = 0;
-#pragma unroll
-        for (int q = 0; q < kFilt; ++q) mine += keep[q] ? 1 : 0;
-        int x = mine;  // inclusive prefix over the warp's lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, x, o);
-          if (lane >= o) x += y;
         }
-        int base = 0;
-        if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
-        base = __shfl_sync(kFull, base, 31) + x - mine;
+        {  // the warp's survivors appended with one shared-memory atomic
+          int mine = 0;
 #pragma unroll
-        for (int q = 0; q < kFilt; ++q)
-          if (keep[q]) q_s[base++] = item[q];
-      }
-      // the next step: the next block of this pass's segments, or the next pass
-      const bool more_blocks = __syncthreads_or(has && (b + 1) * 8 * kFilt < sn);
-      bool done = false;
-      if (more_blocks) {
-        ++b;
-      } else {
-        b = 0;
-        sp += kSegsPerPass;
-        done = sp >= nsg;
+          for (int q = 0; q < kFilt; ++q) mine += keep[q] ? 1 : 0;
+          int x = mine;  // inclusive prefix over the warp's lanes
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+          }
+          int base = 0;
+          if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
+          base = __shfl_sync(kFull, base, 31) + x - mine;
+#pragma unroll
+          for (int q = 0; q < kFilt; ++q)
+            if (keep[q]) q_s[base++] = item[q];
+        }
+        // the next step: the next block of this pass's segments, or the next pass
+        const bool more_blocks = __syncthreads_or(has && (b + 1) * 8 * kFilt < sn);
+        done = false;
+        if (more_blocks) {
+          ++b;
+        } else {
+          b = 0;
+          sp += kSegsPerPass;
+          done = sp >= nsg;
+        }
       }
       const int nq = nq_s;
       if (done || nq > kQCap - kCullThreads * kFilt) {
@@ -923,12 +970,16 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   cnt[kStCirc] = n_circ;
   cnt[kStObs] = n_obs;
   cnt[kStEdges] = n_edge;
+  {  // the warp's sums, then lane k adds sum k (one atomic instruction)
+    unsigned mine = 0u;
 #pragma unroll
-  for (int k = 0; k < kStCount; ++k) {
-    const unsigned t = __reduce_add_sync(kFull, cnt[k]);
-    if (lane == 0 && t)
-      atomicAdd(&a.ws[kStatBase + (long long)blockIdx.x * kStatWords + k],
-                (unsigned long long)t);
+    for (int k = 0; k < kStCount; ++k) {
+      const unsigned t = __reduce_add_sync(kFull, cnt[k]);
+      mine = lane == k ? t : mine;
+    }
+    if (lane < kStCount && mine)
+      atomicAdd(&a.ws[kStatBase + (long long)blockIdx.x * kStatWords + lane],
+                (unsigned long long)mine);
   }
   if (blockIdx.x == 0 && tid == 0) {
     a.ws[0] = gridDim.x;
@@ -1317,7 +1368,7 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   a.poses = poses;
   a.P = P;
   a.grid = scene->grid;
-  a.ub = scene->ubgrid;
+  a.cand = scene->cand;
   a.tile_ab = scene->d_tile_ab;
   a.tile_info = scene->d_tile_info;
   a.T = scene->n_tiles;
@@ -1348,9 +1399,9 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
     const size_t scene_bytes = 32 * (size_t)scene->M + 36 * (size_t)scene->n_edges +
                                16 * (size_t)scene->rows_total +
                                32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles +
-                               (prop == kPropCircles ? sizeof(float4) * kUbCircles *
-                                                           (size_t)scene->ubgrid.nx *
-                                                           scene->ubgrid.ny
+                               (prop == kPropCircles ? (16 * kCand + 4 * kCand + 4) *
+                                                           (size_t)scene->cand.nx *
+                                                           scene->cand.ny
                                                      : 0);
     if (P >= 64 && scene_bytes <= (32u << 20)) {
       auto add = [&](const void *ptr, size_t bytes) {
@@ -1362,9 +1413,12 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
             a.pf.first[a.pf.n] + ((long long)bytes + kPrefetchChunk - 1) / kPrefetchChunk;
         ++a.pf.n;
       };
-      if (prop == kPropCircles && scene->ubgrid.nx > 0)
-        add(scene->d_ub_circ,
-            sizeof(float4) * kUbCircles * (size_t)scene->ubgrid.nx * scene->ubgrid.ny);
+      if (prop == kPropCircles && scene->cand.nx > 0) {
+        const size_t cells = (size_t)scene->cand.nx * scene->cand.ny;
+        add(scene->d_cand_rc, 4 * cells);
+        add(scene->d_cand_circ, 16 * kCand * cells);
+        add(scene->d_cand_obs, 4 * kCand * cells);
+      }
       if (scene->grid.nx > 0 && scene->grid.cap > 0) {
         const size_t slots = (size_t)scene->grid.nx * scene->grid.ny * scene->grid.cap;
         add(scene->d_cell_fab, 16 * slots);

@@ -121,18 +121,25 @@ struct CullGrid {
   const int4 *finfo = nullptr;
 };
 
-// Upper-bound grid of the cull: a uniform grid of nx x ny square cells of
-// side 1 / inv_cs from (x0, y0); cell c holds kUbCircles obstacle circles
-// (circ[c * kUbCircles + i], the CullObs circle {cx, cy, r, rin}) chosen for
-// the smallest distance from the farthest point of the cell to the far side
-// of the circle.  Any obstacle's circle bounds phi from above at any pose, so
-// which cell a pose computes affects how tight its bound is, never whether it
-// holds.  Padding: r = inf, rin = -inf (no bound).  nx = 0: no grid.
-constexpr int kUbCircles = 8;
-struct UbGrid {
+// Candidate grid of the cull: a uniform grid of nx x ny square cells of
+// side 1 / inv_cs from (x0, y0).  Cell c lists the kCand obstacles whose
+// circles come nearest it -- near distance nd(o) = dist(c_o, cell) - r_o,
+// the cell widened by a margin for the rounding of a pose's cell index --
+// their circles circ[c * kCand + i] (CullObs circle {cx, cy, r, rin}) and
+// sorted obstacle indices obs[c * kCand + i] (-1 and r = inf, rin = -inf:
+// padding), and rc[c], a radius that no unlisted obstacle's near distance
+// falls below (+inf when every obstacle is listed).  Any circle bounds phi
+// from above at any pose; and for a pose in the cell whose upper bound UB
+// satisfies rc - r_foot > UB, every unlisted obstacle is separated from the
+// footprint by more than UB, so the listed ones are all it needs.  nx = 0:
+// no grid.
+constexpr int kCand = 32;
+struct CandGrid {
   float x0 = 0.f, y0 = 0.f, inv_cs = 0.f;
   int nx = 0, ny = 0;
   const float4 *circ = nullptr;
+  const int *obs = nullptr;
+  const float *rc = nullptr;
 };
 
 }  // namespace psdf
@@ -158,8 +165,10 @@ struct psdf_scene {
   int4 *d_cell_info = nullptr;
   float4 *d_cell_fab = nullptr;  // fixed-capacity lists (grid.cap > 0)
   int4 *d_cell_finfo = nullptr;
-  psdf::UbGrid ubgrid;                  // the cull's per-cell upper-bound circles
-  float4 *d_ub_circ = nullptr;
+  psdf::CandGrid cand;                  // the cull's per-cell candidate obstacles
+  float4 *d_cand_circ = nullptr;
+  int *d_cand_obs = nullptr;
+  float *d_cand_rc = nullptr;
   psdf::CullObs *d_cull_obs = nullptr;  // [M] cull records in sorted order
   float4 *d_tile_ab = nullptr;          // [n_tiles] AABBs
   int4 *d_tile_info = nullptr;          // [n_tiles] TileInfo

@@ -86,7 +86,9 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_cell_fab);
   cudaFree(s->d_cell_finfo);
   cudaFree(s->d_cull_obs);
-  cudaFree(s->d_ub_circ);
+  cudaFree(s->d_cand_circ);
+  cudaFree(s->d_cand_obs);
+  cudaFree(s->d_cand_rc);
   cudaFree(s->d_tile_ab);
   cudaFree(s->d_tile_info);
   delete s;
@@ -396,98 +398,114 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
   *cell = (float)cs;
 }
 
-// The upper-bound grid over the scene's bounding box: cells of side
-// sqrt(2 W H / M) (about two circle centres a cell), at most 2048 a side.
-// A cell keeps the kUbCircles circles of smallest score
-//     max over the cell's points q of |q - c| + r
-// (footprint-free: the distance from the cell's farthest point to the far
-// side of the circle) among those it sees: the circles centred within two
-// cells of it, then, in a forward and a backward raster pass, the circles
-// its already visited neighbours keep (as a two-pass distance transform
-// carries the nearest sites across empty space).  The choice only tightens
-// or loosens the bound; every circle bounds phi from above.
-void build_ub_grid(const HostScene &hs, UbGrid *g, std::vector<float4> *circ)
+// The candidate grid over the scene's bounding box: cells of side
+// sqrt(kCand W H / (8 M)) (about kCand / 8 circle centres a cell), at most
+// 2048 a side and 2^17 cells.  For every cell, the kCand obstacles of
+// smallest near distance (to the cell widened by a margin for the rounding
+// of a pose's FP32 cell index) and the radius rc below which no unlisted
+// obstacle's near distance falls.  Obstacles whose circle is no larger than
+// a cell are bucketed by their centre's cell and searched ring by ring (a
+// centre r rings away lies at least (r - 1) cs from the cell, so its near
+// distance is at least (r - 2) cs less the margins), up to kRingMax rings;
+// larger ones are checked by every cell.  rc is the smaller of the
+// (kCand + 1)-th near distance seen and that bound for the rings not
+// searched, rounded down to FP32.
+void build_cand_grid(const HostScene &hs, CandGrid *g, std::vector<float4> *circ,
+                     std::vector<int> *obs, std::vector<float> *rcv)
 {
-  *g = UbGrid();
+  *g = CandGrid();
   circ->clear();
+  obs->clear();
+  rcv->clear();
   const int M = (int)hs.cull_obs.size();
   if (M == 0) return;
   const double x0 = hs.bb[0], y0 = hs.bb[1];
   const double W = (double)hs.bb[2] - x0, H = (double)hs.bb[3] - y0;
-  double cs = std::sqrt(2.0 * std::max(W * H, 1e-12) / M);
+  double cs = std::sqrt(kCand * std::max(W * H, 1e-12) / (8.0 * M));
   cs = std::max({cs, std::max(W, H) / 2047.0, 1e-3});
+  while ((std::floor(W / cs) + 1) * (std::floor(H / cs) + 1) > (double)(1 << 17)) cs *= 1.25;
   const int nx = (int)std::floor(W / cs) + 1, ny = (int)std::floor(H / cs) + 1;
   const size_t cells = (size_t)nx * ny;
-  auto cell_of = [&](double x, double y) {
-    const int i = std::min(nx - 1, std::max(0, (int)std::floor((x - x0) / cs)));
-    const int j = std::min(ny - 1, std::max(0, (int)std::floor((y - y0) / cs)));
+  const double mag = std::fabs(x0) + std::fabs(y0) + (nx + ny) * cs;
+  const double margin = 1e-3 * cs + 1e-6 * mag;
+  // small obstacles bucketed by the cell of their circle's centre
+  std::vector<int> off(cells + 1, 0), ids, large;
+  auto cell_of = [&](const float4 &cc) {
+    const int i = std::min(nx - 1, std::max(0, (int)std::floor((cc.x - x0) / cs)));
+    const int j = std::min(ny - 1, std::max(0, (int)std::floor((cc.y - y0) / cs)));
     return (size_t)j * nx + i;
   };
-  // obstacles bucketed by the cell of their circle's centre
-  std::vector<int> off(cells + 1, 0), ids(M);
-  for (int o = 0; o < M; ++o) ++off[cell_of(hs.cull_obs[o].circ.x, hs.cull_obs[o].circ.y) + 1];
+  for (int o = 0; o < M; ++o) {
+    const float4 cc = hs.cull_obs[o].circ;
+    if (cc.z > cs) large.push_back(o);
+    else ++off[cell_of(cc) + 1];
+  }
+  if ((double)large.size() * (double)cells > 2e8) return;  // no grid: the tile path serves
   for (size_t c = 0; c < cells; ++c) off[c + 1] += off[c];
+  ids.resize(off[cells]);
   {
     std::vector<int> cur(off.begin(), off.end() - 1);
-    for (int o = 0; o < M; ++o)
-      ids[cur[cell_of(hs.cull_obs[o].circ.x, hs.cull_obs[o].circ.y)]++] = o;
+    for (int o = 0; o < M; ++o) {
+      const float4 cc = hs.cull_obs[o].circ;
+      if (!(cc.z > cs)) ids[cur[cell_of(cc)]++] = o;
+    }
   }
-  constexpr int K = kUbCircles;
-  std::vector<int> keep(cells * K, -1);  // per cell: obstacles, best first
-  std::vector<double> kscore(cells * K, INFINITY);
-  auto offer = [&](size_t c, int o) {
-    int *ko = &keep[c * K];
-    double *ks = &kscore[c * K];
-    for (int k = 0; k < K; ++k)
-      if (ko[k] == o) return;
-    const int ci = (int)(c % nx), cj = (int)(c / nx);
-    const double qx0 = x0 + ci * cs, qx1 = qx0 + cs, qy0 = y0 + cj * cs, qy1 = qy0 + cs;
-    const float4 cc = hs.cull_obs[o].circ;
-    const double dx = std::max(std::fabs(cc.x - qx0), std::fabs(cc.x - qx1));
-    const double dy = std::max(std::fabs(cc.y - qy0), std::fabs(cc.y - qy1));
-    const double sc = std::sqrt(dx * dx + dy * dy) + cc.z;
-    if (!(sc < ks[K - 1])) return;
-    int k = K - 1;
-    while (k > 0 && ks[k - 1] > sc) {
-      ks[k] = ks[k - 1];
-      ko[k] = ko[k - 1];
-      --k;
-    }
-    ks[k] = sc;
-    ko[k] = o;
-  };
+  constexpr int K1 = kCand + 1;
+  constexpr int kRingMax = 16;
+  circ->assign(cells * kCand, make_float4(0.f, 0.f, INFINITY, -INFINITY));
+  obs->assign(cells * kCand, -1);
+  rcv->assign(cells, INFINITY);
   for (int cj = 0; cj < ny; ++cj)
-    for (int ci = 0; ci < nx; ++ci)
-      for (int j = std::max(0, cj - 2); j <= std::min(ny - 1, cj + 2); ++j)
-        for (int i = std::max(0, ci - 2); i <= std::min(nx - 1, ci + 2); ++i) {
-          const size_t c = (size_t)j * nx + i;
-          for (int e = off[c]; e < off[c + 1]; ++e) offer((size_t)cj * nx + ci, ids[e]);
-        }
-  auto take = [&](size_t c, int i, int j) {
-    if (i < 0 || i >= nx || j < 0 || j >= ny) return;
-    const int *src = &keep[((size_t)j * nx + i) * K];
-    for (int k = 0; k < K && src[k] >= 0; ++k) offer(c, src[k]);
-  };
-  for (int cj = 0; cj < ny; ++cj)  // forward pass
     for (int ci = 0; ci < nx; ++ci) {
+      const double bx0 = x0 + ci * cs - margin, bx1 = x0 + (ci + 1) * cs + margin;
+      const double by0 = y0 + cj * cs - margin, by1 = y0 + (cj + 1) * cs + margin;
+      double bd[K1];
+      int bo[K1], nb = 0;
+      auto offer = [&](int o) {
+        const float4 cc = hs.cull_obs[o].circ;
+        const double dx = std::max({bx0 - cc.x, (double)cc.x - bx1, 0.0});
+        const double dy = std::max({by0 - cc.y, (double)cc.y - by1, 0.0});
+        const double nd = std::sqrt(dx * dx + dy * dy) - cc.z;
+        if (nb == K1 && !(nd < bd[K1 - 1])) return;
+        int k = nb < K1 ? nb++ : K1 - 1;
+        while (k > 0 && bd[k - 1] > nd) {
+          bd[k] = bd[k - 1];
+          bo[k] = bo[k - 1];
+          --k;
+        }
+        bd[k] = nd;
+        bo[k] = o;
+      };
+      for (int o : large) offer(o);
+      double unseen = INFINITY;  // bound on the near distance of every obstacle not offered
+      for (int r = 0;; ++r) {
+        const double lb_r = (r - 2) * cs - 2 * margin;  // every small obstacle r or more rings away
+        if (nb == K1 && lb_r > bd[K1 - 1]) break;
+        if (r > std::max(nx, ny)) break;  // every cell searched
+        if (r > kRingMax) {
+          unseen = lb_r;
+          break;
+        }
+        for (int j = cj - r; j <= cj + r; ++j) {
+          if (j < 0 || j >= ny) continue;
+          const bool full_row = (r == 0 || j == cj - r || j == cj + r);
+          for (int i = ci - r; i <= ci + r; i += full_row ? 1 : 2 * r) {
+            if (i < 0 || i >= nx) continue;
+            const size_t c = (size_t)j * nx + i;
+            for (int e = off[c]; e < off[c + 1]; ++e) offer(ids[e]);
+          }
+        }
+      }
       const size_t c = (size_t)cj * nx + ci;
-      take(c, ci - 1, cj);
-      take(c, ci - 1, cj - 1);
-      take(c, ci, cj - 1);
-      take(c, ci + 1, cj - 1);
+      for (int k = 0; k < std::min(nb, kCand); ++k) {
+        (*circ)[c * kCand + k] = hs.cull_obs[bo[k]].circ;
+        (*obs)[c * kCand + k] = bo[k];
+      }
+      double rc = std::min(nb == K1 ? bd[K1 - 1] : INFINITY, unseen);
+      float rf = (float)rc;
+      if ((double)rf > rc) rf = std::nextafter(rf, -INFINITY);
+      (*rcv)[c] = rf;
     }
-  for (int cj = ny - 1; cj >= 0; --cj)  // backward pass
-    for (int ci = nx - 1; ci >= 0; --ci) {
-      const size_t c = (size_t)cj * nx + ci;
-      take(c, ci + 1, cj);
-      take(c, ci + 1, cj + 1);
-      take(c, ci, cj + 1);
-      take(c, ci - 1, cj + 1);
-    }
-  circ->assign(cells * K, make_float4(0.f, 0.f, INFINITY, -INFINITY));
-  for (size_t c = 0; c < cells; ++c)
-    for (int k = 0; k < K; ++k)
-      if (keep[c * K + k] >= 0) (*circ)[c * K + k] = hs.cull_obs[keep[c * K + k]].circ;
   g->x0 = hs.bb[0];
   g->y0 = hs.bb[1];
   g->inv_cs = (float)(1.0 / cs);
@@ -523,11 +541,17 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   if (!rc) rc = dev_upload(&s->d_tile_ab, hs.tile_ab, st, &s->device_bytes);
   if (!rc) rc = dev_upload(&s->d_tile_info, hs.tile_info, st, &s->device_bytes);
   {
-    std::vector<float4> ub_circ;
-    build_ub_grid(hs, &s->ubgrid, &ub_circ);
-    if (!rc && s->ubgrid.nx > 0) {
-      rc = dev_upload(&s->d_ub_circ, ub_circ, st, &s->device_bytes);
-      s->ubgrid.circ = s->d_ub_circ;
+    std::vector<float4> cand_circ;
+    std::vector<int> cand_obs;
+    std::vector<float> cand_rc;
+    build_cand_grid(hs, &s->cand, &cand_circ, &cand_obs, &cand_rc);
+    if (!rc && s->cand.nx > 0) {
+      rc = dev_upload(&s->d_cand_circ, cand_circ, st, &s->device_bytes);
+      if (!rc) rc = dev_upload(&s->d_cand_obs, cand_obs, st, &s->device_bytes);
+      if (!rc) rc = dev_upload(&s->d_cand_rc, cand_rc, st, &s->device_bytes);
+      s->cand.circ = s->d_cand_circ;
+      s->cand.obs = s->d_cand_obs;
+      s->cand.rc = s->d_cand_rc;
     }
   }
   std::vector<int> cell_off, cell_tiles;
