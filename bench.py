@@ -6,10 +6,12 @@
 One step = one pass of the value+gradient path over the dense-clutter
 workload (rectangle footprint 0.6 x 0.4 m; 25,000 random-yaw rectangles =
 100,000 edges in a 200 x 200 m field; 4,096 pose queries; synthetic, seeded):
-the exact tile cull (one fused kernel: each pose takes an upper bound from
-the 8 obstacle circles its cell of the scene's upper-bound grid keeps, and
-the CTA evaluates exactly every obstacle of every tile of the pose's cull-grid
-cell whose bounds do not exceed it, then the epilogue with the pose
+the exact cull (one fused kernel: each pose takes an upper bound from the 32
+obstacle circles its cell of the scene's candidate grid keeps; when that
+bound lies within the cell's completeness radius -- every pose of this
+workload -- the candidates whose circle bound does not exceed it are
+evaluated exactly, else every obstacle of every tile of the pose's cull-grid
+cell whose bounds do not exceed it; then the epilogue with the pose
 gradient) followed by PSDF_Backward (pose and edge-endpoint gradients of
 sum(phi)) from the forward's saved rows.  The metric counts pose x edge
 pairs of the whole scene per second (the cull's results equal the full
@@ -223,12 +225,14 @@ def run_reference(a, rank, world):
 # --------------------------------------------------------------------------
 CULL_K = 1
 # Where the headline step's upper bound comes from: "circles" (the scene's
-# upper-bound grid: 8 obstacle circles per cell, no proposal), "bound" (the
-# circles of the tile of smallest AABB bound) or "mlp" (of the trained
-# network's best tile).  On the sort-tile-recursive tiles of this workload the
-# network picks the bound's tile 93 % of the time and adds its ranking to
-# every pose's chain, and the grid needs no ranking at all, so the grid is the
-# fastest exact path; the other two are measured beside it.
+# candidate grid: the 32 obstacle circles nearest each cell, no proposal;
+# with its completeness radius the candidates stand for the whole scene),
+# "bound" (the circles of the tile of smallest AABB bound) or "mlp" (of the
+# trained network's best tile).  On the sort-tile-recursive tiles of this
+# workload the network picks the bound's tile 93 % of the time and adds its
+# ranking to every pose's chain, and the grid needs neither a ranking nor
+# tiles, so the grid is the fastest exact path; the other two are measured
+# beside it.
 HEADLINE_MODE = "circles"
 
 
@@ -766,8 +770,11 @@ def run_b300(a, rank, world, local):
                    "obstacles": w.M, "tiles": T, "footprint_vertices": m,
                    "path": ("%s + pose gradient + backward (from the forward's saved "
                             "rows); %s" % (
-                                {"circles": "exact tile cull, upper bound from the scene's "
-                                            "upper-bound grid (8 obstacle circles per cell)",
+                                {"circles": "exact cull by the scene's candidate grid (each "
+                                            "cell's 32 nearest obstacle circles and a "
+                                            "completeness radius: a pose whose upper bound "
+                                            "lies within it evaluates only those candidates, "
+                                            "any other the tiles of its cull-grid cell)",
                                  "bound": "bound-ordered tile cull (k=%d)" % CULL_K,
                                  "mlp": "learned tile cull (k=%d)" % CULL_K}[HEADLINE_MODE],
                                 "the bound-ordered cull (bound_cull) and the learned proposal "
@@ -816,7 +823,11 @@ def run_b300(a, rank, world, local):
                              - int(st_bound.evaluated_obstacles),
                              "note": "positive = the learned proposal costs more than the "
                                      "bound order"}},
-        "cull": {"candidate_fraction": st.proposed_items / (P * T),
+        "cull": {"candidates_per_pose": st.circle_evaluations / P
+                 if HEADLINE_MODE == "circles" else None,
+                 "tile_path_poses": int(st.fallback_poses) if HEADLINE_MODE == "circles"
+                 else None,
+                 "candidate_fraction": st.proposed_items / (P * T),
                  "evaluated_fraction": items / (P * T),
                  "evaluated_obstacles": int(st.evaluated_obstacles),
                  "evaluated_edges": int(st.evaluated_edges),

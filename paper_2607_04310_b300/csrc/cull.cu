@@ -337,7 +337,7 @@ constexpr int kOutSaved = 4;       // out_s: phi, active pair, -, -, the saved r
 constexpr int kOutWords = kOutSaved + 16;
 constexpr int kStatBase = 32;      // first counter word (the header is 256 bytes)
 constexpr long long kPrefetchChunk = 16384;  // bytes per bulk L2 prefetch
-constexpr int kMaxPrefetch = 10;
+constexpr int kMaxPrefetch = 8;
 constexpr unsigned kFull = 0xffffffffu;
 // where the upper bound comes from
 constexpr int kPropBound = 1;    // the circles of the k tiles of smallest bound
@@ -561,6 +561,8 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   }
   // the lane's first two entries (hl, hl + 16) stay in registers for the
   // tile tests below (cell lists rarely hold more than 32)
+  // (not under the candidate grid, whose poses rarely need tiles: those
+  // that do load their entries in the tile tests)
   float4 kab[2];
   int4 kinf[2];
 #pragma unroll
@@ -568,12 +570,12 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     const int i = E.lo + hl + 16 * q;
     kab[q] = make_float4(kInf, kInf, -kInf, -kInf);
     kinf[q] = make_int4(0, 0, 0, -1);
-    if (i < E.hi) {
+    if (!CIRC && i < E.hi) {
       kab[q] = __ldg(E.ab + i);
       kinf[q] = __ldg(E.info + i);
     }
   }
-  {  // a fixed-capacity list's real entries end at its first padding slot
+  if constexpr (!CIRC) {  // a fixed-capacity list's real entries end at its first padding slot
     const int nreal = __popc(__ballot_sync(kFull, kinf[0].w >= 0) & hmask) +
                       __popc(__ballot_sync(kFull, kinf[1].w >= 0) & hmask);
     if (cell >= 0 && a.grid.cap > 0 && nreal < 32) E.hi = E.lo + nreal;
@@ -751,7 +753,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   const bool in_cell = cell >= 0 && cand_radius(ubp, F.radius) <= a.grid.reach_q;
   Entries E2 = entries_of(a, cell, in_cell);
   if (!valid) E2.hi = E2.lo;
-  const bool same = E2.ab == E.ab && E2.lo == E.lo;  // the first entries, in registers
+  const bool same = !CIRC && E2.ab == E.ab && E2.lo == E.lo;  // the first entries, in registers
   if (same) E2.hi = E.hi;
   if constexpr (CIRC) {
     // A pose in its candidate cell whose bound lies within the cell's
@@ -1394,15 +1396,14 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   a.ws = ws;
   const long long grid = (P + kPoses - 1) / kPoses;
   // the scene into L2 when the launch reads a good part of it and it fits
-  // well within L2 (a few poses on a huge scene read only what they need)
-  {
+  // well within L2 (a few poses on a huge scene read only what they need).
+  // Not for the candidate grid: a pose there reads its cell's candidates and
+  // its survivors' vertex records, a small part of the scene, and measured
+  // faster without the prefetch traffic in front of those reads.
+  if (prop != kPropCircles) {
     const size_t scene_bytes = 32 * (size_t)scene->M + 36 * (size_t)scene->n_edges +
                                16 * (size_t)scene->rows_total +
-                               32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles +
-                               (prop == kPropCircles ? (16 * kCand + 4 * kCand + 4) *
-                                                           (size_t)scene->cand.nx *
-                                                           scene->cand.ny
-                                                     : 0);
+                               32 * (size_t)scene->grid_entries + 32 * (size_t)scene->n_tiles;
     if (P >= 64 && scene_bytes <= (32u << 20)) {
       auto add = [&](const void *ptr, size_t bytes) {
         bytes &= ~(size_t)15;
@@ -1413,12 +1414,6 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
             a.pf.first[a.pf.n] + ((long long)bytes + kPrefetchChunk - 1) / kPrefetchChunk;
         ++a.pf.n;
       };
-      if (prop == kPropCircles && scene->cand.nx > 0) {
-        const size_t cells = (size_t)scene->cand.nx * scene->cand.ny;
-        add(scene->d_cand_rc, 4 * cells);
-        add(scene->d_cand_circ, 16 * kCand * cells);
-        add(scene->d_cand_obs, 4 * kCand * cells);
-      }
       if (scene->grid.nx > 0 && scene->grid.cap > 0) {
         const size_t slots = (size_t)scene->grid.nx * scene->grid.ny * scene->grid.cap;
         add(scene->d_cell_fab, 16 * slots);
@@ -1434,7 +1429,8 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
       add(scene->d_cull_obs, sizeof(CullObs) * (size_t)scene->M);
       add(scene->d_vtx, 32 * (size_t)scene->n_edges);
       add(scene->d_far, 4 * (size_t)scene->n_edges);
-      add(scene->d_row_obs, sizeof(ObsRec) * (size_t)scene->rows_total);
+      // the caller rows' records: only the soft minimum's epilogue reads them
+      if (params->eta > 0.f) add(scene->d_row_obs, sizeof(ObsRec) * (size_t)scene->rows_total);
     }
   }
   ParamsK pk{params->eps_sat, params->eta};
