@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   __shared__ int seg_first[kSegCap], seg_n[kSegCap];
   __shared__ unsigned char seg_pose[kSegCap];
   __shared__ int q_s[kQCap];
+  __shared__ int4 q_rec[CIRC ? kPoses * kCand : 1];  // records of the queued candidates
   __shared__ int nseg_s, nq_s;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
   // (candidate grid) the pose's cell's kCand candidates, two a lane, and
   // its completeness radius, loaded beside the cell's tile entries
   float4 cc[2] = {make_float4(0.f, 0.f, kInf, -kInf), make_float4(0.f, 0.f, kInf, -kInf)};
-  int co[2] = {-1, -1};
+  int4 cr[2] = {make_int4(0, 0, 0, -1), make_int4(0, 0, 0, -1)};
   float crc = -kInf;
   bool cin = false;
   if constexpr (CIRC) {
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         cc[q] = __ldg(a.cand.circ + cc0 + hl + 16 * q);
-        co[q] = __ldg(a.cand.obs + cc0 + hl + 16 * q);
+        cr[q] = __ldg(a.cand.rec + cc0 + hl + 16 * q);
       }
       crc = __ldg(a.cand.rc + cc0 / kCand);
     }
@@ -696,7 +697,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     if (valid) {
       ubp = fminf(circle_ub(cc[0], px, py, F.radius, F.inner),
                   circle_ub(cc[1], px, py, F.radius, F.inner));
-      n_circ += (co[0] >= 0) + (co[1] >= 0);
+      n_circ += (cr[0].y > 0) + (cr[1].y > 0);
     }
   } else {
 #pragma unroll
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     bool keep[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      keep[q] = direct && co[q] >= 0 && !(circle_lb_value(cc[q], px, py, F.radius) > thr);
+      keep[q] = direct && cr[q].y > 0 && !(circle_lb_value(cc[q], px, py, F.radius) > thr);
     const int mine = (int)keep[0] + (int)keep[1];
     int x = mine;  // inclusive prefix over the warp's lanes
 #pragma unroll
@@ -777,9 +778,18 @@ __global__ void __launch_bounds__(kCullThreads, 2)
     int base = 0;
     if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
     base = __shfl_sync(kFull, base, 31) + x - mine;
+    // a queued candidate carries its record in shared memory (the first
+    // items of the round's queue: slot d of q_rec, item ~(16 d + pose)), and
+    // its vertex records start on their way while the round's tiles and
+    // circles are tested
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      if (keep[q]) q_s[base++] = (co[q] << 4) | j;
+      if (keep[q]) {
+        q_rec[base] = cr[q];
+        q_s[base] = ~((base << 4) | j);
+        ++base;
+        prefetch_lines_l2(a.vtx + 2 * (long long)cr[q].x, 32 * cr[q].y);
+      }
     if (direct) E2.hi = E2.lo;
   }
   const int nch = (E2.hi - E2.lo + 15) / 16;
@@ -917,10 +927,13 @@ __global__ void __launch_bounds__(kCullThreads, 2)
           const int slot = b0 + tid / kItemLanes;
           const bool live = slot < nq;
           const int it = live ? q_s[slot] : 0;
-          const int ij = it & 15, so = it >> 4;
+          // a candidate's record is in shared memory, a tile obstacle's in
+          // the cull records
+          const int iv = it < 0 ? ~it : it;
+          const int ij = iv & 15;
           const float4 pq = pose_s[ij];
           int4 rec = make_int4(0, 0, 0, 0);
-          if (live) rec = __ldg(&a.obs[so].rec);
+          if (live) rec = it < 0 ? q_rec[iv >> 4] : __ldg(&a.obs[iv >> 4].rec);
           if constexpr (SOFT) {
             const float v = obstacle_value_coop<M, kItemLanes, true>(
                 F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,

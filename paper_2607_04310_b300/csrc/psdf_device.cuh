@@ -78,6 +78,15 @@ __device__ __forceinline__ void prefetch_lines(const void *p, int bytes)
     asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
 }
 
+// The same into L2 only.
+__device__ __forceinline__ void prefetch_lines_l2(const void *p, int bytes)
+{
+  const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)127, a1 = (uintptr_t)p + (uintptr_t)bytes;
+  int n = 0;
+  for (uintptr_t a = a0; a < a1 && n < 16; a += 128, ++n)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // Total order on float values as unsigned bits (-0 is folded onto +0 first
 // so that the order matches IEEE comparison).
 __device__ __forceinline__ uint32_t ordered_bits(float v)

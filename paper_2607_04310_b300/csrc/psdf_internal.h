@@ -125,10 +125,11 @@ struct CullGrid {
 // side 1 / inv_cs from (x0, y0).  Cell c lists the kCand obstacles whose
 // circles come nearest it -- near distance nd(o) = dist(c_o, cell) - r_o,
 // the cell widened by a margin for the rounding of a pose's cell index --
-// their circles circ[c * kCand + i] (CullObs circle {cx, cy, r, rin}) and
-// sorted obstacle indices obs[c * kCand + i] (-1 and r = inf, rin = -inf:
-// padding), and rc[c], a radius that no unlisted obstacle's near distance
-// falls below (+inf when every obstacle is listed).  Any circle bounds phi
+// their circles circ[c * kCand + i] and records rec[c * kCand + i] (the
+// CullObs circle {cx, cy, r, rin} and record {first vertex record, edges,
+// rank, tile}; padding: r = inf, rin = -inf and no edges), and rc[c], a
+// radius that no unlisted obstacle's near distance falls below (+inf when
+// every obstacle is listed).  Any circle bounds phi
 // from above at any pose; and for a pose in the cell whose upper bound UB
 // satisfies rc - r_foot > UB, every unlisted obstacle is separated from the
 // footprint by more than UB, so the listed ones are all it needs.  nx = 0:
@@ -138,7 +139,7 @@ struct CandGrid {
   float x0 = 0.f, y0 = 0.f, inv_cs = 0.f;
   int nx = 0, ny = 0;
   const float4 *circ = nullptr;
-  const int *obs = nullptr;
+  const int4 *rec = nullptr;
   const float *rc = nullptr;
 };
 
@@ -167,7 +168,7 @@ struct psdf_scene {
   int4 *d_cell_finfo = nullptr;
   psdf::CandGrid cand;                  // the cull's per-cell candidate obstacles
   float4 *d_cand_circ = nullptr;
-  int *d_cand_obs = nullptr;
+  int4 *d_cand_rec = nullptr;
   float *d_cand_rc = nullptr;
   psdf::CullObs *d_cull_obs = nullptr;  // [M] cull records in sorted order
   float4 *d_tile_ab = nullptr;          // [n_tiles] AABBs

@@ -87,7 +87,7 @@ void free_scene(psdf_scene *s)
   cudaFree(s->d_cell_finfo);
   cudaFree(s->d_cull_obs);
   cudaFree(s->d_cand_circ);
-  cudaFree(s->d_cand_obs);
+  cudaFree(s->d_cand_rec);
   cudaFree(s->d_cand_rc);
   cudaFree(s->d_tile_ab);
   cudaFree(s->d_tile_info);
@@ -411,11 +411,11 @@ void build_cull_grid(const HostScene &hs, CullGrid *g, float *cell, std::vector<
 // (kCand + 1)-th near distance seen and that bound for the rings not
 // searched, rounded down to FP32.
 void build_cand_grid(const HostScene &hs, CandGrid *g, std::vector<float4> *circ,
-                     std::vector<int> *obs, std::vector<float> *rcv)
+                     std::vector<int4> *rec, std::vector<float> *rcv)
 {
   *g = CandGrid();
   circ->clear();
-  obs->clear();
+  rec->clear();
   rcv->clear();
   const int M = (int)hs.cull_obs.size();
   if (M == 0) return;
@@ -453,7 +453,7 @@ void build_cand_grid(const HostScene &hs, CandGrid *g, std::vector<float4> *circ
   constexpr int K1 = kCand + 1;
   constexpr int kRingMax = 16;
   circ->assign(cells * kCand, make_float4(0.f, 0.f, INFINITY, -INFINITY));
-  obs->assign(cells * kCand, -1);
+  rec->assign(cells * kCand, make_int4(0, 0, 0, -1));
   rcv->assign(cells, INFINITY);
   for (int cj = 0; cj < ny; ++cj)
     for (int ci = 0; ci < nx; ++ci) {
@@ -499,7 +499,7 @@ void build_cand_grid(const HostScene &hs, CandGrid *g, std::vector<float4> *circ
       const size_t c = (size_t)cj * nx + ci;
       for (int k = 0; k < std::min(nb, kCand); ++k) {
         (*circ)[c * kCand + k] = hs.cull_obs[bo[k]].circ;
-        (*obs)[c * kCand + k] = bo[k];
+        (*rec)[c * kCand + k] = hs.cull_obs[bo[k]].rec;
       }
       double rc = std::min(nb == K1 ? bd[K1 - 1] : INFINITY, unseen);
       float rf = (float)rc;
@@ -542,15 +542,15 @@ int build_scene(const float *rows, int64_t rows_total, const std::vector<ObsIn> 
   if (!rc) rc = dev_upload(&s->d_tile_info, hs.tile_info, st, &s->device_bytes);
   {
     std::vector<float4> cand_circ;
-    std::vector<int> cand_obs;
+    std::vector<int4> cand_rec;
     std::vector<float> cand_rc;
-    build_cand_grid(hs, &s->cand, &cand_circ, &cand_obs, &cand_rc);
+    build_cand_grid(hs, &s->cand, &cand_circ, &cand_rec, &cand_rc);
     if (!rc && s->cand.nx > 0) {
       rc = dev_upload(&s->d_cand_circ, cand_circ, st, &s->device_bytes);
-      if (!rc) rc = dev_upload(&s->d_cand_obs, cand_obs, st, &s->device_bytes);
+      if (!rc) rc = dev_upload(&s->d_cand_rec, cand_rec, st, &s->device_bytes);
       if (!rc) rc = dev_upload(&s->d_cand_rc, cand_rc, st, &s->device_bytes);
       s->cand.circ = s->d_cand_circ;
-      s->cand.obs = s->d_cand_obs;
+      s->cand.rec = s->d_cand_rec;
       s->cand.rc = s->d_cand_rc;
     }
   }
