@@ -3,9 +3,11 @@
     python -m paper_2607_04310_b300.build [--force]
 
 nvcc cross-compiles without a GPU.  Objects are compiled in parallel into
-``_build/`` and linked into ``paper_2607_04310_b300/libpsdf_b300.so``.  With
-PSDF_DEBUG=1 in the environment the objects go to ``_build_debug/`` and are
-compiled with PSDF_DEBUG_CHECKS (index checks in the batched kernels).
+``_build/`` and linked into ``paper_2607_04310_b300/libpsdf_b300.so``.  A second
+library, ``libpsdf_b300_debug.so``, links the same objects except the batched
+kernels, which are compiled again with PSDF_DEBUG_CHECKS (every index they
+take from their data checked, the first violation recorded); the tests load
+it in a process of its own (PSDF_LIBRARY).
 """
 from __future__ import annotations
 
@@ -18,13 +20,14 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-DEBUG = os.environ.get("PSDF_DEBUG", "0") not in ("", "0")
-BUILD = os.path.join(ROOT, "_build_debug" if DEBUG else "_build")
+BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpsdf_b300.so")
+LIB_DEBUG = os.path.join(HERE, "libpsdf_b300_debug.so")
+DEBUG_SOURCES = ("batched.cu",)  # compiled again with the index checks
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr"] + (["-DPSDF_DEBUG_CHECKS"] if DEBUG else [])
+              "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:
@@ -50,35 +53,51 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sources()
-    hdrs = headers()
-    nvcc = _nvcc()
-    objs = []
-    jobs = []
-    for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        objs.append(obj)
-        if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
-            jobs.append(cmd)
-    if jobs:
-        with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
-            results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True),
-                                  jobs))
-        for cmd, r in zip(jobs, results):
-            if r.returncode != 0:
-                raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-            if verbose and (r.stdout or r.stderr):
-                print(r.stdout + r.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+def _run_jobs(jobs, verbose):
+    if not jobs:
+        return
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
+    for cmd, r in zip(jobs, results):
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
+        if verbose and (r.stdout or r.stderr):
+            print(r.stdout + r.stderr)
+
+
+def _link(nvcc, objs, lib, force):
+    if force or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Both libraries, recompiling what is stale; returns the release path."""
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sources()
+    hdrs = headers()
+    nvcc = _nvcc()
+    objs, dobjs, jobs = [], [], []
+    for src in srcs:
+        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        objs.append(obj)
+        if force or _stale(obj, [src] + hdrs):
+            jobs.append([nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj])
+        if os.path.basename(src) in DEBUG_SOURCES:
+            dobj = obj.replace(".o", ".debug.o")
+            dobjs.append(dobj)
+            if force or _stale(dobj, [src] + hdrs):
+                jobs.append([nvcc] + ARCH + NVCC_FLAGS + ["-DPSDF_DEBUG_CHECKS", "-c", src, "-o",
+                                                          dobj])
+        else:
+            dobjs.append(obj)
+    _run_jobs(jobs, verbose)
+    _link(nvcc, objs, LIB, force or bool(jobs))
+    _link(nvcc, dobjs, LIB_DEBUG, force or bool(jobs))
     return LIB
 
 

@@ -14,7 +14,10 @@ from typing import Optional, Tuple
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpsdf_b300.so")
+# PSDF_LIBRARY names another build of the library for this process (the
+# tests run the batched kernels' index-checking build, LIB_DEBUG_PATH, so)
+LIB_PATH = os.environ.get("PSDF_LIBRARY") or os.path.join(HERE, "libpsdf_b300.so")
+LIB_DEBUG_PATH = os.path.join(HERE, "libpsdf_b300_debug.so")
 
 PSDF_OK = 0
 PSDF_ERR_ARG = 1

@@ -41,6 +41,14 @@ def test_every_declared_symbol_is_exported(lib):
     assert declared <= set(psdf.exported_symbols())
 
 
+def test_debug_build_exports_the_same_symbols():
+    """The index-checking build (loaded by the GPU tests in a process of its
+    own) declares the same ABI."""
+    dbg = ctypes.CDLL(psdf.LIB_DEBUG_PATH)
+    for name in sorted(_declared()):
+        assert hasattr(dbg, name), name
+
+
 def test_version_and_workspace(lib):
     assert lib.psdf_version() >= 100
     assert psdf.psdf_workspace_bytes(0) >= 256 + 8

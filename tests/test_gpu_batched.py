@@ -276,7 +276,7 @@ def test_soft_plan_matches_single_scene(eta):
 
 
 def test_zz_no_index_violation_recorded():
-    """Run last in this module: a debug build (PSDF_DEBUG=1) checks every
+    """Run last in this module: the debug build (libpsdf_b300_debug.so) checks every
     index the batched kernels take from their data and records the first
     violation; none may have been seen by the tests above."""
     v, enabled = psdf.psdf_plan_debug_read()
