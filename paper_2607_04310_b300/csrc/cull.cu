@@ -322,16 +322,23 @@ __device__ __forceinline__ long long cand_cell(const CandGrid &g, float px, floa
 // the fused cull: each pose's proposals, exact evaluation and epilogue by
 // its own 16 lanes, in one launch
 // ---------------------------------------------------------------------------
-constexpr int kCullThreads = 256;  // 8 warps x 2 poses
-constexpr int kCullWarps = kCullThreads / 32;
-constexpr int kPoses = 2 * kCullWarps;  // poses per CTA
+// CTA shape: 2 poses a warp.  The proposals' tile path shares its tile and
+// circle tests over 16 poses (256 threads); the candidate grid, whose poses
+// rarely take tiles, waits at its barriers for fewer warps with 8 (128).
+template <int THREADS>
+struct CullShape {
+  static constexpr int kThreads = THREADS;
+  static constexpr int kWarps = THREADS / 32;
+  static constexpr int kPoses = 2 * kWarps;                 // poses per CTA
+  static constexpr int kGroups = THREADS / 4;               // items evaluated per pass
+  static constexpr int kSegCap = kPoses * 16;               // segments of one round
+  static constexpr int kSegsPerPass = THREADS / 8;          // segments whose circles a pass tests
+  static constexpr int kQCap = 2 * THREADS * 8;             // queued items: two steps
+  static constexpr int kMinBlocks = 512 / THREADS;          // 128 registers a thread
+};
 constexpr int kRL = 4;             // best tiles a lane keeps from its ranking pass
 constexpr int kFilt = 8;           // circle bounds a thread tests per block
 constexpr int kItemLanes = 4;      // lanes per evaluated (pose, obstacle) item
-constexpr int kGroups = kCullThreads / kItemLanes;  // items evaluated per pass
-constexpr int kSegCap = kPoses * 16;  // segments of one round: 16 tiles per pose
-constexpr int kSegsPerPass = kCullThreads / 8;  // segments whose circles a pass tests
-constexpr int kQCap = 2 * kCullThreads * kFilt;  // queued (pose, obstacle) items: two steps
 constexpr int kStatWords = 8;      // counters per CTA in the workspace
 constexpr int kOutSaved = 4;       // out_s: phi, active pair, -, -, the saved record
 constexpr int kOutWords = kOutSaved + 16;
@@ -342,7 +349,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // where the upper bound comes from
 constexpr int kPropBound = 1;    // the circles of the k tiles of smallest bound
 constexpr int kPropNet = 2;      // the circles of the network's k best tiles
-constexpr int kPropCircles = 3;  // the pose's cell of the upper-bound grid
+constexpr int kPropCircles = 3;  // the pose's cell of the candidate grid
+template <int PROP>
+using ShapeOf = CullShape<PROP == kPropCircles ? 128 : 256>;
+constexpr int kMinPoses = ShapeOf<kPropCircles>::kPoses;  // the smallest CTA's (workspace sizing)
 
 // Per-CTA counters (workspace words kStatBase + kStatWords * CTA + i).
 enum CullStat { kStProp, kStFb, kStFbPoses, kStBound, kStCirc, kStObs, kStEdges, kStCount };
@@ -435,8 +445,8 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
   return s0[j] + (f - st[j]);
 }
 
-// One CTA = 16 poses; one warp = 2 poses, 16 lanes each (lanes 0-15 pose
-// a, 16-31 pose b) for the per-pose stages:
+// One CTA = 16 poses (8 under the candidate grid); one warp = 2 poses, 16
+// lanes each (lanes 0-15 pose a, 16-31 pose b) for the per-pose stages:
 //  1. ranking (PROP = bound or network): the tiles of the pose's cell in the
 //     cull grid (every tile within one cell size of it), else all tiles;
 //     lane hl takes entries hl, hl + 16, ... and keeps its 4 smallest AABB
@@ -458,8 +468,8 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
 //     pose's UB; the survivors go to one CTA-wide queue, evaluated exactly
 //     by 4 lanes each, and merged into the pose's 64-bit key in shared
 //     memory (atomicMin); the item holding a pose's minimum after a pass
-//     leaves its detail.  Sharing the work over the CTA's 256 threads keeps
-//     a pose with several nearby tiles from stretching its own warp.
+//     leaves its detail.  Sharing the work over the CTA's threads keeps a
+//     pose with several nearby tiles from stretching its own warp.
 //  5. epilogue: the hard minimum's gradient by lane 0 of each pose's half
 //     from the winner's detail, the outputs stored by its 16 lanes; the
 //     soft minimum's by one lane a pose in the first two warps.  Each warp
@@ -468,9 +478,16 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
 // minimum does not depend on the order of evaluation, so the outputs equal
 // the full scan's bit for bit.
 template <int M, int PROP, bool SOFT>
-__global__ void __launch_bounds__(kCullThreads, 2)
+__global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBlocks)
     cull_kernel(const FootprintK F, const ParamsK prm, const CullArgs a)
 {
+  using S = ShapeOf<PROP>;
+  constexpr int kCullThreads = S::kThreads, kCullWarps = S::kWarps, kPoses = S::kPoses;
+  constexpr int kGroups = S::kGroups, kSegCap = S::kSegCap, kSegsPerPass = S::kSegsPerPass;
+  constexpr int kQCap = S::kQCap;
+  static_assert(kGroups == kCullThreads / kItemLanes && kQCap == 2 * kCullThreads * kFilt,
+                "CTA shape");
+  static_assert(kPoses * kCand + kCullThreads * kFilt <= kQCap, "queue too small");
   constexpr bool NET = PROP == kPropNet;
   constexpr bool CIRC = PROP == kPropCircles;
   __shared__ int ub_s0[kCullWarps][2][kMaxK + 1];  // proposed tiles, flattened
@@ -1149,7 +1166,7 @@ __global__ void mlp_scores_kernel(const float *__restrict__ poses, long long P,
 // clear before a launch).
 static size_t cull_workspace_bytes(long long P)
 {
-  const long long ctas = (std::max<long long>(P, 0) + kPoses - 1) / kPoses;
+  const long long ctas = (std::max<long long>(P, 0) + kMinPoses - 1) / kMinPoses;
   return 8 * (size_t)kStatBase + 8 * (size_t)kStatWords * (size_t)std::max<long long>(ctas, 1);
 }
 
@@ -1165,7 +1182,9 @@ struct CullCall {
                     ? (soft ? cull_kernel<M, kPropCircles, true>
                             : cull_kernel<M, kPropCircles, false>)
                     : (soft ? cull_kernel<M, kPropBound, true> : cull_kernel<M, kPropBound, false>);
-    kern<<<grid, kCullThreads, 0, st>>>(F, pk, a);
+    const int threads = prop == kPropCircles ? ShapeOf<kPropCircles>::kThreads
+                                             : ShapeOf<kPropBound>::kThreads;
+    kern<<<grid, threads, 0, st>>>(F, pk, a);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PSDF_OK : cuda_fail(e, "kernel launch (cull)");
   }
@@ -1407,7 +1426,9 @@ static int eval_culled(const float *footprint, int32_t m, const psdf_scene *scen
   a.active = active;
   a.saved = saved;
   a.ws = ws;
-  const long long grid = (P + kPoses - 1) / kPoses;
+  const int cta_poses = prop == kPropCircles ? ShapeOf<kPropCircles>::kPoses
+                                             : ShapeOf<kPropBound>::kPoses;
+  const long long grid = (P + cta_poses - 1) / cta_poses;
   // the scene into L2 when the launch reads a good part of it and it fits
   // well within L2 (a few poses on a huge scene read only what they need).
   // Not for the candidate grid: a pose there reads its cell's candidates and
