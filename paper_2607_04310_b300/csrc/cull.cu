@@ -545,23 +545,9 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
     py = a.poses[3 * p + 1];
     th = a.poses[3 * p + 2];
   }
-  float s, c;
-  sincosf(th, &s, &c);
-  // the CTA's counters, keys and lists initialised (early: every warp is
-  // here at about the same time; nothing below waits for another warp
-  // before the tile tests are in)
-  __syncthreads();
-  MlpFrags w;
-  if constexpr (NET) load_frags(a.frag, lane, w);
-  const int K = a.K;
-  unsigned n_bound = 0, n_circ = 0, n_obs = 0, n_edge = 0;
-
-  // ---- 1. ranking and proposals -------------------------------------------
-  const int cell = valid ? grid_cell(a.grid, px, py) : -1;
-  Entries E = entries_of(a, cell, cell >= 0);
-  if (!valid) E.hi = E.lo;
   // (candidate grid) the pose's cell's kCand candidates, two a lane, and
-  // its completeness radius, loaded beside the cell's tile entries
+  // its completeness radius: the loads that follow the pose's, issued
+  // before the barrier below so that no warp waits for another first
   float4 cc[2] = {make_float4(0.f, 0.f, kInf, -kInf), make_float4(0.f, 0.f, kInf, -kInf)};
   int4 cr[2] = {make_int4(0, 0, 0, -1), make_int4(0, 0, 0, -1)};
   float crc = -kInf;
@@ -577,6 +563,21 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
       crc = __ldg(a.cand.rc + cc0 / kCand);
     }
   }
+  float s, c;
+  sincosf(th, &s, &c);
+  // the CTA's counters, keys and lists initialised (early: every warp is
+  // here at about the same time; nothing below waits for another warp
+  // before the tile tests are in)
+  __syncthreads();
+  MlpFrags w;
+  if constexpr (NET) load_frags(a.frag, lane, w);
+  const int K = a.K;
+  unsigned n_bound = 0, n_circ = 0, n_obs = 0, n_edge = 0;
+
+  // ---- 1. ranking and proposals -------------------------------------------
+  const int cell = valid ? grid_cell(a.grid, px, py) : -1;
+  Entries E = entries_of(a, cell, cell >= 0);
+  if (!valid) E.hi = E.lo;
   // the lane's first two entries (hl, hl + 16) stay in registers for the
   // tile tests below (cell lists rarely hold more than 32)
   // (not under the candidate grid, whose poses rarely need tiles: those
@@ -765,14 +766,8 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
     ubp = __uint_as_float(half ? u1 : u0);
   }
   ubp += a.ub_pad;
-  // every tile whose bound does not exceed UB lies within cand_radius(UB) of
-  // p: the cell's list holds them all while that is within the grid's reach
   const float thr = ub_value(ubp);
-  const bool in_cell = cell >= 0 && cand_radius(ubp, F.radius) <= a.grid.reach_q;
-  Entries E2 = entries_of(a, cell, in_cell);
-  if (!valid) E2.hi = E2.lo;
-  const bool same = !CIRC && E2.ab == E.ab && E2.lo == E.lo;  // the first entries, in registers
-  if (same) E2.hi = E.hi;
+  bool direct = false;
   if constexpr (CIRC) {
     // A pose in its candidate cell whose bound lies within the cell's
     // completeness radius needs only the cell's candidates: every unlisted
@@ -780,35 +775,42 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
     // the footprint by more than UB (with a margin for this test's
     // rounding).  Their circle bounds are tested here, the survivors queued
     // for the first evaluation pass, and the pose takes no tiles.
-    const bool direct = cin && crc > (ubp + F.radius) * (1.f + 1e-6f) + 1e-6f;
+    direct = cin && crc > (ubp + F.radius) * (1.f + 1e-6f) + 1e-6f;
     bool keep[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
       keep[q] = direct && cr[q].y > 0 && !(circle_lb_value(cc[q], px, py, F.radius) > thr);
-    const int mine = (int)keep[0] + (int)keep[1];
-    int x = mine;  // inclusive prefix over the warp's lanes
+    // a survivor's vertex records on their way first (the evaluation reads
+    // them after the next barrier), then its queue slot: the warp's
+    // first-candidate survivors in lane order, then its second-candidate
+    // ones (the order of a pose's items does not change its outputs)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
+    for (int q = 0; q < 2; ++q)
+      if (keep[q]) prefetch_lines_l2(a.vtx + 2 * (long long)cr[q].x, 32 * cr[q].y);
+    const unsigned b0 = __ballot_sync(kFull, keep[0]), b1 = __ballot_sync(kFull, keep[1]);
+    const int tot = __popc(b0) + __popc(b1);
     int base = 0;
-    if (lane == 31 && x > 0) base = atomicAdd(&nq_s, x);
-    base = __shfl_sync(kFull, base, 31) + x - mine;
+    if (lane == 0 && tot > 0) base = atomicAdd(&nq_s, tot);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned lt = (1u << lane) - 1u;
     // a queued candidate carries its record in shared memory (the first
-    // items of the round's queue: slot d of q_rec, item ~(16 d + pose)), and
-    // its vertex records start on their way while the round's tiles and
-    // circles are tested
+    // items of the round's queue: slot d of q_rec, item ~(16 d + pose))
 #pragma unroll
     for (int q = 0; q < 2; ++q)
       if (keep[q]) {
-        q_rec[base] = cr[q];
-        q_s[base] = ~((base << 4) | j);
-        ++base;
-        prefetch_lines_l2(a.vtx + 2 * (long long)cr[q].x, 32 * cr[q].y);
+        const int d = base + (q ? __popc(b0) + __popc(b1 & lt) : __popc(b0 & lt));
+        q_rec[d] = cr[q];
+        q_s[d] = ~((d << 4) | j);
       }
-    if (direct) E2.hi = E2.lo;
   }
+  // every tile whose bound does not exceed UB lies within cand_radius(UB) of
+  // p: the cell's list holds them all while that is within the grid's reach
+  // (a pose that takes only its candidates needs no list)
+  const bool in_cell = cell >= 0 && !direct && cand_radius(ubp, F.radius) <= a.grid.reach_q;
+  Entries E2 = entries_of(a, cell, in_cell);
+  if (!valid || direct) E2.hi = E2.lo;
+  const bool same = !CIRC && E2.ab == E.ab && E2.lo == E.lo;  // the first entries, in registers
+  if (same) E2.hi = E.hi;
   const int nch = (E2.hi - E2.lo + 15) / 16;
   if (hl == 0) {
     pose_s[j] = make_float4(px, py, c, s);
@@ -863,7 +865,7 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
       }
     }
     const bool more = ch < nch;  // this pose has chunks left for later rounds
-    __syncthreads();
+    const bool any_more = __syncthreads_or(more);  // a later round follows
     const int nsg = nseg_s;
     // circle tests: 8 threads per segment, kSegsPerPass segments a pass;
     // thread t takes segment t / 8 (+ kSegsPerPass per pass) and, in step b
@@ -943,6 +945,9 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
         for (int b0 = 0; b0 < nq; b0 += kGroups) {
           const int slot = b0 + tid / kItemLanes;
           const bool live = slot < nq;
+          // a warp's slots are consecutive: one without a live item skips
+          // the evaluation (it still meets the pass's barrier)
+          const bool wlive = b0 + warp * (32 / kItemLanes) < nq;
           const int it = live ? q_s[slot] : 0;
           // a candidate's record is in shared memory, a tile obstacle's in
           // the cull records
@@ -952,18 +957,22 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
           int4 rec = make_int4(0, 0, 0, 0);
           if (live) rec = it < 0 ? q_rec[iv >> 4] : __ldg(&a.obs[iv >> 4].rec);
           if constexpr (SOFT) {
-            const float v = obstacle_value_coop<M, kItemLanes, true>(
-                F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,
-                prm.eta, g);
-            if (live && g == 0) atomicMin(&key_s[ij], pack_key(v, rec.z));
+            if (wlive) {
+              const float v = obstacle_value_coop<M, kItemLanes, true>(
+                  F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, prm.eps_sat,
+                  prm.eta, g);
+              if (live && g == 0) atomicMin(&key_s[ij], pack_key(v, rec.z));
+            }
           } else {
             // the key and the exact detail in one evaluation: the item that
             // holds its pose's minimum after the pass leaves its detail for
             // the epilogue
-            float kv;
-            const Active ad = obstacle_scan_detail_coop<M, kItemLanes>(
-                F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, rec.z,
-                prm.eps_sat, g, kv);
+            float kv = 0.f;
+            Active ad;
+            if (wlive)
+              ad = obstacle_scan_detail_coop<M, kItemLanes>(
+                  F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x, rec.y, rec.z,
+                  prm.eps_sat, g, kv);
             const unsigned long long key = pack_key(kv, rec.z);
             if (live && g == 0) {
               atomicMin(&key_s[ij], key);
@@ -983,17 +992,67 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
             n_edge += (unsigned)rec.y;
           }
         }
-        __syncthreads();  // the queue consumed
-        if (tid == 0) nq_s = 0;
-        __syncthreads();
+        __syncthreads();  // the queue consumed, every winner's detail in
+        if (!done || any_more) {  // the queue fills again
+          if (tid == 0) nq_s = 0;
+          __syncthreads();
+        }
       }
       if (done) break;
     }
+    if (!any_more) break;
     if (tid == 0) nseg_s = 0;
-    if (!__syncthreads_or(more)) break;
+    __syncthreads();
   }
 
-  // ---- counters: each warp adds its sums to the CTA's words ---------------
+  // (the rounds ended on a barrier: every key and winner's output is final)
+  if constexpr (SOFT) {
+    // ---- 5. soft-minimum epilogues: 8 poses a warp, one lane each ----------
+    const int jj = 8 * warp + (lane >> 2);
+    const long long pj = (long long)blockIdx.x * kPoses + jj;
+    const bool vj = warp < kPoses / 8 && pj < a.P;
+    if (vj && (lane & 3) == 0) {
+      const float4 q = pose_s[jj];
+      const unsigned long long key = key_s[jj];
+      const bool none = key == ~0ull;
+      ObsRec o{0, 0, 0, 0};
+      if (!none) o = a.row_obs[(int)(unsigned)(key & 0xffffffffu)];
+      const PoseOut r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z,
+                                                   q.w, none, o, a.vtx, a.far, want_grad,
+                                                   prm.eta);
+      write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
+    }
+  } else {
+    // ---- 5. hard minimum: lane 0 of the pose's half takes the active pair's
+    // gradient from the winner's detail (the per-kind branches of a warp's
+    // two poses run one after the other), then 16 lanes store the outputs --
+    const long long pj = (long long)blockIdx.x * kPoses + j;
+    if (valid && hl == 0 && key_s[j] != ~0ull) {
+      const Active ad = det_s[j];
+      const int4 rec = drec_s[j];
+      const float4 pq = pose_s[j];
+      float *o = out_s[j];
+      o[0] = ad.separated ? sqrtf(ad.val) : ad.val;
+      o[1] = __uint_as_float(ad.pid);
+      Grad rows;
+      rows.nrow = -1;
+      if (want_grad && (ad.separated || ad.dlt > 0.f))
+        rows = active_grad<M>(F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x,
+                              a.far + rec.x, rec.y, rec.z, ad.kind, ad.l, ad.k, ad.t,
+                              a.eps_axis);
+      saved_words(rows, &o[kOutSaved]);
+    }
+    __syncwarp();
+    if (valid) {
+      const float *o = out_s[j];
+      if (save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = o[kOutSaved + hl];
+      if (hl == 0 && a.phi) a.phi[pj] = o[0];
+      if (hl == 1 && a.active) a.active[pj] = __float_as_uint(o[1]);
+      if (hl >= 2 && hl < 5 && a.dphi) a.dphi[3 * pj + hl - 2] = o[kOutSaved + hl - 2];
+    }
+  }
+  // ---- counters, after the outputs: each warp adds its sums to the CTA's
+  // words ------------------------------------------------------------------
   unsigned cnt[kStCount];
   cnt[kStProp] = (valid && hl == 0) ? (unsigned)n_prop : 0u;
   cnt[kStFb] = (valid && hl == 0) ? (unsigned)n_fb : 0u;
@@ -1016,52 +1075,6 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
   if (blockIdx.x == 0 && tid == 0) {
     a.ws[0] = gridDim.x;
     a.ws[1] = 0ull;  // the cull has no device-side wait
-  }
-  // (the rounds ended on a barrier: every key and winner's output is final)
-  if constexpr (SOFT) {
-    // ---- 5. soft-minimum epilogues: 8 poses a warp, one lane each ----------
-    if (warp >= kPoses / 8) return;
-    const int jj = 8 * warp + (lane >> 2);
-    const long long pj = (long long)blockIdx.x * kPoses + jj;
-    const bool vj = pj < a.P;
-    if (vj && (lane & 3) == 0) {
-      const float4 q = pose_s[jj];
-      const unsigned long long key = key_s[jj];
-      const bool none = key == ~0ull;
-      ObsRec o{0, 0, 0, 0};
-      if (!none) o = a.row_obs[(int)(unsigned)(key & 0xffffffffu)];
-      const PoseOut r = epilogue_obstacle<M, true>(F, prm.eps_sat, a.eps_axis, q.x, q.y, q.z,
-                                                   q.w, none, o, a.vtx, a.far, want_grad,
-                                                   prm.eta);
-      write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
-    }
-  } else {
-    // ---- 5. hard minimum: lane 0 of the pose's half takes the active pair's
-    // gradient from the winner's detail (the per-kind branches of a warp's
-    // two poses run one after the other), then 16 lanes store the outputs --
-    const long long pj = (long long)blockIdx.x * kPoses + j;
-    if (pj >= a.P) return;
-    if (hl == 0 && key_s[j] != ~0ull) {
-      const Active ad = det_s[j];
-      const int4 rec = drec_s[j];
-      const float4 pq = pose_s[j];
-      float *o = out_s[j];
-      o[0] = ad.separated ? sqrtf(ad.val) : ad.val;
-      o[1] = __uint_as_float(ad.pid);
-      Grad rows;
-      rows.nrow = -1;
-      if (want_grad && (ad.separated || ad.dlt > 0.f))
-        rows = active_grad<M>(F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x,
-                              a.far + rec.x, rec.y, rec.z, ad.kind, ad.l, ad.k, ad.t,
-                              a.eps_axis);
-      saved_words(rows, &o[kOutSaved]);
-    }
-    __syncwarp(hmask);
-    const float *o = out_s[j];
-    if (save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = o[kOutSaved + hl];
-    if (hl == 0 && a.phi) a.phi[pj] = o[0];
-    if (hl == 1 && a.active) a.active[pj] = __float_as_uint(o[1]);
-    if (hl >= 2 && hl < 5 && a.dphi) a.dphi[3 * pj + hl - 2] = o[kOutSaved + hl - 2];
   }
 }
 
