@@ -1025,7 +1025,8 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
   } else {
     // ---- 5. hard minimum: lane 0 of the pose's half takes the active pair's
     // gradient from the winner's detail (the per-kind branches of a warp's
-    // two poses run one after the other), then 16 lanes store the outputs --
+    // two poses run one after the other), its 16 lanes store the saved
+    // record, and the CTA stores phi, the active pair and the gradient -----
     const long long pj = (long long)blockIdx.x * kPoses + j;
     if (valid && hl == 0 && key_s[j] != ~0ull) {
       const Active ad = det_s[j];
@@ -1043,12 +1044,17 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
       saved_words(rows, &o[kOutSaved]);
     }
     __syncwarp();
-    if (valid) {
-      const float *o = out_s[j];
-      if (save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = o[kOutSaved + hl];
-      if (hl == 0 && a.phi) a.phi[pj] = o[0];
-      if (hl == 1 && a.active) a.active[pj] = __float_as_uint(o[1]);
-      if (hl >= 2 && hl < 5 && a.dphi) a.dphi[3 * pj + hl - 2] = o[kOutSaved + hl - 2];
+    if (valid && save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = out_s[j][kOutSaved + hl];
+    // the CTA's outputs as three contiguous blocks (phi, active pair, pose
+    // gradient): few, full transactions also when they live in host memory
+    __syncthreads();
+    const long long p0 = (long long)blockIdx.x * kPoses;
+    const int np = (int)(a.P - p0 < kPoses ? a.P - p0 : kPoses);
+    if (warp == 0 && lane < np && a.phi) a.phi[p0 + lane] = out_s[lane][0];
+    if (warp == 1 && lane < np && a.active) a.active[p0 + lane] = __float_as_uint(out_s[lane][1]);
+    if (warp >= 2 && a.dphi) {
+      const int i = (warp - 2) * 32 + lane;
+      if (i < 3 * np) a.dphi[3 * p0 + i] = out_s[i / 3][kOutSaved + i % 3];
     }
   }
   // ---- counters, after the outputs: each warp adds its sums to the CTA's
