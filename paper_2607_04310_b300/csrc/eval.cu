@@ -313,26 +313,13 @@ __global__ void backward_saved_kernel(const float4 *__restrict__ saved, long lon
                                       float *__restrict__ grad_edges)
 {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  // cache hints while the forward finishes (prefetches read nothing the
-  // kernel uses before the wait): the incoming gradient's lines, and the edge
-  // gradients the atomics below update, in 16 KB bulk prefetches
+  // a cache hint while the forward finishes (a prefetch reads nothing the
+  // kernel uses before the wait): the incoming gradient's lines.  (The edge
+  // gradients the atomics below update are not prefetched: a bulk prefetch
+  // of the whole buffer competes with a short forward's first reads, which
+  // measured slower on the culled step than the atomics' own misses.)
   if (p < P && (threadIdx.x & 31) == 0)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(grad_phi + p));
-  // (a bulk prefetch needs a 16-byte-aligned start: a caller's buffer that is
-  // not gets no prefetch)
-  if (grad_edges && threadIdx.x == 0 && ((uintptr_t)grad_edges & 15u) == 0) {
-    const long long bytes = 16 * rows_total;
-    if (bytes <= (32ll << 20))
-      for (long long off = 16384ll * blockIdx.x; off < bytes; off += 16384ll * gridDim.x) {
-        const long long rest = bytes - off;
-        const unsigned sz = (unsigned)((rest < 16384 ? rest : 16384) & ~15ll);
-        if (sz)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
-                           reinterpret_cast<const char *>(grad_edges) + off),
-                       "r"(sz)
-                       : "memory");
-      }
-  }
   pdl_wait();  // the records may come from the epilogue just before
   if (p >= P) return;
   const float gphi = grad_phi[p];
