@@ -214,6 +214,42 @@ def test_zero_copy_host_buffers_equal_device_buffers():
     assert ei.value.code == psdf.PSDF_ERR_ARG
 
 
+@pytest.mark.parametrize("mode", [psdf.PROPOSE_CIRCLES, psdf.PROPOSE_BOUND])
+@pytest.mark.parametrize("P", [1, 7, 1021])
+def test_cull_outputs_in_blocks_ragged_host_and_absent(mode, P):
+    """The cull stores each CTA's phi, active pairs and pose gradients as
+    contiguous blocks: with a pose count that fills no whole CTA, outputs in
+    pinned host memory, and some outputs absent, every written value equals
+    the full scan's bit for bit and nothing past the last pose is touched."""
+    w = sg.dense_clutter(4, n_rects=4000, n_poses=1024, field_side=80.0)
+    scene = psdf.Scene.from_csr(w.edges, w.offsets)
+    poses = torch.as_tensor(w.poses[:P].copy(), device=DEV)
+    phi0, dphi0, act0, saved0 = _forward_save(w, scene, poses)
+    opts = psdf.CullOpts(mode, 1)
+    ws = torch.empty(psdf.psdf_cull_workspace_bytes(P, scene), dtype=torch.uint8, device=DEV)
+    # host outputs with a sentinel tail after the last pose
+    h_phi = torch.full((P + 9,), 7.0).pin_memory()
+    h_dphi = torch.full((P + 9, 3), 7.0).pin_memory()
+    h_act = torch.full((P + 9,), 12345, dtype=torch.int32).pin_memory()
+    saved = torch.full((P, psdf.SAVED_FLOATS), float("nan"), device=DEV)
+    psdf.psdf_eval_culled_save(w.footprint, scene, None, opts, poses, scene.params, h_phi[:P],
+                               h_dphi[:P], h_act[:P], saved, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(h_phi[:P].numpy().view(np.uint32), _bits(phi0))
+    assert np.array_equal(h_dphi[:P].numpy().view(np.uint32), _bits(dphi0))
+    assert np.array_equal(h_act[:P].numpy(), act0.cpu().numpy())
+    assert np.array_equal(_bits(saved), _bits(saved0))
+    assert np.all(h_phi[P:].numpy() == 7.0) and np.all(h_dphi[P:].numpy() == 7.0)
+    assert np.all(h_act[P:].numpy() == 12345)
+    # phi alone (no gradient, no active pair) into device memory
+    phi1 = torch.full((P + 9,), 7.0, device=DEV)
+    psdf.psdf_eval_culled(w.footprint, scene, None, opts, poses, scene.params, phi1[:P], None,
+                          None, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(phi1[:P]), _bits(phi0))
+    assert np.all(phi1[P:].cpu().numpy() == 7.0)
+
+
 def test_zero_copy_full_scan_and_backward():
     """The full scan with pinned, device-mapped host poses and outputs, then
     the saved-row backward: the device-buffer results bit for bit."""
