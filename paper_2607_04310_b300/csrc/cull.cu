@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
   static_assert(kGroups == kCullThreads / kItemLanes && kQCap == 2 * kCullThreads * kFilt,
                 "CTA shape");
   static_assert(kPoses * kCand + kCullThreads * kFilt <= kQCap, "queue too small");
+  static_assert(kCullWarps % 4 == 0, "the epilogue gives each warp of a group of four one class");
   constexpr bool NET = PROP == kPropNet;
   constexpr bool CIRC = PROP == kPropCircles;
   __shared__ int ub_s0[kCullWarps][2][kMaxK + 1];  // proposed tiles, flattened
@@ -1023,31 +1024,41 @@ __global__ void __launch_bounds__(ShapeOf<PROP>::kThreads, ShapeOf<PROP>::kMinBl
       write_pose_out(r, pj, a.phi, a.dphi, a.active, nullptr, 0.f);
     }
   } else {
-    // ---- 5. hard minimum: lane 0 of the pose's half takes the active pair's
-    // gradient from the winner's detail (the per-kind branches of a warp's
-    // two poses run one after the other), its 16 lanes store the saved
-    // record, and the CTA stores phi, the active pair and the gradient -----
+    // ---- 5. hard minimum: the active pairs' gradients by kind class, one
+    // class a warp (warp w of each group of four warps takes class w % 4 for
+    // the group's 8 poses, one lane a pose: vertex-edge, vertex-robot edge,
+    // robot axis, obstacle axis), so that no warp runs two classes'
+    // branches one after the other; then each pose's 16 lanes store its
+    // saved record, and the CTA its phi, active pairs and pose gradients as
+    // three contiguous blocks (few, full transactions also when they live
+    // in host memory) ----------------------------------------------------
     const long long pj = (long long)blockIdx.x * kPoses + j;
-    if (valid && hl == 0 && key_s[j] != ~0ull) {
-      const Active ad = det_s[j];
-      const int4 rec = drec_s[j];
-      const float4 pq = pose_s[j];
-      float *o = out_s[j];
-      o[0] = ad.separated ? sqrtf(ad.val) : ad.val;
-      o[1] = __uint_as_float(ad.pid);
-      Grad rows;
-      rows.nrow = -1;
-      if (want_grad && (ad.separated || ad.dlt > 0.f))
-        rows = active_grad<M>(F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x,
-                              a.far + rec.x, rec.y, rec.z, ad.kind, ad.l, ad.k, ad.t,
-                              a.eps_axis);
-      saved_words(rows, &o[kOutSaved]);
+    {
+      const int i = 8 * (warp >> 2) + lane;  // lanes 0-7: the pose this lane may take
+      const long long pi = (long long)blockIdx.x * kPoses + i;
+      if (lane < 8 && pi < a.P && key_s[i] != ~0ull) {
+        const Active ad = det_s[i];
+        const int cls = ad.kind == kVertEdge ? 0
+                        : ad.kind <= kObsBRobotEdge ? 1
+                        : ad.kind <= kRAxisRMaxB ? 2 : 3;
+        if (cls == (warp & 3)) {
+          const int4 rec = drec_s[i];
+          const float4 pq = pose_s[i];
+          float *o = out_s[i];
+          o[0] = ad.separated ? sqrtf(ad.val) : ad.val;
+          o[1] = __uint_as_float(ad.pid);
+          Grad rows;
+          rows.nrow = -1;
+          if (want_grad && (ad.separated || ad.dlt > 0.f))
+            rows = active_grad<M>(F, pq.x, pq.y, pq.z, pq.w, a.vtx + 2 * (long long)rec.x,
+                                  a.far + rec.x, rec.y, rec.z, ad.kind, ad.l, ad.k, ad.t,
+                                  a.eps_axis);
+          saved_words(rows, &o[kOutSaved]);
+        }
+      }
     }
-    __syncwarp();
-    if (valid && save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = out_s[j][kOutSaved + hl];
-    // the CTA's outputs as three contiguous blocks (phi, active pair, pose
-    // gradient): few, full transactions also when they live in host memory
     __syncthreads();
+    if (valid && save) reinterpret_cast<float *>(a.saved)[16 * pj + hl] = out_s[j][kOutSaved + hl];
     const long long p0 = (long long)blockIdx.x * kPoses;
     const int np = (int)(a.P - p0 < kPoses ? a.P - p0 : kPoses);
     if (warp == 0 && lane < np && a.phi) a.phi[p0 + lane] = out_s[lane][0];
