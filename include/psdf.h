@@ -275,29 +275,37 @@ int psdf_backward_saved(const psdf_scene *scene, const float *saved, int64_t P,
                         const float *grad_phi, float *grad_pose, float *grad_edges,
                         void *stream);
 
-/* ---- exact tile cull with a proposal (learned or bound-ordered) ----------
+/* ---- exact tile cull with a proposal (learned or bound-ordered) or the
+ * scene's candidate grid ---------------------------------------------------
  * Same outputs as psdf_eval_grad, bit for bit, while evaluating only part of
- * the (pose, tile) pairs.  Each pose first takes an upper bound UB >= phi
- * from obstacle circles (a circle containing the obstacle, and a disc inside
- * it): under PSDF_PROPOSE_BOUND and PSDF_PROPOSE_MLP from the circles of the
- * obstacles of its k proposed tiles -- the k tiles of smallest bound (BOUND),
- * or the network's k tiles of smallest predicted signed distance among the 8
- * of smallest bound (MLP), among the tiles of the pose's cell in the scene's
- * cull grid (every tile within one cell size of the pose; all tiles for a
- * pose outside the grid); under PSDF_PROPOSE_CIRCLES from the 8 circles the
- * scene keeps for the pose's cell of its upper-bound grid (no proposal: the
- * circles whose far side is nearest the cell, chosen when the scene is
- * built).  Then every tile whose conservative lower bound
+ * the (pose, obstacle) pairs (the exact value of Eq. psdf_value, Sec. IV-D,
+ * over the obstacles that can attain it).  Each pose first takes an upper
+ * bound UB >= phi from obstacle circles (a circle containing the obstacle,
+ * and a disc inside it): under PSDF_PROPOSE_BOUND and PSDF_PROPOSE_MLP from
+ * the circles of the obstacles of its k proposed tiles -- the k tiles of
+ * smallest bound (BOUND), or the network's k tiles of smallest predicted
+ * signed distance among the 8 of smallest bound (MLP), among the tiles of
+ * the pose's cell in the scene's cull grid (every tile within one cell size
+ * of the pose; all tiles for a pose outside the grid); under
+ * PSDF_PROPOSE_CIRCLES from the 32 candidate obstacles the scene keeps for
+ * the pose's cell of its candidate grid (the obstacles whose circles come
+ * nearest the cell, chosen when the scene is built, and a completeness
+ * radius: no unlisted obstacle's circle comes within it of the cell).  A pose in its
+ * candidate cell whose UB plus the footprint radius lies within that radius
+ * needs only the candidates.  Any other pose lists every tile whose
+ * conservative lower bound
  *     LB = dist(p, tile AABB) - r_foot - (1e-4 + 1e-5 dist)
- * does not exceed UB is listed ("fallback" pairs; all listed pairs are
- * fallback pairs under PSDF_PROPOSE_CIRCLES), taken from the cell's list
- * when those tiles all lie within its reach, else from all tiles.  The listed
- * tiles' obstacles whose circle bound exceeds UB are skipped, the rest are
- * evaluated exactly.  No skipped tile or obstacle can hold a smaller value or
- * a tie, so phi, the active pair and the gradient equal the full scan's.  The
- * proposal only changes how much work the exact part does.  One launch: 16
- * poses a CTA, each pose's ranking and bound by 16 lanes, the tile tests,
- * circle tests and exact evaluations shared out over the CTA. */
+ * does not exceed UB ("fallback" pairs; all listed pairs are fallback pairs
+ * under PSDF_PROPOSE_CIRCLES), taken from the cull grid cell's list when
+ * those tiles all lie within its reach, else from all tiles.  The obstacles
+ * whose circle bound exceeds UB are skipped, the rest are evaluated exactly.
+ * No skipped tile or obstacle can hold a smaller value or a tie, so phi, the
+ * active pair and the gradient equal the full scan's.  The proposal only
+ * changes how much work the exact part does.  One launch: 16 poses a CTA (8
+ * under PSDF_PROPOSE_CIRCLES), each pose's ranking and bound by 16 lanes,
+ * the tile tests, circle tests and exact evaluations shared out over the
+ * CTA.  phi, dphi and active may be pinned, device-mapped host memory; each
+ * CTA writes them as contiguous blocks. */
 typedef struct psdf_mlp psdf_mlp; /* opaque: tile-proposal network (device) */
 
 /* The cull grid of a scene: a uniform grid of nx x ny square cells of side
