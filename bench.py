@@ -34,6 +34,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -90,8 +91,16 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
+        self.lines = []
+        self._reader = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append(line)
 
     def __enter__(self):
+        self.lines = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
@@ -99,20 +108,28 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+        if self.proc is not None:
+            self._reader = threading.Thread(target=self._read, daemon=True)
+            self._reader.start()
+            # the timed region starts once nvidia-smi has started up and
+            # taken its first sample (its start-up can take a second on a
+            # fresh box): only the periodic queries overlap the timing
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+                self.proc.wait()
+            if self._reader is not None:
+                self._reader.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -238,11 +255,15 @@ HEADLINE_MODE = "circles"
 
 def _time_steps(step, steps, flush, stream, clocks=None):
     """Device time of each step (CUDA events on the launching stream), L2
-    flushed before every step outside the timed interval."""
+    flushed before every step outside the timed interval.  The steps queue
+    up behind a short device-side wait, so that the host has launched many
+    of them before the device reaches the first (a pause of the host thread
+    then does not leave the device idle inside a timed interval)."""
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     torch.cuda.synchronize()
+    torch.cuda._sleep(2_000_000)  # about 1 ms of device time
     for i in range(steps):
         flush.zero_()
         starts[i].record(stream)
