@@ -455,9 +455,11 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
 //     best network scores among its 8 nearest (2 poses x 8 candidates = 16
 //     rows of one tensor-core pass).
 //  2. an upper bound UB >= phi from the circles of the proposed tiles'
-//     obstacles, or (PROP = circles, no stage 1) from the 8 circles of the
-//     pose's cell in the scene's upper-bound grid, one a lane, loaded beside
-//     the cell's tile entries.
+//     obstacles, or (PROP = circles, no stage 1) from the 32 candidates of
+//     the pose's cell in the scene's candidate grid, two a lane, loaded
+//     right after the pose; a pose whose UB lies within its cell's
+//     completeness radius queues its candidates that pass their circle
+//     test and takes no tiles.
 // then, by the whole CTA, in rounds over chunks of 16 list entries per pose
 // (the cell's list when every tile whose bound does not exceed UB lies
 // within the grid's reach, else all tiles):
@@ -470,10 +472,12 @@ __device__ __forceinline__ int flat_obstacle(const int *s0, const int *st, int n
 //     memory (atomicMin); the item holding a pose's minimum after a pass
 //     leaves its detail.  Sharing the work over the CTA's threads keeps a
 //     pose with several nearby tiles from stretching its own warp.
-//  5. epilogue: the hard minimum's gradient by lane 0 of each pose's half
-//     from the winner's detail, the outputs stored by its 16 lanes; the
-//     soft minimum's by one lane a pose in the first two warps.  Each warp
-//     adds its counters to the CTA's workspace words.
+//  5. epilogue: the hard minimum's gradients from the winners' details by
+//     kind class, one class a warp and one lane a pose, then the saved
+//     records by each pose's 16 lanes and phi, the active pairs and the
+//     gradients as three contiguous blocks; the soft minimum's by one lane
+//     a pose in the first warps.  Each warp then adds its counters to the
+//     CTA's workspace words.
 // No skipped tile or obstacle can hold a value at or below phi, and the key
 // minimum does not depend on the order of evaluation, so the outputs equal
 // the full scan's bit for bit.
